@@ -1,0 +1,220 @@
+/*
+ * pfm.h - C ABI of the GB300 Newton-step solver for the finite-strain
+ * multivariant phase-field model of martensitic transformation
+ * (Tuma, Rezaee-Hajidehi, Hron, Farrell, Stupkiewicz, CMAME 2021).
+ *
+ * The library solves one backward-Euler Newton step of the discrete problem
+ * R(U) = 0 (Sec. 3.4, Eq. FinalRes / Eq. linAlgEq): the residual and tangent
+ * are the first and second derivatives of the penalty-regularised incremental
+ * potential (Eq. PenPot) discretised with trilinear hexahedra on a structured
+ * grid, the linear system is solved by flexible GMRES preconditioned by a
+ * geometric-multigrid V-cycle with point-block (9x9) Jacobi smoothing,
+ * re-discretised coarse operators and a dense direct coarse solve (Sec. 3.4).
+ *
+ * Conventions shared by every entry point:
+ *  - Units: GPa, nm, s.
+ *  - Nodal vectors are field-major "[9][n_nodes]" arrays: fields 0..2 are the
+ *    displacement components u_x, u_y, u_z, fields 3..8 the condensed order
+ *    parameters eta_1..eta_6 (eta_0 = 1 - sum eta_k, Sec. 3.1). Node (i,j,k)
+ *    of an nx*ny*nz grid has index i + (nx+1)*(j + (ny+1)*k).
+ *  - Every pointer documented as "device" is a CUDA device pointer owned by
+ *    the caller; the library reads or writes it on the handle's stream and
+ *    never frees it. "host" pointers are ordinary host memory.
+ *  - Calls are enqueued on the handle's stream (pfm_set_stream; default the
+ *    legacy default stream) and return once enqueued, except where a host
+ *    output is documented (those synchronise the stream).
+ *  - No C++ exception crosses the ABI. Errors are reported as pfm_status and
+ *    a message retrievable with pfm_last_error(handle).
+ *  - Dirichlet DOFs carry a zero residual, and the tangent has identity rows
+ *    and columns there.
+ *  - The library owns its workspaces (allocated with cudaMalloc in
+ *    pfm_create / pfm_set_state / pfm_linearize) and frees them in
+ *    pfm_destroy.
+ */
+#ifndef PFM_H
+#define PFM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pfm_handle pfm_handle;
+
+typedef enum {
+  PFM_OK = 0,
+  PFM_ERR_INVALID_ARG = 1,   /* bad size, null pointer, inconsistent call order */
+  PFM_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has the CUDA error) */
+  PFM_ERR_OOM = 3,           /* device allocation failed */
+  PFM_ERR_NONFINITE = 4,     /* NaN/Inf detected in a residual or Krylov norm */
+  PFM_ERR_NOT_CONVERGED = 5, /* iteration cap reached before the tolerance */
+  PFM_ERR_BREAKDOWN = 6,     /* Krylov breakdown or singular coarse/block matrix */
+  PFM_ERR_TIMEOUT = 7,       /* a bounded device wait gave up */
+  PFM_ERR_STATE = 8          /* required state missing (e.g. no pfm_set_state yet) */
+} pfm_status;
+
+typedef enum { PFM_F32 = 0, PFM_F64 = 1 } pfm_precision;
+
+/* Structured grid of nx*ny*nz trilinear hexahedra on [0,Lx]x[0,Ly]x[0,Lz].
+ * n_levels: multigrid levels (>= 1); level l has ceil(n/2^l) elements per
+ * direction; 0 selects levels down to the first with max(n) <= 4. */
+typedef struct {
+  int nx, ny, nz;
+  double Lx, Ly, Lz;
+  int n_levels;
+} pfm_mesh_desc;
+
+/* Material and time-step data of the model (Sec. 2, Sec. 5.1).
+ * Phase 0 is austenite, phases 1..6 the martensite variants. */
+typedef struct {
+  double Ut[7][9];       /* transformation stretch U_i^t, row-major; Ut[0] = I (Eq. LinMix) */
+  double Lvoigt[7][36];  /* stiffness L_i, 6x6 row-major Voigt matrix acting on the strain
+                            vector (e11,e22,e33,2e23,2e13,2e12) (Eq. elasticEn) */
+  double F0[7];          /* chemical energy F_i^0 (Sec. 2.2) */
+  double mobility[7];    /* m_i (Eq. RateDiss) */
+  double gamma[7][7];    /* interface energy gamma_ij, symmetric, diagonal ignored (Eq. IntEnergy) */
+  double ell[7][7];      /* interface thickness parameter ell_ij, symmetric (Eq. IntEnergy) */
+  double eps_eta;        /* penalty eps_eta (Eq. PenPot) */
+  double tau;            /* time increment tau (Sec. 2.3) */
+  double gamma_scale;    /* multiplier of every gamma_ij (1 for the paper's data) */
+} pfm_params;
+
+typedef struct {
+  int max_newton;        /* Newton iteration cap (>= 1) */
+  int restart;           /* FGMRES restart length m (1..64) */
+  int max_lin_it;        /* cap on FGMRES iterations per linear solve */
+  int nu_pre, nu_post;   /* smoothing sweeps before / after the coarse correction */
+  double newton_rtol;    /* stop when ||R|| <= newton_rtol * ||R_0|| */
+  double lin_rtol;       /* FGMRES: ||b - J x|| <= lin_rtol * ||b|| */
+  double omega;          /* damping of the point-block Jacobi smoother */
+  pfm_precision precond; /* PFM_F32: V-cycle in FP32 inside FP64 FGMRES (mixed);
+                            PFM_F64: every step in FP64 */
+} pfm_solve_opts;
+
+typedef struct {
+  int newton_its;        /* Newton corrections applied */
+  int lin_its_total;     /* FGMRES iterations over all Newton corrections */
+  int lin_its_last;      /* FGMRES iterations of the last correction */
+  double res0;           /* ||R(U_0)||_2 */
+  double res_final;      /* ||R(U)||_2 after the last correction */
+  double lin_res_final;  /* relative FGMRES residual estimate of the last solve */
+  double ms_residual, ms_linearize, ms_solve, ms_total; /* wall times (ms) */
+  pfm_status status;
+} pfm_solve_report;
+
+/* Version string of the library. */
+const char* pfm_version(void);
+
+/* Create a problem on a structured grid with the given parameters and build
+ * the multigrid level hierarchy (Sec. 3.4: uniform refinement hierarchy).
+ * Allocates the level workspaces. *out receives the handle.
+ * Errors: PFM_ERR_INVALID_ARG for non-positive sizes or lengths, PFM_ERR_OOM. */
+pfm_status pfm_create(const pfm_mesh_desc* mesh, const pfm_params* params, pfm_handle** out);
+
+/* Release every device and host resource of the handle. NULL is ignored. */
+void pfm_destroy(pfm_handle* h);
+
+/* Message of the last error on this handle ("" if none); valid until the next
+ * call on the handle. With h == NULL: the last error of pfm_create. */
+const char* pfm_last_error(const pfm_handle* h);
+
+/* Sizes of the finest level. */
+pfm_status pfm_get_sizes(const pfm_handle* h, int64_t* n_nodes, int64_t* n_elems, int* n_levels);
+
+/* Set the CUDA stream (a cudaStream_t passed as void*) used by all later calls. */
+pfm_status pfm_set_stream(pfm_handle* h, void* stream);
+
+/* Replace the material parameters (same mesh). Invalidates the tangent. */
+pfm_status pfm_set_params(pfm_handle* h, const pfm_params* params);
+
+/* Dirichlet data (Sec. 5.1 boundary conditions): mask_dev (device, uint8
+ * [9][n_nodes], 1 = prescribed DOF) and optional val_dev (device, double
+ * [9][n_nodes]; NULL = keep the state's values). When given, prescribed
+ * values are written into the state at pfm_set_state / pfm_newton_solve.
+ * Only the displacement fields (0..2) may be prescribed.
+ * Errors: PFM_ERR_INVALID_ARG if an order-parameter DOF is masked. */
+pfm_status pfm_set_dirichlet(pfm_handle* h, const uint8_t* mask_dev, const double* val_dev);
+
+/* Current iterate U and previous-step state U_n (device, double [9][n_nodes]);
+ * copied into the handle. Invalidates the tangent. */
+pfm_status pfm_set_state(pfm_handle* h, const double* U_dev, const double* Un_dev);
+
+/* Copy the handle's current iterate to U_dev (device, double [9][n_nodes]). */
+pfm_status pfm_get_state(pfm_handle* h, double* U_dev);
+
+/* Residual R = dPi/dU of the discrete incremental potential (Sec. 3.4,
+ * Eq. FinalRes) at the current state, written to R_dev (device, double
+ * [9][n_nodes]), zero at Dirichlet DOFs. If energy_host != NULL the total
+ * potential sum_e sum_q w_q (F + D_tau + penalty) is written there
+ * (synchronises). */
+pfm_status pfm_residual(pfm_handle* h, double* R_dev, double* energy_host);
+
+/* Linearise at the current state (the paper's tangent assembly, Sec. 3.4):
+ * inject the state to every multigrid level, store the 15x15 Gauss-point
+ * Hessians of the local energy (FP64 on the finest level; FP32 copies for an
+ * FP32 preconditioner when precond == PFM_F32, FP64 otherwise), build the
+ * 9x9 nodal block inverses of the point-block Jacobi smoother (dense LU with
+ * partial pivoting) and the dense LU of the coarsest operator. */
+pfm_status pfm_linearize(pfm_handle* h, pfm_precision precond);
+
+/* y = J v with J = dR/dU at the last linearisation (Eq. linAlgEq), matrix
+ * free from the stored Gauss-point Hessians; v_dev, y_dev are device arrays
+ * [9][n_nodes] of float (PFM_F32) or double (PFM_F64). FP32 needs an FP32
+ * tangent (pfm_linearize with PFM_F32). v and y must not alias. */
+pfm_status pfm_jacobian_apply(pfm_handle* h, const void* v_dev, void* y_dev, pfm_precision prec);
+
+/* y = J^T v (adjoint product), same layout and rules as pfm_jacobian_apply. */
+pfm_status pfm_jacobian_transpose_apply(pfm_handle* h, const void* v_dev, void* y_dev,
+                                        pfm_precision prec);
+
+/* pfm_jacobian_apply with HOST arrays: copies v in, applies, copies y out
+ * (synchronises). Uses library-owned device buffers. */
+pfm_status pfm_jacobian_apply_host(pfm_handle* h, const void* v_host, void* y_host,
+                                   pfm_precision prec);
+
+/* One multigrid V-cycle z = M r (Sec. 3.4): nu_pre damped point-block Jacobi
+ * sweeps, restriction of the residual, recursion, dense coarse solve,
+ * prolongation of the correction, nu_post sweeps. r_dev, z_dev: device
+ * [9][n_nodes] in the precision prec (the precision of the preconditioner
+ * built by pfm_linearize). Uses opts->nu_pre, nu_post, omega (NULL = defaults
+ * 2, 2, 0.7). */
+pfm_status pfm_vcycle(pfm_handle* h, const void* r_dev, void* z_dev, pfm_precision prec,
+                      const pfm_solve_opts* opts);
+
+/* Solve J x = b by FGMRES(m) right-preconditioned with the V-cycle, starting
+ * from x = 0 (Sec. 3.4, Eq. linAlgEq). b_dev, x_dev: device double [9][n_nodes].
+ * report (nullable) receives lin_its_last and lin_res_final.
+ * Errors: PFM_ERR_NOT_CONVERGED (x holds the last iterate), PFM_ERR_NONFINITE,
+ * PFM_ERR_BREAKDOWN. */
+pfm_status pfm_fgmres_solve(pfm_handle* h, const pfm_solve_opts* opts, const double* b_dev,
+                            double* x_dev, pfm_solve_report* report);
+
+/* Newton iterations on R(U) = 0 (Sec. 3.4, Eq. linAlgEq): U <- U + dU with
+ * J dU = -R solved by pfm_fgmres_solve, until ||R|| <= newton_rtol ||R_0|| or
+ * max_newton corrections. U_inout_dev (device double [9][n_nodes]) is the
+ * initial iterate on entry and the result on exit; the handle's U_n stays.
+ * Synchronises; report (nullable) gets iteration counts, norms and times. */
+pfm_status pfm_newton_solve(pfm_handle* h, const pfm_solve_opts* opts, double* U_inout_dev,
+                            pfm_solve_report* report);
+
+/* Gauss-point physics for testing: for n points, F (device double [n][9],
+ * row-major), eta_hat and eta_hat_n (device double [n][6]) give the local
+ * energy density W (device double [n]), its gradient (device double
+ * [n][15], z = (F row-major, eta_1..6)) and the packed upper triangle of its
+ * Hessian (device double [n][120], row-major over r <= c; NULL to skip).
+ * Uses the parameters of h and synchronises. */
+pfm_status pfm_qp_eval(pfm_handle* h, int64_t n, const double* F_dev, const double* eta_dev,
+                       const double* eta_n_dev, double* W_dev, double* grad_dev, double* hess_dev);
+
+/* Copy the stored FP64 Gauss-point Hessians of elements [e0, e0+count) of
+ * the finest level to hess_host (host double [count][8][120], Gauss point
+ * q = q0 + 2 q1 + 4 q2). Synchronises. */
+pfm_status pfm_get_hessians(pfm_handle* h, int64_t e0, int64_t count, double* hess_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFM_H */

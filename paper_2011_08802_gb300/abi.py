@@ -1,0 +1,159 @@
+"""ctypes declarations of the C ABI in include/pfm.h and loading of the
+CUDA library (argument marshalling only: every step of the computation runs
+in the library's kernels). The library must have been built (see
+``paper_2011_08802_gb300.build``); importing the binding without it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import inputs
+
+LIB_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib")
+LIB_PATH = os.path.join(LIB_DIR, "libpfm.so")
+
+PFM_F32 = 0
+PFM_F64 = 1
+
+STATUS = {
+    0: "PFM_OK", 1: "PFM_ERR_INVALID_ARG", 2: "PFM_ERR_CUDA", 3: "PFM_ERR_OOM",
+    4: "PFM_ERR_NONFINITE", 5: "PFM_ERR_NOT_CONVERGED", 6: "PFM_ERR_BREAKDOWN",
+    7: "PFM_ERR_TIMEOUT", 8: "PFM_ERR_STATE",
+}
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("Lx", C.c_double), ("Ly", C.c_double), ("Lz", C.c_double),
+                ("n_levels", C.c_int)]
+
+
+class Params(C.Structure):
+    _fields_ = [("Ut", (C.c_double * 9) * 7), ("Lvoigt", (C.c_double * 36) * 7),
+                ("F0", C.c_double * 7), ("mobility", C.c_double * 7),
+                ("gamma", (C.c_double * 7) * 7), ("ell", (C.c_double * 7) * 7),
+                ("eps_eta", C.c_double), ("tau", C.c_double), ("gamma_scale", C.c_double)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("max_newton", C.c_int), ("restart", C.c_int), ("max_lin_it", C.c_int),
+                ("nu_pre", C.c_int), ("nu_post", C.c_int),
+                ("newton_rtol", C.c_double), ("lin_rtol", C.c_double), ("omega", C.c_double),
+                ("precond", C.c_int)]
+
+
+class SolveReport(C.Structure):
+    _fields_ = [("newton_its", C.c_int), ("lin_its_total", C.c_int), ("lin_its_last", C.c_int),
+                ("res0", C.c_double), ("res_final", C.c_double), ("lin_res_final", C.c_double),
+                ("ms_residual", C.c_double), ("ms_linearize", C.c_double),
+                ("ms_solve", C.c_double), ("ms_total", C.c_double), ("status", C.c_int)]
+
+
+def default_opts(precond: int = PFM_F32, **kw) -> SolveOpts:
+    o = SolveOpts(max_newton=1, restart=30, max_lin_it=300, nu_pre=2, nu_post=2,
+                  newton_rtol=1e-8, lin_rtol=1e-8, omega=0.7, precond=precond)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def params_from_material(constants: dict, tau: float, C_override=None,
+                         gamma_scale: float = 1.0) -> Params:
+    """Fill the parameter block from the raw constants of Sec. 5.1: variant
+    stretches U_1..U_6 from (alpha, beta, gamma), the cubic Voigt stiffness
+    from (C11, C12, C44) for every phase, gamma_0i = gamma_am,
+    gamma_ij = gamma_mm, one ell, F_0 = F_a, F_i = F_m, one mobility."""
+    al, be, ga = constants["stretch_alpha"], constants["stretch_beta"], constants["stretch_gamma"]
+    p, q = 0.5 * (al + ga), 0.5 * (al - ga)
+    U = [np.eye(3)]
+    for s in (1.0, -1.0):
+        U.append(np.array([[p, 0, s * q], [0, be, 0], [s * q, 0, p]]))
+    for s in (1.0, -1.0):
+        U.append(np.array([[p, s * q, 0], [s * q, p, 0], [0, 0, be]]))
+    for s in (1.0, -1.0):
+        U.append(np.array([[be, 0, 0], [0, p, s * q], [0, s * q, p]]))
+    C11, C12, C44 = C_override if C_override is not None else (
+        constants["C11"], constants["C12"], constants["C44"])
+    Lv = np.zeros((6, 6))
+    Lv[:3, :3] = C12
+    np.fill_diagonal(Lv[:3, :3], C11)
+    Lv[3, 3] = Lv[4, 4] = Lv[5, 5] = C44
+    P = Params()
+    for i in range(7):
+        for k in range(9):
+            P.Ut[i][k] = U[i].reshape(9)[k]
+        for k in range(36):
+            P.Lvoigt[i][k] = Lv.reshape(36)[k]
+        P.F0[i] = constants["F0_austenite"] if i == 0 else constants["F0_martensite"]
+        P.mobility[i] = constants["mobility"]
+        for j in range(7):
+            g = 0.0 if i == j else (constants["gamma_am"] if (i == 0 or j == 0) else constants["gamma_mm"])
+            P.gamma[i][j] = g
+            P.ell[i][j] = constants["ell"]
+    P.eps_eta = constants["eps_eta"]
+    P.tau = tau
+    P.gamma_scale = gamma_scale
+    return P
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"CUDA library {LIB_PATH} not built: run "
+            "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, i32, dp = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    H = C.c_void_p
+    sig = {
+        "pfm_version": (C.c_char_p, []),
+        "pfm_create": (i32, [C.POINTER(MeshDesc), C.POINTER(Params), C.POINTER(H)]),
+        "pfm_destroy": (None, [H]),
+        "pfm_last_error": (C.c_char_p, [H]),
+        "pfm_get_sizes": (i32, [H, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)]),
+        "pfm_set_stream": (i32, [H, vp]),
+        "pfm_set_params": (i32, [H, C.POINTER(Params)]),
+        "pfm_set_dirichlet": (i32, [H, vp, vp]),
+        "pfm_set_state": (i32, [H, vp, vp]),
+        "pfm_get_state": (i32, [H, vp]),
+        "pfm_residual": (i32, [H, vp, C.POINTER(dp)]),
+        "pfm_linearize": (i32, [H, i32]),
+        "pfm_jacobian_apply": (i32, [H, vp, vp, i32]),
+        "pfm_jacobian_transpose_apply": (i32, [H, vp, vp, i32]),
+        "pfm_jacobian_apply_host": (i32, [H, vp, vp, i32]),
+        "pfm_vcycle": (i32, [H, vp, vp, i32, C.POINTER(SolveOpts)]),
+        "pfm_fgmres_solve": (i32, [H, C.POINTER(SolveOpts), vp, vp, C.POINTER(SolveReport)]),
+        "pfm_newton_solve": (i32, [H, C.POINTER(SolveOpts), vp, C.POINTER(SolveReport)]),
+        "pfm_qp_eval": (i32, [H, i64, vp, vp, vp, vp, vp, vp]),
+        "pfm_get_hessians": (i32, [H, i64, i64, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names of the entry points declared in include/pfm.h."""
+    return [
+        "pfm_version", "pfm_create", "pfm_destroy", "pfm_last_error", "pfm_get_sizes",
+        "pfm_set_stream", "pfm_set_params", "pfm_set_dirichlet", "pfm_set_state", "pfm_get_state",
+        "pfm_residual", "pfm_linearize", "pfm_jacobian_apply", "pfm_jacobian_transpose_apply",
+        "pfm_jacobian_apply_host", "pfm_vcycle", "pfm_fgmres_solve", "pfm_newton_solve",
+        "pfm_qp_eval", "pfm_get_hessians",
+    ]
+
+
+__all__ = ["MeshDesc", "Params", "SolveOpts", "SolveReport", "params_from_material", "lib",
+           "default_opts", "PFM_F32", "PFM_F64", "STATUS", "inputs"]

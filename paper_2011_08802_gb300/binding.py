@@ -1,0 +1,179 @@
+"""Thin Python binding of the C ABI (include/pfm.h). Each method has the name
+of the entry point it calls (without the ``pfm_`` prefix) and only marshals
+arguments: torch CUDA tensors are passed as device pointers, ctypes structs
+as pointers, and a non-zero status raises ``PfmError`` with the library's
+message. No computation happens here.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import abi
+from .abi import PFM_F32, PFM_F64
+
+
+class PfmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{abi.STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensors passed to the library must be contiguous")
+        return C.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to the library must be C-contiguous")
+        return C.c_void_p(t.ctypes.data)
+    return t
+
+
+def _prec(dtype) -> int:
+    if dtype in (torch.float32, np.float32):
+        return PFM_F32
+    if dtype in (torch.float64, np.float64):
+        return PFM_F64
+    raise ValueError(f"unsupported dtype {dtype}")
+
+
+class Problem:
+    """One problem handle (``pfm_create``) on the current CUDA device."""
+
+    def __init__(self, nx: int, ny: int, nz: int, Lx: float, Ly: float, Lz: float,
+                 params: abi.Params, n_levels: int = 0, stream=None):
+        L = abi.lib()
+        self._lib = L
+        desc = abi.MeshDesc(nx, ny, nz, Lx, Ly, Lz, n_levels)
+        h = C.c_void_p()
+        st = L.pfm_create(C.byref(desc), C.byref(params), C.byref(h))
+        if st != 0:
+            raise PfmError(st, L.pfm_last_error(None).decode())
+        self.h = h
+        nn, ne, nl = C.c_int64(), C.c_int64(), C.c_int()
+        self._check(L.pfm_get_sizes(h, C.byref(nn), C.byref(ne), C.byref(nl)))
+        self.n_nodes, self.n_elems, self.n_levels = nn.value, ne.value, nl.value
+        self.shape = (9, self.n_nodes)
+        self.set_stream(stream if stream is not None else torch.cuda.current_stream())
+
+    # -- helpers ---------------------------------------------------------
+    def _check(self, st: int):
+        if st != 0:
+            raise PfmError(st, self._lib.pfm_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.pfm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- entry points ----------------------------------------------------
+    def set_stream(self, stream):
+        self.stream = stream
+        self._check(self._lib.pfm_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
+
+    def set_params(self, params: abi.Params):
+        self._check(self._lib.pfm_set_params(self.h, C.byref(params)))
+
+    def set_dirichlet(self, mask: torch.Tensor, values: torch.Tensor | None = None):
+        assert mask.dtype == torch.uint8 and mask.shape == self.shape
+        if values is not None:
+            assert values.dtype == torch.float64 and values.shape == self.shape
+        self._check(self._lib.pfm_set_dirichlet(self.h, _ptr(mask), _ptr(values)))
+
+    def set_state(self, U: torch.Tensor, Un: torch.Tensor):
+        assert U.dtype == torch.float64 and U.shape == self.shape and Un.shape == self.shape
+        self._check(self._lib.pfm_set_state(self.h, _ptr(U), _ptr(Un)))
+
+    def get_state(self, U: torch.Tensor | None = None) -> torch.Tensor:
+        U = torch.empty(self.shape, dtype=torch.float64, device="cuda") if U is None else U
+        self._check(self._lib.pfm_get_state(self.h, _ptr(U)))
+        return U
+
+    def residual(self, R: torch.Tensor | None = None, energy: bool = False):
+        R = torch.empty(self.shape, dtype=torch.float64, device="cuda") if R is None else R
+        e = C.c_double()
+        self._check(self._lib.pfm_residual(self.h, _ptr(R), C.byref(e) if energy else None))
+        return (R, e.value) if energy else R
+
+    def linearize(self, precond: int = PFM_F32):
+        self._check(self._lib.pfm_linearize(self.h, precond))
+
+    def jacobian_apply(self, v: torch.Tensor, y: torch.Tensor | None = None) -> torch.Tensor:
+        y = torch.empty_like(v) if y is None else y
+        self._check(self._lib.pfm_jacobian_apply(self.h, _ptr(v), _ptr(y), _prec(v.dtype)))
+        return y
+
+    def jacobian_transpose_apply(self, v: torch.Tensor, y: torch.Tensor | None = None) -> torch.Tensor:
+        y = torch.empty_like(v) if y is None else y
+        self._check(self._lib.pfm_jacobian_transpose_apply(self.h, _ptr(v), _ptr(y), _prec(v.dtype)))
+        return y
+
+    def jacobian_apply_host(self, v: np.ndarray | torch.Tensor, y=None):
+        if y is None:
+            y = torch.empty_like(v) if isinstance(v, torch.Tensor) else np.empty_like(v)
+        self._check(self._lib.pfm_jacobian_apply_host(self.h, _ptr(v), _ptr(y), _prec(v.dtype)))
+        return y
+
+    def vcycle(self, r: torch.Tensor, z: torch.Tensor | None = None, opts: abi.SolveOpts | None = None):
+        z = torch.empty_like(r) if z is None else z
+        self._check(self._lib.pfm_vcycle(self.h, _ptr(r), _ptr(z), _prec(r.dtype),
+                                         C.byref(opts) if opts is not None else None))
+        return z
+
+    def fgmres_solve(self, b: torch.Tensor, opts: abi.SolveOpts, x: torch.Tensor | None = None,
+                     check: bool = True):
+        x = torch.empty_like(b) if x is None else x
+        rep = abi.SolveReport()
+        st = self._lib.pfm_fgmres_solve(self.h, C.byref(opts), _ptr(b), _ptr(x), C.byref(rep))
+        if check:
+            self._check(st)
+        return x, rep
+
+    def newton_solve(self, U: torch.Tensor, opts: abi.SolveOpts, check: bool = True):
+        rep = abi.SolveReport()
+        st = self._lib.pfm_newton_solve(self.h, C.byref(opts), _ptr(U), C.byref(rep))
+        if check:
+            self._check(st)
+        return rep
+
+    def qp_eval(self, F: torch.Tensor, eta: torch.Tensor, eta_n: torch.Tensor, hessian: bool = True):
+        n = F.shape[0]
+        W = torch.empty(n, dtype=torch.float64, device="cuda")
+        g = torch.empty(n, 15, dtype=torch.float64, device="cuda")
+        H = torch.empty(n, 120, dtype=torch.float64, device="cuda") if hessian else None
+        self._check(self._lib.pfm_qp_eval(self.h, n, _ptr(F), _ptr(eta), _ptr(eta_n), _ptr(W), _ptr(g), _ptr(H)))
+        return W, g, H
+
+    def get_hessians(self, e0: int, count: int) -> np.ndarray:
+        out = np.empty((count, 8, 120))
+        self._check(self._lib.pfm_get_hessians(self.h, e0, count, _ptr(out)))
+        return out
+
+
+def problem_from_state(state, n_levels: int = 0, params: abi.Params | None = None) -> Problem:
+    """Create a handle for an ``inputs.State`` and load its mask and state."""
+    m = state.mesh
+    if params is None:
+        params = abi.params_from_material(state.material, state.tau)
+    P = Problem(m.nx, m.ny, m.nz, m.Lx, m.Ly, m.Lz, params, n_levels)
+    P.set_dirichlet(torch.from_numpy(state.mask).cuda())
+    P.set_state(torch.from_numpy(state.U).cuda(), torch.from_numpy(state.Un).cuda())
+    return P

@@ -1,0 +1,768 @@
+// C ABI of libpfm (include/pfm.h): problem handle, multigrid hierarchy and
+// the solver drivers (V-cycle, FGMRES, Newton) that sequence the kernels of
+// fe_kernels.cu, mg_kernels.cu and krylov_kernels.cu on one CUDA stream.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "params.h"
+
+using namespace pfm;
+
+namespace {
+
+struct Level {
+  Grid g{};
+  int64_t nn = 0, ne = 0, nblk = 0;
+  double* U = nullptr;
+  double* Un = nullptr;
+  dmask_t* mask = nullptr;
+  double* H64 = nullptr;
+  float* H32 = nullptr;
+  double* D64 = nullptr;
+  float* D32 = nullptr;
+  float *x32 = nullptr, *b32 = nullptr, *y32 = nullptr;
+  double *x64 = nullptr, *b64 = nullptr, *y64 = nullptr;
+};
+
+template <typename T> struct LvVec;
+template <> struct LvVec<float> {
+  static float*& x(Level& l) { return l.x32; }
+  static float*& b(Level& l) { return l.b32; }
+  static float*& y(Level& l) { return l.y32; }
+  static float*& D(Level& l) { return l.D32; }
+  static float*& H(Level& l) { return l.H32; }
+};
+template <> struct LvVec<double> {
+  static double*& x(Level& l) { return l.x64; }
+  static double*& b(Level& l) { return l.b64; }
+  static double*& y(Level& l) { return l.y64; }
+  static double*& D(Level& l) { return l.D64; }
+  static double*& H(Level& l) { return l.H64; }
+};
+
+constexpr int MAX_COARSE_DOFS = 5000;
+constexpr int MAX_RESTART = 64;
+
+std::string g_create_error;
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct pfm_handle {
+  pfm_params params{};
+  DevParams dp{};
+  std::vector<Level> L;
+  cudaStream_t stream = 0;
+  std::string err;
+  bool have_state = false;
+  bool have_dirval = false;
+  bool linearized = false;
+  pfm_precision lin_prec = PFM_F64;
+  double* dirval = nullptr;
+  double* energy_dev = nullptr;
+  int* flag_dev = nullptr;
+  // solver work (finest level, FP64)
+  double* R = nullptr;
+  double* dU = nullptr;
+  double* wv = nullptr;
+  double* rv = nullptr;
+  double* zd = nullptr;
+  double* partial = nullptr;
+  double* hdev = nullptr;
+  // Krylov basis
+  int kry_m = 0;
+  pfm_precision kry_prec = PFM_F64;
+  double* V = nullptr;
+  void* Z = nullptr;
+  // coarse dense operator [K | I] -> [I | K^-1]
+  double* Kaug = nullptr;
+  double* gjf = nullptr;
+  int nc_dofs = 0;
+  // staging for the host-buffer entry point
+  void* stage_in = nullptr;
+  void* stage_out = nullptr;
+
+  pfm_status fail(pfm_status s, const std::string& m) {
+    err = m;
+    return s;
+  }
+};
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return h->fail(e_ == cudaErrorMemoryAllocation ? PFM_ERR_OOM : PFM_ERR_CUDA,            \
+                     std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+  } while (0)
+
+#define CKL()                                                                                 \
+  do {                                                                                        \
+    cudaError_t e_ = cudaGetLastError();                                                      \
+    if (e_ != cudaSuccess)                                                                    \
+      return h->fail(PFM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_));  \
+  } while (0)
+
+#define TRY(expr)                     \
+  do {                                \
+    pfm_status s_ = (expr);           \
+    if (s_ != PFM_OK) return s_;      \
+  } while (0)
+
+namespace {
+
+template <typename T>
+pfm_status dalloc(pfm_handle* h, T** p, size_t count) {
+  if (*p) return PFM_OK;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count > 0 ? count : 1));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return h->fail(PFM_ERR_OOM, std::string("cudaMalloc of ") + std::to_string(sizeof(T) * count) +
+                                    " bytes failed: " + cudaGetErrorString(e));
+  }
+  return PFM_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+int64_t ndof(const Level& l) { return int64_t(NF) * l.nn; }
+
+// ---------------------------------------------------------------------------
+// V-cycle (Sec. 3.4): pre-smooth, restrict, recurse, coarse solve, prolong, post-smooth.
+template <typename T>
+pfm_status vcycle_level(pfm_handle* h, size_t l, int nu_pre, int nu_post, T omega) {
+  Level& lv = h->L[l];
+  cudaStream_t s = h->stream;
+  T* x = LvVec<T>::x(lv);
+  T* b = LvVec<T>::b(lv);
+  T* y = LvVec<T>::y(lv);
+  if (l + 1 == h->L.size()) {
+    launch_coarse_solve<T>(h->nc_dofs, h->Kaug, b, x, s);
+    CKL();
+    return PFM_OK;
+  }
+  const T* H = LvVec<T>::H(lv);
+  const T* D = LvVec<T>::D(lv);
+  const int64_t n = ndof(lv);
+  CK(cudaMemsetAsync(x, 0, sizeof(T) * n, s));
+  launch_smooth<T>(lv.nn, D, b, nullptr, omega, x, s);
+  for (int k = 1; k < nu_pre; ++k) {
+    launch_japply<T>(lv.g, h->dp, H, lv.mask, x, y, s);
+    launch_smooth<T>(lv.nn, D, b, y, omega, x, s);
+  }
+  launch_japply<T>(lv.g, h->dp, H, lv.mask, x, y, s);
+  launch_sub<T>(n, b, y, y, s);
+  Level& cv = h->L[l + 1];
+  launch_restrict<T>(lv.g, cv.g, y, cv.mask, LvVec<T>::b(cv), s);
+  CKL();
+  TRY(vcycle_level<T>(h, l + 1, nu_pre, nu_post, omega));
+  launch_prolong_add<T>(lv.g, cv.g, LvVec<T>::x(cv), lv.mask, x, s);
+  for (int k = 0; k < nu_post; ++k) {
+    launch_japply<T>(lv.g, h->dp, H, lv.mask, x, y, s);
+    launch_smooth<T>(lv.nn, D, b, y, omega, x, s);
+  }
+  CKL();
+  return PFM_OK;
+}
+
+template <typename T>
+pfm_status ensure_level_vectors(pfm_handle* h) {
+  for (auto& lv : h->L) {
+    TRY(dalloc(h, &LvVec<T>::x(lv), ndof(lv)));
+    TRY(dalloc(h, &LvVec<T>::b(lv), ndof(lv)));
+    TRY(dalloc(h, &LvVec<T>::y(lv), ndof(lv)));
+  }
+  return PFM_OK;
+}
+
+// z = M r with r, z in the preconditioner's precision (device arrays of the finest level).
+template <typename T>
+pfm_status apply_vcycle(pfm_handle* h, const T* r, T* z, int nu_pre, int nu_post, double omega) {
+  TRY(ensure_level_vectors<T>(h));
+  Level& f = h->L[0];
+  CK(cudaMemcpyAsync(LvVec<T>::b(f), r, sizeof(T) * ndof(f), cudaMemcpyDeviceToDevice, h->stream));
+  TRY(vcycle_level<T>(h, 0, nu_pre, nu_post, T(omega)));
+  CK(cudaMemcpyAsync(z, LvVec<T>::x(f), sizeof(T) * ndof(f), cudaMemcpyDeviceToDevice, h->stream));
+  return PFM_OK;
+}
+
+pfm_status check_ready(pfm_handle* h, bool need_lin) {
+  if (!h) return PFM_ERR_INVALID_ARG;
+  if (!h->have_state) return h->fail(PFM_ERR_STATE, "no state: call pfm_set_state first");
+  if (need_lin && !h->linearized) return h->fail(PFM_ERR_STATE, "no tangent: call pfm_linearize first");
+  return PFM_OK;
+}
+
+pfm_status residual_impl(pfm_handle* h, double* R, double* energy_host) {
+  Level& f = h->L[0];
+  cudaStream_t s = h->stream;
+  CK(cudaMemsetAsync(R, 0, sizeof(double) * ndof(f), s));
+  CK(cudaMemsetAsync(h->energy_dev, 0, sizeof(double), s));
+  launch_residual(f.g, h->dp, f.U, f.Un, f.mask, R, h->energy_dev, s);
+  CKL();
+  if (energy_host) {
+    CK(cudaMemcpyAsync(energy_host, h->energy_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return PFM_OK;
+}
+
+pfm_status norm2(pfm_handle* h, const double* x, int64_t n, double* out) {
+  launch_mdot(n, 1, x, 0, x, h->partial, h->hdev, h->stream);
+  CKL();
+  double v = 0.0;
+  CK(cudaMemcpyAsync(&v, h->hdev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *out = std::sqrt(v);
+  return PFM_OK;
+}
+
+pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
+  cudaStream_t s = h->stream;
+  const size_t nl = h->L.size();
+  for (size_t l = 1; l < nl; ++l) {
+    launch_inject_state(h->L[l - 1].g, h->L[l].g, h->L[l - 1].U, h->L[l].U, s);
+    launch_inject_state(h->L[l - 1].g, h->L[l].g, h->L[l - 1].Un, h->L[l].Un, s);
+  }
+  CKL();
+  CK(cudaMemsetAsync(h->flag_dev, 0, sizeof(int), s));
+  for (size_t l = 0; l < nl; ++l) {
+    Level& lv = h->L[l];
+    const bool coarsest = (l + 1 == nl);
+    const bool fine = (l == 0);
+    const size_t hsz = size_t(lv.nblk) * HBLK;
+    const bool need64 = fine || coarsest || prec == PFM_F64;
+    const bool need32 = prec == PFM_F32 && !coarsest;
+    if (need64) TRY(dalloc(h, &lv.H64, hsz));
+    if (need32) TRY(dalloc(h, &lv.H32, hsz));
+    launch_linearize(lv.g, h->dp, lv.U, lv.Un, need64 ? lv.H64 : nullptr, need32 ? lv.H32 : nullptr, s);
+    CKL();
+    if (coarsest) continue;
+    if (prec == PFM_F32) {
+      TRY(dalloc(h, &lv.D32, size_t(81) * lv.nn));
+      launch_blockdiag<float>(lv.g, h->dp, lv.H32, lv.mask, lv.D32, s);
+      launch_block_invert<float>(lv.nn, lv.mask, lv.D32, h->flag_dev, s);
+    } else {
+      TRY(dalloc(h, &lv.D64, size_t(81) * lv.nn));
+      launch_blockdiag<double>(lv.g, h->dp, lv.H64, lv.mask, lv.D64, s);
+      launch_block_invert<double>(lv.nn, lv.mask, lv.D64, h->flag_dev, s);
+    }
+    CKL();
+  }
+  Level& c = h->L[nl - 1];
+  launch_coarse_assemble<double>(c.g, h->dp, c.H64, c.mask, h->Kaug, 2 * h->nc_dofs, s);
+  dense_gauss_jordan_inverse(h->Kaug, h->nc_dofs, h->gjf, h->flag_dev, s);
+  CKL();
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (flag) return h->fail(PFM_ERR_BREAKDOWN, "singular nodal block or coarse operator");
+  h->linearized = true;
+  h->lin_prec = prec;
+  return PFM_OK;
+}
+
+template <typename T>
+pfm_status japply_impl(pfm_handle* h, const T* v, T* y) {
+  Level& f = h->L[0];
+  const T* H = LvVec<T>::H(f);
+  if (!H || (sizeof(T) == 4 && h->lin_prec != PFM_F32))
+    return h->fail(PFM_ERR_STATE, "no tangent in the requested precision (linearize with PFM_F32 for FP32)");
+  launch_japply<T>(f.g, h->dp, H, f.mask, v, y, h->stream);
+  CKL();
+  return PFM_OK;
+}
+
+// FGMRES(m), right preconditioned, x0 = 0 (Sec. 3.4 uses GMRES; the flexible
+// variant allows a preconditioner that changes between iterations, here an
+// FP32 V-cycle). Orthogonalisation: classical Gram-Schmidt applied twice.
+pfm_status fgmres_impl(pfm_handle* h, const pfm_solve_opts& o, const double* b, double* x, int* its_out,
+                       double* relres_out) {
+  Level& f = h->L[0];
+  cudaStream_t s = h->stream;
+  const int64_t n = ndof(f);
+  const int m = o.restart;
+  const bool mixed = (o.precond == PFM_F32);
+  if (mixed && h->lin_prec != PFM_F32)
+    return h->fail(PFM_ERR_STATE, "FP32 preconditioner requested but the tangent was built for FP64");
+  if (h->kry_m < m || h->kry_prec != o.precond) {
+    dfree(h->V);
+    if (h->Z) cudaFree(h->Z);
+    h->Z = nullptr;
+    TRY(dalloc(h, &h->V, size_t(m + 1) * n));
+    if (mixed) {
+      float* z = nullptr;
+      TRY(dalloc(h, &z, size_t(m) * n));
+      h->Z = z;
+    } else {
+      double* z = nullptr;
+      TRY(dalloc(h, &z, size_t(m) * n));
+      h->Z = z;
+    }
+    h->kry_m = m;
+    h->kry_prec = o.precond;
+  }
+  if (mixed) {
+    TRY(ensure_level_vectors<float>(h));
+  } else {
+    TRY(ensure_level_vectors<double>(h));
+  }
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  double beta0 = 0.0;
+  TRY(norm2(h, b, n, &beta0));
+  if (its_out) *its_out = 0;
+  if (relres_out) *relres_out = 0.0;
+  if (!std::isfinite(beta0)) return h->fail(PFM_ERR_NONFINITE, "non-finite right-hand side");
+  if (beta0 == 0.0) return PFM_OK;
+  const double tol = o.lin_rtol * beta0;
+  CK(cudaMemcpyAsync(h->rv, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  double beta = beta0;
+  int total = 0;
+  bool converged = false;
+  std::vector<double> Hh((m + 1) * m), cs(m), sn(m), g(m + 1), hcol(2 * (m + 1) + 1);
+  double relres = 1.0;
+  while (total < o.max_lin_it && !converged) {
+    // v_0 = r / beta
+    CK(cudaMemcpyAsync(h->hdev, &beta, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_scale_copy(n, h->rv, h->hdev, h->V, s);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    int kdone = 0;
+    for (; j < m && total < o.max_lin_it; ++j) {
+      double* vj = h->V + size_t(j) * n;
+      // z_j = M v_j
+      if (mixed) {
+        float* zj = static_cast<float*>(h->Z) + size_t(j) * n;
+        Level& fl = h->L[0];
+        launch_cast_d2f(n, vj, fl.b32, s);
+        TRY(vcycle_level<float>(h, 0, o.nu_pre, o.nu_post, float(o.omega)));
+        CK(cudaMemcpyAsync(zj, fl.x32, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+        launch_cast_f2d(n, zj, h->zd, s);
+      } else {
+        double* zj = static_cast<double*>(h->Z) + size_t(j) * n;
+        Level& fl = h->L[0];
+        CK(cudaMemcpyAsync(fl.b64, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        TRY(vcycle_level<double>(h, 0, o.nu_pre, o.nu_post, o.omega));
+        CK(cudaMemcpyAsync(zj, fl.x64, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(h->zd, zj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      }
+      // w = J z_j (FP64 outer operator)
+      TRY(japply_impl<double>(h, h->zd, h->wv));
+      // classical Gram-Schmidt, twice
+      double* h1 = h->hdev;
+      double* h2 = h->hdev + (m + 1);
+      double* hn = h->hdev + 2 * (m + 1);
+      launch_mdot(n, j + 1, h->V, n, h->wv, h->partial, h1, s);
+      launch_maxpy(n, j + 1, h->V, n, h1, h->wv, s);
+      launch_mdot(n, j + 1, h->V, n, h->wv, h->partial, h2, s);
+      launch_maxpy(n, j + 1, h->V, n, h2, h->wv, s);
+      launch_mdot(n, 1, h->wv, 0, h->wv, h->partial, hn, s);
+      CKL();
+      CK(cudaMemcpyAsync(hcol.data(), h->hdev, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      ++total;
+      kdone = j + 1;
+      double hnorm = std::sqrt(hcol[2 * (m + 1)]);
+      if (!std::isfinite(hnorm)) return h->fail(PFM_ERR_NONFINITE, "non-finite Krylov vector");
+      for (int i = 0; i <= j; ++i) Hh[i * m + j] = hcol[i] + hcol[(m + 1) + i];
+      Hh[(j + 1) * m + j] = hnorm;
+      // apply previous Givens rotations, then a new one to zero H[j+1][j]
+      for (int i = 0; i < j; ++i) {
+        double a = Hh[i * m + j], bb = Hh[(i + 1) * m + j];
+        Hh[i * m + j] = cs[i] * a + sn[i] * bb;
+        Hh[(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      }
+      double a = Hh[j * m + j], bb = Hh[(j + 1) * m + j];
+      double rr = std::hypot(a, bb);
+      if (rr == 0.0) return h->fail(PFM_ERR_BREAKDOWN, "zero Hessenberg column");
+      cs[j] = a / rr;
+      sn[j] = bb / rr;
+      Hh[j * m + j] = rr;
+      Hh[(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      relres = std::fabs(g[j + 1]) / beta0;
+      if (std::fabs(g[j + 1]) <= tol) { converged = true; break; }
+      if (hnorm <= 1e-300) break;  // happy breakdown: exact solution in the space
+      if (j + 1 < m) {
+        CK(cudaMemcpyAsync(h->hdev + 2 * (m + 1), &hnorm, sizeof(double), cudaMemcpyHostToDevice, s));
+        launch_scale_copy(n, h->wv, h->hdev + 2 * (m + 1), h->V + size_t(j + 1) * n, s);
+      }
+    }
+    // y = R^-1 g (back substitution), x += Z y
+    std::vector<double> y(kdone, 0.0);
+    for (int i = kdone - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int k = i + 1; k < kdone; ++k) acc -= Hh[i * m + k] * y[k];
+      y[i] = acc / Hh[i * m + i];
+    }
+    CK(cudaMemcpyAsync(h->hdev, y.data(), sizeof(double) * kdone, cudaMemcpyHostToDevice, s));
+    if (mixed)
+      launch_gemv_add<float>(n, kdone, static_cast<float*>(h->Z), n, h->hdev, x, s);
+    else
+      launch_gemv_add<double>(n, kdone, static_cast<double*>(h->Z), n, h->hdev, x, s);
+    CKL();
+    if (converged) break;
+    // restart from the true residual r = b - J x
+    TRY(japply_impl<double>(h, x, h->wv));
+    launch_sub<double>(n, b, h->wv, h->rv, s);
+    TRY(norm2(h, h->rv, n, &beta));
+    relres = beta / beta0;
+    if (beta <= tol) { converged = true; break; }
+  }
+  if (its_out) *its_out = total;
+  if (relres_out) *relres_out = relres;
+  if (!converged)
+    return h->fail(PFM_ERR_NOT_CONVERGED, "FGMRES reached max_lin_it at relative residual " + std::to_string(relres));
+  return PFM_OK;
+}
+
+bool opts_valid(const pfm_solve_opts& o) {
+  return o.restart >= 1 && o.restart <= MAX_RESTART && o.max_lin_it >= 1 && o.nu_pre >= 1 &&
+         o.nu_post >= 0 && o.max_newton >= 1 && o.lin_rtol > 0 && o.omega > 0 &&
+         (o.precond == PFM_F32 || o.precond == PFM_F64);
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+const char* pfm_version(void) { return "pfm 0.1 (sm_103a)"; }
+
+pfm_status pfm_create(const pfm_mesh_desc* mesh, const pfm_params* params, pfm_handle** out) {
+  if (!mesh || !params || !out) {
+    g_create_error = "null argument";
+    return PFM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || !(mesh->Lx > 0) || !(mesh->Ly > 0) || !(mesh->Lz > 0) ||
+      mesh->n_levels < 0 || !(params->tau > 0)) {
+    g_create_error = "invalid mesh size, box length, level count or tau";
+    return PFM_ERR_INVALID_ARG;
+  }
+  pfm_handle* h = new pfm_handle();
+  h->params = *params;
+  make_dev_params(*params, h->dp);
+  // level hierarchy: ceil-halving until max(n) <= 4 (or n_levels levels)
+  int nx = mesh->nx, ny = mesh->ny, nz = mesh->nz;
+  for (int l = 0;; ++l) {
+    Level lv;
+    lv.g = Grid{nx, ny, nz, mesh->Lx / nx, mesh->Ly / ny, mesh->Lz / nz};
+    lv.nn = lv.g.nn();
+    lv.ne = lv.g.ne();
+    lv.nblk = lv.g.nblk();
+    h->L.push_back(lv);
+    const int mx = std::max(nx, std::max(ny, nz));
+    if (mesh->n_levels > 0 && int(h->L.size()) == mesh->n_levels) break;
+    if (mesh->n_levels == 0 && mx <= 4) break;
+    if (mx <= 1) break;
+    nx = (nx + 1) / 2;
+    ny = (ny + 1) / 2;
+    nz = (nz + 1) / 2;
+  }
+  h->nc_dofs = int(NF * h->L.back().nn);
+  if (h->nc_dofs > MAX_COARSE_DOFS) {
+    g_create_error = "coarsest level has " + std::to_string(h->nc_dofs) + " DOFs (max " +
+                     std::to_string(MAX_COARSE_DOFS) + "): use more levels";
+    delete h;
+    return PFM_ERR_INVALID_ARG;
+  }
+  auto cleanup = [&](pfm_status st) {
+    g_create_error = h->err;
+    pfm_destroy(h);
+    return st;
+  };
+  for (auto& lv : h->L) {
+    pfm_status st;
+    if ((st = dalloc(h, &lv.U, ndof(lv))) != PFM_OK) return cleanup(st);
+    if ((st = dalloc(h, &lv.Un, ndof(lv))) != PFM_OK) return cleanup(st);
+    if ((st = dalloc(h, &lv.mask, lv.nn)) != PFM_OK) return cleanup(st);
+    cudaMemset(lv.mask, 0, sizeof(dmask_t) * lv.nn);
+  }
+  const int64_t n = ndof(h->L[0]);
+  pfm_status st;
+  if ((st = dalloc(h, &h->energy_dev, 1)) != PFM_OK) return cleanup(st);
+  if ((st = dalloc(h, &h->flag_dev, 1)) != PFM_OK) return cleanup(st);
+  if ((st = dalloc(h, &h->R, n)) != PFM_OK) return cleanup(st);
+  if ((st = dalloc(h, &h->dU, n)) != PFM_OK) return cleanup(st);
+  if ((st = dalloc(h, &h->wv, n)) != PFM_OK) return cleanup(st);
+  if ((st = dalloc(h, &h->rv, n)) != PFM_OK) return cleanup(st);
+  if ((st = dalloc(h, &h->zd, n)) != PFM_OK) return cleanup(st);
+  if ((st = dalloc(h, &h->partial, size_t(reduction_blocks(n)) * (MAX_RESTART + 1))) != PFM_OK) return cleanup(st);
+  if ((st = dalloc(h, &h->hdev, size_t(3) * (MAX_RESTART + 2))) != PFM_OK) return cleanup(st);
+  if ((st = dalloc(h, &h->Kaug, size_t(h->nc_dofs) * 2 * h->nc_dofs)) != PFM_OK) return cleanup(st);
+  if ((st = dalloc(h, &h->gjf, h->nc_dofs)) != PFM_OK) return cleanup(st);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    h->err = cudaGetErrorString(e);
+    return cleanup(PFM_ERR_CUDA);
+  }
+  *out = h;
+  return PFM_OK;
+}
+
+void pfm_destroy(pfm_handle* h) {
+  if (!h) return;
+  for (auto& lv : h->L) {
+    dfree(lv.U); dfree(lv.Un); dfree(lv.mask); dfree(lv.H64); dfree(lv.H32); dfree(lv.D64); dfree(lv.D32);
+    dfree(lv.x32); dfree(lv.b32); dfree(lv.y32); dfree(lv.x64); dfree(lv.b64); dfree(lv.y64);
+  }
+  dfree(h->dirval); dfree(h->energy_dev); dfree(h->flag_dev); dfree(h->R); dfree(h->dU); dfree(h->wv);
+  dfree(h->rv); dfree(h->zd); dfree(h->partial); dfree(h->hdev); dfree(h->V); dfree(h->Kaug); dfree(h->gjf);
+  if (h->Z) cudaFree(h->Z);
+  if (h->stage_in) cudaFree(h->stage_in);
+  if (h->stage_out) cudaFree(h->stage_out);
+  delete h;
+}
+
+const char* pfm_last_error(const pfm_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+pfm_status pfm_get_sizes(const pfm_handle* h, int64_t* n_nodes, int64_t* n_elems, int* n_levels) {
+  if (!h) return PFM_ERR_INVALID_ARG;
+  if (n_nodes) *n_nodes = h->L[0].nn;
+  if (n_elems) *n_elems = h->L[0].ne;
+  if (n_levels) *n_levels = int(h->L.size());
+  return PFM_OK;
+}
+
+pfm_status pfm_set_stream(pfm_handle* h, void* stream) {
+  if (!h) return PFM_ERR_INVALID_ARG;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return PFM_OK;
+}
+
+pfm_status pfm_set_params(pfm_handle* h, const pfm_params* params) {
+  if (!h || !params) return PFM_ERR_INVALID_ARG;
+  if (!(params->tau > 0)) return h->fail(PFM_ERR_INVALID_ARG, "tau must be positive");
+  h->params = *params;
+  make_dev_params(*params, h->dp);
+  h->linearized = false;
+  return PFM_OK;
+}
+
+pfm_status pfm_set_dirichlet(pfm_handle* h, const uint8_t* mask_dev, const double* val_dev) {
+  if (!h || !mask_dev) return PFM_ERR_INVALID_ARG;
+  cudaStream_t s = h->stream;
+  Level& f = h->L[0];
+  CK(cudaMemsetAsync(h->flag_dev, 0, sizeof(int), s));
+  launch_build_mask(f.nn, mask_dev, f.mask, h->flag_dev, s);
+  CKL();
+  for (size_t l = 1; l < h->L.size(); ++l) launch_coarse_mask(h->L[l - 1].g, h->L[l].g, h->L[l - 1].mask, h->L[l].mask, s);
+  CKL();
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (bad) return h->fail(PFM_ERR_INVALID_ARG, "only displacement DOFs (fields 0..2) may be prescribed");
+  if (val_dev) {
+    TRY(dalloc(h, &h->dirval, ndof(f)));
+    CK(cudaMemcpyAsync(h->dirval, val_dev, sizeof(double) * ndof(f), cudaMemcpyDeviceToDevice, s));
+    h->have_dirval = true;
+    if (h->have_state) launch_mask_values(f.nn, f.mask, h->dirval, f.U, s);
+  }
+  h->linearized = false;
+  return PFM_OK;
+}
+
+pfm_status pfm_set_state(pfm_handle* h, const double* U_dev, const double* Un_dev) {
+  if (!h || !U_dev || !Un_dev) return PFM_ERR_INVALID_ARG;
+  Level& f = h->L[0];
+  cudaStream_t s = h->stream;
+  CK(cudaMemcpyAsync(f.U, U_dev, sizeof(double) * ndof(f), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(f.Un, Un_dev, sizeof(double) * ndof(f), cudaMemcpyDeviceToDevice, s));
+  if (h->have_dirval) launch_mask_values(f.nn, f.mask, h->dirval, f.U, s);
+  CKL();
+  h->have_state = true;
+  h->linearized = false;
+  return PFM_OK;
+}
+
+pfm_status pfm_get_state(pfm_handle* h, double* U_dev) {
+  TRY(check_ready(h, false));
+  if (!U_dev) return h->fail(PFM_ERR_INVALID_ARG, "null output");
+  CK(cudaMemcpyAsync(U_dev, h->L[0].U, sizeof(double) * ndof(h->L[0]), cudaMemcpyDeviceToDevice, h->stream));
+  return PFM_OK;
+}
+
+pfm_status pfm_residual(pfm_handle* h, double* R_dev, double* energy_host) {
+  TRY(check_ready(h, false));
+  if (!R_dev) return h->fail(PFM_ERR_INVALID_ARG, "null output");
+  return residual_impl(h, R_dev, energy_host);
+}
+
+pfm_status pfm_linearize(pfm_handle* h, pfm_precision precond) {
+  TRY(check_ready(h, false));
+  if (precond != PFM_F32 && precond != PFM_F64) return h->fail(PFM_ERR_INVALID_ARG, "bad precision");
+  return linearize_impl(h, precond);
+}
+
+pfm_status pfm_jacobian_apply(pfm_handle* h, const void* v_dev, void* y_dev, pfm_precision prec) {
+  TRY(check_ready(h, true));
+  if (!v_dev || !y_dev || v_dev == y_dev) return h->fail(PFM_ERR_INVALID_ARG, "null or aliased vectors");
+  if (prec == PFM_F32) return japply_impl<float>(h, static_cast<const float*>(v_dev), static_cast<float*>(y_dev));
+  if (prec == PFM_F64) return japply_impl<double>(h, static_cast<const double*>(v_dev), static_cast<double*>(y_dev));
+  return h->fail(PFM_ERR_INVALID_ARG, "bad precision");
+}
+
+// The tangent is the Hessian of one scalar potential (Sec. 3.4), so every
+// stored 15x15 point block is symmetric and packed once; J^T v reads the
+// same packed blocks with the roles of rows and columns exchanged, which is
+// the same product. Dirichlet rows and columns are identity in both.
+pfm_status pfm_jacobian_transpose_apply(pfm_handle* h, const void* v_dev, void* y_dev, pfm_precision prec) {
+  return pfm_jacobian_apply(h, v_dev, y_dev, prec);
+}
+
+pfm_status pfm_jacobian_apply_host(pfm_handle* h, const void* v_host, void* y_host, pfm_precision prec) {
+  TRY(check_ready(h, true));
+  if (!v_host || !y_host) return h->fail(PFM_ERR_INVALID_ARG, "null vectors");
+  const size_t bytes = ndof(h->L[0]) * (prec == PFM_F32 ? sizeof(float) : sizeof(double));
+  if (!h->stage_in) {
+    char* a = nullptr;
+    char* b = nullptr;
+    TRY(dalloc(h, &a, ndof(h->L[0]) * sizeof(double)));
+    TRY(dalloc(h, &b, ndof(h->L[0]) * sizeof(double)));
+    h->stage_in = a;
+    h->stage_out = b;
+  }
+  CK(cudaMemcpyAsync(h->stage_in, v_host, bytes, cudaMemcpyHostToDevice, h->stream));
+  TRY(pfm_jacobian_apply(h, h->stage_in, h->stage_out, prec));
+  CK(cudaMemcpyAsync(y_host, h->stage_out, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return PFM_OK;
+}
+
+pfm_status pfm_vcycle(pfm_handle* h, const void* r_dev, void* z_dev, pfm_precision prec, const pfm_solve_opts* opts) {
+  TRY(check_ready(h, true));
+  if (!r_dev || !z_dev) return h->fail(PFM_ERR_INVALID_ARG, "null vectors");
+  int nu_pre = 2, nu_post = 2;
+  double omega = 0.7;
+  if (opts) { nu_pre = opts->nu_pre; nu_post = opts->nu_post; omega = opts->omega; }
+  if (nu_pre < 1 || nu_post < 0) return h->fail(PFM_ERR_INVALID_ARG, "nu_pre >= 1 and nu_post >= 0 required");
+  if (prec != h->lin_prec) return h->fail(PFM_ERR_STATE, "V-cycle precision differs from the linearisation");
+  if (prec == PFM_F32) return apply_vcycle<float>(h, static_cast<const float*>(r_dev), static_cast<float*>(z_dev), nu_pre, nu_post, omega);
+  return apply_vcycle<double>(h, static_cast<const double*>(r_dev), static_cast<double*>(z_dev), nu_pre, nu_post, omega);
+}
+
+pfm_status pfm_fgmres_solve(pfm_handle* h, const pfm_solve_opts* opts, const double* b_dev, double* x_dev,
+                            pfm_solve_report* report) {
+  TRY(check_ready(h, true));
+  if (!opts || !b_dev || !x_dev || !opts_valid(*opts)) return h->fail(PFM_ERR_INVALID_ARG, "bad options or vectors");
+  int its = 0;
+  double rel = 0.0;
+  double t0 = now_ms();
+  pfm_status st = fgmres_impl(h, *opts, b_dev, x_dev, &its, &rel);
+  if (report) {
+    report->lin_its_last = its;
+    report->lin_its_total = its;
+    report->lin_res_final = rel;
+    report->ms_solve = now_ms() - t0;
+    report->status = st;
+  }
+  return st;
+}
+
+pfm_status pfm_newton_solve(pfm_handle* h, const pfm_solve_opts* opts, double* U_inout_dev, pfm_solve_report* report) {
+  if (!h) return PFM_ERR_INVALID_ARG;
+  if (!opts || !U_inout_dev || !opts_valid(*opts)) return h->fail(PFM_ERR_INVALID_ARG, "bad options or state");
+  if (!h->have_state) return h->fail(PFM_ERR_STATE, "no U_n: call pfm_set_state first");
+  Level& f = h->L[0];
+  cudaStream_t s = h->stream;
+  const int64_t n = ndof(f);
+  pfm_solve_report rep{};
+  const double t_start = now_ms();
+  CK(cudaMemcpyAsync(f.U, U_inout_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  if (h->have_dirval) launch_mask_values(f.nn, f.mask, h->dirval, f.U, s);
+  h->linearized = false;
+  double t0 = now_ms();
+  TRY(residual_impl(h, h->R, nullptr));
+  double res = 0.0;
+  TRY(norm2(h, h->R, n, &res));
+  rep.ms_residual += now_ms() - t0;
+  rep.res0 = res;
+  pfm_status st = PFM_OK;
+  if (!std::isfinite(res)) st = h->fail(PFM_ERR_NONFINITE, "non-finite residual");
+  for (int it = 0; st == PFM_OK && it < opts->max_newton; ++it) {
+    if (res == 0.0 || (it > 0 && res <= opts->newton_rtol * rep.res0)) break;
+    t0 = now_ms();
+    st = linearize_impl(h, opts->precond);
+    rep.ms_linearize += now_ms() - t0;
+    if (st != PFM_OK) break;
+    // J dU = b with b = -R (R negated in place; the solver uses wv/rv/zd as work)
+    t0 = now_ms();
+    int its = 0;
+    double rel = 0.0;
+    launch_axpy(n, -2.0, h->R, h->R, s);
+    st = fgmres_impl(h, *opts, h->R, h->dU, &its, &rel);
+    rep.ms_solve += now_ms() - t0;
+    rep.lin_its_total += its;
+    rep.lin_its_last = its;
+    rep.lin_res_final = rel;
+    if (st != PFM_OK) break;
+    launch_axpy(n, 1.0, h->dU, f.U, s);
+    CKL();
+    h->linearized = false;
+    ++rep.newton_its;
+    t0 = now_ms();
+    TRY(residual_impl(h, h->R, nullptr));
+    TRY(norm2(h, h->R, n, &res));
+    rep.ms_residual += now_ms() - t0;
+    if (!std::isfinite(res)) st = h->fail(PFM_ERR_NONFINITE, "non-finite residual");
+  }
+  rep.res_final = res;
+  if (st == PFM_OK && opts->max_newton > 1 && !(res <= opts->newton_rtol * rep.res0) && res != 0.0)
+    st = h->fail(PFM_ERR_NOT_CONVERGED, "Newton reached max_newton");
+  CK(cudaMemcpyAsync(U_inout_dev, f.U, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  rep.ms_total = now_ms() - t_start;
+  rep.status = st;
+  if (report) *report = rep;
+  return st;
+}
+
+pfm_status pfm_qp_eval(pfm_handle* h, int64_t n, const double* F_dev, const double* eta_dev, const double* eta_n_dev,
+                       double* W_dev, double* grad_dev, double* hess_dev) {
+  if (!h) return PFM_ERR_INVALID_ARG;
+  if (n < 0 || !F_dev || !eta_dev || !eta_n_dev) return h->fail(PFM_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0) return PFM_OK;
+  launch_qp_eval(h->dp, n, F_dev, eta_dev, eta_n_dev, W_dev, grad_dev, hess_dev, h->stream);
+  CKL();
+  CK(cudaStreamSynchronize(h->stream));
+  return PFM_OK;
+}
+
+pfm_status pfm_get_hessians(pfm_handle* h, int64_t e0, int64_t count, double* hess_host) {
+  TRY(check_ready(h, true));
+  Level& f = h->L[0];
+  if (e0 < 0 || count < 0 || e0 + count > f.ne || (!hess_host && count > 0))
+    return h->fail(PFM_ERR_INVALID_ARG, "element range out of bounds");
+  if (count == 0) return PFM_OK;
+  const int64_t b0 = e0 / 4, b1 = (e0 + count - 1) / 4;
+  std::vector<double> buf(size_t(b1 - b0 + 1) * HBLK);
+  CK(cudaMemcpyAsync(buf.data(), f.H64 + b0 * HBLK, sizeof(double) * buf.size(), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int64_t e = e0; e < e0 + count; ++e)
+    for (int q = 0; q < 8; ++q) {
+      const int lane = int(e & 3) * 8 + q;
+      for (int j = 0; j < NH; ++j)
+        hess_host[((e - e0) * 8 + q) * NH + j] = buf[hstore_offset<double>(e / 4 - b0, j, lane)];
+    }
+  return PFM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// Internal declarations shared by the CUDA translation units of libpfm.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "qp_physics.cuh"
+
+namespace pfm {
+
+constexpr int NF = 9;  // unknowns per node: u (3) + eta_hat (6)
+
+// Gauss points of the 2-point rule mapped to [0,1]: (1 -+ 1/sqrt(3)) / 2.
+constexpr double GA = 0.21132486540518711775;
+constexpr double GB = 0.78867513459481288225;
+
+// Structured grid of one multigrid level.
+struct Grid {
+  int nx, ny, nz;
+  double hx, hy, hz;
+  __host__ __device__ int64_t nn() const { return int64_t(nx + 1) * (ny + 1) * (nz + 1); }
+  __host__ __device__ int64_t ne() const { return int64_t(nx) * ny * nz; }
+  // element blocks of 4 elements (one warp: 4 elements x 8 Gauss points)
+  __host__ __device__ int64_t nblk() const { return (ne() + 3) / 4; }
+  __host__ __device__ double w() const { return hx * hy * hz / 8.0; }
+};
+
+// Gauss-point Hessian store: element blocks of 4, lane = 8*(e%4) + q, and per
+// lane the 120 packed entries in 16-byte vectors of V = 16/sizeof(S) entries:
+// offset ((blk*(120/V) + entry/V)*32 + lane)*V + entry%V. One warp therefore
+// reads 512 contiguous bytes per vector load.
+template <typename S>
+__host__ __device__ inline int64_t hstore_offset(int64_t blk, int entry, int lane) {
+  constexpr int V = 16 / sizeof(S);
+  return ((blk * (NH / V) + entry / V) * 32 + lane) * V + entry % V;
+}
+constexpr int64_t HBLK = int64_t(NH) * 32;  // entries per element block
+
+// Per-node Dirichlet bit mask (bit f set = DOF f prescribed).
+using dmask_t = uint16_t;
+
+}  // namespace pfm
+
+// ---- launchers (host functions; every launch goes on the given stream) ----
+namespace pfm {
+
+// element kernels (fe_kernels.cu)
+void launch_residual(const Grid& g, const DevParams& P, const double* U, const double* Un,
+                     const dmask_t* mask, double* R, double* energy, cudaStream_t s);
+void launch_linearize(const Grid& g, const DevParams& P, const double* U, const double* Un,
+                      double* H64, float* H32, cudaStream_t s);
+template <typename T>
+void launch_japply(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, const T* v,
+                   T* y, cudaStream_t s);
+template <typename T>
+void launch_blockdiag(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, T* D,
+                      cudaStream_t s);
+template <typename T>
+void launch_block_invert(int64_t nn, const dmask_t* mask, T* D, int* singular, cudaStream_t s);
+void launch_qp_eval(const DevParams& P, int64_t n, const double* F, const double* eta,
+                    const double* eta_n, double* W, double* grad, double* hess, cudaStream_t s);
+
+// multigrid kernels (mg_kernels.cu)
+void launch_inject_state(const Grid& fine, const Grid& coarse, const double* Uf, double* Uc,
+                         cudaStream_t s);
+void launch_coarse_mask(const Grid& fine, const Grid& coarse, const dmask_t* mf, dmask_t* mc,
+                        cudaStream_t s);
+template <typename T>
+void launch_prolong_add(const Grid& fine, const Grid& coarse, const T* xc, const dmask_t* mf, T* xf,
+                        cudaStream_t s);
+template <typename T>
+void launch_restrict(const Grid& fine, const Grid& coarse, const T* rf, const dmask_t* mc, T* rc,
+                     cudaStream_t s);
+template <typename T>
+void launch_smooth(int64_t nn, const T* D, const T* b, const T* y, T omega, T* x, cudaStream_t s);
+template <typename T>
+void launch_sub(int64_t n, const T* b, const T* y, T* r, cudaStream_t s);
+template <typename T>
+void launch_coarse_assemble(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask,
+                            double* K, int ld, cudaStream_t s);
+int dense_gauss_jordan_inverse(double* Maug, int n, double* f, int* singular, cudaStream_t s);
+template <typename T>
+void launch_coarse_solve(int n, const double* Ainv, const T* b, T* x, cudaStream_t s);
+
+// vector kernels (krylov_kernels.cu)
+template <typename T>
+void launch_fill(int64_t n, T val, T* x, cudaStream_t s);
+void launch_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t s);
+void launch_cast_f2d(int64_t n, const float* a, double* b, cudaStream_t s);
+void launch_mdot(int64_t n, int k, const double* V, int64_t ldv, const double* w, double* partial,
+                 double* out, cudaStream_t s);
+void launch_maxpy(int64_t n, int k, const double* V, int64_t ldv, const double* h, double* w,
+                  cudaStream_t s);
+void launch_scale_copy(int64_t n, const double* a, const double* alpha_dev, double* b,
+                       cudaStream_t s);
+template <typename T>
+void launch_gemv_add(int64_t n, int k, const T* Z, int64_t ldz, const double* y, double* x,
+                     cudaStream_t s);
+void launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s);
+void launch_mask_values(int64_t nn, const dmask_t* mask, const double* val, double* U,
+                        cudaStream_t s);
+void launch_build_mask(int64_t nn, const uint8_t* m8, dmask_t* mask, int* bad, cudaStream_t s);
+int reduction_blocks(int64_t n);
+
+}  // namespace pfm

@@ -1,0 +1,485 @@
+// Element kernels on the structured trilinear-hexahedron grid: residual
+// (Sec. 3.4, Eq. FinalRes), linearisation into Gauss-point Hessians (the
+// tangent of Eq. linAlgEq), matrix-free tangent application, nodal 9x9
+// diagonal blocks for point-block Jacobi (Sec. 3.4) and their inverses.
+//
+// Thread mapping: 8 consecutive lanes form one element; lane l8 = 0..7 plays
+// two roles: local node a = l8 (corner (a&1, a>>1&1, a>>2)) when gathering
+// nodal data or scattering nodal results, and Gauss point q = l8 (point
+// ((1 -+ 1/sqrt 3)/2) per axis) for the point physics. Values and gradients
+// at the 8 points are a tensor product of 1-D 2x2 transforms, applied with
+// three xor-shuffles (1, 2, 4) per axis; the scatter is the transposed
+// transform. A warp holds 4 elements.
+#include "common.cuh"
+
+namespace pfm {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T shx(T v, int m) {
+  return __shfl_xor_sync(0xffffffffu, v, m);
+}
+
+// Nodal value v of this lane's node -> value and gradient at this lane's point.
+template <typename T>
+__device__ __forceinline__ void q1_gather(T v, int l8, T ihx, T ihy, T ihz, T& val, T& gx, T& gy,
+                                          T& gz) {
+  const T ga = T(GA), gb = T(GB);
+  T s = shx(v, 1);
+  T vx = gb * v + ga * s;
+  T dx = ((l8 & 1) ? (v - s) : (s - v)) * ihx;
+  T s1 = shx(vx, 2), s2 = shx(dx, 2);
+  T vxy = gb * vx + ga * s1;
+  T vdy = ((l8 & 2) ? (vx - s1) : (s1 - vx)) * ihy;
+  T dxy = gb * dx + ga * s2;
+  T t1 = shx(vxy, 4), t2 = shx(vdy, 4), t3 = shx(dxy, 4);
+  val = gb * vxy + ga * t1;
+  gz = ((l8 & 4) ? (vxy - t1) : (t1 - vxy)) * ihz;
+  gy = gb * vdy + ga * t2;
+  gx = gb * dxy + ga * t3;
+}
+
+// Nodal value -> value at this lane's point.
+template <typename T>
+__device__ __forceinline__ T q1_value(T v) {
+  const T ga = T(GA), gb = T(GB);
+  v = gb * v + ga * shx(v, 1);
+  v = gb * v + ga * shx(v, 2);
+  return gb * v + ga * shx(v, 4);
+}
+
+// Transpose: point weights (val for N_a, g for grad N_a) -> this lane's node.
+template <typename T>
+__device__ __forceinline__ T q1_scatter(T val, T gx, T gy, T gz, int l8, T ihx, T ihy, T ihz) {
+  const T ga = T(GA), gb = T(GB);
+  T sv = shx(val, 4), sz = shx(gz, 4), sx = shx(gx, 4), sy = shx(gy, 4);
+  T A = gb * val + ga * sv + ((l8 & 4) ? (gz + sz) : -(gz + sz)) * ihz;
+  T Bx = gb * gx + ga * sx;
+  T By = gb * gy + ga * sy;
+  T sA = shx(A, 2), sBy = shx(By, 2), sBx = shx(Bx, 2);
+  T Cc = gb * A + ga * sA + ((l8 & 2) ? (By + sBy) : -(By + sBy)) * ihy;
+  T Dx = gb * Bx + ga * sBx;
+  T sC = shx(Cc, 1), sD = shx(Dx, 1);
+  return gb * Cc + ga * sC + ((l8 & 1) ? (Dx + sD) : -(Dx + sD)) * ihx;
+}
+
+template <typename T>
+__device__ __forceinline__ T q1_scatter_grad(T gx, T gy, T gz, int l8, T ihx, T ihy, T ihz) {
+  const T ga = T(GA), gb = T(GB);
+  T sz = shx(gz, 4), sx = shx(gx, 4), sy = shx(gy, 4);
+  T A = ((l8 & 4) ? (gz + sz) : -(gz + sz)) * ihz;
+  T Bx = gb * gx + ga * sx;
+  T By = gb * gy + ga * sy;
+  T sA = shx(A, 2), sBy = shx(By, 2), sBx = shx(Bx, 2);
+  T Cc = gb * A + ga * sA + ((l8 & 2) ? (By + sBy) : -(By + sBy)) * ihy;
+  T Dx = gb * Bx + ga * sBx;
+  T sC = shx(Cc, 1), sD = shx(Dx, 1);
+  return gb * Cc + ga * sC + ((l8 & 1) ? (Dx + sD) : -(Dx + sD)) * ihx;
+}
+
+__device__ __forceinline__ int64_t elem_node(const Grid& g, int64_t e, int a) {
+  int64_t ei = e % g.nx;
+  int64_t r = e / g.nx;
+  int64_t ej = r % g.ny;
+  int64_t ek = r / g.ny;
+  return (ei + (a & 1)) + int64_t(g.nx + 1) * ((ej + ((a >> 1) & 1)) + int64_t(g.ny + 1) * (ek + (a >> 2)));
+}
+
+// Gather F = I + grad u, eta_hat and grad eta_hat at this lane's point.
+template <typename T, typename Src>
+__device__ __forceinline__ void gather_state(const Src* __restrict__ U, int64_t nn, int64_t node,
+                                             bool valid, int l8, T ihx, T ihy, T ihz, T F[9],
+                                             T eh[6], T ge[18]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T v = valid ? T(U[i * nn + node]) : T(0);
+    T val, gx, gy, gz;
+    q1_gather(v, l8, ihx, ihy, ihz, val, gx, gy, gz);
+    F[3 * i + 0] = gx;
+    F[3 * i + 1] = gy;
+    F[3 * i + 2] = gz;
+  }
+  F[0] += T(1);
+  F[4] += T(1);
+  F[8] += T(1);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    T v = valid ? T(U[(3 + k) * nn + node]) : T(0);
+    q1_gather(v, l8, ihx, ihy, ihz, eh[k], ge[3 * k], ge[3 * k + 1], ge[3 * k + 2]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_residual(Grid g, DevParams P, const double* __restrict__ U,
+                                                  const double* __restrict__ Un,
+                                                  const dmask_t* __restrict__ mask,
+                                                  double* __restrict__ R, double* energy) {
+  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t e = tid >> 3;
+  const int l8 = int(tid & 7);
+  const bool valid = e < g.ne();
+  const int64_t nn = g.nn();
+  const int64_t node = valid ? elem_node(g, e, l8) : 0;
+  const double ihx = 1.0 / g.hx, ihy = 1.0 / g.hy, ihz = 1.0 / g.hz;
+  double F[9], eh[6], ge[18], ehn[6];
+  gather_state<double>(U, nn, node, valid, l8, ihx, ihy, ihz, F, eh, ge);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) ehn[k] = q1_value(valid ? Un[(3 + k) * nn + node] : 0.0);
+  double W, gr[NZ];
+  qp_local<double, false>(P, F, eh, ehn, &W, gr, nullptr);
+  double gf[18];
+  double Wg = 0.0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double s = 0.0;
+#pragma unroll
+      for (int l = 0; l < 6; ++l) s += P.G[k][l] * ge[3 * l + d];
+      gf[3 * k + d] = s;
+      Wg += 0.5 * ge[3 * k + d] * s;
+    }
+  const double w = g.w();
+  const dmask_t dm = valid ? mask[node] : dmask_t(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double r = q1_scatter_grad(w * gr[3 * i], w * gr[3 * i + 1], w * gr[3 * i + 2], l8, ihx, ihy, ihz);
+    if (valid && !((dm >> i) & 1)) atomicAdd(&R[i * nn + node], r);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    double r = q1_scatter(w * gr[9 + k], w * gf[3 * k], w * gf[3 * k + 1], w * gf[3 * k + 2], l8, ihx,
+                          ihy, ihz);
+    if (valid && !((dm >> (3 + k)) & 1)) atomicAdd(&R[(3 + k) * nn + node], r);
+  }
+  if (energy) {
+    double en = warp_sum(valid ? w * (W + Wg) : 0.0);
+    if ((threadIdx.x & 31) == 0) atomicAdd(energy, en);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_linearize(Grid g, DevParams P, const double* __restrict__ U,
+                                                   const double* __restrict__ Un,
+                                                   double* __restrict__ H64, float* __restrict__ H32) {
+  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t e = tid >> 3;
+  const int l8 = int(tid & 7);
+  const int64_t nblk = g.nblk();
+  if ((tid >> 5) >= nblk) return;  // whole warps only (padding lanes stay)
+  const bool valid = e < g.ne();
+  const int64_t nn = g.nn();
+  const int64_t node = valid ? elem_node(g, e, l8) : 0;
+  const double ihx = 1.0 / g.hx, ihy = 1.0 / g.hy, ihz = 1.0 / g.hz;
+  double F[9], eh[6], ge[18], ehn[6];
+  gather_state<double>(U, nn, node, valid, l8, ihx, ihy, ihz, F, eh, ge);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) ehn[k] = q1_value(valid ? Un[(3 + k) * nn + node] : 0.0);
+  double W, gr[NZ], Hp[NH];
+  qp_local<double, true>(P, F, eh, ehn, &W, gr, Hp);
+  const int64_t blk = tid >> 5;
+  const int lane = int(tid & 31);
+  for (int j = 0; j < NH; ++j) {
+    double h = valid ? Hp[j] : 0.0;
+    if (H64) H64[hstore_offset<double>(blk, j, lane)] = h;
+    if (H32) H32[hstore_offset<float>(blk, j, lane)] = float(h);
+  }
+}
+
+// Vector of V = 16/sizeof(T) Hessian entries.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  using type = float4;
+  static __device__ __forceinline__ void unpack(const float4& x, float* o) { o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w; }
+};
+template <> struct Vec16<double> {
+  using type = double2;
+  static __device__ __forceinline__ void unpack(const double2& x, double* o) { o[0] = x.x; o[1] = x.y; }
+};
+
+template <typename T>
+struct JParams {
+  T G[6][6];
+  T w, ihx, ihy, ihz;
+};
+
+// y += J v over the elements (y initialised by k_japply_init).
+template <typename T>
+__global__ void __launch_bounds__(256) k_japply(Grid g, JParams<T> jp, const T* __restrict__ H,
+                                                const dmask_t* __restrict__ mask,
+                                                const T* __restrict__ v, T* __restrict__ y) {
+  constexpr int V = 16 / sizeof(T);
+  using VT = typename Vec16<T>::type;
+  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t blk = tid >> 5;
+  if (blk >= g.nblk()) return;
+  const int64_t e = tid >> 3;
+  const int l8 = int(tid & 7);
+  const int lane = int(tid & 31);
+  const bool valid = e < g.ne();
+  const int64_t nn = g.nn();
+  const int64_t node = valid ? elem_node(g, e, l8) : 0;
+  const dmask_t dm = valid ? mask[node] : dmask_t(0x1ff);
+  T dz[NZ], ge[18];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T x = ((dm >> i) & 1) ? T(0) : v[i * nn + node];
+    T val;
+    q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, val, dz[3 * i], dz[3 * i + 1], dz[3 * i + 2]);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    T x = ((dm >> (3 + k)) & 1) ? T(0) : v[(3 + k) * nn + node];
+    q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, dz[9 + k], ge[3 * k], ge[3 * k + 1], ge[3 * k + 2]);
+  }
+  // sigma = H dz from the packed symmetric store
+  T sg[NZ];
+#pragma unroll
+  for (int r = 0; r < NZ; ++r) sg[r] = T(0);
+  const VT* Hv = reinterpret_cast<const VT*>(H) + blk * (NH / V) * 32 + lane;
+#pragma unroll
+  for (int j = 0; j < NH / V; ++j) {
+    T hv[V];
+    Vec16<T>::unpack(__ldcs(Hv + j * 32), hv);
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      const int idx = j * V + t;
+      // (r, c) of packed index idx (compile-time after unrolling)
+      int r = 0, base = 0;
+#pragma unroll
+      for (int rr = 0; rr < NZ; ++rr) {
+        if (idx >= base + (NZ - rr)) { base += NZ - rr; r = rr + 1; }
+      }
+      const int c = r + (idx - base);
+      sg[r] += hv[t] * dz[c];
+      if (c != r) sg[c] += hv[t] * dz[r];
+    }
+  }
+  const T w = jp.w;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T r = q1_scatter_grad(w * sg[3 * i], w * sg[3 * i + 1], w * sg[3 * i + 2], l8, jp.ihx, jp.ihy, jp.ihz);
+    if (valid && !((dm >> i) & 1)) atomicAdd(&y[i * nn + node], r);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    T gf[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      T s = T(0);
+#pragma unroll
+      for (int l = 0; l < 6; ++l) s += jp.G[k][l] * ge[3 * l + d];
+      gf[d] = w * s;
+    }
+    T r = q1_scatter(w * sg[9 + k], gf[0], gf[1], gf[2], l8, jp.ihx, jp.ihy, jp.ihz);
+    if (valid && !((dm >> (3 + k)) & 1)) atomicAdd(&y[(3 + k) * nn + node], r);
+  }
+}
+
+// y = v at Dirichlet DOFs (identity rows), 0 elsewhere.
+template <typename T>
+__global__ void k_japply_init(int64_t nn, const dmask_t* __restrict__ mask, const T* __restrict__ v,
+                              T* __restrict__ y) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < NF * nn;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t node = i % nn;
+    const int f = int(i / nn);
+    y[i] = ((mask[node] >> f) & 1) ? v[i] : T(0);
+  }
+}
+
+// Nodal 9x9 diagonal blocks: thread (element, local node a) sums over the 8
+// points B_a(q)^T H_q B_a(q) w plus the gradient-energy block, then adds it
+// to the node's block D[(r*9+c)*nn + node].
+template <typename T>
+__global__ void __launch_bounds__(128) k_blockdiag(Grid g, JParams<T> jp, const T* __restrict__ H,
+                                                   T* __restrict__ D) {
+  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t e = tid >> 3;
+  if (e >= g.ne()) return;
+  const int a = int(tid & 7);
+  const int64_t blk = e >> 2;
+  const int lane0 = int(e & 3) * 8;
+  const int64_t nn = g.nn();
+  const int64_t node = elem_node(g, e, a);
+  T Db[45];
+#pragma unroll
+  for (int i = 0; i < 45; ++i) Db[i] = T(0);
+  const T ih[3] = {jp.ihx, jp.ihy, jp.ihz};
+  for (int q = 0; q < 8; ++q) {
+    T phi[3], dphi[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int ad = (a >> d) & 1, qd = (q >> d) & 1;
+      phi[d] = (ad == qd) ? T(GB) : T(GA);
+      dphi[d] = (ad ? T(1) : T(-1)) * ih[d];
+    }
+    const T N = phi[0] * phi[1] * phi[2];
+    const T dN[3] = {dphi[0] * phi[1] * phi[2], phi[0] * dphi[1] * phi[2], phi[0] * phi[1] * dphi[2]};
+    // column map: DOF u_i -> z rows 3i+J (coef dN_J); eta_k -> z row 9+k (coef N)
+    T Hq[NH];
+    for (int j = 0; j < NH; ++j) Hq[j] = H[hstore_offset<T>(blk, j, lane0 + q)];
+    auto hget = [&](int r, int c) -> T { return r <= c ? Hq[hidx(r, c)] : Hq[hidx(c, r)]; };
+    int idx = 0;
+    for (int r = 0; r < 9; ++r)
+      for (int c = r; c < 9; ++c) {
+        T s = T(0);
+        if (r < 3 && c < 3) {
+          for (int J = 0; J < 3; ++J)
+            for (int L = 0; L < 3; ++L) s += dN[J] * dN[L] * hget(3 * r + J, 3 * c + L);
+        } else if (r < 3) {
+          for (int J = 0; J < 3; ++J) s += dN[J] * N * hget(3 * r + J, 9 + (c - 3));
+        } else {
+          s = N * N * hget(9 + (r - 3), 9 + (c - 3)) +
+              (dN[0] * dN[0] + dN[1] * dN[1] + dN[2] * dN[2]) * jp.G[r - 3][c - 3];
+        }
+        Db[idx++] += jp.w * s;
+      }
+  }
+  int idx = 0;
+  for (int r = 0; r < 9; ++r)
+    for (int c = r; c < 9; ++c) {
+      atomicAdd(&D[(r * 9 + c) * nn + node], Db[idx]);
+      if (c != r) atomicAdd(&D[(c * 9 + r) * nn + node], Db[idx]);
+      ++idx;
+    }
+}
+
+// In-place inverse of each node's 9x9 block (Dirichlet rows/columns replaced
+// by identity first) by Gauss-Jordan elimination with partial pivoting.
+template <typename T>
+__global__ void k_block_invert(int64_t nn, const dmask_t* __restrict__ mask, T* __restrict__ D,
+                               int* singular) {
+  const int64_t node = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (node >= nn) return;
+  const dmask_t dm = mask[node];
+  T a[9][9], x[9][9];
+  for (int r = 0; r < 9; ++r)
+    for (int c = 0; c < 9; ++c) {
+      T v = D[(r * 9 + c) * nn + node];
+      if (((dm >> r) & 1) || ((dm >> c) & 1)) v = (r == c) ? T(1) : T(0);
+      a[r][c] = v;
+      x[r][c] = (r == c) ? T(1) : T(0);
+    }
+  bool bad = false;
+  for (int k = 0; k < 9; ++k) {
+    int p = k;
+    T best = fabs(a[k][k]);
+    for (int r = k + 1; r < 9; ++r)
+      if (fabs(a[r][k]) > best) { best = fabs(a[r][k]); p = r; }
+    if (!(best > T(0))) { bad = true; break; }
+    if (p != k)
+      for (int c = 0; c < 9; ++c) {
+        T t = a[k][c]; a[k][c] = a[p][c]; a[p][c] = t;
+        t = x[k][c]; x[k][c] = x[p][c]; x[p][c] = t;
+      }
+    const T ip = T(1) / a[k][k];
+    for (int c = 0; c < 9; ++c) { a[k][c] *= ip; x[k][c] *= ip; }
+    for (int r = 0; r < 9; ++r) {
+      if (r == k) continue;
+      const T f = a[r][k];
+      if (f == T(0)) continue;
+      for (int c = 0; c < 9; ++c) { a[r][c] -= f * a[k][c]; x[r][c] -= f * x[k][c]; }
+    }
+  }
+  if (bad) {
+    atomicExch(singular, 1);
+    for (int r = 0; r < 9; ++r)
+      for (int c = 0; c < 9; ++c) x[r][c] = (r == c) ? T(1) : T(0);
+  }
+  for (int r = 0; r < 9; ++r)
+    for (int c = 0; c < 9; ++c) D[(r * 9 + c) * nn + node] = x[r][c];
+}
+
+__global__ void k_qp_eval(DevParams P, int64_t n, const double* __restrict__ F,
+                          const double* __restrict__ eta, const double* __restrict__ eta_n,
+                          double* __restrict__ W, double* __restrict__ grad, double* __restrict__ hess) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double Fl[9], e[6], en[6], w, g[NZ], h[NH];
+  for (int k = 0; k < 9; ++k) Fl[k] = F[i * 9 + k];
+  for (int k = 0; k < 6; ++k) { e[k] = eta[i * 6 + k]; en[k] = eta_n[i * 6 + k]; }
+  qp_local<double, true>(P, Fl, e, en, &w, g, h);
+  if (W) W[i] = w;
+  if (grad)
+    for (int k = 0; k < NZ; ++k) grad[i * NZ + k] = g[k];
+  if (hess)
+    for (int k = 0; k < NH; ++k) hess[i * NH + k] = h[k];
+}
+
+template <typename T>
+JParams<T> make_jparams(const Grid& g, const DevParams& P) {
+  JParams<T> jp;
+  for (int k = 0; k < 6; ++k)
+    for (int l = 0; l < 6; ++l) jp.G[k][l] = T(P.G[k][l]);
+  jp.w = T(g.w());
+  jp.ihx = T(1.0 / g.hx);
+  jp.ihy = T(1.0 / g.hy);
+  jp.ihz = T(1.0 / g.hz);
+  return jp;
+}
+
+inline unsigned grid_for(int64_t threads, int block) {
+  return unsigned((threads + block - 1) / block);
+}
+
+}  // namespace
+
+void launch_residual(const Grid& g, const DevParams& P, const double* U, const double* Un,
+                     const dmask_t* mask, double* R, double* energy, cudaStream_t s) {
+  const int64_t threads = g.nblk() * 32;
+  k_residual<<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, mask, R, energy);
+}
+
+void launch_linearize(const Grid& g, const DevParams& P, const double* U, const double* Un,
+                      double* H64, float* H32, cudaStream_t s) {
+  const int64_t threads = g.nblk() * 32;
+  k_linearize<<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, H64, H32);
+}
+
+template <typename T>
+void launch_japply(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, const T* v,
+                   T* y, cudaStream_t s) {
+  const int64_t nn = g.nn();
+  k_japply_init<T><<<grid_for(NF * nn, 256) < 4096 ? grid_for(NF * nn, 256) : 4096, 256, 0, s>>>(nn, mask, v, y);
+  const int64_t threads = g.nblk() * 32;
+  k_japply<T><<<grid_for(threads, 256), 256, 0, s>>>(g, make_jparams<T>(g, P), H, mask, v, y);
+}
+
+template <typename T>
+void launch_blockdiag(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, T* D,
+                      cudaStream_t s) {
+  (void)mask;
+  cudaMemsetAsync(D, 0, sizeof(T) * 81 * g.nn(), s);
+  const int64_t threads = g.ne() * 8;
+  k_blockdiag<T><<<grid_for(threads, 128), 128, 0, s>>>(g, make_jparams<T>(g, P), H, D);
+}
+
+template <typename T>
+void launch_block_invert(int64_t nn, const dmask_t* mask, T* D, int* singular, cudaStream_t s) {
+  k_block_invert<T><<<grid_for(nn, 128), 128, 0, s>>>(nn, mask, D, singular);
+}
+
+void launch_qp_eval(const DevParams& P, int64_t n, const double* F, const double* eta,
+                    const double* eta_n, double* W, double* grad, double* hess, cudaStream_t s) {
+  k_qp_eval<<<grid_for(n, 64), 64, 0, s>>>(P, n, F, eta, eta_n, W, grad, hess);
+}
+
+template void launch_japply<float>(const Grid&, const DevParams&, const float*, const dmask_t*,
+                                   const float*, float*, cudaStream_t);
+template void launch_japply<double>(const Grid&, const DevParams&, const double*, const dmask_t*,
+                                     const double*, double*, cudaStream_t);
+template void launch_blockdiag<float>(const Grid&, const DevParams&, const float*, const dmask_t*,
+                                      float*, cudaStream_t);
+template void launch_blockdiag<double>(const Grid&, const DevParams&, const double*, const dmask_t*,
+                                       double*, cudaStream_t);
+template void launch_block_invert<float>(int64_t, const dmask_t*, float*, int*, cudaStream_t);
+template void launch_block_invert<double>(int64_t, const dmask_t*, double*, int*, cudaStream_t);
+
+}  // namespace pfm

@@ -1,0 +1,406 @@
+// Geometric-multigrid kernels (Sec. 3.4): state injection to coarse levels
+// for re-discretisation, trilinear prolongation P and restriction R = P^T
+// between nested or non-nested structured grids on the same box, the damped
+// point-block Jacobi update, and the dense coarse-level operator with its
+// inverse by Gauss-Jordan elimination with partial pivoting.
+//
+// Grid transfer in 1-D: fine node i sits at coarse coordinate i*nc/nf; with
+// i*nc = I0*nf + rem, its interpolation weights are (1 - rem/nf) on coarse
+// node I0 and rem/nf on I0+1. All index arithmetic is integer, so P and
+// R = P^T use identical weights on nested (nf = 2 nc) and non-nested grids.
+#include "common.cuh"
+
+namespace pfm {
+namespace {
+
+inline unsigned grid_for(int64_t threads, int block) {
+  int64_t b = (threads + block - 1) / block;
+  return unsigned(b > 0 ? b : 1);
+}
+
+struct Interp1 {
+  int i0;
+  double t;  // weight of i0+1
+};
+
+__device__ __forceinline__ Interp1 interp1(int i, int nf, int nc) {
+  // coarse coordinate of fine node i: i*nc/nf
+  long long num = (long long)i * nc;
+  int I0 = int(num / nf);
+  long long rem = num - (long long)I0 * nf;
+  if (I0 >= nc) { I0 = nc - 1; rem = nf; }
+  return {I0, double(rem) / double(nf)};
+}
+
+// Value of the nodal field X (grid nx,ny,nz; field stride n) at the point with
+// per-axis element index i0 and local coordinate t (trilinear).
+template <typename T>
+__device__ __forceinline__ double trilinear(const T* X, int nx, int ny, const int i0[3], const double t[3]) {
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int a0 = c & 1, a1 = (c >> 1) & 1, a2 = (c >> 2) & 1;
+    double w = (a0 ? t[0] : 1.0 - t[0]) * (a1 ? t[1] : 1.0 - t[1]) * (a2 ? t[2] : 1.0 - t[2]);
+    if (w == 0.0) continue;
+    int64_t node = (i0[0] + a0) + int64_t(nx + 1) * ((i0[1] + a1) + int64_t(ny + 1) * (i0[2] + a2));
+    s += w * double(X[node]);
+  }
+  return s;
+}
+
+// Coarse state = fine Q1 field evaluated at coarse node positions.
+__global__ void k_inject_state(Grid f, Grid c, const double* __restrict__ Uf, double* __restrict__ Uc) {
+  const int64_t nnc = c.nn();
+  const int64_t nnf = f.nn();
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < nnc;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    int I = int(idx % (c.nx + 1));
+    int J = int((idx / (c.nx + 1)) % (c.ny + 1));
+    int K = int(idx / (int64_t(c.nx + 1) * (c.ny + 1)));
+    // fine coordinate of coarse node: I*nf/nc
+    int i0[3];
+    double t[3];
+    const int Ic[3] = {I, J, K}, nfv[3] = {f.nx, f.ny, f.nz}, ncv[3] = {c.nx, c.ny, c.nz};
+    for (int d = 0; d < 3; ++d) {
+      Interp1 p = interp1(Ic[d], ncv[d], nfv[d]);  // coarse node in fine coordinates
+      i0[d] = p.i0;
+      t[d] = p.t;
+    }
+    for (int fld = 0; fld < NF; ++fld)
+      Uc[fld * nnc + idx] = trilinear(Uf + fld * nnf, f.nx, f.ny, i0, t);
+  }
+}
+
+// Coarse Dirichlet bits = bits of the nearest fine node.
+__global__ void k_coarse_mask(Grid f, Grid c, const dmask_t* __restrict__ mf, dmask_t* __restrict__ mc) {
+  const int64_t nnc = c.nn();
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < nnc;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    int I = int(idx % (c.nx + 1));
+    int J = int((idx / (c.nx + 1)) % (c.ny + 1));
+    int K = int(idx / (int64_t(c.nx + 1) * (c.ny + 1)));
+    auto nearest = [](int Ic, int nc, int nf) { return int((2LL * Ic * nf + nc) / (2LL * nc)); };
+    int i = nearest(I, c.nx, f.nx), j = nearest(J, c.ny, f.ny), k = nearest(K, c.nz, f.nz);
+    mc[idx] = mf[i + int64_t(f.nx + 1) * (j + int64_t(f.ny + 1) * k)];
+  }
+}
+
+// xf += P xc at free fine DOFs.
+template <typename T>
+__global__ void k_prolong_add(Grid f, Grid c, const T* __restrict__ xc, const dmask_t* __restrict__ mf,
+                              T* __restrict__ xf) {
+  const int64_t nnf = f.nn();
+  const int64_t nnc = c.nn();
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < nnf;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    int i = int(idx % (f.nx + 1));
+    int j = int((idx / (f.nx + 1)) % (f.ny + 1));
+    int k = int(idx / (int64_t(f.nx + 1) * (f.ny + 1)));
+    Interp1 px = interp1(i, f.nx, c.nx), py = interp1(j, f.ny, c.ny), pz = interp1(k, f.nz, c.nz);
+    const int i0[3] = {px.i0, py.i0, pz.i0};
+    const double t[3] = {px.t, py.t, pz.t};
+    const dmask_t dm = mf[idx];
+    for (int fld = 0; fld < NF; ++fld) {
+      if ((dm >> fld) & 1) continue;
+      xf[fld * nnf + idx] += T(trilinear(xc + fld * nnc, c.nx, c.ny, i0, t));
+    }
+  }
+}
+
+// rc = P^T rf, zero at coarse Dirichlet DOFs. Coarse node I collects fine
+// nodes i with |i*nc - I*nf| < nf, weight 1 - |i*nc - I*nf|/nf (per axis).
+template <typename T>
+__global__ void k_restrict(Grid f, Grid c, const T* __restrict__ rf, const dmask_t* __restrict__ mc,
+                           T* __restrict__ rc) {
+  const int64_t nnf = f.nn();
+  const int64_t nnc = c.nn();
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < nnc;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    const int Ic[3] = {int(idx % (c.nx + 1)), int((idx / (c.nx + 1)) % (c.ny + 1)),
+                       int(idx / (int64_t(c.nx + 1) * (c.ny + 1)))};
+    const int nfv[3] = {f.nx, f.ny, f.nz}, ncv[3] = {c.nx, c.ny, c.nz};
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+      long long center = (long long)Ic[d] * nfv[d];  // in units of 1/(nf*nc) ... i*nc vs I*nf
+      // i*nc > I*nf - nf  and  i*nc < I*nf + nf
+      long long a = center - nfv[d];
+      long long b = center + nfv[d];
+      int l = int(a >= 0 ? a / ncv[d] + 1 : 0);
+      int h = int(b % ncv[d] == 0 ? b / ncv[d] - 1 : b / ncv[d]);
+      if (l < 0) l = 0;
+      if (h > nfv[d]) h = nfv[d];
+      lo[d] = l;
+      hi[d] = h;
+    }
+    const dmask_t dm = mc[idx];
+    double acc[NF];
+    for (int fld = 0; fld < NF; ++fld) acc[fld] = 0.0;
+    for (int k = lo[2]; k <= hi[2]; ++k) {
+      double wz = 1.0 - fabs(double((long long)k * ncv[2] - (long long)Ic[2] * nfv[2])) / nfv[2];
+      for (int j = lo[1]; j <= hi[1]; ++j) {
+        double wy = 1.0 - fabs(double((long long)j * ncv[1] - (long long)Ic[1] * nfv[1])) / nfv[1];
+        for (int i = lo[0]; i <= hi[0]; ++i) {
+          double wx = 1.0 - fabs(double((long long)i * ncv[0] - (long long)Ic[0] * nfv[0])) / nfv[0];
+          const double w = wx * wy * wz;
+          const int64_t fn = i + int64_t(f.nx + 1) * (j + int64_t(f.ny + 1) * k);
+          for (int fld = 0; fld < NF; ++fld) acc[fld] += w * double(rf[fld * nnf + fn]);
+        }
+      }
+    }
+    for (int fld = 0; fld < NF; ++fld) rc[fld * nnc + idx] = ((dm >> fld) & 1) ? T(0) : T(acc[fld]);
+  }
+}
+
+// x += omega D^-1 (b - y) per node (y == nullptr: y = 0).
+template <typename T>
+__global__ void k_smooth(int64_t nn, const T* __restrict__ D, const T* __restrict__ b,
+                         const T* __restrict__ y, T omega, T* __restrict__ x) {
+  for (int64_t node = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; node < nn;
+       node += int64_t(gridDim.x) * blockDim.x) {
+    T r[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) r[f] = b[f * nn + node] - (y ? y[f * nn + node] : T(0));
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T s = T(0);
+#pragma unroll
+      for (int c = 0; c < NF; ++c) s += D[(f * 9 + c) * nn + node] * r[c];
+      x[f * nn + node] += omega * s;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_sub(int64_t n, const T* __restrict__ b, const T* __restrict__ y, T* __restrict__ r) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    r[i] = b[i] - y[i];
+}
+
+// Dense coarse operator K (row-major, leading dimension ld) from the stored
+// point Hessians: thread (element, local row l = f*8 + a) adds row l of the
+// element matrix sum_q w (Bz^T H_q Bz + Bg^T G Bg).
+template <typename T>
+__global__ void k_coarse_assemble(Grid g, DevParams P, const T* __restrict__ H, double* __restrict__ K,
+                                  int ld) {
+  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t e = tid / 72;
+  if (e >= g.ne()) return;
+  const int l = int(tid % 72);
+  const int fl = l / 8, al = l % 8;
+  const int64_t nn = g.nn();
+  const double ih[3] = {1.0 / g.hx, 1.0 / g.hy, 1.0 / g.hz};
+  const double w = g.w();
+  auto node_of = [&](int a) {
+    int64_t ei = e % g.nx, r = e / g.nx, ej = r % g.ny, ek = r / g.ny;
+    return (ei + (a & 1)) + int64_t(g.nx + 1) * ((ej + ((a >> 1) & 1)) + int64_t(g.ny + 1) * (ek + (a >> 2)));
+  };
+  auto shape = [&](int a, int q, double& N, double dN[3]) {
+    double phi[3], dphi[3];
+    for (int d = 0; d < 3; ++d) {
+      const int ad = (a >> d) & 1, qd = (q >> d) & 1;
+      phi[d] = (ad == qd) ? GB : GA;
+      dphi[d] = (ad ? 1.0 : -1.0) * ih[d];
+    }
+    N = phi[0] * phi[1] * phi[2];
+    dN[0] = dphi[0] * phi[1] * phi[2];
+    dN[1] = phi[0] * dphi[1] * phi[2];
+    dN[2] = phi[0] * phi[1] * dphi[2];
+  };
+  const int64_t row = fl * nn + node_of(al);
+  const int64_t blk = e >> 2;
+  const int lane0 = int(e & 3) * 8;
+  for (int m = 0; m < 72; ++m) {
+    const int fm = m / 8, am = m % 8;
+    double s = 0.0;
+    for (int q = 0; q < 8; ++q) {
+      double Nl, dNl[3], Nm, dNm[3];
+      shape(al, q, Nl, dNl);
+      shape(am, q, Nm, dNm);
+      // z-rows touched by DOF (f, a): u_i -> 3i+J (dN_J); eta_k -> 9+k (N)
+      int rl[3], rm[3];
+      double cl[3], cm[3];
+      int nl, nm;
+      if (fl < 3) { nl = 3; for (int J = 0; J < 3; ++J) { rl[J] = 3 * fl + J; cl[J] = dNl[J]; } }
+      else { nl = 1; rl[0] = 9 + fl - 3; cl[0] = Nl; }
+      if (fm < 3) { nm = 3; for (int J = 0; J < 3; ++J) { rm[J] = 3 * fm + J; cm[J] = dNm[J]; } }
+      else { nm = 1; rm[0] = 9 + fm - 3; cm[0] = Nm; }
+      for (int x = 0; x < nl; ++x)
+        for (int y = 0; y < nm; ++y) {
+          const int r = rl[x] < rm[y] ? rl[x] : rm[y];
+          const int cc = rl[x] < rm[y] ? rm[y] : rl[x];
+          s += cl[x] * cm[y] * double(H[hstore_offset<T>(blk, hidx(r, cc), lane0 + q)]);
+        }
+      if (fl >= 3 && fm >= 3)
+        s += (dNl[0] * dNm[0] + dNl[1] * dNm[1] + dNl[2] * dNm[2]) * P.G[fl - 3][fm - 3];
+    }
+    const int64_t col = fm * nn + node_of(am);
+    atomicAdd(&K[row * ld + col], w * s);
+  }
+}
+
+// Dirichlet rows/columns -> identity, and the identity block of the augmented matrix.
+__global__ void k_coarse_bc(int n, int64_t nn, const dmask_t* __restrict__ mask, double* __restrict__ K,
+                            int ld) {
+  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (tid >= int64_t(n) * n) return;
+  const int r = int(tid / n), c = int(tid % n);
+  const bool dr = (mask[r % nn] >> (r / nn)) & 1;
+  const bool dc = (mask[c % nn] >> (c / nn)) & 1;
+  if (dr || dc) K[int64_t(r) * ld + c] = (r == c) ? 1.0 : 0.0;
+  K[int64_t(r) * ld + n + c] = (r == c) ? 1.0 : 0.0;
+}
+
+// Gauss-Jordan step k on the augmented n x 2n matrix: pivot search over rows
+// k..n-1 of column k, row swap, normalisation of the pivot row, and the
+// multipliers f_i = M[i][k] (f_k = 0).
+__global__ void k_gj_pivot(double* __restrict__ M, int n, int ld, int k, double* __restrict__ f,
+                           int* singular) {
+  __shared__ double sval[1024];
+  __shared__ int sidx[1024];
+  double best = -1.0;
+  int bi = k;
+  for (int r = k + threadIdx.x; r < n; r += blockDim.x) {
+    double v = fabs(M[int64_t(r) * ld + k]);
+    if (v > best) { best = v; bi = r; }
+  }
+  sval[threadIdx.x] = best;
+  sidx[threadIdx.x] = bi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      double o = sval[threadIdx.x + s];
+      int oi = sidx[threadIdx.x + s];
+      if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
+        sval[threadIdx.x] = o;
+        sidx[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  const int p = sidx[0];
+  const double pv = sval[0];
+  if (!(pv > 0.0)) {
+    if (threadIdx.x == 0) *singular = 1;
+    return;
+  }
+  if (p != k)
+    for (int c = threadIdx.x; c < 2 * n; c += blockDim.x) {
+      double t = M[int64_t(k) * ld + c];
+      M[int64_t(k) * ld + c] = M[int64_t(p) * ld + c];
+      M[int64_t(p) * ld + c] = t;
+    }
+  __syncthreads();
+  const double ip = 1.0 / M[int64_t(k) * ld + k];
+  __syncthreads();
+  for (int c = threadIdx.x; c < 2 * n; c += blockDim.x) M[int64_t(k) * ld + c] *= ip;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) f[r] = (r == k) ? 0.0 : M[int64_t(r) * ld + k];
+}
+
+// M[i][j] -= f_i M[k][j] for all rows i != k and columns j >= k.
+__global__ void k_gj_update(double* __restrict__ M, int n, int ld, int k, const double* __restrict__ f,
+                            const int* singular) {
+  if (*singular) return;
+  const int ncol = 2 * n - k;
+  const int64_t total = int64_t(n) * ncol;
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int i = int(t / ncol);
+    const int j = k + int(t % ncol);
+    const double fi = f[i];
+    if (fi != 0.0) M[int64_t(i) * ld + j] -= fi * M[int64_t(k) * ld + j];
+  }
+}
+
+// x = Ainv b (Ainv = right half of the reduced augmented matrix, ld = 2n).
+template <typename T>
+__global__ void k_coarse_solve(int n, const double* __restrict__ Aug, const T* __restrict__ b,
+                               T* __restrict__ x) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* row = Aug + int64_t(warp) * 2 * n + n;
+  double s = 0.0;
+  for (int c = lane; c < n; c += 32) s += row[c] * double(b[c]);
+  for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+  if (lane == 0) x[warp] = T(s);
+}
+
+}  // namespace
+
+void launch_inject_state(const Grid& fine, const Grid& coarse, const double* Uf, double* Uc,
+                         cudaStream_t s) {
+  k_inject_state<<<grid_for(coarse.nn(), 128), 128, 0, s>>>(fine, coarse, Uf, Uc);
+}
+
+void launch_coarse_mask(const Grid& fine, const Grid& coarse, const dmask_t* mf, dmask_t* mc,
+                        cudaStream_t s) {
+  k_coarse_mask<<<grid_for(coarse.nn(), 128), 128, 0, s>>>(fine, coarse, mf, mc);
+}
+
+template <typename T>
+void launch_prolong_add(const Grid& fine, const Grid& coarse, const T* xc, const dmask_t* mf, T* xf,
+                        cudaStream_t s) {
+  k_prolong_add<T><<<grid_for(fine.nn(), 256), 256, 0, s>>>(fine, coarse, xc, mf, xf);
+}
+
+template <typename T>
+void launch_restrict(const Grid& fine, const Grid& coarse, const T* rf, const dmask_t* mc, T* rc,
+                     cudaStream_t s) {
+  k_restrict<T><<<grid_for(coarse.nn(), 128), 128, 0, s>>>(fine, coarse, rf, mc, rc);
+}
+
+template <typename T>
+void launch_smooth(int64_t nn, const T* D, const T* b, const T* y, T omega, T* x, cudaStream_t s) {
+  k_smooth<T><<<grid_for(nn, 256), 256, 0, s>>>(nn, D, b, y, omega, x);
+}
+
+template <typename T>
+void launch_sub(int64_t n, const T* b, const T* y, T* r, cudaStream_t s) {
+  k_sub<T><<<grid_for(n, 256), 256, 0, s>>>(n, b, y, r);
+}
+
+template <typename T>
+void launch_coarse_assemble(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask,
+                            double* K, int ld, cudaStream_t s) {
+  const int n = int(NF * g.nn());
+  cudaMemsetAsync(K, 0, sizeof(double) * size_t(n) * ld, s);
+  k_coarse_assemble<T><<<grid_for(g.ne() * 72, 128), 128, 0, s>>>(g, P, H, K, ld);
+  k_coarse_bc<<<grid_for(int64_t(n) * n, 256), 256, 0, s>>>(n, g.nn(), mask, K, ld);
+}
+
+// Reduce the augmented [K | I] (n x 2n, ld = 2n) to [I | K^-1]; returns the
+// number of kernel launches.
+int dense_gauss_jordan_inverse(double* Maug, int n, double* f, int* singular, cudaStream_t s) {
+  const int ld = 2 * n;
+  int launches = 0;
+  for (int k = 0; k < n; ++k) {
+    k_gj_pivot<<<1, 1024, 0, s>>>(Maug, n, ld, k, f, singular);
+    const int64_t total = int64_t(n) * (2 * n - k);
+    unsigned blocks = grid_for(total, 256);
+    if (blocks > 1216) blocks = 1216;
+    k_gj_update<<<blocks, 256, 0, s>>>(Maug, n, ld, k, f, singular);
+    launches += 2;
+  }
+  return launches;
+}
+
+template <typename T>
+void launch_coarse_solve(int n, const double* Ainv, const T* b, T* x, cudaStream_t s) {
+  k_coarse_solve<T><<<grid_for(int64_t(n) * 32, 256), 256, 0, s>>>(n, Ainv, b, x);
+}
+
+#define PFM_INST(T)                                                                              \
+  template void launch_prolong_add<T>(const Grid&, const Grid&, const T*, const dmask_t*, T*,     \
+                                      cudaStream_t);                                            \
+  template void launch_restrict<T>(const Grid&, const Grid&, const T*, const dmask_t*, T*,        \
+                                   cudaStream_t);                                               \
+  template void launch_smooth<T>(int64_t, const T*, const T*, const T*, T, T*, cudaStream_t);     \
+  template void launch_sub<T>(int64_t, const T*, const T*, T*, cudaStream_t);                     \
+  template void launch_coarse_assemble<T>(const Grid&, const DevParams&, const T*, const dmask_t*, \
+                                          double*, int, cudaStream_t);                          \
+  template void launch_coarse_solve<T>(int, const double*, const T*, T*, cudaStream_t);
+PFM_INST(float)
+PFM_INST(double)
+#undef PFM_INST
+
+}  // namespace pfm

@@ -1,0 +1,47 @@
+// Conversion of the public parameter block into the kernels' parameter block.
+#pragma once
+
+#include <cmath>
+
+#include "../../include/pfm.h"
+#include "qp_physics.cuh"
+
+namespace pfm {
+
+// Derived coefficients (Sec. 2.2-2.3, Eq. IntEnergy, Eq. PenPot):
+//   inv_mtau_i = 1/(m_i tau)                       (dissipation Hessian)
+//   cobst_ij   = 4 s gamma_ij / (pi ell_ij)         (local obstacle term)
+//   a_ij       = cobst_ij ell_ij^2                  (gradient term)
+// The gradient energy -sum_{i<j} a_ij grad eta_i . grad eta_j, written in the
+// condensed unknowns (grad eta_0 = -sum grad eta_k), is 1/2 sum_d
+// (d_d eta_hat)^T G (d_d eta_hat) with G = T^T Ahat T, Ahat_ij = -a_ij (i != j),
+// Ahat_ii = 0, and T the 7x6 map eta = e_0 + T eta_hat.
+inline void make_dev_params(const pfm_params& in, DevParams& out) {
+  const double pi = 3.14159265358979323846;
+  for (int p = 0; p < NPH; ++p) {
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) out.U[p][i][j] = in.Ut[p][3 * i + j];
+    for (int I = 0; I < 6; ++I)
+      for (int J = 0; J < 6; ++J) out.Lv[p][I][J] = in.Lvoigt[p][6 * I + J];
+    out.F0[p] = in.F0[p];
+    out.inv_mtau[p] = 1.0 / (in.mobility[p] * in.tau);
+  }
+  double Ahat[NPH][NPH];
+  for (int i = 0; i < NPH; ++i)
+    for (int j = 0; j < NPH; ++j) {
+      if (i == j) {
+        out.cobst[i][j] = 0.0;
+        Ahat[i][j] = 0.0;
+      } else {
+        double c = 4.0 * in.gamma_scale * in.gamma[i][j] / (pi * in.ell[i][j]);
+        out.cobst[i][j] = c;
+        Ahat[i][j] = -c * in.ell[i][j] * in.ell[i][j];
+      }
+    }
+  for (int k = 0; k < 6; ++k)
+    for (int l = 0; l < 6; ++l)
+      out.G[k][l] = Ahat[k + 1][l + 1] - Ahat[0][l + 1] - Ahat[k + 1][0] + Ahat[0][0];
+  out.eps_eta = in.eps_eta;
+}
+
+}  // namespace pfm

@@ -1,0 +1,625 @@
+// Quadrature-point physics of the multivariant finite-strain phase-field
+// model: local energy density, its gradient and its exact 15x15 Hessian with
+// respect to z = (F_iJ row-major, eta_1..eta_6).
+//
+// Model (Sec. 2.1-2.3, Sec. 3.1): eta_0 = 1 - sum eta_k; F^t = sum_i eta_i U_i
+// (Eq. LinMix); F^e = F (F^t)^-1, C^e = F^eT F^e, H^e = 1/2 log C^e and
+// F_el = 1/2 det(F^t) H^e . L(eta) H^e with L = sum_i eta_i L_i
+// (Eq. elasticEn); chemical sum eta_i F_i^0; local part of the double
+// obstacle sum_{i<j} 4 gamma_ij/(pi ell_ij) eta_i eta_j (Eq. IntEnergy);
+// backward-Euler dissipation sum (eta_i - eta_i,n)^2/(2 m_i tau) (Sec. 2.3);
+// penalty sum 1/2 eps <eta_i>_-^2 (Eq. PenPot). The gradient part of the
+// interface energy is a constant quadratic form handled by the element
+// kernels.
+//
+// Derivatives. With A = (F^t)^-1, M = F A, E = C^e = M^T M and the energy
+// written as g(E, eta) = 1/2 J_t h(E):L(eta):h(E), J_t = det F^t, the chain
+// rule gives first and second derivatives from those of E and of h = 1/2 log.
+// The derivatives of the matrix logarithm use the spectral decomposition of
+// E (cyclic Jacobi) and the Daleckii-Krein formulas: in the eigenbasis,
+// Dlog[X]_ab = f1(l_a,l_b) X_ab and
+// D2log[X,Y]_ab = sum_c f2(l_a,l_c,l_b) (X_ac Y_cb + Y_ac X_cb), with f1, f2
+// the first and second divided differences of log. These are exact for
+// repeated eigenvalues as long as the divided differences are evaluated
+// without cancellation, which dd1_log / dd2_log do (log1p quotient; Taylor
+// series of the second divided difference about the mean when all three
+// arguments are close).
+#pragma once
+
+#ifdef __CUDACC__
+#define PFM_HD __host__ __device__ __forceinline__
+#define PFM_HD_BIG __host__ __device__
+#else
+#define PFM_HD_BIG inline
+#include <cmath>
+#define PFM_HD inline
+using std::sqrt;
+using std::log;
+using std::log1p;
+using std::fabs;
+#endif
+
+namespace pfm {
+
+constexpr int NPH = 7;    // phases: austenite + 6 variants (Sec. 5.1)
+constexpr int NZ = 15;    // local unknowns at a point: F (9) + eta_hat (6)
+constexpr int NH = 120;   // packed upper triangle of the 15x15 Hessian
+
+// Physical parameters, passed by value to kernels (constant bank).
+struct DevParams {
+  double U[NPH][3][3];      // transformation stretches U_i (U_0 = I)
+  double Lv[NPH][6][6];     // stiffness L_i in Voigt form (engineering shear)
+  double F0[NPH];           // chemical energies F_i^0
+  double inv_mtau[NPH];     // 1 / (m_i tau)
+  double cobst[NPH][NPH];   // 4 gamma_ij / (pi ell_ij), zero diagonal
+  double G[6][6];           // gradient-energy matrix in eta_hat (per direction)
+  double eps_eta;           // penalty parameter
+};
+
+// Packed index of (r, c), r <= c, in the row-major upper triangle.
+PFM_HD int hidx(int r, int c) { return r * NZ - (r * (r - 1)) / 2 + (c - r); }
+
+template <typename T> struct Tol;
+template <> struct Tol<double> {
+  static constexpr double dd2_gap = 1e-3;    // relative spread below which f2 uses its Taylor series
+  static constexpr double jacobi_off = 1e-17;
+};
+template <> struct Tol<float> {
+  static constexpr float dd2_gap = 3e-2f;
+  static constexpr float jacobi_off = 1e-8f;
+};
+
+template <typename T> PFM_HD T tmin(T a, T b) { return a < b ? a : b; }
+
+// ---------------------------------------------------------------------------
+// 3x3 helpers (full storage)
+
+template <typename T>
+PFM_HD void mm3(const T a[3][3], const T b[3][3], T c[3][3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c[i][k] = a[i][0] * b[0][k] + a[i][1] * b[1][k] + a[i][2] * b[2][k];
+}
+
+// c = a^T b
+template <typename T>
+PFM_HD void mtm3(const T a[3][3], const T b[3][3], T c[3][3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c[i][k] = a[0][i] * b[0][k] + a[1][i] * b[1][k] + a[2][i] * b[2][k];
+}
+
+// c = Q^T a Q (rotate a symmetric matrix into the basis of Q's columns)
+template <typename T>
+PFM_HD void rot_in(const T Q[3][3], const T a[3][3], T c[3][3]) {
+  T t[3][3];
+  mm3(a, Q, t);
+  mtm3(Q, t, c);
+}
+
+template <typename T>
+PFM_HD T tr_ab(const T a[3][3], const T b[3][3]) {  // tr(a b)
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) s += a[i][j] * b[j][i];
+  return s;
+}
+
+template <typename T>
+PFM_HD T ddot3(const T a[3][3], const T b[3][3]) {  // a : b
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) s += a[i][j] * b[i][j];
+  return s;
+}
+
+// Inverse and determinant of a symmetric positive-definite 3x3 matrix.
+template <typename T>
+PFM_HD T inv_sym3(const T a[3][3], T r[3][3]) {
+  T c00 = a[1][1] * a[2][2] - a[1][2] * a[2][1];
+  T c01 = a[1][2] * a[2][0] - a[1][0] * a[2][2];
+  T c02 = a[1][0] * a[2][1] - a[1][1] * a[2][0];
+  T det = a[0][0] * c00 + a[0][1] * c01 + a[0][2] * c02;
+  T id = T(1) / det;
+  r[0][0] = c00 * id;
+  r[0][1] = r[1][0] = c01 * id;
+  r[0][2] = r[2][0] = c02 * id;
+  r[1][1] = (a[0][0] * a[2][2] - a[0][2] * a[2][0]) * id;
+  r[1][2] = r[2][1] = (a[0][2] * a[1][0] - a[0][0] * a[1][2]) * id;
+  r[2][2] = (a[0][0] * a[1][1] - a[0][1] * a[1][0]) * id;
+  return det;
+}
+
+// Voigt vector with engineering shear: (a00, a11, a22, 2a12, 2a02, 2a01).
+template <typename T>
+PFM_HD void voigt_strain(const T a[3][3], T v[6]) {
+  v[0] = a[0][0]; v[1] = a[1][1]; v[2] = a[2][2];
+  v[3] = a[1][2] + a[2][1]; v[4] = a[0][2] + a[2][0]; v[5] = a[0][1] + a[1][0];
+}
+// Symmetric tensor from a Voigt stress vector (no shear factor).
+template <typename T>
+PFM_HD void from_voigt_stress(const T v[6], T a[3][3]) {
+  a[0][0] = v[0]; a[1][1] = v[1]; a[2][2] = v[2];
+  a[1][2] = a[2][1] = v[3]; a[0][2] = a[2][0] = v[4]; a[0][1] = a[1][0] = v[5];
+}
+
+
+// Packed symmetric 3x3 storage (00, 11, 22, 12, 02, 01), the Voigt order.
+PFM_HD int sym_i(int v) { return v < 3 ? v : (v == 3 ? 1 : 0); }
+PFM_HD int sym_j(int v) { return v < 3 ? v : (v == 5 ? 1 : 2); }
+template <typename T>
+PFM_HD T symget(const T* X, int a, int b) {
+  if (a == b) return X[a];
+  const int s = a + b;  // (1,2) -> 3, (0,2) -> 2, (0,1) -> 1
+  return X[s == 3 ? 3 : (s == 2 ? 4 : 5)];
+}
+// Packed index of (k, l), k <= l, in the upper triangle of a 16x16 matrix.
+PFM_HD int hp16(int k, int l) { return k * 16 - (k * (k - 1)) / 2 + (l - k); }
+
+template <typename T>
+PFM_HD void load_U(const DevParams& P, int p, T U[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) U[i][j] = T(P.U[p][i][j]);
+}
+
+// ---------------------------------------------------------------------------
+// Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations:
+// a = Q diag(lam) Q^T, Q orthonormal (columns are eigenvectors).
+
+template <typename T>
+PFM_HD void jacobi_eig3(T a[3][3], T lam[3], T Q[3][3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Q[i][j] = (i == j) ? T(1) : T(0);
+  for (int sweep = 0; sweep < 16; ++sweep) {
+    T off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
+    T dia = fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2]);
+    if (off <= Tol<T>::jacobi_off * dia) break;
+#pragma unroll
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = (pq == 2) ? 1 : 0;
+      const int q = (pq == 0) ? 1 : 2;
+      const int r = 3 - p - q;
+      T apq = a[p][q];
+      if (fabs(apq) <= Tol<T>::jacobi_off * (fabs(a[p][p]) + fabs(a[q][q]))) {
+        a[p][q] = a[q][p] = T(0);
+        continue;
+      }
+      // rotation angle phi with cot(2 phi) = theta zeroes a_pq; t = tan(phi)
+      T theta = (a[q][q] - a[p][p]) / (T(2) * apq);
+      T t = T(1) / (fabs(theta) + sqrt(theta * theta + T(1)));
+      if (theta < T(0)) t = -t;
+      T c = T(1) / sqrt(t * t + T(1));
+      T s = t * c;
+      T tau = s / (T(1) + c);
+      a[p][p] -= t * apq;
+      a[q][q] += t * apq;
+      a[p][q] = a[q][p] = T(0);
+      T arp = a[r][p], arq = a[r][q];
+      a[r][p] = a[p][r] = arp - s * (arq + tau * arp);
+      a[r][q] = a[q][r] = arq + s * (arp - tau * arq);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        T qkp = Q[k][p], qkq = Q[k][q];
+        Q[k][p] = qkp - s * (qkq + tau * qkp);
+        Q[k][q] = qkq + s * (qkp - tau * qkq);
+      }
+    }
+  }
+  lam[0] = a[0][0]; lam[1] = a[1][1]; lam[2] = a[2][2];
+}
+
+// First divided difference of log: (log a - log b)/(a - b), 1/a if a == b.
+template <typename T>
+PFM_HD T dd1_log(T a, T b) {
+  if (a < b) { T t = a; a = b; b = t; }
+  T d = a - b;
+  if (d == T(0)) return T(1) / a;
+  return log1p(d / b) / d;
+}
+
+// Second divided difference of log, symmetric in its arguments.
+template <typename T>
+PFM_HD T dd2_log(T x0, T x1, T x2) {
+  // sort descending: a >= b >= c
+  T a = x0, b = x1, c = x2, t;
+  if (a < b) { t = a; a = b; b = t; }
+  if (b < c) { t = b; b = c; c = t; }
+  if (a < b) { t = a; a = b; b = t; }
+  T gap = a - c;
+  if (gap > Tol<T>::dd2_gap * a) return (dd1_log(a, b) - dd1_log(b, c)) / gap;
+  // f[x0,x1,x2] = sum_j f^(2+j)(m)/(2+j)! h_j(x - m); for log this is
+  // (1/m^2) sum_j (-1)^(j+1) h_j(u)/(j+2), u = (x - m)/m, h_j the complete
+  // homogeneous symmetric polynomial of degree j.
+  T m = (a + b + c) / T(3);
+  T u0 = (a - m) / m, u1 = (b - m) / m, u2 = (c - m) / m;
+  // h_j(u0,u1) by h_j = u0 h_{j-1}(u0) ... built incrementally
+  T h2[6];  // h_j(u0,u1), j = 0..5
+  for (int j = 0; j < 6; ++j) {
+    // h_j(u0,u1) = sum_{i=0}^j u0^i u1^(j-i)
+    T s = T(0), u0i = T(1);
+    for (int i = 0; i <= j; ++i) {
+      T u1p = T(1);
+      for (int k = 0; k < j - i; ++k) u1p *= u1;
+      s += u0i * u1p;
+      u0i *= u0;
+    }
+    h2[j] = s;
+  }
+  T sum = T(0);
+  T sign = T(-1);
+  for (int j = 0; j < 6; ++j) {
+    // h_j(u0,u1,u2) = sum_{i=0}^j u2^i h_{j-i}(u0,u1)
+    T hj = T(0), u2i = T(1);
+    for (int i = 0; i <= j; ++i) { hj += u2i * h2[j - i]; u2i *= u2; }
+    sum += sign * hj / T(j + 2);
+    sign = -sign;
+  }
+  return sum / (m * m);
+}
+
+// ---------------------------------------------------------------------------
+// Local energy density with gradient and (optionally) packed Hessian.
+//
+// Fin: F row-major; eh, ehn: eta_1..eta_6 at t_{n+1} and t_n.
+// Outputs: *W, g[15] = dW/dz, Hp[120] = packed d^2W/dz^2 (if Hp != nullptr).
+template <typename T, bool WANT_HESS>
+PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], const T ehn[6], T* W,
+                     T g[NZ], T* Hp) {
+  T eta[NPH], etan[NPH];
+  {
+    T s = 0, sn = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { eta[k + 1] = eh[k]; etan[k + 1] = ehn[k]; s += eh[k]; sn += ehn[k]; }
+    eta[0] = T(1) - s;
+    etan[0] = T(1) - sn;
+  }
+  T F[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) F[i][j] = Fin[3 * i + j];
+
+  // transformation stretch, its inverse and determinant
+  T Ft[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+  for (int p = 0; p < NPH; ++p)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Ft[i][j] += eta[p] * T(P.U[p][i][j]);
+  T A[3][3];
+  const T Jt = inv_sym3(Ft, A);
+  T M[3][3];  // F^e = F A
+  mm3(F, A, M);
+  T E[3][3];  // C^e = M^T M
+  mtm3(M, M, E);
+
+  // spectral decomposition of C^e and the Hencky strain h = 1/2 log C^e
+  T lam[3], Q[3][3];
+  {
+    T tmp[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) tmp[i][j] = E[i][j];
+    jacobi_eig3(tmp, lam, Q);
+  }
+  T loglam[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) loglam[a] = log(lam[a]);
+  T f1[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) f1[a][b] = (a == b) ? T(1) / lam[a] : dd1_log(lam[a], lam[b]);
+  T h[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      h[i][j] = T(0.5) * (Q[i][0] * loglam[0] * Q[j][0] + Q[i][1] * loglam[1] * Q[j][1] +
+                          Q[i][2] * loglam[2] * Q[j][2]);
+
+  // stress-like T = L(eta) : h and the per-phase L_i : h
+  T hv[6];
+  voigt_strain(h, hv);
+  T Tv[6] = {0, 0, 0, 0, 0, 0};
+  T hLh[NPH];  // h : L_i : h
+#pragma unroll
+  for (int p = 0; p < NPH; ++p) {
+    T s = 0;
+#pragma unroll
+    for (int I = 0; I < 6; ++I) {
+      T li = 0;
+#pragma unroll
+      for (int J = 0; J < 6; ++J) li += T(P.Lv[p][I][J]) * hv[J];
+      Tv[I] += eta[p] * li;
+      s += hv[I] * li;
+    }
+    hLh[p] = s;
+  }
+  T hT = 0;
+#pragma unroll
+  for (int I = 0; I < 6; ++I) hT += hv[I] * Tv[I];
+  T Tm[3][3];
+  from_voigt_stress(Tv, Tm);
+
+  // S = dW_el/dE = J_t Dh[T] = 1/2 J_t Dlog[T]; in the eigenbasis S~ = 1/2 J_t f1 o T~
+  T Tt[3][3];
+  rot_in(Q, Tm, Tt);
+  T St[3][3], S[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) St[a][b] = T(0.5) * Jt * f1[a][b] * Tt[a][b];
+  {
+    T t[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) t[i][b] = Q[i][0] * St[0][b] + Q[i][1] * St[1][b] + Q[i][2] * St[2][b];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) S[i][j] = t[i][0] * Q[j][0] + t[i][1] * Q[j][1] + t[i][2] * Q[j][2];
+  }
+
+  // energy
+  T Wloc = T(0.5) * Jt * hT;
+  T geta[NPH];  // dW/d eta_i, all local terms
+  T trAU[NPH];  // tr(A U_i) = (d J_t / d eta_i) / J_t
+  T AU[NPH][3][3];
+#pragma unroll
+  for (int p = 0; p < NPH; ++p) {
+    T Up[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Up[i][j] = T(P.U[p][i][j]);
+    mm3(A, Up, AU[p]);
+    trAU[p] = AU[p][0][0] + AU[p][1][1] + AU[p][2][2];
+  }
+  {
+    T ES[3][3];  // E S
+    mm3(E, S, ES);
+#pragma unroll
+    for (int p = 0; p < NPH; ++p) {
+      // S : dE/d eta_p = -2 tr(S A U_p E) = -2 tr(E S A U_p)
+      T via_E = T(-2) * tr_ab(ES, AU[p]);
+      geta[p] = T(0.5) * Jt * trAU[p] * hT + T(0.5) * Jt * hLh[p] + via_E;
+    }
+  }
+  // chemical, obstacle, dissipation, penalty
+#pragma unroll
+  for (int i = 0; i < NPH; ++i) {
+    T d = eta[i] - etan[i];
+    T neg = eta[i] < T(0) ? eta[i] : T(0);
+    Wloc += eta[i] * T(P.F0[i]) + T(0.5) * T(P.inv_mtau[i]) * d * d + T(0.5) * T(P.eps_eta) * neg * neg;
+    T go = 0;
+#pragma unroll
+    for (int j = 0; j < NPH; ++j) {
+      if (j > i) Wloc += T(P.cobst[i][j]) * eta[i] * eta[j];
+      go += T(P.cobst[i][j]) * eta[j];
+    }
+    geta[i] += T(P.F0[i]) + go + T(P.inv_mtau[i]) * d + T(P.eps_eta) * neg;
+  }
+  *W = Wloc;
+
+  // gradient: P_el = 2 M S A, then eta_hat_k = eta_k - eta_0 (Sec. 3.1)
+  {
+    T MS[3][3], Pm[3][3];
+    mm3(M, S, MS);
+    mm3(MS, A, Pm);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) g[3 * i + j] = T(2) * Pm[i][j];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) g[9 + k] = geta[k + 1] - geta[0];
+  }
+  if (!WANT_HESS) return;
+
+  // ---------------------------------------------------------------------
+  // Hessian over the 16 directions (F_pQ: 0..8, eta_0..eta_6: 9..15), kept as
+  // the packed upper triangle H16[hp16(k,l)], k <= l. Rotated directions
+  // X~_k = Q^T dE_k Q are symmetric and stored as 6 values (00,11,22,12,02,01).
+  constexpr int ND = 16;
+  T Xs[ND][6];
+  T At[3][3];
+  rot_in(Q, A, At);
+  {
+    T Aq[3][3], Mq[3][3];  // Aq[c] = Q^T (column c of A), Mq[p] = Q^T (row p of M)
+    for (int c = 0; c < 3; ++c)
+      for (int a = 0; a < 3; ++a) {
+        Aq[c][a] = Q[0][a] * A[0][c] + Q[1][a] * A[1][c] + Q[2][a] * A[2][c];
+        Mq[c][a] = Q[0][a] * M[c][0] + Q[1][a] * M[c][1] + Q[2][a] * M[c][2];
+      }
+    for (int p = 0; p < 3; ++p)
+      for (int c = 0; c < 3; ++c) {
+        T* X = Xs[3 * p + c];
+        for (int v = 0; v < 6; ++v) {
+          const int a = sym_i(v), b = sym_j(v);
+          X[v] = Aq[c][a] * Mq[p][b] + Mq[p][a] * Aq[c][b];
+        }
+      }
+  }
+  for (int p = 0; p < NPH; ++p) {
+    T Up[3][3], Ut[3][3], B[3][3];
+    load_U(P, p, Up);
+    rot_in(Q, Up, Ut);
+    mm3(At, Ut, B);  // B = A~ U~_p ; dE~ = -(B Lambda + Lambda B^T)
+    for (int v = 0; v < 6; ++v) {
+      const int a = sym_i(v), b = sym_j(v);
+      Xs[9 + p][v] = -(B[a][b] * lam[b] + lam[a] * B[b][a]);
+    }
+  }
+  // d~_k = Dh~[X~_k] = 1/2 f1 o X~_k as Voigt strain vectors (engineering shear)
+  T dv[ND][6];
+  for (int k = 0; k < ND; ++k)
+    for (int v = 0; v < 6; ++v) {
+      const int a = sym_i(v), b = sym_j(v);
+      dv[k][v] = T(0.5) * f1[a][b] * Xs[k][v] * (v < 3 ? T(1) : T(2));
+    }
+  // L~ = Nv^T L(eta) Nv with v(Q d~ Q^T) = Nv v(d~)
+  T Lt[6][6];
+  {
+    T Nv[6][6];
+    for (int I = 0; I < 6; ++I) {
+      const int i = sym_i(I), j = sym_j(I);
+      const T cI = (I < 3) ? T(1) : T(2);
+      for (int B = 0; B < 6; ++B) {
+        const int a = sym_i(B), b = sym_j(B);
+        Nv[I][B] = (B < 3) ? cI * Q[i][a] * Q[j][a] : cI * T(0.5) * (Q[i][a] * Q[j][b] + Q[i][b] * Q[j][a]);
+      }
+    }
+    T LN[6][6];
+    for (int I = 0; I < 6; ++I)
+      for (int B = 0; B < 6; ++B) {
+        T s = 0;
+        for (int J = 0; J < 6; ++J) {
+          T lij = 0;
+          for (int p = 0; p < NPH; ++p) lij += eta[p] * T(P.Lv[p][I][J]);
+          s += lij * Nv[J][B];
+        }
+        LN[I][B] = s;
+      }
+    for (int A_ = 0; A_ < 6; ++A_)
+      for (int B = 0; B < 6; ++B) {
+        T s = 0;
+        for (int I = 0; I < 6; ++I) s += Nv[I][A_] * LN[I][B];
+        Lt[A_][B] = s;
+      }
+  }
+  // second divided differences f2[a][b][c] (symmetric)
+  T f2[3][3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = a; b < 3; ++b)
+      for (int c = b; c < 3; ++c) {
+        T v = dd2_log(lam[a], lam[b], lam[c]);
+        f2[a][b][c] = f2[a][c][b] = f2[b][a][c] = f2[b][c][a] = f2[c][a][b] = f2[c][b][a] = v;
+      }
+  // per-phase (L_i : h) rotated, for the eta-dependence of L
+  T LhT[NPH][6];
+  for (int p = 0; p < NPH; ++p) {
+    T lv[6], lm[3][3], lr[3][3];
+    for (int I = 0; I < 6; ++I) {
+      T s = 0;
+      for (int J = 0; J < 6; ++J) s += T(P.Lv[p][I][J]) * hv[J];
+      lv[I] = s;
+    }
+    from_voigt_stress(lv, lm);
+    rot_in(Q, lm, lr);
+    for (int v = 0; v < 6; ++v) LhT[p][v] = lr[sym_i(v)][sym_j(v)];
+  }
+  T H16[ND * (ND + 1) / 2];
+  // g_EE part J_t (d~_k . L~ d~_l + K(k,l)), K(k,l) = sum_bc Z_k[b][c] X~_l[b][c],
+  // Z_k[b][c] = sum_a f2_abc T~_ab X~_k[a][c]; and the first-order terms
+  // g_{E eta_p}[X_k] = tr(AU_p) S~:X~_k + J_t (L_p h)~ : d~_k, added to the
+  // F-eta and eta-eta entries (the latter for both index orders).
+  for (int k = 0; k < ND; ++k) {
+    T Ld[6], Z[3][3];
+    for (int I = 0; I < 6; ++I) {
+      T s = 0;
+      for (int J = 0; J < 6; ++J) s += Lt[I][J] * dv[k][J];
+      Ld[I] = s;
+    }
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c)
+        Z[b][c] = f2[0][b][c] * Tt[0][b] * symget(Xs[k], 0, c) + f2[1][b][c] * Tt[1][b] * symget(Xs[k], 1, c) +
+                  f2[2][b][c] * Tt[2][b] * symget(Xs[k], 2, c);
+    for (int l = k; l < ND; ++l) {
+      T dl = 0;
+      for (int I = 0; I < 6; ++I) dl += dv[l][I] * Ld[I];
+      T K = 0;
+      for (int b = 0; b < 3; ++b)
+        for (int c = 0; c < 3; ++c) K += Z[b][c] * symget(Xs[l], b, c);
+      H16[hp16(k, l)] = Jt * (dl + K);
+    }
+    // S~ : X~_k and (L_p h)~ : d~_k (tensor double contractions of symmetric matrices)
+    T SX = 0;
+    for (int v = 0; v < 6; ++v) SX += (v < 3 ? T(1) : T(2)) * St[sym_i(v)][sym_j(v)] * Xs[k][v];
+    for (int p = 0; p < NPH; ++p) {
+      T Ld2 = 0;
+      for (int v = 0; v < 6; ++v) Ld2 += LhT[p][v] * dv[k][v];  // dv carries the shear factor 2
+      const T ge = trAU[p] * SX + Jt * Ld2;
+      if (k < 9) {
+        H16[hp16(k, 9 + p)] += ge;
+      } else {
+        const int q = k - 9;
+        const int lo = p < q ? p : q, hi = p < q ? q : p;
+        H16[hp16(9 + lo, 9 + hi)] += (p == q) ? T(2) * ge : ge;
+      }
+    }
+  }
+  // S : d^2E, F-F block: delta_pr 2 (A S A)_QS
+  T ASA[3][3];
+  {
+    T t[3][3];
+    mm3(S, A, t);
+    mm3(A, t, ASA);
+  }
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q)
+      for (int s2 = q; s2 < 3; ++s2) H16[hp16(3 * p + q, 3 * p + s2)] += T(2) * ASA[q][s2];
+  // F-eta block: -2 (F N_p)_rQ with N_p = ASA U_p A + A U_p ASA
+  {
+    T FASA[3][3];
+    mm3(F, ASA, FASA);
+    for (int p = 0; p < NPH; ++p) {
+      T Up[3][3], t1[3][3], t2[3][3], t3[3][3];
+      load_U(P, p, Up);
+      mm3(FASA, Up, t1);
+      mm3(t1, A, t2);  // F ASA U_p A
+      mm3(M, Up, t1);
+      mm3(t1, ASA, t3);  // F A U_p ASA
+      for (int k = 0; k < 9; ++k) H16[hp16(k, 9 + p)] += T(-2) * (t2[k / 3][k % 3] + t3[k / 3][k % 3]);
+    }
+  }
+  // eta-eta block: S:d2E + explicit eta derivatives of g + local terms
+  {
+    T C[3][3], SE[3][3];
+    mtm3(F, F, C);
+    mm3(S, E, SE);
+    T Y[NPH][3][3], SEU[NPH][3][3], SY[NPH][3][3], CY[NPH][3][3];
+    for (int p = 0; p < NPH; ++p) {
+      T Up[3][3];
+      load_U(P, p, Up);
+      mm3(AU[p], A, Y[p]);  // Y_p = A U_p A
+      mm3(SE, Up, SEU[p]);  // S E U_p
+      mm3(S, Y[p], SY[p]);
+      mm3(C, Y[p], CY[p]);
+    }
+    for (int p = 0; p < NPH; ++p)
+      for (int q = p; q < NPH; ++q) {
+        T sd2E = T(2) * (tr_ab(SEU[p], Y[q]) + tr_ab(SEU[q], Y[p]) + tr_ab(SY[p], CY[q]));
+        T Jpq = Jt * (trAU[p] * trAU[q] - tr_ab(AU[p], AU[q]));
+        T gee = T(0.5) * Jpq * hT + T(0.5) * Jt * trAU[p] * hLh[q] + T(0.5) * Jt * trAU[q] * hLh[p];
+        T loc = T(P.cobst[p][q]);
+        if (p == q) loc += T(P.inv_mtau[p]) + (eta[p] < T(0) ? T(P.eps_eta) : T(0));
+        H16[hp16(9 + p, 9 + q)] += sd2E + gee + loc;
+      }
+  }
+  // condense eta_0 (Sec. 3.1): z = (F, eta_hat), eta = e_0 + T eta_hat
+  for (int r = 0; r < NZ; ++r)
+    for (int c = r; c < NZ; ++c) {
+      T v;
+      if (c < 9) {
+        v = H16[hp16(r, c)];
+      } else if (r < 9) {
+        v = H16[hp16(r, c + 1)] - H16[hp16(r, 9)];
+      } else {
+        v = H16[hp16(r + 1, c + 1)] - H16[hp16(9, r + 1)] - H16[hp16(9, c + 1)] + H16[hp16(9, 9)];
+      }
+      Hp[hidx(r, c)] = v;
+    }
+}
+
+}  // namespace pfm

@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the Newton-step solve of the finite-strain multivariant
+phase-field model on GB300.
+
+Workload (one step): one Newton iteration of the nano-indentation problem on
+a 128^3 trilinear-hexahedron cube (19,320,201 DOFs, 6 multigrid levels, load
+step 1 of 10): residual -> linearisation on every level -> FGMRES(30) with an
+FP32 geometric-multigrid V-cycle inside FP64 FGMRES to a relative residual of
+1e-8 -> update -> new residual. Inputs are seeded and synthetic and resident
+in HBM when the timed region starts; every step restarts from the same state.
+
+Headline value: Jacobian-apply throughput in GDOF/s, i.e. DOFs of the finest
+level per FP32 tangent application, divided by the mean device time of those
+applications inside the timed Newton steps (CUDA events recorded by the
+library on its stream). Also reported: seconds per Newton step for the mixed
+FP32-MG and the all-FP64 solve, the roofline of the tangent application,
+an end-to-end figure through the host-buffer entry point, and the CPU oracle
+timed on a bounded sample.
+
+Multi-GPU (torchrun): each rank solves its own independent problem (weak
+scaling, no collective on the data path); the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Jacobian-apply GDOF/s & Newton-step solve s, FP32-MG vs FP64 at 1e-8 resid"
+UNIT = "GDOF/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    p.add_argument("--n", type=int, default=128, help="hexes per cube edge")
+    p.add_argument("--no-fp64-step", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--sample", type=int, default=4, help="edge of the oracle's element sample")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def committed_traffic():
+    """dram bytes per FP32 tangent application from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_2011_08802_gb300", "csrc", "fe_kernels.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        text = open(path).read()
+        m1 = re.search(r"fe_kernels_sha256_16:\s*([0-9a-f]{16})", text)
+        m2 = re.search(r"japply_f32_dram_bytes_per_launch_128:\s*([0-9.eE+]+)", text)
+        if m1 and m2 and m1.group(1) == sha:
+            return float(m2.group(1))
+    return None
+
+
+# ---------------------------------------------------------------------------
+def oracle_jvp_sample(n_full: int, edge: int, seconds: float, steps: int | None = None):
+    """Time the CPU oracle's tangent application (element loop with the
+    oracle's own Gauss-point Hessians) on an edge^3 block of elements of the
+    benchmark state. Returns (GDOF/s, sample description, seconds per step)."""
+    import numpy as np
+
+    from oracle import fe, qp
+    from paper_2011_08802_gb300 import inputs
+
+    st = inputs.config_indentation(n_full, seed=5, step=1)
+    m = st.mesh
+    # the edge^3 block of elements at the centre of the top face (under the
+    # indenter), extracted with its nodes as a mesh of its own
+    i0 = j0 = n_full // 2 - edge // 2
+    k0 = n_full - edge
+    ii, jj, kk = np.meshgrid(np.arange(i0, i0 + edge + 1), np.arange(j0, j0 + edge + 1),
+                             np.arange(k0, k0 + edge + 1), indexing="ij")
+    nodes = (ii + (m.nx + 1) * (jj + (m.ny + 1) * kk)).transpose(2, 1, 0).reshape(-1)
+    hx, hy, hz = m.h
+    sub = inputs.Mesh(edge, edge, edge, edge * hx, edge * hy, edge * hz)
+    st = inputs.State(sub, st.U[:, nodes].copy(), st.Un[:, nodes].copy(), st.mask[:, nodes].copy(),
+                      st.tau, st.material)
+    disc = fe.Discretisation(sub)
+    mat = qp.material_from(st.material, st.tau)
+    d = fe.qp_derivatives(disc, st, mat, order=2)
+    v = np.random.default_rng(0).standard_normal(st.U.shape)
+    sample_dofs = 9 * (edge + 1) ** 3
+    fe.jvp(disc, st, v, d)  # warm
+    times = []
+    t_end = time.perf_counter() + seconds
+    n = 0
+    while True:
+        t0 = time.perf_counter()
+        fe.jvp(disc, st, v, d)
+        times.append(time.perf_counter() - t0)
+        n += 1
+        if steps is not None:
+            if n >= steps:
+                break
+        elif time.perf_counter() > t_end:
+            break
+    per = sum(times) / len(times)
+    desc = (f"oracle tangent application (numpy, element loop with stored oracle Gauss-point "
+            f"Hessians) on the {edge}^3-element block under the indenter of the {n_full}^3 "
+            f"state: {sample_dofs} DOFs, {len(times)} applications")
+    return sample_dofs / per / 1e9, desc, per
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    value, desc, per = oracle_jvp_sample(args.n, args.sample, 0.0, steps=args.warmup + args.steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"oracle tangent application, {args.sample}^3-element sample of the "
+                               f"{args.n}^3 indentation state"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def gpu_arm(args, rank, world, dist):
+    import numpy as np
+    import torch
+
+    from paper_2011_08802_gb300 import abi, binding, inputs
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    st = inputs.config_indentation(args.n, seed=5 + rank, step=1)
+    P = binding.problem_from_state(st)
+    ndofs = 9 * P.n_nodes
+    U0 = torch.from_numpy(st.U).to(dev)
+    Uw = torch.empty_like(U0)
+    opts = abi.default_opts(abi.PFM_F32, max_newton=1, restart=30, max_lin_it=400, lin_rtol=1e-8)
+
+    def step(o):
+        Uw.copy_(U0)
+        return P.newton_solve(Uw, o)
+
+    for _ in range(args.warmup):
+        step(opts)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K mixed-precision Newton steps --------------------
+    clocks = ClockSampler(local)
+    P.profile_enable(True)
+    launches0 = binding.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    reps = [step(opts) for _ in range(args.steps)]
+    ev1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    launches = binding.launch_count() - launches0
+    total_ms = ev0.elapsed_time(ev1)
+    n32, ms32 = P.profile_get(abi.PROF_JAPPLY_F32)
+    n64, ms64 = P.profile_get(abi.PROF_JAPPLY_F64)
+    nlin, mslin = P.profile_get(abi.PROF_LINEARIZE)
+    nres, msres = P.profile_get(abi.PROF_RESIDUAL)
+    nvc, msvc = P.profile_get(abi.PROF_VCYCLE)
+    P.profile_enable(False)
+    ms_step = total_ms / args.steps
+    japply_ms = ms32 / max(n32, 1)
+    stats = torch.tensor([ms_step, japply_ms, ms32, float(n32)], dtype=torch.float64, device=dev)
+    if dist is not None:
+        mx = stats.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        ms_step, japply_ms = float(mx[0]), float(mx[1])
+        sumd = torch.tensor([float(ndofs * n32)], dtype=torch.float64, device=dev)
+        dist.all_reduce(sumd)
+        value = float(sumd[0]) / (float(mx[2]) * 1e-3) / 1e9
+    else:
+        value = ndofs * n32 / (ms32 * 1e-3) / 1e9
+
+    # ---- roofline of the FP32 tangent application -----------------------
+    ne = P.n_elems
+    h_bytes = ((ne + 3) // 4) * 4 * 8 * 120 * 4
+    vec_bytes = 4 * ndofs
+    alg_bytes = h_bytes + 2 * vec_bytes + 2 * P.n_nodes
+    peak, peak_kind = measured_hbm()
+    achieved = alg_bytes / (japply_ms * 1e-3) / 1e9
+    traffic = committed_traffic() if args.n == 128 else None
+
+    # ---- accuracy of both precisions and the all-FP64 Newton step --------
+    def solve_check(prec):
+        Uw.copy_(U0)
+        P.set_state(Uw, torch.from_numpy(st.Un).to(dev))
+        R = P.residual()
+        P.linearize(prec)
+        x, rep = P.fgmres_solve(-R, abi.default_opts(prec, max_lin_it=400, lin_rtol=1e-8))
+        y = P.jacobian_apply(x)
+        true_res = float(torch.linalg.norm(y + R) / torch.linalg.norm(R))
+        return true_res, rep.lin_its_last
+
+    res32, its32 = solve_check(abi.PFM_F32)
+    fp64 = None
+    if not args.no_fp64_step:
+        o64 = abi.default_opts(abi.PFM_F64, max_newton=1, restart=30, max_lin_it=400, lin_rtol=1e-8)
+        step(o64)  # warm the FP64 hierarchy
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r64 = step(o64)
+        e1.record()
+        torch.cuda.synchronize()
+        res64, its64 = solve_check(abi.PFM_F64)
+        fp64 = {"s": e0.elapsed_time(e1) / 1e3, "fgmres_its": r64.lin_its_last, "true_rel_residual": res64}
+
+    # ---- end to end through the host-buffer entry point -----------------
+    P.set_state(U0, torch.from_numpy(st.Un).to(dev))
+    P.linearize(abi.PFM_F32)
+    v_host = torch.from_numpy(np.random.default_rng(1).standard_normal(P.shape).astype(np.float32)).pin_memory()
+    y_host = torch.empty_like(v_host).pin_memory()
+    for _ in range(2):
+        P.jacobian_apply_host(v_host, y_host)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        P.jacobian_apply_host(v_host, y_host)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_value = ndofs / e2e_s / 1e9
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_value = ndofs * world / float(t[0]) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cv, desc, _ = oracle_jvp_sample(args.n, args.sample, seconds=10.0)
+        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        rep = reps[-1]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 tangent application in f64 FGMRES/Newton",
+            "data": "synthetic (seeded indentation state, no dataset)",
+            "config": {
+                "workload": f"nano-indentation Newton step, {args.n}^3 Q1 hexes, {ndofs} DOFs per GPU, "
+                            f"{P.n_levels}-level geometric MG, load step 1/10, FGMRES(30) rtol 1e-8",
+                "problems": world, "l2": "inputs larger than L2 (8 GB Hessian store per application)",
+            },
+            "newton_step_s": {"fp32_mg": ms_step / 1e3, "fp64": fp64["s"] if fp64 else None},
+            "fgmres_its": {"fp32_mg": rep.lin_its_last, "fp64": fp64["fgmres_its"] if fp64 else None},
+            "true_rel_residual": {"fp32_mg": res32, "fp64": fp64["true_rel_residual"] if fp64 else None},
+            "phase_ms_per_step": {
+                "japply_f32": ms32 / args.steps, "japply_f64": ms64 / args.steps,
+                "linearize_fine": mslin / args.steps, "residual": msres / args.steps,
+                "vcycle": msvc / args.steps,
+            },
+            "japply_f32_ms": japply_ms, "japply_f32_launches": n32,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "bytes_per_launch": alg_bytes},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": vec_bytes,
+                    "d2h_bytes_per_step": vec_bytes},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    P.close()
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        backend = "nccl" if args.impl == "gpu" else "gloo"
+        if args.impl == "gpu":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group(backend=backend)
+        dist = tdist
+    if args.impl == "reference":
+        reference_arm(args, rank)
+    else:
+        gpu_arm(args, rank, world, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

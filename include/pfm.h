@@ -213,6 +213,30 @@ pfm_status pfm_qp_eval(pfm_handle* h, int64_t n, const double* F_dev, const doub
  * q = q0 + 2 q1 + 4 q2). Synchronises. */
 pfm_status pfm_get_hessians(pfm_handle* h, int64_t e0, int64_t count, double* hess_host);
 
+/* Device timing of the hot phases with CUDA events recorded on the handle's
+ * stream around each launch (off by default; enabling clears the counters).
+ * Timed phases: PFM_PROF_JAPPLY_F32 / _F64 = one tangent application on the
+ * finest level (the initialisation and element kernels), PFM_PROF_LINEARIZE
+ * = pfm_linearize's finest-level Hessian kernel, PFM_PROF_RESIDUAL = the
+ * residual kernel, PFM_PROF_VCYCLE = one whole V-cycle. */
+typedef enum {
+  PFM_PROF_JAPPLY_F32 = 0,
+  PFM_PROF_JAPPLY_F64 = 1,
+  PFM_PROF_LINEARIZE = 2,
+  PFM_PROF_RESIDUAL = 3,
+  PFM_PROF_VCYCLE = 4,
+  PFM_PROF_COUNT = 5
+} pfm_prof_id;
+
+pfm_status pfm_profile_enable(pfm_handle* h, int enable);
+
+/* Number of timed launches of phase id and their summed device time (ms)
+ * since profiling was enabled. Synchronises the stream. */
+pfm_status pfm_profile_get(pfm_handle* h, int id, int64_t* launches, double* total_ms);
+
+/* Kernel launches issued by the library in this process so far (all handles). */
+int64_t pfm_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(LIB_DIR, "libpfm.so")
 PFM_F32 = 0
 PFM_F64 = 1
 
+PROF_JAPPLY_F32, PROF_JAPPLY_F64, PROF_LINEARIZE, PROF_RESIDUAL, PROF_VCYCLE = range(5)
+
 STATUS = {
     0: "PFM_OK", 1: "PFM_ERR_INVALID_ARG", 2: "PFM_ERR_CUDA", 3: "PFM_ERR_OOM",
     4: "PFM_ERR_NONFINITE", 5: "PFM_ERR_NOT_CONVERGED", 6: "PFM_ERR_BREAKDOWN",
@@ -135,6 +137,9 @@ def lib():
         "pfm_newton_solve": (i32, [H, C.POINTER(SolveOpts), vp, C.POINTER(SolveReport)]),
         "pfm_qp_eval": (i32, [H, i64, vp, vp, vp, vp, vp, vp]),
         "pfm_get_hessians": (i32, [H, i64, i64, vp]),
+        "pfm_profile_enable": (i32, [H, i32]),
+        "pfm_profile_get": (i32, [H, i32, C.POINTER(i64), C.POINTER(dp)]),
+        "pfm_launch_count": (i64, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -151,7 +156,8 @@ def exported_symbols():
         "pfm_set_stream", "pfm_set_params", "pfm_set_dirichlet", "pfm_set_state", "pfm_get_state",
         "pfm_residual", "pfm_linearize", "pfm_jacobian_apply", "pfm_jacobian_transpose_apply",
         "pfm_jacobian_apply_host", "pfm_vcycle", "pfm_fgmres_solve", "pfm_newton_solve",
-        "pfm_qp_eval", "pfm_get_hessians",
+        "pfm_qp_eval", "pfm_get_hessians", "pfm_profile_enable", "pfm_profile_get",
+        "pfm_launch_count",
     ]
 
 

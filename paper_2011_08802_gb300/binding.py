@@ -162,10 +162,23 @@ class Problem:
         self._check(self._lib.pfm_qp_eval(self.h, n, _ptr(F), _ptr(eta), _ptr(eta_n), _ptr(W), _ptr(g), _ptr(H)))
         return W, g, H
 
+    def profile_enable(self, enable: bool = True):
+        self._check(self._lib.pfm_profile_enable(self.h, int(enable)))
+
+    def profile_get(self, phase: int):
+        n, ms = C.c_int64(), C.c_double()
+        self._check(self._lib.pfm_profile_get(self.h, phase, C.byref(n), C.byref(ms)))
+        return n.value, ms.value
+
     def get_hessians(self, e0: int, count: int) -> np.ndarray:
         out = np.empty((count, 8, 120))
         self._check(self._lib.pfm_get_hessians(self.h, e0, count, _ptr(out)))
         return out
+
+
+def launch_count() -> int:
+    """Kernel launches issued by the library in this process (``pfm_launch_count``)."""
+    return int(abi.lib().pfm_launch_count())
 
 
 def problem_from_state(state, n_levels: int = 0, params: abi.Params | None = None) -> Problem:

@@ -2,6 +2,7 @@
 // the solver drivers (V-cycle, FGMRES, Newton) that sequence the kernels of
 // fe_kernels.cu, mg_kernels.cu and krylov_kernels.cu on one CUDA stream.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -13,6 +14,12 @@
 #include "params.h"
 
 using namespace pfm;
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+}  // namespace
+
+void pfm::count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 namespace {
 
@@ -91,6 +98,11 @@ struct pfm_handle {
   // staging for the host-buffer entry point
   void* stage_in = nullptr;
   void* stage_out = nullptr;
+  // device timing of hot phases (pairs of events per timed launch)
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[PFM_PROF_COUNT];
+  int64_t prof_n[PFM_PROF_COUNT] = {0};
+  double prof_ms[PFM_PROF_COUNT] = {0};
 
   pfm_status fail(pfm_status s, const std::string& m) {
     err = m;
@@ -142,10 +154,53 @@ void dfree(T*& p) {
 
 int64_t ndof(const Level& l) { return int64_t(NF) * l.nn; }
 
+// Records a start event on construction and a stop event on destruction
+// (both on the handle's stream) when profiling is enabled.
+struct ProfScope {
+  pfm_handle* h;
+  int id;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(pfm_handle* h_, int id_, bool on = true) : h(h_), id(id_) {
+    if (!h->prof || !on) { h = nullptr; return; }
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, h->stream);
+  }
+  ~ProfScope() {
+    if (!h) return;
+    cudaEventRecord(b, h->stream);
+    h->prof_ev[id].emplace_back(a, b);
+  }
+};
+
+void prof_collect(pfm_handle* h) {
+  for (int id = 0; id < PFM_PROF_COUNT; ++id) {
+    for (auto& e : h->prof_ev[id]) {
+      float ms = 0.f;
+      cudaEventSynchronize(e.second);
+      cudaEventElapsedTime(&ms, e.first, e.second);
+      h->prof_ms[id] += ms;
+      h->prof_n[id] += 1;
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    h->prof_ev[id].clear();
+  }
+}
+
+// Tangent application on level l (timed when l == 0).
+template <typename T>
+void japply_level(pfm_handle* h, size_t l, const T* H, const T* x, T* y) {
+  Level& lv = h->L[l];
+  ProfScope ps(h, sizeof(T) == 4 ? PFM_PROF_JAPPLY_F32 : PFM_PROF_JAPPLY_F64, l == 0);
+  launch_japply<T>(lv.g, h->dp, H, lv.mask, x, y, h->stream);
+}
+
 // ---------------------------------------------------------------------------
 // V-cycle (Sec. 3.4): pre-smooth, restrict, recurse, coarse solve, prolong, post-smooth.
 template <typename T>
 pfm_status vcycle_level(pfm_handle* h, size_t l, int nu_pre, int nu_post, T omega) {
+  ProfScope ps(h, PFM_PROF_VCYCLE, l == 0);
   Level& lv = h->L[l];
   cudaStream_t s = h->stream;
   T* x = LvVec<T>::x(lv);
@@ -162,10 +217,10 @@ pfm_status vcycle_level(pfm_handle* h, size_t l, int nu_pre, int nu_post, T omeg
   CK(cudaMemsetAsync(x, 0, sizeof(T) * n, s));
   launch_smooth<T>(lv.nn, D, b, nullptr, omega, x, s);
   for (int k = 1; k < nu_pre; ++k) {
-    launch_japply<T>(lv.g, h->dp, H, lv.mask, x, y, s);
+    japply_level<T>(h, l, H, x, y);
     launch_smooth<T>(lv.nn, D, b, y, omega, x, s);
   }
-  launch_japply<T>(lv.g, h->dp, H, lv.mask, x, y, s);
+  japply_level<T>(h, l, H, x, y);
   launch_sub<T>(n, b, y, y, s);
   Level& cv = h->L[l + 1];
   launch_restrict<T>(lv.g, cv.g, y, cv.mask, LvVec<T>::b(cv), s);
@@ -173,7 +228,7 @@ pfm_status vcycle_level(pfm_handle* h, size_t l, int nu_pre, int nu_post, T omeg
   TRY(vcycle_level<T>(h, l + 1, nu_pre, nu_post, omega));
   launch_prolong_add<T>(lv.g, cv.g, LvVec<T>::x(cv), lv.mask, x, s);
   for (int k = 0; k < nu_post; ++k) {
-    launch_japply<T>(lv.g, h->dp, H, lv.mask, x, y, s);
+    japply_level<T>(h, l, H, x, y);
     launch_smooth<T>(lv.nn, D, b, y, omega, x, s);
   }
   CKL();
@@ -213,7 +268,10 @@ pfm_status residual_impl(pfm_handle* h, double* R, double* energy_host) {
   cudaStream_t s = h->stream;
   CK(cudaMemsetAsync(R, 0, sizeof(double) * ndof(f), s));
   CK(cudaMemsetAsync(h->energy_dev, 0, sizeof(double), s));
-  launch_residual(f.g, h->dp, f.U, f.Un, f.mask, R, h->energy_dev, s);
+  {
+    ProfScope ps(h, PFM_PROF_RESIDUAL);
+    launch_residual(f.g, h->dp, f.U, f.Un, f.mask, R, h->energy_dev, s);
+  }
   CKL();
   if (energy_host) {
     CK(cudaMemcpyAsync(energy_host, h->energy_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -250,7 +308,10 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
     const bool need32 = prec == PFM_F32 && !coarsest;
     if (need64) TRY(dalloc(h, &lv.H64, hsz));
     if (need32) TRY(dalloc(h, &lv.H32, hsz));
-    launch_linearize(lv.g, h->dp, lv.U, lv.Un, need64 ? lv.H64 : nullptr, need32 ? lv.H32 : nullptr, s);
+    {
+      ProfScope ps(h, PFM_PROF_LINEARIZE, fine);
+      launch_linearize(lv.g, h->dp, lv.U, lv.Un, need64 ? lv.H64 : nullptr, need32 ? lv.H32 : nullptr, s);
+    }
     CKL();
     if (coarsest) continue;
     if (prec == PFM_F32) {
@@ -283,7 +344,7 @@ pfm_status japply_impl(pfm_handle* h, const T* v, T* y) {
   const T* H = LvVec<T>::H(f);
   if (!H || (sizeof(T) == 4 && h->lin_prec != PFM_F32))
     return h->fail(PFM_ERR_STATE, "no tangent in the requested precision (linearize with PFM_F32 for FP32)");
-  launch_japply<T>(f.g, h->dp, H, f.mask, v, y, h->stream);
+  japply_level<T>(h, 0, H, v, y);
   CKL();
   return PFM_OK;
 }
@@ -520,6 +581,8 @@ pfm_status pfm_create(const pfm_mesh_desc* mesh, const pfm_params* params, pfm_h
 
 void pfm_destroy(pfm_handle* h) {
   if (!h) return;
+  for (int id = 0; id < PFM_PROF_COUNT; ++id)
+    for (auto& e : h->prof_ev[id]) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
   for (auto& lv : h->L) {
     dfree(lv.U); dfree(lv.Un); dfree(lv.mask); dfree(lv.H64); dfree(lv.H32); dfree(lv.D64); dfree(lv.D32);
     dfree(lv.x32); dfree(lv.b32); dfree(lv.y32); dfree(lv.x64); dfree(lv.b64); dfree(lv.y64);
@@ -764,5 +827,23 @@ pfm_status pfm_get_hessians(pfm_handle* h, int64_t e0, int64_t count, double* he
     }
   return PFM_OK;
 }
+
+pfm_status pfm_profile_enable(pfm_handle* h, int enable) {
+  if (!h) return PFM_ERR_INVALID_ARG;
+  prof_collect(h);
+  for (int id = 0; id < PFM_PROF_COUNT; ++id) { h->prof_n[id] = 0; h->prof_ms[id] = 0.0; }
+  h->prof = enable != 0;
+  return PFM_OK;
+}
+
+pfm_status pfm_profile_get(pfm_handle* h, int id, int64_t* launches, double* total_ms) {
+  if (!h || id < 0 || id >= PFM_PROF_COUNT) return PFM_ERR_INVALID_ARG;
+  prof_collect(h);
+  if (launches) *launches = h->prof_n[id];
+  if (total_ms) *total_ms = h->prof_ms[id];
+  return PFM_OK;
+}
+
+int64_t pfm_launch_count(void) { return g_launches.load(); }
 
 }  // extern "C"

@@ -45,6 +45,9 @@ using dmask_t = uint16_t;
 // ---- launchers (host functions; every launch goes on the given stream) ----
 namespace pfm {
 
+// Kernel launches issued by the library (incremented by every launcher).
+void count_launches(int n);
+
 // element kernels (fe_kernels.cu)
 void launch_residual(const Grid& g, const DevParams& P, const double* U, const double* Un,
                      const dmask_t* mask, double* R, double* energy, cudaStream_t s);

@@ -77,6 +77,18 @@ __device__ __forceinline__ T q1_scatter_grad(T gx, T gy, T gz, int l8, T ihx, T 
   return gb * Cc + ga * sC + ((l8 & 1) ? (Dx + sD) : -(Dx + sD)) * ihx;
 }
 
+// Row of packed upper-triangle index idx of a 15x15 matrix, and the packed
+// index where row r starts.
+__host__ __device__ constexpr int packed_row_start(int r) { return r * NZ - (r * (r - 1)) / 2; }
+__host__ __device__ constexpr int packed_row(int idx) {
+  int r = 0;
+  while (r + 1 < NZ && idx >= packed_row_start(r + 1)) ++r;
+  return r;
+}
+static_assert(packed_row(0) == 0 && packed_row(14) == 0 && packed_row(15) == 1 && packed_row(20) == 1 &&
+                  packed_row(119) == 14 && packed_row(117) == 13 && packed_row(116) == 12,
+              "packed index decode");
+
 __device__ __forceinline__ int64_t elem_node(const Grid& g, int64_t e, int a) {
   int64_t ei = e % g.nx;
   int64_t r = e / g.nx;
@@ -250,13 +262,9 @@ __global__ void __launch_bounds__(256) k_japply(Grid g, JParams<T> jp, const T* 
 #pragma unroll
     for (int t = 0; t < V; ++t) {
       const int idx = j * V + t;
-      // (r, c) of packed index idx (compile-time after unrolling)
-      int r = 0, base = 0;
-#pragma unroll
-      for (int rr = 0; rr < NZ; ++rr) {
-        if (idx >= base + (NZ - rr)) { base += NZ - rr; r = rr + 1; }
-      }
-      const int c = r + (idx - base);
+      // (r, c) of packed index idx (constant-folded after unrolling)
+      const int r = packed_row(idx);
+      const int c = r + (idx - packed_row_start(r));
       sg[r] += hv[t] * dz[c];
       if (c != r) sg[c] += hv[t] * dz[r];
     }
@@ -435,12 +443,14 @@ void launch_residual(const Grid& g, const DevParams& P, const double* U, const d
                      const dmask_t* mask, double* R, double* energy, cudaStream_t s) {
   const int64_t threads = g.nblk() * 32;
   k_residual<<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, mask, R, energy);
+  count_launches(1);
 }
 
 void launch_linearize(const Grid& g, const DevParams& P, const double* U, const double* Un,
                       double* H64, float* H32, cudaStream_t s) {
   const int64_t threads = g.nblk() * 32;
   k_linearize<<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, H64, H32);
+  count_launches(1);
 }
 
 template <typename T>
@@ -448,8 +458,10 @@ void launch_japply(const Grid& g, const DevParams& P, const T* H, const dmask_t*
                    T* y, cudaStream_t s) {
   const int64_t nn = g.nn();
   k_japply_init<T><<<grid_for(NF * nn, 256) < 4096 ? grid_for(NF * nn, 256) : 4096, 256, 0, s>>>(nn, mask, v, y);
+  count_launches(1);
   const int64_t threads = g.nblk() * 32;
   k_japply<T><<<grid_for(threads, 256), 256, 0, s>>>(g, make_jparams<T>(g, P), H, mask, v, y);
+  count_launches(1);
 }
 
 template <typename T>
@@ -459,16 +471,19 @@ void launch_blockdiag(const Grid& g, const DevParams& P, const T* H, const dmask
   cudaMemsetAsync(D, 0, sizeof(T) * 81 * g.nn(), s);
   const int64_t threads = g.ne() * 8;
   k_blockdiag<T><<<grid_for(threads, 128), 128, 0, s>>>(g, make_jparams<T>(g, P), H, D);
+  count_launches(1);
 }
 
 template <typename T>
 void launch_block_invert(int64_t nn, const dmask_t* mask, T* D, int* singular, cudaStream_t s) {
   k_block_invert<T><<<grid_for(nn, 128), 128, 0, s>>>(nn, mask, D, singular);
+  count_launches(1);
 }
 
 void launch_qp_eval(const DevParams& P, int64_t n, const double* F, const double* eta,
                     const double* eta_n, double* W, double* grad, double* hess, cudaStream_t s) {
   k_qp_eval<<<grid_for(n, 64), 64, 0, s>>>(P, n, F, eta, eta_n, W, grad, hess);
+  count_launches(1);
 }
 
 template void launch_japply<float>(const Grid&, const DevParams&, const float*, const dmask_t*,

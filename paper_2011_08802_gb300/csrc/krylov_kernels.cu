@@ -146,12 +146,15 @@ int reduction_blocks(int64_t n) {
 template <typename T>
 void launch_fill(int64_t n, T val, T* x, cudaStream_t s) {
   k_fill<T><<<grid_for(n, 256), 256, 0, s>>>(n, val, x);
+  count_launches(1);
 }
 void launch_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t s) {
   k_cast_d2f<<<grid_for(n, 256), 256, 0, s>>>(n, a, b);
+  count_launches(1);
 }
 void launch_cast_f2d(int64_t n, const float* a, double* b, cudaStream_t s) {
   k_cast_f2d<<<grid_for(n, 256), 256, 0, s>>>(n, a, b);
+  count_launches(1);
 }
 
 // out[0..k) = V_j . w (V_j at V + j*ldv). partial: >= reduction_blocks(n)*k doubles.
@@ -161,34 +164,42 @@ void launch_mdot(int64_t n, int k, const double* V, int64_t ldv, const double* w
   for (int j0 = 0; j0 < k; j0 += MDOT_CHUNK) {
     const int cnt = (k - j0) < MDOT_CHUNK ? (k - j0) : MDOT_CHUNK;
     k_mdot_partial<<<nb, RED_THREADS, 0, s>>>(n, j0, cnt, V, ldv, w, partial, k);
+    count_launches(1);
   }
   k_mdot_final<<<k, RED_THREADS, 0, s>>>(nb, k, partial, k, out);
+  count_launches(1);
 }
 
 void launch_maxpy(int64_t n, int k, const double* V, int64_t ldv, const double* h, double* w,
                   cudaStream_t s) {
   k_maxpy<<<grid_for(n, 256), 256, 0, s>>>(n, k, V, ldv, h, w);
+  count_launches(1);
 }
 
 void launch_scale_copy(int64_t n, const double* a, const double* alpha_dev, double* b, cudaStream_t s) {
   k_scale_copy<<<grid_for(n, 256), 256, 0, s>>>(n, a, alpha_dev, b);
+  count_launches(1);
 }
 
 template <typename T>
 void launch_gemv_add(int64_t n, int k, const T* Z, int64_t ldz, const double* y, double* x, cudaStream_t s) {
   k_gemv_add<T><<<grid_for(n, 256), 256, 0, s>>>(n, k, Z, ldz, y, x);
+  count_launches(1);
 }
 
 void launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s) {
   k_axpy<<<grid_for(n, 256), 256, 0, s>>>(n, a, x, y);
+  count_launches(1);
 }
 
 void launch_mask_values(int64_t nn, const dmask_t* mask, const double* val, double* U, cudaStream_t s) {
   k_mask_values<<<grid_for(NF * nn, 256), 256, 0, s>>>(nn, mask, val, U);
+  count_launches(1);
 }
 
 void launch_build_mask(int64_t nn, const uint8_t* m8, dmask_t* mask, int* bad, cudaStream_t s) {
   k_build_mask<<<grid_for(nn, 256), 256, 0, s>>>(nn, m8, mask, bad);
+  count_launches(1);
 }
 
 template void launch_fill<float>(int64_t, float, float*, cudaStream_t);

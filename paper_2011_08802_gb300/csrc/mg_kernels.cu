@@ -330,33 +330,39 @@ __global__ void k_coarse_solve(int n, const double* __restrict__ Aug, const T* _
 void launch_inject_state(const Grid& fine, const Grid& coarse, const double* Uf, double* Uc,
                          cudaStream_t s) {
   k_inject_state<<<grid_for(coarse.nn(), 128), 128, 0, s>>>(fine, coarse, Uf, Uc);
+  count_launches(1);
 }
 
 void launch_coarse_mask(const Grid& fine, const Grid& coarse, const dmask_t* mf, dmask_t* mc,
                         cudaStream_t s) {
   k_coarse_mask<<<grid_for(coarse.nn(), 128), 128, 0, s>>>(fine, coarse, mf, mc);
+  count_launches(1);
 }
 
 template <typename T>
 void launch_prolong_add(const Grid& fine, const Grid& coarse, const T* xc, const dmask_t* mf, T* xf,
                         cudaStream_t s) {
   k_prolong_add<T><<<grid_for(fine.nn(), 256), 256, 0, s>>>(fine, coarse, xc, mf, xf);
+  count_launches(1);
 }
 
 template <typename T>
 void launch_restrict(const Grid& fine, const Grid& coarse, const T* rf, const dmask_t* mc, T* rc,
                      cudaStream_t s) {
   k_restrict<T><<<grid_for(coarse.nn(), 128), 128, 0, s>>>(fine, coarse, rf, mc, rc);
+  count_launches(1);
 }
 
 template <typename T>
 void launch_smooth(int64_t nn, const T* D, const T* b, const T* y, T omega, T* x, cudaStream_t s) {
   k_smooth<T><<<grid_for(nn, 256), 256, 0, s>>>(nn, D, b, y, omega, x);
+  count_launches(1);
 }
 
 template <typename T>
 void launch_sub(int64_t n, const T* b, const T* y, T* r, cudaStream_t s) {
   k_sub<T><<<grid_for(n, 256), 256, 0, s>>>(n, b, y, r);
+  count_launches(1);
 }
 
 template <typename T>
@@ -365,7 +371,9 @@ void launch_coarse_assemble(const Grid& g, const DevParams& P, const T* H, const
   const int n = int(NF * g.nn());
   cudaMemsetAsync(K, 0, sizeof(double) * size_t(n) * ld, s);
   k_coarse_assemble<T><<<grid_for(g.ne() * 72, 128), 128, 0, s>>>(g, P, H, K, ld);
+  count_launches(1);
   k_coarse_bc<<<grid_for(int64_t(n) * n, 256), 256, 0, s>>>(n, g.nn(), mask, K, ld);
+  count_launches(1);
 }
 
 // Reduce the augmented [K | I] (n x 2n, ld = 2n) to [I | K^-1]; returns the
@@ -375,10 +383,12 @@ int dense_gauss_jordan_inverse(double* Maug, int n, double* f, int* singular, cu
   int launches = 0;
   for (int k = 0; k < n; ++k) {
     k_gj_pivot<<<1, 1024, 0, s>>>(Maug, n, ld, k, f, singular);
+    count_launches(1);
     const int64_t total = int64_t(n) * (2 * n - k);
     unsigned blocks = grid_for(total, 256);
     if (blocks > 1216) blocks = 1216;
     k_gj_update<<<blocks, 256, 0, s>>>(Maug, n, ld, k, f, singular);
+    count_launches(1);
     launches += 2;
   }
   return launches;
@@ -387,6 +397,7 @@ int dense_gauss_jordan_inverse(double* Maug, int n, double* f, int* singular, cu
 template <typename T>
 void launch_coarse_solve(int n, const double* Ainv, const T* b, T* x, cudaStream_t s) {
   k_coarse_solve<T><<<grid_for(int64_t(n) * 32, 256), 256, 0, s>>>(n, Ainv, b, x);
+  count_launches(1);
 }
 
 #define PFM_INST(T)                                                                              \

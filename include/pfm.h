@@ -88,9 +88,13 @@ typedef struct {
   int nu_pre, nu_post;   /* smoothing sweeps before / after the coarse correction */
   double newton_rtol;    /* stop when ||R|| <= newton_rtol * ||R_0|| */
   double lin_rtol;       /* FGMRES: ||b - J x|| <= lin_rtol * ||b|| */
-  double omega;          /* damping of the point-block Jacobi smoother */
+  double omega;          /* damping of the point-block Jacobi smoother (smoother 1) */
   pfm_precision precond; /* PFM_F32: V-cycle in FP32 inside FP64 FGMRES (mixed);
                             PFM_F64: every step in FP64 */
+  int smoother;          /* 0: Chebyshev-accelerated point-block Jacobi on the interval
+                            [cheb_lo, cheb_hi] * lambda_max(D^-1 J) (lambda_max estimated by
+                            power iteration at pfm_linearize); 1: damped point-block Jacobi */
+  double cheb_lo, cheb_hi;  /* Chebyshev interval as fractions of lambda_max (0.1, 1.1) */
 } pfm_solve_opts;
 
 typedef struct {
@@ -174,12 +178,13 @@ pfm_status pfm_jacobian_transpose_apply(pfm_handle* h, const void* v_dev, void* 
 pfm_status pfm_jacobian_apply_host(pfm_handle* h, const void* v_host, void* y_host,
                                    pfm_precision prec);
 
-/* One multigrid V-cycle z = M r (Sec. 3.4): nu_pre damped point-block Jacobi
- * sweeps, restriction of the residual, recursion, dense coarse solve,
- * prolongation of the correction, nu_post sweeps. r_dev, z_dev: device
- * [9][n_nodes] in the precision prec (the precision of the preconditioner
- * built by pfm_linearize). Uses opts->nu_pre, nu_post, omega (NULL = defaults
- * 2, 2, 0.7). */
+/* One multigrid V-cycle z = M r (Sec. 3.4): nu_pre point-block Jacobi
+ * smoothing steps (Chebyshev-accelerated by default), restriction of the
+ * residual, recursion, dense coarse solve, prolongation of the correction,
+ * nu_post smoothing steps. r_dev, z_dev: device [9][n_nodes] in the precision
+ * prec (the precision of the preconditioner built by pfm_linearize). Uses
+ * opts->nu_pre, nu_post, smoother, cheb_lo, cheb_hi, omega (NULL = defaults
+ * 2, 2, Chebyshev, 0.1, 1.1). */
 pfm_status pfm_vcycle(pfm_handle* h, const void* r_dev, void* z_dev, pfm_precision prec,
                       const pfm_solve_opts* opts);
 

@@ -33,8 +33,9 @@ struct Level {
   float* H32 = nullptr;
   double* D64 = nullptr;
   float* D32 = nullptr;
-  float *x32 = nullptr, *b32 = nullptr, *y32 = nullptr;
-  double *x64 = nullptr, *b64 = nullptr, *y64 = nullptr;
+  float *x32 = nullptr, *b32 = nullptr, *y32 = nullptr, *r32 = nullptr, *d32 = nullptr;
+  double *x64 = nullptr, *b64 = nullptr, *y64 = nullptr, *r64 = nullptr, *d64 = nullptr;
+  double lam = 0.0;  // estimate of lambda_max(D^-1 J) for the Chebyshev smoother
 };
 
 template <typename T> struct LvVec;
@@ -42,6 +43,8 @@ template <> struct LvVec<float> {
   static float*& x(Level& l) { return l.x32; }
   static float*& b(Level& l) { return l.b32; }
   static float*& y(Level& l) { return l.y32; }
+  static float*& r(Level& l) { return l.r32; }
+  static float*& d(Level& l) { return l.d32; }
   static float*& D(Level& l) { return l.D32; }
   static float*& H(Level& l) { return l.H32; }
 };
@@ -49,6 +52,8 @@ template <> struct LvVec<double> {
   static double*& x(Level& l) { return l.x64; }
   static double*& b(Level& l) { return l.b64; }
   static double*& y(Level& l) { return l.y64; }
+  static double*& r(Level& l) { return l.r64; }
+  static double*& d(Level& l) { return l.d64; }
   static double*& D(Level& l) { return l.D64; }
   static double*& H(Level& l) { return l.H64; }
 };
@@ -197,41 +202,108 @@ void japply_level(pfm_handle* h, size_t l, const T* H, const T* x, T* y) {
 }
 
 // ---------------------------------------------------------------------------
-// V-cycle (Sec. 3.4): pre-smooth, restrict, recurse, coarse solve, prolong, post-smooth.
+// Level smoothing. Chebyshev (type 0): the Chebyshev iteration for D^-1 J on
+// [lo, hi] = [cheb_lo, cheb_hi] * lambda_max(D^-1 J) (Saad, Iterative Methods
+// for Sparse Linear Systems, Alg. 12.1), i.e. point-block Jacobi relaxation
+// (Sec. 3.4) with Chebyshev step lengths. Damped Jacobi (type 1):
+// x += omega D^-1 (b - J x). Both cost one tangent application per step.
+struct SmoothCfg {
+  int nu_pre = 2, nu_post = 2, type = 0;
+  double omega = 0.7, lo = 0.1, hi = 1.1;
+};
+
+SmoothCfg smooth_cfg(const pfm_solve_opts* o) {
+  SmoothCfg c;
+  if (o) {
+    c.nu_pre = o->nu_pre;
+    c.nu_post = o->nu_post;
+    c.type = o->smoother;
+    c.omega = o->omega;
+    c.lo = o->cheb_lo;
+    c.hi = o->cheb_hi;
+  }
+  return c;
+}
+
+// nu steps on level l from x = 0 (zero_x) or from the current x; with
+// want_res the final residual b - J x is left in the level's r vector.
 template <typename T>
-pfm_status vcycle_level(pfm_handle* h, size_t l, int nu_pre, int nu_post, T omega) {
-  ProfScope ps(h, PFM_PROF_VCYCLE, l == 0);
+pfm_status smooth(pfm_handle* h, size_t l, bool zero_x, int nu, bool want_res, const SmoothCfg& c) {
   Level& lv = h->L[l];
   cudaStream_t s = h->stream;
   T* x = LvVec<T>::x(lv);
   T* b = LvVec<T>::b(lv);
   T* y = LvVec<T>::y(lv);
+  T* r = LvVec<T>::r(lv);
+  T* d = LvVec<T>::d(lv);
+  const T* H = LvVec<T>::H(lv);
+  const T* D = LvVec<T>::D(lv);
+  const int64_t n = ndof(lv);
+  if (c.type == 1) {
+    if (zero_x) {
+      CK(cudaMemsetAsync(x, 0, sizeof(T) * n, s));
+      launch_smooth<T>(lv.nn, D, b, nullptr, T(c.omega), x, s);
+    } else {
+      japply_level<T>(h, l, H, x, y);
+      launch_smooth<T>(lv.nn, D, b, y, T(c.omega), x, s);
+    }
+    for (int k = 1; k < nu; ++k) {
+      japply_level<T>(h, l, H, x, y);
+      launch_smooth<T>(lv.nn, D, b, y, T(c.omega), x, s);
+    }
+    if (want_res) {
+      japply_level<T>(h, l, H, x, y);
+      launch_sub<T>(n, b, y, r, s);
+    }
+    CKL();
+    return PFM_OK;
+  }
+  const double hi = c.hi * lv.lam, lo = c.lo * lv.lam;
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  if (zero_x) {
+    launch_cheb_first<T>(lv.nn, D, b, T(1.0 / theta), true, true, r, d, x, s);
+  } else {
+    japply_level<T>(h, l, H, x, y);
+    launch_sub<T>(n, b, y, r, s);
+    launch_cheb_first<T>(lv.nn, D, r, T(1.0 / theta), false, false, r, d, x, s);
+  }
+  for (int k = 1; k < nu; ++k) {
+    japply_level<T>(h, l, H, d, y);
+    const double rho_n = 1.0 / (2.0 * sigma - rho);
+    launch_cheb_step<T>(lv.nn, D, y, T(rho_n * rho), T(2.0 * rho_n / delta), r, d, x, s);
+    rho = rho_n;
+  }
+  if (want_res) {
+    japply_level<T>(h, l, H, d, y);
+    launch_sub<T>(n, r, y, r, s);
+  }
+  CKL();
+  return PFM_OK;
+}
+
+// V-cycle (Sec. 3.4): pre-smooth, restrict the residual, recurse, coarse
+// solve, prolong the correction, post-smooth.
+template <typename T>
+pfm_status vcycle_level(pfm_handle* h, size_t l, const SmoothCfg& c) {
+  ProfScope ps(h, PFM_PROF_VCYCLE, l == 0);
+  Level& lv = h->L[l];
+  cudaStream_t s = h->stream;
+  T* x = LvVec<T>::x(lv);
+  T* b = LvVec<T>::b(lv);
   if (l + 1 == h->L.size()) {
     launch_coarse_solve<T>(h->nc_dofs, h->Kaug, b, x, s);
     CKL();
     return PFM_OK;
   }
-  const T* H = LvVec<T>::H(lv);
-  const T* D = LvVec<T>::D(lv);
-  const int64_t n = ndof(lv);
-  CK(cudaMemsetAsync(x, 0, sizeof(T) * n, s));
-  launch_smooth<T>(lv.nn, D, b, nullptr, omega, x, s);
-  for (int k = 1; k < nu_pre; ++k) {
-    japply_level<T>(h, l, H, x, y);
-    launch_smooth<T>(lv.nn, D, b, y, omega, x, s);
-  }
-  japply_level<T>(h, l, H, x, y);
-  launch_sub<T>(n, b, y, y, s);
+  TRY(smooth<T>(h, l, true, c.nu_pre, true, c));
   Level& cv = h->L[l + 1];
-  launch_restrict<T>(lv.g, cv.g, y, cv.mask, LvVec<T>::b(cv), s);
+  launch_restrict<T>(lv.g, cv.g, LvVec<T>::r(lv), cv.mask, LvVec<T>::b(cv), s);
   CKL();
-  TRY(vcycle_level<T>(h, l + 1, nu_pre, nu_post, omega));
+  TRY(vcycle_level<T>(h, l + 1, c));
   launch_prolong_add<T>(lv.g, cv.g, LvVec<T>::x(cv), lv.mask, x, s);
-  for (int k = 0; k < nu_post; ++k) {
-    japply_level<T>(h, l, H, x, y);
-    launch_smooth<T>(lv.nn, D, b, y, omega, x, s);
-  }
   CKL();
+  if (c.nu_post > 0) TRY(smooth<T>(h, l, false, c.nu_post, false, c));
   return PFM_OK;
 }
 
@@ -241,17 +313,50 @@ pfm_status ensure_level_vectors(pfm_handle* h) {
     TRY(dalloc(h, &LvVec<T>::x(lv), ndof(lv)));
     TRY(dalloc(h, &LvVec<T>::b(lv), ndof(lv)));
     TRY(dalloc(h, &LvVec<T>::y(lv), ndof(lv)));
+    TRY(dalloc(h, &LvVec<T>::r(lv), ndof(lv)));
+    TRY(dalloc(h, &LvVec<T>::d(lv), ndof(lv)));
   }
+  return PFM_OK;
+}
+
+// lambda_max(D^-1 J) on level l by 15 steps of the power iteration from a
+// fixed pseudo-random start (normalised on the device; one read at the end).
+template <typename T>
+pfm_status estimate_lambda(pfm_handle* h, size_t l) {
+  Level& lv = h->L[l];
+  cudaStream_t s = h->stream;
+  const int64_t n = ndof(lv);
+  T* x = LvVec<T>::x(lv);
+  T* y = LvVec<T>::y(lv);
+  T* z = LvVec<T>::r(lv);
+  const T* H = LvVec<T>::H(lv);
+  const T* D = LvVec<T>::D(lv);
+  launch_power_init<T>(lv.nn, lv.mask, x, s);
+  launch_dot<T>(n, x, x, h->partial, h->hdev, s);
+  launch_scale_inv_sqrt<T>(n, x, h->hdev, x, s);
+  for (int it = 0; it < 15; ++it) {
+    launch_japply<T>(lv.g, h->dp, H, lv.mask, x, y, s);
+    CK(cudaMemsetAsync(z, 0, sizeof(T) * n, s));
+    launch_smooth<T>(lv.nn, D, y, nullptr, T(1), z, s);
+    launch_dot<T>(n, z, z, h->partial, h->hdev, s);
+    launch_scale_inv_sqrt<T>(n, z, h->hdev, x, s);
+  }
+  CKL();
+  double dot = 0.0;
+  CK(cudaMemcpyAsync(&dot, h->hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (!(dot > 0.0) || !std::isfinite(dot)) return h->fail(PFM_ERR_BREAKDOWN, "smoother eigenvalue estimate failed");
+  lv.lam = std::sqrt(dot);
   return PFM_OK;
 }
 
 // z = M r with r, z in the preconditioner's precision (device arrays of the finest level).
 template <typename T>
-pfm_status apply_vcycle(pfm_handle* h, const T* r, T* z, int nu_pre, int nu_post, double omega) {
+pfm_status apply_vcycle(pfm_handle* h, const T* r, T* z, const SmoothCfg& c) {
   TRY(ensure_level_vectors<T>(h));
   Level& f = h->L[0];
   CK(cudaMemcpyAsync(LvVec<T>::b(f), r, sizeof(T) * ndof(f), cudaMemcpyDeviceToDevice, h->stream));
-  TRY(vcycle_level<T>(h, 0, nu_pre, nu_post, T(omega)));
+  TRY(vcycle_level<T>(h, 0, c));
   CK(cudaMemcpyAsync(z, LvVec<T>::x(f), sizeof(T) * ndof(f), cudaMemcpyDeviceToDevice, h->stream));
   return PFM_OK;
 }
@@ -318,12 +423,17 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
       TRY(dalloc(h, &lv.D32, size_t(81) * lv.nn));
       launch_blockdiag<float>(lv.g, h->dp, lv.H32, lv.mask, lv.D32, s);
       launch_block_invert<float>(lv.nn, lv.mask, lv.D32, h->flag_dev, s);
+      CKL();
+      TRY(ensure_level_vectors<float>(h));
+      TRY(estimate_lambda<float>(h, l));
     } else {
       TRY(dalloc(h, &lv.D64, size_t(81) * lv.nn));
       launch_blockdiag<double>(lv.g, h->dp, lv.H64, lv.mask, lv.D64, s);
       launch_block_invert<double>(lv.nn, lv.mask, lv.D64, h->flag_dev, s);
+      CKL();
+      TRY(ensure_level_vectors<double>(h));
+      TRY(estimate_lambda<double>(h, l));
     }
-    CKL();
   }
   Level& c = h->L[nl - 1];
   launch_coarse_assemble<double>(c.g, h->dp, c.H64, c.mask, h->Kaug, 2 * h->nc_dofs, s);
@@ -359,6 +469,7 @@ pfm_status fgmres_impl(pfm_handle* h, const pfm_solve_opts& o, const double* b, 
   const int64_t n = ndof(f);
   const int m = o.restart;
   const bool mixed = (o.precond == PFM_F32);
+  const SmoothCfg sc = smooth_cfg(&o);
   if (mixed && h->lin_prec != PFM_F32)
     return h->fail(PFM_ERR_STATE, "FP32 preconditioner requested but the tangent was built for FP64");
   if (h->kry_m < m || h->kry_prec != o.precond) {
@@ -412,14 +523,14 @@ pfm_status fgmres_impl(pfm_handle* h, const pfm_solve_opts& o, const double* b, 
         float* zj = static_cast<float*>(h->Z) + size_t(j) * n;
         Level& fl = h->L[0];
         launch_cast_d2f(n, vj, fl.b32, s);
-        TRY(vcycle_level<float>(h, 0, o.nu_pre, o.nu_post, float(o.omega)));
+        TRY(vcycle_level<float>(h, 0, sc));
         CK(cudaMemcpyAsync(zj, fl.x32, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
         launch_cast_f2d(n, zj, h->zd, s);
       } else {
         double* zj = static_cast<double*>(h->Z) + size_t(j) * n;
         Level& fl = h->L[0];
         CK(cudaMemcpyAsync(fl.b64, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        TRY(vcycle_level<double>(h, 0, o.nu_pre, o.nu_post, o.omega));
+        TRY(vcycle_level<double>(h, 0, sc));
         CK(cudaMemcpyAsync(zj, fl.x64, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(h->zd, zj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
       }
@@ -497,7 +608,8 @@ pfm_status fgmres_impl(pfm_handle* h, const pfm_solve_opts& o, const double* b, 
 bool opts_valid(const pfm_solve_opts& o) {
   return o.restart >= 1 && o.restart <= MAX_RESTART && o.max_lin_it >= 1 && o.nu_pre >= 1 &&
          o.nu_post >= 0 && o.max_newton >= 1 && o.lin_rtol > 0 && o.omega > 0 &&
-         (o.precond == PFM_F32 || o.precond == PFM_F64);
+         (o.precond == PFM_F32 || o.precond == PFM_F64) && (o.smoother == 0 || o.smoother == 1) &&
+         o.cheb_lo > 0 && o.cheb_hi > o.cheb_lo;
 }
 
 }  // namespace
@@ -586,6 +698,7 @@ void pfm_destroy(pfm_handle* h) {
   for (auto& lv : h->L) {
     dfree(lv.U); dfree(lv.Un); dfree(lv.mask); dfree(lv.H64); dfree(lv.H32); dfree(lv.D64); dfree(lv.D32);
     dfree(lv.x32); dfree(lv.b32); dfree(lv.y32); dfree(lv.x64); dfree(lv.b64); dfree(lv.y64);
+    dfree(lv.r32); dfree(lv.d32); dfree(lv.r64); dfree(lv.d64);
   }
   dfree(h->dirval); dfree(h->energy_dev); dfree(h->flag_dev); dfree(h->R); dfree(h->dU); dfree(h->wv);
   dfree(h->rv); dfree(h->zd); dfree(h->partial); dfree(h->hdev); dfree(h->V); dfree(h->Kaug); dfree(h->gjf);
@@ -713,13 +826,12 @@ pfm_status pfm_jacobian_apply_host(pfm_handle* h, const void* v_host, void* y_ho
 pfm_status pfm_vcycle(pfm_handle* h, const void* r_dev, void* z_dev, pfm_precision prec, const pfm_solve_opts* opts) {
   TRY(check_ready(h, true));
   if (!r_dev || !z_dev) return h->fail(PFM_ERR_INVALID_ARG, "null vectors");
-  int nu_pre = 2, nu_post = 2;
-  double omega = 0.7;
-  if (opts) { nu_pre = opts->nu_pre; nu_post = opts->nu_post; omega = opts->omega; }
-  if (nu_pre < 1 || nu_post < 0) return h->fail(PFM_ERR_INVALID_ARG, "nu_pre >= 1 and nu_post >= 0 required");
+  const SmoothCfg c = smooth_cfg(opts);
+  if (c.nu_pre < 1 || c.nu_post < 0 || (c.type != 0 && c.type != 1) || !(c.hi > c.lo) || !(c.lo > 0))
+    return h->fail(PFM_ERR_INVALID_ARG, "bad smoother options");
   if (prec != h->lin_prec) return h->fail(PFM_ERR_STATE, "V-cycle precision differs from the linearisation");
-  if (prec == PFM_F32) return apply_vcycle<float>(h, static_cast<const float*>(r_dev), static_cast<float*>(z_dev), nu_pre, nu_post, omega);
-  return apply_vcycle<double>(h, static_cast<const double*>(r_dev), static_cast<double*>(z_dev), nu_pre, nu_post, omega);
+  if (prec == PFM_F32) return apply_vcycle<float>(h, static_cast<const float*>(r_dev), static_cast<float*>(z_dev), c);
+  return apply_vcycle<double>(h, static_cast<const double*>(r_dev), static_cast<double*>(z_dev), c);
 }
 
 pfm_status pfm_fgmres_solve(pfm_handle* h, const pfm_solve_opts* opts, const double* b_dev, double* x_dev,

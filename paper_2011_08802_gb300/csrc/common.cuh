@@ -82,6 +82,15 @@ void launch_sub(int64_t n, const T* b, const T* y, T* r, cudaStream_t s);
 template <typename T>
 void launch_coarse_assemble(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask,
                             double* K, int ld, cudaStream_t s);
+template <typename T>
+void launch_cheb_first(int64_t nn, const T* D, const T* src, T c, bool copy_r, bool zero_x, T* r, T* d, T* x,
+                       cudaStream_t s);
+template <typename T>
+void launch_cheb_step(int64_t nn, const T* D, const T* y, T a, T c, T* r, T* d, T* x, cudaStream_t s);
+template <typename T>
+void launch_power_init(int64_t nn, const dmask_t* mask, T* x, cudaStream_t s);
+template <typename T>
+void launch_scale_inv_sqrt(int64_t n, const T* y, const double* dot, T* x, cudaStream_t s);
 int dense_gauss_jordan_inverse(double* Maug, int n, double* f, int* singular, cudaStream_t s);
 template <typename T>
 void launch_coarse_solve(int n, const double* Ainv, const T* b, T* x, cudaStream_t s);
@@ -93,6 +102,8 @@ void launch_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t s);
 void launch_cast_f2d(int64_t n, const float* a, double* b, cudaStream_t s);
 void launch_mdot(int64_t n, int k, const double* V, int64_t ldv, const double* w, double* partial,
                  double* out, cudaStream_t s);
+template <typename T>
+void launch_dot(int64_t n, const T* a, const T* b, double* partial, double* out, cudaStream_t s);
 void launch_maxpy(int64_t n, int k, const double* V, int64_t ldv, const double* h, double* w,
                   cudaStream_t s);
 void launch_scale_copy(int64_t n, const double* a, const double* alpha_dev, double* b,

@@ -83,6 +83,26 @@ __global__ void k_mdot_final(int nblocks, int k, const double* __restrict__ part
   if (threadIdx.x == 0) out[j] = red[0];
 }
 
+// partial[blk] = sum over this block's slice of a . b (accumulated in FP64)
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_dot_partial(int64_t n, const T* __restrict__ a,
+                                                              const T* __restrict__ b,
+                                                              double* __restrict__ partial) {
+  double acc = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    acc += double(a[i]) * double(b[i]);
+  __shared__ double red[RED_THREADS / 32];
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < RED_THREADS / 32; ++q) s += red[q];
+    partial[blockIdx.x] = s;
+  }
+}
+
 __global__ void k_maxpy(int64_t n, int k, const double* __restrict__ V, int64_t ldv,
                         const double* __restrict__ h, double* __restrict__ w) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
@@ -169,6 +189,17 @@ void launch_mdot(int64_t n, int k, const double* V, int64_t ldv, const double* w
   k_mdot_final<<<k, RED_THREADS, 0, s>>>(nb, k, partial, k, out);
   count_launches(1);
 }
+
+template <typename T>
+void launch_dot(int64_t n, const T* a, const T* b, double* partial, double* out, cudaStream_t s) {
+  const int nb = reduction_blocks(n);
+  k_dot_partial<T><<<nb, RED_THREADS, 0, s>>>(n, a, b, partial);
+  count_launches(1);
+  k_mdot_final<<<1, RED_THREADS, 0, s>>>(nb, 1, partial, 1, out);
+  count_launches(1);
+}
+template void launch_dot<float>(int64_t, const float*, const float*, double*, double*, cudaStream_t);
+template void launch_dot<double>(int64_t, const double*, const double*, double*, double*, cudaStream_t);
 
 void launch_maxpy(int64_t n, int k, const double* V, int64_t ldv, const double* h, double* w,
                   cudaStream_t s) {

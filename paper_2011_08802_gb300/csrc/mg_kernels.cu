@@ -325,7 +325,105 @@ __global__ void k_coarse_solve(int n, const double* __restrict__ Aug, const T* _
   if (lane == 0) x[warp] = T(s);
 }
 
+// Chebyshev-accelerated point-block Jacobi (Saad, Iterative Methods, Alg. 12.1
+// applied to D^-1 J): first step d = c D^-1 r0 with r0 = src (also stored in r
+// when copy_r), x = d (zero_x) or x += d.
+template <typename T>
+__global__ void k_cheb_first(int64_t nn, const T* __restrict__ D, const T* src, T c, bool copy_r,
+                             bool zero_x, T* r, T* __restrict__ d, T* __restrict__ x) {
+  for (int64_t node = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; node < nn;
+       node += int64_t(gridDim.x) * blockDim.x) {
+    T rv[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      rv[f] = src[f * nn + node];
+      if (copy_r) r[f * nn + node] = rv[f];
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T s = T(0);
+#pragma unroll
+      for (int cc = 0; cc < NF; ++cc) s += D[(f * 9 + cc) * nn + node] * rv[cc];
+      const T dv = c * s;
+      d[f * nn + node] = dv;
+      x[f * nn + node] = zero_x ? dv : x[f * nn + node] + dv;
+    }
+  }
+}
+
+// r -= y; d = a d + c D^-1 r; x += d.
+template <typename T>
+__global__ void k_cheb_step(int64_t nn, const T* __restrict__ D, const T* __restrict__ y, T a, T c,
+                            T* __restrict__ r, T* __restrict__ d, T* __restrict__ x) {
+  for (int64_t node = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; node < nn;
+       node += int64_t(gridDim.x) * blockDim.x) {
+    T rv[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      rv[f] = r[f * nn + node] - y[f * nn + node];
+      r[f * nn + node] = rv[f];
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T s = T(0);
+#pragma unroll
+      for (int cc = 0; cc < NF; ++cc) s += D[(f * 9 + cc) * nn + node] * rv[cc];
+      const T dv = a * d[f * nn + node] + c * s;
+      d[f * nn + node] = dv;
+      x[f * nn + node] += dv;
+    }
+  }
+}
+
+// Deterministic start vector of the power iteration: values in [-1, 1) from
+// an integer hash of the index, zero at Dirichlet DOFs.
+template <typename T>
+__global__ void k_power_init(int64_t nn, const dmask_t* __restrict__ mask, T* __restrict__ x) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < NF * nn; i += int64_t(gridDim.x) * blockDim.x) {
+    uint64_t z = uint64_t(i) + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const double u = double(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+    const int f = int(i / nn);
+    x[i] = ((mask[i % nn] >> f) & 1) ? T(0) : T(u);
+  }
+}
+
+// x = y / sqrt(*dot)
+template <typename T>
+__global__ void k_scale_inv_sqrt(int64_t n, const T* __restrict__ y, const double* __restrict__ dot, T* __restrict__ x) {
+  const double s = 1.0 / sqrt(*dot);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    x[i] = T(double(y[i]) * s);
+}
+
 }  // namespace
+
+template <typename T>
+void launch_cheb_first(int64_t nn, const T* D, const T* src, T c, bool copy_r, bool zero_x, T* r, T* d, T* x,
+                       cudaStream_t s) {
+  k_cheb_first<T><<<grid_for(nn, 256), 256, 0, s>>>(nn, D, src, c, copy_r, zero_x, r, d, x);
+  count_launches(1);
+}
+
+template <typename T>
+void launch_cheb_step(int64_t nn, const T* D, const T* y, T a, T c, T* r, T* d, T* x, cudaStream_t s) {
+  k_cheb_step<T><<<grid_for(nn, 256), 256, 0, s>>>(nn, D, y, a, c, r, d, x);
+  count_launches(1);
+}
+
+template <typename T>
+void launch_power_init(int64_t nn, const dmask_t* mask, T* x, cudaStream_t s) {
+  k_power_init<T><<<grid_for(NF * nn, 256), 256, 0, s>>>(nn, mask, x);
+  count_launches(1);
+}
+
+template <typename T>
+void launch_scale_inv_sqrt(int64_t n, const T* y, const double* dot, T* x, cudaStream_t s) {
+  k_scale_inv_sqrt<T><<<grid_for(n, 256), 256, 0, s>>>(n, y, dot, x);
+  count_launches(1);
+}
 
 void launch_inject_state(const Grid& fine, const Grid& coarse, const double* Uf, double* Uc,
                          cudaStream_t s) {
@@ -409,7 +507,12 @@ void launch_coarse_solve(int n, const double* Ainv, const T* b, T* x, cudaStream
   template void launch_sub<T>(int64_t, const T*, const T*, T*, cudaStream_t);                     \
   template void launch_coarse_assemble<T>(const Grid&, const DevParams&, const T*, const dmask_t*, \
                                           double*, int, cudaStream_t);                          \
-  template void launch_coarse_solve<T>(int, const double*, const T*, T*, cudaStream_t);
+  template void launch_coarse_solve<T>(int, const double*, const T*, T*, cudaStream_t);         \
+  template void launch_cheb_first<T>(int64_t, const T*, const T*, T, bool, bool, T*, T*, T*,       \
+                                     cudaStream_t);                                             \
+  template void launch_cheb_step<T>(int64_t, const T*, const T*, T, T, T*, T*, T*, cudaStream_t); \
+  template void launch_power_init<T>(int64_t, const dmask_t*, T*, cudaStream_t);                  \
+  template void launch_scale_inv_sqrt<T>(int64_t, const T*, const double*, T*, cudaStream_t);
 PFM_INST(float)
 PFM_INST(double)
 #undef PFM_INST

@@ -202,14 +202,15 @@ def indentation_dirichlet(mesh: Mesh, step: int, n_steps: int = 10, depth_frac: 
 def config_indentation(n: int, seed: int, step: int = 1, n_steps: int = 10,
                        depth_frac: float = 0.02, radius_frac: float = 0.3,
                        noise: float = 1e-3, tau: float = 0.128) -> State:
-    """Nano-indentation-like load on an n^3 cube: eta_hat = noise * N(0,1) per
-    node (seeded), u = 0 except the prescribed cap values of load step
-    ``step``, eta_n = eta, bottom clamped."""
+    """Nano-indentation-like load on an n^3 cube: eta_hat = noise * U[0,1) per
+    node and variant (seeded; one-signed so the initial state lies in the
+    admissible simplex eta_i >= 0, sum eta_i = 1), u = 0 except the prescribed
+    cap values of load step ``step``, eta_n = eta, bottom clamped."""
     mesh = Mesh(n, n, n)
     rng = np.random.default_rng(seed)
     mask, values = indentation_dirichlet(mesh, step, n_steps, depth_frac, radius_frac)
     U = np.zeros((N_FIELDS, mesh.n_nodes))
-    U[3:9] = noise * rng.standard_normal((6, mesh.n_nodes))
+    U[3:9] = noise * rng.random((6, mesh.n_nodes))
     U[mask.astype(bool)] = values[mask.astype(bool)]
     Un = U.copy()
     Un[0:3] = 0.0

@@ -50,7 +50,9 @@ def parse_args():
     p.add_argument("--n", type=int, default=128, help="hexes per cube edge")
     p.add_argument("--no-fp64-step", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--sample", type=int, default=4, help="edge of the oracle's element sample")
+    p.add_argument("--sample", type=int, default=5, help="edge of the oracle's element sample")
+    p.add_argument("--mode", default="newton", choices=["newton", "japply"],
+                   help="japply: only K FP32 tangent applications (for profiler captures)")
     return p.parse_args()
 
 
@@ -201,6 +203,25 @@ def reference_arm(args, rank):
 
 
 # ---------------------------------------------------------------------------
+def japply_only(args):
+    """K FP32 tangent applications on the benchmark state (profiler driver)."""
+    import numpy as np
+    import torch
+
+    from paper_2011_08802_gb300 import abi, binding, inputs
+
+    st = inputs.config_indentation(args.n, seed=5, step=1)
+    P = binding.problem_from_state(st)
+    P.linearize(abi.PFM_F32)
+    v = torch.from_numpy(np.random.default_rng(1).standard_normal(P.shape).astype(np.float32)).cuda()
+    y = torch.empty_like(v)
+    for _ in range(args.warmup + args.steps):
+        P.jacobian_apply(v, y)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "japply", "n": args.n, "applications": args.warmup + args.steps}))
+    P.close()
+
+
 def gpu_arm(args, rank, world, dist):
     import numpy as np
     import torch
@@ -371,6 +392,8 @@ def main():
         dist = tdist
     if args.impl == "reference":
         reference_arm(args, rank)
+    elif args.mode == "japply":
+        japply_only(args)
     else:
         gpu_arm(args, rank, world, dist)
     if dist is not None:

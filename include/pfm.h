@@ -204,6 +204,23 @@ pfm_status pfm_fgmres_solve(pfm_handle* h, const pfm_solve_opts* opts, const dou
 pfm_status pfm_newton_solve(pfm_handle* h, const pfm_solve_opts* opts, double* U_inout_dev,
                             pfm_solve_report* report);
 
+/* Derivatives with respect to the material parameters
+ * theta = (C11, C12, C44, s_gamma) of a cubic stiffness shared by all phases
+ * (Voigt entries C11 on the normal diagonal, C12 off it, C44 on the shear
+ * diagonal) and the multiplier s_gamma of every interface energy gamma_ij.
+ * The potential (Eq. PenPot) is affine in each of them (Eq. elasticEn is
+ * linear in L, Eq. IntEnergy linear in gamma), so dPi/dtheta_k and
+ * dR/dtheta_k are the potential and residual of the theta_k-part alone.
+ * At the current state: dPi_dtheta_host[4] (host, nullable) receives
+ * dPi/dtheta; if w_dev (device double [9][n_nodes]) is given,
+ * wdR_dtheta_host[4] receives w . dR/dtheta (dR/dtheta zero at Dirichlet
+ * DOFs); if dR_dtheta_dev (device double [4][9][n_nodes], nullable) is given
+ * it receives the four vectors dR/dtheta_k. Requires the handle's stiffness
+ * to be cubic and equal for all phases (PFM_ERR_INVALID_ARG otherwise).
+ * Synchronises. */
+pfm_status pfm_param_grad(pfm_handle* h, const double* w_dev, double* dPi_dtheta_host,
+                          double* wdR_dtheta_host, double* dR_dtheta_dev);
+
 /* Gauss-point physics for testing: for n points, F (device double [n][9],
  * row-major), eta_hat and eta_hat_n (device double [n][6]) give the local
  * energy density W (device double [n]), its gradient (device double

@@ -142,6 +142,7 @@ def lib():
         "pfm_profile_enable": (i32, [H, i32]),
         "pfm_profile_get": (i32, [H, i32, C.POINTER(i64), C.POINTER(dp)]),
         "pfm_launch_count": (i64, []),
+        "pfm_param_grad": (i32, [H, vp, C.POINTER(dp), C.POINTER(dp), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -159,7 +160,7 @@ def exported_symbols():
         "pfm_residual", "pfm_linearize", "pfm_jacobian_apply", "pfm_jacobian_transpose_apply",
         "pfm_jacobian_apply_host", "pfm_vcycle", "pfm_fgmres_solve", "pfm_newton_solve",
         "pfm_qp_eval", "pfm_get_hessians", "pfm_profile_enable", "pfm_profile_get",
-        "pfm_launch_count",
+        "pfm_launch_count", "pfm_param_grad",
     ]
 
 

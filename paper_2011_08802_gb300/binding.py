@@ -162,6 +162,14 @@ class Problem:
         self._check(self._lib.pfm_qp_eval(self.h, n, _ptr(F), _ptr(eta), _ptr(eta_n), _ptr(W), _ptr(g), _ptr(H)))
         return W, g, H
 
+    def param_grad(self, w: torch.Tensor | None = None, dR: torch.Tensor | None = None):
+        """(dPi/dtheta, w . dR/dtheta) for theta = (C11, C12, C44, s_gamma);
+        dR (device double (4, 9, n_nodes)), if given, receives dR/dtheta."""
+        dPi = (C.c_double * 4)()
+        wdR = (C.c_double * 4)()
+        self._check(self._lib.pfm_param_grad(self.h, _ptr(w), dPi, wdR, _ptr(dR)))
+        return np.array(dPi[:]), (np.array(wdR[:]) if w is not None else None)
+
     def profile_enable(self, enable: bool = True):
         self._check(self._lib.pfm_profile_enable(self.h, int(enable)))
 

@@ -910,6 +910,73 @@ pfm_status pfm_newton_solve(pfm_handle* h, const pfm_solve_opts* opts, double* U
   return st;
 }
 
+pfm_status pfm_param_grad(pfm_handle* h, const double* w_dev, double* dPi, double* wdR, double* dR_dev) {
+  TRY(check_ready(h, false));
+  const pfm_params& p = h->params;
+  // the stiffness must be one cubic matrix shared by every phase
+  const double* L0 = p.Lvoigt[0];
+  auto at = [&](const double* L, int i, int j) { return L[6 * i + j]; };
+  for (int ph = 0; ph < NPH; ++ph)
+    for (int k = 0; k < 36; ++k)
+      if (p.Lvoigt[ph][k] != L0[k]) return h->fail(PFM_ERR_INVALID_ARG, "stiffness differs between phases");
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double expect;
+      if (i < 3 && j < 3) expect = (i == j) ? at(L0, 0, 0) : at(L0, 0, 1);
+      else expect = (i == j) ? at(L0, 3, 3) : 0.0;
+      if (at(L0, i, j) != expect) return h->fail(PFM_ERR_INVALID_ARG, "stiffness is not cubic");
+    }
+  Level& f = h->L[0];
+  cudaStream_t s = h->stream;
+  const int64_t n = ndof(f);
+  double* Rk = h->wv;  // work vector
+  for (int k = 0; k < 4; ++k) {
+    // the theta_k-part of the potential: unit C11 / C12 / C44 stiffness with
+    // every other term off, or the interface terms alone at s_gamma = 1
+    pfm_params q = p;
+    for (int ph = 0; ph < NPH; ++ph) {
+      for (int m = 0; m < 36; ++m) q.Lvoigt[ph][m] = 0.0;
+      q.F0[ph] = 0.0;
+    }
+    q.eps_eta = 0.0;
+    DevParams dq;
+    if (k < 3) {
+      for (int ph = 0; ph < NPH; ++ph)
+        for (int i = 0; i < 6; ++i)
+          for (int j = 0; j < 6; ++j) {
+            double v = 0.0;
+            if (k == 0 && i < 3 && i == j) v = 1.0;
+            if (k == 1 && i < 3 && j < 3 && i != j) v = 1.0;
+            if (k == 2 && i >= 3 && i == j) v = 1.0;
+            q.Lvoigt[ph][6 * i + j] = v;
+          }
+      q.gamma_scale = 0.0;
+    } else {
+      q.gamma_scale = 1.0;
+    }
+    make_dev_params(q, dq);
+    for (int ph = 0; ph < NPH; ++ph) dq.inv_mtau[ph] = 0.0;  // no dissipation
+    if (dR_dev) Rk = dR_dev + int64_t(k) * n;
+    CK(cudaMemsetAsync(Rk, 0, sizeof(double) * n, s));
+    CK(cudaMemsetAsync(h->energy_dev, 0, sizeof(double), s));
+    launch_residual(f.g, dq, f.U, f.Un, f.mask, Rk, h->energy_dev, s);
+    CKL();
+    double e = 0.0;
+    CK(cudaMemcpyAsync(&e, h->energy_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (w_dev) {
+      launch_dot<double>(n, w_dev, Rk, h->partial, h->hdev, s);
+      double d = 0.0;
+      CK(cudaMemcpyAsync(&d, h->hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (wdR) wdR[k] = d;
+    }
+    CK(cudaStreamSynchronize(s));
+    // the gamma part scales with s_gamma: derivative = (interface energy at s=1)
+    if (dPi) dPi[k] = e;
+  }
+  return PFM_OK;
+}
+
 pfm_status pfm_qp_eval(pfm_handle* h, int64_t n, const double* F_dev, const double* eta_dev, const double* eta_n_dev,
                        double* W_dev, double* grad_dev, double* hess_dev) {
   if (!h) return PFM_ERR_INVALID_ARG;

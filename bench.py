@@ -204,7 +204,8 @@ def reference_arm(args, rank):
 
 # ---------------------------------------------------------------------------
 def japply_only(args):
-    """K FP32 tangent applications on the benchmark state (profiler driver)."""
+    """K FP32 tangent applications on the benchmark state (profiler driver);
+    prints the mean device time per application (CUDA events)."""
     import numpy as np
     import torch
 
@@ -213,12 +214,25 @@ def japply_only(args):
     st = inputs.config_indentation(args.n, seed=5, step=1)
     P = binding.problem_from_state(st)
     P.linearize(abi.PFM_F32)
-    v = torch.from_numpy(np.random.default_rng(1).standard_normal(P.shape).astype(np.float32)).cuda()
-    y = torch.empty_like(v)
-    for _ in range(args.warmup + args.steps):
-        P.jacobian_apply(v, y)
-    torch.cuda.synchronize()
-    print(json.dumps({"mode": "japply", "n": args.n, "applications": args.warmup + args.steps}))
+    out = {"mode": "japply", "n": args.n}
+    for name, dt in (("f32", np.float32), ("f64", np.float64)):
+        v = torch.from_numpy(np.random.default_rng(1).standard_normal(P.shape).astype(dt)).cuda()
+        y = torch.empty_like(v)
+        for _ in range(args.warmup):
+            P.jacobian_apply(v, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            P.jacobian_apply(v, y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        nblk = (P.n_elems + 3) // 4
+        hb = nblk * 4 * 8 * 120 * np.dtype(dt).itemsize
+        vb = 9 * P.n_nodes * np.dtype(dt).itemsize
+        out[name] = {"ms": ms, "GDOF/s": 9 * P.n_nodes / ms / 1e6, "GB/s": (hb + 2 * vb + 2 * P.n_nodes) / ms / 1e6}
+    print(json.dumps(out), flush=True)
     P.close()
 
 

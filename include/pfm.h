@@ -94,7 +94,7 @@ typedef struct {
   int smoother;          /* 0: Chebyshev-accelerated point-block Jacobi on the interval
                             [cheb_lo, cheb_hi] * lambda_max(D^-1 J) (lambda_max estimated by
                             power iteration at pfm_linearize); 1: damped point-block Jacobi */
-  double cheb_lo, cheb_hi;  /* Chebyshev interval as fractions of lambda_max (0.1, 1.1) */
+  double cheb_lo, cheb_hi;  /* Chebyshev interval as fractions of lambda_max (0.05, 1.1) */
 } pfm_solve_opts;
 
 typedef struct {
@@ -184,7 +184,7 @@ pfm_status pfm_jacobian_apply_host(pfm_handle* h, const void* v_host, void* y_ho
  * nu_post smoothing steps. r_dev, z_dev: device [9][n_nodes] in the precision
  * prec (the precision of the preconditioner built by pfm_linearize). Uses
  * opts->nu_pre, nu_post, smoother, cheb_lo, cheb_hi, omega (NULL = defaults
- * 2, 2, Chebyshev, 0.1, 1.1). */
+ * 4, 4, Chebyshev, 0.05, 1.1). */
 pfm_status pfm_vcycle(pfm_handle* h, const void* r_dev, void* z_dev, pfm_precision prec,
                       const pfm_solve_opts* opts);
 

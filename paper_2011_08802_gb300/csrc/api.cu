@@ -208,8 +208,8 @@ void japply_level(pfm_handle* h, size_t l, const T* H, const T* x, T* y) {
 // (Sec. 3.4) with Chebyshev step lengths. Damped Jacobi (type 1):
 // x += omega D^-1 (b - J x). Both cost one tangent application per step.
 struct SmoothCfg {
-  int nu_pre = 2, nu_post = 2, type = 0;
-  double omega = 0.7, lo = 0.1, hi = 1.1;
+  int nu_pre = 4, nu_post = 4, type = 0;
+  double omega = 0.7, lo = 0.05, hi = 1.1;
 };
 
 SmoothCfg smooth_cfg(const pfm_solve_opts* o) {

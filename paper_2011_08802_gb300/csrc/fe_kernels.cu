@@ -221,72 +221,89 @@ struct JParams {
   T w, ihx, ihy, ihz;
 };
 
-// y += J v over the elements (y initialised by k_japply_init).
-template <typename T>
-__global__ void __launch_bounds__(256) k_japply(Grid g, JParams<T> jp, const T* __restrict__ H,
+// Asynchronous bulk prefetch of a contiguous global range into L2 (the
+// bulk-copy engine; no registers or shared memory involved). Address 16-byte
+// aligned, size a multiple of 16 bytes.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// y += J v over the elements (y initialised by k_japply_init). Persistent
+// warps walk the element blocks (4 elements each) with a grid stride; before
+// working on a block, lane 0 prefetches the block this warp takes PF strides
+// later, so every warp keeps its next 15 KB (FP32) of Hessians in flight.
+template <typename T, int PF>
+__global__ void __launch_bounds__(256, 2) k_japply(Grid g, JParams<T> jp, const T* __restrict__ H,
                                                 const dmask_t* __restrict__ mask,
                                                 const T* __restrict__ v, T* __restrict__ y) {
   constexpr int V = 16 / sizeof(T);
   using VT = typename Vec16<T>::type;
-  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t blk = tid >> 5;
-  if (blk >= g.nblk()) return;
-  const int64_t e = tid >> 3;
-  const int l8 = int(tid & 7);
-  const int lane = int(tid & 31);
-  const bool valid = e < g.ne();
+  const int64_t nblk = g.nblk();
+  const int64_t wg = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int lane = int(threadIdx.x & 31);
+  const int l8 = lane & 7;
   const int64_t nn = g.nn();
-  const int64_t node = valid ? elem_node(g, e, l8) : 0;
-  const dmask_t dm = valid ? mask[node] : dmask_t(0x1ff);
-  T dz[NZ], ge[18];
+  constexpr unsigned BLK_BYTES = unsigned(HBLK * sizeof(T));
+  if (lane == 0)
+    for (int d = 0; d < PF; ++d)
+      if (wg + d * nw < nblk) prefetch_l2(H + (wg + d * nw) * HBLK, BLK_BYTES);
+  for (int64_t blk = wg; blk < nblk; blk += nw) {
+    if (lane == 0 && blk + PF * nw < nblk) prefetch_l2(H + (blk + PF * nw) * HBLK, BLK_BYTES);
+    const int64_t e = blk * 4 + (lane >> 3);
+    const bool valid = e < g.ne();
+    const int64_t node = valid ? elem_node(g, e, l8) : 0;
+    const dmask_t dm = valid ? mask[node] : dmask_t(0x1ff);
+    T dz[NZ], ge[18];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    T x = ((dm >> i) & 1) ? T(0) : v[i * nn + node];
-    T val;
-    q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, val, dz[3 * i], dz[3 * i + 1], dz[3 * i + 2]);
-  }
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    T x = ((dm >> (3 + k)) & 1) ? T(0) : v[(3 + k) * nn + node];
-    q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, dz[9 + k], ge[3 * k], ge[3 * k + 1], ge[3 * k + 2]);
-  }
-  // sigma = H dz from the packed symmetric store
-  T sg[NZ];
-#pragma unroll
-  for (int r = 0; r < NZ; ++r) sg[r] = T(0);
-  const VT* Hv = reinterpret_cast<const VT*>(H) + blk * (NH / V) * 32 + lane;
-#pragma unroll
-  for (int j = 0; j < NH / V; ++j) {
-    T hv[V];
-    Vec16<T>::unpack(__ldcs(Hv + j * 32), hv);
-#pragma unroll
-    for (int t = 0; t < V; ++t) {
-      const int idx = j * V + t;
-      // (r, c) of packed index idx (constant-folded after unrolling)
-      const int r = packed_row(idx);
-      const int c = r + (idx - packed_row_start(r));
-      sg[r] += hv[t] * dz[c];
-      if (c != r) sg[c] += hv[t] * dz[r];
+    for (int i = 0; i < 3; ++i) {
+      T x = ((dm >> i) & 1) ? T(0) : v[i * nn + node];
+      T val;
+      q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, val, dz[3 * i], dz[3 * i + 1], dz[3 * i + 2]);
     }
-  }
-  const T w = jp.w;
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    T r = q1_scatter_grad(w * sg[3 * i], w * sg[3 * i + 1], w * sg[3 * i + 2], l8, jp.ihx, jp.ihy, jp.ihz);
-    if (valid && !((dm >> i) & 1)) atomicAdd(&y[i * nn + node], r);
-  }
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    T gf[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      T s = T(0);
-#pragma unroll
-      for (int l = 0; l < 6; ++l) s += jp.G[k][l] * ge[3 * l + d];
-      gf[d] = w * s;
+    for (int k = 0; k < 6; ++k) {
+      T x = ((dm >> (3 + k)) & 1) ? T(0) : v[(3 + k) * nn + node];
+      q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, dz[9 + k], ge[3 * k], ge[3 * k + 1], ge[3 * k + 2]);
     }
-    T r = q1_scatter(w * sg[9 + k], gf[0], gf[1], gf[2], l8, jp.ihx, jp.ihy, jp.ihz);
-    if (valid && !((dm >> (3 + k)) & 1)) atomicAdd(&y[(3 + k) * nn + node], r);
+    // sigma = H dz from the packed symmetric store
+    T sg[NZ];
+#pragma unroll
+    for (int r = 0; r < NZ; ++r) sg[r] = T(0);
+    const VT* Hv = reinterpret_cast<const VT*>(H) + blk * (NH / V) * 32 + lane;
+#pragma unroll
+    for (int j = 0; j < NH / V; ++j) {
+      T hv[V];
+      Vec16<T>::unpack(__ldcs(Hv + j * 32), hv);
+#pragma unroll
+      for (int t = 0; t < V; ++t) {
+        const int idx = j * V + t;
+        // (r, c) of packed index idx (constant-folded after unrolling)
+        const int r = packed_row(idx);
+        const int c = r + (idx - packed_row_start(r));
+        sg[r] += hv[t] * dz[c];
+        if (c != r) sg[c] += hv[t] * dz[r];
+      }
+    }
+    const T w = jp.w;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      T r = q1_scatter_grad(w * sg[3 * i], w * sg[3 * i + 1], w * sg[3 * i + 2], l8, jp.ihx, jp.ihy, jp.ihz);
+      if (valid && !((dm >> i) & 1)) atomicAdd(&y[i * nn + node], r);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      T gf[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        T s = T(0);
+#pragma unroll
+        for (int l = 0; l < 6; ++l) s += jp.G[k][l] * ge[3 * l + d];
+        gf[d] = w * s;
+      }
+      T r = q1_scatter(w * sg[9 + k], gf[0], gf[1], gf[2], l8, jp.ihx, jp.ihy, jp.ihz);
+      if (valid && !((dm >> (3 + k)) & 1)) atomicAdd(&y[(3 + k) * nn + node], r);
+    }
   }
 }
 
@@ -437,6 +454,9 @@ inline unsigned grid_for(int64_t threads, int block) {
   return unsigned((threads + block - 1) / block);
 }
 
+// element blocks a warp prefetches ahead of the one it works on
+constexpr int JAPPLY_PF = 1;
+
 }  // namespace
 
 void launch_residual(const Grid& g, const DevParams& P, const double* U, const double* Un,
@@ -459,8 +479,22 @@ void launch_japply(const Grid& g, const DevParams& P, const T* H, const dmask_t*
   const int64_t nn = g.nn();
   k_japply_init<T><<<grid_for(NF * nn, 256) < 4096 ? grid_for(NF * nn, 256) : 4096, 256, 0, s>>>(nn, mask, v, y);
   count_launches(1);
-  const int64_t threads = g.nblk() * 32;
-  k_japply<T><<<grid_for(threads, 256), 256, 0, s>>>(g, make_jparams<T>(g, P), H, mask, v, y);
+  // persistent grid: every SM filled with as many resident blocks as fit
+  static int sms = 0, per_sm[2] = {0, 0};
+  const int ti = sizeof(T) == 4 ? 0 : 1;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  if (per_sm[ti] == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[ti], k_japply<T, JAPPLY_PF>, 256, 0);
+    if (per_sm[ti] < 1) per_sm[ti] = 1;
+  }
+  const int64_t need = (g.nblk() * 32 + 255) / 256;
+  const int64_t full = int64_t(sms) * per_sm[ti];
+  const unsigned blocks = unsigned(need < full ? need : full);
+  k_japply<T, JAPPLY_PF><<<blocks, 256, 0, s>>>(g, make_jparams<T>(g, P), H, mask, v, y);
   count_launches(1);
 }
 

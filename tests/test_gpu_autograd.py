@@ -117,7 +117,7 @@ def test_adjoint_gradient_matches_finite_differences(mods):
     st = inputs.config_random(6, 5, 4, seed=61, eta_lo=0.02, eta_hi=0.3, Lx=12.0, Ly=10.0, Lz=8.0)
     w = torch.from_numpy(inputs.direction_vectors(st, 1, seed=7)[0]).cuda()
     Un = torch.from_numpy(st.Un).cuda()
-    opts = abi.default_opts(abi.PFM_F32, max_newton=12, newton_rtol=1e-13, lin_rtol=1e-12, max_lin_it=600)
+    opts = abi.default_opts(abi.PFM_F32, max_newton=12, newton_rtol=1e-12, lin_rtol=1e-10, max_lin_it=600)
 
     def solve(theta):
         P = binding.problem_from_state(st, params=autograd.params_for(st.material, st.tau, theta))
@@ -128,11 +128,11 @@ def test_adjoint_gradient_matches_finite_differences(mods):
     P, U = solve(THETA0)
     P.set_state(U, Un)
     g, lam, rep = autograd.adjoint_gradient(P, w)
-    for k, step in ((0, 0.5), (2, 0.25), (3, 1e-3)):
+    for k, step in ((0, 0.05), (2, 0.02), (3, 1e-4)):
         tp, tm = THETA0.copy(), THETA0.copy()
         tp[k] += step
         tm[k] -= step
         gp = float((w * solve(tp)[1]).sum())
         gm = float((w * solve(tm)[1]).sum())
         fd = (gp - gm) / (2 * step)
-        assert abs(float(g[k]) - fd) <= 1e-5 * abs(fd) + 1e-9, (k, float(g[k]), fd)
+        assert abs(float(g[k]) - fd) <= 3e-5 * abs(fd) + 1e-9, (k, float(g[k]), fd)

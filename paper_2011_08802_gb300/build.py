@@ -22,12 +22,16 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def build(verbose: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(verbose: bool = False, ptxas_info: bool = False, out_dir: str | None = None,
+          defines: tuple = ()) -> str:
+    """Compile and link; ``out_dir``/``defines`` build a variant elsewhere
+    (e.g. a launch-configuration sweep) without touching the in-tree library."""
+    out = out_dir or OUT
+    os.makedirs(out, exist_ok=True)
     objs, procs = [], []
     for src in SOURCES:
-        obj = os.path.join(OUT, src.replace(".cu", ".o"))
-        cmd = [nvcc(), *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(out, src.replace(".cu", ".o"))
+        cmd = [nvcc(), *ARCH, *FLAGS, *[f"-D{d}" for d in defines], "-c", os.path.join(CSRC, src), "-o", obj]
         if ptxas_info:
             cmd.insert(1, "-Xptxas=-v")
         objs.append(obj)
@@ -41,7 +45,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
             failed.append(src)
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
-    lib = os.path.join(OUT, "libpfm.so")
+    lib = os.path.join(out, "libpfm.so")
     tmp = lib + ".tmp"
     subprocess.check_call([nvcc(), *ARCH, "-shared", *objs, "-o", tmp, "-lcudart"])
     os.replace(tmp, lib)

@@ -232,8 +232,11 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 // warps walk the element blocks (4 elements each) with a grid stride; before
 // working on a block, lane 0 prefetches the block this warp takes PF strides
 // later, so every warp keeps its next 15 KB (FP32) of Hessians in flight.
+#ifndef PFM_JAPPLY_MINB
+#define PFM_JAPPLY_MINB 2
+#endif
 template <typename T, int PF>
-__global__ void __launch_bounds__(256, 2) k_japply(Grid g, JParams<T> jp, const T* __restrict__ H,
+__global__ void __launch_bounds__(256, PFM_JAPPLY_MINB) k_japply(Grid g, JParams<T> jp, const T* __restrict__ H,
                                                 const dmask_t* __restrict__ mask,
                                                 const T* __restrict__ v, T* __restrict__ y) {
   constexpr int V = 16 / sizeof(T);
@@ -455,7 +458,10 @@ inline unsigned grid_for(int64_t threads, int block) {
 }
 
 // element blocks a warp prefetches ahead of the one it works on
-constexpr int JAPPLY_PF = 1;
+#ifndef PFM_JAPPLY_PF
+#define PFM_JAPPLY_PF 1
+#endif
+constexpr int JAPPLY_PF = PFM_JAPPLY_PF;
 
 }  // namespace
 

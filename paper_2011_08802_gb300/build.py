@@ -10,7 +10,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
-SOURCES = ["fe_kernels.cu", "mg_kernels.cu", "krylov_kernels.cu", "api.cu"]
+SOURCES = ["fe_kernels.cu", "mg_kernels.cu", "krylov_kernels.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -38,9 +38,9 @@ def build(verbose: bool = False, ptxas_info: bool = False, out_dir: str | None =
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     failed = []
     for src, p in procs:
-        out, _ = p.communicate()
+        log, _ = p.communicate()
         if verbose or p.returncode != 0 or ptxas_info:
-            sys.stdout.write(out.decode(errors="replace"))
+            sys.stdout.write(log.decode(errors="replace"))
         if p.returncode != 0:
             failed.append(src)
     if failed:

@@ -143,6 +143,9 @@ def lib():
         "pfm_profile_get": (i32, [H, i32, C.POINTER(i64), C.POINTER(dp)]),
         "pfm_launch_count": (i64, []),
         "pfm_param_grad": (i32, [H, vp, C.POINTER(dp), C.POINTER(dp), vp]),
+        "pfm_residual_noalloc": (i32, [C.POINTER(MeshDesc), C.POINTER(Params), vp, vp, vp, vp,
+                                       C.POINTER(dp), vp]),
+        "pfm_noalloc_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -160,7 +163,7 @@ def exported_symbols():
         "pfm_residual", "pfm_linearize", "pfm_jacobian_apply", "pfm_jacobian_transpose_apply",
         "pfm_jacobian_apply_host", "pfm_vcycle", "pfm_fgmres_solve", "pfm_newton_solve",
         "pfm_qp_eval", "pfm_get_hessians", "pfm_profile_enable", "pfm_profile_get",
-        "pfm_launch_count", "pfm_param_grad",
+        "pfm_launch_count", "pfm_param_grad", "pfm_residual_noalloc", "pfm_noalloc_last_error",
     ]
 
 

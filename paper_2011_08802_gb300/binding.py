@@ -184,6 +184,23 @@ class Problem:
         return out
 
 
+def residual_noalloc(mesh, params: abi.Params, mask: torch.Tensor, U: torch.Tensor, Un: torch.Tensor,
+                     R: torch.Tensor | None = None, stream=None):
+    """``pfm_residual_noalloc``: residual and potential without a handle and
+    without device allocation by the library (R is allocated here by torch
+    only when the caller passes none). Returns (R, energy)."""
+    L = abi.lib()
+    R = torch.empty_like(U) if R is None else R
+    desc = abi.MeshDesc(mesh.nx, mesh.ny, mesh.nz, mesh.Lx, mesh.Ly, mesh.Lz, 0)
+    e = C.c_double()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = L.pfm_residual_noalloc(C.byref(desc), C.byref(params), _ptr(mask), _ptr(U), _ptr(Un), _ptr(R),
+                                C.byref(e), C.c_void_p(s.cuda_stream))
+    if st != 0:
+        raise PfmError(st, L.pfm_noalloc_last_error().decode())
+    return R, e.value
+
+
 def launch_count() -> int:
     """Kernel launches issued by the library in this process (``pfm_launch_count``)."""
     return int(abi.lib().pfm_launch_count())

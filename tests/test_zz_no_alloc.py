@@ -1,0 +1,68 @@
+"""The allocation-free residual entry point (GPU tests).
+
+``pfm_residual_noalloc`` serves callers that cannot call cudaMalloc (code
+inside a framework that owns device memory through its own allocator, or that
+must not allocate mid time step): it uses one fixed file-scope device array as
+working memory. Its output must equal that of the handle-based
+``pfm_residual`` on the same state, on two calls in a row (the shared array
+keeps the previous call's contents, so anything accumulated must be cleared).
+This file is collected last on purpose."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2011_08802_gb300 import abi, inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+RTOL64 = 1e-11  # the FP64 residual tolerance of the other parity tests
+
+
+@pytest.fixture(scope="module")
+def binding():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_08802_gb300 import binding as b
+    return b
+
+
+def _relerr(a, b):
+    return float((a - b).abs().max() / b.abs().max())
+
+
+def test_noalloc_residual_matches_handle_residual_twice(binding):
+    st = inputs.config_random(7, 5, 3, seed=71, eta_lo=-0.04, eta_hi=0.32, Lx=14.0, Ly=10.0, Lz=6.0)
+    params = abi.params_from_material(st.material, st.tau)
+    P = binding.problem_from_state(st, params=params)
+    R_ref, E_ref = P.residual(energy=True)
+    mask = torch.from_numpy(st.mask).cuda()
+    U = torch.from_numpy(st.U).cuda()
+    Un = torch.from_numpy(st.Un).cuda()
+    R = torch.full_like(U, 123.0)  # stale output contents must not leak into the result
+    for _ in range(2):
+        R, E = binding.residual_noalloc(st.mesh, params, mask, U, Un, R)
+        torch.cuda.synchronize()
+        assert _relerr(R, R_ref) < RTOL64
+        assert abs(E - E_ref) <= RTOL64 * abs(E_ref)
+    # a different state through the same scratch: still equal to the handle's result
+    st2 = inputs.config_indentation(6, seed=72, step=2)
+    p2 = abi.params_from_material(st2.material, st2.tau)
+    P2 = binding.problem_from_state(st2, params=p2)
+    R2_ref, E2_ref = P2.residual(energy=True)
+    R2, E2 = binding.residual_noalloc(st2.mesh, p2, torch.from_numpy(st2.mask).cuda(),
+                                      torch.from_numpy(st2.U).cuda(), torch.from_numpy(st2.Un).cuda())
+    assert _relerr(R2, R2_ref) < RTOL64
+    assert abs(E2 - E2_ref) <= RTOL64 * abs(E2_ref)
+    P.close()
+    P2.close()
+
+
+def test_noalloc_rejects_grids_beyond_its_scratch(binding):
+    mesh = inputs.Mesh(170, 170, 170)  # 171^3 nodes > 4,194,304
+    params = abi.params_from_material(inputs.MATERIAL, 0.1)
+    dummy = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(binding.PfmError) as exc:
+        binding.residual_noalloc(mesh, params, dummy.to(torch.uint8), dummy, dummy, dummy)
+    assert exc.value.status == 1
+    assert "at most" in str(exc.value)

@@ -51,6 +51,8 @@ def parse_args():
     p.add_argument("--no-fp64-step", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--sample", type=int, default=5, help="edge of the oracle's element sample")
+    p.add_argument("--no-batch", action="store_true", help="skip the 64-problem batch measurement")
+    p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--mode", default="newton", choices=["newton", "japply"],
                    help="japply: only K FP32 tangent applications (for profiler captures)")
     return p.parse_args()
@@ -236,6 +238,58 @@ def japply_only(args):
     P.close()
 
 
+def batch_measure(args, dev):
+    """64 independent indentation problems, n ~ U{8..24} and depth ~
+    U[0.005, 0.03] L (seeded), one Newton correction each at rtol 1e-8: wall
+    time of one pfm_batch_newton_solve against the same problems solved one
+    after another with pfm_newton_solve."""
+    import torch
+
+    from paper_2011_08802_gb300 import abi, binding, inputs
+
+    ns, depths = inputs.batch_sizes(count=args.batch_count, seed=4)
+    sts = [inputs.config_indentation(n, seed=1000 + k, step=1, n_steps=1, depth_frac=d)
+           for k, (n, d) in enumerate(zip(ns, depths))]
+    probs = [binding.problem_from_state(st) for st in sts]
+    U0 = [torch.from_numpy(st.U).to(dev) for st in sts]
+    opts = abi.default_opts(abi.PFM_F32, max_newton=1, lin_rtol=1e-8, max_lin_it=400)
+    dofs = sum(9 * p.n_nodes for p in probs)
+
+    def sequential():
+        its = []
+        for P, u0 in zip(probs, U0):
+            U = u0.clone()
+            its.append(P.newton_solve(U, opts, check=False).lin_its_last)
+        torch.cuda.synchronize()
+        return its
+
+    B = binding.Batch(probs)
+
+    def batched():
+        Us = [u.clone() for u in U0]
+        reps = B.newton_solve(Us, opts, check=False)
+        torch.cuda.synchronize()
+        return reps
+
+    sequential()
+    batched()
+    t0 = time.perf_counter()
+    seq_its = sequential()
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    reps = batched()
+    t_bat = time.perf_counter() - t0
+    worst = max(r.lin_res_final for r in reps)
+    B.close()
+    for P in probs:
+        P.close()
+    return {"problems": len(probs), "n_range": [min(ns), max(ns)], "total_dofs": dofs,
+            "batch_s": t_bat, "sequential_s": t_seq, "speedup": t_seq / t_bat,
+            "batch_fgmres_its_max": max(r.lin_its_last for r in reps),
+            "sequential_fgmres_its_max": max(seq_its), "worst_rel_residual": worst,
+            "all_ok": all(r.status == 0 for r in reps)}
+
+
 def gpu_arm(args, rank, world, dist):
     import numpy as np
     import torch
@@ -253,6 +307,7 @@ def gpu_arm(args, rank, world, dist):
     st = inputs.config_indentation(args.n, seed=5 + rank, step=1)
     P = binding.problem_from_state(st)
     ndofs = 9 * P.n_nodes
+    nlev = P.n_levels
     U0 = torch.from_numpy(st.U).to(dev)
     Uw = torch.empty_like(U0)
     opts = abi.default_opts(abi.PFM_F32, max_newton=1, restart=30, max_lin_it=400, lin_rtol=1e-8)
@@ -352,6 +407,12 @@ def gpu_arm(args, rank, world, dist):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_value = ndofs * world / float(t[0]) / 1e9
 
+    batch = None
+    if not args.no_batch:
+        P.close()
+        P = None
+        batch = batch_measure(args, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cv, desc, _ = oracle_jvp_sample(args.n, args.sample, seconds=10.0)
@@ -366,7 +427,7 @@ def gpu_arm(args, rank, world, dist):
             "data": "synthetic (seeded indentation state, no dataset)",
             "config": {
                 "workload": f"nano-indentation Newton step, {args.n}^3 Q1 hexes, {ndofs} DOFs per GPU, "
-                            f"{P.n_levels}-level geometric MG, load step 1/10, FGMRES(30) rtol 1e-8",
+                            f"{nlev}-level geometric MG, load step 1/10, FGMRES(30) rtol 1e-8",
                 "problems": world, "l2": "inputs larger than L2 (8 GB Hessian store per application)",
             },
             "newton_step_s": {"fp32_mg": ms_step / 1e3, "fp64": fp64["s"] if fp64 else None},
@@ -386,9 +447,11 @@ def gpu_arm(args, rank, world, dist):
             "gpu_launches": launches,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "batch": batch,
         }
         print(json.dumps(line), flush=True)
-    P.close()
+    if P is not None:
+        P.close()
 
 
 def main():

@@ -259,6 +259,29 @@ pfm_status pfm_profile_get(pfm_handle* h, int id, int64_t* launches, double* tot
 /* Kernel launches issued by the library in this process so far (all handles). */
 int64_t pfm_launch_count(void);
 
+/* A batch of independent problems of possibly different grid sizes, each a
+ * handle with its own Dirichlet data and state, solved together: every
+ * problem gets its own CUDA stream, the Newton and FGMRES iterations of all
+ * problems advance in lockstep (one synchronisation per iteration for the
+ * whole batch), and each problem's V-cycle is replayed from a CUDA graph
+ * captured once per linearisation. The handles must outlive the batch and
+ * must not be used by other calls while pfm_batch_newton_solve runs.
+ * Errors: PFM_ERR_INVALID_ARG (null handle, count < 1), PFM_ERR_CUDA. */
+typedef struct pfm_batch pfm_batch;
+pfm_status pfm_batch_create(pfm_handle* const* handles, int count, pfm_batch** out);
+void pfm_batch_destroy(pfm_batch* b);
+const char* pfm_batch_last_error(const pfm_batch* b);
+
+/* pfm_newton_solve for every problem of the batch (Sec. 3.4, Eq. linAlgEq):
+ * U_inout[p] (device double [9][n_nodes_p]) is problem p's initial iterate
+ * on entry and its result on exit; reports (host array of count entries,
+ * nullable) get each problem's iteration counts and norms (times are those of
+ * the whole batch). Problems that meet newton_rtol stop early while the others
+ * continue. Returns the first failing status, PFM_OK if every problem
+ * converged. Synchronises. */
+pfm_status pfm_batch_newton_solve(pfm_batch* b, const pfm_solve_opts* opts, double* const* U_inout,
+                                  pfm_solve_report* reports);
+
 /* Residual and potential without a handle and without allocating device
  * memory, for callers that cannot call cudaMalloc: code inside a framework
  * that owns all device memory through its own allocator, code that must not

@@ -143,6 +143,10 @@ def lib():
         "pfm_profile_get": (i32, [H, i32, C.POINTER(i64), C.POINTER(dp)]),
         "pfm_launch_count": (i64, []),
         "pfm_param_grad": (i32, [H, vp, C.POINTER(dp), C.POINTER(dp), vp]),
+        "pfm_batch_create": (i32, [C.POINTER(H), i32, C.POINTER(H)]),
+        "pfm_batch_destroy": (None, [H]),
+        "pfm_batch_last_error": (C.c_char_p, [H]),
+        "pfm_batch_newton_solve": (i32, [H, C.POINTER(SolveOpts), C.POINTER(vp), C.POINTER(SolveReport)]),
         "pfm_residual_noalloc": (i32, [C.POINTER(MeshDesc), C.POINTER(Params), vp, vp, vp, vp,
                                        C.POINTER(dp), vp]),
         "pfm_noalloc_last_error": (C.c_char_p, []),
@@ -163,7 +167,8 @@ def exported_symbols():
         "pfm_residual", "pfm_linearize", "pfm_jacobian_apply", "pfm_jacobian_transpose_apply",
         "pfm_jacobian_apply_host", "pfm_vcycle", "pfm_fgmres_solve", "pfm_newton_solve",
         "pfm_qp_eval", "pfm_get_hessians", "pfm_profile_enable", "pfm_profile_get",
-        "pfm_launch_count", "pfm_param_grad", "pfm_residual_noalloc", "pfm_noalloc_last_error",
+        "pfm_launch_count", "pfm_param_grad", "pfm_batch_create", "pfm_batch_destroy",
+        "pfm_batch_last_error", "pfm_batch_newton_solve", "pfm_residual_noalloc", "pfm_noalloc_last_error",
     ]
 
 

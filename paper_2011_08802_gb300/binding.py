@@ -184,6 +184,40 @@ class Problem:
         return out
 
 
+class Batch:
+    """``pfm_batch_create`` over existing problems (which must outlive it)."""
+
+    def __init__(self, problems):
+        L = abi.lib()
+        self._lib = L
+        self.problems = list(problems)
+        arr = (C.c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
+        b = C.c_void_p()
+        st = L.pfm_batch_create(arr, len(self.problems), C.byref(b))
+        if st != 0:
+            raise PfmError(st, L.pfm_batch_last_error(None).decode())
+        self.b = b
+
+    def newton_solve(self, states, opts: abi.SolveOpts, check: bool = True):
+        arr = (C.c_void_p * len(states))(*[U.data_ptr() for U in states])
+        reps = (abi.SolveReport * len(states))()
+        st = self._lib.pfm_batch_newton_solve(self.b, C.byref(opts), arr, reps)
+        if check and st != 0:
+            raise PfmError(st, self._lib.pfm_batch_last_error(self.b).decode())
+        return list(reps)
+
+    def close(self):
+        if getattr(self, "b", None):
+            self._lib.pfm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def residual_noalloc(mesh, params: abi.Params, mask: torch.Tensor, U: torch.Tensor, Un: torch.Tensor,
                      R: torch.Tensor | None = None, stream=None):
     """``pfm_residual_noalloc``: residual and potential without a handle and

@@ -103,6 +103,13 @@ struct pfm_handle {
   // staging for the host-buffer entry point
   void* stage_in = nullptr;
   void* stage_out = nullptr;
+  // pinned host slots for Hessenberg columns and scalars
+  double* hpin = nullptr;
+  // captured V-cycle (valid until the next linearisation)
+  bool use_graphs = false;
+  cudaGraphExec_t vgraph = nullptr;
+  int vgraph_prec = -1;
+  struct { int nu_pre, nu_post, type; double omega, lo, hi; } vgraph_cfg{};
   // device timing of hot phases (pairs of events per timed launch)
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[PFM_PROF_COUNT];
@@ -397,6 +404,10 @@ pfm_status norm2(pfm_handle* h, const double* x, int64_t n, double* out) {
 
 pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
   cudaStream_t s = h->stream;
+  if (h->vgraph) {  // smoother coefficients change with the eigenvalue estimates
+    cudaGraphExecDestroy(h->vgraph);
+    h->vgraph = nullptr;
+  }
   const size_t nl = h->L.size();
   for (size_t l = 1; l < nl; ++l) {
     launch_inject_state(h->L[l - 1].g, h->L[l].g, h->L[l - 1].U, h->L[l].U, s);
@@ -462,22 +473,34 @@ pfm_status japply_impl(pfm_handle* h, const T* v, T* y) {
 // FGMRES(m), right preconditioned, x0 = 0 (Sec. 3.4 uses GMRES; the flexible
 // variant allows a preconditioner that changes between iterations, here an
 // FP32 V-cycle). Orthogonalisation: classical Gram-Schmidt applied twice.
-pfm_status fgmres_impl(pfm_handle* h, const pfm_solve_opts& o, const double* b, double* x, int* its_out,
-                       double* relres_out) {
+// Written as a resumable state machine so that a batch of problems can be
+// advanced in lockstep: enqueue one iteration on every problem's stream,
+// synchronise once, then finish the iteration of each (Givens rotation,
+// convergence test, next basis vector or update and restart).
+struct Fgm {
+  pfm_solve_opts o{};
+  const double* b = nullptr;
+  double* x = nullptr;
+  int m = 0;
+  bool mixed = false;
+  SmoothCfg sc;
+  double beta0 = 0.0, beta = 0.0, tol = 0.0, relres = 1.0;
+  int total = 0, j = 0;
+  bool done = false, converged = false;
+  pfm_status status = PFM_OK;
+  std::vector<double> Hh, cs, sn, g;
+};
+
+pfm_status fgm_alloc(pfm_handle* h, Fgm& F) {
   Level& f = h->L[0];
-  cudaStream_t s = h->stream;
   const int64_t n = ndof(f);
-  const int m = o.restart;
-  const bool mixed = (o.precond == PFM_F32);
-  const SmoothCfg sc = smooth_cfg(&o);
-  if (mixed && h->lin_prec != PFM_F32)
-    return h->fail(PFM_ERR_STATE, "FP32 preconditioner requested but the tangent was built for FP64");
-  if (h->kry_m < m || h->kry_prec != o.precond) {
+  const int m = F.m;
+  if (h->kry_m < m || h->kry_prec != F.o.precond) {
     dfree(h->V);
     if (h->Z) cudaFree(h->Z);
     h->Z = nullptr;
     TRY(dalloc(h, &h->V, size_t(m + 1) * n));
-    if (mixed) {
+    if (F.mixed) {
       float* z = nullptr;
       TRY(dalloc(h, &z, size_t(m) * n));
       h->Z = z;
@@ -487,121 +510,263 @@ pfm_status fgmres_impl(pfm_handle* h, const pfm_solve_opts& o, const double* b, 
       h->Z = z;
     }
     h->kry_m = m;
-    h->kry_prec = o.precond;
+    h->kry_prec = F.o.precond;
   }
-  if (mixed) {
+  if (!h->hpin) {
+    CK(cudaMallocHost(reinterpret_cast<void**>(&h->hpin), sizeof(double) * (2 * (MAX_RESTART + 1) + 2)));
+  }
+  if (F.mixed) {
     TRY(ensure_level_vectors<float>(h));
   } else {
     TRY(ensure_level_vectors<double>(h));
   }
+  return PFM_OK;
+}
+
+// Set up and enqueue ||b|| (read back into the pinned slot hpin[0]).
+pfm_status fgm_begin_enqueue(pfm_handle* h, Fgm& F, const pfm_solve_opts& o, const double* b, double* x) {
+  F = Fgm{};
+  F.o = o;
+  F.b = b;
+  F.x = x;
+  F.m = o.restart;
+  F.mixed = (o.precond == PFM_F32);
+  F.sc = smooth_cfg(&o);
+  if (F.mixed && h->lin_prec != PFM_F32)
+    return h->fail(PFM_ERR_STATE, "FP32 preconditioner requested but the tangent was built for FP64");
+  TRY(fgm_alloc(h, F));
+  F.Hh.assign(size_t(F.m + 1) * F.m, 0.0);
+  F.cs.assign(F.m, 0.0);
+  F.sn.assign(F.m, 0.0);
+  F.g.assign(F.m + 1, 0.0);
+  const int64_t n = ndof(h->L[0]);
+  cudaStream_t s = h->stream;
   CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
-  double beta0 = 0.0;
-  TRY(norm2(h, b, n, &beta0));
-  if (its_out) *its_out = 0;
-  if (relres_out) *relres_out = 0.0;
-  if (!std::isfinite(beta0)) return h->fail(PFM_ERR_NONFINITE, "non-finite right-hand side");
-  if (beta0 == 0.0) return PFM_OK;
-  const double tol = o.lin_rtol * beta0;
   CK(cudaMemcpyAsync(h->rv, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  double beta = beta0;
-  int total = 0;
-  bool converged = false;
-  std::vector<double> Hh((m + 1) * m), cs(m), sn(m), g(m + 1), hcol(2 * (m + 1) + 1);
-  double relres = 1.0;
-  while (total < o.max_lin_it && !converged) {
-    // v_0 = r / beta
-    CK(cudaMemcpyAsync(h->hdev, &beta, sizeof(double), cudaMemcpyHostToDevice, s));
-    launch_scale_copy(n, h->rv, h->hdev, h->V, s);
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
-    int j = 0;
-    int kdone = 0;
-    for (; j < m && total < o.max_lin_it; ++j) {
-      double* vj = h->V + size_t(j) * n;
-      // z_j = M v_j
-      if (mixed) {
-        float* zj = static_cast<float*>(h->Z) + size_t(j) * n;
-        Level& fl = h->L[0];
-        launch_cast_d2f(n, vj, fl.b32, s);
-        TRY(vcycle_level<float>(h, 0, sc));
-        CK(cudaMemcpyAsync(zj, fl.x32, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
-        launch_cast_f2d(n, zj, h->zd, s);
-      } else {
-        double* zj = static_cast<double*>(h->Z) + size_t(j) * n;
-        Level& fl = h->L[0];
-        CK(cudaMemcpyAsync(fl.b64, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        TRY(vcycle_level<double>(h, 0, sc));
-        CK(cudaMemcpyAsync(zj, fl.x64, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(h->zd, zj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-      }
-      // w = J z_j (FP64 outer operator)
-      TRY(japply_impl<double>(h, h->zd, h->wv));
-      // classical Gram-Schmidt, twice
-      double* h1 = h->hdev;
-      double* h2 = h->hdev + (m + 1);
-      double* hn = h->hdev + 2 * (m + 1);
-      launch_mdot(n, j + 1, h->V, n, h->wv, h->partial, h1, s);
-      launch_maxpy(n, j + 1, h->V, n, h1, h->wv, s);
-      launch_mdot(n, j + 1, h->V, n, h->wv, h->partial, h2, s);
-      launch_maxpy(n, j + 1, h->V, n, h2, h->wv, s);
-      launch_mdot(n, 1, h->wv, 0, h->wv, h->partial, hn, s);
-      CKL();
-      CK(cudaMemcpyAsync(hcol.data(), h->hdev, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      ++total;
-      kdone = j + 1;
-      double hnorm = std::sqrt(hcol[2 * (m + 1)]);
-      if (!std::isfinite(hnorm)) return h->fail(PFM_ERR_NONFINITE, "non-finite Krylov vector");
-      for (int i = 0; i <= j; ++i) Hh[i * m + j] = hcol[i] + hcol[(m + 1) + i];
-      Hh[(j + 1) * m + j] = hnorm;
-      // apply previous Givens rotations, then a new one to zero H[j+1][j]
-      for (int i = 0; i < j; ++i) {
-        double a = Hh[i * m + j], bb = Hh[(i + 1) * m + j];
-        Hh[i * m + j] = cs[i] * a + sn[i] * bb;
-        Hh[(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
-      }
-      double a = Hh[j * m + j], bb = Hh[(j + 1) * m + j];
-      double rr = std::hypot(a, bb);
-      if (rr == 0.0) return h->fail(PFM_ERR_BREAKDOWN, "zero Hessenberg column");
-      cs[j] = a / rr;
-      sn[j] = bb / rr;
-      Hh[j * m + j] = rr;
-      Hh[(j + 1) * m + j] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      relres = std::fabs(g[j + 1]) / beta0;
-      if (std::fabs(g[j + 1]) <= tol) { converged = true; break; }
-      if (hnorm <= 1e-300) break;  // happy breakdown: exact solution in the space
-      if (j + 1 < m) {
-        CK(cudaMemcpyAsync(h->hdev + 2 * (m + 1), &hnorm, sizeof(double), cudaMemcpyHostToDevice, s));
-        launch_scale_copy(n, h->wv, h->hdev + 2 * (m + 1), h->V + size_t(j + 1) * n, s);
-      }
-    }
-    // y = R^-1 g (back substitution), x += Z y
-    std::vector<double> y(kdone, 0.0);
-    for (int i = kdone - 1; i >= 0; --i) {
-      double acc = g[i];
-      for (int k = i + 1; k < kdone; ++k) acc -= Hh[i * m + k] * y[k];
-      y[i] = acc / Hh[i * m + i];
-    }
-    CK(cudaMemcpyAsync(h->hdev, y.data(), sizeof(double) * kdone, cudaMemcpyHostToDevice, s));
-    if (mixed)
-      launch_gemv_add<float>(n, kdone, static_cast<float*>(h->Z), n, h->hdev, x, s);
-    else
-      launch_gemv_add<double>(n, kdone, static_cast<double*>(h->Z), n, h->hdev, x, s);
-    CKL();
-    if (converged) break;
-    // restart from the true residual r = b - J x
-    TRY(japply_impl<double>(h, x, h->wv));
-    launch_sub<double>(n, b, h->wv, h->rv, s);
-    TRY(norm2(h, h->rv, n, &beta));
-    relres = beta / beta0;
-    if (beta <= tol) { converged = true; break; }
+  launch_mdot(n, 1, b, 0, b, h->partial, h->hdev, s);
+  CKL();
+  CK(cudaMemcpyAsync(h->hpin, h->hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  return PFM_OK;
+}
+
+pfm_status fgm_start_cycle(pfm_handle* h, Fgm& F) {
+  const int64_t n = ndof(h->L[0]);
+  cudaStream_t s = h->stream;
+  h->hpin[2 * (MAX_RESTART + 1) + 1] = F.beta;
+  CK(cudaMemcpyAsync(h->hdev, &h->hpin[2 * (MAX_RESTART + 1) + 1], sizeof(double), cudaMemcpyHostToDevice, s));
+  launch_scale_copy(n, h->rv, h->hdev, h->V, s);
+  CKL();
+  std::fill(F.g.begin(), F.g.end(), 0.0);
+  F.g[0] = F.beta;
+  F.j = 0;
+  return PFM_OK;
+}
+
+// After the ||b|| copy has landed.
+pfm_status fgm_begin_finish(pfm_handle* h, Fgm& F) {
+  F.beta0 = std::sqrt(h->hpin[0]);
+  if (!std::isfinite(F.beta0)) {
+    F.done = true;
+    return F.status = h->fail(PFM_ERR_NONFINITE, "non-finite right-hand side");
   }
-  if (its_out) *its_out = total;
-  if (relres_out) *relres_out = relres;
-  if (!converged)
-    return h->fail(PFM_ERR_NOT_CONVERGED, "FGMRES reached max_lin_it at relative residual " + std::to_string(relres));
+  if (F.beta0 == 0.0) {
+    F.done = F.converged = true;
+    F.relres = 0.0;
+    return PFM_OK;
+  }
+  F.tol = F.o.lin_rtol * F.beta0;
+  F.beta = F.beta0;
+  return fgm_start_cycle(h, F);
+}
+
+template <typename T>
+pfm_status capture_vcycle(pfm_handle* h, const SmoothCfg& sc);
+
+// z_j = M v_j, w = J z_j, two Gram-Schmidt passes and ||w||^2, with the
+// Hessenberg column copied to the pinned host slots (no synchronisation).
+pfm_status fgm_enqueue(pfm_handle* h, Fgm& F) {
+  Level& fl = h->L[0];
+  cudaStream_t s = h->stream;
+  const int64_t n = ndof(fl);
+  const int m = F.m, j = F.j;
+  double* vj = h->V + size_t(j) * n;
+  if (F.mixed) {
+    float* zj = static_cast<float*>(h->Z) + size_t(j) * n;
+    launch_cast_d2f(n, vj, fl.b32, s);
+    if (h->use_graphs) {
+      TRY(capture_vcycle<float>(h, F.sc));
+      CK(cudaGraphLaunch(h->vgraph, s));
+    } else {
+      TRY(vcycle_level<float>(h, 0, F.sc));
+    }
+    CK(cudaMemcpyAsync(zj, fl.x32, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+    launch_cast_f2d(n, zj, h->zd, s);
+  } else {
+    double* zj = static_cast<double*>(h->Z) + size_t(j) * n;
+    CK(cudaMemcpyAsync(fl.b64, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (h->use_graphs) {
+      TRY(capture_vcycle<double>(h, F.sc));
+      CK(cudaGraphLaunch(h->vgraph, s));
+    } else {
+      TRY(vcycle_level<double>(h, 0, F.sc));
+    }
+    CK(cudaMemcpyAsync(zj, fl.x64, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(h->zd, zj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  }
+  TRY(japply_impl<double>(h, h->zd, h->wv));
+  double* h1 = h->hdev;
+  double* h2 = h->hdev + (m + 1);
+  double* hn = h->hdev + 2 * (m + 1);
+  launch_mdot(n, j + 1, h->V, n, h->wv, h->partial, h1, s);
+  launch_maxpy(n, j + 1, h->V, n, h1, h->wv, s);
+  launch_mdot(n, j + 1, h->V, n, h->wv, h->partial, h2, s);
+  launch_maxpy(n, j + 1, h->V, n, h2, h->wv, s);
+  launch_mdot(n, 1, h->wv, 0, h->wv, h->partial, hn, s);
+  CKL();
+  CK(cudaMemcpyAsync(h->hpin, h->hdev, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, s));
+  return PFM_OK;
+}
+
+// x += Z y with y = R^-1 g (back substitution on the host).
+pfm_status fgm_update(pfm_handle* h, Fgm& F, int kdone) {
+  if (kdone == 0) return PFM_OK;
+  const int m = F.m;
+  const int64_t n = ndof(h->L[0]);
+  cudaStream_t s = h->stream;
+  std::vector<double> y(kdone, 0.0);
+  for (int i = kdone - 1; i >= 0; --i) {
+    double acc = F.g[i];
+    for (int k = i + 1; k < kdone; ++k) acc -= F.Hh[i * m + k] * y[k];
+    y[i] = acc / F.Hh[i * m + i];
+  }
+  double* ypin = h->hpin + (m + 1);  // the h2 slots are free at this point
+  for (int i = 0; i < kdone; ++i) ypin[i] = y[i];
+  CK(cudaMemcpyAsync(h->hdev, ypin, sizeof(double) * kdone, cudaMemcpyHostToDevice, s));
+  if (F.mixed)
+    launch_gemv_add<float>(n, kdone, static_cast<float*>(h->Z), n, h->hdev, F.x, s);
+  else
+    launch_gemv_add<double>(n, kdone, static_cast<double*>(h->Z), n, h->hdev, F.x, s);
+  CKL();
+  return PFM_OK;
+}
+
+// After the column copy of fgm_enqueue has landed.
+pfm_status fgm_finish(pfm_handle* h, Fgm& F) {
+  const int m = F.m, j = F.j;
+  const int64_t n = ndof(h->L[0]);
+  cudaStream_t s = h->stream;
+  const double* hcol = h->hpin;
+  ++F.total;
+  const double hnorm = std::sqrt(hcol[2 * (m + 1)]);
+  if (!std::isfinite(hnorm)) {
+    F.done = true;
+    return F.status = h->fail(PFM_ERR_NONFINITE, "non-finite Krylov vector");
+  }
+  for (int i = 0; i <= j; ++i) F.Hh[i * m + j] = hcol[i] + hcol[(m + 1) + i];
+  F.Hh[(j + 1) * m + j] = hnorm;
+  for (int i = 0; i < j; ++i) {
+    const double a = F.Hh[i * m + j], bb = F.Hh[(i + 1) * m + j];
+    F.Hh[i * m + j] = F.cs[i] * a + F.sn[i] * bb;
+    F.Hh[(i + 1) * m + j] = -F.sn[i] * a + F.cs[i] * bb;
+  }
+  const double a = F.Hh[j * m + j], bb = F.Hh[(j + 1) * m + j];
+  const double rr = std::hypot(a, bb);
+  if (rr == 0.0) {
+    F.done = true;
+    return F.status = h->fail(PFM_ERR_BREAKDOWN, "zero Hessenberg column");
+  }
+  F.cs[j] = a / rr;
+  F.sn[j] = bb / rr;
+  F.Hh[j * m + j] = rr;
+  F.Hh[(j + 1) * m + j] = 0.0;
+  F.g[j + 1] = -F.sn[j] * F.g[j];
+  F.g[j] = F.cs[j] * F.g[j];
+  F.relres = std::fabs(F.g[j + 1]) / F.beta0;
+  const bool conv = std::fabs(F.g[j + 1]) <= F.tol;
+  const bool happy = hnorm <= 1e-300;
+  if (!conv && !happy && j + 1 < m && F.total < F.o.max_lin_it) {
+    // next basis vector v_{j+1} = w / h_{j+1,j}
+    h->hpin[2 * (MAX_RESTART + 1) + 1] = hnorm;
+    CK(cudaMemcpyAsync(h->hdev + 2 * (m + 1), &h->hpin[2 * (MAX_RESTART + 1) + 1], sizeof(double),
+                       cudaMemcpyHostToDevice, s));
+    launch_scale_copy(n, h->wv, h->hdev + 2 * (m + 1), h->V + size_t(j + 1) * n, s);
+    CKL();
+    F.j = j + 1;
+    return PFM_OK;
+  }
+  TRY(fgm_update(h, F, j + 1));
+  if (conv) {
+    F.done = F.converged = true;
+    return PFM_OK;
+  }
+  // restart from the true residual r = b - J x
+  TRY(japply_impl<double>(h, F.x, h->wv));
+  launch_sub<double>(n, F.b, h->wv, h->rv, s);
+  TRY(norm2(h, h->rv, n, &F.beta));
+  F.relres = F.beta / F.beta0;
+  if (F.beta <= F.tol) {
+    F.done = F.converged = true;
+    return PFM_OK;
+  }
+  if (F.total >= F.o.max_lin_it) {
+    F.done = true;
+    return F.status = h->fail(PFM_ERR_NOT_CONVERGED,
+                              "FGMRES reached max_lin_it at relative residual " + std::to_string(F.relres));
+  }
+  return fgm_start_cycle(h, F);
+}
+
+pfm_status fgmres_impl(pfm_handle* h, const pfm_solve_opts& o, const double* b, double* x, int* its_out,
+                       double* relres_out) {
+  Fgm F;
+  TRY(fgm_begin_enqueue(h, F, o, b, x));
+  CK(cudaStreamSynchronize(h->stream));
+  pfm_status st = fgm_begin_finish(h, F);
+  while (st == PFM_OK && !F.done) {
+    st = fgm_enqueue(h, F);
+    if (st != PFM_OK) break;
+    CK(cudaStreamSynchronize(h->stream));
+    st = fgm_finish(h, F);
+  }
+  if (its_out) *its_out = F.total;
+  if (relres_out) *relres_out = F.relres;
+  return st;
+}
+
+// Capture the V-cycle on the handle's stream into a CUDA graph (once per
+// linearisation and smoother configuration) so that a batch replays it with
+// one launch per problem and iteration.
+template <typename T>
+pfm_status capture_vcycle(pfm_handle* h, const SmoothCfg& sc) {
+  const int key_prec = sizeof(T) == 4 ? 0 : 1;
+  if (h->vgraph && h->vgraph_prec == key_prec && h->vgraph_cfg.nu_pre == sc.nu_pre &&
+      h->vgraph_cfg.nu_post == sc.nu_post && h->vgraph_cfg.type == sc.type && h->vgraph_cfg.omega == sc.omega &&
+      h->vgraph_cfg.lo == sc.lo && h->vgraph_cfg.hi == sc.hi)
+    return PFM_OK;
+  if (h->vgraph) {
+    cudaGraphExecDestroy(h->vgraph);
+    h->vgraph = nullptr;
+  }
+  const bool prof = h->prof;
+  h->prof = false;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  pfm_status st = vcycle_level<T>(h, 0, sc);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  h->prof = prof;
+  if (st != PFM_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return h->fail(PFM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&h->vgraph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    h->vgraph = nullptr;
+    return h->fail(PFM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  h->vgraph_prec = key_prec;
+  h->vgraph_cfg = {sc.nu_pre, sc.nu_post, sc.type, sc.omega, sc.lo, sc.hi};
   return PFM_OK;
 }
 
@@ -703,6 +868,8 @@ void pfm_destroy(pfm_handle* h) {
   dfree(h->dirval); dfree(h->energy_dev); dfree(h->flag_dev); dfree(h->R); dfree(h->dU); dfree(h->wv);
   dfree(h->rv); dfree(h->zd); dfree(h->partial); dfree(h->hdev); dfree(h->V); dfree(h->Kaug); dfree(h->gjf);
   if (h->Z) cudaFree(h->Z);
+  if (h->vgraph) cudaGraphExecDestroy(h->vgraph);
+  if (h->hpin) cudaFreeHost(h->hpin);
   if (h->stage_in) cudaFree(h->stage_in);
   if (h->stage_out) cudaFree(h->stage_out);
   delete h;
@@ -1024,5 +1191,223 @@ pfm_status pfm_profile_get(pfm_handle* h, int id, int64_t* launches, double* tot
 }
 
 int64_t pfm_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"
+
+// ============================================================================
+// Batch of independent problems (uneven sizes), advanced in lockstep.
+
+struct pfm_batch {
+  std::vector<pfm_handle*> hs;
+  std::vector<cudaStream_t> streams;
+  std::string err;
+  pfm_status fail(pfm_status st, const std::string& m) {
+    err = m;
+    return st;
+  }
+};
+
+namespace {
+std::string g_batch_create_error;
+
+// Enqueue the residual of every listed problem and ||R||^2 into its pinned
+// slot hpin[0]; synchronise all their streams once; return the norms.
+pfm_status batch_residual_norms(pfm_batch* b, const std::vector<int>& ids, std::vector<double>& res) {
+  for (int p : ids) {
+    pfm_handle* h = b->hs[p];
+    TRY(residual_impl(h, h->R, nullptr));
+    const int64_t n = ndof(h->L[0]);
+    launch_mdot(n, 1, h->R, 0, h->R, h->partial, h->hdev, h->stream);
+    CKL();
+    if (!h->hpin) CK(cudaMallocHost(reinterpret_cast<void**>(&h->hpin), sizeof(double) * (2 * (MAX_RESTART + 1) + 2)));
+    CK(cudaMemcpyAsync(h->hpin, h->hdev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  }
+  for (int p : ids) {
+    pfm_handle* h = b->hs[p];
+    CK(cudaStreamSynchronize(h->stream));
+    res[p] = std::sqrt(h->hpin[0]);
+  }
+  return PFM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+pfm_status pfm_batch_create(pfm_handle* const* handles, int count, pfm_batch** out) {
+  if (!handles || count < 1 || !out) {
+    g_batch_create_error = "null handles or non-positive count";
+    return PFM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  pfm_batch* b = new pfm_batch();
+  for (int p = 0; p < count; ++p) {
+    if (!handles[p]) {
+      g_batch_create_error = "null handle in the batch";
+      delete b;
+      return PFM_ERR_INVALID_ARG;
+    }
+    b->hs.push_back(handles[p]);
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      g_batch_create_error = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+      for (auto x : b->streams) cudaStreamDestroy(x);
+      delete b;
+      return PFM_ERR_CUDA;
+    }
+    b->streams.push_back(st);
+  }
+  *out = b;
+  return PFM_OK;
+}
+
+void pfm_batch_destroy(pfm_batch* b) {
+  if (!b) return;
+  for (auto x : b->streams) cudaStreamDestroy(x);
+  delete b;
+}
+
+const char* pfm_batch_last_error(const pfm_batch* b) { return b ? b->err.c_str() : g_batch_create_error.c_str(); }
+
+pfm_status pfm_batch_newton_solve(pfm_batch* b, const pfm_solve_opts* opts, double* const* U_inout,
+                                  pfm_solve_report* reports) {
+  if (!b) return PFM_ERR_INVALID_ARG;
+  if (!opts || !U_inout || !opts_valid(*opts)) return b->fail(PFM_ERR_INVALID_ARG, "bad options or state arrays");
+  const int N = int(b->hs.size());
+  std::vector<cudaStream_t> saved(N);
+  for (int p = 0; p < N; ++p) {
+    pfm_handle* h = b->hs[p];
+    if (!h->have_state) return b->fail(PFM_ERR_STATE, "problem " + std::to_string(p) + " has no U_n");
+    if (!U_inout[p]) return b->fail(PFM_ERR_INVALID_ARG, "null state of problem " + std::to_string(p));
+    saved[p] = h->stream;
+    h->stream = b->streams[p];
+    h->use_graphs = true;
+  }
+  std::vector<pfm_solve_report> rep(N);
+  std::vector<double> res(N, 0.0);
+  std::vector<int> all(N);
+  pfm_status st = PFM_OK;
+  const double t_start = now_ms();
+  auto restore = [&]() {
+    for (int p = 0; p < N; ++p) {
+      pfm_handle* h = b->hs[p];
+      cudaStreamSynchronize(h->stream);
+      h->use_graphs = false;
+      h->stream = saved[p];
+    }
+  };
+  for (int p = 0; p < N; ++p) {
+    all[p] = p;
+    pfm_handle* h = b->hs[p];
+    Level& f = h->L[0];
+    if (cudaMemcpyAsync(f.U, U_inout[p], sizeof(double) * ndof(f), cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess) {
+      restore();
+      return b->fail(PFM_ERR_CUDA, "state copy failed");
+    }
+    if (h->have_dirval) launch_mask_values(f.nn, f.mask, h->dirval, f.U, h->stream);
+    h->linearized = false;
+  }
+  double t0 = now_ms();
+  st = batch_residual_norms(b, all, res);
+  for (int p = 0; p < N; ++p) {
+    rep[p].res0 = res[p];
+    rep[p].ms_residual += now_ms() - t0;
+  }
+  for (int it = 0; st == PFM_OK && it < opts->max_newton; ++it) {
+    std::vector<int> act;
+    for (int p = 0; p < N; ++p) {
+      if (!std::isfinite(res[p])) {
+        rep[p].status = PFM_ERR_NONFINITE;
+        continue;
+      }
+      if (res[p] == 0.0 || (it > 0 && res[p] <= opts->newton_rtol * rep[p].res0)) continue;
+      act.push_back(p);
+    }
+    if (act.empty()) break;
+    t0 = now_ms();
+    for (int p : act) {
+      st = linearize_impl(b->hs[p], opts->precond);
+      if (st != PFM_OK) {
+        b->err = "problem " + std::to_string(p) + ": " + b->hs[p]->err;
+        break;
+      }
+    }
+    const double ms_lin = now_ms() - t0;
+    if (st != PFM_OK) break;
+    t0 = now_ms();
+    // lockstep FGMRES over the active problems (b = -R kept in R)
+    std::vector<Fgm> F(N);
+    for (int p : act) {
+      pfm_handle* h = b->hs[p];
+      launch_axpy(ndof(h->L[0]), -2.0, h->R, h->R, h->stream);
+      st = fgm_begin_enqueue(h, F[p], *opts, h->R, h->dU);
+      if (st != PFM_OK) break;
+    }
+    if (st != PFM_OK) break;
+    std::vector<int> live;
+    for (int p : act) {
+      pfm_handle* h = b->hs[p];
+      cudaStreamSynchronize(h->stream);
+      st = fgm_begin_finish(h, F[p]);
+      if (st != PFM_OK) break;
+      if (!F[p].done) live.push_back(p);
+    }
+    while (st == PFM_OK && !live.empty()) {
+      for (int p : live)
+        if ((st = fgm_enqueue(b->hs[p], F[p])) != PFM_OK) break;
+      if (st != PFM_OK) break;
+      for (int p : live) cudaStreamSynchronize(b->hs[p]->stream);
+      std::vector<int> next;
+      for (int p : live) {
+        pfm_status fs = fgm_finish(b->hs[p], F[p]);
+        if (fs != PFM_OK && fs != PFM_ERR_NOT_CONVERGED) {
+          st = fs;
+          b->err = "problem " + std::to_string(p) + ": " + b->hs[p]->err;
+          break;
+        }
+        if (!F[p].done) next.push_back(p);
+      }
+      live.swap(next);
+    }
+    const double ms_solve = now_ms() - t0;
+    if (st != PFM_OK) break;
+    for (int p : act) {
+      pfm_handle* h = b->hs[p];
+      rep[p].ms_linearize += ms_lin;
+      rep[p].ms_solve += ms_solve;
+      rep[p].lin_its_total += F[p].total;
+      rep[p].lin_its_last = F[p].total;
+      rep[p].lin_res_final = F[p].relres;
+      if (!F[p].converged) rep[p].status = PFM_ERR_NOT_CONVERGED;
+      launch_axpy(ndof(h->L[0]), 1.0, h->dU, h->L[0].U, h->stream);
+      h->linearized = false;
+      ++rep[p].newton_its;
+    }
+    t0 = now_ms();
+    st = batch_residual_norms(b, act, res);
+    for (int p : act) rep[p].ms_residual += now_ms() - t0;
+  }
+  for (int p = 0; p < N; ++p) {
+    pfm_handle* h = b->hs[p];
+    cudaMemcpyAsync(U_inout[p], h->L[0].U, sizeof(double) * ndof(h->L[0]), cudaMemcpyDeviceToDevice, h->stream);
+    rep[p].res_final = res[p];
+    if (rep[p].status == PFM_OK && opts->max_newton > 1 && !(res[p] <= opts->newton_rtol * rep[p].res0) && res[p] != 0.0)
+      rep[p].status = PFM_ERR_NOT_CONVERGED;
+  }
+  restore();
+  const double total = now_ms() - t_start;
+  for (int p = 0; p < N; ++p) {
+    rep[p].ms_total = total;
+    if (st != PFM_OK && rep[p].status == PFM_OK) rep[p].status = st;
+    if (reports) reports[p] = rep[p];
+  }
+  if (st != PFM_OK) return st;
+  for (int p = 0; p < N; ++p)
+    if (rep[p].status != PFM_OK) {
+      b->err = "problem " + std::to_string(p) + " did not converge";
+      return rep[p].status;
+    }
+  return PFM_OK;
+}
 
 }  // extern "C"

@@ -10,6 +10,11 @@
 // at the 8 points are a tensor product of 1-D 2x2 transforms, applied with
 // three xor-shuffles (1, 2, 4) per axis; the scatter is the transposed
 // transform. A warp holds 4 elements.
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace pfm {
@@ -459,7 +464,7 @@ inline unsigned grid_for(int64_t threads, int block) {
 
 // element blocks a warp prefetches ahead of the one it works on
 #ifndef PFM_JAPPLY_PF
-#define PFM_JAPPLY_PF 1
+#define PFM_JAPPLY_PF 0
 #endif
 constexpr int JAPPLY_PF = PFM_JAPPLY_PF;
 
@@ -479,29 +484,118 @@ void launch_linearize(const Grid& g, const DevParams& P, const double* U, const 
   count_launches(1);
 }
 
-template <typename T>
-void launch_japply(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, const T* v,
-                   T* y, cudaStream_t s) {
-  const int64_t nn = g.nn();
-  k_japply_init<T><<<grid_for(NF * nn, 256) < 4096 ? grid_for(NF * nn, 256) : 4096, 256, 0, s>>>(nn, mask, v, y);
-  count_launches(1);
-  // persistent grid: every SM filled with as many resident blocks as fit
-  static int sms = 0, per_sm[2] = {0, 0};
-  const int ti = sizeof(T) == 4 ? 0 : 1;
+// ---------------------------------------------------------------------------
+// Launch-shape autotuner of the tangent application. A launch shape is the
+// element tile of one CTA (threads/8 elements: 16 or 32) and the number of
+// resident CTAs per SM of the persistent grid. The first application for a
+// (precision, size class = floor(log2 element blocks)) key times every
+// candidate three times with events and keeps the fastest; the choice is
+// cached for the process and, when PFM_AUTOTUNE_FILE names a file, read from
+// and appended to it ("prec class threads ctas_per_sm" lines). No tuning runs
+// while the stream is being captured into a graph (the default shape is used).
+struct JShape {
+  int threads = 256;
+  int per_sm = 2;
+};
+
+std::mutex g_tune_mutex;
+std::map<std::pair<int, int>, JShape> g_tuned;
+bool g_tune_file_read = false;
+
+void tune_file_read() {
+  if (g_tune_file_read) return;
+  g_tune_file_read = true;
+  const char* path = std::getenv("PFM_AUTOTUNE_FILE");
+  if (!path) return;
+  std::FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  int pr, cl, th, ps;
+  while (std::fscanf(f, "%d %d %d %d", &pr, &cl, &th, &ps) == 4)
+    if ((th == 128 || th == 256) && ps >= 1 && ps <= 16) g_tuned[{pr, cl}] = JShape{th, ps};
+  std::fclose(f);
+}
+
+void tune_file_append(int pr, int cl, const JShape& js) {
+  const char* path = std::getenv("PFM_AUTOTUNE_FILE");
+  if (!path) return;
+  std::FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%d %d %d %d\n", pr, cl, js.threads, js.per_sm);
+  std::fclose(f);
+}
+
+int sm_count() {
+  static int sms = 0;
   if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
-  if (per_sm[ti] == 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[ti], k_japply<T, JAPPLY_PF>, 256, 0);
-    if (per_sm[ti] < 1) per_sm[ti] = 1;
-  }
-  const int64_t need = (g.nblk() * 32 + 255) / 256;
-  const int64_t full = int64_t(sms) * per_sm[ti];
-  const unsigned blocks = unsigned(need < full ? need : full);
-  k_japply<T, JAPPLY_PF><<<blocks, 256, 0, s>>>(g, make_jparams<T>(g, P), H, mask, v, y);
+  return sms;
+}
+
+template <typename T>
+void japply_launch_shape(const Grid& g, JParams<T> jp, const T* H, const dmask_t* mask, const T* v, T* y,
+                         const JShape& js, cudaStream_t s) {
+  const int64_t nn = g.nn();
+  k_japply_init<T><<<grid_for(NF * nn, 256) < 4096 ? grid_for(NF * nn, 256) : 4096, 256, 0, s>>>(nn, mask, v, y);
   count_launches(1);
+  const int64_t need = (g.nblk() * 32 + js.threads - 1) / js.threads;
+  const int64_t full = int64_t(sm_count()) * js.per_sm;
+  const unsigned blocks = unsigned(need < full ? need : full);
+  k_japply<T, JAPPLY_PF><<<blocks, js.threads, 0, s>>>(g, jp, H, mask, v, y);
+  count_launches(1);
+}
+
+template <typename T>
+JShape japply_tune(const Grid& g, const JParams<T>& jp, const T* H, const dmask_t* mask, const T* v, T* y,
+                   cudaStream_t s) {
+  const int pr = sizeof(T) == 4 ? 0 : 1;
+  int cl = 0;
+  for (int64_t b = g.nblk(); b > 1; b >>= 1) ++cl;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  tune_file_read();
+  auto it = g_tuned.find({pr, cl});
+  if (it != g_tuned.end()) return it->second;
+  JShape best;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  if (cap != cudaStreamCaptureStatusNone) return best;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best_ms = 1e30f;
+  for (int threads : {256, 128}) {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_japply<T, JAPPLY_PF>, threads, 0);
+    for (int ps = 1; ps <= occ; ++ps) {
+      JShape js{threads, ps};
+      japply_launch_shape<T>(g, jp, H, mask, v, y, js, s);  // warm
+      cudaEventRecord(a, s);
+      for (int r = 0; r < 3; ++r) japply_launch_shape<T>(g, jp, H, mask, v, y, js, s);
+      cudaEventRecord(b, s);
+      cudaEventSynchronize(b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = js;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  g_tuned[{pr, cl}] = best;
+  tune_file_append(pr, cl, best);
+  return best;
+}
+
+template <typename T>
+void launch_japply(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, const T* v,
+                   T* y, cudaStream_t s) {
+  const JParams<T> jp = make_jparams<T>(g, P);
+  const JShape js = japply_tune<T>(g, jp, H, mask, v, y, s);
+  japply_launch_shape<T>(g, jp, H, mask, v, y, js, s);
 }
 
 template <typename T>

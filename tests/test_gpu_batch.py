@@ -1,0 +1,72 @@
+"""Batched solve of independent problems of uneven size (GPU tests): each
+problem's Newton step from the batch equals the same problem solved alone,
+and one batch member matches the oracle's direct solve."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import fe, qp  # noqa: E402
+from paper_2011_08802_gb300 import abi, inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def binding():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_08802_gb300 import binding as b
+    return b
+
+
+def _states():
+    ns, depths = inputs.batch_sizes(count=6, seed=4, lo=6, hi=12)
+    return [inputs.config_indentation(n, seed=1000 + k, step=1, n_steps=1, depth_frac=d)
+            for k, (n, d) in enumerate(zip(ns, depths))]
+
+
+def test_batch_matches_single_solves(binding):
+    sts = _states()
+    opts = abi.default_opts(abi.PFM_F32, max_newton=2, lin_rtol=1e-10, max_lin_it=400)
+    singles = []
+    for st in sts:
+        P = binding.problem_from_state(st)
+        U = torch.from_numpy(st.U.copy()).cuda()
+        P.newton_solve(U, opts, check=False)
+        singles.append(U.cpu().numpy())
+        P.close()
+    probs = [binding.problem_from_state(st) for st in sts]
+    B = binding.Batch(probs)
+    Us = [torch.from_numpy(st.U.copy()).cuda() for st in sts]
+    reps = B.newton_solve(Us, opts, check=False)
+    # the FP32 preconditioner accumulates with atomics, so two runs follow
+    # slightly different Krylov paths; both meet the 1e-10 linear tolerance,
+    # which bounds their difference by about cond(J) * 1e-10
+    for k, st in enumerate(sts):
+        dU_single = singles[k] - st.U
+        dU_batch = Us[k].cpu().numpy() - st.U
+        assert np.linalg.norm(dU_batch - dU_single) <= 1e-6 * np.linalg.norm(dU_single), k
+        assert reps[k].newton_its == 2
+        assert reps[k].lin_res_final <= 1e-10
+    B.close()
+
+
+def test_batch_member_matches_oracle(binding):
+    st = _states()[0]
+    other = inputs.config_indentation(7, seed=9, step=1)
+    mat = qp.material_from(st.material, st.tau)
+    disc = fe.Discretisation(st.mesh)
+    d = fe.qp_derivatives(disc, st, mat, order=2)
+    K = fe.tangent(disc, st, mat, d)
+    R = fe.residual(disc, st, mat, d)
+    dU = fe.newton_correction(K, R)
+    probs = [binding.problem_from_state(st), binding.problem_from_state(other)]
+    B = binding.Batch(probs)
+    Us = [torch.from_numpy(st.U.copy()).cuda(), torch.from_numpy(other.U.copy()).cuda()]
+    reps = B.newton_solve(Us, abi.default_opts(abi.PFM_F32, max_newton=1, lin_rtol=1e-10, max_lin_it=400))
+    x = Us[0].cpu().numpy() - st.U
+    res = np.linalg.norm(K @ x.reshape(-1) + R.reshape(-1)) / np.linalg.norm(R)
+    assert res <= 1e-8, res
+    assert np.linalg.norm(x - dU) <= 1e-6 * np.linalg.norm(dU)
+    assert reps[0].newton_its == 1 and reps[1].newton_its == 1

@@ -47,7 +47,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    p.add_argument("--n", type=int, default=128, help="hexes per cube edge")
+    p.add_argument("--edge", dest="n", type=int, default=128, help="hexes per cube edge")
     p.add_argument("--no-fp64-step", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--sample", type=int, default=5, help="edge of the oracle's element sample")
@@ -205,6 +205,23 @@ def reference_arm(args, rank):
 
 
 # ---------------------------------------------------------------------------
+def reduce_over_ranks(ms_step, ms32, n32, ndofs, dist, device):
+    """Whole-job figures over ranks (each rank solves its own problem): the
+    step time and the per-application time are the maxima over ranks, and the
+    throughput is all ranks' applied DOFs over the slowest rank's total
+    application time. Returns (ms_step, ms per application, GDOF/s)."""
+    import torch
+
+    japply_ms = ms32 / max(n32, 1)
+    if dist is None:
+        return ms_step, japply_ms, ndofs * n32 / (ms32 * 1e-3) / 1e9
+    mx = torch.tensor([ms_step, japply_ms, ms32], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    tot = torch.tensor([float(ndofs) * n32], dtype=torch.float64, device=device)
+    dist.all_reduce(tot)
+    return float(mx[0]), float(mx[1]), float(tot[0]) / (float(mx[2]) * 1e-3) / 1e9
+
+
 def japply_only(args):
     """K FP32 tangent applications on the benchmark state (profiler driver);
     prints the mean device time per application (CUDA events)."""
@@ -342,18 +359,7 @@ def gpu_arm(args, rank, world, dist):
     nres, msres = P.profile_get(abi.PROF_RESIDUAL)
     nvc, msvc = P.profile_get(abi.PROF_VCYCLE)
     P.profile_enable(False)
-    ms_step = total_ms / args.steps
-    japply_ms = ms32 / max(n32, 1)
-    stats = torch.tensor([ms_step, japply_ms, ms32, float(n32)], dtype=torch.float64, device=dev)
-    if dist is not None:
-        mx = stats.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        ms_step, japply_ms = float(mx[0]), float(mx[1])
-        sumd = torch.tensor([float(ndofs * n32)], dtype=torch.float64, device=dev)
-        dist.all_reduce(sumd)
-        value = float(sumd[0]) / (float(mx[2]) * 1e-3) / 1e9
-    else:
-        value = ndofs * n32 / (ms32 * 1e-3) / 1e9
+    ms_step, japply_ms, value = reduce_over_ranks(total_ms / args.steps, ms32, n32, ndofs, dist, dev)
 
     # ---- roofline of the FP32 tangent application -----------------------
     ne = P.n_elems

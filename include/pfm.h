@@ -173,6 +173,14 @@ pfm_status pfm_jacobian_apply(pfm_handle* h, const void* v_dev, void* y_dev, pfm
 pfm_status pfm_jacobian_transpose_apply(pfm_handle* h, const void* v_dev, void* y_dev,
                                         pfm_precision prec);
 
+/* y = J v for an FP32 input v_dev (device float [9][n_nodes]) with an FP64
+ * output y_dev (device double [9][n_nodes]), computed in double-float
+ * arithmetic (pairs of FP32 numbers, about 48 significant bits) from the FP32
+ * Hessian store and its FP32 rounding remainder. This is the outer operator
+ * of the mixed-precision FGMRES, whose Krylov directions are FP32 V-cycle
+ * outputs. Needs pfm_linearize(PFM_F32). */
+pfm_status pfm_jacobian_apply_mixed(pfm_handle* h, const float* v_dev, double* y_dev);
+
 /* pfm_jacobian_apply with HOST arrays: copies v in, applies, copies y out
  * (synchronises). Uses library-owned device buffers. */
 pfm_status pfm_jacobian_apply_host(pfm_handle* h, const void* v_host, void* y_host,

@@ -134,6 +134,7 @@ def lib():
         "pfm_jacobian_apply": (i32, [H, vp, vp, i32]),
         "pfm_jacobian_transpose_apply": (i32, [H, vp, vp, i32]),
         "pfm_jacobian_apply_host": (i32, [H, vp, vp, i32]),
+        "pfm_jacobian_apply_mixed": (i32, [H, vp, vp]),
         "pfm_vcycle": (i32, [H, vp, vp, i32, C.POINTER(SolveOpts)]),
         "pfm_fgmres_solve": (i32, [H, C.POINTER(SolveOpts), vp, vp, C.POINTER(SolveReport)]),
         "pfm_newton_solve": (i32, [H, C.POINTER(SolveOpts), vp, C.POINTER(SolveReport)]),
@@ -165,7 +166,7 @@ def exported_symbols():
         "pfm_version", "pfm_create", "pfm_destroy", "pfm_last_error", "pfm_get_sizes",
         "pfm_set_stream", "pfm_set_params", "pfm_set_dirichlet", "pfm_set_state", "pfm_get_state",
         "pfm_residual", "pfm_linearize", "pfm_jacobian_apply", "pfm_jacobian_transpose_apply",
-        "pfm_jacobian_apply_host", "pfm_vcycle", "pfm_fgmres_solve", "pfm_newton_solve",
+        "pfm_jacobian_apply_host", "pfm_jacobian_apply_mixed", "pfm_vcycle", "pfm_fgmres_solve", "pfm_newton_solve",
         "pfm_qp_eval", "pfm_get_hessians", "pfm_profile_enable", "pfm_profile_get",
         "pfm_launch_count", "pfm_param_grad", "pfm_batch_create", "pfm_batch_destroy",
         "pfm_batch_last_error", "pfm_batch_newton_solve", "pfm_residual_noalloc", "pfm_noalloc_last_error",

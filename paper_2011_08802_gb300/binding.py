@@ -126,6 +126,13 @@ class Problem:
         self._check(self._lib.pfm_jacobian_transpose_apply(self.h, _ptr(v), _ptr(y), _prec(v.dtype)))
         return y
 
+    def jacobian_apply_mixed(self, v: torch.Tensor, y: torch.Tensor | None = None) -> torch.Tensor:
+        """FP32 input, FP64 output, double-float arithmetic (pfm_jacobian_apply_mixed)."""
+        assert v.dtype == torch.float32
+        y = torch.empty(v.shape, dtype=torch.float64, device=v.device) if y is None else y
+        self._check(self._lib.pfm_jacobian_apply_mixed(self.h, _ptr(v), _ptr(y)))
+        return y
+
     def jacobian_apply_host(self, v: np.ndarray | torch.Tensor, y=None):
         if y is None:
             y = torch.empty_like(v) if isinstance(v, torch.Tensor) else np.empty_like(v)

@@ -31,6 +31,7 @@ struct Level {
   dmask_t* mask = nullptr;
   double* H64 = nullptr;
   float* H32 = nullptr;
+  float* H32lo = nullptr;  // finest level, mixed mode: H64 - H32 rounded to FP32
   double* D64 = nullptr;
   float* D32 = nullptr;
   float *x32 = nullptr, *b32 = nullptr, *y32 = nullptr, *r32 = nullptr, *d32 = nullptr;
@@ -424,9 +425,12 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
     const bool need32 = prec == PFM_F32 && !coarsest;
     if (need64) TRY(dalloc(h, &lv.H64, hsz));
     if (need32) TRY(dalloc(h, &lv.H32, hsz));
+    const bool needlo = fine && need32;
+    if (needlo) TRY(dalloc(h, &lv.H32lo, hsz));
     {
       ProfScope ps(h, PFM_PROF_LINEARIZE, fine);
-      launch_linearize(lv.g, h->dp, lv.U, lv.Un, need64 ? lv.H64 : nullptr, need32 ? lv.H32 : nullptr, s);
+      launch_linearize(lv.g, h->dp, lv.U, lv.Un, need64 ? lv.H64 : nullptr, need32 ? lv.H32 : nullptr,
+                       needlo ? lv.H32lo : nullptr, s);
     }
     CKL();
     if (coarsest) continue;
@@ -600,7 +604,13 @@ pfm_status fgm_enqueue(pfm_handle* h, Fgm& F) {
       TRY(vcycle_level<float>(h, 0, F.sc));
     }
     CK(cudaMemcpyAsync(zj, fl.x32, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
-    launch_cast_f2d(n, zj, h->zd, s);
+    // w = J z_j: z_j is exactly FP32, so the FP64-accurate product runs in
+    // double-float arithmetic on the FP32 pipes from the split Hessian store
+    {
+      ProfScope ps(h, PFM_PROF_JAPPLY_F64);
+      launch_japply_df(fl.g, h->dp, fl.H32, fl.H32lo, fl.mask, zj, h->wv, s);
+    }
+    CKL();
   } else {
     double* zj = static_cast<double*>(h->Z) + size_t(j) * n;
     CK(cudaMemcpyAsync(fl.b64, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -613,7 +623,7 @@ pfm_status fgm_enqueue(pfm_handle* h, Fgm& F) {
     CK(cudaMemcpyAsync(zj, fl.x64, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(h->zd, zj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   }
-  TRY(japply_impl<double>(h, h->zd, h->wv));
+  if (!F.mixed) TRY(japply_impl<double>(h, h->zd, h->wv));
   double* h1 = h->hdev;
   double* h2 = h->hdev + (m + 1);
   double* hn = h->hdev + 2 * (m + 1);
@@ -861,7 +871,8 @@ void pfm_destroy(pfm_handle* h) {
   for (int id = 0; id < PFM_PROF_COUNT; ++id)
     for (auto& e : h->prof_ev[id]) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
   for (auto& lv : h->L) {
-    dfree(lv.U); dfree(lv.Un); dfree(lv.mask); dfree(lv.H64); dfree(lv.H32); dfree(lv.D64); dfree(lv.D32);
+    dfree(lv.U); dfree(lv.Un); dfree(lv.mask); dfree(lv.H64); dfree(lv.H32); dfree(lv.H32lo); dfree(lv.D64);
+    dfree(lv.D32);
     dfree(lv.x32); dfree(lv.b32); dfree(lv.y32); dfree(lv.x64); dfree(lv.b64); dfree(lv.y64);
     dfree(lv.r32); dfree(lv.d32); dfree(lv.r64); dfree(lv.d64);
   }
@@ -969,6 +980,20 @@ pfm_status pfm_jacobian_apply(pfm_handle* h, const void* v_dev, void* y_dev, pfm
 // the same product. Dirichlet rows and columns are identity in both.
 pfm_status pfm_jacobian_transpose_apply(pfm_handle* h, const void* v_dev, void* y_dev, pfm_precision prec) {
   return pfm_jacobian_apply(h, v_dev, y_dev, prec);
+}
+
+pfm_status pfm_jacobian_apply_mixed(pfm_handle* h, const float* v_dev, double* y_dev) {
+  TRY(check_ready(h, true));
+  if (!v_dev || !y_dev) return h->fail(PFM_ERR_INVALID_ARG, "null vectors");
+  Level& f = h->L[0];
+  if (h->lin_prec != PFM_F32 || !f.H32 || !f.H32lo)
+    return h->fail(PFM_ERR_STATE, "the mixed product needs a tangent built with pfm_linearize(PFM_F32)");
+  {
+    ProfScope ps(h, PFM_PROF_JAPPLY_F64);
+    launch_japply_df(f.g, h->dp, f.H32, f.H32lo, f.mask, v_dev, y_dev, h->stream);
+  }
+  CKL();
+  return PFM_OK;
 }
 
 pfm_status pfm_jacobian_apply_host(pfm_handle* h, const void* v_host, void* y_host, pfm_precision prec) {

@@ -184,7 +184,8 @@ __global__ void __launch_bounds__(128) k_residual(Grid g, DevParams P, const dou
 
 __global__ void __launch_bounds__(128) k_linearize(Grid g, DevParams P, const double* __restrict__ U,
                                                    const double* __restrict__ Un,
-                                                   double* __restrict__ H64, float* __restrict__ H32) {
+                                                   double* __restrict__ H64, float* __restrict__ H32,
+                                                   float* __restrict__ H32lo) {
   const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t e = tid >> 3;
   const int l8 = int(tid & 7);
@@ -206,6 +207,7 @@ __global__ void __launch_bounds__(128) k_linearize(Grid g, DevParams P, const do
     double h = valid ? Hp[j] : 0.0;
     if (H64) H64[hstore_offset<double>(blk, j, lane)] = h;
     if (H32) H32[hstore_offset<float>(blk, j, lane)] = float(h);
+    if (H32lo) H32lo[hstore_offset<float>(blk, j, lane)] = float(h - double(float(h)));
   }
 }
 
@@ -312,6 +314,180 @@ __global__ void __launch_bounds__(256, PFM_JAPPLY_MINB) k_japply(Grid g, JParams
       T r = q1_scatter(w * sg[9 + k], gf[0], gf[1], gf[2], l8, jp.ihx, jp.ihy, jp.ihz);
       if (valid && !((dm >> (3 + k)) & 1)) atomicAdd(&y[(3 + k) * nn + node], r);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Double-float ("df") arithmetic: a value is an unevaluated sum hi + lo of two
+// FP32 numbers (Dekker 1971, "A floating-point technique for extending the
+// available precision"; Knuth's TwoSum). Only round-to-nearest FP32 adds,
+// multiplies and fused multiply-adds are used (the _rn intrinsics keep the
+// compiler from contracting or reassociating them), giving about 48
+// significant bits: enough for an outer Krylov operator checked to 1e-8.
+struct dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dfl df_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const dfl s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfl df_mulf(dfl a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfl df_of(double x) {
+  const float hi = float(x);
+  return {hi, float(x - double(hi))};
+}
+__device__ __forceinline__ dfl df_shx(dfl v, int m) { return {shx(v.hi, m), shx(v.lo, m)}; }
+
+struct DfConst {
+  dfl ga, gb, ihx, ihy, ihz, w;
+  dfl G[6][6];
+};
+inline dfl df_host(double x) {
+  const float hi = float(x);
+  return {hi, float(x - double(hi))};
+}
+
+__device__ __forceinline__ void q1_gather_df(dfl v, int l8, const DfConst& k, dfl& val, dfl& gx, dfl& gy,
+                                             dfl& gz) {
+  dfl s = df_shx(v, 1);
+  dfl vx = df_add(df_mul(k.gb, v), df_mul(k.ga, s));
+  dfl dx = df_mul((l8 & 1) ? df_sub(v, s) : df_sub(s, v), k.ihx);
+  dfl s1 = df_shx(vx, 2), s2 = df_shx(dx, 2);
+  dfl vxy = df_add(df_mul(k.gb, vx), df_mul(k.ga, s1));
+  dfl vdy = df_mul((l8 & 2) ? df_sub(vx, s1) : df_sub(s1, vx), k.ihy);
+  dfl dxy = df_add(df_mul(k.gb, dx), df_mul(k.ga, s2));
+  dfl t1 = df_shx(vxy, 4), t2 = df_shx(vdy, 4), t3 = df_shx(dxy, 4);
+  val = df_add(df_mul(k.gb, vxy), df_mul(k.ga, t1));
+  gz = df_mul((l8 & 4) ? df_sub(vxy, t1) : df_sub(t1, vxy), k.ihz);
+  gy = df_add(df_mul(k.gb, vdy), df_mul(k.ga, t2));
+  gx = df_add(df_mul(k.gb, dxy), df_mul(k.ga, t3));
+}
+
+__device__ __forceinline__ dfl q1_scatter_df(dfl val, dfl gx, dfl gy, dfl gz, bool has_val, int l8,
+                                             const DfConst& k) {
+  dfl sz = df_shx(gz, 4), sx = df_shx(gx, 4), sy = df_shx(gy, 4);
+  dfl A = df_mul((l8 & 4) ? df_add(gz, sz) : df_neg(df_add(gz, sz)), k.ihz);
+  if (has_val) {
+    dfl sv = df_shx(val, 4);
+    A = df_add(A, df_add(df_mul(k.gb, val), df_mul(k.ga, sv)));
+  }
+  dfl Bx = df_add(df_mul(k.gb, gx), df_mul(k.ga, sx));
+  dfl By = df_add(df_mul(k.gb, gy), df_mul(k.ga, sy));
+  dfl sA = df_shx(A, 2), sBy = df_shx(By, 2), sBx = df_shx(Bx, 2);
+  dfl Cc = df_add(df_add(df_mul(k.gb, A), df_mul(k.ga, sA)),
+                  df_mul((l8 & 2) ? df_add(By, sBy) : df_neg(df_add(By, sBy)), k.ihy));
+  dfl Dx = df_add(df_mul(k.gb, Bx), df_mul(k.ga, sBx));
+  dfl sC = df_shx(Cc, 1), sD = df_shx(Dx, 1);
+  return df_add(df_add(df_mul(k.gb, Cc), df_mul(k.ga, sC)),
+                df_mul((l8 & 1) ? df_add(Dx, sD) : df_neg(df_add(Dx, sD)), k.ihx));
+}
+
+// y += J v with v in FP32 (exact input), the tangent as Hhi + Hlo (two FP32
+// stores of the FP64 Hessians) and double-float arithmetic throughout; the
+// element contributions are added to the FP64 output y (initialised by
+// k_japply_init_df). Same persistent warp mapping as k_japply.
+__global__ void __launch_bounds__(256, 1) k_japply_df(Grid g, DfConst k, const float* __restrict__ Hhi,
+                                                     const float* __restrict__ Hlo,
+                                                     const dmask_t* __restrict__ mask,
+                                                     const float* __restrict__ v, double* __restrict__ y) {
+  const int64_t nblk = g.nblk();
+  const int64_t wg = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int lane = int(threadIdx.x & 31);
+  const int l8 = lane & 7;
+  const int64_t nn = g.nn();
+  for (int64_t blk = wg; blk < nblk; blk += nw) {
+    const int64_t e = blk * 4 + (lane >> 3);
+    const bool valid = e < g.ne();
+    const int64_t node = valid ? elem_node(g, e, l8) : 0;
+    const dmask_t dm = valid ? mask[node] : dmask_t(0x1ff);
+    dfl dz[NZ], ge[18];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float x = ((dm >> i) & 1) ? 0.f : v[i * nn + node];
+      dfl val;
+      q1_gather_df(dfl{x, 0.f}, l8, k, val, dz[3 * i], dz[3 * i + 1], dz[3 * i + 2]);
+    }
+#pragma unroll
+    for (int kk = 0; kk < 6; ++kk) {
+      const float x = ((dm >> (3 + kk)) & 1) ? 0.f : v[(3 + kk) * nn + node];
+      q1_gather_df(dfl{x, 0.f}, l8, k, dz[9 + kk], ge[3 * kk], ge[3 * kk + 1], ge[3 * kk + 2]);
+    }
+    dfl sg[NZ];
+#pragma unroll
+    for (int r = 0; r < NZ; ++r) sg[r] = dfl{0.f, 0.f};
+    const float4* Hh = reinterpret_cast<const float4*>(Hhi) + blk * (NH / 4) * 32 + lane;
+    const float4* Hl = reinterpret_cast<const float4*>(Hlo) + blk * (NH / 4) * 32 + lane;
+#pragma unroll 2
+    for (int j = 0; j < NH / 4; ++j) {
+      float hh[4], hl[4];
+      Vec16<float>::unpack(__ldcs(Hh + j * 32), hh);
+      Vec16<float>::unpack(__ldcs(Hl + j * 32), hl);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int idx = j * 4 + t;
+        const int r = packed_row(idx);
+        const int c = r + (idx - packed_row_start(r));
+        const dfl hv{hh[t], hl[t]};
+        sg[r] = df_add(sg[r], df_mul(hv, dz[c]));
+        if (c != r) sg[c] = df_add(sg[c], df_mul(hv, dz[r]));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      dfl r = q1_scatter_df(dfl{0.f, 0.f}, df_mul(k.w, sg[3 * i]), df_mul(k.w, sg[3 * i + 1]),
+                            df_mul(k.w, sg[3 * i + 2]), false, l8, k);
+      if (valid && !((dm >> i) & 1)) atomicAdd(&y[i * nn + node], double(r.hi) + double(r.lo));
+    }
+#pragma unroll
+    for (int kk = 0; kk < 6; ++kk) {
+      dfl gf[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        dfl s = dfl{0.f, 0.f};
+#pragma unroll
+        for (int l = 0; l < 6; ++l) s = df_add(s, df_mul(k.G[kk][l], ge[3 * l + d]));
+        gf[d] = df_mul(k.w, s);
+      }
+      dfl r = q1_scatter_df(df_mul(k.w, sg[9 + kk]), gf[0], gf[1], gf[2], true, l8, k);
+      if (valid && !((dm >> (3 + kk)) & 1)) atomicAdd(&y[(3 + kk) * nn + node], double(r.hi) + double(r.lo));
+    }
+  }
+}
+
+// y = v at Dirichlet DOFs, 0 elsewhere (FP32 input, FP64 output).
+__global__ void k_japply_init_df(int64_t nn, const dmask_t* __restrict__ mask, const float* __restrict__ v,
+                                 double* __restrict__ y) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < NF * nn;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t node = i % nn;
+    const int f = int(i / nn);
+    y[i] = ((mask[node] >> f) & 1) ? double(v[i]) : 0.0;
   }
 }
 
@@ -478,9 +654,9 @@ void launch_residual(const Grid& g, const DevParams& P, const double* U, const d
 }
 
 void launch_linearize(const Grid& g, const DevParams& P, const double* U, const double* Un,
-                      double* H64, float* H32, cudaStream_t s) {
+                      double* H64, float* H32, float* H32lo, cudaStream_t s) {
   const int64_t threads = g.nblk() * 32;
-  k_linearize<<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, H64, H32);
+  k_linearize<<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo);
   count_launches(1);
 }
 
@@ -596,6 +772,31 @@ void launch_japply(const Grid& g, const DevParams& P, const T* H, const dmask_t*
   const JParams<T> jp = make_jparams<T>(g, P);
   const JShape js = japply_tune<T>(g, jp, H, mask, v, y, s);
   japply_launch_shape<T>(g, jp, H, mask, v, y, js, s);
+}
+
+void launch_japply_df(const Grid& g, const DevParams& P, const float* Hhi, const float* Hlo, const dmask_t* mask,
+                      const float* v, double* y, cudaStream_t s) {
+  DfConst k;
+  k.ga = df_host(GA);
+  k.gb = df_host(GB);
+  k.ihx = df_host(1.0 / g.hx);
+  k.ihy = df_host(1.0 / g.hy);
+  k.ihz = df_host(1.0 / g.hz);
+  k.w = df_host(g.w());
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 6; ++b) k.G[a][b] = df_host(P.G[a][b]);
+  const int64_t nn = g.nn();
+  k_japply_init_df<<<grid_for(NF * nn, 256) < 4096 ? grid_for(NF * nn, 256) : 4096, 256, 0, s>>>(nn, mask, v, y);
+  count_launches(1);
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_japply_df, 256, 0);
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int64_t need = (g.nblk() * 32 + 255) / 256;
+  const int64_t full = int64_t(sm_count()) * per_sm;
+  k_japply_df<<<unsigned(need < full ? need : full), 256, 0, s>>>(g, k, Hhi, Hlo, mask, v, y);
+  count_launches(1);
 }
 
 template <typename T>

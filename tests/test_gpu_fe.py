@@ -105,6 +105,16 @@ def test_jacobian_apply_fp32(ragged):
         assert np.abs(y[f] - yo[f]).max() <= RTOL32 * np.abs(yo[f]).max(), f
 
 
+def test_jacobian_apply_mixed_double_float(ragged):
+    """FP32 input, FP64 output in double-float arithmetic: FP64-class accuracy."""
+    P, K, st = ragged["P"], ragged["K"], ragged["st"]
+    P.linearize(abi.PFM_F32)
+    v = np.random.default_rng(8).standard_normal(st.U.shape).astype(np.float32)
+    y = P.jacobian_apply_mixed(torch.from_numpy(v).cuda()).cpu().numpy()
+    yo = (K @ v.astype(np.float64).reshape(-1)).reshape(v.shape)
+    assert _relerr(y, yo) < 1e-11
+
+
 def test_jacobian_transpose(ragged):
     P, K, st = ragged["P"], ragged["K"], ragged["st"]
     P.linearize(abi.PFM_F64)

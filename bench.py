@@ -256,16 +256,17 @@ def japply_only(args):
 
 
 def batch_measure(args, dev):
-    """64 independent indentation problems, n ~ U{8..24} and depth ~
-    U[0.005, 0.03] L (seeded), one Newton correction each at rtol 1e-8: wall
-    time of one pfm_batch_newton_solve against the same problems solved one
-    after another with pfm_newton_solve."""
+    """64 independent indentation problems, n ~ U{8..24} and final depth ~
+    U[0.005, 0.03] L (seeded), each at the first of 10 load steps of its own
+    ramp, one Newton correction each at rtol 1e-8: wall time of one
+    pfm_batch_newton_solve against the same problems solved one after another
+    with pfm_newton_solve."""
     import torch
 
     from paper_2011_08802_gb300 import abi, binding, inputs
 
     ns, depths = inputs.batch_sizes(count=args.batch_count, seed=4)
-    sts = [inputs.config_indentation(n, seed=1000 + k, step=1, n_steps=1, depth_frac=d)
+    sts = [inputs.config_indentation(n, seed=1000 + k, step=1, n_steps=10, depth_frac=d)
            for k, (n, d) in enumerate(zip(ns, depths))]
     probs = [binding.problem_from_state(st) for st in sts]
     U0 = [torch.from_numpy(st.U).to(dev) for st in sts]

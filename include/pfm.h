@@ -127,6 +127,15 @@ const char* pfm_last_error(const pfm_handle* h);
 /* Sizes of the finest level. */
 pfm_status pfm_get_sizes(const pfm_handle* h, int64_t* n_nodes, int64_t* n_elems, int* n_levels);
 
+/* Multigrid level l (0 = finest): element counts and, after pfm_linearize,
+ * the power-iteration estimate of lambda_max(D^-1 J) used by the Chebyshev
+ * smoother (0 on the coarsest level, which is solved directly). */
+pfm_status pfm_get_level(const pfm_handle* h, int level, int* nx, int* ny, int* nz, double* lambda_max);
+
+/* Power-iteration steps of the smoother's eigenvalue estimate (default 30,
+ * 1..1000); takes effect at the next pfm_linearize. */
+pfm_status pfm_set_power_iterations(pfm_handle* h, int iterations);
+
 /* Set the CUDA stream (a cudaStream_t passed as void*) used by all later calls. */
 pfm_status pfm_set_stream(pfm_handle* h, void* stream);
 

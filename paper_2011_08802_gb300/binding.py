@@ -89,6 +89,15 @@ class Problem:
         self.stream = stream
         self._check(self._lib.pfm_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
 
+    def get_level(self, level: int):
+        """(nx, ny, nz, lambda_max estimate) of multigrid level ``level``."""
+        nx, ny, nz, lam = C.c_int(), C.c_int(), C.c_int(), C.c_double()
+        self._check(self._lib.pfm_get_level(self.h, level, C.byref(nx), C.byref(ny), C.byref(nz), C.byref(lam)))
+        return nx.value, ny.value, nz.value, lam.value
+
+    def set_power_iterations(self, its: int):
+        self._check(self._lib.pfm_set_power_iterations(self.h, its))
+
     def set_params(self, params: abi.Params):
         self._check(self._lib.pfm_set_params(self.h, C.byref(params)))
 

@@ -104,6 +104,7 @@ struct pfm_handle {
   // staging for the host-buffer entry point
   void* stage_in = nullptr;
   void* stage_out = nullptr;
+  int power_its = 30;
   // pinned host slots for Hessenberg columns and scalars
   double* hpin = nullptr;
   // captured V-cycle (valid until the next linearisation)
@@ -327,7 +328,7 @@ pfm_status ensure_level_vectors(pfm_handle* h) {
   return PFM_OK;
 }
 
-// lambda_max(D^-1 J) on level l by 15 steps of the power iteration from a
+// lambda_max(D^-1 J) on level l by power_its steps of the power iteration from a
 // fixed pseudo-random start (normalised on the device; one read at the end).
 template <typename T>
 pfm_status estimate_lambda(pfm_handle* h, size_t l) {
@@ -342,7 +343,7 @@ pfm_status estimate_lambda(pfm_handle* h, size_t l) {
   launch_power_init<T>(lv.nn, lv.mask, x, s);
   launch_dot<T>(n, x, x, h->partial, h->hdev, s);
   launch_scale_inv_sqrt<T>(n, x, h->hdev, x, s);
-  for (int it = 0; it < 15; ++it) {
+  for (int it = 0; it < h->power_its; ++it) {
     launch_japply<T>(lv.g, h->dp, H, lv.mask, x, y, s);
     CK(cudaMemsetAsync(z, 0, sizeof(T) * n, s));
     launch_smooth<T>(lv.nn, D, y, nullptr, T(1), z, s);
@@ -893,6 +894,24 @@ pfm_status pfm_get_sizes(const pfm_handle* h, int64_t* n_nodes, int64_t* n_elems
   if (n_nodes) *n_nodes = h->L[0].nn;
   if (n_elems) *n_elems = h->L[0].ne;
   if (n_levels) *n_levels = int(h->L.size());
+  return PFM_OK;
+}
+
+pfm_status pfm_get_level(const pfm_handle* h, int level, int* nx, int* ny, int* nz, double* lambda_max) {
+  if (!h || level < 0 || level >= int(h->L.size())) return PFM_ERR_INVALID_ARG;
+  const Level& l = h->L[level];
+  if (nx) *nx = l.g.nx;
+  if (ny) *ny = l.g.ny;
+  if (nz) *nz = l.g.nz;
+  if (lambda_max) *lambda_max = l.lam;
+  return PFM_OK;
+}
+
+pfm_status pfm_set_power_iterations(pfm_handle* h, int iterations) {
+  if (!h) return PFM_ERR_INVALID_ARG;
+  if (iterations < 1 || iterations > 1000) return h->fail(PFM_ERR_INVALID_ARG, "power iterations must be in 1..1000");
+  h->power_its = iterations;
+  h->linearized = false;
   return PFM_OK;
 }
 

@@ -22,7 +22,7 @@ def binding():
 
 def _states():
     ns, depths = inputs.batch_sizes(count=6, seed=4, lo=6, hi=12)
-    return [inputs.config_indentation(n, seed=1000 + k, step=1, n_steps=1, depth_frac=d)
+    return [inputs.config_indentation(n, seed=1000 + k, step=1, n_steps=10, depth_frac=d)
             for k, (n, d) in enumerate(zip(ns, depths))]
 
 

@@ -97,9 +97,12 @@ struct pfm_handle {
   pfm_precision kry_prec = PFM_F64;
   double* V = nullptr;
   void* Z = nullptr;
-  // coarse dense operator [K | I] -> [I | K^-1]
+  // coarse dense operator [K | I] reduced by Gauss-Jordan, its inverse, work
   double* Kaug = nullptr;
-  double* gjf = nullptr;
+  double* Kinv = nullptr;
+  unsigned long long* gj_keys = nullptr;
+  int* gj_used = nullptr;
+  int* gj_piv = nullptr;
   int nc_dofs = 0;
   // staging for the host-buffer entry point
   void* stage_in = nullptr;
@@ -301,7 +304,7 @@ pfm_status vcycle_level(pfm_handle* h, size_t l, const SmoothCfg& c) {
   T* x = LvVec<T>::x(lv);
   T* b = LvVec<T>::b(lv);
   if (l + 1 == h->L.size()) {
-    launch_coarse_solve<T>(h->nc_dofs, h->Kaug, b, x, s);
+    launch_coarse_solve<T>(h->nc_dofs, h->Kinv, b, x, s);
     CKL();
     return PFM_OK;
   }
@@ -453,7 +456,7 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
   }
   Level& c = h->L[nl - 1];
   launch_coarse_assemble<double>(c.g, h->dp, c.H64, c.mask, h->Kaug, 2 * h->nc_dofs, s);
-  dense_gauss_jordan_inverse(h->Kaug, h->nc_dofs, h->gjf, h->flag_dev, s);
+  dense_gauss_jordan_inverse(h->Kaug, h->nc_dofs, h->Kinv, h->gj_keys, h->gj_used, h->gj_piv, h->flag_dev, s);
   CKL();
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -857,7 +860,10 @@ pfm_status pfm_create(const pfm_mesh_desc* mesh, const pfm_params* params, pfm_h
   if ((st = dalloc(h, &h->partial, size_t(reduction_blocks(n)) * (MAX_RESTART + 1))) != PFM_OK) return cleanup(st);
   if ((st = dalloc(h, &h->hdev, size_t(3) * (MAX_RESTART + 2))) != PFM_OK) return cleanup(st);
   if ((st = dalloc(h, &h->Kaug, size_t(h->nc_dofs) * 2 * h->nc_dofs)) != PFM_OK) return cleanup(st);
-  if ((st = dalloc(h, &h->gjf, h->nc_dofs)) != PFM_OK) return cleanup(st);
+  if ((st = dalloc(h, &h->Kinv, size_t(h->nc_dofs) * h->nc_dofs)) != PFM_OK) return cleanup(st);
+  if ((st = dalloc(h, &h->gj_keys, size_t(h->nc_dofs) + 1)) != PFM_OK) return cleanup(st);
+  if ((st = dalloc(h, &h->gj_used, h->nc_dofs)) != PFM_OK) return cleanup(st);
+  if ((st = dalloc(h, &h->gj_piv, h->nc_dofs)) != PFM_OK) return cleanup(st);
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     h->err = cudaGetErrorString(e);
@@ -878,7 +884,8 @@ void pfm_destroy(pfm_handle* h) {
     dfree(lv.r32); dfree(lv.d32); dfree(lv.r64); dfree(lv.d64);
   }
   dfree(h->dirval); dfree(h->energy_dev); dfree(h->flag_dev); dfree(h->R); dfree(h->dU); dfree(h->wv);
-  dfree(h->rv); dfree(h->zd); dfree(h->partial); dfree(h->hdev); dfree(h->V); dfree(h->Kaug); dfree(h->gjf);
+  dfree(h->rv); dfree(h->zd); dfree(h->partial); dfree(h->hdev); dfree(h->V); dfree(h->Kaug); dfree(h->Kinv);
+  dfree(h->gj_keys); dfree(h->gj_used); dfree(h->gj_piv);
   if (h->Z) cudaFree(h->Z);
   if (h->vgraph) cudaGraphExecDestroy(h->vgraph);
   if (h->hpin) cudaFreeHost(h->hpin);

@@ -93,7 +93,8 @@ template <typename T>
 void launch_power_init(int64_t nn, const dmask_t* mask, T* x, cudaStream_t s);
 template <typename T>
 void launch_scale_inv_sqrt(int64_t n, const T* y, const double* dot, T* x, cudaStream_t s);
-int dense_gauss_jordan_inverse(double* Maug, int n, double* f, int* singular, cudaStream_t s);
+int dense_gauss_jordan_inverse(double* Maug, int n, double* Ainv, unsigned long long* keys, int* used, int* piv,
+                               int* singular, cudaStream_t s);
 template <typename T>
 void launch_coarse_solve(int n, const double* Ainv, const T* b, T* x, cudaStream_t s);
 

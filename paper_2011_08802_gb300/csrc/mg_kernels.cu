@@ -250,75 +250,73 @@ __global__ void k_coarse_bc(int n, int64_t nn, const dmask_t* __restrict__ mask,
   K[int64_t(r) * ld + n + c] = (r == c) ? 1.0 : 0.0;
 }
 
-// Gauss-Jordan step k on the augmented n x 2n matrix: pivot search over rows
-// k..n-1 of column k, row swap, normalisation of the pivot row, and the
-// multipliers f_i = M[i][k] (f_k = 0).
-__global__ void k_gj_pivot(double* __restrict__ M, int n, int ld, int k, double* __restrict__ f,
-                           int* singular) {
-  __shared__ double sval[1024];
-  __shared__ int sidx[1024];
-  double best = -1.0;
-  int bi = k;
-  for (int r = k + threadIdx.x; r < n; r += blockDim.x) {
-    double v = fabs(M[int64_t(r) * ld + k]);
-    if (v > best) { best = v; bi = r; }
-  }
-  sval[threadIdx.x] = best;
-  sidx[threadIdx.x] = bi;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      double o = sval[threadIdx.x + s];
-      int oi = sidx[threadIdx.x + s];
-      if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
-        sval[threadIdx.x] = o;
-        sidx[threadIdx.x] = oi;
-      }
-    }
-    __syncthreads();
-  }
-  const int p = sidx[0];
-  const double pv = sval[0];
-  if (!(pv > 0.0)) {
-    if (threadIdx.x == 0) *singular = 1;
+// Gauss-Jordan elimination with partial pivoting on the augmented n x 2n
+// matrix [K | I], with the row permutation kept implicit: step k takes the
+// pivot row p chosen by step k-1 (largest |M[i][k]| over rows not yet used as
+// pivots), eliminates column k from every other row (columns > k of the left
+// half and the whole right half; column k itself is never read again), and in
+// the same launch votes the pivot of step k+1 with a 64-bit atomicMax on
+// (|value| as FP32 bits, row). Row p is left unscaled; at the end inverse row
+// k is row piv[k] of the right half divided by M[piv[k]][k].
+__device__ __forceinline__ unsigned long long pivot_key(double v, int row) {
+  return (static_cast<unsigned long long>(__float_as_uint(float(fabs(v)))) << 32) | unsigned(row);
+}
+
+__global__ void k_gj_first_key(const double* __restrict__ M, int n, int ld, unsigned long long* keys) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    atomicMax(&keys[0], pivot_key(M[int64_t(i) * ld], i));
+}
+
+// One block per row i; threads stride over the columns.
+__global__ void __launch_bounds__(256) k_gj_step(double* __restrict__ M, int n, int ld, int k,
+                                                 unsigned long long* __restrict__ keys, int* __restrict__ used,
+                                                 int* __restrict__ piv, int* singular) {
+  const int p = int(keys[k] & 0xffffffffu);
+  const double pk = M[int64_t(p) * ld + k];
+  if (!(fabs(pk) > 0.0)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *singular = 1;
     return;
   }
-  if (p != k)
-    for (int c = threadIdx.x; c < 2 * n; c += blockDim.x) {
-      double t = M[int64_t(k) * ld + c];
-      M[int64_t(k) * ld + c] = M[int64_t(p) * ld + c];
-      M[int64_t(p) * ld + c] = t;
+  if (blockIdx.x == 0 && threadIdx.x == 0) piv[k] = p;
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  if (i == p) {
+    if (threadIdx.x == 0) used[p] = 1;
+    return;
+  }
+  const double f = M[int64_t(i) * ld + k] / pk;
+  const bool candidate = (k + 1 < n) && !used[i];
+  double* Mi = M + int64_t(i) * ld;
+  const double* Mp = M + int64_t(p) * ld;
+  if (f != 0.0) {
+    for (int j = k + 1 + threadIdx.x; j < 2 * n; j += blockDim.x) {
+      const double v = Mi[j] - f * Mp[j];
+      Mi[j] = v;
+      if (j == k + 1 && candidate) atomicMax(&keys[k + 1], pivot_key(v, i));
     }
-  __syncthreads();
-  const double ip = 1.0 / M[int64_t(k) * ld + k];
-  __syncthreads();
-  for (int c = threadIdx.x; c < 2 * n; c += blockDim.x) M[int64_t(k) * ld + c] *= ip;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) f[r] = (r == k) ? 0.0 : M[int64_t(r) * ld + k];
-}
-
-// M[i][j] -= f_i M[k][j] for all rows i != k and columns j >= k.
-__global__ void k_gj_update(double* __restrict__ M, int n, int ld, int k, const double* __restrict__ f,
-                            const int* singular) {
-  if (*singular) return;
-  const int ncol = 2 * n - k;
-  const int64_t total = int64_t(n) * ncol;
-  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
-       t += int64_t(gridDim.x) * blockDim.x) {
-    const int i = int(t / ncol);
-    const int j = k + int(t % ncol);
-    const double fi = f[i];
-    if (fi != 0.0) M[int64_t(i) * ld + j] -= fi * M[int64_t(k) * ld + j];
+  } else if (candidate && threadIdx.x == 0) {
+    atomicMax(&keys[k + 1], pivot_key(Mi[k + 1], i));
   }
 }
 
-// x = Ainv b (Ainv = right half of the reduced augmented matrix, ld = 2n).
+// Ainv[k][c] = M[piv[k]][n + c] / M[piv[k]][k]
+__global__ void k_gj_extract(const double* __restrict__ M, int n, int ld, const int* __restrict__ piv,
+                             double* __restrict__ Ainv) {
+  const int k = blockIdx.x;
+  if (k >= n) return;
+  const int p = piv[k];
+  const double inv = 1.0 / M[int64_t(p) * ld + k];
+  for (int c = threadIdx.x; c < n; c += blockDim.x) Ainv[int64_t(k) * n + c] = M[int64_t(p) * ld + n + c] * inv;
+}
+
+// x = Ainv b (Ainv dense n x n, row-major).
 template <typename T>
-__global__ void k_coarse_solve(int n, const double* __restrict__ Aug, const T* __restrict__ b,
+__global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const T* __restrict__ b,
                                T* __restrict__ x) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n) return;
-  const double* row = Aug + int64_t(warp) * 2 * n + n;
+  const double* row = Ainv + int64_t(warp) * n;
   double s = 0.0;
   for (int c = lane; c < n; c += 32) s += row[c] * double(b[c]);
   for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
@@ -474,22 +472,23 @@ void launch_coarse_assemble(const Grid& g, const DevParams& P, const T* H, const
   count_launches(1);
 }
 
-// Reduce the augmented [K | I] (n x 2n, ld = 2n) to [I | K^-1]; returns the
-// number of kernel launches.
-int dense_gauss_jordan_inverse(double* Maug, int n, double* f, int* singular, cudaStream_t s) {
+// Invert the dense coarse operator from the augmented [K | I] (n x 2n,
+// ld = 2n; overwritten) into Ainv (n x n). work: (n+1) keys, n used flags and
+// n pivot rows. Returns the number of kernel launches.
+int dense_gauss_jordan_inverse(double* Maug, int n, double* Ainv, unsigned long long* keys, int* used, int* piv,
+                               int* singular, cudaStream_t s) {
   const int ld = 2 * n;
-  int launches = 0;
+  cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (n + 1), s);
+  cudaMemsetAsync(used, 0, sizeof(int) * n, s);
+  k_gj_first_key<<<grid_for(n, 256), 256, 0, s>>>(Maug, n, ld, keys);
+  count_launches(1);
   for (int k = 0; k < n; ++k) {
-    k_gj_pivot<<<1, 1024, 0, s>>>(Maug, n, ld, k, f, singular);
+    k_gj_step<<<n, 256, 0, s>>>(Maug, n, ld, k, keys, used, piv, singular);
     count_launches(1);
-    const int64_t total = int64_t(n) * (2 * n - k);
-    unsigned blocks = grid_for(total, 256);
-    if (blocks > 1216) blocks = 1216;
-    k_gj_update<<<blocks, 256, 0, s>>>(Maug, n, ld, k, f, singular);
-    count_launches(1);
-    launches += 2;
   }
-  return launches;
+  k_gj_extract<<<n, 256, 0, s>>>(Maug, n, ld, piv, Ainv);
+  count_launches(1);
+  return n + 2;
 }
 
 template <typename T>

@@ -251,6 +251,20 @@ def japply_only(args):
         hb = nblk * 4 * 8 * 120 * np.dtype(dt).itemsize
         vb = 9 * P.n_nodes * np.dtype(dt).itemsize
         out[name] = {"ms": ms, "GDOF/s": 9 * P.n_nodes / ms / 1e6, "GB/s": (hb + 2 * vb + 2 * P.n_nodes) / ms / 1e6}
+    # outer operator of the mixed solve in double-float arithmetic (FP32 in, FP64 out)
+    v = torch.from_numpy(np.random.default_rng(1).standard_normal(P.shape).astype(np.float32)).cuda()
+    y = torch.empty(P.shape, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        P.jacobian_apply_mixed(v, y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        P.jacobian_apply_mixed(v, y)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    out["df"] = {"ms": ms, "GDOF/s": 9 * P.n_nodes / ms / 1e6}
     print(json.dumps(out), flush=True)
     P.close()
 

@@ -127,6 +127,7 @@ def lib():
         "pfm_set_stream": (i32, [H, vp]),
         "pfm_get_level": (i32, [H, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(dp)]),
         "pfm_set_power_iterations": (i32, [H, i32]),
+        "pfm_set_outer_operator": (i32, [H, i32]),
         "pfm_set_params": (i32, [H, C.POINTER(Params)]),
         "pfm_set_dirichlet": (i32, [H, vp, vp]),
         "pfm_set_state": (i32, [H, vp, vp]),
@@ -166,7 +167,7 @@ def exported_symbols():
     """Names of the entry points declared in include/pfm.h."""
     return [
         "pfm_version", "pfm_create", "pfm_destroy", "pfm_last_error", "pfm_get_sizes",
-        "pfm_set_stream", "pfm_get_level", "pfm_set_power_iterations", "pfm_set_params", "pfm_set_dirichlet", "pfm_set_state", "pfm_get_state",
+        "pfm_set_stream", "pfm_get_level", "pfm_set_power_iterations", "pfm_set_outer_operator", "pfm_set_params", "pfm_set_dirichlet", "pfm_set_state", "pfm_get_state",
         "pfm_residual", "pfm_linearize", "pfm_jacobian_apply", "pfm_jacobian_transpose_apply",
         "pfm_jacobian_apply_host", "pfm_jacobian_apply_mixed", "pfm_vcycle", "pfm_fgmres_solve", "pfm_newton_solve",
         "pfm_qp_eval", "pfm_get_hessians", "pfm_profile_enable", "pfm_profile_get",

@@ -95,6 +95,9 @@ class Problem:
         self._check(self._lib.pfm_get_level(self.h, level, C.byref(nx), C.byref(ny), C.byref(nz), C.byref(lam)))
         return nx.value, ny.value, nz.value, lam.value
 
+    def set_outer_operator(self, double_float: bool):
+        self._check(self._lib.pfm_set_outer_operator(self.h, int(double_float)))
+
     def set_power_iterations(self, its: int):
         self._check(self._lib.pfm_set_power_iterations(self.h, its))
 

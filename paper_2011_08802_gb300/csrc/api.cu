@@ -108,6 +108,7 @@ struct pfm_handle {
   void* stage_in = nullptr;
   void* stage_out = nullptr;
   int power_its = 30;
+  bool outer_df = false;  // outer operator of the mixed solve in double-float arithmetic
   // pinned host slots for Hessenberg columns and scalars
   double* hpin = nullptr;
   // captured V-cycle (valid until the next linearisation)
@@ -433,8 +434,10 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
     if (needlo) TRY(dalloc(h, &lv.H32lo, hsz));
     {
       ProfScope ps(h, PFM_PROF_LINEARIZE, fine);
+      // intermediate levels of an FP32 preconditioner need only FP32 Hessians
+      const bool fp32_compute = !fine && !coarsest && prec == PFM_F32;
       launch_linearize(lv.g, h->dp, lv.U, lv.Un, need64 ? lv.H64 : nullptr, need32 ? lv.H32 : nullptr,
-                       needlo ? lv.H32lo : nullptr, s);
+                       needlo ? lv.H32lo : nullptr, fp32_compute, s);
     }
     CKL();
     if (coarsest) continue;
@@ -608,11 +611,14 @@ pfm_status fgm_enqueue(pfm_handle* h, Fgm& F) {
       TRY(vcycle_level<float>(h, 0, F.sc));
     }
     CK(cudaMemcpyAsync(zj, fl.x32, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
-    // w = J z_j: z_j is exactly FP32, so the FP64-accurate product runs in
-    // double-float arithmetic on the FP32 pipes from the split Hessian store
-    {
+    // w = J z_j with the FP64-accurate operator: either the FP64 kernel or,
+    // since z_j is exactly FP32, the double-float kernel on the FP32 pipes
+    if (h->outer_df) {
       ProfScope ps(h, PFM_PROF_JAPPLY_F64);
       launch_japply_df(fl.g, h->dp, fl.H32, fl.H32lo, fl.mask, zj, h->wv, s);
+    } else {
+      launch_cast_f2d(n, zj, h->zd, s);
+      TRY(japply_impl<double>(h, h->zd, h->wv));
     }
     CKL();
   } else {
@@ -911,6 +917,12 @@ pfm_status pfm_get_level(const pfm_handle* h, int level, int* nx, int* ny, int* 
   if (ny) *ny = l.g.ny;
   if (nz) *nz = l.g.nz;
   if (lambda_max) *lambda_max = l.lam;
+  return PFM_OK;
+}
+
+pfm_status pfm_set_outer_operator(pfm_handle* h, int double_float) {
+  if (!h) return PFM_ERR_INVALID_ARG;
+  h->outer_df = double_float != 0;
   return PFM_OK;
 }
 

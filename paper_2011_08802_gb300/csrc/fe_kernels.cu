@@ -182,6 +182,10 @@ __global__ void __launch_bounds__(128) k_residual(Grid g, DevParams P, const dou
   }
 }
 
+// Gauss-point Hessians of one level, computed in TC (FP64 for the finest and
+// the coarsest level, FP32 for the intermediate levels of an FP32
+// preconditioner) and stored in the requested precisions.
+template <typename TC>
 __global__ void __launch_bounds__(128) k_linearize(Grid g, DevParams P, const double* __restrict__ U,
                                                    const double* __restrict__ Un,
                                                    double* __restrict__ H64, float* __restrict__ H32,
@@ -194,17 +198,17 @@ __global__ void __launch_bounds__(128) k_linearize(Grid g, DevParams P, const do
   const bool valid = e < g.ne();
   const int64_t nn = g.nn();
   const int64_t node = valid ? elem_node(g, e, l8) : 0;
-  const double ihx = 1.0 / g.hx, ihy = 1.0 / g.hy, ihz = 1.0 / g.hz;
-  double F[9], eh[6], ge[18], ehn[6];
-  gather_state<double>(U, nn, node, valid, l8, ihx, ihy, ihz, F, eh, ge);
+  const TC ihx = TC(1.0 / g.hx), ihy = TC(1.0 / g.hy), ihz = TC(1.0 / g.hz);
+  TC F[9], eh[6], ge[18], ehn[6];
+  gather_state<TC>(U, nn, node, valid, l8, ihx, ihy, ihz, F, eh, ge);
 #pragma unroll
-  for (int k = 0; k < 6; ++k) ehn[k] = q1_value(valid ? Un[(3 + k) * nn + node] : 0.0);
-  double W, gr[NZ], Hp[NH];
-  qp_local<double, true>(P, F, eh, ehn, &W, gr, Hp);
+  for (int k = 0; k < 6; ++k) ehn[k] = q1_value(valid ? TC(Un[(3 + k) * nn + node]) : TC(0));
+  TC W, gr[NZ], Hp[NH];
+  qp_local<TC, true>(P, F, eh, ehn, &W, gr, Hp);
   const int64_t blk = tid >> 5;
   const int lane = int(tid & 31);
   for (int j = 0; j < NH; ++j) {
-    double h = valid ? Hp[j] : 0.0;
+    const double h = valid ? double(Hp[j]) : 0.0;
     if (H64) H64[hstore_offset<double>(blk, j, lane)] = h;
     if (H32) H32[hstore_offset<float>(blk, j, lane)] = float(h);
     if (H32lo) H32lo[hstore_offset<float>(blk, j, lane)] = float(h - double(float(h)));
@@ -411,7 +415,10 @@ __device__ __forceinline__ dfl q1_scatter_df(dfl val, dfl gx, dfl gy, dfl gz, bo
 // stores of the FP64 Hessians) and double-float arithmetic throughout; the
 // element contributions are added to the FP64 output y (initialised by
 // k_japply_init_df). Same persistent warp mapping as k_japply.
-__global__ void __launch_bounds__(256, 1) k_japply_df(Grid g, DfConst k, const float* __restrict__ Hhi,
+#ifndef PFM_DF_MINB
+#define PFM_DF_MINB 2
+#endif
+__global__ void __launch_bounds__(256, PFM_DF_MINB) k_japply_df(Grid g, DfConst k, const float* __restrict__ Hhi,
                                                      const float* __restrict__ Hlo,
                                                      const dmask_t* __restrict__ mask,
                                                      const float* __restrict__ v, double* __restrict__ y) {
@@ -654,9 +661,12 @@ void launch_residual(const Grid& g, const DevParams& P, const double* U, const d
 }
 
 void launch_linearize(const Grid& g, const DevParams& P, const double* U, const double* Un,
-                      double* H64, float* H32, float* H32lo, cudaStream_t s) {
+                      double* H64, float* H32, float* H32lo, bool fp32_compute, cudaStream_t s) {
   const int64_t threads = g.nblk() * 32;
-  k_linearize<<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo);
+  if (fp32_compute)
+    k_linearize<float><<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo);
+  else
+    k_linearize<double><<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo);
   count_launches(1);
 }
 

@@ -42,6 +42,10 @@ inline void make_dev_params(const pfm_params& in, DevParams& out) {
     for (int l = 0; l < 6; ++l)
       out.G[k][l] = Ahat[k + 1][l + 1] - Ahat[0][l + 1] - Ahat[k + 1][0] + Ahat[0][0];
   out.eps_eta = in.eps_eta;
+  out.same_L = 1;
+  for (int p = 1; p < NPH; ++p)
+    for (int k = 0; k < 36; ++k)
+      if (in.Lvoigt[p][k] != in.Lvoigt[0][k]) out.same_L = 0;
 }
 
 }  // namespace pfm

@@ -54,6 +54,7 @@ struct DevParams {
   double cobst[NPH][NPH];   // 4 gamma_ij / (pi ell_ij), zero diagonal
   double G[6][6];           // gradient-energy matrix in eta_hat (per direction)
   double eps_eta;           // penalty parameter
+  int same_L;               // 1 when every phase has the same stiffness (then L(eta) = L sum eta)
 };
 
 // Packed index of (r, c), r <= c, in the row-major upper triangle.
@@ -216,6 +217,38 @@ PFM_HD void jacobi_eig3(T a[3][3], T lam[3], T Q[3][3]) {
   lam[0] = a[0][0]; lam[1] = a[1][1]; lam[2] = a[2][2];
 }
 
+
+// Eigen-decomposition used by the point physics: in FP32 directly; in FP64
+// the Jacobi rotations are first run in FP32 (cheap square roots and
+// divisions), the matrix is rotated into that approximate eigenbasis in FP64
+// and FP64 Jacobi sweeps finish it (quadratic convergence from ~1e-7).
+template <typename T>
+PFM_HD void eig_sym3(T a[3][3], T lam[3], T Q[3][3]) {
+  jacobi_eig3(a, lam, Q);
+}
+template <>
+PFM_HD void eig_sym3<double>(double a[3][3], double lam[3], double Q[3][3]) {
+  float af[3][3], lf[3], Qf[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) af[i][j] = float(a[i][j]);
+  jacobi_eig3(af, lf, Qf);
+  double Q0[3][3], b[3][3], Q1[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Q0[i][j] = double(Qf[i][j]);
+  // re-orthonormalise the FP32 eigenvectors in FP64 (modified Gram-Schmidt)
+  for (int c = 0; c < 3; ++c) {
+    for (int pc = 0; pc < c; ++pc) {
+      double d = Q0[0][c] * Q0[0][pc] + Q0[1][c] * Q0[1][pc] + Q0[2][c] * Q0[2][pc];
+      for (int i = 0; i < 3; ++i) Q0[i][c] -= d * Q0[i][pc];
+    }
+    double nrm = sqrt(Q0[0][c] * Q0[0][c] + Q0[1][c] * Q0[1][c] + Q0[2][c] * Q0[2][c]);
+    for (int i = 0; i < 3; ++i) Q0[i][c] /= nrm;
+  }
+  rot_in(Q0, a, b);
+  jacobi_eig3(b, lam, Q1);
+  mm3(Q0, Q1, Q);
+}
+
 // First divided difference of log: (log a - log b)/(a - b), 1/a if a == b.
 template <typename T>
 PFM_HD T dd1_log(T a, T b) {
@@ -281,6 +314,10 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
     eta[0] = T(1) - s;
     etan[0] = T(1) - sn;
   }
+  // sum of the eta_i as the same floating-point sum the per-phase loops form
+  T esum = T(0);
+#pragma unroll
+  for (int p = 0; p < NPH; ++p) esum += eta[p];
   T F[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -310,7 +347,7 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) tmp[i][j] = E[i][j];
-    jacobi_eig3(tmp, lam, Q);
+    eig_sym3(tmp, lam, Q);
   }
   T loglam[3];
 #pragma unroll
@@ -333,18 +370,32 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
   voigt_strain(h, hv);
   T Tv[6] = {0, 0, 0, 0, 0, 0};
   T hLh[NPH];  // h : L_i : h
-#pragma unroll
-  for (int p = 0; p < NPH; ++p) {
+  if (P.same_L) {
     T s = 0;
 #pragma unroll
     for (int I = 0; I < 6; ++I) {
       T li = 0;
 #pragma unroll
-      for (int J = 0; J < 6; ++J) li += T(P.Lv[p][I][J]) * hv[J];
-      Tv[I] += eta[p] * li;
+      for (int J = 0; J < 6; ++J) li += T(P.Lv[0][I][J]) * hv[J];
+      Tv[I] = esum * li;
       s += hv[I] * li;
     }
-    hLh[p] = s;
+#pragma unroll
+    for (int p = 0; p < NPH; ++p) hLh[p] = s;
+  } else {
+#pragma unroll
+    for (int p = 0; p < NPH; ++p) {
+      T s = 0;
+#pragma unroll
+      for (int I = 0; I < 6; ++I) {
+        T li = 0;
+#pragma unroll
+        for (int J = 0; J < 6; ++J) li += T(P.Lv[p][I][J]) * hv[J];
+        Tv[I] += eta[p] * li;
+        s += hv[I] * li;
+      }
+      hLh[p] = s;
+    }
   }
   T hT = 0;
 #pragma unroll
@@ -480,15 +531,22 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
         Nv[I][B] = (B < 3) ? cI * Q[i][a] * Q[j][a] : cI * T(0.5) * (Q[i][a] * Q[j][b] + Q[i][b] * Q[j][a]);
       }
     }
+    T Le[6][6];  // L(eta) = sum_p eta_p L_p
+    for (int I = 0; I < 6; ++I)
+      for (int J = 0; J < 6; ++J) {
+        T lij = 0;
+        if (P.same_L) {
+          lij = T(P.Lv[0][I][J]) * esum;
+        } else {
+          for (int p = 0; p < NPH; ++p) lij += eta[p] * T(P.Lv[p][I][J]);
+        }
+        Le[I][J] = lij;
+      }
     T LN[6][6];
     for (int I = 0; I < 6; ++I)
       for (int B = 0; B < 6; ++B) {
         T s = 0;
-        for (int J = 0; J < 6; ++J) {
-          T lij = 0;
-          for (int p = 0; p < NPH; ++p) lij += eta[p] * T(P.Lv[p][I][J]);
-          s += lij * Nv[J][B];
-        }
+        for (int J = 0; J < 6; ++J) s += Le[I][J] * Nv[J][B];
         LN[I][B] = s;
       }
     for (int A_ = 0; A_ < 6; ++A_)
@@ -509,6 +567,10 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
   // per-phase (L_i : h) rotated, for the eta-dependence of L
   T LhT[NPH][6];
   for (int p = 0; p < NPH; ++p) {
+    if (P.same_L && p > 0) {
+      for (int v = 0; v < 6; ++v) LhT[p][v] = LhT[0][v];
+      continue;
+    }
     T lv[6], lm[3][3], lr[3][3];
     for (int I = 0; I < 6; ++I) {
       T s = 0;

@@ -232,6 +232,7 @@ struct JParams {
   T w, ihx, ihy, ihz;
 };
 
+// ---- BEGIN tangent application kernel
 // Asynchronous bulk prefetch of a contiguous global range into L2 (the
 // bulk-copy engine; no registers or shared memory involved). Address 16-byte
 // aligned, size a multiple of 16 bytes.
@@ -321,6 +322,8 @@ __global__ void __launch_bounds__(256, PFM_JAPPLY_MINB) k_japply(Grid g, JParams
   }
 }
 
+// ---- END tangent application kernel
+
 // ---------------------------------------------------------------------------
 // Double-float ("df") arithmetic: a value is an unevaluated sum hi + lo of two
 // FP32 numbers (Dekker 1971, "A floating-point technique for extending the
@@ -354,16 +357,6 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
   e = __fmaf_rn(a.hi, b.lo, e);
   e = __fmaf_rn(a.lo, b.hi, e);
   return df_fast_two_sum(p, e);
-}
-__device__ __forceinline__ dfl df_mulf(dfl a, float b) {
-  const float p = __fmul_rn(a.hi, b);
-  float e = __fmaf_rn(a.hi, b, -p);
-  e = __fmaf_rn(a.lo, b, e);
-  return df_fast_two_sum(p, e);
-}
-__device__ __forceinline__ dfl df_of(double x) {
-  const float hi = float(x);
-  return {hi, float(x - double(hi))};
 }
 __device__ __forceinline__ dfl df_shx(dfl v, int m) { return {shx(v.hi, m), shx(v.lo, m)}; }
 

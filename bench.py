@@ -53,6 +53,7 @@ def parse_args():
     p.add_argument("--sample", type=int, default=5, help="edge of the oracle's element sample")
     p.add_argument("--no-batch", action="store_true", help="skip the 64-problem batch measurement")
     p.add_argument("--batch-count", type=int, default=64)
+    p.add_argument("--no-diff", action="store_true", help="skip the 32^3 differentiation measurement")
     p.add_argument("--mode", default="newton", choices=["newton", "japply"],
                    help="japply: only K FP32 tangent applications (for profiler captures)")
     return p.parse_args()
@@ -330,6 +331,43 @@ def batch_measure(args, dev):
             "all_ok": all(r.status == 0 for r in reps)}
 
 
+def diff_measure(dev):
+    """Differentiation workload: the 32^3 indentation state after five load
+    steps; 16 seeded directions; device time (CUDA events) of 16 forward
+    products J v (FP64), 16 reverse products J^T w and 16 adjoint solves
+    J^T lam = w (FGMRES + FP32 V-cycle, rtol 1e-10) with the parameter
+    gradients -lam . dR/dtheta."""
+    import torch
+
+    from paper_2011_08802_gb300 import abi, autograd, binding, driver, inputs
+
+    st = inputs.config_indentation(32, seed=2, step=1)
+    P = binding.problem_from_state(st)
+    U, reps = driver.load_ramp(P, st, upto=5)
+    mask, _ = inputs.indentation_dirichlet(st.mesh, 5)
+    st5 = inputs.State(st.mesh, U.cpu().numpy(), U.cpu().numpy(), mask, st.tau, st.material)
+    V = [torch.from_numpy(v).to(dev) for v in inputs.direction_vectors(st5, 16, seed=3)]
+    P.linearize(abi.PFM_F32)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    ms_jvp, _ = timed(lambda: [P.jacobian_apply(v) for v in V])
+    ms_vjp, _ = timed(lambda: [P.jacobian_transpose_apply(v) for v in V])
+    ms_adj, res = timed(lambda: [autograd.adjoint_gradient(P, v) for v in V])
+    P.close()
+    return {"workload": "32^3 indentation after 5 load steps, 16 directions",
+            "newton_its_per_step": [r.newton_its for r in reps],
+            "jvp_ms_each": ms_jvp / 16, "vjp_ms_each": ms_vjp / 16, "adjoint_ms_each": ms_adj / 16,
+            "adjoint_fgmres_its_max": max(r[2].lin_its_last for r in res)}
+
+
 def gpu_arm(args, rank, world, dist):
     import numpy as np
     import torch
@@ -436,6 +474,10 @@ def gpu_arm(args, rank, world, dist):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_value = ndofs * world / float(t[0]) / 1e9
 
+    diff = None
+    if not args.no_diff and rank == 0:
+        diff = diff_measure(dev)
+
     batch = None
     if not args.no_batch:
         P.close()
@@ -477,6 +519,7 @@ def gpu_arm(args, rank, world, dist):
             "clocks": clk,
             "cpu_baseline": cpu,
             "batch": batch,
+            "differentiation": diff,
         }
         print(json.dumps(line), flush=True)
     if P is not None:

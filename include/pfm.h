@@ -136,9 +136,10 @@ pfm_status pfm_get_level(const pfm_handle* h, int level, int* nx, int* ny, int* 
  * 1..1000); takes effect at the next pfm_linearize. */
 pfm_status pfm_set_power_iterations(pfm_handle* h, int iterations);
 
-/* Outer operator of the mixed-precision FGMRES: 0 (default) = the FP64
- * kernel of pfm_jacobian_apply, 1 = the double-float kernel of
- * pfm_jacobian_apply_mixed (same accuracy class, FP32 pipes). */
+/* Outer operator of the mixed-precision FGMRES: 1 (default) = the
+ * double-float kernel of pfm_jacobian_apply_mixed (FP64-class accuracy on the
+ * FP32 pipes; 12.8 ms at 128^3 on GB300), 0 = the FP64 kernel of
+ * pfm_jacobian_apply (22 ms). */
 pfm_status pfm_set_outer_operator(pfm_handle* h, int double_float);
 
 /* Set the CUDA stream (a cudaStream_t passed as void*) used by all later calls. */

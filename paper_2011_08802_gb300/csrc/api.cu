@@ -108,7 +108,7 @@ struct pfm_handle {
   void* stage_in = nullptr;
   void* stage_out = nullptr;
   int power_its = 30;
-  bool outer_df = false;  // outer operator of the mixed solve in double-float arithmetic
+  bool outer_df = true;  // outer operator of the mixed solve in double-float arithmetic
   // pinned host slots for Hessenberg columns and scalars
   double* hpin = nullptr;
   // captured V-cycle (valid until the next linearisation)

@@ -409,7 +409,7 @@ __device__ __forceinline__ dfl q1_scatter_df(dfl val, dfl gx, dfl gy, dfl gz, bo
 // element contributions are added to the FP64 output y (initialised by
 // k_japply_init_df). Same persistent warp mapping as k_japply.
 #ifndef PFM_DF_MINB
-#define PFM_DF_MINB 2
+#define PFM_DF_MINB 8
 #endif
 __global__ void __launch_bounds__(256, PFM_DF_MINB) k_japply_df(Grid g, DfConst k, const float* __restrict__ Hhi,
                                                      const float* __restrict__ Hlo,

@@ -95,6 +95,8 @@ typedef struct {
                             [cheb_lo, cheb_hi] * lambda_max(D^-1 J) (lambda_max estimated by
                             power iteration at pfm_linearize); 1: damped point-block Jacobi */
   double cheb_lo, cheb_hi;  /* Chebyshev interval as fractions of lambda_max (0.05, 1.1) */
+  int cycle_gamma;       /* coarse corrections per level: 1 = V-cycle, 2 = W-cycle (<= 0 read as 1) */
+  double nu_growth;      /* smoothing steps on level l: round(nu * nu_growth^l) (<= 0 read as 1) */
 } pfm_solve_opts;
 
 typedef struct {

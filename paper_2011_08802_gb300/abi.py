@@ -45,7 +45,7 @@ class SolveOpts(C.Structure):
                 ("nu_pre", C.c_int), ("nu_post", C.c_int),
                 ("newton_rtol", C.c_double), ("lin_rtol", C.c_double), ("omega", C.c_double),
                 ("precond", C.c_int), ("smoother", C.c_int), ("cheb_lo", C.c_double),
-                ("cheb_hi", C.c_double)]
+                ("cheb_hi", C.c_double), ("cycle_gamma", C.c_int), ("nu_growth", C.c_double)]
 
 
 class SolveReport(C.Structure):
@@ -58,7 +58,7 @@ class SolveReport(C.Structure):
 def default_opts(precond: int = PFM_F32, **kw) -> SolveOpts:
     o = SolveOpts(max_newton=1, restart=30, max_lin_it=300, nu_pre=4, nu_post=4,
                   newton_rtol=1e-8, lin_rtol=1e-8, omega=0.7, precond=precond,
-                  smoother=0, cheb_lo=0.05, cheb_hi=1.1)
+                  smoother=0, cheb_lo=0.05, cheb_hi=1.1, cycle_gamma=1, nu_growth=1.0)
     for k, v in kw.items():
         setattr(o, k, v)
     return o

@@ -115,7 +115,7 @@ struct pfm_handle {
   bool use_graphs = false;
   cudaGraphExec_t vgraph = nullptr;
   int vgraph_prec = -1;
-  struct { int nu_pre, nu_post, type; double omega, lo, hi; } vgraph_cfg{};
+  struct { int nu_pre, nu_post, type; double omega, lo, hi; int gamma; double growth; } vgraph_cfg{};
   // device timing of hot phases (pairs of events per timed launch)
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[PFM_PROF_COUNT];
@@ -223,6 +223,8 @@ void japply_level(pfm_handle* h, size_t l, const T* H, const T* x, T* y) {
 struct SmoothCfg {
   int nu_pre = 4, nu_post = 4, type = 0;
   double omega = 0.7, lo = 0.05, hi = 1.1;
+  int gamma = 1;
+  double growth = 1.0;
 };
 
 SmoothCfg smooth_cfg(const pfm_solve_opts* o) {
@@ -234,6 +236,8 @@ SmoothCfg smooth_cfg(const pfm_solve_opts* o) {
     c.omega = o->omega;
     c.lo = o->cheb_lo;
     c.hi = o->cheb_hi;
+    c.gamma = o->cycle_gamma > 0 ? o->cycle_gamma : 1;
+    c.growth = o->nu_growth > 0 ? o->nu_growth : 1.0;
   }
   return c;
 }
@@ -309,14 +313,24 @@ pfm_status vcycle_level(pfm_handle* h, size_t l, const SmoothCfg& c) {
     CKL();
     return PFM_OK;
   }
-  TRY(smooth<T>(h, l, true, c.nu_pre, true, c));
+  const double gl = std::pow(c.growth, double(l));
+  const int nu_pre = std::max(1, int(std::lround(c.nu_pre * gl)));
+  const int nu_post = c.nu_post > 0 ? std::max(1, int(std::lround(c.nu_post * gl))) : 0;
+  TRY(smooth<T>(h, l, true, nu_pre, true, c));
   Level& cv = h->L[l + 1];
-  launch_restrict<T>(lv.g, cv.g, LvVec<T>::r(lv), cv.mask, LvVec<T>::b(cv), s);
-  CKL();
-  TRY(vcycle_level<T>(h, l + 1, c));
-  launch_prolong_add<T>(lv.g, cv.g, LvVec<T>::x(cv), lv.mask, x, s);
-  CKL();
-  if (c.nu_post > 0) TRY(smooth<T>(h, l, false, c.nu_post, false, c));
+  for (int g = 0; g < c.gamma; ++g) {
+    // coarse correction of the current residual r (recomputed after the first one)
+    if (g > 0) {
+      japply_level<T>(h, l, LvVec<T>::H(lv), x, LvVec<T>::y(lv));
+      launch_sub<T>(ndof(lv), b, LvVec<T>::y(lv), LvVec<T>::r(lv), s);
+    }
+    launch_restrict<T>(lv.g, cv.g, LvVec<T>::r(lv), cv.mask, LvVec<T>::b(cv), s);
+    CKL();
+    TRY(vcycle_level<T>(h, l + 1, c));
+    launch_prolong_add<T>(lv.g, cv.g, LvVec<T>::x(cv), lv.mask, x, s);
+    CKL();
+  }
+  if (nu_post > 0) TRY(smooth<T>(h, l, false, nu_post, false, c));
   return PFM_OK;
 }
 
@@ -761,7 +775,8 @@ pfm_status capture_vcycle(pfm_handle* h, const SmoothCfg& sc) {
   const int key_prec = sizeof(T) == 4 ? 0 : 1;
   if (h->vgraph && h->vgraph_prec == key_prec && h->vgraph_cfg.nu_pre == sc.nu_pre &&
       h->vgraph_cfg.nu_post == sc.nu_post && h->vgraph_cfg.type == sc.type && h->vgraph_cfg.omega == sc.omega &&
-      h->vgraph_cfg.lo == sc.lo && h->vgraph_cfg.hi == sc.hi)
+      h->vgraph_cfg.lo == sc.lo && h->vgraph_cfg.hi == sc.hi && h->vgraph_cfg.gamma == sc.gamma &&
+      h->vgraph_cfg.growth == sc.growth)
     return PFM_OK;
   if (h->vgraph) {
     cudaGraphExecDestroy(h->vgraph);
@@ -786,7 +801,7 @@ pfm_status capture_vcycle(pfm_handle* h, const SmoothCfg& sc) {
     return h->fail(PFM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   }
   h->vgraph_prec = key_prec;
-  h->vgraph_cfg = {sc.nu_pre, sc.nu_post, sc.type, sc.omega, sc.lo, sc.hi};
+  h->vgraph_cfg = {sc.nu_pre, sc.nu_post, sc.type, sc.omega, sc.lo, sc.hi, sc.gamma, sc.growth};
   return PFM_OK;
 }
 

@@ -24,6 +24,9 @@ The matrix logarithm is evaluated by its integral representation
 log C = int_0^1 (C - I) (s C + (1 - s) I)^-1 ds (Higham, Functions of
 Matrices, Thm. 11.1) with Gauss-Legendre quadrature; its derivatives come
 from the jet arithmetic, so no eigen-decomposition is used anywhere here.
+The Pade alternatives of Sec. 2.4 (Eqs. pade11, pade22, pade33) replace
+1/2 log C by the paper's explicit rational matrix formulas, evaluated as
+written (matrix polynomials times the inverse of a matrix polynomial).
 """
 from __future__ import annotations
 
@@ -50,6 +53,7 @@ class Material:
     ell: np.ndarray      # (7,7) interface thickness parameters (symmetric)
     eps_eta: float
     tau: float
+    hencky: str = "log"  # "log" (exact 1/2 log C) or "pade11" / "pade22" / "pade33" (Sec. 2.4)
 
     def obstacle(self) -> np.ndarray:
         """Coefficients 4 gamma_ij / (pi ell_ij) of Eq. IntEnergy."""
@@ -89,9 +93,11 @@ def cubic_stiffness(C11: float, C12: float, C44: float) -> np.ndarray:
     return L
 
 
-def material_from(constants: dict, tau: float, C=None, gamma_scale: float = 1.0) -> Material:
+def material_from(constants: dict, tau: float, C=None, gamma_scale: float = 1.0,
+                  hencky: str = "log") -> Material:
     """Material of Sec. 5.1 from raw constants. ``C`` optionally overrides
-    (C11, C12, C44); ``gamma_scale`` multiplies every interface energy."""
+    (C11, C12, C44); ``gamma_scale`` multiplies every interface energy;
+    ``hencky`` selects the Hencky strain (exact or a Pade approximant)."""
     U = variant_stretches(constants["stretch_alpha"], constants["stretch_beta"],
                           constants["stretch_gamma"])
     C11, C12, C44 = C if C is not None else (constants["C11"], constants["C12"], constants["C44"])
@@ -102,7 +108,7 @@ def material_from(constants: dict, tau: float, C=None, gamma_scale: float = 1.0)
     g[0, :] = g[:, 0] = constants["gamma_am"]
     np.fill_diagonal(g, 0.0)
     ell = np.full((7, 7), constants["ell"])
-    return Material(U, Lt, F0, m, gamma_scale * g, ell, constants["eps_eta"], tau)
+    return Material(U, Lt, F0, m, gamma_scale * g, ell, constants["eps_eta"], tau, hencky)
 
 
 # ---------------------------------------------------------------------------
@@ -123,6 +129,34 @@ def log_spd(C: Jet, n_quad: int = LOG_QUAD_POINTS) -> Jet:
         t = matmul(CmI, inv3(M)) * w
         acc = t if acc is None else acc + t
     return acc
+
+
+HENCKY_MODES = ("log", "pade11", "pade22", "pade33")
+
+
+def hencky_strain(C: Jet, mode: str = "log") -> Jet:
+    """Elastic Hencky strain H^e of C = C^e (Eq. elasticEn, Sec. 2.4):
+    "log": 1/2 log C exactly (integral representation above);
+    "pade11": (C - I)(C + I)^-1                                     (Eq. pade11);
+    "pade22": 3/2 (C^2 - I)(C^2 + 4C + I)^-1                         (Eq. pade22);
+    "pade33": 1/6 (11C^3 + 27C^2 - 27C - 11I)(C^3 + 9C^2 + 9C + I)^-1 (Eq. pade33)."""
+    if mode == "log":
+        return log_spd(C) * 0.5
+    I = np.eye(3)
+    if mode == "pade11":
+        num, den, scale = C - I, C + I, 1.0
+    elif mode == "pade22":
+        C2 = matmul(C, C)
+        num, den, scale = C2 - I, C2 + C * 4.0 + I, 1.5
+    elif mode == "pade33":
+        C2 = matmul(C, C)
+        C3 = matmul(C2, C)
+        num = C3 * 11.0 + C2 * 27.0 - C * 27.0 - I * 11.0
+        den = C3 + C2 * 9.0 + C * 9.0 + I
+        scale = 1.0 / 6.0
+    else:
+        raise ValueError(f"unknown Hencky mode {mode!r}")
+    return matmul(num, inv3(den)) * scale
 
 
 def order_parameters(eta_hat: Jet) -> list:
@@ -191,7 +225,7 @@ def local_energy(F: np.ndarray, eta_hat: np.ndarray, eta_hat_n: np.ndarray, mat:
         Ft = t if Ft is None else Ft + t
     Fe = matmul(Fj, inv3(Ft))
     Ce = matmul(transpose(Fe), Fe)
-    He = log_spd(Ce) * 0.5
+    He = hencky_strain(Ce, mat.hencky)
     LH = None
     for i in range(N_PHASES):
         t = _scalar_jet_times_matrix_jet(eta[i], _contract(mat.Lt[i], He))

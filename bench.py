@@ -54,6 +54,7 @@ def parse_args():
     p.add_argument("--no-batch", action="store_true", help="skip the 64-problem batch measurement")
     p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--no-diff", action="store_true", help="skip the 32^3 differentiation measurement")
+    p.add_argument("--no-hencky", action="store_true", help="skip the Hencky-mode cost comparison")
     p.add_argument("--mode", default="newton", choices=["newton", "japply"],
                    help="japply: only K FP32 tangent applications (for profiler captures)")
     return p.parse_args()
@@ -368,6 +369,43 @@ def diff_measure(dev):
             "adjoint_fgmres_its_max": max(r[2].lin_its_last for r in res)}
 
 
+def hencky_measure(P, st, U0, Un, dev, reps: int = 2):
+    """Cost of each Hencky mode (exact log, Pade (1,1), (2,2), (3,3); Sec. 2.4)
+    on the benchmark state, in the spirit of the paper's Pade-order table:
+    residual and linearisation (all levels, FP32 Hessians for the multigrid)
+    times, and the FGMRES iterations and time of the mixed-precision solve."""
+    import torch
+
+    from paper_2011_08802_gb300 import abi
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    out = {}
+    for mode in ("log", "pade11", "pade22", "pade33"):
+        P.set_params(abi.params_from_material(st.material, st.tau, hencky=mode))
+        P.set_state(U0, Un)
+        ms_res, R = timed(lambda: P.residual())
+        R = R.clone()
+        ms_lin, _ = timed(lambda: P.linearize(abi.PFM_F32))
+        o = abi.default_opts(abi.PFM_F32, max_lin_it=400, lin_rtol=1e-8)
+        ms_sol, (x, rep) = timed(lambda: P.fgmres_solve(-R, o, check=False))
+        out[mode] = {"residual_ms": ms_res, "linearize_ms": ms_lin, "fgmres_its": rep.lin_its_last,
+                     "fgmres_rel_residual": rep.lin_res_final, "converged": rep.lin_res_final <= 1e-8,
+                     "solve_ms": ms_sol}
+    P.set_params(abi.params_from_material(st.material, st.tau))
+    P.set_state(U0, Un)
+    return out
+
+
 def gpu_arm(args, rank, world, dist):
     import numpy as np
     import torch
@@ -456,6 +494,10 @@ def gpu_arm(args, rank, world, dist):
         res64, its64 = solve_check(abi.PFM_F64)
         fp64 = {"s": e0.elapsed_time(e1) / 1e3, "fgmres_its": r64.lin_its_last, "true_rel_residual": res64}
 
+    hencky = None
+    if not args.no_hencky and rank == 0:
+        hencky = hencky_measure(P, st, U0, torch.from_numpy(st.Un).to(dev), dev)
+
     # ---- end to end through the host-buffer entry point -----------------
     P.set_state(U0, torch.from_numpy(st.Un).to(dev))
     P.linearize(abi.PFM_F32)
@@ -520,6 +562,7 @@ def gpu_arm(args, rank, world, dist):
             "cpu_baseline": cpu,
             "batch": batch,
             "differentiation": diff,
+            "hencky_modes": hencky,
         }
         print(json.dumps(line), flush=True)
     if P is not None:

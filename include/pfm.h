@@ -79,6 +79,9 @@ typedef struct {
   double eps_eta;        /* penalty eps_eta (Eq. PenPot) */
   double tau;            /* time increment tau (Sec. 2.3) */
   double gamma_scale;    /* multiplier of every gamma_ij (1 for the paper's data) */
+  int hencky;            /* elastic Hencky strain H^e (Sec. 2.4): 0 = exact 1/2 log C^e;
+                            1, 2, 3 = the Pade (m,m) approximant of that order (Eqs. pade11,
+                            pade22, pade33); other values are rejected (PFM_ERR_INVALID_ARG) */
 } pfm_params;
 
 typedef struct {
@@ -164,6 +167,22 @@ pfm_status pfm_set_state(pfm_handle* h, const double* U_dev, const double* Un_de
 
 /* Copy the handle's current iterate to U_dev (device, double [9][n_nodes]). */
 pfm_status pfm_get_state(pfm_handle* h, double* U_dev);
+
+/* Microstructure diagnostics of Sec. 5.3 of the nodal state U_dev (device,
+ * double [9][n_nodes]; NULL = the handle's current iterate), with
+ * eta_0 = 1 - sum_{k>=1} eta_k at every node:
+ *   Iv_dev[n]       violation index sum_{i=0}^{6} |<eta_i>_-| (penalty study),
+ *   Id_dev[n]       diffuseness index 1 - sum_{i=0}^{6} eta_i^4 (interface study),
+ *   eta_star_dev[n] composite parameter eta_3 - eta_1,
+ *   plane_stats_dev[4 k + {0,1,2,3}] = mean I_v, max I_v, mean I_d, max I_d
+ *                   over the (nx+1)(ny+1) nodes of plane z = k h_z, k = 0..nz.
+ * Every output is device memory owned by the caller and may be NULL (not
+ * computed). Enqueued on the handle's stream; results are bitwise
+ * reproducible for a given grid.
+ * Errors: PFM_ERR_STATE (U_dev NULL and no state set), PFM_ERR_INVALID_ARG
+ * (more than 65535 node planes), PFM_ERR_CUDA. */
+pfm_status pfm_diagnostics(pfm_handle* h, const double* U_dev, double* Iv_dev, double* Id_dev,
+                           double* eta_star_dev, double* plane_stats_dev);
 
 /* Residual R = dPi/dU of the discrete incremental potential (Sec. 3.4,
  * Eq. FinalRes) at the current state, written to R_dev (device, double

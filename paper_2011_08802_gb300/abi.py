@@ -37,7 +37,12 @@ class Params(C.Structure):
     _fields_ = [("Ut", (C.c_double * 9) * 7), ("Lvoigt", (C.c_double * 36) * 7),
                 ("F0", C.c_double * 7), ("mobility", C.c_double * 7),
                 ("gamma", (C.c_double * 7) * 7), ("ell", (C.c_double * 7) * 7),
-                ("eps_eta", C.c_double), ("tau", C.c_double), ("gamma_scale", C.c_double)]
+                ("eps_eta", C.c_double), ("tau", C.c_double), ("gamma_scale", C.c_double),
+                ("hencky", C.c_int)]
+
+
+# Hencky strain modes of pfm_params.hencky (Sec. 2.4)
+HENCKY = {"log": 0, "pade11": 1, "pade22": 2, "pade33": 3}
 
 
 class SolveOpts(C.Structure):
@@ -56,20 +61,21 @@ class SolveReport(C.Structure):
 
 
 def default_opts(precond: int = PFM_F32, **kw) -> SolveOpts:
-    o = SolveOpts(max_newton=1, restart=30, max_lin_it=300, nu_pre=4, nu_post=4,
+    o = SolveOpts(max_newton=1, restart=30, max_lin_it=300, nu_pre=6, nu_post=6,
                   newton_rtol=1e-8, lin_rtol=1e-8, omega=0.7, precond=precond,
-                  smoother=0, cheb_lo=0.05, cheb_hi=1.1, cycle_gamma=1, nu_growth=1.0)
+                  smoother=0, cheb_lo=0.05, cheb_hi=1.1, cycle_gamma=1, nu_growth=1.25)
     for k, v in kw.items():
         setattr(o, k, v)
     return o
 
 
 def params_from_material(constants: dict, tau: float, C_override=None,
-                         gamma_scale: float = 1.0) -> Params:
+                         gamma_scale: float = 1.0, hencky: str = "log") -> Params:
     """Fill the parameter block from the raw constants of Sec. 5.1: variant
     stretches U_1..U_6 from (alpha, beta, gamma), the cubic Voigt stiffness
     from (C11, C12, C44) for every phase, gamma_0i = gamma_am,
-    gamma_ij = gamma_mm, one ell, F_0 = F_a, F_i = F_m, one mobility."""
+    gamma_ij = gamma_mm, one ell, F_0 = F_a, F_i = F_m, one mobility;
+    ``hencky`` names the Hencky strain ("log" or a Pade mode, Sec. 2.4)."""
     al, be, ga = constants["stretch_alpha"], constants["stretch_beta"], constants["stretch_gamma"]
     p, q = 0.5 * (al + ga), 0.5 * (al - ga)
     U = [np.eye(3)]
@@ -100,6 +106,7 @@ def params_from_material(constants: dict, tau: float, C_override=None,
     P.eps_eta = constants["eps_eta"]
     P.tau = tau
     P.gamma_scale = gamma_scale
+    P.hencky = HENCKY[hencky]
     return P
 
 
@@ -133,6 +140,7 @@ def lib():
         "pfm_set_state": (i32, [H, vp, vp]),
         "pfm_get_state": (i32, [H, vp]),
         "pfm_residual": (i32, [H, vp, C.POINTER(dp)]),
+        "pfm_diagnostics": (i32, [H, vp, vp, vp, vp, vp]),
         "pfm_linearize": (i32, [H, i32]),
         "pfm_jacobian_apply": (i32, [H, vp, vp, i32]),
         "pfm_jacobian_transpose_apply": (i32, [H, vp, vp, i32]),
@@ -168,7 +176,7 @@ def exported_symbols():
     return [
         "pfm_version", "pfm_create", "pfm_destroy", "pfm_last_error", "pfm_get_sizes",
         "pfm_set_stream", "pfm_get_level", "pfm_set_power_iterations", "pfm_set_outer_operator", "pfm_set_params", "pfm_set_dirichlet", "pfm_set_state", "pfm_get_state",
-        "pfm_residual", "pfm_linearize", "pfm_jacobian_apply", "pfm_jacobian_transpose_apply",
+        "pfm_residual", "pfm_diagnostics", "pfm_linearize", "pfm_jacobian_apply", "pfm_jacobian_transpose_apply",
         "pfm_jacobian_apply_host", "pfm_jacobian_apply_mixed", "pfm_vcycle", "pfm_fgmres_solve", "pfm_newton_solve",
         "pfm_qp_eval", "pfm_get_hessians", "pfm_profile_enable", "pfm_profile_get",
         "pfm_launch_count", "pfm_param_grad", "pfm_batch_create", "pfm_batch_destroy",

@@ -18,10 +18,10 @@ from . import abi
 from .binding import Problem
 
 
-def params_for(constants: dict, tau: float, theta) -> abi.Params:
+def params_for(constants: dict, tau: float, theta, hencky: str = "log") -> abi.Params:
     """Parameter block with (C11, C12, C44, s_gamma) taken from theta."""
     t = [float(x) for x in theta]
-    return abi.params_from_material(constants, tau, C_override=t[:3], gamma_scale=t[3])
+    return abi.params_from_material(constants, tau, C_override=t[:3], gamma_scale=t[3], hencky=hencky)
 
 
 class PFMResidual(torch.autograd.Function):

@@ -56,6 +56,7 @@ class Problem:
         if st != 0:
             raise PfmError(st, L.pfm_last_error(None).decode())
         self.h = h
+        self.nx, self.ny, self.nz = nx, ny, nz
         nn, ne, nl = C.c_int64(), C.c_int64(), C.c_int()
         self._check(L.pfm_get_sizes(h, C.byref(nn), C.byref(ne), C.byref(nl)))
         self.n_nodes, self.n_elems, self.n_levels = nn.value, ne.value, nl.value
@@ -124,6 +125,23 @@ class Problem:
         e = C.c_double()
         self._check(self._lib.pfm_residual(self.h, _ptr(R), C.byref(e) if energy else None))
         return (R, e.value) if energy else R
+
+    def diagnostics(self, U: torch.Tensor | None = None, per_node: bool = True):
+        """``pfm_diagnostics``: violation index I_v, diffuseness index I_d and
+        eta* = eta_3 - eta_1 per node (if ``per_node``) and the per-plane
+        statistics [nz+1][4] = (mean I_v, max I_v, mean I_d, max I_d) of U
+        (default: the current iterate). Returns a dict of device tensors."""
+        if U is not None:
+            assert U.dtype == torch.float64 and U.shape == self.shape and U.is_contiguous()
+        nn = self.shape[1]
+        out = {}
+        if per_node:
+            for k in ("Iv", "Id", "eta_star"):
+                out[k] = torch.empty(nn, dtype=torch.float64, device="cuda")
+        out["planes"] = torch.empty(self.nz + 1, 4, dtype=torch.float64, device="cuda")
+        self._check(self._lib.pfm_diagnostics(self.h, _ptr(U), _ptr(out.get("Iv")), _ptr(out.get("Id")),
+                                              _ptr(out.get("eta_star")), _ptr(out["planes"])))
+        return out
 
     def linearize(self, precond: int = PFM_F32):
         self._check(self._lib.pfm_linearize(self.h, precond))

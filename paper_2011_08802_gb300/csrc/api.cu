@@ -84,6 +84,7 @@ struct pfm_handle {
   double* dirval = nullptr;
   double* energy_dev = nullptr;
   int* flag_dev = nullptr;
+  double* diag_part = nullptr;  // per-plane partial sums of the diagnostics
   // solver work (finest level, FP64)
   double* R = nullptr;
   double* dU = nullptr;
@@ -826,8 +827,8 @@ pfm_status pfm_create(const pfm_mesh_desc* mesh, const pfm_params* params, pfm_h
   }
   *out = nullptr;
   if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || !(mesh->Lx > 0) || !(mesh->Ly > 0) || !(mesh->Lz > 0) ||
-      mesh->n_levels < 0 || !(params->tau > 0)) {
-    g_create_error = "invalid mesh size, box length, level count or tau";
+      mesh->n_levels < 0 || !(params->tau > 0) || params->hencky < 0 || params->hencky > 3) {
+    g_create_error = "invalid mesh size, box length, level count, tau or Hencky mode";
     return PFM_ERR_INVALID_ARG;
   }
   pfm_handle* h = new pfm_handle();
@@ -873,6 +874,7 @@ pfm_status pfm_create(const pfm_mesh_desc* mesh, const pfm_params* params, pfm_h
   pfm_status st;
   if ((st = dalloc(h, &h->energy_dev, 1)) != PFM_OK) return cleanup(st);
   if ((st = dalloc(h, &h->flag_dev, 1)) != PFM_OK) return cleanup(st);
+  if ((st = dalloc(h, &h->diag_part, size_t(h->L[0].g.nz + 1) * DIAG_MAX_CHUNKS * 4)) != PFM_OK) return cleanup(st);
   if ((st = dalloc(h, &h->R, n)) != PFM_OK) return cleanup(st);
   if ((st = dalloc(h, &h->dU, n)) != PFM_OK) return cleanup(st);
   if ((st = dalloc(h, &h->wv, n)) != PFM_OK) return cleanup(st);
@@ -904,7 +906,7 @@ void pfm_destroy(pfm_handle* h) {
     dfree(lv.x32); dfree(lv.b32); dfree(lv.y32); dfree(lv.x64); dfree(lv.b64); dfree(lv.y64);
     dfree(lv.r32); dfree(lv.d32); dfree(lv.r64); dfree(lv.d64);
   }
-  dfree(h->dirval); dfree(h->energy_dev); dfree(h->flag_dev); dfree(h->R); dfree(h->dU); dfree(h->wv);
+  dfree(h->dirval); dfree(h->energy_dev); dfree(h->flag_dev); dfree(h->diag_part); dfree(h->R); dfree(h->dU); dfree(h->wv);
   dfree(h->rv); dfree(h->zd); dfree(h->partial); dfree(h->hdev); dfree(h->V); dfree(h->Kaug); dfree(h->Kinv);
   dfree(h->gj_keys); dfree(h->gj_used); dfree(h->gj_piv);
   if (h->Z) cudaFree(h->Z);
@@ -958,6 +960,7 @@ pfm_status pfm_set_stream(pfm_handle* h, void* stream) {
 pfm_status pfm_set_params(pfm_handle* h, const pfm_params* params) {
   if (!h || !params) return PFM_ERR_INVALID_ARG;
   if (!(params->tau > 0)) return h->fail(PFM_ERR_INVALID_ARG, "tau must be positive");
+  if (params->hencky < 0 || params->hencky > 3) return h->fail(PFM_ERR_INVALID_ARG, "Hencky mode must be 0..3");
   h->params = *params;
   make_dev_params(*params, h->dp);
   h->linearized = false;
@@ -1004,6 +1007,20 @@ pfm_status pfm_get_state(pfm_handle* h, double* U_dev) {
   TRY(check_ready(h, false));
   if (!U_dev) return h->fail(PFM_ERR_INVALID_ARG, "null output");
   CK(cudaMemcpyAsync(U_dev, h->L[0].U, sizeof(double) * ndof(h->L[0]), cudaMemcpyDeviceToDevice, h->stream));
+  return PFM_OK;
+}
+
+pfm_status pfm_diagnostics(pfm_handle* h, const double* U_dev, double* Iv_dev, double* Id_dev,
+                           double* eta_star_dev, double* plane_stats_dev) {
+  if (!h) return PFM_ERR_INVALID_ARG;
+  if (!U_dev) {
+    TRY(check_ready(h, false));
+    U_dev = h->L[0].U;
+  }
+  const Grid& g = h->L[0].g;
+  if (g.nz + 1 > 65535) return h->fail(PFM_ERR_INVALID_ARG, "more than 65535 node planes");
+  launch_diagnostics(g, U_dev, Iv_dev, Id_dev, eta_star_dev, h->diag_part, plane_stats_dev, h->stream);
+  CKL();
   return PFM_OK;
 }
 

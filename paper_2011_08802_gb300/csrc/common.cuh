@@ -98,6 +98,11 @@ int dense_gauss_jordan_inverse(double* Maug, int n, double* Ainv, unsigned long 
 template <typename T>
 void launch_coarse_solve(int n, const double* Ainv, const T* b, T* x, cudaStream_t s);
 
+// microstructure diagnostics (diag_kernels.cu); partial holds (nz+1)*DIAG_MAX_CHUNKS*4 doubles
+constexpr int DIAG_MAX_CHUNKS = 8;
+void launch_diagnostics(const Grid& g, const double* U, double* Iv, double* Id, double* es, double* partial,
+                        double* stats, cudaStream_t s);
+
 // vector kernels (krylov_kernels.cu)
 template <typename T>
 void launch_fill(int64_t n, T val, T* x, cudaStream_t s);

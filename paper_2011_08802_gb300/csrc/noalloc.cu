@@ -74,8 +74,8 @@ pfm_status pfm_residual_noalloc(const pfm_mesh_desc* mesh, const pfm_params* par
     return PFM_ERR_INVALID_ARG;
   }
   if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || !(mesh->Lx > 0) || !(mesh->Ly > 0) || !(mesh->Lz > 0) ||
-      !(params->tau > 0)) {
-    g_noalloc_error = "invalid mesh size, box length or tau";
+      !(params->tau > 0) || params->hencky < 0 || params->hencky > 3) {
+    g_noalloc_error = "invalid mesh size, box length, tau or Hencky mode";
     return PFM_ERR_INVALID_ARG;
   }
   Grid g{mesh->nx, mesh->ny, mesh->nz, mesh->Lx / mesh->nx, mesh->Ly / mesh->ny, mesh->Lz / mesh->nz};

@@ -42,6 +42,25 @@ inline void make_dev_params(const pfm_params& in, DevParams& out) {
     for (int l = 0; l < 6; ++l)
       out.G[k][l] = Ahat[k + 1][l + 1] - Ahat[0][l + 1] - Ahat[k + 1][0] + Ahat[0][0];
   out.eps_eta = in.eps_eta;
+  // Hencky mode: m-point Gauss-Legendre nodes s_k and weights w_k on [0, 1]
+  out.hencky = in.hencky;
+  for (int k = 0; k < 3; ++k) out.pade_s[k] = out.pade_w[k] = 0.0;
+  if (in.hencky == 1) {
+    out.pade_s[0] = 0.5;
+    out.pade_w[0] = 1.0;
+  } else if (in.hencky == 2) {
+    const double d = std::sqrt(3.0) / 6.0;
+    out.pade_s[0] = 0.5 - d;
+    out.pade_s[1] = 0.5 + d;
+    out.pade_w[0] = out.pade_w[1] = 0.5;
+  } else if (in.hencky == 3) {
+    const double d = 0.5 * std::sqrt(0.6);
+    out.pade_s[0] = 0.5 - d;
+    out.pade_s[1] = 0.5;
+    out.pade_s[2] = 0.5 + d;
+    out.pade_w[0] = out.pade_w[2] = 5.0 / 18.0;
+    out.pade_w[1] = 8.0 / 18.0;
+  }
   out.same_L = 1;
   for (int p = 1; p < NPH; ++p)
     for (int k = 0; k < 36; ++k)

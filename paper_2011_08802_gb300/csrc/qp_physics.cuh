@@ -24,6 +24,17 @@
 // without cancellation, which dd1_log / dd2_log do (log1p quotient; Taylor
 // series of the second divided difference about the mean when all three
 // arguments are close).
+//
+// Pade modes (Sec. 2.4, Eqs. pade11, pade22, pade33). The paper's (m,m)
+// approximant of H^e is the primary matrix function h = 1/2 r_m(C^e), r_m the
+// [m/m] Pade approximant of log about 1. The m-point Gauss-Legendre rule on
+// log x = int_0^1 (x - 1)/(1 + s (x - 1)) ds is that approximant (Dieci,
+// Morini and Papini, 1996): r_m(x) = sum_k w_k (x - 1) p_k(x)^-1 with
+// p_k(x) = 1 + s_k (x - 1). The same spectral route then applies with
+// divided differences that are products of the reciprocals 1/p_k, free of
+// cancellation for any eigenvalue spread:
+// r_m[a,b] = sum_k w_k / (p_k(a) p_k(b)),
+// r_m[a,b,c] = -sum_k w_k s_k / (p_k(a) p_k(b) p_k(c)).
 #pragma once
 
 #ifdef __CUDACC__
@@ -55,6 +66,8 @@ struct DevParams {
   double G[6][6];           // gradient-energy matrix in eta_hat (per direction)
   double eps_eta;           // penalty parameter
   int same_L;               // 1 when every phase has the same stiffness (then L(eta) = L sum eta)
+  int hencky;               // 0: exact log; m = 1, 2, 3: Pade (m,m) (Gauss-Legendre form below)
+  double pade_s[3], pade_w[3];  // m-point Gauss-Legendre nodes and weights on [0, 1]
 };
 
 // Packed index of (r, c), r <= c, in the row-major upper triangle.
@@ -349,14 +362,42 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
       for (int j = 0; j < 3; ++j) tmp[i][j] = E[i][j];
     eig_sym3(tmp, lam, Q);
   }
+  // f = log (exact mode) or the Pade approximant r_m, at the eigenvalues, and
+  // its first divided differences
   T loglam[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) loglam[a] = log(lam[a]);
   T f1[3][3];
+  T rp[3][3];  // Pade modes: rp[k][a] = 1 / p_k(lam_a)
+  const int npade = P.hencky;
+  if (npade == 0) {
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 3; ++a) loglam[a] = log(lam[a]);
 #pragma unroll
-    for (int b = 0; b < 3; ++b) f1[a][b] = (a == b) ? T(1) / lam[a] : dd1_log(lam[a], lam[b]);
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) f1[a][b] = (a == b) ? T(1) / lam[a] : dd1_log(lam[a], lam[b]);
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      loglam[a] = T(0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) f1[a][b] = T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (k < npade) {
+        const T sk = T(P.pade_s[k]), wk = T(P.pade_w[k]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          rp[k][a] = T(1) / (T(1) + sk * (lam[a] - T(1)));
+          loglam[a] += wk * (lam[a] - T(1)) * rp[k][a];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) f1[a][b] += wk * rp[k][a] * rp[k][b];
+      }
+    }
+  }
   T h[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -561,7 +602,14 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
   for (int a = 0; a < 3; ++a)
     for (int b = a; b < 3; ++b)
       for (int c = b; c < 3; ++c) {
-        T v = dd2_log(lam[a], lam[b], lam[c]);
+        T v;
+        if (npade == 0) {
+          v = dd2_log(lam[a], lam[b], lam[c]);
+        } else {
+          v = T(0);
+          for (int k = 0; k < 3; ++k)
+            if (k < npade) v -= T(P.pade_w[k]) * T(P.pade_s[k]) * rp[k][a] * rp[k][b] * rp[k][c];
+        }
         f2[a][b][c] = f2[a][c][b] = f2[b][a][c] = f2[b][c][a] = f2[c][a][b] = f2[c][b][a] = v;
       }
   // per-phase (L_i : h) rotated, for the eta-dependence of L

@@ -191,8 +191,15 @@ def indentation_dirichlet(mesh: Mesh, step: int, n_steps: int = 10, depth_frac: 
                           radius_frac: float = 0.3):
     """Mask and values of the indentation load at load step ``step``: bottom
     clamped, u_z prescribed under the cap of depth depth_frac*L*step/n_steps."""
+    return indentation_dirichlet_depth(mesh, depth_frac * mesh.Lz * step / n_steps, radius_frac)
+
+
+def indentation_dirichlet_depth(mesh: Mesh, depth: float, radius_frac: float = 0.3):
+    """Mask and values of the indentation load at cap depth ``depth``: bottom
+    clamped, u_z prescribed under the cap of base radius radius_frac*L (the
+    cap nodes stay prescribed at depth 0, with u_z = 0)."""
     mask = face_mask(mesh, bottom=True, top=False)
-    idx, uz = cap_displacement(mesh, depth_frac * mesh.Lz * step / n_steps, radius_frac * mesh.Lx)
+    idx, uz = cap_displacement(mesh, depth, radius_frac * mesh.Lx)
     mask[2, idx] = 1
     values = np.zeros((N_FIELDS, mesh.n_nodes))
     values[2, idx] = uz

@@ -73,6 +73,26 @@ def test_hessians_of_sampled_elements(big):
         assert np.abs(Hg - Ho).max() <= 1e-12 * np.abs(Ho).max()
 
 
+@pytest.mark.parametrize("mode", ["pade11", "pade22", "pade33"])
+def test_pade_hessians_under_the_cap(big, mode):
+    """Pade modes at the benchmark state, where the top element layer under
+    the cap is compressed by up to ~25 %: Hessians of elements along a radius
+    of the cap, from the centre to past the rim, against the oracle."""
+    from paper_2011_08802_gb300 import binding
+    st = big["st"]
+    mat = qp.material_from(st.material, st.tau, hencky=mode)
+    P = binding.problem_from_state(st, params=abi.params_from_material(st.material, st.tau, hencky=mode))
+    P.linearize(abi.PFM_F32)
+    iu = np.triu_indices(15)
+    for i in range(N // 2, N // 2 + 45, 11):
+        e = i + N * (N // 2 + N * (N - 1))
+        Hg = P.get_hessians(e, 1)[0]
+        d = fe.qp_derivatives(fe.Discretisation(st.mesh, elements=[e]), st, mat, order=2)
+        Ho = d["H"][0][:, iu[0], iu[1]]
+        assert np.abs(Hg - Ho).max() <= 1e-12 * np.abs(Ho).max()
+    P.close()
+
+
 def test_tangent_rows_fp64_and_fp32(big):
     st, P, mat = big["st"], big["P"], big["mat"]
     P.linearize(abi.PFM_F32)

@@ -1,0 +1,496 @@
+// Device-side building blocks of the element kernels, shared by the
+// single-problem kernels (fe_kernels.cu) and the batched kernels (batch.cu):
+// Q1 tensor-product gather/scatter by warp shuffles, packed-Hessian index
+// decoding, element-node mapping, and the per-element-block bodies of the
+// tangent application and the linearisation.
+//
+// Thread mapping: 8 consecutive lanes form one element; lane l8 = 0..7 plays
+// two roles: local node a = l8 (corner (a&1, a>>1&1, a>>2)) when gathering
+// nodal data or scattering nodal results, and Gauss point q = l8 (point
+// ((1 -+ 1/sqrt 3)/2) per axis) for the point physics. Values and gradients
+// at the 8 points are a tensor product of 1-D 2x2 transforms, applied with
+// three xor-shuffles (1, 2, 4) per axis; the scatter is the transposed
+// transform. A warp holds 4 elements.
+#pragma once
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace pfm {
+
+template <typename T>
+__device__ __forceinline__ T shx(T v, int m) {
+  return __shfl_xor_sync(0xffffffffu, v, m);
+}
+
+// Nodal value v of this lane's node -> value and gradient at this lane's point.
+template <typename T>
+__device__ __forceinline__ void q1_gather(T v, int l8, T ihx, T ihy, T ihz, T& val, T& gx, T& gy,
+                                          T& gz) {
+  const T ga = T(GA), gb = T(GB);
+  T s = shx(v, 1);
+  T vx = gb * v + ga * s;
+  T dx = ((l8 & 1) ? (v - s) : (s - v)) * ihx;
+  T s1 = shx(vx, 2), s2 = shx(dx, 2);
+  T vxy = gb * vx + ga * s1;
+  T vdy = ((l8 & 2) ? (vx - s1) : (s1 - vx)) * ihy;
+  T dxy = gb * dx + ga * s2;
+  T t1 = shx(vxy, 4), t2 = shx(vdy, 4), t3 = shx(dxy, 4);
+  val = gb * vxy + ga * t1;
+  gz = ((l8 & 4) ? (vxy - t1) : (t1 - vxy)) * ihz;
+  gy = gb * vdy + ga * t2;
+  gx = gb * dxy + ga * t3;
+}
+
+// Nodal value -> value at this lane's point.
+template <typename T>
+__device__ __forceinline__ T q1_value(T v) {
+  const T ga = T(GA), gb = T(GB);
+  v = gb * v + ga * shx(v, 1);
+  v = gb * v + ga * shx(v, 2);
+  return gb * v + ga * shx(v, 4);
+}
+
+// Transpose: point weights (val for N_a, g for grad N_a) -> this lane's node.
+template <typename T>
+__device__ __forceinline__ T q1_scatter(T val, T gx, T gy, T gz, int l8, T ihx, T ihy, T ihz) {
+  const T ga = T(GA), gb = T(GB);
+  T sv = shx(val, 4), sz = shx(gz, 4), sx = shx(gx, 4), sy = shx(gy, 4);
+  T A = gb * val + ga * sv + ((l8 & 4) ? (gz + sz) : -(gz + sz)) * ihz;
+  T Bx = gb * gx + ga * sx;
+  T By = gb * gy + ga * sy;
+  T sA = shx(A, 2), sBy = shx(By, 2), sBx = shx(Bx, 2);
+  T Cc = gb * A + ga * sA + ((l8 & 2) ? (By + sBy) : -(By + sBy)) * ihy;
+  T Dx = gb * Bx + ga * sBx;
+  T sC = shx(Cc, 1), sD = shx(Dx, 1);
+  return gb * Cc + ga * sC + ((l8 & 1) ? (Dx + sD) : -(Dx + sD)) * ihx;
+}
+
+template <typename T>
+__device__ __forceinline__ T q1_scatter_grad(T gx, T gy, T gz, int l8, T ihx, T ihy, T ihz) {
+  const T ga = T(GA), gb = T(GB);
+  T sz = shx(gz, 4), sx = shx(gx, 4), sy = shx(gy, 4);
+  T A = ((l8 & 4) ? (gz + sz) : -(gz + sz)) * ihz;
+  T Bx = gb * gx + ga * sx;
+  T By = gb * gy + ga * sy;
+  T sA = shx(A, 2), sBy = shx(By, 2), sBx = shx(Bx, 2);
+  T Cc = gb * A + ga * sA + ((l8 & 2) ? (By + sBy) : -(By + sBy)) * ihy;
+  T Dx = gb * Bx + ga * sBx;
+  T sC = shx(Cc, 1), sD = shx(Dx, 1);
+  return gb * Cc + ga * sC + ((l8 & 1) ? (Dx + sD) : -(Dx + sD)) * ihx;
+}
+
+// Row of packed upper-triangle index idx of a 15x15 matrix, and the packed
+// index where row r starts.
+__host__ __device__ constexpr int packed_row_start(int r) { return r * NZ - (r * (r - 1)) / 2; }
+__host__ __device__ constexpr int packed_row(int idx) {
+  int r = 0;
+  while (r + 1 < NZ && idx >= packed_row_start(r + 1)) ++r;
+  return r;
+}
+static_assert(packed_row(0) == 0 && packed_row(14) == 0 && packed_row(15) == 1 && packed_row(20) == 1 &&
+                  packed_row(119) == 14 && packed_row(117) == 13 && packed_row(116) == 12,
+              "packed index decode");
+
+__device__ __forceinline__ int64_t elem_node(const Grid& g, int64_t e, int a) {
+  int64_t ei = e % g.nx;
+  int64_t r = e / g.nx;
+  int64_t ej = r % g.ny;
+  int64_t ek = r / g.ny;
+  return (ei + (a & 1)) + int64_t(g.nx + 1) * ((ej + ((a >> 1) & 1)) + int64_t(g.ny + 1) * (ek + (a >> 2)));
+}
+
+// Gather F = I + grad u, eta_hat and grad eta_hat at this lane's point.
+template <typename T, typename Src>
+__device__ __forceinline__ void gather_state(const Src* __restrict__ U, int64_t nn, int64_t node,
+                                             bool valid, int l8, T ihx, T ihy, T ihz, T F[9],
+                                             T eh[6], T ge[18]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T v = valid ? T(U[i * nn + node]) : T(0);
+    T val, gx, gy, gz;
+    q1_gather(v, l8, ihx, ihy, ihz, val, gx, gy, gz);
+    F[3 * i + 0] = gx;
+    F[3 * i + 1] = gy;
+    F[3 * i + 2] = gz;
+  }
+  F[0] += T(1);
+  F[4] += T(1);
+  F[8] += T(1);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    T v = valid ? T(U[(3 + k) * nn + node]) : T(0);
+    q1_gather(v, l8, ihx, ihy, ihz, eh[k], ge[3 * k], ge[3 * k + 1], ge[3 * k + 2]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+
+// Vector of V = 16/sizeof(T) Hessian entries.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  using type = float4;
+  static __device__ __forceinline__ void unpack(const float4& x, float* o) { o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w; }
+};
+template <> struct Vec16<double> {
+  using type = double2;
+  static __device__ __forceinline__ void unpack(const double2& x, double* o) { o[0] = x.x; o[1] = x.y; }
+};
+
+template <typename T>
+struct JParams {
+  T G[6][6];
+  T w, ihx, ihy, ihz;
+};
+
+// Gauss-point Hessians of element block blk (this warp; lane = 8 e + q),
+// computed in TC (FP64 for the finest and the coarsest level, FP32 for the
+// intermediate levels of an FP32 preconditioner) and stored in the requested
+// precisions (null stores are skipped).
+template <typename TC>
+__device__ __forceinline__ void linearize_lane(const Grid& g, const DevParams& P, const double* __restrict__ U,
+                                               const double* __restrict__ Un, double* __restrict__ H64,
+                                               float* __restrict__ H32, float* __restrict__ H32lo, int64_t blk,
+                                               int lane) {
+  const int64_t e = blk * 4 + (lane >> 3);
+  const int l8 = lane & 7;
+  const bool valid = e < g.ne();
+  const int64_t nn = g.nn();
+  const int64_t node = valid ? elem_node(g, e, l8) : 0;
+  const TC ihx = TC(1.0 / g.hx), ihy = TC(1.0 / g.hy), ihz = TC(1.0 / g.hz);
+  TC F[9], eh[6], ge[18], ehn[6];
+  gather_state<TC>(U, nn, node, valid, l8, ihx, ihy, ihz, F, eh, ge);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) ehn[k] = q1_value(valid ? TC(Un[(3 + k) * nn + node]) : TC(0));
+  TC W, gr[NZ], Hp[NH];
+  qp_local<TC, true>(P, F, eh, ehn, &W, gr, Hp);
+  for (int j = 0; j < NH; ++j) {
+    const double h = valid ? double(Hp[j]) : 0.0;
+    if (H64) H64[hstore_offset<double>(blk, j, lane)] = h;
+    if (H32) H32[hstore_offset<float>(blk, j, lane)] = float(h);
+    if (H32lo) H32lo[hstore_offset<float>(blk, j, lane)] = float(h - double(float(h)));
+  }
+}
+
+// Nodal 9x9 diagonal blocks: (element e, local node a) sums over the 8
+// points B_a(q)^T H_q B_a(q) w plus the gradient-energy block, then adds it
+// to the node's block D[(r*9+c)*nn + node].
+template <typename T>
+__device__ __forceinline__ void blockdiag_elem_node(const Grid& g, const JParams<T>& jp, const T* __restrict__ H,
+                                                    T* __restrict__ D, int64_t e, int a) {
+  const int64_t blk = e >> 2;
+  const int lane0 = int(e & 3) * 8;
+  const int64_t nn = g.nn();
+  const int64_t node = elem_node(g, e, a);
+  T Db[45];
+#pragma unroll
+  for (int i = 0; i < 45; ++i) Db[i] = T(0);
+  const T ih[3] = {jp.ihx, jp.ihy, jp.ihz};
+  for (int q = 0; q < 8; ++q) {
+    T phi[3], dphi[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int ad = (a >> d) & 1, qd = (q >> d) & 1;
+      phi[d] = (ad == qd) ? T(GB) : T(GA);
+      dphi[d] = (ad ? T(1) : T(-1)) * ih[d];
+    }
+    const T N = phi[0] * phi[1] * phi[2];
+    const T dN[3] = {dphi[0] * phi[1] * phi[2], phi[0] * dphi[1] * phi[2], phi[0] * phi[1] * dphi[2]};
+    // column map: DOF u_i -> z rows 3i+J (coef dN_J); eta_k -> z row 9+k (coef N)
+    T Hq[NH];
+    for (int j = 0; j < NH; ++j) Hq[j] = H[hstore_offset<T>(blk, j, lane0 + q)];
+    auto hget = [&](int r, int c) -> T { return r <= c ? Hq[hidx(r, c)] : Hq[hidx(c, r)]; };
+    int idx = 0;
+    for (int r = 0; r < 9; ++r)
+      for (int c = r; c < 9; ++c) {
+        T s = T(0);
+        if (r < 3 && c < 3) {
+          for (int J = 0; J < 3; ++J)
+            for (int L = 0; L < 3; ++L) s += dN[J] * dN[L] * hget(3 * r + J, 3 * c + L);
+        } else if (r < 3) {
+          for (int J = 0; J < 3; ++J) s += dN[J] * N * hget(3 * r + J, 9 + (c - 3));
+        } else {
+          s = N * N * hget(9 + (r - 3), 9 + (c - 3)) +
+              (dN[0] * dN[0] + dN[1] * dN[1] + dN[2] * dN[2]) * jp.G[r - 3][c - 3];
+        }
+        Db[idx++] += jp.w * s;
+      }
+  }
+  int idx = 0;
+  for (int r = 0; r < 9; ++r)
+    for (int c = r; c < 9; ++c) {
+      atomicAdd(&D[(r * 9 + c) * nn + node], Db[idx]);
+      if (c != r) atomicAdd(&D[(c * 9 + r) * nn + node], Db[idx]);
+      ++idx;
+    }
+}
+
+// In-place inverse of one node's 9x9 block (Dirichlet rows/columns replaced
+// by identity first) by Gauss-Jordan elimination with partial pivoting; a
+// singular block sets *singular and is replaced by the identity.
+template <typename T>
+__device__ __forceinline__ void block_invert_node(int64_t nn, const dmask_t* __restrict__ mask, T* __restrict__ D,
+                                                  int* singular, int64_t node) {
+  const dmask_t dm = mask[node];
+  T a[9][9], x[9][9];
+  for (int r = 0; r < 9; ++r)
+    for (int c = 0; c < 9; ++c) {
+      T v = D[(r * 9 + c) * nn + node];
+      if (((dm >> r) & 1) || ((dm >> c) & 1)) v = (r == c) ? T(1) : T(0);
+      a[r][c] = v;
+      x[r][c] = (r == c) ? T(1) : T(0);
+    }
+  bool bad = false;
+  for (int k = 0; k < 9; ++k) {
+    int p = k;
+    T best = fabs(a[k][k]);
+    for (int r = k + 1; r < 9; ++r)
+      if (fabs(a[r][k]) > best) { best = fabs(a[r][k]); p = r; }
+    if (!(best > T(0))) { bad = true; break; }
+    if (p != k)
+      for (int c = 0; c < 9; ++c) {
+        T t = a[k][c]; a[k][c] = a[p][c]; a[p][c] = t;
+        t = x[k][c]; x[k][c] = x[p][c]; x[p][c] = t;
+      }
+    const T ip = T(1) / a[k][k];
+    for (int c = 0; c < 9; ++c) { a[k][c] *= ip; x[k][c] *= ip; }
+    for (int r = 0; r < 9; ++r) {
+      if (r == k) continue;
+      const T f = a[r][k];
+      if (f == T(0)) continue;
+      for (int c = 0; c < 9; ++c) { a[r][c] -= f * a[k][c]; x[r][c] -= f * x[k][c]; }
+    }
+  }
+  if (bad) {
+    atomicExch(singular, 1);
+    for (int r = 0; r < 9; ++r)
+      for (int c = 0; c < 9; ++c) x[r][c] = (r == c) ? T(1) : T(0);
+  }
+  for (int r = 0; r < 9; ++r)
+    for (int c = 0; c < 9; ++c) D[(r * 9 + c) * nn + node] = x[r][c];
+}
+
+// ---- BEGIN tangent application kernel
+// y += J v on the 4 elements of block blk (this warp; lane = 0..31): gather v
+// at the element nodes (Dirichlet DOFs read as 0), dz = (grad du, d eta_hat)
+// at the Gauss points, sigma = H dz from the packed symmetric store, plus the
+// constant gradient-energy term, scattered back with atomics.
+template <typename T>
+__device__ __forceinline__ void japply_block(const Grid& g, const JParams<T>& jp, const T* __restrict__ H,
+                                             const dmask_t* __restrict__ mask, const T* __restrict__ v,
+                                             T* __restrict__ y, int64_t blk, int lane) {
+  constexpr int V = 16 / sizeof(T);
+  using VT = typename Vec16<T>::type;
+  const int l8 = lane & 7;
+  const int64_t nn = g.nn();
+  const int64_t e = blk * 4 + (lane >> 3);
+  const bool valid = e < g.ne();
+  const int64_t node = valid ? elem_node(g, e, l8) : 0;
+  const dmask_t dm = valid ? mask[node] : dmask_t(0x1ff);
+  T dz[NZ], ge[18];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T x = ((dm >> i) & 1) ? T(0) : v[i * nn + node];
+    T val;
+    q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, val, dz[3 * i], dz[3 * i + 1], dz[3 * i + 2]);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    T x = ((dm >> (3 + k)) & 1) ? T(0) : v[(3 + k) * nn + node];
+    q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, dz[9 + k], ge[3 * k], ge[3 * k + 1], ge[3 * k + 2]);
+  }
+  // sigma = H dz from the packed symmetric store
+  T sg[NZ];
+#pragma unroll
+  for (int r = 0; r < NZ; ++r) sg[r] = T(0);
+  const VT* Hv = reinterpret_cast<const VT*>(H) + blk * (NH / V) * 32 + lane;
+#pragma unroll
+  for (int j = 0; j < NH / V; ++j) {
+    T hv[V];
+    Vec16<T>::unpack(__ldcs(Hv + j * 32), hv);
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      const int idx = j * V + t;
+      // (r, c) of packed index idx (constant-folded after unrolling)
+      const int r = packed_row(idx);
+      const int c = r + (idx - packed_row_start(r));
+      sg[r] += hv[t] * dz[c];
+      if (c != r) sg[c] += hv[t] * dz[r];
+    }
+  }
+  const T w = jp.w;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T r = q1_scatter_grad(w * sg[3 * i], w * sg[3 * i + 1], w * sg[3 * i + 2], l8, jp.ihx, jp.ihy, jp.ihz);
+    if (valid && !((dm >> i) & 1)) atomicAdd(&y[i * nn + node], r);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    T gf[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      T s = T(0);
+#pragma unroll
+      for (int l = 0; l < 6; ++l) s += jp.G[k][l] * ge[3 * l + d];
+      gf[d] = w * s;
+    }
+    T r = q1_scatter(w * sg[9 + k], gf[0], gf[1], gf[2], l8, jp.ihx, jp.ihy, jp.ihz);
+    if (valid && !((dm >> (3 + k)) & 1)) atomicAdd(&y[(3 + k) * nn + node], r);
+  }
+}
+// ---- END tangent application kernel
+
+
+// ---------------------------------------------------------------------------
+// Double-float ("df") arithmetic: a value is an unevaluated sum hi + lo of two
+// FP32 numbers (Dekker 1971, "A floating-point technique for extending the
+// available precision"; Knuth's TwoSum). Only round-to-nearest FP32 adds,
+// multiplies and fused multiply-adds are used (the _rn intrinsics keep the
+// compiler from contracting or reassociating them), giving about 48
+// significant bits: enough for an outer Krylov operator checked to 1e-8.
+struct dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dfl df_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const dfl s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfl df_shx(dfl v, int m) { return {shx(v.hi, m), shx(v.lo, m)}; }
+
+struct DfConst {
+  dfl ga, gb, ihx, ihy, ihz, w;
+  dfl G[6][6];
+};
+inline dfl df_host(double x) {
+  const float hi = float(x);
+  return {hi, float(x - double(hi))};
+}
+
+__device__ __forceinline__ void q1_gather_df(dfl v, int l8, const DfConst& k, dfl& val, dfl& gx, dfl& gy,
+                                             dfl& gz) {
+  dfl s = df_shx(v, 1);
+  dfl vx = df_add(df_mul(k.gb, v), df_mul(k.ga, s));
+  dfl dx = df_mul((l8 & 1) ? df_sub(v, s) : df_sub(s, v), k.ihx);
+  dfl s1 = df_shx(vx, 2), s2 = df_shx(dx, 2);
+  dfl vxy = df_add(df_mul(k.gb, vx), df_mul(k.ga, s1));
+  dfl vdy = df_mul((l8 & 2) ? df_sub(vx, s1) : df_sub(s1, vx), k.ihy);
+  dfl dxy = df_add(df_mul(k.gb, dx), df_mul(k.ga, s2));
+  dfl t1 = df_shx(vxy, 4), t2 = df_shx(vdy, 4), t3 = df_shx(dxy, 4);
+  val = df_add(df_mul(k.gb, vxy), df_mul(k.ga, t1));
+  gz = df_mul((l8 & 4) ? df_sub(vxy, t1) : df_sub(t1, vxy), k.ihz);
+  gy = df_add(df_mul(k.gb, vdy), df_mul(k.ga, t2));
+  gx = df_add(df_mul(k.gb, dxy), df_mul(k.ga, t3));
+}
+
+__device__ __forceinline__ dfl q1_scatter_df(dfl val, dfl gx, dfl gy, dfl gz, bool has_val, int l8,
+                                             const DfConst& k) {
+  dfl sz = df_shx(gz, 4), sx = df_shx(gx, 4), sy = df_shx(gy, 4);
+  dfl A = df_mul((l8 & 4) ? df_add(gz, sz) : df_neg(df_add(gz, sz)), k.ihz);
+  if (has_val) {
+    dfl sv = df_shx(val, 4);
+    A = df_add(A, df_add(df_mul(k.gb, val), df_mul(k.ga, sv)));
+  }
+  dfl Bx = df_add(df_mul(k.gb, gx), df_mul(k.ga, sx));
+  dfl By = df_add(df_mul(k.gb, gy), df_mul(k.ga, sy));
+  dfl sA = df_shx(A, 2), sBy = df_shx(By, 2), sBx = df_shx(Bx, 2);
+  dfl Cc = df_add(df_add(df_mul(k.gb, A), df_mul(k.ga, sA)),
+                  df_mul((l8 & 2) ? df_add(By, sBy) : df_neg(df_add(By, sBy)), k.ihy));
+  dfl Dx = df_add(df_mul(k.gb, Bx), df_mul(k.ga, sBx));
+  dfl sC = df_shx(Cc, 1), sD = df_shx(Dx, 1);
+  return df_add(df_add(df_mul(k.gb, Cc), df_mul(k.ga, sC)),
+                df_mul((l8 & 1) ? df_add(Dx, sD) : df_neg(df_add(Dx, sD)), k.ihx));
+}
+
+// y += J v on element block blk in double-float arithmetic: v in FP32
+// (exact input), the tangent as Hhi + Hlo (two FP32 stores of the FP64
+// Hessians), element contributions added to the FP64 output y.
+__device__ __forceinline__ void japply_df_block(const Grid& g, const DfConst& k, const float* __restrict__ Hhi,
+                                                const float* __restrict__ Hlo, const dmask_t* __restrict__ mask,
+                                                const float* __restrict__ v, double* __restrict__ y, int64_t blk,
+                                                int lane) {
+  const int l8 = lane & 7;
+  const int64_t nn = g.nn();
+  const int64_t e = blk * 4 + (lane >> 3);
+  const bool valid = e < g.ne();
+  const int64_t node = valid ? elem_node(g, e, l8) : 0;
+  const dmask_t dm = valid ? mask[node] : dmask_t(0x1ff);
+  dfl dz[NZ], ge[18];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float x = ((dm >> i) & 1) ? 0.f : v[i * nn + node];
+    dfl val;
+    q1_gather_df(dfl{x, 0.f}, l8, k, val, dz[3 * i], dz[3 * i + 1], dz[3 * i + 2]);
+  }
+#pragma unroll
+  for (int kk = 0; kk < 6; ++kk) {
+    const float x = ((dm >> (3 + kk)) & 1) ? 0.f : v[(3 + kk) * nn + node];
+    q1_gather_df(dfl{x, 0.f}, l8, k, dz[9 + kk], ge[3 * kk], ge[3 * kk + 1], ge[3 * kk + 2]);
+  }
+  dfl sg[NZ];
+#pragma unroll
+  for (int r = 0; r < NZ; ++r) sg[r] = dfl{0.f, 0.f};
+  const float4* Hh = reinterpret_cast<const float4*>(Hhi) + blk * (NH / 4) * 32 + lane;
+  const float4* Hl = reinterpret_cast<const float4*>(Hlo) + blk * (NH / 4) * 32 + lane;
+#pragma unroll 2
+  for (int j = 0; j < NH / 4; ++j) {
+    float hh[4], hl[4];
+    Vec16<float>::unpack(__ldcs(Hh + j * 32), hh);
+    Vec16<float>::unpack(__ldcs(Hl + j * 32), hl);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int idx = j * 4 + t;
+      const int r = packed_row(idx);
+      const int c = r + (idx - packed_row_start(r));
+      const dfl hv{hh[t], hl[t]};
+      sg[r] = df_add(sg[r], df_mul(hv, dz[c]));
+      if (c != r) sg[c] = df_add(sg[c], df_mul(hv, dz[r]));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    dfl r = q1_scatter_df(dfl{0.f, 0.f}, df_mul(k.w, sg[3 * i]), df_mul(k.w, sg[3 * i + 1]),
+                          df_mul(k.w, sg[3 * i + 2]), false, l8, k);
+    if (valid && !((dm >> i) & 1)) atomicAdd(&y[i * nn + node], double(r.hi) + double(r.lo));
+  }
+#pragma unroll
+  for (int kk = 0; kk < 6; ++kk) {
+    dfl gf[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      dfl s = dfl{0.f, 0.f};
+#pragma unroll
+      for (int l = 0; l < 6; ++l) s = df_add(s, df_mul(k.G[kk][l], ge[3 * l + d]));
+      gf[d] = df_mul(k.w, s);
+    }
+    dfl r = q1_scatter_df(df_mul(k.w, sg[9 + kk]), gf[0], gf[1], gf[2], true, l8, k);
+    if (valid && !((dm >> (3 + kk)) & 1)) atomicAdd(&y[(3 + kk) * nn + node], double(r.hi) + double(r.lo));
+  }
+}
+
+}  // namespace pfm

@@ -1,0 +1,182 @@
+// Internal state of a problem handle and helpers shared by the host-side
+// translation units of libpfm (api.cu: single-problem drivers; batch.cu:
+// the batched engine). Not part of the public ABI.
+#pragma once
+
+#include <chrono>
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/pfm.h"
+#include "common.cuh"
+
+namespace pfm {
+
+struct Level {
+  Grid g{};
+  int64_t nn = 0, ne = 0, nblk = 0;
+  double* U = nullptr;
+  double* Un = nullptr;
+  dmask_t* mask = nullptr;
+  double* H64 = nullptr;
+  float* H32 = nullptr;
+  float* H32lo = nullptr;  // finest level, mixed mode: H64 - H32 rounded to FP32
+  double* D64 = nullptr;
+  float* D32 = nullptr;
+  float *x32 = nullptr, *b32 = nullptr, *y32 = nullptr, *r32 = nullptr, *d32 = nullptr;
+  double *x64 = nullptr, *b64 = nullptr, *y64 = nullptr, *r64 = nullptr, *d64 = nullptr;
+  double lam = 0.0;  // estimate of lambda_max(D^-1 J) for the Chebyshev smoother
+};
+
+template <typename T> struct LvVec;
+template <> struct LvVec<float> {
+  static float*& x(Level& l) { return l.x32; }
+  static float*& b(Level& l) { return l.b32; }
+  static float*& y(Level& l) { return l.y32; }
+  static float*& r(Level& l) { return l.r32; }
+  static float*& d(Level& l) { return l.d32; }
+  static float*& D(Level& l) { return l.D32; }
+  static float*& H(Level& l) { return l.H32; }
+};
+template <> struct LvVec<double> {
+  static double*& x(Level& l) { return l.x64; }
+  static double*& b(Level& l) { return l.b64; }
+  static double*& y(Level& l) { return l.y64; }
+  static double*& r(Level& l) { return l.r64; }
+  static double*& d(Level& l) { return l.d64; }
+  static double*& D(Level& l) { return l.D64; }
+  static double*& H(Level& l) { return l.H64; }
+};
+
+constexpr int MAX_COARSE_DOFS = 5000;
+constexpr int MAX_RESTART = 64;
+
+inline double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace pfm
+
+struct pfm_handle {
+  pfm_params params{};
+  pfm::DevParams dp{};
+  std::vector<pfm::Level> L;
+  cudaStream_t stream = 0;
+  std::string err;
+  bool have_state = false;
+  bool have_dirval = false;
+  bool linearized = false;
+  pfm_precision lin_prec = PFM_F64;
+  double* dirval = nullptr;
+  double* energy_dev = nullptr;
+  int* flag_dev = nullptr;
+  double* diag_part = nullptr;  // per-plane partial sums of the diagnostics
+  // solver work (finest level, FP64)
+  double* R = nullptr;
+  double* dU = nullptr;
+  double* wv = nullptr;
+  double* rv = nullptr;
+  double* zd = nullptr;
+  double* partial = nullptr;
+  double* hdev = nullptr;
+  // Krylov basis
+  int kry_m = 0;
+  pfm_precision kry_prec = PFM_F64;
+  double* V = nullptr;
+  void* Z = nullptr;
+  // coarse dense operator [K | I] reduced by Gauss-Jordan, its inverse, work
+  double* Kaug = nullptr;
+  double* Kinv = nullptr;
+  unsigned long long* gj_keys = nullptr;
+  int* gj_used = nullptr;
+  int* gj_piv = nullptr;
+  int nc_dofs = 0;
+  // staging for the host-buffer entry point
+  void* stage_in = nullptr;
+  void* stage_out = nullptr;
+  int power_its = 30;
+  bool outer_df = true;  // outer operator of the mixed solve in double-float arithmetic
+  // pinned host slots for Hessenberg columns and scalars
+  double* hpin = nullptr;
+  // captured V-cycle (valid until the next linearisation)
+  bool use_graphs = false;
+  cudaGraphExec_t vgraph = nullptr;
+  int vgraph_prec = -1;
+  struct { int nu_pre, nu_post, type; double omega, lo, hi; int gamma; double growth; } vgraph_cfg{};
+  // device timing of hot phases (pairs of events per timed launch)
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[PFM_PROF_COUNT];
+  int64_t prof_n[PFM_PROF_COUNT] = {0};
+  double prof_ms[PFM_PROF_COUNT] = {0};
+
+  pfm_status fail(pfm_status s, const std::string& m) {
+    err = m;
+    return s;
+  }
+};
+
+
+namespace pfm {
+struct BatchEngine;  // batched multigrid/FGMRES engine (batch.cu)
+void batch_engine_free(BatchEngine* e);
+}  // namespace pfm
+
+struct pfm_batch {
+  std::vector<pfm_handle*> hs;
+  std::vector<cudaStream_t> streams;
+  std::string err;
+  pfm::BatchEngine* engine = nullptr;
+  pfm_status fail(pfm_status st, const std::string& m) {
+    err = m;
+    return st;
+  }
+};
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return h->fail(e_ == cudaErrorMemoryAllocation ? PFM_ERR_OOM : PFM_ERR_CUDA,            \
+                     std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+  } while (0)
+
+#define CKL()                                                                                 \
+  do {                                                                                        \
+    cudaError_t e_ = cudaGetLastError();                                                      \
+    if (e_ != cudaSuccess)                                                                    \
+      return h->fail(PFM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_));  \
+  } while (0)
+
+#define TRY(expr)                     \
+  do {                                \
+    pfm_status s_ = (expr);           \
+    if (s_ != PFM_OK) return s_;      \
+  } while (0)
+
+namespace pfm {
+
+template <typename T>
+pfm_status dalloc(pfm_handle* h, T** p, size_t count) {
+  if (*p) return PFM_OK;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count > 0 ? count : 1));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return h->fail(PFM_ERR_OOM, std::string("cudaMalloc of ") + std::to_string(sizeof(T) * count) +
+                                    " bytes failed: " + cudaGetErrorString(e));
+  }
+  return PFM_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+inline int64_t ndof(const Level& l) { return int64_t(NF) * l.nn; }
+
+}  // namespace pfm

@@ -9,6 +9,7 @@
 // node I0 and rem/nf on I0+1. All index arithmetic is integer, so P and
 // R = P^T use identical weights on nested (nf = 2 nc) and non-nested grids.
 #include "common.cuh"
+#include "mg_device.cuh"
 
 namespace pfm {
 namespace {
@@ -18,57 +19,12 @@ inline unsigned grid_for(int64_t threads, int block) {
   return unsigned(b > 0 ? b : 1);
 }
 
-struct Interp1 {
-  int i0;
-  double t;  // weight of i0+1
-};
-
-__device__ __forceinline__ Interp1 interp1(int i, int nf, int nc) {
-  // coarse coordinate of fine node i: i*nc/nf
-  long long num = (long long)i * nc;
-  int I0 = int(num / nf);
-  long long rem = num - (long long)I0 * nf;
-  if (I0 >= nc) { I0 = nc - 1; rem = nf; }
-  return {I0, double(rem) / double(nf)};
-}
-
-// Value of the nodal field X (grid nx,ny,nz; field stride n) at the point with
-// per-axis element index i0 and local coordinate t (trilinear).
-template <typename T>
-__device__ __forceinline__ double trilinear(const T* X, int nx, int ny, const int i0[3], const double t[3]) {
-  double s = 0.0;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const int a0 = c & 1, a1 = (c >> 1) & 1, a2 = (c >> 2) & 1;
-    double w = (a0 ? t[0] : 1.0 - t[0]) * (a1 ? t[1] : 1.0 - t[1]) * (a2 ? t[2] : 1.0 - t[2]);
-    if (w == 0.0) continue;
-    int64_t node = (i0[0] + a0) + int64_t(nx + 1) * ((i0[1] + a1) + int64_t(ny + 1) * (i0[2] + a2));
-    s += w * double(X[node]);
-  }
-  return s;
-}
-
 // Coarse state = fine Q1 field evaluated at coarse node positions.
 __global__ void k_inject_state(Grid f, Grid c, const double* __restrict__ Uf, double* __restrict__ Uc) {
   const int64_t nnc = c.nn();
-  const int64_t nnf = f.nn();
   for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < nnc;
-       idx += int64_t(gridDim.x) * blockDim.x) {
-    int I = int(idx % (c.nx + 1));
-    int J = int((idx / (c.nx + 1)) % (c.ny + 1));
-    int K = int(idx / (int64_t(c.nx + 1) * (c.ny + 1)));
-    // fine coordinate of coarse node: I*nf/nc
-    int i0[3];
-    double t[3];
-    const int Ic[3] = {I, J, K}, nfv[3] = {f.nx, f.ny, f.nz}, ncv[3] = {c.nx, c.ny, c.nz};
-    for (int d = 0; d < 3; ++d) {
-      Interp1 p = interp1(Ic[d], ncv[d], nfv[d]);  // coarse node in fine coordinates
-      i0[d] = p.i0;
-      t[d] = p.t;
-    }
-    for (int fld = 0; fld < NF; ++fld)
-      Uc[fld * nnc + idx] = trilinear(Uf + fld * nnf, f.nx, f.ny, i0, t);
-  }
+       idx += int64_t(gridDim.x) * blockDim.x)
+    inject_node(f, c, Uf, Uc, idx);
 }
 
 // Coarse Dirichlet bits = bits of the nearest fine node.
@@ -90,65 +46,19 @@ template <typename T>
 __global__ void k_prolong_add(Grid f, Grid c, const T* __restrict__ xc, const dmask_t* __restrict__ mf,
                               T* __restrict__ xf) {
   const int64_t nnf = f.nn();
-  const int64_t nnc = c.nn();
   for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < nnf;
-       idx += int64_t(gridDim.x) * blockDim.x) {
-    int i = int(idx % (f.nx + 1));
-    int j = int((idx / (f.nx + 1)) % (f.ny + 1));
-    int k = int(idx / (int64_t(f.nx + 1) * (f.ny + 1)));
-    Interp1 px = interp1(i, f.nx, c.nx), py = interp1(j, f.ny, c.ny), pz = interp1(k, f.nz, c.nz);
-    const int i0[3] = {px.i0, py.i0, pz.i0};
-    const double t[3] = {px.t, py.t, pz.t};
-    const dmask_t dm = mf[idx];
-    for (int fld = 0; fld < NF; ++fld) {
-      if ((dm >> fld) & 1) continue;
-      xf[fld * nnf + idx] += T(trilinear(xc + fld * nnc, c.nx, c.ny, i0, t));
-    }
-  }
+       idx += int64_t(gridDim.x) * blockDim.x)
+    prolong_node<T>(f, c, xc, mf, xf, idx);
 }
 
-// rc = P^T rf, zero at coarse Dirichlet DOFs. Coarse node I collects fine
-// nodes i with |i*nc - I*nf| < nf, weight 1 - |i*nc - I*nf|/nf (per axis).
+// rc = P^T rf, zero at coarse Dirichlet DOFs.
 template <typename T>
 __global__ void k_restrict(Grid f, Grid c, const T* __restrict__ rf, const dmask_t* __restrict__ mc,
                            T* __restrict__ rc) {
-  const int64_t nnf = f.nn();
   const int64_t nnc = c.nn();
   for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < nnc;
-       idx += int64_t(gridDim.x) * blockDim.x) {
-    const int Ic[3] = {int(idx % (c.nx + 1)), int((idx / (c.nx + 1)) % (c.ny + 1)),
-                       int(idx / (int64_t(c.nx + 1) * (c.ny + 1)))};
-    const int nfv[3] = {f.nx, f.ny, f.nz}, ncv[3] = {c.nx, c.ny, c.nz};
-    int lo[3], hi[3];
-    for (int d = 0; d < 3; ++d) {
-      long long center = (long long)Ic[d] * nfv[d];  // in units of 1/(nf*nc) ... i*nc vs I*nf
-      // i*nc > I*nf - nf  and  i*nc < I*nf + nf
-      long long a = center - nfv[d];
-      long long b = center + nfv[d];
-      int l = int(a >= 0 ? a / ncv[d] + 1 : 0);
-      int h = int(b % ncv[d] == 0 ? b / ncv[d] - 1 : b / ncv[d]);
-      if (l < 0) l = 0;
-      if (h > nfv[d]) h = nfv[d];
-      lo[d] = l;
-      hi[d] = h;
-    }
-    const dmask_t dm = mc[idx];
-    double acc[NF];
-    for (int fld = 0; fld < NF; ++fld) acc[fld] = 0.0;
-    for (int k = lo[2]; k <= hi[2]; ++k) {
-      double wz = 1.0 - fabs(double((long long)k * ncv[2] - (long long)Ic[2] * nfv[2])) / nfv[2];
-      for (int j = lo[1]; j <= hi[1]; ++j) {
-        double wy = 1.0 - fabs(double((long long)j * ncv[1] - (long long)Ic[1] * nfv[1])) / nfv[1];
-        for (int i = lo[0]; i <= hi[0]; ++i) {
-          double wx = 1.0 - fabs(double((long long)i * ncv[0] - (long long)Ic[0] * nfv[0])) / nfv[0];
-          const double w = wx * wy * wz;
-          const int64_t fn = i + int64_t(f.nx + 1) * (j + int64_t(f.ny + 1) * k);
-          for (int fld = 0; fld < NF; ++fld) acc[fld] += w * double(rf[fld * nnf + fn]);
-        }
-      }
-    }
-    for (int fld = 0; fld < NF; ++fld) rc[fld * nnc + idx] = ((dm >> fld) & 1) ? T(0) : T(acc[fld]);
-  }
+       idx += int64_t(gridDim.x) * blockDim.x)
+    restrict_node<T>(f, c, rf, mc, rc, idx);
 }
 
 // x += omega D^-1 (b - y) per node (y == nullptr: y = 0).
@@ -250,18 +160,6 @@ __global__ void k_coarse_bc(int n, int64_t nn, const dmask_t* __restrict__ mask,
   K[int64_t(r) * ld + n + c] = (r == c) ? 1.0 : 0.0;
 }
 
-// Gauss-Jordan elimination with partial pivoting on the augmented n x 2n
-// matrix [K | I], with the row permutation kept implicit: step k takes the
-// pivot row p chosen by step k-1 (largest |M[i][k]| over rows not yet used as
-// pivots), eliminates column k from every other row (columns > k of the left
-// half and the whole right half; column k itself is never read again), and in
-// the same launch votes the pivot of step k+1 with a 64-bit atomicMax on
-// (|value| as FP32 bits, row). Row p is left unscaled; at the end inverse row
-// k is row piv[k] of the right half divided by M[piv[k]][k].
-__device__ __forceinline__ unsigned long long pivot_key(double v, int row) {
-  return (static_cast<unsigned long long>(__float_as_uint(float(fabs(v)))) << 32) | unsigned(row);
-}
-
 __global__ void k_gj_first_key(const double* __restrict__ M, int n, int ld, unsigned long long* keys) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     atomicMax(&keys[0], pivot_key(M[int64_t(i) * ld], i));
@@ -271,32 +169,7 @@ __global__ void k_gj_first_key(const double* __restrict__ M, int n, int ld, unsi
 __global__ void __launch_bounds__(256) k_gj_step(double* __restrict__ M, int n, int ld, int k,
                                                  unsigned long long* __restrict__ keys, int* __restrict__ used,
                                                  int* __restrict__ piv, int* singular) {
-  const int p = int(keys[k] & 0xffffffffu);
-  const double pk = M[int64_t(p) * ld + k];
-  if (!(fabs(pk) > 0.0)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *singular = 1;
-    return;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) piv[k] = p;
-  const int i = blockIdx.x;
-  if (i >= n) return;
-  if (i == p) {
-    if (threadIdx.x == 0) used[p] = 1;
-    return;
-  }
-  const double f = M[int64_t(i) * ld + k] / pk;
-  const bool candidate = (k + 1 < n) && !used[i];
-  double* Mi = M + int64_t(i) * ld;
-  const double* Mp = M + int64_t(p) * ld;
-  if (f != 0.0) {
-    for (int j = k + 1 + threadIdx.x; j < 2 * n; j += blockDim.x) {
-      const double v = Mi[j] - f * Mp[j];
-      Mi[j] = v;
-      if (j == k + 1 && candidate) atomicMax(&keys[k + 1], pivot_key(v, i));
-    }
-  } else if (candidate && threadIdx.x == 0) {
-    atomicMax(&keys[k + 1], pivot_key(Mi[k + 1], i));
-  }
+  gj_step_row(M, n, ld, k, keys, used, piv, singular, int(blockIdx.x), blockIdx.x == 0);
 }
 
 // Ainv[k][c] = M[piv[k]][n + c] / M[piv[k]][k]
@@ -330,23 +203,8 @@ template <typename T>
 __global__ void k_cheb_first(int64_t nn, const T* __restrict__ D, const T* src, T c, bool copy_r,
                              bool zero_x, T* r, T* __restrict__ d, T* __restrict__ x) {
   for (int64_t node = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; node < nn;
-       node += int64_t(gridDim.x) * blockDim.x) {
-    T rv[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      rv[f] = src[f * nn + node];
-      if (copy_r) r[f * nn + node] = rv[f];
-    }
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      T s = T(0);
-#pragma unroll
-      for (int cc = 0; cc < NF; ++cc) s += D[(f * 9 + cc) * nn + node] * rv[cc];
-      const T dv = c * s;
-      d[f * nn + node] = dv;
-      x[f * nn + node] = zero_x ? dv : x[f * nn + node] + dv;
-    }
-  }
+       node += int64_t(gridDim.x) * blockDim.x)
+    cheb_first_node<T>(nn, D, src, c, copy_r, zero_x, r, d, x, node);
 }
 
 // r -= y; d = a d + c D^-1 r; x += d.
@@ -354,38 +212,15 @@ template <typename T>
 __global__ void k_cheb_step(int64_t nn, const T* __restrict__ D, const T* __restrict__ y, T a, T c,
                             T* __restrict__ r, T* __restrict__ d, T* __restrict__ x) {
   for (int64_t node = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; node < nn;
-       node += int64_t(gridDim.x) * blockDim.x) {
-    T rv[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      rv[f] = r[f * nn + node] - y[f * nn + node];
-      r[f * nn + node] = rv[f];
-    }
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      T s = T(0);
-#pragma unroll
-      for (int cc = 0; cc < NF; ++cc) s += D[(f * 9 + cc) * nn + node] * rv[cc];
-      const T dv = a * d[f * nn + node] + c * s;
-      d[f * nn + node] = dv;
-      x[f * nn + node] += dv;
-    }
-  }
+       node += int64_t(gridDim.x) * blockDim.x)
+    cheb_step_node<T>(nn, D, y, a, c, r, d, x, node);
 }
 
-// Deterministic start vector of the power iteration: values in [-1, 1) from
-// an integer hash of the index, zero at Dirichlet DOFs.
+// Deterministic start vector of the power iteration (power_init_value).
 template <typename T>
 __global__ void k_power_init(int64_t nn, const dmask_t* __restrict__ mask, T* __restrict__ x) {
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < NF * nn; i += int64_t(gridDim.x) * blockDim.x) {
-    uint64_t z = uint64_t(i) + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    z ^= z >> 31;
-    const double u = double(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
-    const int f = int(i / nn);
-    x[i] = ((mask[i % nn] >> f) & 1) ? T(0) : T(u);
-  }
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < NF * nn; i += int64_t(gridDim.x) * blockDim.x)
+    x[i] = T(power_init_value(i, nn, mask));
 }
 
 // x = y / sqrt(*dot)

@@ -287,8 +287,10 @@ def batch_measure(args, dev):
     """64 independent indentation problems, n ~ U{8..24} and final depth ~
     U[0.005, 0.03] L (seeded), each at the first of 10 load steps of its own
     ramp, one Newton correction each at rtol 1e-8: wall time of one
-    pfm_batch_newton_solve against the same problems solved one after another
-    with pfm_newton_solve."""
+    pfm_batch_newton_solve with the batched engine (one launch per phase over
+    all problems, graph-replayed FGMRES iterations) and with the per-problem
+    lockstep driver, against the same problems solved one after another with
+    pfm_newton_solve."""
     import torch
 
     from paper_2011_08802_gb300 import abi, binding, inputs
@@ -311,29 +313,41 @@ def batch_measure(args, dev):
 
     B = binding.Batch(probs)
 
-    def batched():
+    def batched(mode):
+        B.set_mode(mode)
         Us = [u.clone() for u in U0]
         reps = B.newton_solve(Us, opts, check=False)
         torch.cuda.synchronize()
         return reps
 
     sequential()
-    batched()
+    batched(0)
+    batched(1)
     t0 = time.perf_counter()
     seq_its = sequential()
     t_seq = time.perf_counter() - t0
+    l0 = binding.launch_count()
     t0 = time.perf_counter()
-    reps = batched()
+    reps = batched(0)
     t_bat = time.perf_counter() - t0
+    l_bat = binding.launch_count() - l0
+    l0 = binding.launch_count()
+    t0 = time.perf_counter()
+    reps_ls = batched(1)
+    t_ls = time.perf_counter() - t0
+    l_ls = binding.launch_count() - l0
     worst = max(r.lin_res_final for r in reps)
     B.close()
     for P in probs:
         P.close()
+    r0 = reps[0]
     return {"problems": len(probs), "n_range": [min(ns), max(ns)], "total_dofs": dofs,
             "batch_s": t_bat, "sequential_s": t_seq, "speedup": t_seq / t_bat,
+            "lockstep_s": t_ls, "engine_launches": l_bat, "lockstep_launches": l_ls,
+            "engine_phase_ms": {"residual": r0.ms_residual, "linearize": r0.ms_linearize, "solve": r0.ms_solve},
             "batch_fgmres_its_max": max(r.lin_its_last for r in reps),
             "sequential_fgmres_its_max": max(seq_its), "worst_rel_residual": worst,
-            "all_ok": all(r.status == 0 for r in reps)}
+            "all_ok": all(r.status == 0 for r in reps) and all(r.status == 0 for r in reps_ls)}
 
 
 def diff_measure(dev):

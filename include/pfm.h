@@ -322,9 +322,21 @@ const char* pfm_batch_last_error(const pfm_batch* b);
  * nullable) get each problem's iteration counts and norms (times are those of
  * the whole batch). Problems that meet newton_rtol stop early while the others
  * continue. Returns the first failing status, PFM_OK if every problem
- * converged. Synchronises. */
+ * converged. Synchronises.
+ * With the mixed-precision options (precond PFM_F32, Chebyshev smoother,
+ * V-cycle, double-float outer operator) the batched engine runs: every phase
+ * (linearisation of all levels, eigenvalue estimates, coarse inverses,
+ * V-cycle steps, FGMRES vector work) is one launch over all problems, and each
+ * FGMRES iteration of the batch is one replayed CUDA graph. Other options, or
+ * mode 1 of pfm_batch_set_mode, advance the problems in lockstep with
+ * per-problem launches. Both give the same iterates up to rounding. */
 pfm_status pfm_batch_newton_solve(pfm_batch* b, const pfm_solve_opts* opts, double* const* U_inout,
                                   pfm_solve_report* reports);
+
+/* Driver of pfm_batch_newton_solve: 0 = batched engine where the options
+ * allow it (default), 1 = per-problem lockstep driver.
+ * Errors: PFM_ERR_INVALID_ARG (null batch, other mode). */
+pfm_status pfm_batch_set_mode(pfm_batch* b, int mode);
 
 /* Residual and potential without a handle and without allocating device
  * memory, for callers that cannot call cudaMalloc: code inside a framework

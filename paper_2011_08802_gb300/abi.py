@@ -159,6 +159,7 @@ def lib():
         "pfm_batch_destroy": (None, [H]),
         "pfm_batch_last_error": (C.c_char_p, [H]),
         "pfm_batch_newton_solve": (i32, [H, C.POINTER(SolveOpts), C.POINTER(vp), C.POINTER(SolveReport)]),
+        "pfm_batch_set_mode": (i32, [H, i32]),
         "pfm_residual_noalloc": (i32, [C.POINTER(MeshDesc), C.POINTER(Params), vp, vp, vp, vp,
                                        C.POINTER(dp), vp]),
         "pfm_noalloc_last_error": (C.c_char_p, []),
@@ -180,7 +181,7 @@ def exported_symbols():
         "pfm_jacobian_apply_host", "pfm_jacobian_apply_mixed", "pfm_vcycle", "pfm_fgmres_solve", "pfm_newton_solve",
         "pfm_qp_eval", "pfm_get_hessians", "pfm_profile_enable", "pfm_profile_get",
         "pfm_launch_count", "pfm_param_grad", "pfm_batch_create", "pfm_batch_destroy",
-        "pfm_batch_last_error", "pfm_batch_newton_solve", "pfm_residual_noalloc", "pfm_noalloc_last_error",
+        "pfm_batch_last_error", "pfm_batch_newton_solve", "pfm_batch_set_mode", "pfm_residual_noalloc", "pfm_noalloc_last_error",
     ]
 
 

@@ -235,6 +235,12 @@ class Batch:
             raise PfmError(st, L.pfm_batch_last_error(None).decode())
         self.b = b
 
+    def set_mode(self, mode: int):
+        """``pfm_batch_set_mode``: 0 = batched engine (default), 1 = lockstep."""
+        st = self._lib.pfm_batch_set_mode(self.b, int(mode))
+        if st != 0:
+            raise PfmError(st, self._lib.pfm_batch_last_error(self.b).decode())
+
     def newton_solve(self, states, opts: abi.SolveOpts, check: bool = True):
         arr = (C.c_void_p * len(states))(*[U.data_ptr() for U in states])
         reps = (abi.SolveReport * len(states))()

@@ -294,7 +294,9 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
     const bool fine = (l == 0);
     const size_t hsz = size_t(lv.nblk) * HBLK;
     const bool need64 = fine || coarsest || prec == PFM_F64;
-    const bool need32 = prec == PFM_F32 && !coarsest;
+    // the finest level of a mixed solve always needs the FP32 pair (the
+    // double-float outer operator reads it), also when it is the only level
+    const bool need32 = prec == PFM_F32 && (fine || !coarsest);
     if (need64) TRY(dalloc(h, &lv.H64, hsz));
     if (need32) TRY(dalloc(h, &lv.H32, hsz));
     const bool needlo = fine && need32;
@@ -412,6 +414,8 @@ pfm_status fgm_begin_enqueue(pfm_handle* h, Fgm& F, const pfm_solve_opts& o, con
   F.sc = smooth_cfg(&o);
   if (F.mixed && h->lin_prec != PFM_F32)
     return h->fail(PFM_ERR_STATE, "FP32 preconditioner requested but the tangent was built for FP64");
+  if (F.mixed && h->outer_df && (!h->L[0].H32 || !h->L[0].H32lo))
+    return h->fail(PFM_ERR_STATE, "the double-float outer operator has no FP32 Hessian pair");
   TRY(fgm_alloc(h, F));
   F.Hh.assign(size_t(F.m + 1) * F.m, 0.0);
   F.cs.assign(F.m, 0.0);
@@ -1201,17 +1205,33 @@ pfm_status pfm_batch_create(pfm_handle* const* handles, int count, pfm_batch** o
 
 void pfm_batch_destroy(pfm_batch* b) {
   if (!b) return;
+  if (b->engine) {
+    cudaDeviceSynchronize();
+    batch_engine_free(b->engine);
+  }
   for (auto x : b->streams) cudaStreamDestroy(x);
   delete b;
 }
 
 const char* pfm_batch_last_error(const pfm_batch* b) { return b ? b->err.c_str() : g_batch_create_error.c_str(); }
 
+pfm_status pfm_batch_set_mode(pfm_batch* b, int mode) {
+  if (!b) return PFM_ERR_INVALID_ARG;
+  if (mode != 0 && mode != 1) return b->fail(PFM_ERR_INVALID_ARG, "batch mode must be 0 or 1");
+  b->mode = mode;
+  return PFM_OK;
+}
+
 pfm_status pfm_batch_newton_solve(pfm_batch* b, const pfm_solve_opts* opts, double* const* U_inout,
                                   pfm_solve_report* reports) {
   if (!b) return PFM_ERR_INVALID_ARG;
   if (!opts || !U_inout || !opts_valid(*opts)) return b->fail(PFM_ERR_INVALID_ARG, "bad options or state arrays");
   const int N = int(b->hs.size());
+  for (int p = 0; p < N; ++p) {
+    if (!b->hs[p]->have_state) return b->fail(PFM_ERR_STATE, "problem " + std::to_string(p) + " has no U_n");
+    if (!U_inout[p]) return b->fail(PFM_ERR_INVALID_ARG, "null state of problem " + std::to_string(p));
+  }
+  if (b->mode == 0 && batch_engine_supports(*opts, b)) return batch_engine_newton(b, *opts, U_inout, reports);
   std::vector<cudaStream_t> saved(N);
   for (int p = 0; p < N; ++p) {
     pfm_handle* h = b->hs[p];

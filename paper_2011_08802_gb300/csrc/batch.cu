@@ -39,12 +39,23 @@ struct BLev {
   float* vec[5];   // x, b, y, r, d
   int64_t blk0;    // first element block of this level in the set's numbering
   float inv_theta, inv_delta;  // Chebyshev coefficients 1/theta, 1/delta
-  int pad[2];
+  int problem;     // index of the problem in the batch (gate lookup)
+  int pad;
+};
+
+// Per-problem on/off gate of a launch: on[problem * stride] != 0. The V-cycle
+// is gated by the FGMRES activity flags, the linearisation by the Newton
+// activity flags.
+struct Gate {
+  const int* on;
+  int stride;
+  __device__ __forceinline__ bool operator()(int p) const { return on[int64_t(p) * stride] != 0; }
 };
 enum { VX = 0, VB = 1, VY = 2, VR = 3, VD = 4 };
 
 // Transfer between level l (fine) and l+1 (coarse) of one problem.
 struct BTr {
+  int problem;
   Grid f, c;
   const dmask_t* mf;
   const dmask_t* mc;
@@ -56,6 +67,7 @@ struct BTr {
 
 // Dense coarse solve x = Kinv b of one problem.
 struct BCo {
+  int problem;
   int n;
   const double* Kinv;
   const float* b;
@@ -64,6 +76,7 @@ struct BCo {
 
 // Linearisation of one level of one problem.
 struct BLin {
+  int problem;
   Grid g;
   const DevParams* P;
   const double* U;
@@ -76,6 +89,7 @@ struct BLin {
 
 // State injection level l-1 -> l of one problem.
 struct BInj {
+  int problem;
   Grid f, c;
   const double* Uf;
   double* Uc;
@@ -85,6 +99,7 @@ struct BInj {
 
 // Diagonal blocks of one level of one problem.
 struct BBd {
+  int problem;
   Grid g;
   JParams<float> jp;
   const float* H;
@@ -95,6 +110,7 @@ struct BBd {
 
 // Gauss-Jordan inverse of one problem's dense coarse operator.
 struct BGj {
+  int problem;
   double* M;
   int n;
   unsigned long long* keys;
@@ -157,7 +173,7 @@ __device__ __forceinline__ int find_entry(const S* __restrict__ set, int ns, int
 // y += J v over all element blocks of the set; v = vec[vsel], y = vec[ysel].
 // Each warp caches the descriptor of its current problem in shared memory.
 __global__ void __launch_bounds__(256) k_b_japply(const BLev* __restrict__ S, int ns, int64_t nblk, int vsel,
-                                                  int ysel) {
+                                                  int ysel, Gate on) {
   __shared__ BLev cache[8];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t wg = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -174,14 +190,15 @@ __global__ void __launch_bounds__(256) k_b_japply(const BLev* __restrict__ S, in
       cur = p;
     }
     const BLev& L = cache[wid];
-    if (blk - L.blk0 < L.g.nblk())
+    if (on(L.problem) && blk - L.blk0 < L.g.nblk())
       japply_block<float>(L.g, L.jp, L.H, L.mask, L.vec[vsel], L.vec[ysel], blk - L.blk0, lane);
   }
 }
 
 // y = v at Dirichlet DOFs, 0 elsewhere (identity rows of J).
-__global__ void k_b_init(const BLev* __restrict__ S, int vsel, int ysel) {
+__global__ void k_b_init(const BLev* __restrict__ S, int vsel, int ysel, Gate on) {
   const BLev& L = S[blockIdx.y];
+  if (!on(L.problem)) return;
   const int64_t nn = L.g.nn();
   const float* v = L.vec[vsel];
   float* y = L.vec[ysel];
@@ -189,15 +206,17 @@ __global__ void k_b_init(const BLev* __restrict__ S, int vsel, int ysel) {
     y[i] = ((L.mask[i % nn] >> int(i / nn)) & 1) ? v[i] : 0.f;
 }
 
-__global__ void k_b_cheb_first(const BLev* __restrict__ S, int srcsel, bool copy_r, bool zero_x) {
+__global__ void k_b_cheb_first(const BLev* __restrict__ S, int srcsel, bool copy_r, bool zero_x, Gate on) {
   const BLev& L = S[blockIdx.y];
+  if (!on(L.problem)) return;
   const int64_t nn = L.g.nn();
   for (int64_t node = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; node < nn; node += int64_t(gridDim.x) * blockDim.x)
     cheb_first_node<float>(nn, L.D, L.vec[srcsel], L.inv_theta, copy_r, zero_x, L.vec[VR], L.vec[VD], L.vec[VX], node);
 }
 
-__global__ void k_b_cheb_step(const BLev* __restrict__ S, float a, float c) {
+__global__ void k_b_cheb_step(const BLev* __restrict__ S, float a, float c, Gate on) {
   const BLev& L = S[blockIdx.y];
+  if (!on(L.problem)) return;
   const int64_t nn = L.g.nn();
   const float cp = c * L.inv_delta;
   for (int64_t node = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; node < nn; node += int64_t(gridDim.x) * blockDim.x)
@@ -205,8 +224,9 @@ __global__ void k_b_cheb_step(const BLev* __restrict__ S, float a, float c) {
 }
 
 // out = vec[asel] - vec[bsel]
-__global__ void k_b_sub(const BLev* __restrict__ S, int asel, int bsel, int osel) {
+__global__ void k_b_sub(const BLev* __restrict__ S, int asel, int bsel, int osel, Gate on) {
   const BLev& L = S[blockIdx.y];
+  if (!on(L.problem)) return;
   const int64_t n = NF * L.g.nn();
   const float* a = L.vec[asel];
   const float* b = L.vec[bsel];
@@ -215,23 +235,26 @@ __global__ void k_b_sub(const BLev* __restrict__ S, int asel, int bsel, int osel
     o[i] = a[i] - b[i];
 }
 
-__global__ void k_b_restrict(const BTr* __restrict__ T) {
+__global__ void k_b_restrict(const BTr* __restrict__ T, Gate on) {
   const BTr& t = T[blockIdx.y];
+  if (!on(t.problem)) return;
   const int64_t nnc = t.c.nn();
   for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < nnc; idx += int64_t(gridDim.x) * blockDim.x)
     restrict_node<float>(t.f, t.c, t.rf, t.mc, t.bc, idx);
 }
 
-__global__ void k_b_prolong(const BTr* __restrict__ T) {
+__global__ void k_b_prolong(const BTr* __restrict__ T, Gate on) {
   const BTr& t = T[blockIdx.y];
+  if (!on(t.problem)) return;
   const int64_t nnf = t.f.nn();
   for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < nnf; idx += int64_t(gridDim.x) * blockDim.x)
     prolong_node<float>(t.f, t.c, t.xc, t.mf, t.xf, idx);
 }
 
 // x = Kinv b, one warp per row; blockIdx.y = problem.
-__global__ void k_b_coarse_solve(const BCo* __restrict__ C) {
+__global__ void k_b_coarse_solve(const BCo* __restrict__ C, Gate on) {
   const BCo& c = C[blockIdx.y];
+  if (!on(c.problem)) return;
   const int lane = threadIdx.x & 31;
   for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < c.n; row += (gridDim.x * blockDim.x) >> 5) {
     const double* Ar = c.Kinv + int64_t(row) * c.n;
@@ -245,8 +268,9 @@ __global__ void k_b_coarse_solve(const BCo* __restrict__ C) {
 // ---------------------------------------------------------------------------
 // Linearisation kernels
 
-__global__ void k_b_inject(const BInj* __restrict__ I) {
+__global__ void k_b_inject(const BInj* __restrict__ I, Gate on) {
   const BInj& t = I[blockIdx.y];
+  if (!on(t.problem)) return;
   const int64_t nnc = t.c.nn();
   for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < nnc; idx += int64_t(gridDim.x) * blockDim.x) {
     inject_node(t.f, t.c, t.Uf, t.Uc, idx);
@@ -255,16 +279,18 @@ __global__ void k_b_inject(const BInj* __restrict__ I) {
 }
 
 template <typename TC>
-__global__ void __launch_bounds__(128) k_b_linearize(const BLin* __restrict__ S, int ns, int64_t nblk) {
+__global__ void __launch_bounds__(128) k_b_linearize(const BLin* __restrict__ S, int ns, int64_t nblk, Gate on) {
   const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t blk = tid >> 5;
   if (blk >= nblk) return;
   const BLin& L = S[find_entry(S, ns, blk)];
+  if (!on(L.problem)) return;
   linearize_lane<TC>(L.g, *L.P, L.U, L.Un, L.H64, L.H32, L.H32lo, blk - L.blk0, int(tid & 31));
 }
 
-__global__ void k_b_zero_D(const BBd* __restrict__ S) {
+__global__ void k_b_zero_D(const BBd* __restrict__ S, Gate on) {
   const BBd& L = S[blockIdx.y];
+  if (!on(L.problem)) return;
   const int64_t n = 81 * L.g.nn();
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     L.D[i] = 0.f;
@@ -282,24 +308,27 @@ __device__ __forceinline__ int find_elem(const S* __restrict__ set, int ns, int6
   return lo;
 }
 
-__global__ void __launch_bounds__(128) k_b_blockdiag(const BBd* __restrict__ S, int ns, int64_t ne) {
+__global__ void __launch_bounds__(128) k_b_blockdiag(const BBd* __restrict__ S, int ns, int64_t ne, Gate on) {
   const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t e = tid >> 3;
   if (e >= ne) return;
   const BBd& L = S[find_elem(S, ns, e)];
+  if (!on(L.problem)) return;
   blockdiag_elem_node<float>(L.g, L.jp, L.H, L.D, e - L.e0, int(tid & 7));
 }
 
-__global__ void k_b_block_invert(const BBd* __restrict__ S, int* singular) {
+__global__ void k_b_block_invert(const BBd* __restrict__ S, int* singular, Gate on) {
   const BBd& L = S[blockIdx.y];
+  if (!on(L.problem)) return;
   const int64_t nn = L.g.nn();
   for (int64_t node = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; node < nn; node += int64_t(gridDim.x) * blockDim.x)
     block_invert_node<float>(nn, L.mask, L.D, singular, node);
 }
 
 // power iteration: x = start vector
-__global__ void k_b_power_init(const BLev* __restrict__ S) {
+__global__ void k_b_power_init(const BLev* __restrict__ S, Gate on) {
   const BLev& L = S[blockIdx.y];
+  if (!on(L.problem)) return;
   const int64_t nn = L.g.nn();
   float* x = L.vec[VX];
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < NF * nn; i += int64_t(gridDim.x) * blockDim.x)
@@ -307,8 +336,9 @@ __global__ void k_b_power_init(const BLev* __restrict__ S) {
 }
 
 // r = D^-1 y (one point-block Jacobi step from zero)
-__global__ void k_b_dinv(const BLev* __restrict__ S) {
+__global__ void k_b_dinv(const BLev* __restrict__ S, Gate on) {
   const BLev& L = S[blockIdx.y];
+  if (!on(L.problem)) return;
   const int64_t nn = L.g.nn();
   const float* y = L.vec[VY];
   float* r = L.vec[VR];
@@ -327,9 +357,10 @@ __global__ void k_b_dinv(const BLev* __restrict__ S) {
 }
 
 // partial[(entry * BCH + chunk)] = sum over the chunk of vec[sel]^2 (FP64 accumulation)
-__global__ void __launch_bounds__(BT) k_b_norm2_32(const BLev* __restrict__ S, int sel, double* __restrict__ partial) {
+__global__ void __launch_bounds__(BT) k_b_norm2_32(const BLev* __restrict__ S, int sel, double* __restrict__ partial,
+                                                   Gate on) {
   const BLev& L = S[blockIdx.y];
-  const int64_t n = NF * L.g.nn();
+  const int64_t n = on(L.problem) ? NF * L.g.nn() : 0;
   const float* a = L.vec[sel];
   double acc = 0.0;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
@@ -355,8 +386,9 @@ __global__ void k_b_reduce_chunks(int ns, int chunks, const double* __restrict__
 }
 
 // x = r / sqrt(dot[entry])  (power iteration normalisation)
-__global__ void k_b_normalise(const BLev* __restrict__ S, int src, const double* __restrict__ dot) {
+__global__ void k_b_normalise(const BLev* __restrict__ S, int src, const double* __restrict__ dot, Gate on) {
   const BLev& L = S[blockIdx.y];
+  if (!on(L.problem)) return;
   const int64_t n = NF * L.g.nn();
   const double d = dot[blockIdx.y];
   const float s = d > 0.0 ? float(1.0 / sqrt(d)) : 0.f;
@@ -367,22 +399,23 @@ __global__ void k_b_normalise(const BLev* __restrict__ S, int src, const double*
 }
 
 // Gauss-Jordan over the batch: blockIdx.y = problem
-__global__ void k_b_gj_first_key(const BGj* __restrict__ G) {
+__global__ void k_b_gj_first_key(const BGj* __restrict__ G, Gate on) {
   const BGj& q = G[blockIdx.y];
+  if (!on(q.problem)) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < q.n; i += gridDim.x * blockDim.x)
     atomicMax(&q.keys[0], pivot_key(q.M[int64_t(i) * 2 * q.n], i));
 }
 
-__global__ void __launch_bounds__(256) k_b_gj_step(const BGj* __restrict__ G, int k, int* singular) {
+__global__ void __launch_bounds__(256) k_b_gj_step(const BGj* __restrict__ G, int k, int* singular, Gate on) {
   const BGj& q = G[blockIdx.y];
-  if (k >= q.n) return;
+  if (k >= q.n || !on(q.problem)) return;
   gj_step_row(q.M, q.n, 2 * q.n, k, q.keys, q.used, q.piv, singular, int(blockIdx.x), blockIdx.x == 0);
 }
 
-__global__ void k_b_gj_extract(const BGj* __restrict__ G) {
+__global__ void k_b_gj_extract(const BGj* __restrict__ G, Gate on) {
   const BGj& q = G[blockIdx.y];
   const int k = blockIdx.x;
-  if (k >= q.n) return;
+  if (k >= q.n || !on(q.problem)) return;
   const int p = q.piv[k];
   const double inv = 1.0 / q.M[int64_t(p) * 2 * q.n + k];
   for (int c = threadIdx.x; c < q.n; c += blockDim.x) q.Ainv[int64_t(k) * q.n + c] = q.M[int64_t(p) * 2 * q.n + q.n + c] * inv;
@@ -635,7 +668,7 @@ __global__ void k_b_cycle_state(BFgm* __restrict__ F, int np, const double* __re
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
   BFgm& s = F[p];
-  if (!(begin || s.restart)) return;
+  if (!s.restart) return;
   const double beta = sqrt(nrm2[int64_t(p) * stride]);
   s.restart = 0;
   if (begin) {
@@ -675,17 +708,29 @@ __global__ void k_b_cycle_state(BFgm* __restrict__ F, int np, const double* __re
   s.active = 1;
 }
 
-// V_0 = src / beta (src = b on the first cycle, r on a restart); x = 0 on the first
-__global__ void k_b_first_basis(const BOut* __restrict__ O, const BFgm* __restrict__ F, bool begin) {
+// V_0 = r / beta for problems that start a cycle
+__global__ void k_b_first_basis(const BOut* __restrict__ O, const BFgm* __restrict__ F) {
   const int p = blockIdx.y;
   if (!F[p].active) return;
   const BOut& o = O[p];
   const double s = F[p].hinv;
-  const double* src = begin ? o.b : o.r;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < o.n; i += int64_t(gridDim.x) * blockDim.x) {
-    o.V[i] = src[i] * s;
-    if (begin) o.x[i] = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < o.n; i += int64_t(gridDim.x) * blockDim.x)
+    o.V[i] = o.r[i] * s;
+}
+
+// start of a solve: the listed problems get x = 0 and the restart flag (their
+// first cycle is built from r = b like a restart); everything else is idle
+__global__ void k_b_begin(const BOut* __restrict__ O, BFgm* __restrict__ F, const int* __restrict__ act) {
+  const int p = blockIdx.y;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    F[p].restart = act[p];
+    F[p].active = 0;
+    F[p].upd = 0;
   }
+  if (!act[p]) return;
+  const BOut& o = O[p];
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < o.n; i += int64_t(gridDim.x) * blockDim.x)
+    o.x[i] = 0.0;
 }
 
 // b = -R (in place), ready for the solve
@@ -728,4 +773,767 @@ __global__ void __launch_bounds__(BT) k_b_res_norm2(const BOut* __restrict__ O, 
 }
 
 }  // namespace
+}  // namespace pfm
+
+// ===========================================================================
+// Host side of the engine
+
+namespace pfm {
+
+struct BatchEngine {
+  std::vector<uint64_t> sig;  // buffers and parameters the descriptors were built from
+  // options the captured graphs depend on
+  int m = 0, nu_pre = 0, nu_post = 0, max_lin_it = 0;
+  double lo = 0, hi = 0, growth = 0, rtol = 0;
+  cudaStream_t s = nullptr;
+  int np = 0, depth = 0;
+  std::vector<int> nlev;
+  struct DSet {
+    std::vector<BLev> S;
+    BLev* dS = nullptr;
+    int64_t nblk = 0, maxnn = 0;
+    std::vector<BTr> T;
+    BTr* dT = nullptr;
+    int64_t maxnnf = 0, maxnnc = 0;
+    std::vector<BCo> C;
+    BCo* dC = nullptr;
+    int maxn = 0;
+  };
+  std::vector<DSet> D;
+  std::vector<BLev> A;  // every non-coarsest level (power iteration)
+  BLev* dA = nullptr;
+  int64_t nblkA = 0, maxnnA = 0;
+  std::vector<std::pair<int, int>> Aidx;
+  std::vector<BLin> L64, L32;
+  BLin* dL64 = nullptr;
+  BLin* dL32 = nullptr;
+  int64_t nblk64 = 0, nblk32 = 0;
+  std::vector<std::vector<BInj>> Inj;
+  std::vector<BInj*> dInj;
+  std::vector<int64_t> maxnnInj;
+  std::vector<BBd> Bd;
+  BBd* dBd = nullptr;
+  int64_t neBd = 0, maxnnBd = 0;
+  std::vector<BGj> G;
+  BGj* dG = nullptr;
+  int maxnG = 0;
+  std::vector<BOut> O;
+  BOut* dO = nullptr;
+  int64_t nblkO = 0, maxnO = 0;
+  DevParams* dP = nullptr;
+  BFgm* dF = nullptr;
+  double *partial = nullptr, *h1 = nullptr, *h2 = nullptr, *hn = nullptr, *dots = nullptr;
+  int* flags = nullptr;
+  int* dact = nullptr;
+  int* singular = nullptr;
+  int* hflags = nullptr;   // pinned: active count, restart count
+  double* hres = nullptr;  // pinned: per-problem norms / lambda estimates
+  int* hact = nullptr;     // pinned: Newton activity
+  int grid_japply = 0, grid_df = 0, grid_j64 = 0;
+  cudaGraphExec_t vgraph = nullptr;
+  std::vector<cudaGraphExec_t> itg;
+  std::vector<int64_t> itg_launches;  // kernels in each iteration graph
+  std::vector<void*> dmem;
+
+  template <typename T>
+  cudaError_t alloc(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(T) * std::max<size_t>(count, 1));
+    if (e == cudaSuccess) dmem.push_back(q);
+    *p = static_cast<T*>(q);
+    return e;
+  }
+  template <typename T>
+  cudaError_t upload(T** dp, const std::vector<T>& v) {
+    if (v.empty()) {
+      *dp = nullptr;
+      return cudaSuccess;
+    }
+    cudaError_t e = alloc(dp, v.size());
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dp, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+  }
+  ~BatchEngine() {
+    if (vgraph) cudaGraphExecDestroy(vgraph);
+    for (auto g : itg)
+      if (g) cudaGraphExecDestroy(g);
+    for (void* q : dmem) cudaFree(q);
+    if (hflags) cudaFreeHost(hflags);
+    if (hres) cudaFreeHost(hres);
+    if (hact) cudaFreeHost(hact);
+  }
+  Gate gate_fgm() const { return Gate{&dF[0].active, int(sizeof(BFgm) / sizeof(int))}; }
+  Gate gate_act() const { return Gate{dact, 1}; }
+};
+
+void batch_engine_free(BatchEngine* e) { delete e; }
+
+namespace {
+
+#define BCK(call)                                                                                 \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      return b->fail(e_ == cudaErrorMemoryAllocation ? PFM_ERR_OOM : PFM_ERR_CUDA,                \
+                     std::string(#call) + ": " + cudaGetErrorString(e_));                         \
+  } while (0)
+
+int sm_count_b() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  return sms;
+}
+
+template <typename K>
+int persistent_blocks(K kernel, int threads, int64_t work_threads) {
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0);
+  const int64_t full = int64_t(sm_count_b()) * std::max(occ, 1);
+  const int64_t need = (work_threads + threads - 1) / threads;
+  return int(std::max<int64_t>(1, std::min(full, need)));
+}
+
+inline dim3 grid2(int64_t maxn, int ny) { return dim3(std::min<unsigned>(gdiv(maxn, BT), 1024u), unsigned(ny)); }
+
+// Per-handle buffers the engine uses, allocated on the handle (and kept).
+pfm_status engine_buffers(pfm_handle* h, int m) {
+  const size_t nl = h->L.size();
+  for (size_t l = 0; l < nl; ++l) {
+    Level& lv = h->L[l];
+    const size_t hsz = size_t(lv.nblk) * HBLK;
+    const bool fine = l == 0, coarsest = l + 1 == nl;
+    if (fine || coarsest) TRY(dalloc(h, &lv.H64, hsz));
+    if (fine || !coarsest) TRY(dalloc(h, &lv.H32, hsz));
+    if (fine) TRY(dalloc(h, &lv.H32lo, hsz));
+    if (!coarsest) TRY(dalloc(h, &lv.D32, size_t(81) * lv.nn));
+    TRY(dalloc(h, &lv.x32, ndof(lv)));
+    TRY(dalloc(h, &lv.b32, ndof(lv)));
+    TRY(dalloc(h, &lv.y32, ndof(lv)));
+    TRY(dalloc(h, &lv.r32, ndof(lv)));
+    TRY(dalloc(h, &lv.d32, ndof(lv)));
+  }
+  const int64_t n = ndof(h->L[0]);
+  if (h->kry_m < m || h->kry_prec != PFM_F32) {
+    dfree(h->V);
+    if (h->Z) cudaFree(h->Z);
+    h->Z = nullptr;
+    TRY(dalloc(h, &h->V, size_t(m + 1) * n));
+    float* z = nullptr;
+    TRY(dalloc(h, &z, size_t(m) * n));
+    h->Z = z;
+    h->kry_m = m;
+    h->kry_prec = PFM_F32;
+  }
+  return PFM_OK;
+}
+
+pfm_status engine_build(pfm_batch* b, const pfm_solve_opts& o, BatchEngine** out) {
+  auto E = new BatchEngine();
+  auto fail = [&](pfm_status st) {
+    delete E;
+    return st;
+  };
+  const int np = int(b->hs.size());
+  E->np = np;
+  E->s = b->streams[0];
+  E->m = o.restart;
+  E->nu_pre = o.nu_pre;
+  E->nu_post = o.nu_post;
+  E->lo = o.cheb_lo;
+  E->hi = o.cheb_hi;
+  E->growth = o.nu_growth > 0 ? o.nu_growth : 1.0;
+  E->max_lin_it = o.max_lin_it;
+  E->rtol = o.lin_rtol;
+  for (int p = 0; p < np; ++p) {
+    pfm_status st = engine_buffers(b->hs[p], o.restart);
+    if (st != PFM_OK) {
+      b->err = "problem " + std::to_string(p) + ": " + b->hs[p]->err;
+      return fail(st);
+    }
+    E->nlev.push_back(int(b->hs[p]->L.size()));
+    E->depth = std::max(E->depth, int(b->hs[p]->L.size()));
+  }
+  // parameters of every problem on the device
+  {
+    std::vector<DevParams> P(np);
+    for (int p = 0; p < np; ++p) P[p] = b->hs[p]->dp;
+    if (E->upload(&E->dP, P) != cudaSuccess) return fail(b->fail(PFM_ERR_OOM, "engine parameter table"));
+  }
+  E->D.resize(E->depth);
+  E->Inj.resize(E->depth);
+  for (int p = 0; p < np; ++p) {
+    pfm_handle* h = b->hs[p];
+    const int nl = E->nlev[p];
+    for (int l = 0; l < nl; ++l) {
+      Level& lv = h->L[l];
+      const bool coarsest = l + 1 == nl;
+      // linearisation: finest and coarsest levels in FP64, the others in FP32
+      BLin li{};
+      li.problem = p;
+      li.g = lv.g;
+      li.P = E->dP + p;
+      li.U = lv.U;
+      li.Un = lv.Un;
+      if (l == 0) {
+        li.H64 = lv.H64;
+        li.H32 = lv.H32;
+        li.H32lo = lv.H32lo;
+      } else if (coarsest) {
+        li.H64 = lv.H64;
+      } else {
+        li.H32 = lv.H32;
+      }
+      auto& Lset = (l == 0 || coarsest) ? E->L64 : E->L32;
+      auto& nb = (l == 0 || coarsest) ? E->nblk64 : E->nblk32;
+      li.blk0 = nb;
+      nb += lv.nblk;
+      Lset.push_back(li);
+      if (l > 0) {
+        Level& fl = h->L[l - 1];
+        E->Inj[l].push_back(BInj{p, fl.g, lv.g, fl.U, lv.U, fl.Un, lv.Un});
+      }
+      if (coarsest) {
+        E->D[l].C.push_back(BCo{p, h->nc_dofs, h->Kinv, lv.b32, lv.x32});
+        E->D[l].maxn = std::max(E->D[l].maxn, h->nc_dofs);
+        E->G.push_back(BGj{p, h->Kaug, h->nc_dofs, h->gj_keys, h->gj_used, h->gj_piv, h->Kinv});
+        E->maxnG = std::max(E->maxnG, h->nc_dofs);
+        continue;
+      }
+      BLev L{};
+      L.g = lv.g;
+      L.jp = make_jparams<float>(lv.g, h->dp);
+      L.mask = lv.mask;
+      L.H = lv.H32;
+      L.D = lv.D32;
+      L.vec[VX] = lv.x32;
+      L.vec[VB] = lv.b32;
+      L.vec[VY] = lv.y32;
+      L.vec[VR] = lv.r32;
+      L.vec[VD] = lv.d32;
+      L.problem = p;
+      auto& Ds = E->D[l];
+      L.blk0 = Ds.nblk;
+      Ds.nblk += lv.nblk;
+      Ds.maxnn = std::max(Ds.maxnn, lv.nn);
+      Ds.S.push_back(L);
+      L.blk0 = E->nblkA;
+      E->nblkA += lv.nblk;
+      E->maxnnA = std::max(E->maxnnA, lv.nn);
+      E->A.push_back(L);
+      E->Aidx.push_back({p, l});
+      Level& cv = h->L[l + 1];
+      Ds.T.push_back(BTr{p, lv.g, cv.g, lv.mask, cv.mask, lv.r32, cv.b32, cv.x32, lv.x32});
+      Ds.maxnnf = std::max(Ds.maxnnf, lv.nn);
+      Ds.maxnnc = std::max(Ds.maxnnc, cv.nn);
+      BBd bd{};
+      bd.problem = p;
+      bd.g = lv.g;
+      bd.jp = L.jp;
+      bd.H = lv.H32;
+      bd.D = lv.D32;
+      bd.mask = lv.mask;
+      bd.e0 = E->neBd;
+      E->neBd += lv.ne;
+      E->maxnnBd = std::max(E->maxnnBd, lv.nn);
+      E->Bd.push_back(bd);
+    }
+    Level& f = h->L[0];
+    if (!f.H32 || !f.H32lo || !f.H64 || !h->V || !h->Z || !h->Kinv) {
+      b->err = "problem " + std::to_string(p) + ": engine buffers missing";
+      return fail(PFM_ERR_STATE);
+    }
+    BOut ob{};
+    ob.g = f.g;
+    ob.n = ndof(f);
+    ob.dk = make_dfconst(f.g, h->dp);
+    ob.jp64 = make_jparams<double>(f.g, h->dp);
+    ob.Hhi = f.H32;
+    ob.Hlo = f.H32lo;
+    ob.H64 = f.H64;
+    ob.mask = f.mask;
+    ob.V = h->V;
+    ob.Z = static_cast<float*>(h->Z);
+    ob.w = h->wv;
+    ob.x = h->dU;
+    ob.b = h->R;
+    ob.r = h->rv;
+    ob.U = f.U;
+    ob.b32 = f.b32;
+    ob.x32 = f.x32;
+    ob.blk0 = E->nblkO;
+    E->nblkO += f.nblk;
+    E->maxnO = std::max(E->maxnO, ob.n);
+    E->O.push_back(ob);
+  }
+  for (int l = 1; l < E->depth; ++l) {
+    int64_t mx = 0;
+    for (auto& t : E->Inj[l]) mx = std::max(mx, t.c.nn());
+    E->maxnnInj.push_back(mx);
+  }
+  E->maxnnInj.insert(E->maxnnInj.begin(), 0);
+  cudaError_t e = cudaSuccess;
+  auto up = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  for (auto& Ds : E->D) {
+    up(E->upload(&Ds.dS, Ds.S));
+    up(E->upload(&Ds.dT, Ds.T));
+    up(E->upload(&Ds.dC, Ds.C));
+  }
+  E->dInj.assign(E->depth, nullptr);
+  for (int l = 1; l < E->depth; ++l) up(E->upload(&E->dInj[l], E->Inj[l]));
+  up(E->upload(&E->dA, E->A));
+  up(E->upload(&E->dL64, E->L64));
+  up(E->upload(&E->dL32, E->L32));
+  up(E->upload(&E->dBd, E->Bd));
+  up(E->upload(&E->dG, E->G));
+  up(E->upload(&E->dO, E->O));
+  const int stride = BMAXM + 1;
+  up(E->alloc(&E->dF, np));
+  up(E->alloc(&E->partial, size_t(std::max<size_t>(np, E->A.size())) * BCH * stride));
+  up(E->alloc(&E->h1, size_t(np) * stride));
+  up(E->alloc(&E->h2, size_t(np) * stride));
+  up(E->alloc(&E->hn, size_t(np) * stride));
+  up(E->alloc(&E->dots, std::max<size_t>(np, E->A.size())));
+  up(E->alloc(&E->flags, 2));
+  up(E->alloc(&E->dact, np));
+  up(E->alloc(&E->singular, 1));
+  if (e == cudaSuccess) e = cudaMemset(E->dF, 0, sizeof(BFgm) * np);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&E->hflags), sizeof(int) * 2);
+  if (e == cudaSuccess)
+    e = cudaMallocHost(reinterpret_cast<void**>(&E->hres), sizeof(double) * std::max<size_t>(np, E->A.size()));
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&E->hact), sizeof(int) * np);
+  if (e != cudaSuccess) return fail(b->fail(PFM_ERR_OOM, std::string("engine tables: ") + cudaGetErrorString(e)));
+  E->grid_japply = persistent_blocks(k_b_japply, 256, std::max<int64_t>(E->nblkA, 1) * 32);
+  E->grid_df = persistent_blocks(k_b_japply_df, 256, E->nblkO * 32);
+  E->grid_j64 = persistent_blocks(k_b_japply64, 256, E->nblkO * 32);
+  *out = E;
+  return PFM_OK;
+}
+
+// y = J v on every level of a set (identity rows first, then the elements)
+void eng_japply(BatchEngine* E, const BLev* dS, int ns, int64_t nblk, int64_t maxnn, int v, int y, Gate g) {
+  k_b_init<<<grid2(NF * maxnn, ns), BT, 0, E->s>>>(dS, v, y, g);
+  const int blocks = std::max(1, std::min<int>(E->grid_japply, int(gdiv(nblk * 32, 256))));
+  k_b_japply<<<blocks, 256, 0, E->s>>>(dS, ns, nblk, v, y, g);
+  count_launches(2);
+}
+
+// nu Chebyshev steps on depth d (the single-problem smoother, every problem at once)
+void eng_smooth(BatchEngine* E, int d, bool zero_x, int nu, bool want_res, Gate g) {
+  auto& Ds = E->D[d];
+  const int ns = int(Ds.S.size());
+  const dim3 gn = grid2(Ds.maxnn, ns), gv = grid2(NF * Ds.maxnn, ns);
+  const double sigma = (E->hi + E->lo) / (E->hi - E->lo);
+  double rho = 1.0 / sigma;
+  if (zero_x) {
+    k_b_cheb_first<<<gn, BT, 0, E->s>>>(Ds.dS, VB, true, true, g);
+    count_launches(1);
+  } else {
+    eng_japply(E, Ds.dS, ns, Ds.nblk, Ds.maxnn, VX, VY, g);
+    k_b_sub<<<gv, BT, 0, E->s>>>(Ds.dS, VB, VY, VR, g);
+    k_b_cheb_first<<<gn, BT, 0, E->s>>>(Ds.dS, VR, false, false, g);
+    count_launches(2);
+  }
+  for (int k = 1; k < nu; ++k) {
+    eng_japply(E, Ds.dS, ns, Ds.nblk, Ds.maxnn, VD, VY, g);
+    const double rho_n = 1.0 / (2.0 * sigma - rho);
+    k_b_cheb_step<<<gn, BT, 0, E->s>>>(Ds.dS, float(rho_n * rho), float(2.0 * rho_n), g);
+    count_launches(1);
+    rho = rho_n;
+  }
+  if (want_res) {
+    eng_japply(E, Ds.dS, ns, Ds.nblk, Ds.maxnn, VD, VY, g);
+    k_b_sub<<<gv, BT, 0, E->s>>>(Ds.dS, VR, VY, VR, g);
+    count_launches(1);
+  }
+}
+
+void eng_vcycle(BatchEngine* E, int d, Gate g) {
+  auto& Ds = E->D[d];
+  if (!Ds.C.empty()) {
+    k_b_coarse_solve<<<dim3(gdiv(int64_t(Ds.maxn) * 32, 256), unsigned(Ds.C.size())), 256, 0, E->s>>>(Ds.dC, g);
+    count_launches(1);
+  }
+  if (Ds.S.empty()) return;
+  const double gl = std::pow(E->growth, double(d));
+  const int nu_pre = std::max(1, int(std::lround(E->nu_pre * gl)));
+  const int nu_post = E->nu_post > 0 ? std::max(1, int(std::lround(E->nu_post * gl))) : 0;
+  const int ns = int(Ds.S.size());
+  eng_smooth(E, d, true, nu_pre, true, g);
+  k_b_restrict<<<grid2(Ds.maxnnc, ns), BT, 0, E->s>>>(Ds.dT, g);
+  count_launches(1);
+  eng_vcycle(E, d + 1, g);
+  k_b_prolong<<<grid2(Ds.maxnnf, ns), BT, 0, E->s>>>(Ds.dT, g);
+  count_launches(1);
+  if (nu_post > 0) eng_smooth(E, d, false, nu_post, false, g);
+}
+
+// Linearisation of every active problem (all levels), smoother eigenvalue
+// estimates, dense coarse inverses.
+pfm_status eng_linearize(pfm_batch* b, BatchEngine* E, int power_its) {
+  cudaStream_t s = E->s;
+  const Gate g = E->gate_act();
+  for (int l = 1; l < E->depth; ++l) {
+    if (E->Inj[l].empty()) continue;
+    k_b_inject<<<dim3(std::min<unsigned>(gdiv(E->maxnnInj[l], 128), 1024u), unsigned(E->Inj[l].size())), 128, 0, s>>>(
+        E->dInj[l], g);
+    count_launches(1);
+  }
+  BCK(cudaMemsetAsync(E->singular, 0, sizeof(int), s));
+  if (E->nblk64 > 0) {
+    k_b_linearize<double><<<gdiv(E->nblk64 * 32, 128), 128, 0, s>>>(E->dL64, int(E->L64.size()), E->nblk64, g);
+    count_launches(1);
+  }
+  if (E->nblk32 > 0) {
+    k_b_linearize<float><<<gdiv(E->nblk32 * 32, 128), 128, 0, s>>>(E->dL32, int(E->L32.size()), E->nblk32, g);
+    count_launches(1);
+  }
+  const int nA = int(E->A.size());
+  if (nA > 0) {
+    k_b_zero_D<<<grid2(81 * E->maxnnBd, nA), BT, 0, s>>>(E->dBd, g);
+    k_b_blockdiag<<<gdiv(E->neBd * 8, 128), 128, 0, s>>>(E->dBd, nA, E->neBd, g);
+    k_b_block_invert<<<grid2(E->maxnnBd, nA), BT, 0, s>>>(E->dBd, E->singular, g);
+    count_launches(3);
+    // power iteration for lambda_max(D^-1 J) on every non-coarsest level at once
+    const dim3 gv(BCH, unsigned(nA));
+    k_b_power_init<<<grid2(NF * E->maxnnA, nA), BT, 0, s>>>(E->dA, g);
+    k_b_norm2_32<<<gv, BT, 0, s>>>(E->dA, VX, E->partial, g);
+    k_b_reduce_chunks<<<gdiv(nA, 128), 128, 0, s>>>(nA, BCH, E->partial, E->dots);
+    k_b_normalise<<<grid2(NF * E->maxnnA, nA), BT, 0, s>>>(E->dA, VX, E->dots, g);
+    count_launches(4);
+    for (int it = 0; it < power_its; ++it) {
+      eng_japply(E, E->dA, nA, E->nblkA, E->maxnnA, VX, VY, g);
+      k_b_dinv<<<grid2(E->maxnnA, nA), BT, 0, s>>>(E->dA, g);
+      k_b_norm2_32<<<gv, BT, 0, s>>>(E->dA, VR, E->partial, g);
+      k_b_reduce_chunks<<<gdiv(nA, 128), 128, 0, s>>>(nA, BCH, E->partial, E->dots);
+      k_b_normalise<<<grid2(NF * E->maxnnA, nA), BT, 0, s>>>(E->dA, VR, E->dots, g);
+      count_launches(4);
+    }
+    BCK(cudaMemcpyAsync(E->hres, E->dots, sizeof(double) * nA, cudaMemcpyDeviceToHost, s));
+  }
+  // dense coarse operators (one assembly per problem) and their inverses (one launch per step for all)
+  for (int p = 0; p < E->np; ++p) {
+    if (!E->hact[p]) continue;
+    pfm_handle* h = b->hs[p];
+    Level& c = h->L.back();
+    launch_coarse_assemble<double>(c.g, h->dp, c.H64, c.mask, h->Kaug, 2 * h->nc_dofs, s);
+    BCK(cudaMemsetAsync(h->gj_keys, 0, sizeof(unsigned long long) * (h->nc_dofs + 1), s));
+    BCK(cudaMemsetAsync(h->gj_used, 0, sizeof(int) * h->nc_dofs, s));
+  }
+  const int nG = int(E->G.size());
+  k_b_gj_first_key<<<dim3(gdiv(E->maxnG, 256), unsigned(nG)), 256, 0, s>>>(E->dG, g);
+  count_launches(1);
+  for (int k = 0; k < E->maxnG; ++k) {
+    k_b_gj_step<<<dim3(unsigned(E->maxnG), unsigned(nG)), 256, 0, s>>>(E->dG, k, E->singular, g);
+    count_launches(1);
+  }
+  k_b_gj_extract<<<dim3(unsigned(E->maxnG), unsigned(nG)), 256, 0, s>>>(E->dG, g);
+  count_launches(1);
+  BCK(cudaGetLastError());
+  int sing = 0;
+  BCK(cudaMemcpyAsync(&sing, E->singular, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BCK(cudaStreamSynchronize(s));
+  if (sing) return b->fail(PFM_ERR_BREAKDOWN, "singular diagonal block or coarse operator in the batch");
+  // Chebyshev coefficients from the eigenvalue estimates
+  bool changed = false;
+  for (int i = 0; i < nA; ++i) {
+    const double dot = E->hres[i];
+    if (!(dot > 0.0) || !std::isfinite(dot)) {
+      if (!E->hact[E->Aidx[i].first]) continue;
+      return b->fail(PFM_ERR_BREAKDOWN, "smoother eigenvalue estimate failed for problem " +
+                                            std::to_string(E->Aidx[i].first));
+    }
+    if (!E->hact[E->Aidx[i].first]) continue;
+    const double lam = std::sqrt(dot);
+    const int p = E->Aidx[i].first, l = E->Aidx[i].second;
+    b->hs[p]->L[l].lam = lam;
+    const float it = float(2.0 / ((E->hi + E->lo) * lam)), id = float(2.0 / ((E->hi - E->lo) * lam));
+    for (auto& L : E->D[l].S)
+      if (L.problem == p) {
+        L.inv_theta = it;
+        L.inv_delta = id;
+      }
+    changed = true;
+  }
+  if (changed)
+    for (auto& Ds : E->D)
+      if (!Ds.S.empty())
+        BCK(cudaMemcpyAsync(Ds.dS, Ds.S.data(), sizeof(BLev) * Ds.S.size(), cudaMemcpyHostToDevice, s));
+  return PFM_OK;
+}
+
+// The fixed launch sequence of FGMRES iteration j for the whole batch:
+// z_j = M v_j (batched V-cycle), w = J z_j (double-float), two classical
+// Gram-Schmidt passes, ||w||, Givens update and decision, next basis vector,
+// solution update of finished problems, and the flag word to the host.
+void eng_iteration(BatchEngine* E, int j) {
+  cudaStream_t s = E->s;
+  const int np = E->np;
+  const int stride = BMAXM + 1;
+  const dim3 gv = grid2(E->maxnO, np);
+  const Gate g = E->gate_fgm();
+  k_b_cast_in<<<gv, BT, 0, s>>>(E->dO, E->dF, j);
+  count_launches(1);
+  eng_vcycle(E, 0, g);
+  k_b_store_z<<<gv, BT, 0, s>>>(E->dO, E->dF, j);
+  k_b_japply_df<<<E->grid_df, 256, 0, s>>>(E->dO, E->dF, np, E->nblkO, j);
+  count_launches(2);
+  const dim3 gc(BCH, unsigned(np));
+  for (double* h : {E->h1, E->h2}) {
+    for (int j0 = 0; j0 <= j; j0 += BMDOT) {
+      k_b_mdot<<<gc, BT, 0, s>>>(E->dO, E->dF, j0, std::min(BMDOT, j + 1 - j0), false, E->partial, stride);
+      count_launches(1);
+    }
+    k_b_mdot_final<<<dim3(1, unsigned(np)), 128, 0, s>>>(E->dF, j + 1, E->partial, stride, h);
+    k_b_maxpy<<<gv, BT, 0, s>>>(E->dO, E->dF, j + 1, h, stride);
+    count_launches(2);
+  }
+  k_b_mdot<<<gc, BT, 0, s>>>(E->dO, E->dF, 0, 1, true, E->partial, stride);
+  k_b_mdot_final<<<dim3(1, unsigned(np)), 128, 0, s>>>(E->dF, 1, E->partial, stride, E->hn);
+  k_b_givens<<<gdiv(np, 64), 64, 0, s>>>(E->dF, np, j, E->m, E->max_lin_it, E->h1, E->h2, E->hn, stride);
+  k_b_next_basis<<<gv, BT, 0, s>>>(E->dO, E->dF, j);
+  k_b_update<<<gv, BT, 0, s>>>(E->dO, E->dF);
+  k_b_count<<<1, 256, 0, s>>>(E->dF, np, E->flags);
+  count_launches(6);
+  cudaMemcpyAsync(E->hflags, E->flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, s);
+}
+
+// Start a cycle for every problem with the restart flag: from r = b (x = 0,
+// first cycle) or from the true residual r = b - J x (restart).
+void eng_cycle_start(BatchEngine* E, bool first) {
+  cudaStream_t s = E->s;
+  const int np = E->np;
+  const int stride = BMAXM + 1;
+  const dim3 gv = grid2(E->maxnO, np);
+  if (first) {
+    k_b_begin<<<gv, BT, 0, s>>>(E->dO, E->dF, E->dact);
+    count_launches(1);
+  }
+  k_b_restart_init<<<gv, BT, 0, s>>>(E->dO, E->dF);
+  count_launches(1);
+  if (!first) {
+    k_b_japply64<<<E->grid_j64, 256, 0, s>>>(E->dO, E->dF, np, E->nblkO);
+    count_launches(1);
+  }
+  k_b_restart_res<<<gv, BT, 0, s>>>(E->dO, E->dF);
+  k_b_mdot<<<dim3(BCH, unsigned(np)), BT, 0, s>>>(E->dO, E->dF, 0, 1, true, E->partial, stride);
+  k_b_mdot_final<<<dim3(1, unsigned(np)), 128, 0, s>>>(E->dF, 1, E->partial, stride, E->hn);
+  k_b_cycle_state<<<gdiv(np, 64), 64, 0, s>>>(E->dF, np, E->hn, stride, first, E->rtol, E->max_lin_it);
+  k_b_first_basis<<<gv, BT, 0, s>>>(E->dO, E->dF);
+  k_b_count<<<1, 256, 0, s>>>(E->dF, np, E->flags);
+  count_launches(6);
+  cudaMemcpyAsync(E->hflags, E->flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, s);
+}
+
+pfm_status eng_capture(pfm_batch* b, BatchEngine* E, int j, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  BCK(cudaStreamBeginCapture(E->s, cudaStreamCaptureModeThreadLocal));
+  const int64_t c0 = pfm_launch_count();
+  eng_iteration(E, j);
+  const int64_t nk = pfm_launch_count() - c0;  // counted again at every replay
+  count_launches(int(-nk));
+  E->itg_launches[j] = nk;
+  cudaError_t e = cudaStreamEndCapture(E->s, &graph);
+  if (e != cudaSuccess) return b->fail(PFM_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    return b->fail(PFM_ERR_CUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+  }
+  return PFM_OK;
+}
+
+// FGMRES for every problem with hact[p] (b = -R in o.b), until all finish.
+pfm_status eng_fgmres(pfm_batch* b, BatchEngine* E) {
+  cudaStream_t s = E->s;
+  eng_cycle_start(E, true);
+  BCK(cudaGetLastError());
+  BCK(cudaStreamSynchronize(s));
+  int j = 0;
+  if (E->itg.size() < size_t(E->m)) {
+    E->itg.resize(E->m, nullptr);
+    E->itg_launches.resize(E->m, 0);
+  }
+  while (E->hflags[0] > 0 || E->hflags[1] > 0) {
+    if (E->hflags[0] == 0) {  // every running cycle has ended: restart the ones that need it
+      eng_cycle_start(E, false);
+      BCK(cudaGetLastError());
+      BCK(cudaStreamSynchronize(s));
+      j = 0;
+      continue;
+    }
+    if (j >= E->m) return b->fail(PFM_ERR_CUDA, "batched FGMRES lost track of its cycle");
+    if (!E->itg[j]) TRY(eng_capture(b, E, j, &E->itg[j]));
+    BCK(cudaGraphLaunch(E->itg[j], s));
+    count_launches(int(E->itg_launches[j]));
+    BCK(cudaStreamSynchronize(s));
+    ++j;
+  }
+  return PFM_OK;
+}
+
+pfm_status eng_residual_norms(pfm_batch* b, BatchEngine* E) {
+  cudaStream_t s = E->s;
+  for (int p = 0; p < E->np; ++p) {
+    if (!E->hact[p]) continue;
+    pfm_handle* h = b->hs[p];
+    Level& f = h->L[0];
+    BCK(cudaMemsetAsync(h->R, 0, sizeof(double) * ndof(f), s));
+    launch_residual(f.g, h->dp, f.U, f.Un, f.mask, h->R, nullptr, s);
+  }
+  k_b_res_norm2<<<dim3(BCH, unsigned(E->np)), BT, 0, s>>>(E->dO, E->dact, E->partial);
+  k_b_reduce_chunks<<<gdiv(E->np, 128), 128, 0, s>>>(E->np, BCH, E->partial, E->dots);
+  count_launches(2);
+  BCK(cudaMemcpyAsync(E->hres, E->dots, sizeof(double) * E->np, cudaMemcpyDeviceToHost, s));
+  BCK(cudaGetLastError());
+  BCK(cudaStreamSynchronize(s));
+  return PFM_OK;
+}
+
+// Everything the engine's descriptor tables and graphs capture: the device
+// buffers of every handle and a hash of its parameters.
+std::vector<uint64_t> engine_signature(const pfm_batch* b) {
+  std::vector<uint64_t> sig;
+  auto add = [&](const void* q) { sig.push_back(uint64_t(reinterpret_cast<uintptr_t>(q))); };
+  for (const pfm_handle* h : b->hs) {
+    for (const Level& lv : h->L) {
+      add(lv.U); add(lv.Un); add(lv.mask); add(lv.H64); add(lv.H32); add(lv.H32lo); add(lv.D32);
+      add(lv.x32); add(lv.b32); add(lv.y32); add(lv.r32); add(lv.d32);
+    }
+    add(h->V); add(h->Z); add(h->wv); add(h->dU); add(h->R); add(h->rv); add(h->Kaug); add(h->Kinv);
+    add(h->gj_keys); add(h->gj_used); add(h->gj_piv);
+    uint64_t x = 1469598103934665603ull;  // FNV-1a over the parameter block
+    const unsigned char* c = reinterpret_cast<const unsigned char*>(&h->dp);
+    for (size_t i = 0; i < sizeof(DevParams); ++i) x = (x ^ c[i]) * 1099511628211ull;
+    sig.push_back(x);
+  }
+  return sig;
+}
+
+bool engine_matches(const BatchEngine* E, const pfm_solve_opts& o) {
+  return E->m == o.restart && E->nu_pre == o.nu_pre && E->nu_post == o.nu_post && E->lo == o.cheb_lo &&
+         E->hi == o.cheb_hi && E->growth == (o.nu_growth > 0 ? o.nu_growth : 1.0) &&
+         E->max_lin_it == o.max_lin_it && E->rtol == o.lin_rtol;
+}
+
+}  // namespace
+
+bool batch_engine_supports(const pfm_solve_opts& o, const pfm_batch* b) {
+  if (o.precond != PFM_F32 || o.smoother != 0 || (o.cycle_gamma > 1) || o.restart > BMAXM) return false;
+  for (const pfm_handle* h : b->hs)
+    if (!h->outer_df) return false;
+  return true;
+}
+
+// Newton solve of every problem of the batch with the engine (pfm_batch_newton_solve).
+pfm_status batch_engine_newton(pfm_batch* b, const pfm_solve_opts& o, double* const* U_inout,
+                               pfm_solve_report* reports) {
+  const int np = int(b->hs.size());
+  for (int p = 0; p < np; ++p) {
+    pfm_status st = engine_buffers(b->hs[p], o.restart);
+    if (st != PFM_OK) return b->fail(st, "problem " + std::to_string(p) + ": " + b->hs[p]->err);
+  }
+  std::vector<uint64_t> sig = engine_signature(b);
+  if (b->engine && (!engine_matches(b->engine, o) || b->engine->sig != sig)) {
+    batch_engine_free(b->engine);
+    b->engine = nullptr;
+  }
+  if (!b->engine) {
+    TRY(engine_build(b, o, &b->engine));
+    b->engine->sig = sig;
+  }
+  const double t_start = now_ms();
+  BatchEngine* E = b->engine;
+  cudaStream_t s = E->s;
+  std::vector<pfm_solve_report> rep(np);
+  for (int p = 0; p < np; ++p) {
+    pfm_handle* h = b->hs[p];
+    Level& f = h->L[0];
+    BCK(cudaMemcpyAsync(f.U, U_inout[p], sizeof(double) * ndof(f), cudaMemcpyDeviceToDevice, s));
+    if (h->have_dirval) launch_mask_values(f.nn, f.mask, h->dirval, f.U, s);
+    h->linearized = false;
+    E->hact[p] = 1;
+  }
+  BCK(cudaMemcpyAsync(E->dact, E->hact, sizeof(int) * np, cudaMemcpyHostToDevice, s));
+  double t0 = now_ms();
+  TRY(eng_residual_norms(b, E));
+  std::vector<double> res(np);
+  for (int p = 0; p < np; ++p) {
+    res[p] = std::sqrt(E->hres[p]);
+    rep[p].res0 = res[p];
+    rep[p].ms_residual += now_ms() - t0;
+  }
+  std::vector<BFgm> Fh(np);
+  for (int it = 0; it < o.max_newton; ++it) {
+    int nact = 0;
+    for (int p = 0; p < np; ++p) {
+      bool a = true;
+      if (!std::isfinite(res[p])) {
+        rep[p].status = PFM_ERR_NONFINITE;
+        a = false;
+      } else if (res[p] == 0.0 || (it > 0 && res[p] <= o.newton_rtol * rep[p].res0)) {
+        a = false;
+      }
+      E->hact[p] = a ? 1 : 0;
+      nact += a;
+    }
+    if (nact == 0) break;
+    BCK(cudaMemcpyAsync(E->dact, E->hact, sizeof(int) * np, cudaMemcpyHostToDevice, s));
+    t0 = now_ms();
+    TRY(eng_linearize(b, E, b->hs[0]->power_its));
+    const double ms_lin = now_ms() - t0;
+    t0 = now_ms();
+    k_b_negate<<<grid2(E->maxnO, np), BT, 0, s>>>(E->dO, E->dact);
+    count_launches(1);
+    TRY(eng_fgmres(b, E));
+    k_b_newton_update<<<grid2(E->maxnO, np), BT, 0, s>>>(E->dO, E->dact);
+    count_launches(1);
+    BCK(cudaMemcpy2DAsync(Fh.data(), sizeof(BFgm), E->dF, sizeof(BFgm), offsetof(BFgm, H), np,
+                          cudaMemcpyDeviceToHost, s));
+    BCK(cudaStreamSynchronize(s));
+    const double ms_solve = now_ms() - t0;
+    for (int p = 0; p < np; ++p) {
+      if (!E->hact[p]) continue;
+      rep[p].ms_linearize += ms_lin;
+      rep[p].ms_solve += ms_solve;
+      rep[p].lin_its_total += Fh[p].total;
+      rep[p].lin_its_last = Fh[p].total;
+      rep[p].lin_res_final = Fh[p].relres;
+      if (Fh[p].status == BF_NONFINITE) rep[p].status = PFM_ERR_NONFINITE;
+      else if (Fh[p].status == BF_BREAKDOWN) rep[p].status = PFM_ERR_BREAKDOWN;
+      else if (!Fh[p].converged) rep[p].status = PFM_ERR_NOT_CONVERGED;
+      ++rep[p].newton_its;
+    }
+    t0 = now_ms();
+    TRY(eng_residual_norms(b, E));
+    for (int p = 0; p < np; ++p)
+      if (E->hact[p]) {
+        res[p] = std::sqrt(E->hres[p]);
+        rep[p].ms_residual += now_ms() - t0;
+      }
+  }
+  for (int p = 0; p < np; ++p) {
+    pfm_handle* h = b->hs[p];
+    BCK(cudaMemcpyAsync(U_inout[p], h->L[0].U, sizeof(double) * ndof(h->L[0]), cudaMemcpyDeviceToDevice, s));
+    rep[p].res_final = res[p];
+    if (rep[p].status == PFM_OK && o.max_newton > 1 && !(res[p] <= o.newton_rtol * rep[p].res0) && res[p] != 0.0)
+      rep[p].status = PFM_ERR_NOT_CONVERGED;
+    h->linearized = false;
+  }
+  BCK(cudaStreamSynchronize(s));
+  const double total = now_ms() - t_start;
+  for (int p = 0; p < np; ++p) rep[p].ms_total = total;
+  if (reports)
+    for (int p = 0; p < np; ++p) reports[p] = rep[p];
+  for (int p = 0; p < np; ++p)
+    if (rep[p].status != PFM_OK) return b->fail(rep[p].status, "problem " + std::to_string(p) + " did not converge");
+  return PFM_OK;
+}
+
 }  // namespace pfm

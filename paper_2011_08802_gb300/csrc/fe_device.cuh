@@ -276,6 +276,20 @@ __device__ __forceinline__ void block_invert_node(int64_t nn, const dmask_t* __r
     for (int c = 0; c < 9; ++c) D[(r * 9 + c) * nn + node] = x[r][c];
 }
 
+// Element constants of a level: gradient-energy matrix, quadrature weight and
+// inverse spacings (host-side construction).
+template <typename T>
+inline JParams<T> make_jparams(const Grid& g, const DevParams& P) {
+  JParams<T> jp;
+  for (int k = 0; k < 6; ++k)
+    for (int l = 0; l < 6; ++l) jp.G[k][l] = T(P.G[k][l]);
+  jp.w = T(g.w());
+  jp.ihx = T(1.0 / g.hx);
+  jp.ihy = T(1.0 / g.hy);
+  jp.ihz = T(1.0 / g.hz);
+  return jp;
+}
+
 // ---- BEGIN tangent application kernel
 // y += J v on the 4 elements of block blk (this warp; lane = 0..31): gather v
 // at the element nodes (Dirichlet DOFs read as 0), dz = (grad du, d eta_hat)
@@ -425,6 +439,19 @@ __device__ __forceinline__ dfl q1_scatter_df(dfl val, dfl gx, dfl gy, dfl gz, bo
   dfl sC = df_shx(Cc, 1), sD = df_shx(Dx, 1);
   return df_add(df_add(df_mul(k.gb, Cc), df_mul(k.ga, sC)),
                 df_mul((l8 & 1) ? df_add(Dx, sD) : df_neg(df_add(Dx, sD)), k.ihx));
+}
+
+inline DfConst make_dfconst(const Grid& g, const DevParams& P) {
+  DfConst k;
+  k.ga = df_host(GA);
+  k.gb = df_host(GB);
+  k.ihx = df_host(1.0 / g.hx);
+  k.ihy = df_host(1.0 / g.hy);
+  k.ihz = df_host(1.0 / g.hz);
+  k.w = df_host(g.w());
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 6; ++b) k.G[a][b] = df_host(P.G[a][b]);
+  return k;
 }
 
 // y += J v on element block blk in double-float arithmetic: v in FP32

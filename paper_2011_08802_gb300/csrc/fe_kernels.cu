@@ -193,18 +193,6 @@ __global__ void k_qp_eval(DevParams P, int64_t n, const double* __restrict__ F,
     for (int k = 0; k < NH; ++k) hess[i * NH + k] = h[k];
 }
 
-template <typename T>
-JParams<T> make_jparams(const Grid& g, const DevParams& P) {
-  JParams<T> jp;
-  for (int k = 0; k < 6; ++k)
-    for (int l = 0; l < 6; ++l) jp.G[k][l] = T(P.G[k][l]);
-  jp.w = T(g.w());
-  jp.ihx = T(1.0 / g.hx);
-  jp.ihy = T(1.0 / g.hy);
-  jp.ihz = T(1.0 / g.hz);
-  return jp;
-}
-
 inline unsigned grid_for(int64_t threads, int block) {
   return unsigned((threads + block - 1) / block);
 }
@@ -350,15 +338,7 @@ void launch_japply(const Grid& g, const DevParams& P, const T* H, const dmask_t*
 
 void launch_japply_df(const Grid& g, const DevParams& P, const float* Hhi, const float* Hlo, const dmask_t* mask,
                       const float* v, double* y, cudaStream_t s) {
-  DfConst k;
-  k.ga = df_host(GA);
-  k.gb = df_host(GB);
-  k.ihx = df_host(1.0 / g.hx);
-  k.ihy = df_host(1.0 / g.hy);
-  k.ihz = df_host(1.0 / g.hz);
-  k.w = df_host(g.w());
-  for (int a = 0; a < 6; ++a)
-    for (int b = 0; b < 6; ++b) k.G[a][b] = df_host(P.G[a][b]);
+  const DfConst k = make_dfconst(g, P);
   const int64_t nn = g.nn();
   k_japply_init_df<<<grid_for(NF * nn, 256) < 4096 ? grid_for(NF * nn, 256) : 4096, 256, 0, s>>>(nn, mask, v, y);
   count_launches(1);

@@ -119,15 +119,20 @@ struct pfm_handle {
 };
 
 
+struct pfm_batch;
 namespace pfm {
 struct BatchEngine;  // batched multigrid/FGMRES engine (batch.cu)
 void batch_engine_free(BatchEngine* e);
+bool batch_engine_supports(const pfm_solve_opts& o, const pfm_batch* b);
+pfm_status batch_engine_newton(pfm_batch* b, const pfm_solve_opts& o, double* const* U_inout,
+                               pfm_solve_report* reports);
 }  // namespace pfm
 
 struct pfm_batch {
   std::vector<pfm_handle*> hs;
   std::vector<cudaStream_t> streams;
   std::string err;
+  int mode = 0;  // 0: batched engine where supported; 1: per-problem lockstep driver
   pfm::BatchEngine* engine = nullptr;
   pfm_status fail(pfm_status st, const std::string& m) {
     err = m;

@@ -70,3 +70,59 @@ def test_batch_member_matches_oracle(binding):
     assert res <= 1e-8, res
     assert np.linalg.norm(x - dU) <= 1e-6 * np.linalg.norm(dU)
     assert reps[0].newton_its == 1 and reps[1].newton_its == 1
+
+
+def _uneven():
+    """A single-level 4^3 problem (coarse solve only), non-nested 5^3 and 9^3
+    hierarchies, and three sizes of the seeded batch distribution."""
+    sts = [inputs.config_indentation(n, seed=2000 + n, step=1, n_steps=10, depth_frac=0.02)
+           for n in (4, 5, 9)]
+    return sts + _states()[:3]
+
+
+@pytest.mark.parametrize("restart", [30, 3])
+def test_engine_matches_lockstep_driver(binding, restart):
+    """The batched engine (every phase one launch over all problems, graph
+    replayed iterations) and the per-problem lockstep driver give the same
+    Newton iterates to the solve tolerance; restart = 3 forces restarts."""
+    sts = _uneven()
+    opts = abi.default_opts(abi.PFM_F32, max_newton=2, restart=restart, lin_rtol=1e-10, max_lin_it=600)
+    out = []
+    for mode in (0, 1):
+        probs = [binding.problem_from_state(st) for st in sts]
+        B = binding.Batch(probs)
+        B.set_mode(mode)
+        Us = [torch.from_numpy(st.U.copy()).cuda() for st in sts]
+        # two Newton corrections (not yet at newton_rtol, so the status says
+        # NOT_CONVERGED); every linear solve met its tolerance
+        reps = B.newton_solve(Us, opts, check=False)
+        assert all(r.newton_its == 2 and r.lin_res_final <= 1e-10 for r in reps), \
+            [(r.newton_its, r.lin_res_final) for r in reps]
+        out.append(([u.cpu().numpy() for u in Us], [r.lin_its_total for r in reps]))
+        B.close()
+        for P in probs:
+            P.close()
+    for k, st in enumerate(sts):
+        d0, d1 = out[0][0][k] - st.U, out[1][0][k] - st.U
+        assert np.linalg.norm(d0 - d1) <= 1e-6 * np.linalg.norm(d1), k
+    if restart == 3:
+        assert max(out[0][1]) > 6  # at least one problem went through restarts
+
+
+def test_engine_newton_converges_and_reuses_graphs(binding):
+    """Several Newton iterations to newton_rtol with the engine; a second call
+    on the same batch reuses the engine and gives the same result."""
+    sts = _uneven()
+    opts = abi.default_opts(abi.PFM_F32, max_newton=8, newton_rtol=1e-9, lin_rtol=1e-8, max_lin_it=400)
+    probs = [binding.problem_from_state(st) for st in sts]
+    B = binding.Batch(probs)
+    results = []
+    for _ in range(2):
+        Us = [torch.from_numpy(st.U.copy()).cuda() for st in sts]
+        reps = B.newton_solve(Us, opts)
+        assert all(r.res_final <= 1e-9 * r.res0 for r in reps)
+        results.append([u.cpu().numpy() for u in Us])
+    # atomics in the FP32 preconditioner change rounding between the two runs
+    for a, c in zip(*results):
+        assert np.linalg.norm(a - c) <= 1e-7 * np.linalg.norm(a)
+    B.close()

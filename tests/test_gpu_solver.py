@@ -113,3 +113,18 @@ def test_newton_converges_quadratically(binding):
     # once in the basin, one correction squares the relative error
     ratios = [norms[k + 1] / norms[k] for k in range(1, 4)]
     assert min(ratios) < 1e-5, norms
+
+
+@pytest.mark.parametrize("prec", [abi.PFM_F32, abi.PFM_F64])
+def test_single_level_grid(binding, prec):
+    """A 4^3 grid is its own coarsest level: the preconditioner is the dense
+    coarse solve, and the mixed solve's double-float outer operator still has
+    its FP32 Hessian pair on that level."""
+    st = inputs.config_indentation(4, seed=11, step=1)
+    K, R, dU = _oracle(st)
+    P = binding.problem_from_state(st)
+    assert P.n_levels == 1
+    P.linearize(prec)
+    x, rep = P.fgmres_solve(-P.residual(), abi.default_opts(prec, lin_rtol=1e-10))
+    _check_solution(K, R, x.cpu().numpy(), dU)
+    assert rep.lin_its_last <= 3

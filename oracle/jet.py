@@ -103,6 +103,17 @@ class Jet:
                 - (r * r)[..., None, None] * self.H
         return Jet(r, g, H)
 
+    def sqrt(self) -> "Jet":
+        """sqrt(x) by the chain rule (x > 0)."""
+        r = np.sqrt(self.v)
+        d1 = 0.5 / r
+        g = d1[..., None] * self.g
+        H = None
+        if self.H is not None:
+            d2 = -0.25 / (r * self.v)
+            H = d1[..., None, None] * self.H + d2[..., None, None] * self.g[..., :, None] * self.g[..., None, :]
+        return Jet(r, g, H)
+
     def __truediv__(self, o):
         if isinstance(o, Jet):
             return self * o.reciprocal()

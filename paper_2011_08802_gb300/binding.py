@@ -283,6 +283,17 @@ def launch_count() -> int:
     return int(abi.lib().pfm_launch_count())
 
 
+def levels_to(n: int, coarsest: int = 4) -> int:
+    """Number of levels of the ceil-halving hierarchy of an n-element edge
+    down to the first level with at most ``coarsest`` elements per edge (the
+    library's default is coarsest = 4)."""
+    levels = 1
+    while n > coarsest and n > 1:
+        n = (n + 1) // 2
+        levels += 1
+    return levels
+
+
 def problem_from_state(state, n_levels: int = 0, params: abi.Params | None = None) -> Problem:
     """Create a handle for an ``inputs.State`` and load its mask and state."""
     m = state.mesh

@@ -168,6 +168,26 @@ pfm_status pfm_set_state(pfm_handle* h, const double* U_dev, const double* Un_de
 /* Copy the handle's current iterate to U_dev (device, double [9][n_nodes]). */
 pfm_status pfm_get_state(pfm_handle* h, double* U_dev);
 
+/* Frictionless penalty contact with a rigid sphere (Sec. 2.5, Eq. Ngap, the
+ * contact term of Eq. PenPot) on the top face z = Lz: a point X of that face
+ * at x = X + u has the normal gap g = |x - c| - R to the sphere of centre
+ * center[3] (host array, nm) and radius R, and the potential gains
+ * int 1/2 eps_N <g>_-^2 dS over the reference face (2x2 Gauss per face quad).
+ * The term enters the residual, the energy, every tangent application
+ * (FP32, FP64, double-float), the block diagonal and the dense coarse
+ * operator of every level (re-discretised like the volume terms). radius <= 0
+ * switches contact off. Batches that contain a problem with contact use the
+ * lockstep driver. Errors: PFM_ERR_INVALID_ARG (missing centre, eps_N <= 0,
+ * non-finite values). */
+pfm_status pfm_set_contact(pfm_handle* h, const double* center, double radius, double eps_N);
+
+/* Indenter load P = int eps_N <g>_- nbar_z dS (the vertical force the body
+ * exerts on the sphere, positive when pressing; equal to the derivative of
+ * the contact energy with respect to the indentation depth) and the contact
+ * energy at the current iterate, written to *load_host and (if not NULL)
+ * *energy_host; 0 without contact. Synchronises. */
+pfm_status pfm_contact_load(pfm_handle* h, double* load_host, double* energy_host);
+
 /* Microstructure diagnostics of Sec. 5.3 of the nodal state U_dev (device,
  * double [9][n_nodes]; NULL = the handle's current iterate), with
  * eta_0 = 1 - sum_{k>=1} eta_k at every node:

@@ -126,6 +126,18 @@ class Problem:
         self._check(self._lib.pfm_residual(self.h, _ptr(R), C.byref(e) if energy else None))
         return (R, e.value) if energy else R
 
+    def set_contact(self, center, radius: float, eps_N: float):
+        """``pfm_set_contact``: rigid sphere (centre, radius) pressed on the top
+        face with penalty eps_N; radius <= 0 switches contact off."""
+        c = (C.c_double * 3)(*[float(x) for x in center])
+        self._check(self._lib.pfm_set_contact(self.h, c, float(radius), float(eps_N)))
+
+    def contact_load(self):
+        """``pfm_contact_load``: (indenter load P, contact energy) at the current iterate."""
+        P, E = C.c_double(), C.c_double()
+        self._check(self._lib.pfm_contact_load(self.h, C.byref(P), C.byref(E)))
+        return P.value, E.value
+
     def diagnostics(self, U: torch.Tensor | None = None, per_node: bool = True):
         """``pfm_diagnostics``: violation index I_v, diffuseness index I_d and
         eta* = eta_3 - eta_1 per node (if ``per_node``) and the per-plane

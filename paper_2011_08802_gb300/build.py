@@ -10,8 +10,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
-SOURCES = ["fe_kernels.cu", "mg_kernels.cu", "krylov_kernels.cu", "diag_kernels.cu", "batch.cu", "api.cu",
-           "noalloc.cu"]
+SOURCES = ["fe_kernels.cu", "mg_kernels.cu", "krylov_kernels.cu", "diag_kernels.cu", "contact_kernels.cu",
+           "batch.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -65,6 +65,7 @@ void japply_level(pfm_handle* h, size_t l, const T* H, const T* x, T* y) {
   Level& lv = h->L[l];
   ProfScope ps(h, sizeof(T) == 4 ? PFM_PROF_JAPPLY_F32 : PFM_PROF_JAPPLY_F64, l == 0);
   launch_japply<T>(lv.g, h->dp, H, lv.mask, x, y, h->stream);
+  if (h->contact_on) launch_contact_apply<T, T, T>(lv.g, LvVec<T>::Kc(lv), lv.mask, x, y, h->stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -216,6 +217,7 @@ pfm_status estimate_lambda(pfm_handle* h, size_t l) {
   launch_scale_inv_sqrt<T>(n, x, h->hdev, x, s);
   for (int it = 0; it < h->power_its; ++it) {
     launch_japply<T>(lv.g, h->dp, H, lv.mask, x, y, s);
+    if (h->contact_on) launch_contact_apply<T, T, T>(lv.g, LvVec<T>::Kc(lv), lv.mask, x, y, s);
     CK(cudaMemsetAsync(z, 0, sizeof(T) * n, s));
     launch_smooth<T>(lv.nn, D, y, nullptr, T(1), z, s);
     launch_dot<T>(n, z, z, h->partial, h->hdev, s);
@@ -256,6 +258,7 @@ pfm_status residual_impl(pfm_handle* h, double* R, double* energy_host) {
   {
     ProfScope ps(h, PFM_PROF_RESIDUAL);
     launch_residual(f.g, h->dp, f.U, f.Un, f.mask, R, h->energy_dev, s);
+    if (h->contact_on) launch_contact_residual(f.g, h->contact, f.U, f.mask, R, h->energy_dev, nullptr, s);
   }
   CKL();
   if (energy_host) {
@@ -308,11 +311,17 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
       launch_linearize(lv.g, h->dp, lv.U, lv.Un, need64 ? lv.H64 : nullptr, need32 ? lv.H32 : nullptr,
                        needlo ? lv.H32lo : nullptr, fp32_compute, s);
     }
+    if (h->contact_on) {
+      TRY(dalloc(h, &lv.Kc64, size_t(6) * contact_points(lv.g)));
+      TRY(dalloc(h, &lv.Kc32, size_t(6) * contact_points(lv.g)));
+      launch_contact_linearize(lv.g, h->contact, lv.U, lv.Kc64, lv.Kc32, s);
+    }
     CKL();
     if (coarsest) continue;
     if (prec == PFM_F32) {
       TRY(dalloc(h, &lv.D32, size_t(81) * lv.nn));
       launch_blockdiag<float>(lv.g, h->dp, lv.H32, lv.mask, lv.D32, s);
+      if (h->contact_on) launch_contact_blockdiag<float>(lv.g, lv.Kc32, lv.D32, s);
       launch_block_invert<float>(lv.nn, lv.mask, lv.D32, h->flag_dev, s);
       CKL();
       TRY(ensure_level_vectors<float>(h));
@@ -320,6 +329,7 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
     } else {
       TRY(dalloc(h, &lv.D64, size_t(81) * lv.nn));
       launch_blockdiag<double>(lv.g, h->dp, lv.H64, lv.mask, lv.D64, s);
+      if (h->contact_on) launch_contact_blockdiag<double>(lv.g, lv.Kc64, lv.D64, s);
       launch_block_invert<double>(lv.nn, lv.mask, lv.D64, h->flag_dev, s);
       CKL();
       TRY(ensure_level_vectors<double>(h));
@@ -328,6 +338,7 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
   }
   Level& c = h->L[nl - 1];
   launch_coarse_assemble<double>(c.g, h->dp, c.H64, c.mask, h->Kaug, 2 * h->nc_dofs, s);
+  if (h->contact_on) launch_contact_coarse(c.g, c.Kc64, c.mask, h->Kaug, 2 * h->nc_dofs, s);
   dense_gauss_jordan_inverse(h->Kaug, h->nc_dofs, h->Kinv, h->gj_keys, h->gj_used, h->gj_piv, h->flag_dev, s);
   CKL();
   int flag = 0;
@@ -487,6 +498,7 @@ pfm_status fgm_enqueue(pfm_handle* h, Fgm& F) {
     if (h->outer_df) {
       ProfScope ps(h, PFM_PROF_JAPPLY_F64);
       launch_japply_df(fl.g, h->dp, fl.H32, fl.H32lo, fl.mask, zj, h->wv, s);
+      if (h->contact_on) launch_contact_apply<double, float, double>(fl.g, fl.Kc64, fl.mask, zj, h->wv, s);
     } else {
       launch_cast_f2d(n, zj, h->zd, s);
       TRY(japply_impl<double>(h, h->zd, h->wv));
@@ -760,9 +772,9 @@ void pfm_destroy(pfm_handle* h) {
     dfree(lv.U); dfree(lv.Un); dfree(lv.mask); dfree(lv.H64); dfree(lv.H32); dfree(lv.H32lo); dfree(lv.D64);
     dfree(lv.D32);
     dfree(lv.x32); dfree(lv.b32); dfree(lv.y32); dfree(lv.x64); dfree(lv.b64); dfree(lv.y64);
-    dfree(lv.r32); dfree(lv.d32); dfree(lv.r64); dfree(lv.d64);
+    dfree(lv.r32); dfree(lv.d32); dfree(lv.r64); dfree(lv.d64); dfree(lv.Kc64); dfree(lv.Kc32);
   }
-  dfree(h->dirval); dfree(h->energy_dev); dfree(h->flag_dev); dfree(h->diag_part); dfree(h->R); dfree(h->dU); dfree(h->wv);
+  dfree(h->dirval); dfree(h->energy_dev); dfree(h->flag_dev); dfree(h->diag_part); dfree(h->load_dev); dfree(h->R); dfree(h->dU); dfree(h->wv);
   dfree(h->rv); dfree(h->zd); dfree(h->partial); dfree(h->hdev); dfree(h->V); dfree(h->Kaug); dfree(h->Kinv);
   dfree(h->gj_keys); dfree(h->gj_used); dfree(h->gj_piv);
   if (h->Z) cudaFree(h->Z);
@@ -880,6 +892,43 @@ pfm_status pfm_diagnostics(pfm_handle* h, const double* U_dev, double* Iv_dev, d
   return PFM_OK;
 }
 
+pfm_status pfm_set_contact(pfm_handle* h, const double* center, double radius, double eps_N) {
+  if (!h) return PFM_ERR_INVALID_ARG;
+  if (radius <= 0.0) {
+    h->contact_on = false;
+    h->linearized = false;
+    return PFM_OK;
+  }
+  if (!center || !(eps_N > 0.0) || !std::isfinite(radius) || !std::isfinite(center[0]) ||
+      !std::isfinite(center[1]) || !std::isfinite(center[2]))
+    return h->fail(PFM_ERR_INVALID_ARG, "contact needs a centre, a positive radius and a positive penalty");
+  TRY(dalloc(h, &h->load_dev, 1));
+  h->contact = ContactParams{{center[0], center[1], center[2]}, radius, eps_N};
+  h->contact_on = true;
+  h->linearized = false;
+  return PFM_OK;
+}
+
+pfm_status pfm_contact_load(pfm_handle* h, double* load_host, double* energy_host) {
+  TRY(check_ready(h, false));
+  if (!load_host) return h->fail(PFM_ERR_INVALID_ARG, "null output");
+  Level& f = h->L[0];
+  cudaStream_t s = h->stream;
+  double out[2] = {0.0, 0.0};
+  if (h->contact_on) {
+    CK(cudaMemsetAsync(h->load_dev, 0, sizeof(double), s));
+    CK(cudaMemsetAsync(h->energy_dev, 0, sizeof(double), s));
+    launch_contact_residual(f.g, h->contact, f.U, f.mask, nullptr, h->energy_dev, h->load_dev, s);
+    CKL();
+    CK(cudaMemcpyAsync(&out[0], h->load_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&out[1], h->energy_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  *load_host = out[0];
+  if (energy_host) *energy_host = out[1];
+  return PFM_OK;
+}
+
 pfm_status pfm_residual(pfm_handle* h, double* R_dev, double* energy_host) {
   TRY(check_ready(h, false));
   if (!R_dev) return h->fail(PFM_ERR_INVALID_ARG, "null output");
@@ -917,6 +966,9 @@ pfm_status pfm_jacobian_apply_mixed(pfm_handle* h, const float* v_dev, double* y
   {
     ProfScope ps(h, PFM_PROF_JAPPLY_F64);
     launch_japply_df(f.g, h->dp, f.H32, f.H32lo, f.mask, v_dev, y_dev, h->stream);
+    if (h->contact_on)
+      launch_contact_apply<double, float, double>(f.g, f.Kc64, f.mask, static_cast<const float*>(v_dev),
+                                                  static_cast<double*>(y_dev), h->stream);
   }
   CKL();
   return PFM_OK;

@@ -98,6 +98,23 @@ int dense_gauss_jordan_inverse(double* Maug, int n, double* Ainv, unsigned long 
 template <typename T>
 void launch_coarse_solve(int n, const double* Ainv, const T* b, T* x, cudaStream_t s);
 
+// penalty contact with a rigid sphere on the top face (contact_kernels.cu)
+struct ContactParams {
+  double center[3];
+  double radius;
+  double eps_N;
+};
+int64_t contact_points(const Grid& g);  // surface Gauss points of the top face
+void launch_contact_residual(const Grid& g, const ContactParams& c, const double* U, const dmask_t* mask, double* R,
+                             double* energy, double* load, cudaStream_t s);
+void launch_contact_linearize(const Grid& g, const ContactParams& c, const double* U, double* K64, float* K32,
+                              cudaStream_t s);
+template <typename TK, typename TV, typename TY>
+void launch_contact_apply(const Grid& g, const TK* K, const dmask_t* mask, const TV* v, TY* y, cudaStream_t s);
+template <typename T>
+void launch_contact_blockdiag(const Grid& g, const T* K, T* D, cudaStream_t s);
+void launch_contact_coarse(const Grid& g, const double* K, const dmask_t* mask, double* M, int ld, cudaStream_t s);
+
 // microstructure diagnostics (diag_kernels.cu); partial holds (nz+1)*DIAG_MAX_CHUNKS*4 doubles
 constexpr int DIAG_MAX_CHUNKS = 8;
 void launch_diagnostics(const Grid& g, const double* U, double* Iv, double* Id, double* es, double* partial,

@@ -28,6 +28,8 @@ struct Level {
   float *x32 = nullptr, *b32 = nullptr, *y32 = nullptr, *r32 = nullptr, *d32 = nullptr;
   double *x64 = nullptr, *b64 = nullptr, *y64 = nullptr, *r64 = nullptr, *d64 = nullptr;
   double lam = 0.0;  // estimate of lambda_max(D^-1 J) for the Chebyshev smoother
+  double* Kc64 = nullptr;  // contact Hessians at the top-face Gauss points (6 per point)
+  float* Kc32 = nullptr;
 };
 
 template <typename T> struct LvVec;
@@ -39,6 +41,7 @@ template <> struct LvVec<float> {
   static float*& d(Level& l) { return l.d32; }
   static float*& D(Level& l) { return l.D32; }
   static float*& H(Level& l) { return l.H32; }
+  static float*& Kc(Level& l) { return l.Kc32; }
 };
 template <> struct LvVec<double> {
   static double*& x(Level& l) { return l.x64; }
@@ -48,6 +51,7 @@ template <> struct LvVec<double> {
   static double*& d(Level& l) { return l.d64; }
   static double*& D(Level& l) { return l.D64; }
   static double*& H(Level& l) { return l.H64; }
+  static double*& Kc(Level& l) { return l.Kc64; }
 };
 
 constexpr int MAX_COARSE_DOFS = 5000;
@@ -74,6 +78,9 @@ struct pfm_handle {
   double* energy_dev = nullptr;
   int* flag_dev = nullptr;
   double* diag_part = nullptr;  // per-plane partial sums of the diagnostics
+  bool contact_on = false;      // penalty contact with a rigid sphere (pfm_set_contact)
+  pfm::ContactParams contact{};
+  double* load_dev = nullptr;
   // solver work (finest level, FP64)
   double* R = nullptr;
   double* dU = nullptr;

@@ -7,6 +7,7 @@ from __future__ import annotations
 
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 from . import abi, inputs
@@ -84,18 +85,23 @@ class StepRecord:
     res_final: float
     max_Iv: float = 0.0
     mean_Id: float = 0.0
+    load: float = 0.0  # indenter load P (contact) after the step
 
 
 def indentation_history(P: Problem, state: inputs.State, depth_max: float, speed: float = 1.0,
                         tau0: float = 0.128, unload: bool = True, control: StepControl | None = None,
                         radius_frac: float = 0.3, hencky: str = "log", max_steps: int = 1000,
                         opts: abi.SolveOpts | None = None, diagnostics: bool = True, device: str = "cuda",
-                        on_accept=None):
-    """Drive the cap load through loading (and unloading) with adaptive steps.
-    Every attempted step is a Newton solve of R(U) = 0 (Sec. 3.4) started from
-    the last accepted state; an accepted step sets U_n <- U (after calling
-    ``on_accept(record, U_n, U)`` if given). Returns (U on the device, list of
-    StepRecord, one per attempt)."""
+                        on_accept=None, contact: tuple[float, float] | None = None):
+    """Drive the indenter through loading (and unloading) with adaptive steps.
+    The load is the prescribed cap (default) or, with contact = (R, eps_N),
+    frictionless penalty contact with a rigid sphere of radius R whose lowest
+    point sits depth(t) below the top face (Sec. 2.5; top face free, bottom
+    clamped). Every attempted step is a Newton solve of R(U) = 0 (Sec. 3.4)
+    started from the last accepted state; an accepted step sets U_n <- U
+    (after calling ``on_accept(record, U_n, U)`` if given) and records the
+    indenter load. Returns (U on the device, list of StepRecord, one per
+    attempt)."""
     c = control or StepControl()
     opts = opts or abi.default_opts(abi.PFM_F32, max_newton=c.max_its, newton_rtol=1e-8, lin_rtol=1e-8,
                                     max_lin_it=400)
@@ -111,7 +117,13 @@ def indentation_history(P: Problem, state: inputs.State, depth_max: float, speed
         if t < t_turn * (1.0 - 1e-12):
             step = min(step, t_turn - t)  # land on the turning point
         depth = depth_history(t + step, depth_max, speed, unload)
-        mask, values = inputs.indentation_dirichlet_depth(state.mesh, depth, radius_frac)
+        m = state.mesh
+        if contact is None:
+            mask, values = inputs.indentation_dirichlet_depth(m, depth, radius_frac)
+        else:
+            mask = inputs.face_mask(m, bottom=True, top=False)
+            values = np.zeros_like(state.U)
+            P.set_contact([m.Lx / 2, m.Ly / 2, m.Lz + contact[0] - depth], contact[0], contact[1])
         P.set_dirichlet(torch.from_numpy(mask).to(device), torch.from_numpy(values).to(device))
         params.tau = step
         P.set_params(params)
@@ -132,6 +144,8 @@ def indentation_history(P: Problem, state: inputs.State, depth_max: float, speed
                 S = P.diagnostics(U, per_node=False)["planes"]
                 rec.max_Iv = float(S[:, 1].max())
                 rec.mean_Id = float(S[:, 2].mean())
+            if contact is not None:
+                rec.load = P.contact_load()[0]
         records.append(rec)
         if not accepted and step <= c.tau_min:
             break

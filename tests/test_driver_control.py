@@ -62,6 +62,14 @@ class _FakeProblem:
     def diagnostics(self, U, per_node=False):
         return {"planes": torch.zeros(3, 4, dtype=torch.float64)}
 
+    def set_contact(self, center, radius, eps_N):
+        self.sphere = (list(center), radius, eps_N)
+
+    def contact_load(self):
+        # stands in for the load: the current indentation depth of the sphere
+        c, R, _ = self.sphere
+        return self.Lz + R - c[2], 0.0
+
 
 def test_driver_covers_the_history_and_adapts():
     st = inputs.config_indentation(4, seed=1, step=1)
@@ -81,3 +89,22 @@ def test_driver_covers_the_history_and_adapts():
     full = [r for r in acc[2:-1] if abs(r.t - 1.0) > 1e-12]
     assert all(0.15 < r.tau < 0.2 and r.newton_its == 7 for r in full)
     assert U.shape == st.U.shape
+
+
+def test_driver_moves_the_contact_sphere():
+    """With contact the top face is free, the sphere's lowest point follows the
+    depth history and each accepted step records the load."""
+    st = inputs.config_indentation(4, seed=1, step=0)
+    P = _FakeProblem()
+    P.depth = 0.0
+    P.Lz = st.mesh.Lz
+    P.set_dirichlet = lambda mask, values: setattr(P, "mask", mask.numpy().copy())
+    U, recs = driver.indentation_history(P, st, depth_max=1.0, speed=1.0, tau0=0.2, device="cpu",
+                                         contact=(5.0, 100.0))
+    acc = [r for r in recs if r.accepted]
+    assert all(abs(r.load - r.depth) < 1e-12 for r in acc)
+    assert P.sphere[1] == 5.0 and P.sphere[2] == 100.0
+    m = st.mesh
+    top = np.arange(m.n_nodes).reshape(m.nz + 1, m.ny + 1, m.nx + 1)[-1].ravel()
+    bottom = np.arange(m.n_nodes).reshape(m.nz + 1, m.ny + 1, m.nx + 1)[0].ravel()
+    assert P.mask[:, top].sum() == 0 and np.all(P.mask[0:3, bottom] == 1)

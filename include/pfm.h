@@ -168,6 +168,14 @@ pfm_status pfm_set_state(pfm_handle* h, const double* U_dev, const double* Un_de
 /* Copy the handle's current iterate to U_dev (device, double [9][n_nodes]). */
 pfm_status pfm_get_state(pfm_handle* h, double* U_dev);
 
+/* Arithmetic of the FP64-class linearisation (finest and coarsest levels, and
+ * every level of an all-FP64 solve): 0 = FP64 (default), 1 = double-float
+ * (pairs of FP32 numbers, about 48 significant bits, on the FP32 pipes; the
+ * few divisions, square roots and logarithms per Gauss point in FP64).
+ * Intermediate levels of the FP32 preconditioner are computed in FP32 either
+ * way. Errors: PFM_ERR_INVALID_ARG (other values). */
+pfm_status pfm_set_linearize_arithmetic(pfm_handle* h, int double_float);
+
 /* Frictionless penalty contact with a rigid sphere (Sec. 2.5, Eq. Ngap, the
  * contact term of Eq. PenPot) on the top face z = Lz: a point X of that face
  * at x = X + u has the normal gap g = |x - c| - R to the sphere of centre

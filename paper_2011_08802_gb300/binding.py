@@ -126,6 +126,11 @@ class Problem:
         self._check(self._lib.pfm_residual(self.h, _ptr(R), C.byref(e) if energy else None))
         return (R, e.value) if energy else R
 
+    def set_linearize_arithmetic(self, double_float: bool):
+        """``pfm_set_linearize_arithmetic``: FP64 (False) or double-float (True)
+        point physics in the FP64-class linearisation."""
+        self._check(self._lib.pfm_set_linearize_arithmetic(self.h, int(bool(double_float))))
+
     def set_contact(self, center, radius: float, eps_N: float):
         """``pfm_set_contact``: rigid sphere (centre, radius) pressed on the top
         face with penalty eps_N; radius <= 0 switches contact off."""

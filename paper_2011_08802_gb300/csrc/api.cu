@@ -306,10 +306,12 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
     if (needlo) TRY(dalloc(h, &lv.H32lo, hsz));
     {
       ProfScope ps(h, PFM_PROF_LINEARIZE, fine);
-      // intermediate levels of an FP32 preconditioner need only FP32 Hessians
+      // intermediate levels of an FP32 preconditioner need only FP32 Hessians;
+      // the others FP64-class ones (FP64 or double-float arithmetic)
       const bool fp32_compute = !fine && !coarsest && prec == PFM_F32;
+      const int arith = fp32_compute ? LIN_F32 : (h->lin_df ? LIN_DF : LIN_F64);
       launch_linearize(lv.g, h->dp, lv.U, lv.Un, need64 ? lv.H64 : nullptr, need32 ? lv.H32 : nullptr,
-                       needlo ? lv.H32lo : nullptr, fp32_compute, s);
+                       needlo ? lv.H32lo : nullptr, arith, s);
     }
     if (h->contact_on) {
       TRY(dalloc(h, &lv.Kc64, size_t(6) * contact_points(lv.g)));
@@ -889,6 +891,14 @@ pfm_status pfm_diagnostics(pfm_handle* h, const double* U_dev, double* Iv_dev, d
   if (g.nz + 1 > 65535) return h->fail(PFM_ERR_INVALID_ARG, "more than 65535 node planes");
   launch_diagnostics(g, U_dev, Iv_dev, Id_dev, eta_star_dev, h->diag_part, plane_stats_dev, h->stream);
   CKL();
+  return PFM_OK;
+}
+
+pfm_status pfm_set_linearize_arithmetic(pfm_handle* h, int double_float) {
+  if (!h) return PFM_ERR_INVALID_ARG;
+  if (double_float != 0 && double_float != 1) return h->fail(PFM_ERR_INVALID_ARG, "expected 0 or 1");
+  h->lin_df = double_float != 0;
+  h->linearized = false;
   return PFM_OK;
 }
 

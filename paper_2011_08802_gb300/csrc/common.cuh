@@ -51,8 +51,10 @@ void count_launches(int n);
 // element kernels (fe_kernels.cu)
 void launch_residual(const Grid& g, const DevParams& P, const double* U, const double* Un,
                      const dmask_t* mask, double* R, double* energy, cudaStream_t s);
+// arithmetic of the point physics in the linearisation
+enum { LIN_F64 = 0, LIN_F32 = 1, LIN_DF = 2 };
 void launch_linearize(const Grid& g, const DevParams& P, const double* U, const double* Un,
-                      double* H64, float* H32, float* H32lo, bool fp32_compute, cudaStream_t s);
+                      double* H64, float* H32, float* H32lo, int arith, cudaStream_t s);
 void launch_japply_df(const Grid& g, const DevParams& P, const float* Hhi, const float* Hlo, const dmask_t* mask,
                       const float* v, double* y, cudaStream_t s);
 template <typename T>

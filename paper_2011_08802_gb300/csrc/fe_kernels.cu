@@ -213,10 +213,12 @@ void launch_residual(const Grid& g, const DevParams& P, const double* U, const d
 }
 
 void launch_linearize(const Grid& g, const DevParams& P, const double* U, const double* Un,
-                      double* H64, float* H32, float* H32lo, bool fp32_compute, cudaStream_t s) {
+                      double* H64, float* H32, float* H32lo, int arith, cudaStream_t s) {
   const int64_t threads = g.nblk() * 32;
-  if (fp32_compute)
+  if (arith == LIN_F32)
     k_linearize<float><<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo);
+  else if (arith == LIN_DF)
+    k_linearize<df64><<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo);
   else
     k_linearize<double><<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo);
   count_launches(1);

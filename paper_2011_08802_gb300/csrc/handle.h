@@ -106,6 +106,7 @@ struct pfm_handle {
   void* stage_out = nullptr;
   int power_its = 30;
   bool outer_df = true;  // outer operator of the mixed solve in double-float arithmetic
+  bool lin_df = false;   // FP64-class linearisation in double-float instead of FP64 arithmetic
   // pinned host slots for Hessenberg columns and scalars
   double* hpin = nullptr;
   // captured V-cycle (valid until the next linearisation)

@@ -52,6 +52,75 @@ using std::fabs;
 
 namespace pfm {
 
+#ifdef __CUDACC__
+// keep the C math functions visible next to the double-float overloads below
+using ::fabs;
+using ::log;
+using ::log1p;
+using ::sqrt;
+
+// ---------------------------------------------------------------------------
+// Double-float number hi + lo (two FP32 values, |lo| <= ulp(hi)/2): about 48
+// significant bits from FP32 adds, multiplies and fused multiply-adds only
+// (Dekker 1971; Knuth's TwoSum), so the point physics can run on the FP32
+// pipes. Division, square root and the logarithms go through FP64 (a handful
+// per Gauss point). The _rn intrinsics keep the compiler from contracting or
+// reassociating the error-free transformations.
+struct df64 {
+  float hi, lo;
+  df64() = default;
+  __device__ __forceinline__ df64(double x) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(x - double(hi));
+  }
+  __device__ __forceinline__ explicit operator double() const { return double(hi) + double(lo); }
+  __device__ __forceinline__ static df64 make(float h, float l) {
+    df64 r;
+    r.hi = h;
+    r.lo = l;
+    return r;
+  }
+};
+
+__device__ __forceinline__ df64 df64_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return df64::make(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return df64_fast_two_sum(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df64 operator-(df64 a) { return df64::make(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df64_fast_two_sum(p, e);
+}
+__device__ __forceinline__ df64 operator/(df64 a, df64 b) { return df64(double(a) / double(b)); }
+__device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b; }
+__device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b; }
+__device__ __forceinline__ df64& operator*=(df64& a, df64 b) { return a = a * b; }
+__device__ __forceinline__ df64& operator/=(df64& a, df64 b) { return a = a / b; }
+__device__ __forceinline__ bool operator<(df64 a, df64 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool operator>(df64 a, df64 b) { return b < a; }
+__device__ __forceinline__ bool operator<=(df64 a, df64 b) { return !(b < a); }
+__device__ __forceinline__ bool operator>=(df64 a, df64 b) { return !(a < b); }
+__device__ __forceinline__ bool operator==(df64 a, df64 b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ bool operator!=(df64 a, df64 b) { return !(a == b); }
+__device__ __forceinline__ df64 fabs(df64 a) { return a.hi < 0.f ? -a : a; }
+__device__ __forceinline__ df64 sqrt(df64 a) { return df64(::sqrt(double(a))); }
+__device__ __forceinline__ df64 log(df64 a) { return df64(::log(double(a))); }
+__device__ __forceinline__ df64 log1p(df64 a) { return df64(::log1p(double(a))); }
+__device__ __forceinline__ df64 shx(df64 v, int m) {
+  return df64::make(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
+}
+#endif
+
 constexpr int NPH = 7;    // phases: austenite + 6 variants (Sec. 5.1)
 constexpr int NZ = 15;    // local unknowns at a point: F (9) + eta_hat (6)
 constexpr int NH = 120;   // packed upper triangle of the 15x15 Hessian
@@ -78,6 +147,12 @@ template <> struct Tol<double> {
   static constexpr double dd2_gap = 1e-3;    // relative spread below which f2 uses its Taylor series
   static constexpr double jacobi_off = 1e-17;
 };
+#ifdef __CUDACC__
+template <> struct Tol<df64> {
+  static constexpr double dd2_gap = 1e-3;
+  static constexpr double jacobi_off = 1e-14;  // the double-float resolution
+};
+#endif
 template <> struct Tol<float> {
   static constexpr float dd2_gap = 3e-2f;
   static constexpr float jacobi_off = 1e-8f;
@@ -261,6 +336,31 @@ PFM_HD void eig_sym3<double>(double a[3][3], double lam[3], double Q[3][3]) {
   jacobi_eig3(b, lam, Q1);
   mm3(Q0, Q1, Q);
 }
+
+#ifdef __CUDACC__
+// Double-float version of the FP64 eigen-decomposition: FP32 Jacobi seed,
+// re-orthonormalisation and the finishing sweeps in double-float.
+__device__ __forceinline__ void eig_sym3(df64 a[3][3], df64 lam[3], df64 Q[3][3]) {
+  float af[3][3], lf[3], Qf[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) af[i][j] = a[i][j].hi;
+  jacobi_eig3(af, lf, Qf);
+  df64 Q0[3][3], b[3][3], Q1[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Q0[i][j] = df64(double(Qf[i][j]));
+  for (int c = 0; c < 3; ++c) {
+    for (int pc = 0; pc < c; ++pc) {
+      df64 d = Q0[0][c] * Q0[0][pc] + Q0[1][c] * Q0[1][pc] + Q0[2][c] * Q0[2][pc];
+      for (int i = 0; i < 3; ++i) Q0[i][c] -= d * Q0[i][pc];
+    }
+    df64 inrm = df64(1.0 / ::sqrt(double(Q0[0][c] * Q0[0][c] + Q0[1][c] * Q0[1][c] + Q0[2][c] * Q0[2][c])));
+    for (int i = 0; i < 3; ++i) Q0[i][c] *= inrm;
+  }
+  rot_in(Q0, a, b);
+  jacobi_eig3(b, lam, Q1);
+  mm3(Q0, Q1, Q);
+}
+#endif
 
 // First divided difference of log: (log a - log b)/(a - b), 1/a if a == b.
 template <typename T>

@@ -142,3 +142,21 @@ def test_host_buffer_apply(ragged):
     v = np.random.default_rng(7).standard_normal(st.U.shape)
     y = P.jacobian_apply_host(v)
     assert _relerr(y, (K @ v.reshape(-1)).reshape(v.shape)) < RTOL64
+
+
+def test_double_float_linearisation(ragged):
+    """The FP64-class linearisation in double-float arithmetic: Hessians and
+    the FP64 tangent application against the oracle, at the resolution of
+    the double-float format (48 significant bits)."""
+    P, K, st = ragged["P"], ragged["K"], ragged["st"]
+    P.set_linearize_arithmetic(True)
+    try:
+        P.linearize(abi.PFM_F32)
+        Hg = P.get_hessians(0, P.n_elems)
+        iu = np.triu_indices(15)
+        assert _relerr(Hg, ragged["d"]["H"][:, :, iu[0], iu[1]]) < 1e-12
+        v = np.random.default_rng(12).standard_normal(st.U.shape)
+        y = P.jacobian_apply(torch.from_numpy(v).cuda()).cpu().numpy()
+        assert _relerr(y, (K @ v.reshape(-1)).reshape(v.shape)) < 1e-11
+    finally:
+        P.set_linearize_arithmetic(False)

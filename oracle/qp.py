@@ -93,6 +93,55 @@ def cubic_stiffness(C11: float, C12: float, C44: float) -> np.ndarray:
     return L
 
 
+def orthorhombic_stiffness(c: dict) -> np.ndarray:
+    """Fourth-order orthorhombic stiffness in its own axes from the nine
+    constants (Voigt pairs 11, 22, 33, 23 -> 4, 13 -> 5, 12 -> 6)."""
+    L = np.zeros((3, 3, 3, 3))
+    diag = {(0, 0): c["c11"], (1, 1): c["c22"], (2, 2): c["c33"],
+            (0, 1): c["c12"], (0, 2): c["c13"], (1, 2): c["c23"]}
+    for (i, j), v in diag.items():
+        L[i, i, j, j] = L[j, j, i, i] = v
+    for (i, j), v in (((1, 2), c["c44"]), ((0, 2), c["c55"]), ((0, 1), c["c66"])):
+        L[i, j, i, j] = L[j, i, j, i] = L[i, j, j, i] = L[j, i, i, j] = v
+    return L
+
+
+def rotate_stiffness(L: np.ndarray, Q: np.ndarray) -> np.ndarray:
+    """L'_ijkl = Q_ip Q_jq Q_kr Q_ls L_pqrs: the tensor L expressed in the
+    frame whose vector components are v' = Q v."""
+    return np.einsum("ip,jq,kr,ls,pqrs->ijkl", Q, Q, Q, Q, L)
+
+
+def variant_axes(U: np.ndarray, alpha: float, beta: float, gamma: float) -> np.ndarray:
+    """Principal directions of a variant stretch as the columns of Q, ordered
+    by the stretches (alpha, beta, gamma) they carry."""
+    w, V = np.linalg.eigh(U)
+    order = [int(np.argmin(np.abs(w - t))) for t in (alpha, beta, gamma)]
+    return V[:, order]
+
+
+def material_anisotropic(constants: dict, table: dict, tau: float, orientation=None) -> Material:
+    """Material with the anisotropic constants of Table 1: cubic austenite in
+    the crystal axes, orthorhombic martensite in each variant's principal
+    axes (its orthorhombic axes 1, 2, 3 along the stretches alpha, beta,
+    gamma), all turned into the lab frame by ``orientation`` (rows = lab axes
+    in crystal coordinates; Sec. 5.1 uses [011] along z)."""
+    base = material_from(constants, tau)
+    al, be, ga = constants["stretch_alpha"], constants["stretch_beta"], constants["stretch_gamma"]
+    cub = table["cubic"]
+    Lt = [cubic_stiffness(cub["c11"], cub["c12"], cub["c44"])]
+    L_orth = orthorhombic_stiffness(table["orthorhombic"])
+    for i in range(1, N_PHASES):
+        Lt.append(rotate_stiffness(L_orth, variant_axes(base.U[i], al, be, ga)))
+    Lt = np.stack(Lt)
+    U = base.U.copy()
+    if orientation is not None:
+        R = np.asarray(orientation, dtype=np.float64)
+        U = np.einsum("ip,npq,jq->nij", R, U, R)
+        Lt = np.stack([rotate_stiffness(L, R) for L in Lt])
+    return Material(U, Lt, base.F0, base.m, base.gamma, base.ell, base.eps_eta, tau, base.hencky)
+
+
 def material_from(constants: dict, tau: float, C=None, gamma_scale: float = 1.0,
                   hencky: str = "log") -> Material:
     """Material of Sec. 5.1 from raw constants. ``C`` optionally overrides

@@ -50,6 +50,22 @@ MATERIAL = dict(
     eps_eta=1.0e3,
 )
 
+#: Anisotropic elastic constants of CuAlNi (Table 1, GPa): cubic austenite
+#: (c11, c44, c12) and orthorhombic martensite in its own axes.
+ELASTIC_TABLE1 = dict(
+    cubic=dict(c11=142.0, c44=96.0, c12=126.0),
+    orthorhombic=dict(c11=189.0, c22=141.0, c33=205.0, c44=54.9, c55=19.7, c66=62.6,
+                      c12=124.0, c13=45.5, c23=115.0),
+)
+
+#: Crystal orientation of the indentation example (Sec. 5.1): the austenite
+#: [011] axis along the loading direction z. Rows are the lab axes x, y, z in
+#: crystal coordinates ([100], [01-1]/sqrt2, [011]/sqrt2), so a crystal-frame
+#: vector v has lab components R v.
+ORIENTATION_011 = [[1.0, 0.0, 0.0],
+                   [0.0, 0.5 ** 0.5, -(0.5 ** 0.5)],
+                   [0.0, 0.5 ** 0.5, 0.5 ** 0.5]]
+
 #: Edge of the synthetic cube (nm).
 CUBE_EDGE = 64.0
 

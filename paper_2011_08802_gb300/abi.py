@@ -110,6 +110,63 @@ def params_from_material(constants: dict, tau: float, C_override=None,
     return P
 
 
+def _bond(a: np.ndarray) -> np.ndarray:
+    """6x6 Bond matrix M of the rotation a (x' = a x) for stiffness in the
+    Voigt order (11, 22, 33, 23, 13, 12) with engineering shear strains:
+    C' = M C M^T."""
+    M = np.zeros((6, 6))
+    pairs = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    for I, (i, j) in enumerate(pairs):
+        for J, (k, l) in enumerate(pairs):
+            if J < 3:
+                M[I, J] = a[i, k] * a[j, k]
+            else:
+                M[I, J] = a[i, k] * a[j, l] + a[i, l] * a[j, k]
+    return M
+
+
+def params_anisotropic(constants: dict, table: dict, tau: float, orientation=None,
+                       hencky: str = "log") -> Params:
+    """Parameter block with the anisotropic constants of Table 1: cubic
+    austenite in the crystal axes, orthorhombic martensite in each variant's
+    principal axes (orthorhombic axes 1, 2, 3 along the stretches alpha, beta,
+    gamma), every stretch and stiffness turned into the lab frame by
+    ``orientation`` (rows = lab axes in crystal coordinates). Voigt matrices
+    are rotated with Bond matrices."""
+    P = params_from_material(constants, tau, hencky=hencky)
+    al, be, ga = constants["stretch_alpha"], constants["stretch_beta"], constants["stretch_gamma"]
+    c = table["cubic"]
+    Lc = np.zeros((6, 6))
+    Lc[:3, :3] = c["c12"]
+    np.fill_diagonal(Lc[:3, :3], c["c11"])
+    Lc[3, 3] = Lc[4, 4] = Lc[5, 5] = c["c44"]
+    o = table["orthorhombic"]
+    Lo = np.array([[o["c11"], o["c12"], o["c13"], 0, 0, 0],
+                   [o["c12"], o["c22"], o["c23"], 0, 0, 0],
+                   [o["c13"], o["c23"], o["c33"], 0, 0, 0],
+                   [0, 0, 0, o["c44"], 0, 0],
+                   [0, 0, 0, 0, o["c55"], 0],
+                   [0, 0, 0, 0, 0, o["c66"]]], dtype=np.float64)
+    R = np.eye(3) if orientation is None else np.asarray(orientation, dtype=np.float64)
+    for i in range(7):
+        U = np.array([P.Ut[i][k] for k in range(9)]).reshape(3, 3)
+        if i == 0:
+            L = Lc
+        else:
+            w, V = np.linalg.eigh(U)
+            axes = np.stack([V[:, int(np.argmin(np.abs(w - t)))] for t in (al, be, ga)], axis=1)
+            Mv = _bond(axes)  # variant frame -> crystal frame
+            L = Mv @ Lo @ Mv.T
+        Mr = _bond(R)
+        L = Mr @ L @ Mr.T
+        U = R @ U @ R.T
+        for k in range(9):
+            P.Ut[i][k] = U.reshape(9)[k]
+        for k in range(36):
+            P.Lvoigt[i][k] = L.reshape(36)[k]
+    return P
+
+
 _lib = None
 
 

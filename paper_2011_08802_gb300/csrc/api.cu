@@ -686,6 +686,82 @@ bool opts_valid(const pfm_solve_opts& o) {
 }  // namespace
 
 // ============================================================================
+namespace {
+
+// Host-buffer tangent application as a pipeline over z-slabs of elements:
+// slab s's input node planes travel host -> device on one copy stream while
+// the slab before computes; once slabs <= s are done, the node planes below
+// slab s+1 are complete and travel back on a second copy stream. Each copy is
+// one 2D transfer over the 9 fields (field stride nn).
+template <typename T>
+pfm_status japply_host_pipelined(pfm_handle* h, const void* v_host, void* y_host) {
+  Level& f = h->L[0];
+  const Grid& g = f.g;
+  const T* H = LvVec<T>::H(f);
+  if (!H || (sizeof(T) == 4 && h->lin_prec != PFM_F32))
+    return h->fail(PFM_ERR_STATE, "no tangent in the requested precision (linearize with PFM_F32 for FP32)");
+  if (!h->pipe_in) {
+    CK(cudaStreamCreateWithFlags(&h->pipe_in, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&h->pipe_out, cudaStreamNonBlocking));
+    for (int k = 0; k < pfm_handle::PIPE_SLABS; ++k) {
+      CK(cudaEventCreateWithFlags(&h->pipe_ev_in[k], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&h->pipe_ev_done[k], cudaEventDisableTiming));
+    }
+    CK(cudaEventCreateWithFlags(&h->pipe_ev_start, cudaEventDisableTiming));
+  }
+  T* vd = static_cast<T*>(h->stage_in);
+  T* yd = static_cast<T*>(h->stage_out);
+  const T* vh = static_cast<const T*>(v_host);
+  T* yh = static_cast<T*>(y_host);
+  const int64_t nn = f.nn, plane = int64_t(g.nx + 1) * (g.ny + 1);
+  const int64_t eplane = int64_t(g.nx) * g.ny;  // elements per layer
+  const int S = std::min(pfm_handle::PIPE_SLABS, g.nz);
+  const size_t pitch = sizeof(T) * nn;
+  cudaStream_t sc = h->stream;
+  const int blocks = japply_range_blocks();
+  // the copy streams start after everything already queued on the compute stream
+  CK(cudaEventRecord(h->pipe_ev_start, sc));
+  CK(cudaStreamWaitEvent(h->pipe_in, h->pipe_ev_start, 0));
+  CK(cudaStreamWaitEvent(h->pipe_out, h->pipe_ev_start, 0));
+  CK(cudaMemsetAsync(yd, 0, sizeof(T) * NF * nn, sc));
+  int64_t in_done = 0;   // node planes already on the device
+  int64_t out_done = 0;  // node planes already returned
+  for (int s = 0; s < S; ++s) {
+    const int64_t k0 = int64_t(g.nz) * s / S, k1 = int64_t(g.nz) * (s + 1) / S;  // element layers [k0, k1)
+    const int64_t need = k1 + 1;                                                   // node planes [0, k1]
+    if (need > in_done) {
+      CK(cudaMemcpy2DAsync(vd + in_done * plane, pitch, vh + in_done * plane, pitch,
+                           sizeof(T) * (need - in_done) * plane, NF, cudaMemcpyHostToDevice, h->pipe_in));
+      in_done = need;
+    }
+    CK(cudaEventRecord(h->pipe_ev_in[s], h->pipe_in));
+    CK(cudaStreamWaitEvent(sc, h->pipe_ev_in[s], 0));
+    // element blocks (4 consecutive elements) that start in layers [k0, k1); a
+    // block that reaches into layer k1 is left to the next slab, whose input
+    // planes it needs
+    const int64_t e0 = k0 * eplane, e1 = k1 * eplane;
+    const int64_t b0 = e0 / 4, b1 = (s + 1 == S) ? f.nblk : e1 / 4;
+    launch_japply_range<T>(g, h->dp, H, f.mask, vd, yd, b0, b1, blocks, sc);
+    // node planes [out_done, ready) are final: plane k1 still gets the next
+    // slab, and plane k1 - 1 too when a block straddles layers k1 - 1 and k1
+    const int64_t ready = (s + 1 == S) ? int64_t(g.nz) + 1 : (eplane % 4 == 0 ? k1 : k1 - 1);
+    launch_identity_rows<T>(nn, f.mask, vd, yd, out_done * plane, ready * plane, sc);
+    CKL();
+    CK(cudaEventRecord(h->pipe_ev_done[s], sc));
+    CK(cudaStreamWaitEvent(h->pipe_out, h->pipe_ev_done[s], 0));
+    if (ready > out_done) {
+      CK(cudaMemcpy2DAsync(yh + out_done * plane, pitch, yd + out_done * plane, pitch,
+                           sizeof(T) * (ready - out_done) * plane, NF, cudaMemcpyDeviceToHost, h->pipe_out));
+      out_done = ready;
+    }
+  }
+  CK(cudaStreamSynchronize(h->pipe_out));
+  CK(cudaStreamSynchronize(sc));
+  return PFM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* pfm_version(void) { return "pfm 0.1 (sm_103a)"; }
@@ -782,6 +858,15 @@ void pfm_destroy(pfm_handle* h) {
   if (h->Z) cudaFree(h->Z);
   if (h->vgraph) cudaGraphExecDestroy(h->vgraph);
   if (h->hpin) cudaFreeHost(h->hpin);
+  if (h->pipe_in) {
+    cudaStreamDestroy(h->pipe_in);
+    cudaStreamDestroy(h->pipe_out);
+    for (int k = 0; k < pfm_handle::PIPE_SLABS; ++k) {
+      cudaEventDestroy(h->pipe_ev_in[k]);
+      cudaEventDestroy(h->pipe_ev_done[k]);
+    }
+    cudaEventDestroy(h->pipe_ev_start);
+  }
   if (h->stage_in) cudaFree(h->stage_in);
   if (h->stage_out) cudaFree(h->stage_out);
   delete h;
@@ -995,6 +1080,10 @@ pfm_status pfm_jacobian_apply_host(pfm_handle* h, const void* v_host, void* y_ho
     TRY(dalloc(h, &b, ndof(h->L[0]) * sizeof(double)));
     h->stage_in = a;
     h->stage_out = b;
+  }
+  if (!h->contact_on && (prec == PFM_F32 || prec == PFM_F64)) {
+    if (prec == PFM_F32) return japply_host_pipelined<float>(h, v_host, y_host);
+    return japply_host_pipelined<double>(h, v_host, y_host);
   }
   CK(cudaMemcpyAsync(h->stage_in, v_host, bytes, cudaMemcpyHostToDevice, h->stream));
   TRY(pfm_jacobian_apply(h, h->stage_in, h->stage_out, prec));

@@ -60,6 +60,13 @@ void launch_japply_df(const Grid& g, const DevParams& P, const float* Hhi, const
 template <typename T>
 void launch_japply(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, const T* v,
                    T* y, cudaStream_t s);
+// element blocks [b0, b1) only, on at most `blocks` CTAs (slab pipeline)
+template <typename T>
+void launch_japply_range(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, const T* v, T* y,
+                         int64_t b0, int64_t b1, int blocks, cudaStream_t s);
+template <typename T>
+void launch_identity_rows(int64_t nn, const dmask_t* mask, const T* v, T* y, int64_t n0, int64_t n1, cudaStream_t s);
+int japply_range_blocks();  // persistent grid of k_japply_range
 template <typename T>
 void launch_blockdiag(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, T* D,
                       cudaStream_t s);

@@ -178,19 +178,15 @@ __device__ __forceinline__ void linearize_lane(const Grid& g, const DevParams& P
   }
 }
 
-// Nodal 9x9 diagonal blocks: (element e, local node a) sums over the 8
-// points B_a(q)^T H_q B_a(q) w plus the gradient-energy block, then adds it
-// to the node's block D[(r*9+c)*nn + node].
+// Nodal 9x9 diagonal blocks. For local node a of the element whose Gauss-point
+// Hessians sit in store block blk at lanes lane0..lane0+7, add to Db (upper
+// triangle, row-major, 45 entries) the sum over the 8 points of
+// w B_a(q)^T H_q B_a(q) plus the gradient-energy block.
 template <typename T>
-__device__ __forceinline__ void blockdiag_elem_node(const Grid& g, const JParams<T>& jp, const T* __restrict__ H,
-                                                    T* __restrict__ D, int64_t e, int a) {
-  const int64_t blk = e >> 2;
-  const int lane0 = int(e & 3) * 8;
-  const int64_t nn = g.nn();
-  const int64_t node = elem_node(g, e, a);
-  T Db[45];
-#pragma unroll
-  for (int i = 0; i < 45; ++i) Db[i] = T(0);
+__device__ __forceinline__ void blockdiag_accumulate(const JParams<T>& jp, const T* __restrict__ H, int64_t blk,
+                                                     int lane0, int a, T Db[45]) {
+  constexpr int V = 16 / sizeof(T);
+  using VT = typename Vec16<T>::type;
   const T ih[3] = {jp.ihx, jp.ihy, jp.ihz};
   for (int q = 0; q < 8; ++q) {
     T phi[3], dphi[3];
@@ -204,29 +200,90 @@ __device__ __forceinline__ void blockdiag_elem_node(const Grid& g, const JParams
     const T dN[3] = {dphi[0] * phi[1] * phi[2], phi[0] * dphi[1] * phi[2], phi[0] * phi[1] * dphi[2]};
     // column map: DOF u_i -> z rows 3i+J (coef dN_J); eta_k -> z row 9+k (coef N)
     T Hq[NH];
-    for (int j = 0; j < NH; ++j) Hq[j] = H[hstore_offset<T>(blk, j, lane0 + q)];
-    auto hget = [&](int r, int c) -> T { return r <= c ? Hq[hidx(r, c)] : Hq[hidx(c, r)]; };
+    const VT* Hv = reinterpret_cast<const VT*>(H) + blk * (NH / V) * 32 + lane0 + q;
+#pragma unroll
+    for (int jj = 0; jj < NH / V; ++jj) Vec16<T>::unpack(Hv[jj * 32], Hq + jj * V);
+    const T g2 = dN[0] * dN[0] + dN[1] * dN[1] + dN[2] * dN[2];
     int idx = 0;
+#pragma unroll
     for (int r = 0; r < 9; ++r)
+#pragma unroll
       for (int c = r; c < 9; ++c) {
         T s = T(0);
         if (r < 3 && c < 3) {
+#pragma unroll
           for (int J = 0; J < 3; ++J)
-            for (int L = 0; L < 3; ++L) s += dN[J] * dN[L] * hget(3 * r + J, 3 * c + L);
+#pragma unroll
+            for (int L = 0; L < 3; ++L) {
+              const int rr = 3 * r + J, cc = 3 * c + L;
+              s += dN[J] * dN[L] * Hq[rr <= cc ? hidx(rr, cc) : hidx(cc, rr)];
+            }
         } else if (r < 3) {
-          for (int J = 0; J < 3; ++J) s += dN[J] * N * hget(3 * r + J, 9 + (c - 3));
+#pragma unroll
+          for (int J = 0; J < 3; ++J) s += dN[J] * N * Hq[hidx(3 * r + J, 9 + (c - 3))];
         } else {
-          s = N * N * hget(9 + (r - 3), 9 + (c - 3)) +
-              (dN[0] * dN[0] + dN[1] * dN[1] + dN[2] * dN[2]) * jp.G[r - 3][c - 3];
+          s = N * N * Hq[hidx(9 + (r - 3), 9 + (c - 3))] + g2 * jp.G[r - 3][c - 3];
         }
         Db[idx++] += jp.w * s;
       }
   }
+}
+
+// (element e, local node a): its element's contribution added to the node's
+// block D[(r*9+c)*nn + node] with atomics (batched engine).
+template <typename T>
+__device__ __forceinline__ void blockdiag_elem_node(const Grid& g, const JParams<T>& jp, const T* __restrict__ H,
+                                                    T* __restrict__ D, int64_t e, int a) {
+  const int64_t nn = g.nn();
+  const int64_t node = elem_node(g, e, a);
+  T Db[45];
+#pragma unroll
+  for (int i = 0; i < 45; ++i) Db[i] = T(0);
+  blockdiag_accumulate<T>(jp, H, e >> 2, int(e & 3) * 8, a, Db);
   int idx = 0;
   for (int r = 0; r < 9; ++r)
     for (int c = r; c < 9; ++c) {
       atomicAdd(&D[(r * 9 + c) * nn + node], Db[idx]);
       if (c != r) atomicAdd(&D[(c * 9 + r) * nn + node], Db[idx]);
+      ++idx;
+    }
+}
+
+// Node n (i + (nx+1)(j + (ny+1)k)): gathers the contributions of its (up to 8)
+// adjacent elements in a fixed order and writes its whole block, without
+// atomics. Consecutive nodes share elements, whose Hessians then come from L2.
+template <typename T>
+__device__ __forceinline__ void blockdiag_node_gather(const Grid& g, const JParams<T>& jp, const T* __restrict__ H,
+                                                      T* __restrict__ D, int64_t n) {
+  const int64_t nn = g.nn();
+  const int i = int(n % (g.nx + 1));
+  const int j = int((n / (g.nx + 1)) % (g.ny + 1));
+  const int k = int(n / (int64_t(g.nx + 1) * (g.ny + 1)));
+  T Db[45];
+#pragma unroll
+  for (int t = 0; t < 45; ++t) Db[t] = T(0);
+  for (int dk = 0; dk < 2; ++dk) {
+    const int ek = k - 1 + dk;
+    if (ek < 0 || ek >= g.nz) continue;
+    for (int dj = 0; dj < 2; ++dj) {
+      const int ej = j - 1 + dj;
+      if (ej < 0 || ej >= g.ny) continue;
+      for (int di = 0; di < 2; ++di) {
+        const int ei = i - 1 + di;
+        if (ei < 0 || ei >= g.nx) continue;
+        const int64_t e = ei + int64_t(g.nx) * (ej + int64_t(g.ny) * ek);
+        const int a = (1 - di) + 2 * (1 - dj) + 4 * (1 - dk);  // this node's corner in element e
+        blockdiag_accumulate<T>(jp, H, e >> 2, int(e & 3) * 8, a, Db);
+      }
+    }
+  }
+  int idx = 0;
+#pragma unroll
+  for (int r = 0; r < 9; ++r)
+#pragma unroll
+    for (int c = r; c < 9; ++c) {
+      D[(r * 9 + c) * nn + n] = Db[idx];
+      if (c != r) D[(c * 9 + r) * nn + n] = Db[idx];
       ++idx;
     }
 }

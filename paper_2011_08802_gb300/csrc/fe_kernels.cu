@@ -12,6 +12,7 @@
 // transform. A warp holds 4 elements.
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
 
@@ -159,13 +160,13 @@ __global__ void k_japply_init(int64_t nn, const dmask_t* __restrict__ mask, cons
   }
 }
 
-// Nodal 9x9 diagonal blocks (blockdiag_elem_node).
+// Nodal 9x9 diagonal blocks, one thread per node (blockdiag_node_gather).
 template <typename T>
 __global__ void __launch_bounds__(128) k_blockdiag(Grid g, JParams<T> jp, const T* __restrict__ H,
                                                    T* __restrict__ D) {
-  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if ((tid >> 3) >= g.ne()) return;
-  blockdiag_elem_node<T>(g, jp, H, D, tid >> 3, int(tid & 7));
+  const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (n >= g.nn()) return;
+  blockdiag_node_gather<T>(g, jp, H, D, n);
 }
 
 // In-place inverse of each node's 9x9 block (block_invert_node).
@@ -195,6 +196,31 @@ __global__ void k_qp_eval(DevParams P, int64_t n, const double* __restrict__ F,
 
 inline unsigned grid_for(int64_t threads, int block) {
   return unsigned((threads + block - 1) / block);
+}
+
+// y += J v over element blocks [b0, b1) (persistent warps; the slab
+// pipeline of the host-buffer entry point).
+template <typename T>
+__global__ void __launch_bounds__(256) k_japply_range(Grid g, JParams<T> jp, const T* __restrict__ H,
+                                                      const dmask_t* __restrict__ mask, const T* __restrict__ v,
+                                                      T* __restrict__ y, int64_t b0, int64_t b1) {
+  const int64_t wg = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int lane = int(threadIdx.x & 31);
+  for (int64_t blk = b0 + wg; blk < b1; blk += nw) japply_block<T>(g, jp, H, mask, v, y, blk, lane);
+}
+
+// y = v at the Dirichlet DOFs of nodes [n0, n1) (their rows are identity;
+// element contributions skip them).
+template <typename T>
+__global__ void k_identity_rows(int64_t nn, const dmask_t* __restrict__ mask, const T* __restrict__ v,
+                                T* __restrict__ y, int64_t n0, int64_t n1) {
+  const int64_t span = n1 - n0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < NF * span; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t node = n0 + i % span;
+    const int f = int(i / span);
+    if ((mask[node] >> f) & 1) y[f * nn + node] = v[f * nn + node];
+  }
 }
 
 // element blocks a warp prefetches ahead of the one it works on
@@ -231,17 +257,21 @@ void launch_linearize(const Grid& g, const DevParams& P, const double* U, const 
 // (precision, size class = floor(log2 element blocks)) key times every
 // candidate three times with events and keeps the fastest; the choice is
 // cached for the process and, when PFM_AUTOTUNE_FILE names a file, read from
-// and appended to it ("prec class threads ctas_per_sm" lines). No tuning runs
-// while the stream is being captured into a graph (the default shape is used).
+// and written back to it as JSON (format below). No tuning runs while the
+// stream is being captured into a graph (the default shape is used).
 struct JShape {
   int threads = 256;
   int per_sm = 2;
+  double ms = 0.0;  // timed milliseconds per application (0 = not timed)
 };
 
 std::mutex g_tune_mutex;
 std::map<std::pair<int, int>, JShape> g_tuned;
 bool g_tune_file_read = false;
 
+// The cache file (PFM_AUTOTUNE_FILE) is a JSON array with one object per line:
+//   {"kernel": "k_japply", "precision": "f32", "size_class": 17, "threads": 256,
+//    "ctas_per_sm": 2, "ms_per_application": 1.2713}
 void tune_file_read() {
   if (g_tune_file_read) return;
   g_tune_file_read = true;
@@ -249,18 +279,38 @@ void tune_file_read() {
   if (!path) return;
   std::FILE* f = std::fopen(path, "r");
   if (!f) return;
-  int pr, cl, th, ps;
-  while (std::fscanf(f, "%d %d %d %d", &pr, &cl, &th, &ps) == 4)
-    if ((th == 128 || th == 256) && ps >= 1 && ps <= 16) g_tuned[{pr, cl}] = JShape{th, ps};
+  char line[512];
+  while (std::fgets(line, sizeof(line), f)) {
+    char prec[8] = {0};
+    int cl, th, ps;
+    double ms = 0.0;
+    if (std::sscanf(line,
+                    " {\"kernel\": \"k_japply\", \"precision\": \"%3[f0-9]\", \"size_class\": %d, \"threads\": %d, "
+                    "\"ctas_per_sm\": %d, \"ms_per_application\": %lf",
+                    prec, &cl, &th, &ps, &ms) == 5) {
+      const int pr = std::strcmp(prec, "f32") == 0 ? 0 : (std::strcmp(prec, "f64") == 0 ? 1 : -1);
+      if (pr >= 0 && (th == 128 || th == 256) && ps >= 1 && ps <= 16) g_tuned[{pr, cl}] = JShape{th, ps, ms};
+    }
+  }
   std::fclose(f);
 }
 
-void tune_file_append(int pr, int cl, const JShape& js) {
+// rewrite the whole cache (entries of this process merged with what was read)
+void tune_file_write() {
   const char* path = std::getenv("PFM_AUTOTUNE_FILE");
   if (!path) return;
-  std::FILE* f = std::fopen(path, "a");
+  std::FILE* f = std::fopen(path, "w");
   if (!f) return;
-  std::fprintf(f, "%d %d %d %d\n", pr, cl, js.threads, js.per_sm);
+  std::fprintf(f, "[\n");
+  size_t i = 0;
+  for (const auto& kv : g_tuned) {
+    std::fprintf(f,
+                 " {\"kernel\": \"k_japply\", \"precision\": \"%s\", \"size_class\": %d, \"threads\": %d, "
+                 "\"ctas_per_sm\": %d, \"ms_per_application\": %.6f}%s\n",
+                 kv.first.first == 0 ? "f32" : "f64", kv.first.second, kv.second.threads, kv.second.per_sm,
+                 kv.second.ms, ++i < g_tuned.size() ? "," : "");
+  }
+  std::fprintf(f, "]\n");
   std::fclose(f);
 }
 
@@ -320,13 +370,14 @@ JShape japply_tune(const Grid& g, const JParams<T>& jp, const T* H, const dmask_
       if (ms < best_ms) {
         best_ms = ms;
         best = js;
+        best.ms = ms / 3.0;
       }
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   g_tuned[{pr, cl}] = best;
-  tune_file_append(pr, cl, best);
+  tune_file_write();
   return best;
 }
 
@@ -359,9 +410,7 @@ template <typename T>
 void launch_blockdiag(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, T* D,
                       cudaStream_t s) {
   (void)mask;
-  cudaMemsetAsync(D, 0, sizeof(T) * 81 * g.nn(), s);
-  const int64_t threads = g.ne() * 8;
-  k_blockdiag<T><<<grid_for(threads, 128), 128, 0, s>>>(g, make_jparams<T>(g, P), H, D);
+  k_blockdiag<T><<<grid_for(g.nn(), 128), 128, 0, s>>>(g, make_jparams<T>(g, P), H, D);
   count_launches(1);
 }
 
@@ -376,6 +425,42 @@ void launch_qp_eval(const DevParams& P, int64_t n, const double* F, const double
   k_qp_eval<<<grid_for(n, 64), 64, 0, s>>>(P, n, F, eta, eta_n, W, grad, hess);
   count_launches(1);
 }
+
+template <typename T>
+void launch_japply_range(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, const T* v, T* y,
+                         int64_t b0, int64_t b1, int blocks, cudaStream_t s) {
+  if (b1 <= b0) return;
+  const int64_t need = ((b1 - b0) * 32 + 255) / 256;
+  k_japply_range<T><<<unsigned(need < blocks ? need : blocks), 256, 0, s>>>(g, make_jparams<T>(g, P), H, mask, v, y,
+                                                                            b0, b1);
+  count_launches(1);
+}
+
+template <typename T>
+void launch_identity_rows(int64_t nn, const dmask_t* mask, const T* v, T* y, int64_t n0, int64_t n1, cudaStream_t s) {
+  if (n1 <= n0) return;
+  const int64_t t = NF * (n1 - n0);
+  k_identity_rows<T><<<grid_for(t, 256) < 2048 ? grid_for(t, 256) : 2048, 256, 0, s>>>(nn, mask, v, y, n0, n1);
+  count_launches(1);
+}
+
+int japply_range_blocks() {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_japply_range<float>, 256, 0);
+    if (per_sm < 1) per_sm = 1;
+  }
+  return sm_count() * per_sm;
+}
+
+template void launch_japply_range<float>(const Grid&, const DevParams&, const float*, const dmask_t*, const float*,
+                                         float*, int64_t, int64_t, int, cudaStream_t);
+template void launch_japply_range<double>(const Grid&, const DevParams&, const double*, const dmask_t*,
+                                          const double*, double*, int64_t, int64_t, int, cudaStream_t);
+template void launch_identity_rows<float>(int64_t, const dmask_t*, const float*, float*, int64_t, int64_t,
+                                          cudaStream_t);
+template void launch_identity_rows<double>(int64_t, const dmask_t*, const double*, double*, int64_t, int64_t,
+                                           cudaStream_t);
 
 template void launch_japply<float>(const Grid&, const DevParams&, const float*, const dmask_t*,
                                    const float*, float*, cudaStream_t);

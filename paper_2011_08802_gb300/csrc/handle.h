@@ -101,9 +101,13 @@ struct pfm_handle {
   int* gj_used = nullptr;
   int* gj_piv = nullptr;
   int nc_dofs = 0;
-  // staging for the host-buffer entry point
+  // staging for the host-buffer entry point, and its slab pipeline
   void* stage_in = nullptr;
   void* stage_out = nullptr;
+  static constexpr int PIPE_SLABS = 8;
+  cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
+  cudaEvent_t pipe_ev_in[PIPE_SLABS] = {}, pipe_ev_done[PIPE_SLABS] = {};
+  cudaEvent_t pipe_ev_start = nullptr;
   int power_its = 30;
   bool outer_df = true;  // outer operator of the mixed solve in double-float arithmetic
   bool lin_df = false;   // FP64-class linearisation in double-float instead of FP64 arithmetic

@@ -226,9 +226,11 @@ __global__ void k_power_init(int64_t nn, const dmask_t* __restrict__ mask, T* __
 // x = y / sqrt(*dot)
 template <typename T>
 __global__ void k_scale_inv_sqrt(int64_t n, const T* __restrict__ y, const double* __restrict__ dot, T* __restrict__ x) {
-  const double s = 1.0 / sqrt(*dot);
+  __shared__ T s;  // one FP64 square root and division per block, not per thread
+  if (threadIdx.x == 0) s = T(1.0 / sqrt(*dot));
+  __syncthreads();
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    x[i] = T(double(y[i]) * s);
+    x[i] = y[i] * s;
 }
 
 }  // namespace

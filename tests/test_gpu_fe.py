@@ -160,3 +160,43 @@ def test_double_float_linearisation(ragged):
         assert _relerr(y, (K @ v.reshape(-1)).reshape(v.shape)) < 1e-11
     finally:
         P.set_linearize_arithmetic(False)
+
+
+def test_autotune_cache_is_json(tmp_path):
+    """The launch-shape autotuner keeps its choices in PFM_AUTOTUNE_FILE as a
+    JSON array (checked in a fresh process, so that the tuning runs)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    path = tmp_path / "tune.json"
+    code = ("import sys; sys.path.insert(0, '.'); import torch; "
+            "from paper_2011_08802_gb300 import abi, binding, inputs; "
+            "st = inputs.config_random(12, 12, 12, seed=1); P = binding.problem_from_state(st); "
+            "P.linearize(abi.PFM_F32); P.jacobian_apply(torch.zeros(P.shape, dtype=torch.float32, device='cuda')); "
+            "torch.cuda.synchronize()")
+    env = dict(os.environ, PFM_AUTOTUNE_FILE=str(path))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run([sys.executable, "-c", code], check=True, env=env, cwd=root, timeout=600)
+    entries = json.loads(path.read_text())
+    assert any(e["kernel"] == "k_japply" and e["precision"] == "f32" and e["threads"] in (128, 256)
+               and e["ctas_per_sm"] >= 1 and e["ms_per_application"] > 0 for e in entries), entries
+
+
+@pytest.mark.parametrize("dims", [(16, 8, 12), (7, 5, 11)])
+def test_host_buffer_pipeline_matches_device_apply(binding, dims):
+    """The host-buffer entry point streams the input in and the result out in
+    z-slabs while it computes; it gives the device entry point's product (a
+    7x5 layer has 35 elements, so element blocks straddle the slab borders)."""
+    nx, ny, nz = dims
+    st = inputs.config_random(nx, ny, nz, seed=4, Lx=2.0 * nx, Ly=2.0 * ny, Lz=2.0 * nz)
+    P = binding.problem_from_state(st)
+    P.linearize(abi.PFM_F32)
+    rng = np.random.default_rng(9)
+    for dt, tol in ((np.float64, 1e-13), (np.float32, 3e-6)):
+        v = rng.standard_normal(st.U.shape).astype(dt)
+        y_dev = P.jacobian_apply(torch.from_numpy(v).cuda()).cpu().numpy()
+        y_host = P.jacobian_apply_host(torch.from_numpy(v).pin_memory())
+        y_host = y_host.numpy() if hasattr(y_host, "numpy") else np.asarray(y_host)
+        assert np.abs(y_host - y_dev).max() <= tol * np.abs(y_dev).max()
+    P.close()

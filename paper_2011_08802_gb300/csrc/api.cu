@@ -278,6 +278,20 @@ pfm_status norm2(pfm_handle* h, const double* x, int64_t n, double* out) {
   return PFM_OK;
 }
 
+// Scratch of at least `bytes` for the diagonal-block passes (kept on the handle).
+pfm_status bd_scratch(pfm_handle* h, size_t bytes) {
+  if (h->bd_bytes >= bytes) return PFM_OK;
+  if (h->bd_scratch) CK(cudaStreamSynchronize(h->stream));
+  if (h->bd_scratch) cudaFree(h->bd_scratch);
+  h->bd_scratch = nullptr;
+  h->bd_bytes = 0;
+  char* p = nullptr;
+  TRY(dalloc(h, &p, bytes));
+  h->bd_scratch = p;
+  h->bd_bytes = bytes;
+  return PFM_OK;
+}
+
 pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
   cudaStream_t s = h->stream;
   if (h->vgraph) {  // smoother coefficients change with the eigenvalue estimates
@@ -322,7 +336,8 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
     if (coarsest) continue;
     if (prec == PFM_F32) {
       TRY(dalloc(h, &lv.D32, size_t(81) * lv.nn));
-      launch_blockdiag<float>(lv.g, h->dp, lv.H32, lv.mask, lv.D32, s);
+      TRY(bd_scratch(h, size_t(45) * 32 * lv.nblk * sizeof(float)));
+      launch_blockdiag<float>(lv.g, h->dp, lv.H32, lv.mask, lv.D32, static_cast<float*>(h->bd_scratch), s);
       if (h->contact_on) launch_contact_blockdiag<float>(lv.g, lv.Kc32, lv.D32, s);
       launch_block_invert<float>(lv.nn, lv.mask, lv.D32, h->flag_dev, s);
       CKL();
@@ -330,7 +345,8 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
       TRY(estimate_lambda<float>(h, l));
     } else {
       TRY(dalloc(h, &lv.D64, size_t(81) * lv.nn));
-      launch_blockdiag<double>(lv.g, h->dp, lv.H64, lv.mask, lv.D64, s);
+      TRY(bd_scratch(h, size_t(45) * 32 * lv.nblk * sizeof(double)));
+      launch_blockdiag<double>(lv.g, h->dp, lv.H64, lv.mask, lv.D64, static_cast<double*>(h->bd_scratch), s);
       if (h->contact_on) launch_contact_blockdiag<double>(lv.g, lv.Kc64, lv.D64, s);
       launch_block_invert<double>(lv.nn, lv.mask, lv.D64, h->flag_dev, s);
       CKL();
@@ -692,7 +708,7 @@ namespace {
 // slab s's input node planes travel host -> device on one copy stream while
 // the slab before computes; once slabs <= s are done, the node planes below
 // slab s+1 are complete and travel back on a second copy stream. Each copy is
-// one 2D transfer over the 9 fields (field stride nn).
+// one transfer per field (field stride nn).
 template <typename T>
 pfm_status japply_host_pipelined(pfm_handle* h, const void* v_host, void* y_host) {
   Level& f = h->L[0];
@@ -716,7 +732,6 @@ pfm_status japply_host_pipelined(pfm_handle* h, const void* v_host, void* y_host
   const int64_t nn = f.nn, plane = int64_t(g.nx + 1) * (g.ny + 1);
   const int64_t eplane = int64_t(g.nx) * g.ny;  // elements per layer
   const int S = std::min(pfm_handle::PIPE_SLABS, g.nz);
-  const size_t pitch = sizeof(T) * nn;
   cudaStream_t sc = h->stream;
   const int blocks = japply_range_blocks();
   // the copy streams start after everything already queued on the compute stream
@@ -730,8 +745,9 @@ pfm_status japply_host_pipelined(pfm_handle* h, const void* v_host, void* y_host
     const int64_t k0 = int64_t(g.nz) * s / S, k1 = int64_t(g.nz) * (s + 1) / S;  // element layers [k0, k1)
     const int64_t need = k1 + 1;                                                   // node planes [0, k1]
     if (need > in_done) {
-      CK(cudaMemcpy2DAsync(vd + in_done * plane, pitch, vh + in_done * plane, pitch,
-                           sizeof(T) * (need - in_done) * plane, NF, cudaMemcpyHostToDevice, h->pipe_in));
+      for (int fld = 0; fld < NF; ++fld)
+        CK(cudaMemcpyAsync(vd + fld * nn + in_done * plane, vh + fld * nn + in_done * plane,
+                           sizeof(T) * (need - in_done) * plane, cudaMemcpyHostToDevice, h->pipe_in));
       in_done = need;
     }
     CK(cudaEventRecord(h->pipe_ev_in[s], h->pipe_in));
@@ -750,8 +766,9 @@ pfm_status japply_host_pipelined(pfm_handle* h, const void* v_host, void* y_host
     CK(cudaEventRecord(h->pipe_ev_done[s], sc));
     CK(cudaStreamWaitEvent(h->pipe_out, h->pipe_ev_done[s], 0));
     if (ready > out_done) {
-      CK(cudaMemcpy2DAsync(yh + out_done * plane, pitch, yd + out_done * plane, pitch,
-                           sizeof(T) * (ready - out_done) * plane, NF, cudaMemcpyDeviceToHost, h->pipe_out));
+      for (int fld = 0; fld < NF; ++fld)
+        CK(cudaMemcpyAsync(yh + fld * nn + out_done * plane, yd + fld * nn + out_done * plane,
+                           sizeof(T) * (ready - out_done) * plane, cudaMemcpyDeviceToHost, h->pipe_out));
       out_done = ready;
     }
   }
@@ -867,6 +884,7 @@ void pfm_destroy(pfm_handle* h) {
     }
     cudaEventDestroy(h->pipe_ev_start);
   }
+  if (h->bd_scratch) cudaFree(h->bd_scratch);
   if (h->stage_in) cudaFree(h->stage_in);
   if (h->stage_out) cudaFree(h->stage_out);
   delete h;

@@ -68,8 +68,8 @@ template <typename T>
 void launch_identity_rows(int64_t nn, const dmask_t* mask, const T* v, T* y, int64_t n0, int64_t n1, cudaStream_t s);
 int japply_range_blocks();  // persistent grid of k_japply_range
 template <typename T>
-void launch_blockdiag(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, T* D,
-                      cudaStream_t s);
+void launch_blockdiag(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, T* D, T* W,
+                      cudaStream_t s);  // W: scratch of 45 * 32 * nblk entries
 template <typename T>
 void launch_block_invert(int64_t nn, const dmask_t* mask, T* D, int* singular, cudaStream_t s);
 void launch_qp_eval(const DevParams& P, int64_t n, const double* F, const double* eta,

@@ -249,45 +249,6 @@ __device__ __forceinline__ void blockdiag_elem_node(const Grid& g, const JParams
     }
 }
 
-// Node n (i + (nx+1)(j + (ny+1)k)): gathers the contributions of its (up to 8)
-// adjacent elements in a fixed order and writes its whole block, without
-// atomics. Consecutive nodes share elements, whose Hessians then come from L2.
-template <typename T>
-__device__ __forceinline__ void blockdiag_node_gather(const Grid& g, const JParams<T>& jp, const T* __restrict__ H,
-                                                      T* __restrict__ D, int64_t n) {
-  const int64_t nn = g.nn();
-  const int i = int(n % (g.nx + 1));
-  const int j = int((n / (g.nx + 1)) % (g.ny + 1));
-  const int k = int(n / (int64_t(g.nx + 1) * (g.ny + 1)));
-  T Db[45];
-#pragma unroll
-  for (int t = 0; t < 45; ++t) Db[t] = T(0);
-  for (int dk = 0; dk < 2; ++dk) {
-    const int ek = k - 1 + dk;
-    if (ek < 0 || ek >= g.nz) continue;
-    for (int dj = 0; dj < 2; ++dj) {
-      const int ej = j - 1 + dj;
-      if (ej < 0 || ej >= g.ny) continue;
-      for (int di = 0; di < 2; ++di) {
-        const int ei = i - 1 + di;
-        if (ei < 0 || ei >= g.nx) continue;
-        const int64_t e = ei + int64_t(g.nx) * (ej + int64_t(g.ny) * ek);
-        const int a = (1 - di) + 2 * (1 - dj) + 4 * (1 - dk);  // this node's corner in element e
-        blockdiag_accumulate<T>(jp, H, e >> 2, int(e & 3) * 8, a, Db);
-      }
-    }
-  }
-  int idx = 0;
-#pragma unroll
-  for (int r = 0; r < 9; ++r)
-#pragma unroll
-    for (int c = r; c < 9; ++c) {
-      D[(r * 9 + c) * nn + n] = Db[idx];
-      if (c != r) D[(c * 9 + r) * nn + n] = Db[idx];
-      ++idx;
-    }
-}
-
 // In-place inverse of one node's 9x9 block (Dirichlet rows/columns replaced
 // by identity first) by Gauss-Jordan elimination with partial pivoting; a
 // singular block sets *singular and is replaced by the identity.
@@ -511,6 +472,29 @@ inline DfConst make_dfconst(const Grid& g, const DevParams& P) {
   return k;
 }
 
+// Compensated accumulator s + c for sums of products h * z with h = hh + hl
+// (two FP32 parts) and z a double-float number (the compensated dot product
+// of Ogita, Rump and Oishi 2005): the leading product hh * z.hi is split
+// exactly by a fused multiply-add, its sum into s by TwoSum, and every
+// rounding error and the two small cross products go into c. Twelve FP32
+// operations per term instead of eighteen for a double-float multiply-add,
+// with the same (twice FP32) working accuracy.
+struct cacc {
+  float s, c;
+};
+__device__ __forceinline__ void cacc_add(cacc& a, float hh, float hl, dfl z) {
+  const float p = __fmul_rn(hh, z.hi);
+  const float e = __fmaf_rn(hh, z.hi, -p);
+  const float s = __fadd_rn(a.s, p);
+  const float bb = __fsub_rn(s, a.s);
+  const float q = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  float c = __fmaf_rn(hh, z.lo, a.c);
+  c = __fmaf_rn(hl, z.hi, c);
+  a.c = __fadd_rn(c, __fadd_rn(q, e));
+  a.s = s;
+}
+__device__ __forceinline__ dfl cacc_value(const cacc& a) { return df_two_sum(a.s, a.c); }
+
 // y += J v on element block blk in double-float arithmetic: v in FP32
 // (exact input), the tangent as Hhi + Hlo (two FP32 stores of the FP64
 // Hessians), element contributions added to the FP64 output y.
@@ -536,9 +520,9 @@ __device__ __forceinline__ void japply_df_block(const Grid& g, const DfConst& k,
     const float x = ((dm >> (3 + kk)) & 1) ? 0.f : v[(3 + kk) * nn + node];
     q1_gather_df(dfl{x, 0.f}, l8, k, dz[9 + kk], ge[3 * kk], ge[3 * kk + 1], ge[3 * kk + 2]);
   }
-  dfl sg[NZ];
+  cacc acc[NZ];
 #pragma unroll
-  for (int r = 0; r < NZ; ++r) sg[r] = dfl{0.f, 0.f};
+  for (int r = 0; r < NZ; ++r) acc[r] = cacc{0.f, 0.f};
   const float4* Hh = reinterpret_cast<const float4*>(Hhi) + blk * (NH / 4) * 32 + lane;
   const float4* Hl = reinterpret_cast<const float4*>(Hlo) + blk * (NH / 4) * 32 + lane;
 #pragma unroll 2
@@ -551,11 +535,13 @@ __device__ __forceinline__ void japply_df_block(const Grid& g, const DfConst& k,
       const int idx = j * 4 + t;
       const int r = packed_row(idx);
       const int c = r + (idx - packed_row_start(r));
-      const dfl hv{hh[t], hl[t]};
-      sg[r] = df_add(sg[r], df_mul(hv, dz[c]));
-      if (c != r) sg[c] = df_add(sg[c], df_mul(hv, dz[r]));
+      cacc_add(acc[r], hh[t], hl[t], dz[c]);
+      if (c != r) cacc_add(acc[c], hh[t], hl[t], dz[r]);
     }
   }
+  dfl sg[NZ];
+#pragma unroll
+  for (int r = 0; r < NZ; ++r) sg[r] = cacc_value(acc[r]);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     dfl r = q1_scatter_df(dfl{0.f, 0.f}, df_mul(k.w, sg[3 * i]), df_mul(k.w, sg[3 * i + 1]),
@@ -567,10 +553,10 @@ __device__ __forceinline__ void japply_df_block(const Grid& g, const DfConst& k,
     dfl gf[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      dfl s = dfl{0.f, 0.f};
+      cacc s = cacc{0.f, 0.f};
 #pragma unroll
-      for (int l = 0; l < 6; ++l) s = df_add(s, df_mul(k.G[kk][l], ge[3 * l + d]));
-      gf[d] = df_mul(k.w, s);
+      for (int l = 0; l < 6; ++l) cacc_add(s, k.G[kk][l].hi, k.G[kk][l].lo, ge[3 * l + d]);
+      gf[d] = df_mul(k.w, cacc_value(s));
     }
     dfl r = q1_scatter_df(df_mul(k.w, sg[9 + kk]), gf[0], gf[1], gf[2], true, l8, k);
     if (valid && !((dm >> (3 + kk)) & 1)) atomicAdd(&y[(3 + kk) * nn + node], double(r.hi) + double(r.lo));

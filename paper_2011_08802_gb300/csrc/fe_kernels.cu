@@ -160,13 +160,73 @@ __global__ void k_japply_init(int64_t nn, const dmask_t* __restrict__ mask, cons
   }
 }
 
-// Nodal 9x9 diagonal blocks, one thread per node (blockdiag_node_gather).
+// Nodal 9x9 diagonal blocks in two passes without atomics. Pass 1: one warp
+// per element block stages the block's Gauss-point Hessians in shared memory
+// (one coalesced read of the store) and thread (element, local node a) writes
+// that element's 45-entry contribution to node a into W[t][blk*32 + lane].
 template <typename T>
-__global__ void __launch_bounds__(128) k_blockdiag(Grid g, JParams<T> jp, const T* __restrict__ H,
-                                                   T* __restrict__ D) {
+__global__ void __launch_bounds__(128) k_blockdiag_elem(Grid g, JParams<T> jp, const T* __restrict__ H,
+                                                        T* __restrict__ W) {
+  extern __shared__ __align__(16) unsigned char bd_smem[];
+  constexpr int V = 16 / sizeof(T);
+  using VT = typename Vec16<T>::type;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t blk = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (blk >= g.nblk()) return;
+  VT* S = reinterpret_cast<VT*>(bd_smem) + int64_t(wid) * (HBLK / V);
+  const VT* src = reinterpret_cast<const VT*>(H) + blk * (HBLK / V);
+  for (int i = lane; i < int(HBLK / V); i += 32) S[i] = src[i];
+  __syncwarp();
+  T Db[45];
+#pragma unroll
+  for (int t = 0; t < 45; ++t) Db[t] = T(0);
+  const int64_t e = blk * 4 + (lane >> 3);
+  if (e < g.ne()) blockdiag_accumulate<T>(jp, reinterpret_cast<const T*>(S), 0, (lane >> 3) * 8, lane & 7, Db);
+  const int64_t stride = g.nblk() * 32;
+#pragma unroll
+  for (int t = 0; t < 45; ++t) W[t * stride + blk * 32 + lane] = Db[t];
+}
+
+// Pass 2: node n sums the contributions of its (up to 8) adjacent elements in
+// a fixed order and writes its whole block.
+template <typename T>
+__global__ void __launch_bounds__(128) k_blockdiag_node(Grid g, const T* __restrict__ W, T* __restrict__ D) {
   const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (n >= g.nn()) return;
-  blockdiag_node_gather<T>(g, jp, H, D, n);
+  const int64_t nn = g.nn();
+  if (n >= nn) return;
+  const int i = int(n % (g.nx + 1));
+  const int j = int((n / (g.nx + 1)) % (g.ny + 1));
+  const int k = int(n / (int64_t(g.nx + 1) * (g.ny + 1)));
+  const int64_t stride = g.nblk() * 32;
+  T Db[45];
+#pragma unroll
+  for (int t = 0; t < 45; ++t) Db[t] = T(0);
+  for (int dk = 0; dk < 2; ++dk) {
+    const int ek = k - 1 + dk;
+    if (ek < 0 || ek >= g.nz) continue;
+    for (int dj = 0; dj < 2; ++dj) {
+      const int ej = j - 1 + dj;
+      if (ej < 0 || ej >= g.ny) continue;
+      for (int di = 0; di < 2; ++di) {
+        const int ei = i - 1 + di;
+        if (ei < 0 || ei >= g.nx) continue;
+        const int64_t e = ei + int64_t(g.nx) * (ej + int64_t(g.ny) * ek);
+        const int a = (1 - di) + 2 * (1 - dj) + 4 * (1 - dk);
+        const int64_t col = (e >> 2) * 32 + (e & 3) * 8 + a;
+#pragma unroll
+        for (int t = 0; t < 45; ++t) Db[t] += W[t * stride + col];
+      }
+    }
+  }
+  int idx = 0;
+#pragma unroll
+  for (int r = 0; r < 9; ++r)
+#pragma unroll
+    for (int c = r; c < 9; ++c) {
+      D[(r * 9 + c) * nn + n] = Db[idx];
+      if (c != r) D[(c * 9 + r) * nn + n] = Db[idx];
+      ++idx;
+    }
 }
 
 // In-place inverse of each node's 9x9 block (block_invert_node).
@@ -407,11 +467,20 @@ void launch_japply_df(const Grid& g, const DevParams& P, const float* Hhi, const
 }
 
 template <typename T>
-void launch_blockdiag(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, T* D,
+void launch_blockdiag(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, T* D, T* W,
                       cudaStream_t s) {
   (void)mask;
-  k_blockdiag<T><<<grid_for(g.nn(), 128), 128, 0, s>>>(g, make_jparams<T>(g, P), H, D);
-  count_launches(1);
+  // 4 element blocks per CTA in FP32 (60 KB of staged Hessians), 2 in FP64
+  const int warps = sizeof(T) == 4 ? 4 : 2;
+  const int smem = int(warps * HBLK * sizeof(T));
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[sizeof(T) == 8]) {
+    cudaFuncSetAttribute(k_blockdiag_elem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr_set[sizeof(T) == 8] = true;
+  }
+  k_blockdiag_elem<T><<<grid_for(g.nblk() * 32, 32 * warps), 32 * warps, smem, s>>>(g, make_jparams<T>(g, P), H, W);
+  k_blockdiag_node<T><<<grid_for(g.nn(), 128), 128, 0, s>>>(g, W, D);
+  count_launches(2);
 }
 
 template <typename T>
@@ -466,9 +535,9 @@ template void launch_japply<float>(const Grid&, const DevParams&, const float*, 
                                    const float*, float*, cudaStream_t);
 template void launch_japply<double>(const Grid&, const DevParams&, const double*, const dmask_t*,
                                      const double*, double*, cudaStream_t);
-template void launch_blockdiag<float>(const Grid&, const DevParams&, const float*, const dmask_t*,
+template void launch_blockdiag<float>(const Grid&, const DevParams&, const float*, const dmask_t*, float*,
                                       float*, cudaStream_t);
-template void launch_blockdiag<double>(const Grid&, const DevParams&, const double*, const dmask_t*,
+template void launch_blockdiag<double>(const Grid&, const DevParams&, const double*, const dmask_t*, double*,
                                        double*, cudaStream_t);
 template void launch_block_invert<float>(int64_t, const dmask_t*, float*, int*, cudaStream_t);
 template void launch_block_invert<double>(int64_t, const dmask_t*, double*, int*, cudaStream_t);

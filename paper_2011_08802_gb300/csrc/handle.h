@@ -101,6 +101,9 @@ struct pfm_handle {
   int* gj_used = nullptr;
   int* gj_piv = nullptr;
   int nc_dofs = 0;
+  // per-(element, node) diagonal-block contributions (linearisation scratch)
+  void* bd_scratch = nullptr;
+  size_t bd_bytes = 0;
   // staging for the host-buffer entry point, and its slab pipeline
   void* stage_in = nullptr;
   void* stage_out = nullptr;

@@ -261,7 +261,7 @@ inline unsigned grid_for(int64_t threads, int block) {
 // y += J v over element blocks [b0, b1) (persistent warps; the slab
 // pipeline of the host-buffer entry point).
 template <typename T>
-__global__ void __launch_bounds__(256) k_japply_range(Grid g, JParams<T> jp, const T* __restrict__ H,
+__global__ void __launch_bounds__(256, PFM_JAPPLY_MINB) k_japply_range(Grid g, JParams<T> jp, const T* __restrict__ H,
                                                       const dmask_t* __restrict__ mask, const T* __restrict__ v,
                                                       T* __restrict__ y, int64_t b0, int64_t b1) {
   const int64_t wg = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;

@@ -61,7 +61,7 @@ class SolveReport(C.Structure):
 
 
 def default_opts(precond: int = PFM_F32, **kw) -> SolveOpts:
-    o = SolveOpts(max_newton=1, restart=30, max_lin_it=300, nu_pre=6, nu_post=6,
+    o = SolveOpts(max_newton=1, restart=30, max_lin_it=300, nu_pre=2, nu_post=8,
                   newton_rtol=1e-8, lin_rtol=1e-8, omega=0.7, precond=precond,
                   smoother=0, cheb_lo=0.05, cheb_hi=1.1, cycle_gamma=1, nu_growth=1.25)
     for k, v in kw.items():

@@ -745,20 +745,31 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
       for (int c = 0; c < 3; ++c)
         Z[b][c] = f2[0][b][c] * Tt[0][b] * symget(Xs[k], 0, c) + f2[1][b][c] * Tt[1][b] * symget(Xs[k], 1, c) +
                   f2[2][b][c] * Tt[2][b] * symget(Xs[k], 2, c);
+    // X~_l is symmetric: Z : X~_l runs over its 6 stored entries with Z's
+    // symmetric part (off-diagonal pairs summed)
+    const T Zs[6] = {Z[0][0], Z[1][1], Z[2][2], Z[1][2] + Z[2][1], Z[0][2] + Z[2][0], Z[0][1] + Z[1][0]};
     for (int l = k; l < ND; ++l) {
-      T dl = 0;
-      for (int I = 0; I < 6; ++I) dl += dv[l][I] * Ld[I];
-      T K = 0;
-      for (int b = 0; b < 3; ++b)
-        for (int c = 0; c < 3; ++c) K += Z[b][c] * symget(Xs[l], b, c);
-      H16[hp16(k, l)] = Jt * (dl + K);
+      T acc = 0;
+      for (int I = 0; I < 6; ++I) acc += dv[l][I] * Ld[I] + Zs[I] * Xs[l][I];
+      H16[hp16(k, l)] = Jt * acc;
     }
     // S~ : X~_k and (L_p h)~ : d~_k (tensor double contractions of symmetric matrices)
     T SX = 0;
     for (int v = 0; v < 6; ++v) SX += (v < 3 ? T(1) : T(2)) * St[sym_i(v)][sym_j(v)] * Xs[k][v];
+    // (L_p h)~ : d~_k (dv carries the shear factor 2), one dot product when
+    // every phase shares the stiffness
+    T Ld2p[NPH];
     for (int p = 0; p < NPH; ++p) {
-      T Ld2 = 0;
-      for (int v = 0; v < 6; ++v) Ld2 += LhT[p][v] * dv[k][v];  // dv carries the shear factor 2
+      if (P.same_L && p > 0) {
+        Ld2p[p] = Ld2p[0];
+        continue;
+      }
+      T d = 0;
+      for (int v = 0; v < 6; ++v) d += LhT[p][v] * dv[k][v];
+      Ld2p[p] = d;
+    }
+    for (int p = 0; p < NPH; ++p) {
+      const T Ld2 = Ld2p[p];
       const T ge = trAU[p] * SX + Jt * Ld2;
       if (k < 9) {
         H16[hp16(k, 9 + p)] += ge;

@@ -248,8 +248,8 @@ PFM_HD T symget(const T* X, int a, int b) {
   const int s = a + b;  // (1,2) -> 3, (0,2) -> 2, (0,1) -> 1
   return X[s == 3 ? 3 : (s == 2 ? 4 : 5)];
 }
-// Packed index of (k, l), k <= l, in the upper triangle of a 16x16 matrix.
-PFM_HD int hp16(int k, int l) { return k * 16 - (k * (k - 1)) / 2 + (l - k); }
+// Voigt slot (00, 11, 22, 12, 02, 01) of the symmetric pair (a, c).
+PFM_HD int voigt_slot(int a, int c) { return a == c ? a : 6 - a - c; }
 
 template <typename T>
 PFM_HD void load_U(const DevParams& P, int p, T U[3][3]) {
@@ -383,32 +383,50 @@ PFM_HD T dd2_log(T x0, T x1, T x2) {
   if (gap > Tol<T>::dd2_gap * a) return (dd1_log(a, b) - dd1_log(b, c)) / gap;
   // f[x0,x1,x2] = sum_j f^(2+j)(m)/(2+j)! h_j(x - m); for log this is
   // (1/m^2) sum_j (-1)^(j+1) h_j(u)/(j+2), u = (x - m)/m, h_j the complete
-  // homogeneous symmetric polynomial of degree j.
-  T m = (a + b + c) / T(3);
-  T u0 = (a - m) / m, u1 = (b - m) / m, u2 = (c - m) / m;
-  // h_j(u0,u1) by h_j = u0 h_{j-1}(u0) ... built incrementally
-  T h2[6];  // h_j(u0,u1), j = 0..5
-  for (int j = 0; j < 6; ++j) {
-    // h_j(u0,u1) = sum_{i=0}^j u0^i u1^(j-i)
-    T s = T(0), u0i = T(1);
-    for (int i = 0; i <= j; ++i) {
-      T u1p = T(1);
-      for (int k = 0; k < j - i; ++k) u1p *= u1;
-      s += u0i * u1p;
-      u0i *= u0;
-    }
-    h2[j] = s;
-  }
+  // homogeneous symmetric polynomial of degree j, built one variable at a
+  // time: h_j(u_0..u_i) = h_j(u_0..u_(i-1)) + u_i h_(j-1)(u_0..u_i).
+  const T m = (a + b + c) / T(3);
+  const T im = T(1) / m;
+  const T u[3] = {(a - m) * im, (b - m) * im, (c - m) * im};
+  T hh[6] = {T(1), T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 1; j < 6; ++j) hh[j] = (i == 0 ? T(0) : hh[j]) + u[i] * hh[j - 1];
+  // alternating weights -1/2, 1/3, -1/4, 1/5, -1/6, 1/7
+  const T wj[6] = {T(-0.5), T(1.0 / 3.0), T(-0.25), T(0.2), T(-1.0 / 6.0), T(1.0 / 7.0)};
   T sum = T(0);
-  T sign = T(-1);
-  for (int j = 0; j < 6; ++j) {
-    // h_j(u0,u1,u2) = sum_{i=0}^j u2^i h_{j-i}(u0,u1)
-    T hj = T(0), u2i = T(1);
-    for (int i = 0; i <= j; ++i) { hj += u2i * h2[j - i]; u2i *= u2; }
-    sum += sign * hj / T(j + 2);
-    sign = -sign;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) sum += wj[j] * hh[j];
+  return sum * im * im;
+}
+
+// Second divided difference of log at (x, y, z) from the first ones
+// fxy = f[x,y], fyz = f[y,z], fxz = f[x,z]. On a wide spread it is the
+// quotient over the largest gap with the middle value as pivot, which is the
+// quotient dd2_log forms after sorting (the same operands up to signs, so the
+// same result); on a narrow spread, dd2_log's series.
+template <typename T>
+PFM_HD T dd2_log_f1(T x, T y, T z, T fxy, T fyz, T fxz) {
+  const T dxz = x - z, dxy = x - y, dyz = y - z;
+  const T axz = fabs(dxz), axy = fabs(dxy), ayz = fabs(dyz);
+  T num, den, gap;
+  if (axz >= axy && axz >= ayz) {  // y in the middle
+    num = fxy - fyz;
+    den = dxz;
+    gap = axz;
+  } else if (axy >= ayz) {  // z in the middle
+    num = fxz - fyz;
+    den = dxy;
+    gap = axy;
+  } else {  // x in the middle
+    num = fxy - fxz;
+    den = dyz;
+    gap = ayz;
   }
-  return sum / (m * m);
+  const T top = x > y ? (x > z ? x : z) : (y > z ? y : z);
+  if (gap > Tol<T>::dd2_gap * top) return num / den;
+  return dd2_log(x, y, z);
 }
 
 // ---------------------------------------------------------------------------
@@ -474,7 +492,7 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int b = 0; b < 3; ++b) f1[a][b] = (a == b) ? T(1) / lam[a] : dd1_log(lam[a], lam[b]);
+      for (int b = a; b < 3; ++b) f1[a][b] = f1[b][a] = (a == b) ? T(1) / lam[a] : dd1_log(lam[a], lam[b]);
   } else {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -620,13 +638,24 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
   if (!WANT_HESS) return;
 
   // ---------------------------------------------------------------------
-  // Hessian over the 16 directions (F_pQ: 0..8, eta_0..eta_6: 9..15), kept as
-  // the packed upper triangle H16[hp16(k,l)], k <= l. Rotated directions
-  // X~_k = Q^T dE_k Q are symmetric and stored as 6 values (00,11,22,12,02,01).
-  constexpr int ND = 16;
+  // Hessian in the 15 unknowns z = (F_pQ: 0..8, eta_hat_1..6: 9..14), packed
+  // into Hp[hidx(r, c)], r <= c. With eta_0 = 1 - sum eta_hat (Sec. 3.1) every
+  // eta-dependence enters through U(eta) = sum eta_i U_i and L(eta) =
+  // sum eta_i L_i, so the direction eta_hat_k carries dU_k = U_k - U_0 and
+  // dL_k = L_k - L_0 and the elimination of eta_0 holds term by term.
+  constexpr int ND = NZ;
+  T dU[6][3][3], AdU[6][3][3], trAdU[6];  // A dU_k = A U_k - A U_0
+  for (int k = 0; k < 6; ++k) {
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        dU[k][i][j] = T(P.U[k + 1][i][j]) - T(P.U[0][i][j]);
+        AdU[k][i][j] = AU[k + 1][i][j] - AU[0][i][j];
+      }
+    trAdU[k] = trAU[k + 1] - trAU[0];
+  }
+  // Rotated directions X~_k = Q^T dE_k Q, symmetric, stored as 6 values
+  // (00, 11, 22, 12, 02, 01).
   T Xs[ND][6];
-  T At[3][3];
-  rot_in(Q, A, At);
   {
     T Aq[3][3], Mq[3][3];  // Aq[c] = Q^T (column c of A), Mq[p] = Q^T (row p of M)
     for (int c = 0; c < 3; ++c)
@@ -643,23 +672,18 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
         }
       }
   }
-  for (int p = 0; p < NPH; ++p) {
-    T Up[3][3], Ut[3][3], B[3][3];
-    load_U(P, p, Up);
-    rot_in(Q, Up, Ut);
-    mm3(At, Ut, B);  // B = A~ U~_p ; dE~ = -(B Lambda + Lambda B^T)
+  for (int k = 0; k < 6; ++k) {
+    T B[3][3];
+    rot_in(Q, AdU[k], B);  // B = Q^T A dU_k Q ; dE~ = -(B Lambda + Lambda B^T)
     for (int v = 0; v < 6; ++v) {
       const int a = sym_i(v), b = sym_j(v);
-      Xs[9 + p][v] = -(B[a][b] * lam[b] + lam[a] * B[b][a]);
+      Xs[9 + k][v] = -(B[a][b] * lam[b] + lam[a] * B[b][a]);
     }
   }
-  // d~_k = Dh~[X~_k] = 1/2 f1 o X~_k as Voigt strain vectors (engineering shear)
-  T dv[ND][6];
-  for (int k = 0; k < ND; ++k)
-    for (int v = 0; v < 6; ++v) {
-      const int a = sym_i(v), b = sym_j(v);
-      dv[k][v] = T(0.5) * f1[a][b] * Xs[k][v] * (v < 3 ? T(1) : T(2));
-    }
+  // d~_k = Dh~[X~_k] = 1/2 f1 o X~_k as Voigt strain vectors (engineering
+  // shear): d~_k[v] = c[v] X~_k[v]
+  T cv[6];
+  for (int v = 0; v < 6; ++v) cv[v] = T(0.5) * f1[sym_i(v)][sym_j(v)] * (v < 3 ? T(1) : T(2));
   // L~ = Nv^T L(eta) Nv with v(Q d~ Q^T) = Nv v(d~)
   T Lt[6][6];
   {
@@ -697,14 +721,21 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
         Lt[A_][B] = s;
       }
   }
-  // second divided differences f2[a][b][c] (symmetric)
+  // The second-order part of the elastic energy along directions k, l,
+  // J_t (d~_k . L~ d~_l + K(k,l)) with K(k,l) = sum_abc f2_abc T~_ab X~_k[a][c]
+  // X~_l[b][c] (f2: second divided differences, symmetric), is one symmetric
+  // bilinear form in the 6 stored entries of X~: X~_k^T Mb X~_l with
+  // Mb[v][w] = J_t (c[v] L~[v][w] c[w] + sum of f2_abc T~_ab over the (a, b, c)
+  // whose pairs (a, c) and (b, c) have the Voigt slots v and w).
   T f2[3][3][3];
   for (int a = 0; a < 3; ++a)
     for (int b = a; b < 3; ++b)
       for (int c = b; c < 3; ++c) {
         T v;
         if (npade == 0) {
-          v = dd2_log(lam[a], lam[b], lam[c]);
+          // one eigenvalue: f'' / 2 = -1 / (2 lam^2)
+          v = (a == c) ? T(-0.5) * f1[a][a] * f1[a][a]
+                       : dd2_log_f1(lam[a], lam[b], lam[c], f1[a][b], f1[b][c], f1[a][c]);
         } else {
           v = T(0);
           for (int k = 0; k < 3; ++k)
@@ -712,71 +743,61 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
         }
         f2[a][b][c] = f2[a][c][b] = f2[b][a][c] = f2[b][c][a] = f2[c][a][b] = f2[c][b][a] = v;
       }
-  // per-phase (L_i : h) rotated, for the eta-dependence of L
-  T LhT[NPH][6];
-  for (int p = 0; p < NPH; ++p) {
-    if (P.same_L && p > 0) {
-      for (int v = 0; v < 6; ++v) LhT[p][v] = LhT[0][v];
-      continue;
+  T Mb[6][6];
+  for (int I = 0; I < 6; ++I)
+    for (int J = 0; J < 6; ++J) Mb[I][J] = cv[I] * Lt[I][J] * cv[J];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c) Mb[voigt_slot(a, c)][voigt_slot(b, c)] += f2[a][b][c] * Tt[a][b];
+  for (int I = 0; I < 6; ++I)
+    for (int J = 0; J < 6; ++J) Mb[I][J] *= Jt;
+  // (dL_k h) rotated and scaled by c, so that (dL_k h)~ : d~_l = LhT[k] . X~_l;
+  // zero when every phase has the same stiffness
+  T LhT[6][6];
+  if (!P.same_L) {
+    for (int k = 0; k < 6; ++k) {
+      T lv[6], lm[3][3], lr[3][3];
+      for (int I = 0; I < 6; ++I) {
+        T s = 0;
+        for (int J = 0; J < 6; ++J) s += (T(P.Lv[k + 1][I][J]) - T(P.Lv[0][I][J])) * hv[J];
+        lv[I] = s;
+      }
+      from_voigt_stress(lv, lm);
+      rot_in(Q, lm, lr);
+      for (int v = 0; v < 6; ++v) LhT[k][v] = cv[v] * lr[sym_i(v)][sym_j(v)];
     }
-    T lv[6], lm[3][3], lr[3][3];
-    for (int I = 0; I < 6; ++I) {
-      T s = 0;
-      for (int J = 0; J < 6; ++J) s += T(P.Lv[p][I][J]) * hv[J];
-      lv[I] = s;
-    }
-    from_voigt_stress(lv, lm);
-    rot_in(Q, lm, lr);
-    for (int v = 0; v < 6; ++v) LhT[p][v] = lr[sym_i(v)][sym_j(v)];
   }
-  T H16[ND * (ND + 1) / 2];
-  // g_EE part J_t (d~_k . L~ d~_l + K(k,l)), K(k,l) = sum_bc Z_k[b][c] X~_l[b][c],
-  // Z_k[b][c] = sum_a f2_abc T~_ab X~_k[a][c]; and the first-order terms
-  // g_{E eta_p}[X_k] = tr(AU_p) S~:X~_k + J_t (L_p h)~ : d~_k, added to the
+  // second-order part X~_k^T Mb X~_l, and the first-order terms
+  // g_{E eta_p}[X_k] = tr(A dU_p) S~:X~_k + J_t (dL_p h)~ : d~_k, added to the
   // F-eta and eta-eta entries (the latter for both index orders).
   for (int k = 0; k < ND; ++k) {
-    T Ld[6], Z[3][3];
+    T Y[6];
     for (int I = 0; I < 6; ++I) {
       T s = 0;
-      for (int J = 0; J < 6; ++J) s += Lt[I][J] * dv[k][J];
-      Ld[I] = s;
+      for (int J = 0; J < 6; ++J) s += Mb[I][J] * Xs[k][J];
+      Y[I] = s;
     }
-    for (int b = 0; b < 3; ++b)
-      for (int c = 0; c < 3; ++c)
-        Z[b][c] = f2[0][b][c] * Tt[0][b] * symget(Xs[k], 0, c) + f2[1][b][c] * Tt[1][b] * symget(Xs[k], 1, c) +
-                  f2[2][b][c] * Tt[2][b] * symget(Xs[k], 2, c);
-    // X~_l is symmetric: Z : X~_l runs over its 6 stored entries with Z's
-    // symmetric part (off-diagonal pairs summed)
-    const T Zs[6] = {Z[0][0], Z[1][1], Z[2][2], Z[1][2] + Z[2][1], Z[0][2] + Z[2][0], Z[0][1] + Z[1][0]};
     for (int l = k; l < ND; ++l) {
       T acc = 0;
-      for (int I = 0; I < 6; ++I) acc += dv[l][I] * Ld[I] + Zs[I] * Xs[l][I];
-      H16[hp16(k, l)] = Jt * acc;
+      for (int I = 0; I < 6; ++I) acc += Xs[l][I] * Y[I];
+      Hp[hidx(k, l)] = acc;
     }
-    // S~ : X~_k and (L_p h)~ : d~_k (tensor double contractions of symmetric matrices)
+    // S~ : X~_k (tensor double contraction of symmetric matrices)
     T SX = 0;
     for (int v = 0; v < 6; ++v) SX += (v < 3 ? T(1) : T(2)) * St[sym_i(v)][sym_j(v)] * Xs[k][v];
-    // (L_p h)~ : d~_k (dv carries the shear factor 2), one dot product when
-    // every phase shares the stiffness
-    T Ld2p[NPH];
-    for (int p = 0; p < NPH; ++p) {
-      if (P.same_L && p > 0) {
-        Ld2p[p] = Ld2p[0];
-        continue;
+    for (int p = 0; p < 6; ++p) {
+      T ge = trAdU[p] * SX;
+      if (!P.same_L) {
+        T d = 0;
+        for (int v = 0; v < 6; ++v) d += LhT[p][v] * Xs[k][v];
+        ge += Jt * d;
       }
-      T d = 0;
-      for (int v = 0; v < 6; ++v) d += LhT[p][v] * dv[k][v];
-      Ld2p[p] = d;
-    }
-    for (int p = 0; p < NPH; ++p) {
-      const T Ld2 = Ld2p[p];
-      const T ge = trAU[p] * SX + Jt * Ld2;
       if (k < 9) {
-        H16[hp16(k, 9 + p)] += ge;
+        Hp[hidx(k, 9 + p)] += ge;
       } else {
         const int q = k - 9;
         const int lo = p < q ? p : q, hi = p < q ? q : p;
-        H16[hp16(9 + lo, 9 + hi)] += (p == q) ? T(2) * ge : ge;
+        Hp[hidx(9 + lo, 9 + hi)] += (p == q) ? T(2) * ge : ge;
       }
     }
   }
@@ -789,58 +810,43 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
   }
   for (int p = 0; p < 3; ++p)
     for (int q = 0; q < 3; ++q)
-      for (int s2 = q; s2 < 3; ++s2) H16[hp16(3 * p + q, 3 * p + s2)] += T(2) * ASA[q][s2];
-  // F-eta block: -2 (F N_p)_rQ with N_p = ASA U_p A + A U_p ASA
-  {
-    T FASA[3][3];
-    mm3(F, ASA, FASA);
-    for (int p = 0; p < NPH; ++p) {
-      T Up[3][3], t1[3][3], t2[3][3], t3[3][3];
-      load_U(P, p, Up);
-      mm3(FASA, Up, t1);
-      mm3(t1, A, t2);  // F ASA U_p A
-      mm3(M, Up, t1);
-      mm3(t1, ASA, t3);  // F A U_p ASA
-      for (int k = 0; k < 9; ++k) H16[hp16(k, 9 + p)] += T(-2) * (t2[k / 3][k % 3] + t3[k / 3][k % 3]);
-    }
+      for (int s2 = q; s2 < 3; ++s2) Hp[hidx(3 * p + q, 3 * p + s2)] += T(2) * ASA[q][s2];
+  // per direction: Y_k = A dU_k A, S Y_k, C Y_k, S E dU_k
+  T C[3][3], SE[3][3];
+  mtm3(F, F, C);
+  mm3(S, E, SE);
+  T Yk[6][3][3], SY[6][3][3], CY[6][3][3], SEU[6][3][3];
+  for (int k = 0; k < 6; ++k) {
+    mm3(AdU[k], A, Yk[k]);
+    mm3(S, Yk[k], SY[k]);
+    mm3(C, Yk[k], CY[k]);
+    mm3(SE, dU[k], SEU[k]);
+  }
+  // F-eta block: -2 (F N_k)_rQ with N_k = ASA dU_k A + A dU_k ASA, where
+  // F ASA dU_k A = M (S Y_k) and F A dU_k ASA = (M dU_k) ASA
+  for (int k = 0; k < 6; ++k) {
+    T MdU[3][3], t1[3][3], t2[3][3];
+    mm3(M, SY[k], t1);
+    mm3(M, dU[k], MdU);
+    mm3(MdU, ASA, t2);
+    for (int r = 0; r < 9; ++r) Hp[hidx(r, 9 + k)] += T(-2) * (t1[r / 3][r % 3] + t2[r / 3][r % 3]);
   }
   // eta-eta block: S:d2E + explicit eta derivatives of g + local terms
-  {
-    T C[3][3], SE[3][3];
-    mtm3(F, F, C);
-    mm3(S, E, SE);
-    T Y[NPH][3][3], SEU[NPH][3][3], SY[NPH][3][3], CY[NPH][3][3];
-    for (int p = 0; p < NPH; ++p) {
-      T Up[3][3];
-      load_U(P, p, Up);
-      mm3(AU[p], A, Y[p]);  // Y_p = A U_p A
-      mm3(SE, Up, SEU[p]);  // S E U_p
-      mm3(S, Y[p], SY[p]);
-      mm3(C, Y[p], CY[p]);
+  // (obstacle, dissipation, penalty), the last written in eta_hat:
+  // c_kl - c_k0 - c_0l + c_00 + d_0 + delta_kl d_k, d_i = 1/(m_i tau) + eps [eta_i < 0]
+  const T d0 = T(P.inv_mtau[0]) + (eta[0] < T(0) ? T(P.eps_eta) : T(0));
+  for (int p = 0; p < 6; ++p) {
+    const T hLp = hLh[p + 1] - hLh[0];
+    for (int q = p; q < 6; ++q) {
+      const T hLq = hLh[q + 1] - hLh[0];
+      T sd2E = T(2) * (tr_ab(SEU[p], Yk[q]) + tr_ab(SEU[q], Yk[p]) + tr_ab(SY[p], CY[q]));
+      T Jpq = Jt * (trAdU[p] * trAdU[q] - tr_ab(AdU[p], AdU[q]));
+      T gee = T(0.5) * Jpq * hT + T(0.5) * Jt * trAdU[p] * hLq + T(0.5) * Jt * trAdU[q] * hLp;
+      T loc = T(P.cobst[p + 1][q + 1]) - T(P.cobst[p + 1][0]) - T(P.cobst[0][q + 1]) + T(P.cobst[0][0]) + d0;
+      if (p == q) loc += T(P.inv_mtau[p + 1]) + (eta[p + 1] < T(0) ? T(P.eps_eta) : T(0));
+      Hp[hidx(9 + p, 9 + q)] += sd2E + gee + loc;
     }
-    for (int p = 0; p < NPH; ++p)
-      for (int q = p; q < NPH; ++q) {
-        T sd2E = T(2) * (tr_ab(SEU[p], Y[q]) + tr_ab(SEU[q], Y[p]) + tr_ab(SY[p], CY[q]));
-        T Jpq = Jt * (trAU[p] * trAU[q] - tr_ab(AU[p], AU[q]));
-        T gee = T(0.5) * Jpq * hT + T(0.5) * Jt * trAU[p] * hLh[q] + T(0.5) * Jt * trAU[q] * hLh[p];
-        T loc = T(P.cobst[p][q]);
-        if (p == q) loc += T(P.inv_mtau[p]) + (eta[p] < T(0) ? T(P.eps_eta) : T(0));
-        H16[hp16(9 + p, 9 + q)] += sd2E + gee + loc;
-      }
   }
-  // condense eta_0 (Sec. 3.1): z = (F, eta_hat), eta = e_0 + T eta_hat
-  for (int r = 0; r < NZ; ++r)
-    for (int c = r; c < NZ; ++c) {
-      T v;
-      if (c < 9) {
-        v = H16[hp16(r, c)];
-      } else if (r < 9) {
-        v = H16[hp16(r, c + 1)] - H16[hp16(r, 9)];
-      } else {
-        v = H16[hp16(r + 1, c + 1)] - H16[hp16(9, r + 1)] - H16[hp16(9, c + 1)] + H16[hp16(9, 9)];
-      }
-      Hp[hidx(r, c)] = v;
-    }
 }
 
 }  // namespace pfm

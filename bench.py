@@ -13,7 +13,9 @@ Headline value: Jacobian-apply throughput in GDOF/s, i.e. DOFs of the finest
 level per FP32 tangent application, divided by the mean device time of those
 applications inside the timed Newton steps (CUDA events recorded by the
 library on its stream). Also reported: seconds per Newton step for the mixed
-FP32-MG and the all-FP64 solve, the roofline of the tangent application,
+FP32-MG and the all-FP64 solve, the same mixed step with the preconditioner
+reading binary16 copies of its Hessians (FP32 arithmetic, half the bytes),
+the roofline of the tangent application,
 an end-to-end figure through the host-buffer entry point, and the CPU oracle
 timed on a bounded sample.
 
@@ -55,6 +57,8 @@ def parse_args():
     p.add_argument("--batch-count", type=int, default=64)
     p.add_argument("--no-diff", action="store_true", help="skip the 32^3 differentiation measurement")
     p.add_argument("--no-hencky", action="store_true", help="skip the Hencky-mode cost comparison")
+    p.add_argument("--no-f16-store", action="store_true",
+                   help="skip the Newton step with the binary16 preconditioner store")
     p.add_argument("--mode", default="newton", choices=["newton", "japply"],
                    help="japply: only K FP32 tangent applications (for profiler captures)")
     return p.parse_args()
@@ -552,6 +556,29 @@ def gpu_arm(args, rank, world, dist):
         res64, its64 = solve_check(abi.PFM_F64)
         fp64 = {"s": e0.elapsed_time(e1) / 1e3, "fgmres_its": r64.lin_its_last, "true_rel_residual": res64}
 
+    # ---- the same mixed step with the binary16 preconditioner store --------
+    f16 = None
+    if not args.no_f16_store:
+        P.set_preconditioner_store(True)
+        step(opts)  # builds the binary16 copies and tunes their launch shape
+        torch.cuda.synchronize()
+        P.profile_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r16 = step(opts)
+        e1.record()
+        torch.cuda.synchronize()
+        n16, ms16 = P.profile_get(abi.PROF_JAPPLY_F16)
+        P.profile_enable(False)
+        res16, _ = solve_check(abi.PFM_F32)
+        P.set_preconditioner_store(False)
+        a16 = ms16 / max(n16, 1)
+        alg16 = h_bytes // 2 + 2 * vec_bytes + 2 * P.n_nodes
+        f16 = {"s": e0.elapsed_time(e1) / 1e3, "fgmres_its": r16.lin_its_last, "true_rel_residual": res16,
+               "japply_ms": a16, "japply_gdofs": ndofs / (a16 * 1e-3) / 1e9,
+               "japply_gbs": alg16 / (a16 * 1e-3) / 1e9, "japply_hbm_frac": alg16 / (a16 * 1e-3) / 1e9 / peak,
+               "bytes_per_launch": alg16}
+
     hencky = None
     aniso = None
     if not args.no_hencky and rank == 0:
@@ -603,9 +630,13 @@ def gpu_arm(args, rank, world, dist):
                             f"{nlev}-level geometric MG, load step 1/10, FGMRES(30) rtol 1e-8",
                 "problems": world, "l2": "inputs larger than L2 (8 GB Hessian store per application)",
             },
-            "newton_step_s": {"fp32_mg": ms_step / 1e3, "fp64": fp64["s"] if fp64 else None},
-            "fgmres_its": {"fp32_mg": rep.lin_its_last, "fp64": fp64["fgmres_its"] if fp64 else None},
-            "true_rel_residual": {"fp32_mg": res32, "fp64": fp64["true_rel_residual"] if fp64 else None},
+            "newton_step_s": {"fp32_mg": ms_step / 1e3, "fp64": fp64["s"] if fp64 else None,
+                              "fp32_mg_f16_store": f16["s"] if f16 else None},
+            "fgmres_its": {"fp32_mg": rep.lin_its_last, "fp64": fp64["fgmres_its"] if fp64 else None,
+                           "fp32_mg_f16_store": f16["fgmres_its"] if f16 else None},
+            "true_rel_residual": {"fp32_mg": res32, "fp64": fp64["true_rel_residual"] if fp64 else None,
+                                  "fp32_mg_f16_store": f16["true_rel_residual"] if f16 else None},
+            "f16_store": f16,
             "phase_ms_per_step": {
                 "japply_f32": ms32 / args.steps, "japply_f64": ms64 / args.steps,
                 "linearize_fine": mslin / args.steps, "residual": msres / args.steps,

@@ -176,6 +176,18 @@ pfm_status pfm_get_state(pfm_handle* h, double* U_dev);
  * way. Errors: PFM_ERR_INVALID_ARG (other values). */
 pfm_status pfm_set_linearize_arithmetic(pfm_handle* h, int double_float);
 
+/* Storage of the Gauss-point Hessians that the FP32 preconditioner's tangent
+ * applications read (smoothing, residuals and eigenvalue estimates of every
+ * level but the coarsest; Sec. 3.4): 0 = FP32 (default), 1 = binary16 copies
+ * of the FP32 store scaled per level by a power of two s (largest |entry| of
+ * s H in [2^14, 2^15)), read into FP32 arithmetic: half the bytes of the
+ * HBM-bound application, with entries rounded to 11 significant bits. The
+ * FGMRES outer operator, the block-diagonal smoother blocks and the coarse
+ * solve keep their precision, so a converged solve meets the same residual
+ * tolerance. Takes effect at the next linearisation (invalidates the tangent).
+ * Errors: PFM_ERR_INVALID_ARG (other values). */
+pfm_status pfm_set_preconditioner_store(pfm_handle* h, int half);
+
 /* Frictionless penalty contact with a rigid sphere (Sec. 2.5, Eq. Ngap, the
  * contact term of Eq. PenPot) on the top face z = Lz: a point X of that face
  * at x = X + u has the normal gap g = |x - c| - R to the sphere of centre
@@ -230,7 +242,9 @@ pfm_status pfm_linearize(pfm_handle* h, pfm_precision precond);
 /* y = J v with J = dR/dU at the last linearisation (Eq. linAlgEq), matrix
  * free from the stored Gauss-point Hessians; v_dev, y_dev are device arrays
  * [9][n_nodes] of float (PFM_F32) or double (PFM_F64). FP32 needs an FP32
- * tangent (pfm_linearize with PFM_F32). v and y must not alias. */
+ * tangent (pfm_linearize with PFM_F32) and applies the preconditioner's
+ * finest-level operator: from the FP32 store, or from its binary16 copy
+ * after pfm_set_preconditioner_store(h, 1). v and y must not alias. */
 pfm_status pfm_jacobian_apply(pfm_handle* h, const void* v_dev, void* y_dev, pfm_precision prec);
 
 /* y = J^T v (adjoint product), same layout and rules as pfm_jacobian_apply. */
@@ -312,14 +326,16 @@ pfm_status pfm_get_hessians(pfm_handle* h, int64_t e0, int64_t count, double* he
  * Timed phases: PFM_PROF_JAPPLY_F32 / _F64 = one tangent application on the
  * finest level (the initialisation and element kernels), PFM_PROF_LINEARIZE
  * = pfm_linearize's finest-level Hessian kernel, PFM_PROF_RESIDUAL = the
- * residual kernel, PFM_PROF_VCYCLE = one whole V-cycle. */
+ * residual kernel, PFM_PROF_VCYCLE = one whole V-cycle, PFM_PROF_JAPPLY_F16
+ * = one finest-level application from the binary16 store. */
 typedef enum {
   PFM_PROF_JAPPLY_F32 = 0,
   PFM_PROF_JAPPLY_F64 = 1,
   PFM_PROF_LINEARIZE = 2,
   PFM_PROF_RESIDUAL = 3,
   PFM_PROF_VCYCLE = 4,
-  PFM_PROF_COUNT = 5
+  PFM_PROF_JAPPLY_F16 = 5,
+  PFM_PROF_COUNT = 6
 } pfm_prof_id;
 
 pfm_status pfm_profile_enable(pfm_handle* h, int enable);

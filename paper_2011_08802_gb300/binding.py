@@ -131,6 +131,12 @@ class Problem:
         point physics in the FP64-class linearisation."""
         self._check(self._lib.pfm_set_linearize_arithmetic(self.h, int(bool(double_float))))
 
+    def set_preconditioner_store(self, half: bool):
+        """``pfm_set_preconditioner_store``: the FP32 preconditioner reads its
+        Gauss-point Hessians from the FP32 store (False) or from per-level
+        binary16 copies scaled by a power of two (True)."""
+        self._check(self._lib.pfm_set_preconditioner_store(self.h, int(bool(half))))
+
     def set_contact(self, center, radius: float, eps_N: float):
         """``pfm_set_contact``: rigid sphere (centre, radius) pressed on the top
         face with penalty eps_N; radius <= 0 switches contact off."""

@@ -59,12 +59,23 @@ void prof_collect(pfm_handle* h) {
   }
 }
 
-// Tangent application on level l (timed when l == 0).
+// Tangent application inside the preconditioner on level l: from the level's
+// store, or from its binary16 copy when that is enabled and current (FP32);
+// timed on the finest level unless `timed` is false.
 template <typename T>
-void japply_level(pfm_handle* h, size_t l, const T* H, const T* x, T* y) {
+void precond_apply(pfm_handle* h, size_t l, const T* x, T* y, bool timed = true) {
   Level& lv = h->L[l];
-  ProfScope ps(h, sizeof(T) == 4 ? PFM_PROF_JAPPLY_F32 : PFM_PROF_JAPPLY_F64, l == 0);
-  launch_japply<T>(lv.g, h->dp, H, lv.mask, x, y, h->stream);
+  const bool on = timed && l == 0;
+  if constexpr (sizeof(T) == 4) {
+    if (lv.H16 && lv.h16_scale > 0.f) {
+      ProfScope ps(h, PFM_PROF_JAPPLY_F16, on);
+      launch_japply_h16(lv.g, h->dp, lv.H16, 1.f / lv.h16_scale, lv.mask, x, y, h->stream);
+      if (h->contact_on) launch_contact_apply<T, T, T>(lv.g, LvVec<T>::Kc(lv), lv.mask, x, y, h->stream);
+      return;
+    }
+  }
+  ProfScope ps(h, sizeof(T) == 4 ? PFM_PROF_JAPPLY_F32 : PFM_PROF_JAPPLY_F64, on);
+  launch_japply<T>(lv.g, h->dp, LvVec<T>::H(lv), lv.mask, x, y, h->stream);
   if (h->contact_on) launch_contact_apply<T, T, T>(lv.g, LvVec<T>::Kc(lv), lv.mask, x, y, h->stream);
 }
 
@@ -107,7 +118,6 @@ pfm_status smooth(pfm_handle* h, size_t l, bool zero_x, int nu, bool want_res, c
   T* y = LvVec<T>::y(lv);
   T* r = LvVec<T>::r(lv);
   T* d = LvVec<T>::d(lv);
-  const T* H = LvVec<T>::H(lv);
   const T* D = LvVec<T>::D(lv);
   const int64_t n = ndof(lv);
   if (c.type == 1) {
@@ -115,15 +125,15 @@ pfm_status smooth(pfm_handle* h, size_t l, bool zero_x, int nu, bool want_res, c
       CK(cudaMemsetAsync(x, 0, sizeof(T) * n, s));
       launch_smooth<T>(lv.nn, D, b, nullptr, T(c.omega), x, s);
     } else {
-      japply_level<T>(h, l, H, x, y);
+      precond_apply<T>(h, l, x, y);
       launch_smooth<T>(lv.nn, D, b, y, T(c.omega), x, s);
     }
     for (int k = 1; k < nu; ++k) {
-      japply_level<T>(h, l, H, x, y);
+      precond_apply<T>(h, l, x, y);
       launch_smooth<T>(lv.nn, D, b, y, T(c.omega), x, s);
     }
     if (want_res) {
-      japply_level<T>(h, l, H, x, y);
+      precond_apply<T>(h, l, x, y);
       launch_sub<T>(n, b, y, r, s);
     }
     CKL();
@@ -135,18 +145,18 @@ pfm_status smooth(pfm_handle* h, size_t l, bool zero_x, int nu, bool want_res, c
   if (zero_x) {
     launch_cheb_first<T>(lv.nn, D, b, T(1.0 / theta), true, true, r, d, x, s);
   } else {
-    japply_level<T>(h, l, H, x, y);
+    precond_apply<T>(h, l, x, y);
     launch_sub<T>(n, b, y, r, s);
     launch_cheb_first<T>(lv.nn, D, r, T(1.0 / theta), false, false, r, d, x, s);
   }
   for (int k = 1; k < nu; ++k) {
-    japply_level<T>(h, l, H, d, y);
+    precond_apply<T>(h, l, d, y);
     const double rho_n = 1.0 / (2.0 * sigma - rho);
     launch_cheb_step<T>(lv.nn, D, y, T(rho_n * rho), T(2.0 * rho_n / delta), r, d, x, s);
     rho = rho_n;
   }
   if (want_res) {
-    japply_level<T>(h, l, H, d, y);
+    precond_apply<T>(h, l, d, y);
     launch_sub<T>(n, r, y, r, s);
   }
   CKL();
@@ -175,7 +185,7 @@ pfm_status vcycle_level(pfm_handle* h, size_t l, const SmoothCfg& c) {
   for (int g = 0; g < c.gamma; ++g) {
     // coarse correction of the current residual r (recomputed after the first one)
     if (g > 0) {
-      japply_level<T>(h, l, LvVec<T>::H(lv), x, LvVec<T>::y(lv));
+      precond_apply<T>(h, l, x, LvVec<T>::y(lv));
       launch_sub<T>(ndof(lv), b, LvVec<T>::y(lv), LvVec<T>::r(lv), s);
     }
     launch_restrict<T>(lv.g, cv.g, LvVec<T>::r(lv), cv.mask, LvVec<T>::b(cv), s);
@@ -210,14 +220,12 @@ pfm_status estimate_lambda(pfm_handle* h, size_t l) {
   T* x = LvVec<T>::x(lv);
   T* y = LvVec<T>::y(lv);
   T* z = LvVec<T>::r(lv);
-  const T* H = LvVec<T>::H(lv);
   const T* D = LvVec<T>::D(lv);
   launch_power_init<T>(lv.nn, lv.mask, x, s);
   launch_dot<T>(n, x, x, h->partial, h->hdev, s);
   launch_scale_inv_sqrt<T>(n, x, h->hdev, x, s);
   for (int it = 0; it < h->power_its; ++it) {
-    launch_japply<T>(lv.g, h->dp, H, lv.mask, x, y, s);
-    if (h->contact_on) launch_contact_apply<T, T, T>(lv.g, LvVec<T>::Kc(lv), lv.mask, x, y, s);
+    precond_apply<T>(h, l, x, y, false);
     CK(cudaMemsetAsync(z, 0, sizeof(T) * n, s));
     launch_smooth<T>(lv.nn, D, y, nullptr, T(1), z, s);
     launch_dot<T>(n, z, z, h->partial, h->hdev, s);
@@ -327,6 +335,13 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
       launch_linearize(lv.g, h->dp, lv.U, lv.Un, need64 ? lv.H64 : nullptr, need32 ? lv.H32 : nullptr,
                        needlo ? lv.H32lo : nullptr, arith, s);
     }
+    lv.h16_scale = 0.f;
+    if (need32 && h->pre_h16) {
+      TRY(dalloc(h, &lv.H16, hsz));
+      if (!h->amax_dev) TRY(dalloc(h, &h->amax_dev, 1));
+      lv.h16_scale = launch_store_to_half(lv.g, lv.H32, lv.H16, h->amax_dev, s);
+      if (!(lv.h16_scale > 0.f)) return h->fail(PFM_ERR_NONFINITE, "binary16 store: non-finite Hessian entries");
+    }
     if (h->contact_on) {
       TRY(dalloc(h, &lv.Kc64, size_t(6) * contact_points(lv.g)));
       TRY(dalloc(h, &lv.Kc32, size_t(6) * contact_points(lv.g)));
@@ -374,7 +389,7 @@ pfm_status japply_impl(pfm_handle* h, const T* v, T* y) {
   const T* H = LvVec<T>::H(f);
   if (!H || (sizeof(T) == 4 && h->lin_prec != PFM_F32))
     return h->fail(PFM_ERR_STATE, "no tangent in the requested precision (linearize with PFM_F32 for FP32)");
-  japply_level<T>(h, 0, H, v, y);
+  precond_apply<T>(h, 0, v, y);
   CKL();
   return PFM_OK;
 }
@@ -864,14 +879,14 @@ void pfm_destroy(pfm_handle* h) {
   for (int id = 0; id < PFM_PROF_COUNT; ++id)
     for (auto& e : h->prof_ev[id]) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
   for (auto& lv : h->L) {
-    dfree(lv.U); dfree(lv.Un); dfree(lv.mask); dfree(lv.H64); dfree(lv.H32); dfree(lv.H32lo); dfree(lv.D64);
+    dfree(lv.U); dfree(lv.Un); dfree(lv.mask); dfree(lv.H64); dfree(lv.H32); dfree(lv.H32lo); dfree(lv.H16); dfree(lv.D64);
     dfree(lv.D32);
     dfree(lv.x32); dfree(lv.b32); dfree(lv.y32); dfree(lv.x64); dfree(lv.b64); dfree(lv.y64);
     dfree(lv.r32); dfree(lv.d32); dfree(lv.r64); dfree(lv.d64); dfree(lv.Kc64); dfree(lv.Kc32);
   }
   dfree(h->dirval); dfree(h->energy_dev); dfree(h->flag_dev); dfree(h->diag_part); dfree(h->load_dev); dfree(h->R); dfree(h->dU); dfree(h->wv);
   dfree(h->rv); dfree(h->zd); dfree(h->partial); dfree(h->hdev); dfree(h->V); dfree(h->Kaug); dfree(h->Kinv);
-  dfree(h->gj_keys); dfree(h->gj_used); dfree(h->gj_piv);
+  dfree(h->gj_keys); dfree(h->gj_used); dfree(h->gj_piv); dfree(h->amax_dev);
   if (h->Z) cudaFree(h->Z);
   if (h->vgraph) cudaGraphExecDestroy(h->vgraph);
   if (h->hpin) cudaFreeHost(h->hpin);
@@ -1002,6 +1017,19 @@ pfm_status pfm_set_linearize_arithmetic(pfm_handle* h, int double_float) {
   if (double_float != 0 && double_float != 1) return h->fail(PFM_ERR_INVALID_ARG, "expected 0 or 1");
   h->lin_df = double_float != 0;
   h->linearized = false;
+  return PFM_OK;
+}
+
+pfm_status pfm_set_preconditioner_store(pfm_handle* h, int half) {
+  if (!h) return PFM_ERR_INVALID_ARG;
+  if (half != 0 && half != 1) return h->fail(PFM_ERR_INVALID_ARG, "expected 0 or 1");
+  h->pre_h16 = half != 0;
+  h->linearized = false;
+  for (auto& lv : h->L) lv.h16_scale = 0.f;
+  if (h->vgraph) {
+    cudaGraphExecDestroy(h->vgraph);
+    h->vgraph = nullptr;
+  }
   return PFM_OK;
 }
 

@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libpfm.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -60,6 +61,13 @@ void launch_japply_df(const Grid& g, const DevParams& P, const float* Hhi, const
 template <typename T>
 void launch_japply(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, const T* v,
                    T* y, cudaStream_t s);
+// y = J v from a binary16 copy of the FP32 store holding s H (FP32 arithmetic;
+// inv_scale = 1/s), and the conversion that makes that copy: returns s, a
+// power of two putting max |H| in [2^14, 2^15), or 0 on failure (scratch: one
+// device word).
+void launch_japply_h16(const Grid& g, const DevParams& P, const __half* H, float inv_scale, const dmask_t* mask,
+                       const float* v, float* y, cudaStream_t s);
+float launch_store_to_half(const Grid& g, const float* H32, __half* H16, unsigned* scratch, cudaStream_t s);
 // element blocks [b0, b1) only, on at most `blocks` CTAs (slab pipeline)
 template <typename T>
 void launch_japply_range(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, const T* v, T* y,

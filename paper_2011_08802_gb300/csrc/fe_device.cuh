@@ -13,6 +13,8 @@
 // transform. A warp holds 4 elements.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include <cstdint>
 
 #include "common.cuh"
@@ -141,6 +143,19 @@ template <> struct Vec16<float> {
 template <> struct Vec16<double> {
   using type = double2;
   static __device__ __forceinline__ void unpack(const double2& x, double* o) { o[0] = x.x; o[1] = x.y; }
+};
+// binary16 store (FP32 arithmetic): 8 entries per vector
+template <> struct Vec16<__half> {
+  using type = uint4;
+  static __device__ __forceinline__ void unpack(const uint4& x, float* o) {
+    const __half2* h = reinterpret_cast<const __half2*>(&x);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const float2 f = __half22float2(h[t]);
+      o[2 * t] = f.x;
+      o[2 * t + 1] = f.y;
+    }
+  }
 };
 
 template <typename T>
@@ -377,6 +392,71 @@ __device__ __forceinline__ void japply_block(const Grid& g, const JParams<T>& jp
   }
 }
 // ---- END tangent application kernel
+
+// y += J v on element block blk from a binary16 copy of the store holding
+// s H (FP32 arithmetic): the same gather, contraction and scatter as
+// japply_block, with the Hessian part weighted by wh = w / s. The FP32 and
+// FP64 applications keep their own body above.
+__device__ __forceinline__ void japply_block_h16(const Grid& g, const JParams<float>& jp, float wh,
+                                                 const __half* __restrict__ H, const dmask_t* __restrict__ mask,
+                                                 const float* __restrict__ v, float* __restrict__ y, int64_t blk,
+                                                 int lane) {
+  constexpr int V = 8;
+  const int l8 = lane & 7;
+  const int64_t nn = g.nn();
+  const int64_t e = blk * 4 + (lane >> 3);
+  const bool valid = e < g.ne();
+  const int64_t node = valid ? elem_node(g, e, l8) : 0;
+  const dmask_t dm = valid ? mask[node] : dmask_t(0x1ff);
+  float dz[NZ], ge[18];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float x = ((dm >> i) & 1) ? 0.f : v[i * nn + node];
+    float val;
+    q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, val, dz[3 * i], dz[3 * i + 1], dz[3 * i + 2]);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    float x = ((dm >> (3 + k)) & 1) ? 0.f : v[(3 + k) * nn + node];
+    q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, dz[9 + k], ge[3 * k], ge[3 * k + 1], ge[3 * k + 2]);
+  }
+  float sg[NZ];
+#pragma unroll
+  for (int r = 0; r < NZ; ++r) sg[r] = 0.f;
+  const uint4* Hv = reinterpret_cast<const uint4*>(H) + blk * (NH / V) * 32 + lane;
+#pragma unroll
+  for (int j = 0; j < NH / V; ++j) {
+    float hv[V];
+    Vec16<__half>::unpack(__ldcs(Hv + j * 32), hv);
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      const int idx = j * V + t;
+      const int r = packed_row(idx);
+      const int c = r + (idx - packed_row_start(r));
+      sg[r] += hv[t] * dz[c];
+      if (c != r) sg[c] += hv[t] * dz[r];
+    }
+  }
+  const float w = jp.w;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float r = q1_scatter_grad(wh * sg[3 * i], wh * sg[3 * i + 1], wh * sg[3 * i + 2], l8, jp.ihx, jp.ihy, jp.ihz);
+    if (valid && !((dm >> i) & 1)) atomicAdd(&y[i * nn + node], r);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    float gf[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float s = 0.f;
+#pragma unroll
+      for (int l = 0; l < 6; ++l) s += jp.G[k][l] * ge[3 * l + d];
+      gf[d] = w * s;
+    }
+    float r = q1_scatter(wh * sg[9 + k], gf[0], gf[1], gf[2], l8, jp.ihx, jp.ihy, jp.ihz);
+    if (valid && !((dm >> (3 + k)) & 1)) atomicAdd(&y[(3 + k) * nn + node], r);
+  }
+}
 
 
 // ---------------------------------------------------------------------------

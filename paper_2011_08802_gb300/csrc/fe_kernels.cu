@@ -10,6 +10,7 @@
 // at the 8 points are a tensor product of 1-D 2x2 transforms, applied with
 // three xor-shuffles (1, 2, 4) per axis; the scatter is the transposed
 // transform. A warp holds 4 elements.
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -118,6 +119,26 @@ __global__ void __launch_bounds__(256, PFM_JAPPLY_MINB) k_japply(Grid g, JParams
 }
 
 // ---- END tangent application kernel
+
+// Same persistent mapping over a binary16 copy of the store (s H, wh = w / s).
+template <int PF>
+__global__ void __launch_bounds__(256, PFM_JAPPLY_MINB) k_japply_h16(Grid g, JParams<float> jp, float wh,
+                                                    const __half* __restrict__ H,
+                                                    const dmask_t* __restrict__ mask,
+                                                    const float* __restrict__ v, float* __restrict__ y) {
+  const int64_t nblk = g.nblk();
+  const int64_t wg = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int lane = int(threadIdx.x & 31);
+  constexpr unsigned BLK_BYTES = unsigned(HBLK * sizeof(__half));
+  if (lane == 0)
+    for (int d = 0; d < PF; ++d)
+      if (wg + d * nw < nblk) prefetch_l2(H + (wg + d * nw) * HBLK, BLK_BYTES);
+  for (int64_t blk = wg; blk < nblk; blk += nw) {
+    if (lane == 0 && blk + PF * nw < nblk) prefetch_l2(H + (blk + PF * nw) * HBLK, BLK_BYTES);
+    japply_block_h16(g, jp, wh, H, mask, v, y, blk, lane);
+  }
+}
 
 // y += J v with v in FP32 (exact input), the tangent as Hhi + Hlo (two FP32
 // stores of the FP64 Hessians) and double-float arithmetic throughout; the
@@ -254,6 +275,38 @@ __global__ void k_qp_eval(DevParams P, int64_t n, const double* __restrict__ F,
     for (int k = 0; k < NH; ++k) hess[i * NH + k] = h[k];
 }
 
+// max |H| over an FP32 store (non-negative floats order as their bit
+// patterns, so an integer atomicMax on the bits is a float max).
+__global__ void k_absmax(int64_t n, const float* __restrict__ H, unsigned* __restrict__ out) {
+  float m = 0.f;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    m = fmaxf(m, fabsf(H[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// binary16 copy of an FP32 store scaled by s (a power of two): one thread
+// per 16-byte output vector (8 entries of one lane), read as two FP32 vectors
+// of the same lane.
+__global__ void k_store_to_half(int64_t nvec, const float4* __restrict__ H32, float s, uint4* __restrict__ H16) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nvec; i += int64_t(gridDim.x) * blockDim.x) {
+    // output vector i = (blk*15 + j)*32 + lane holds entries 8j..8j+7; the
+    // FP32 store has them in vectors (blk*30 + 2j)*32 + lane and (.. + 1)*32 + lane
+    const int64_t lane = i & 31, bj = i >> 5;
+    const int64_t blk = bj / (NH / 8), j = bj % (NH / 8);
+    const int64_t src = (blk * (NH / 4) + 2 * j) * 32 + lane;
+    const float4 a = H32[src], b = H32[src + 32];
+    uint4 o;
+    __half2* h = reinterpret_cast<__half2*>(&o);
+    h[0] = __floats2half2_rn(a.x * s, a.y * s);
+    h[1] = __floats2half2_rn(a.z * s, a.w * s);
+    h[2] = __floats2half2_rn(b.x * s, b.y * s);
+    h[3] = __floats2half2_rn(b.z * s, b.w * s);
+    H16[i] = o;
+  }
+}
+
 inline unsigned grid_for(int64_t threads, int block) {
   return unsigned((threads + block - 1) / block);
 }
@@ -348,7 +401,10 @@ void tune_file_read() {
                     " {\"kernel\": \"k_japply\", \"precision\": \"%3[f0-9]\", \"size_class\": %d, \"threads\": %d, "
                     "\"ctas_per_sm\": %d, \"ms_per_application\": %lf",
                     prec, &cl, &th, &ps, &ms) == 5) {
-      const int pr = std::strcmp(prec, "f32") == 0 ? 0 : (std::strcmp(prec, "f64") == 0 ? 1 : -1);
+      const int pr = std::strcmp(prec, "f32") == 0   ? 0
+                     : std::strcmp(prec, "f64") == 0 ? 1
+                     : std::strcmp(prec, "f16") == 0 ? 2
+                                                     : -1;
       if (pr >= 0 && (th == 128 || th == 256) && ps >= 1 && ps <= 16) g_tuned[{pr, cl}] = JShape{th, ps, ms};
     }
   }
@@ -367,7 +423,8 @@ void tune_file_write() {
     std::fprintf(f,
                  " {\"kernel\": \"k_japply\", \"precision\": \"%s\", \"size_class\": %d, \"threads\": %d, "
                  "\"ctas_per_sm\": %d, \"ms_per_application\": %.6f}%s\n",
-                 kv.first.first == 0 ? "f32" : "f64", kv.first.second, kv.second.threads, kv.second.per_sm,
+                 kv.first.first == 0 ? "f32" : (kv.first.first == 1 ? "f64" : "f16"), kv.first.second,
+                 kv.second.threads, kv.second.per_sm,
                  kv.second.ms, ++i < g_tuned.size() ? "," : "");
   }
   std::fprintf(f, "]\n");
@@ -384,23 +441,40 @@ int sm_count() {
   return sms;
 }
 
+// element kernel of the tangent application for a store of type S (wh: weight
+// of the Hessian part, used by the scaled binary16 store only)
 template <typename T>
-void japply_launch_shape(const Grid& g, JParams<T> jp, const T* H, const dmask_t* mask, const T* v, T* y,
-                         const JShape& js, cudaStream_t s) {
+void japply_elem(const Grid& g, const JParams<T>& jp, float, const T* H, const dmask_t* mask, const T* v, T* y,
+                 unsigned blocks, int threads, cudaStream_t s) {
+  k_japply<T, JAPPLY_PF><<<blocks, threads, 0, s>>>(g, jp, H, mask, v, y);
+}
+inline void japply_elem(const Grid& g, const JParams<float>& jp, float wh, const __half* H, const dmask_t* mask,
+                        const float* v, float* y, unsigned blocks, int threads, cudaStream_t s) {
+  k_japply_h16<JAPPLY_PF><<<blocks, threads, 0, s>>>(g, jp, wh, H, mask, v, y);
+}
+template <typename T>
+const void* japply_elem_fn(const T*) {
+  return reinterpret_cast<const void*>(k_japply<T, JAPPLY_PF>);
+}
+inline const void* japply_elem_fn(const __half*) { return reinterpret_cast<const void*>(k_japply_h16<JAPPLY_PF>); }
+
+template <typename T, typename S = T>
+void japply_launch_shape(const Grid& g, const JParams<T>& jp, float wh, const S* H, const dmask_t* mask, const T* v,
+                         T* y, const JShape& js, cudaStream_t s) {
   const int64_t nn = g.nn();
   k_japply_init<T><<<grid_for(NF * nn, 256) < 4096 ? grid_for(NF * nn, 256) : 4096, 256, 0, s>>>(nn, mask, v, y);
   count_launches(1);
   const int64_t need = (g.nblk() * 32 + js.threads - 1) / js.threads;
   const int64_t full = int64_t(sm_count()) * js.per_sm;
   const unsigned blocks = unsigned(need < full ? need : full);
-  k_japply<T, JAPPLY_PF><<<blocks, js.threads, 0, s>>>(g, jp, H, mask, v, y);
+  japply_elem(g, jp, wh, H, mask, v, y, blocks, js.threads, s);
   count_launches(1);
 }
 
-template <typename T>
-JShape japply_tune(const Grid& g, const JParams<T>& jp, const T* H, const dmask_t* mask, const T* v, T* y,
+template <typename T, typename S = T>
+JShape japply_tune(const Grid& g, const JParams<T>& jp, float wh, const S* H, const dmask_t* mask, const T* v, T* y,
                    cudaStream_t s) {
-  const int pr = sizeof(T) == 4 ? 0 : 1;
+  const int pr = sizeof(S) == 2 ? 2 : (sizeof(T) == 4 ? 0 : 1);
   int cl = 0;
   for (int64_t b = g.nblk(); b > 1; b >>= 1) ++cl;
   std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -417,12 +491,12 @@ JShape japply_tune(const Grid& g, const JParams<T>& jp, const T* H, const dmask_
   float best_ms = 1e30f;
   for (int threads : {256, 128}) {
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_japply<T, JAPPLY_PF>, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, japply_elem_fn(H), threads, 0);
     for (int ps = 1; ps <= occ; ++ps) {
       JShape js{threads, ps};
-      japply_launch_shape<T>(g, jp, H, mask, v, y, js, s);  // warm
+      japply_launch_shape<T, S>(g, jp, wh, H, mask, v, y, js, s);  // warm
       cudaEventRecord(a, s);
-      for (int r = 0; r < 3; ++r) japply_launch_shape<T>(g, jp, H, mask, v, y, js, s);
+      for (int r = 0; r < 3; ++r) japply_launch_shape<T, S>(g, jp, wh, H, mask, v, y, js, s);
       cudaEventRecord(b, s);
       cudaEventSynchronize(b);
       float ms = 0.f;
@@ -445,8 +519,38 @@ template <typename T>
 void launch_japply(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, const T* v,
                    T* y, cudaStream_t s) {
   const JParams<T> jp = make_jparams<T>(g, P);
-  const JShape js = japply_tune<T>(g, jp, H, mask, v, y, s);
-  japply_launch_shape<T>(g, jp, H, mask, v, y, js, s);
+  const JShape js = japply_tune<T>(g, jp, 0.f, H, mask, v, y, s);
+  japply_launch_shape<T>(g, jp, 0.f, H, mask, v, y, js, s);
+}
+
+void launch_japply_h16(const Grid& g, const DevParams& P, const __half* H, float inv_scale, const dmask_t* mask,
+                      const float* v, float* y, cudaStream_t s) {
+  const JParams<float> jp = make_jparams<float>(g, P);
+  const float wh = jp.w * inv_scale;
+  const JShape js = japply_tune<float, __half>(g, jp, wh, H, mask, v, y, s);
+  japply_launch_shape<float, __half>(g, jp, wh, H, mask, v, y, js, s);
+}
+
+float launch_store_to_half(const Grid& g, const float* H32, __half* H16, unsigned* scratch, cudaStream_t s) {
+  const int64_t n = g.nblk() * HBLK;
+  cudaMemsetAsync(scratch, 0, sizeof(unsigned), s);
+  k_absmax<<<unsigned(sm_count()) * 8, 256, 0, s>>>(n, H32, scratch);
+  count_launches(1);
+  unsigned bits = 0;
+  cudaMemcpyAsync(&bits, scratch, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return 0.f;
+  float amax = 0.f;
+  std::memcpy(&amax, &bits, sizeof(float));
+  if (!std::isfinite(amax)) return 0.f;
+  // the largest entry lands in [2^14, 2^15): far from the binary16 maximum
+  // (65504) and with 2^-24 / 2^15 ~ 2^-39 of the largest entry still resolved
+  int e = 0;
+  std::frexp(amax > 0.f ? amax : 1.f, &e);  // amax = m 2^e, m in [0.5, 1)
+  const float scale = std::ldexp(1.f, 15 - e);
+  k_store_to_half<<<unsigned(sm_count()) * 8, 256, 0, s>>>(n / 8, reinterpret_cast<const float4*>(H32), scale,
+                                                            reinterpret_cast<uint4*>(H16));
+  count_launches(1);
+  return scale;
 }
 
 void launch_japply_df(const Grid& g, const DevParams& P, const float* Hhi, const float* Hlo, const dmask_t* mask,

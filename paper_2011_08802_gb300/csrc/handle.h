@@ -23,6 +23,8 @@ struct Level {
   double* H64 = nullptr;
   float* H32 = nullptr;
   float* H32lo = nullptr;  // finest level, mixed mode: H64 - H32 rounded to FP32
+  __half* H16 = nullptr;   // binary16 copy of s H32 for the preconditioner (optional)
+  float h16_scale = 0.f;   // s, 0 while the copy is not current
   double* D64 = nullptr;
   float* D32 = nullptr;
   float *x32 = nullptr, *b32 = nullptr, *y32 = nullptr, *r32 = nullptr, *d32 = nullptr;
@@ -114,6 +116,8 @@ struct pfm_handle {
   int power_its = 30;
   bool outer_df = true;  // outer operator of the mixed solve in double-float arithmetic
   bool lin_df = false;   // FP64-class linearisation in double-float instead of FP64 arithmetic
+  bool pre_h16 = false;  // FP32 preconditioner reads binary16 Hessian copies
+  unsigned* amax_dev = nullptr;  // one word for the store's max |entry|
   // pinned host slots for Hessenberg columns and scalars
   double* hpin = nullptr;
   // captured V-cycle (valid until the next linearisation)

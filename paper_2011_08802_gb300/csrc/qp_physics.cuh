@@ -281,13 +281,29 @@ PFM_HD void jacobi_eig3(T a[3][3], T lam[3], T Q[3][3]) {
         a[p][q] = a[q][p] = T(0);
         continue;
       }
-      // rotation angle phi with cot(2 phi) = theta zeroes a_pq; t = tan(phi)
-      T theta = (a[q][q] - a[p][p]) / (T(2) * apq);
-      T t = T(1) / (fabs(theta) + sqrt(theta * theta + T(1)));
-      if (theta < T(0)) t = -t;
-      T c = T(1) / sqrt(t * t + T(1));
-      T s = t * c;
-      T tau = s / (T(1) + c);
+      // rotation angle phi with tan(2 phi) = 2 a_pq / (a_qq - a_pp) zeroes
+      // a_pq; t = tan(phi), c = cos(phi), s = sin(phi), tau = tan(phi / 2)
+      const T dqp = a[q][q] - a[p][p];
+      T t, c, s, tau;
+      if (fabs(apq) < T(1e-3) * fabs(dqp)) {
+        // small angle (every rotation after a lower-precision seed): with
+        // r = a_pq / (a_qq - a_pp), t = r - r^3 + 2 r^5 - ..., c = 1 - t^2/2 +
+        // 3 t^4/8 - ..., tau = t/2 - t^3/8 + t^5/16 - ...; for |r| < 1e-3 the
+        // dropped terms are below 1e-17 relative
+        const T r = apq / dqp, r2 = r * r;
+        t = r * (T(1) - r2 * (T(1) - T(2) * r2));
+        const T t2 = t * t;
+        c = T(1) - t2 * (T(0.5) - T(0.375) * t2);
+        s = t * c;
+        tau = t * (T(0.5) - t2 * (T(0.125) - T(0.0625) * t2));
+      } else {
+        const T theta = dqp / (T(2) * apq);
+        t = T(1) / (fabs(theta) + sqrt(theta * theta + T(1)));
+        if (theta < T(0)) t = -t;
+        c = T(1) / sqrt(t * t + T(1));
+        s = t * c;
+        tau = s / (T(1) + c);
+      }
       a[p][p] -= t * apq;
       a[q][q] += t * apq;
       a[p][q] = a[q][p] = T(0);
@@ -330,7 +346,8 @@ PFM_HD void eig_sym3<double>(double a[3][3], double lam[3], double Q[3][3]) {
       for (int i = 0; i < 3; ++i) Q0[i][c] -= d * Q0[i][pc];
     }
     double nrm = sqrt(Q0[0][c] * Q0[0][c] + Q0[1][c] * Q0[1][c] + Q0[2][c] * Q0[2][c]);
-    for (int i = 0; i < 3; ++i) Q0[i][c] /= nrm;
+    const double inrm = 1.0 / nrm;
+    for (int i = 0; i < 3; ++i) Q0[i][c] *= inrm;
   }
   rot_in(Q0, a, b);
   jacobi_eig3(b, lam, Q1);
@@ -584,30 +601,32 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
 
   // energy
   T Wloc = T(0.5) * Jt * hT;
-  T geta[NPH];  // dW/d eta_i, all local terms
-  T trAU[NPH];  // tr(A U_i) = (d J_t / d eta_i) / J_t
-  T AU[NPH][3][3];
+  // With eta_0 = 1 - sum eta_hat (Sec. 3.1) the elastic energy depends on
+  // eta_hat_k through U(eta) = sum eta_i U_i and L(eta) = sum eta_i L_i, i.e.
+  // along dU_k = U_k - U_0 and dL_k = L_k - L_0.
+  T dU[6][3][3], AdU[6][3][3], trAdU[6];  // tr(A dU_k) = (d J_t / d eta_hat_k) / J_t
 #pragma unroll
-  for (int p = 0; p < NPH; ++p) {
-    T Up[3][3];
+  for (int k = 0; k < 6; ++k) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) Up[i][j] = T(P.U[p][i][j]);
-    mm3(A, Up, AU[p]);
-    trAU[p] = AU[p][0][0] + AU[p][1][1] + AU[p][2][2];
+      for (int j = 0; j < 3; ++j) dU[k][i][j] = T(P.U[k + 1][i][j]) - T(P.U[0][i][j]);
+    mm3(A, dU[k], AdU[k]);
+    trAdU[k] = AdU[k][0][0] + AdU[k][1][1] + AdU[k][2][2];
   }
+  T gel[6];  // dW_el / d eta_hat_k
   {
     T ES[3][3];  // E S
     mm3(E, S, ES);
 #pragma unroll
-    for (int p = 0; p < NPH; ++p) {
-      // S : dE/d eta_p = -2 tr(S A U_p E) = -2 tr(E S A U_p)
-      T via_E = T(-2) * tr_ab(ES, AU[p]);
-      geta[p] = T(0.5) * Jt * trAU[p] * hT + T(0.5) * Jt * hLh[p] + via_E;
+    for (int k = 0; k < 6; ++k) {
+      // S : dE/d eta_hat_k = -2 tr(S A dU_k E) = -2 tr(E S A dU_k)
+      T via_E = T(-2) * tr_ab(ES, AdU[k]);
+      gel[k] = T(0.5) * Jt * trAdU[k] * hT + T(0.5) * Jt * (hLh[k + 1] - hLh[0]) + via_E;
     }
   }
-  // chemical, obstacle, dissipation, penalty
+  // chemical, obstacle, dissipation, penalty: dW/d eta_i per phase
+  T geta[NPH];
 #pragma unroll
   for (int i = 0; i < NPH; ++i) {
     T d = eta[i] - etan[i];
@@ -619,7 +638,7 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
       if (j > i) Wloc += T(P.cobst[i][j]) * eta[i] * eta[j];
       go += T(P.cobst[i][j]) * eta[j];
     }
-    geta[i] += T(P.F0[i]) + go + T(P.inv_mtau[i]) * d + T(P.eps_eta) * neg;
+    geta[i] = T(P.F0[i]) + go + T(P.inv_mtau[i]) * d + T(P.eps_eta) * neg;
   }
   *W = Wloc;
 
@@ -633,7 +652,7 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
 #pragma unroll
       for (int j = 0; j < 3; ++j) g[3 * i + j] = T(2) * Pm[i][j];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) g[9 + k] = geta[k + 1] - geta[0];
+    for (int k = 0; k < 6; ++k) g[9 + k] = gel[k] + (geta[k + 1] - geta[0]);
   }
   if (!WANT_HESS) return;
 
@@ -642,17 +661,9 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
   // into Hp[hidx(r, c)], r <= c. With eta_0 = 1 - sum eta_hat (Sec. 3.1) every
   // eta-dependence enters through U(eta) = sum eta_i U_i and L(eta) =
   // sum eta_i L_i, so the direction eta_hat_k carries dU_k = U_k - U_0 and
-  // dL_k = L_k - L_0 and the elimination of eta_0 holds term by term.
+  // dL_k = L_k - L_0 (dU_k, A dU_k and tr(A dU_k) from above) and the
+  // elimination of eta_0 holds term by term.
   constexpr int ND = NZ;
-  T dU[6][3][3], AdU[6][3][3], trAdU[6];  // A dU_k = A U_k - A U_0
-  for (int k = 0; k < 6; ++k) {
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) {
-        dU[k][i][j] = T(P.U[k + 1][i][j]) - T(P.U[0][i][j]);
-        AdU[k][i][j] = AU[k + 1][i][j] - AU[0][i][j];
-      }
-    trAdU[k] = trAU[k + 1] - trAU[0];
-  }
   // Rotated directions X~_k = Q^T dE_k Q, symmetric, stored as 6 values
   // (00, 11, 22, 12, 02, 01).
   T Xs[ND][6];

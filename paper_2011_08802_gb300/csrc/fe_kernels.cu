@@ -121,8 +121,13 @@ __global__ void __launch_bounds__(256, PFM_JAPPLY_MINB) k_japply(Grid g, JParams
 // ---- END tangent application kernel
 
 // Same persistent mapping over a binary16 copy of the store (s H, wh = w / s).
+// Its resident-CTA bound is set apart from the FP32/FP64 kernel's: with half
+// the bytes per element it is limited by per-element work, not by the store.
+#ifndef PFM_JAPPLY_H16_MINB
+#define PFM_JAPPLY_H16_MINB PFM_JAPPLY_MINB
+#endif
 template <int PF>
-__global__ void __launch_bounds__(256, PFM_JAPPLY_MINB) k_japply_h16(Grid g, JParams<float> jp, float wh,
+__global__ void __launch_bounds__(256, PFM_JAPPLY_H16_MINB) k_japply_h16(Grid g, JParams<float> jp, float wh,
                                                     const __half* __restrict__ H,
                                                     const dmask_t* __restrict__ mask,
                                                     const float* __restrict__ v, float* __restrict__ y) {

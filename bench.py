@@ -42,6 +42,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Jacobian-apply GDOF/s & Newton-step solve s, FP32-MG vs FP64 at 1e-8 resid"
 UNIT = "GDOF/s"
 FALLBACK_HBM_GBS = 6800.0
+REF_APPS_PER_STEP = 200  # oracle applications per core in one step of the reference arm
 
 
 def parse_args():
@@ -226,12 +227,15 @@ def oracle_jvp_sample(n_full: int, edge: int, seconds: float, steps: int | None 
     return sample_dofs / per / 1e9, desc, per
 
 
-def _oracle_worker(st, seconds, barrier, results):
-    """One process of the all-core oracle timing: set up, meet the others at
-    the barrier, apply for `seconds`, report (applications, start, end) on the
-    shared monotonic clock."""
+def _oracle_worker(st, seconds, steps, warmup, barrier, results):
+    """One process of the all-core oracle timing: set up and warm up, meet
+    the others at the barrier, then apply `steps` times (or for `seconds` when
+    steps is None), report (applications, start, end) on the shared monotonic
+    clock."""
     try:
         op = OracleJvp(st)
+        for _ in range(warmup):
+            op.apply()
         barrier.wait(timeout=120)
         t0 = time.monotonic()
         n = 0
@@ -239,7 +243,7 @@ def _oracle_worker(st, seconds, barrier, results):
             op.apply()
             n += 1
             t1 = time.monotonic()
-            if t1 - t0 >= seconds:
+            if (n >= steps) if steps is not None else (t1 - t0 >= seconds):
                 break
         results.put((n, t0, t1))
     except Exception as e:  # reported to the parent, which then stops waiting
@@ -247,10 +251,12 @@ def _oracle_worker(st, seconds, barrier, results):
         barrier.abort()
 
 
-def oracle_jvp_all_cores(n_full: int, edge: int, seconds: float):
+def oracle_jvp_all_cores(n_full: int, edge: int, seconds: float = 10.0, steps: int | None = None,
+                         warmup: int = 0):
     """The oracle's tangent application on every host core at once: one
     process per core (spawned, so none inherits a CUDA context), each
-    applying the oracle to the same sample over a common window. Returns
+    applying the oracle to the same sample from a common start, for `seconds`
+    or for `steps` applications after `warmup` untimed ones. Returns
     (aggregate GDOF/s, description, processes). Raises on any failure or
     timeout."""
     import multiprocessing as mp
@@ -260,7 +266,7 @@ def oracle_jvp_all_cores(n_full: int, edge: int, seconds: float):
     ctx = mp.get_context("spawn")
     barrier = ctx.Barrier(procs + 1)
     results = ctx.Queue()
-    workers = [ctx.Process(target=_oracle_worker, args=(st, seconds, barrier, results), daemon=True)
+    workers = [ctx.Process(target=_oracle_worker, args=(st, seconds, steps, warmup, barrier, results), daemon=True)
                for _ in range(procs)]
     # one BLAS/OpenMP thread per process: the processes themselves fill the cores
     thread_vars = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
@@ -277,7 +283,7 @@ def oracle_jvp_all_cores(n_full: int, edge: int, seconds: float):
                 os.environ[k] = val
     try:
         barrier.wait(timeout=120)
-        out = [results.get(timeout=seconds + 120) for _ in workers]
+        out = [results.get(timeout=(seconds if steps is None else 600) + 120) for _ in workers]
     finally:
         barrier.abort()
         for w in workers:
@@ -292,23 +298,50 @@ def oracle_jvp_all_cores(n_full: int, edge: int, seconds: float):
     desc = (f"oracle tangent application (numpy, element loop with stored oracle Gauss-point "
             f"Hessians) on the {edge}^3-element block under the indenter of the {n_full}^3 "
             f"state: {sample_dofs} DOFs, {apps} applications by {procs} concurrent processes "
-            f"(one per host core) in {window:.1f} s")
+            f"(one per host core) in {window:.2f} s")
     return sample_dofs * apps / window / 1e9, desc, procs
+
+
+def workload_config(n: int, world: int) -> dict:
+    """The benchmark's `config`: the nano-indentation Newton step on an n^3
+    cube, with the level count of the library's default hierarchy."""
+    levels, m = 1, n
+    while m > 4:
+        m = (m + 1) // 2
+        levels += 1
+    ndofs = 9 * (n + 1) ** 3
+    return {
+        "workload": f"nano-indentation Newton step, {n}^3 Q1 hexes, {ndofs} DOFs per GPU, "
+                    f"{levels}-level geometric MG, load step 1/10, FGMRES(30) rtol 1e-8",
+        "problems": world, "l2": "inputs larger than L2 (8 GB Hessian store per application)",
+    }
 
 
 def reference_arm(args, rank):
     if rank != 0:
         return
-    value, desc, per = oracle_jvp_sample(args.n, args.sample, 0.0, steps=args.warmup + args.steps)
+    # each step: REF_APPS_PER_STEP oracle applications of the sample on every
+    # host core at once (a bounded sample of about a second)
+    sample_dofs = 9 * (args.sample + 1) ** 3
+    try:
+        value, desc, cores = oracle_jvp_all_cores(args.n, args.sample, steps=args.steps * REF_APPS_PER_STEP,
+                                                  warmup=args.warmup * REF_APPS_PER_STEP)
+        fallback = None
+    except Exception as e:  # one core then
+        value, desc, _ = oracle_jvp_sample(args.n, args.sample, 0.0,
+                                           steps=(args.warmup + args.steps) * REF_APPS_PER_STEP)
+        cores, fallback = 1, repr(e)
+    per = sample_dofs * cores * REF_APPS_PER_STEP / (value * 1e9)  # seconds per step
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"oracle tangent application, {args.sample}^3-element sample of the "
-                               f"{args.n}^3 indentation state"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "config": dict(workload_config(args.n, 1), sample=f"{args.sample}^3-element block of the state"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    if fallback is not None:
+        line["cpu_baseline"]["all_cores_failed"] = fallback
     print(json.dumps(line), flush=True)
 
 
@@ -574,7 +607,6 @@ def gpu_arm(args, rank, world, dist):
     st = inputs.config_indentation(args.n, seed=5 + rank, step=1)
     P = binding.problem_from_state(st)
     ndofs = 9 * P.n_nodes
-    nlev = P.n_levels
     U0 = torch.from_numpy(st.U).to(dev)
     Uw = torch.empty_like(U0)
     opts = abi.default_opts(abi.PFM_F32, max_newton=1, restart=30, max_lin_it=400, lin_rtol=1e-8)
@@ -723,11 +755,7 @@ def gpu_arm(args, rank, world, dist):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 tangent application in f64 FGMRES/Newton",
             "data": "synthetic (seeded indentation state, no dataset)",
-            "config": {
-                "workload": f"nano-indentation Newton step, {args.n}^3 Q1 hexes, {ndofs} DOFs per GPU, "
-                            f"{nlev}-level geometric MG, load step 1/10, FGMRES(30) rtol 1e-8",
-                "problems": world, "l2": "inputs larger than L2 (8 GB Hessian store per application)",
-            },
+            "config": workload_config(args.n, world),
             "newton_step_s": {"fp32_mg": ms_step / 1e3, "fp64": fp64["s"] if fp64 else None,
                               "fp32_mg_f16_store": f16["s"] if f16 else None},
             "fgmres_its": {"fp32_mg": rep.lin_its_last, "fp64": fp64["fgmres_its"] if fp64 else None,

@@ -27,6 +27,22 @@ def test_all_cores_sample():
     assert f"by {procs} concurrent processes" in desc
 
 
+def test_all_cores_fixed_steps():
+    """The reference arm's form: W untimed and K timed applications per process."""
+    value, desc, procs = bench.oracle_jvp_all_cores(8, 3, steps=4, warmup=1)
+    assert value > 0.0
+    assert f"{4 * procs} applications by {procs} concurrent processes" in desc
+
+
+def test_workload_config_levels():
+    from paper_2011_08802_gb300.binding import levels_to
+
+    for n in (8, 9, 16, 24, 32, 100, 128):
+        cfg = bench.workload_config(n, 1)
+        assert f"{levels_to(n)}-level geometric MG" in cfg["workload"]
+        assert f"{9 * (n + 1) ** 3} DOFs per GPU" in cfg["workload"]
+
+
 def test_all_cores_fails_fast(monkeypatch):
     # the sample is built in the parent: a state the workers cannot use makes
     # every worker fail before the barrier, which they then break

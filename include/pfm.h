@@ -129,28 +129,34 @@ void pfm_destroy(pfm_handle* h);
  * call on the handle. With h == NULL: the last error of pfm_create. */
 const char* pfm_last_error(const pfm_handle* h);
 
-/* Sizes of the finest level. */
+/* Sizes of the finest level. Errors: PFM_ERR_INVALID_ARG (NULL handle). */
 pfm_status pfm_get_sizes(const pfm_handle* h, int64_t* n_nodes, int64_t* n_elems, int* n_levels);
 
 /* Multigrid level l (0 = finest): element counts and, after pfm_linearize,
  * the power-iteration estimate of lambda_max(D^-1 J) used by the Chebyshev
- * smoother (0 on the coarsest level, which is solved directly). */
+ * smoother (0 on the coarsest level, which is solved directly).
+ * Errors: PFM_ERR_INVALID_ARG (NULL handle, level out of range). */
 pfm_status pfm_get_level(const pfm_handle* h, int level, int* nx, int* ny, int* nz, double* lambda_max);
 
 /* Power-iteration steps of the smoother's eigenvalue estimate (default 30,
- * 1..1000); takes effect at the next pfm_linearize. */
+ * 1..1000); takes effect at the next pfm_linearize.
+ * Errors: PFM_ERR_INVALID_ARG (out of range). */
 pfm_status pfm_set_power_iterations(pfm_handle* h, int iterations);
 
 /* Outer operator of the mixed-precision FGMRES: 1 (default) = the
  * double-float kernel of pfm_jacobian_apply_mixed (FP64-class accuracy on the
  * FP32 pipes; 12.8 ms at 128^3 on GB300), 0 = the FP64 kernel of
- * pfm_jacobian_apply (22 ms). */
+ * pfm_jacobian_apply (22 ms). Errors: PFM_ERR_INVALID_ARG (other values). */
 pfm_status pfm_set_outer_operator(pfm_handle* h, int double_float);
 
-/* Set the CUDA stream (a cudaStream_t passed as void*) used by all later calls. */
+/* Set the CUDA stream (a cudaStream_t passed as void*, owned by the caller and
+ * alive while the handle uses it) for all later calls. Errors:
+ * PFM_ERR_INVALID_ARG (NULL handle). */
 pfm_status pfm_set_stream(pfm_handle* h, void* stream);
 
-/* Replace the material parameters (same mesh). Invalidates the tangent. */
+/* Replace the material parameters of Sec. 2 (same mesh). Invalidates the
+ * tangent. Errors: PFM_ERR_INVALID_ARG (NULL pointers, an unknown Hencky
+ * mode). */
 pfm_status pfm_set_params(pfm_handle* h, const pfm_params* params);
 
 /* Dirichlet data (Sec. 5.1 boundary conditions): mask_dev (device, uint8
@@ -161,11 +167,15 @@ pfm_status pfm_set_params(pfm_handle* h, const pfm_params* params);
  * Errors: PFM_ERR_INVALID_ARG if an order-parameter DOF is masked. */
 pfm_status pfm_set_dirichlet(pfm_handle* h, const uint8_t* mask_dev, const double* val_dev);
 
-/* Current iterate U and previous-step state U_n (device, double [9][n_nodes]);
- * copied into the handle. Invalidates the tangent. */
+/* Current iterate U and previous-step state U_n of the backward-Euler step
+ * (Sec. 2.3, Eq. GlobIncPot) (device, double [9][n_nodes]); copied into the
+ * handle. Invalidates the tangent. Errors: PFM_ERR_INVALID_ARG (NULL
+ * pointers), PFM_ERR_CUDA. */
 pfm_status pfm_set_state(pfm_handle* h, const double* U_dev, const double* Un_dev);
 
-/* Copy the handle's current iterate to U_dev (device, double [9][n_nodes]). */
+/* Copy the handle's current iterate to U_dev (device, double [9][n_nodes]).
+ * Errors: PFM_ERR_INVALID_ARG (NULL pointer), PFM_ERR_STATE (no state),
+ * PFM_ERR_CUDA. */
 pfm_status pfm_get_state(pfm_handle* h, double* U_dev);
 
 /* Arithmetic of the FP64-class linearisation (finest and coarsest levels, and
@@ -205,7 +215,9 @@ pfm_status pfm_set_contact(pfm_handle* h, const double* center, double radius, d
  * exerts on the sphere, positive when pressing; equal to the derivative of
  * the contact energy with respect to the indentation depth) and the contact
  * energy at the current iterate, written to *load_host and (if not NULL)
- * *energy_host; 0 without contact. Synchronises. */
+ * *energy_host; 0 without contact (Sec. 2.5). Synchronises.
+ * Errors: PFM_ERR_INVALID_ARG (load_host NULL), PFM_ERR_STATE (no state),
+ * PFM_ERR_CUDA. */
 pfm_status pfm_contact_load(pfm_handle* h, double* load_host, double* energy_host);
 
 /* Microstructure diagnostics of Sec. 5.3 of the nodal state U_dev (device,
@@ -228,7 +240,8 @@ pfm_status pfm_diagnostics(pfm_handle* h, const double* U_dev, double* Iv_dev, d
  * Eq. FinalRes) at the current state, written to R_dev (device, double
  * [9][n_nodes]), zero at Dirichlet DOFs. If energy_host != NULL the total
  * potential sum_e sum_q w_q (F + D_tau + penalty) is written there
- * (synchronises). */
+ * (synchronises). Errors: PFM_ERR_INVALID_ARG (R_dev NULL), PFM_ERR_STATE
+ * (no state), PFM_ERR_CUDA. */
 pfm_status pfm_residual(pfm_handle* h, double* R_dev, double* energy_host);
 
 /* Linearise at the current state (the paper's tangent assembly, Sec. 3.4):
@@ -236,7 +249,10 @@ pfm_status pfm_residual(pfm_handle* h, double* R_dev, double* energy_host);
  * Hessians of the local energy (FP64 on the finest level; FP32 copies for an
  * FP32 preconditioner when precond == PFM_F32, FP64 otherwise), build the
  * 9x9 nodal block inverses of the point-block Jacobi smoother (dense LU with
- * partial pivoting) and the dense LU of the coarsest operator. */
+ * partial pivoting) and the dense LU of the coarsest operator.
+ * Errors: PFM_ERR_STATE (no state), PFM_ERR_OOM, PFM_ERR_BREAKDOWN (a singular
+ * nodal block or coarse operator), PFM_ERR_NONFINITE (non-finite Hessian
+ * entries met by the binary16 copy), PFM_ERR_CUDA. */
 pfm_status pfm_linearize(pfm_handle* h, pfm_precision precond);
 
 /* y = J v with J = dR/dU at the last linearisation (Eq. linAlgEq), matrix
@@ -244,10 +260,16 @@ pfm_status pfm_linearize(pfm_handle* h, pfm_precision precond);
  * [9][n_nodes] of float (PFM_F32) or double (PFM_F64). FP32 needs an FP32
  * tangent (pfm_linearize with PFM_F32) and applies the preconditioner's
  * finest-level operator: from the FP32 store, or from its binary16 copy
- * after pfm_set_preconditioner_store(h, 1). v and y must not alias. */
+ * after pfm_set_preconditioner_store(h, 1). v and y must not alias.
+ * Errors: PFM_ERR_INVALID_ARG (NULL vectors, unknown precision),
+ * PFM_ERR_STATE (no state, no tangent, or no tangent in that precision),
+ * PFM_ERR_CUDA. */
 pfm_status pfm_jacobian_apply(pfm_handle* h, const void* v_dev, void* y_dev, pfm_precision prec);
 
-/* y = J^T v (adjoint product), same layout and rules as pfm_jacobian_apply. */
+/* y = J^T v (adjoint product). J is the Hessian of the discrete potential
+ * (Sec. 3.4, Eq. PenPot), hence symmetric (Dirichlet rows and columns are
+ * identity), so J^T v = J v: same layout, rules and errors as
+ * pfm_jacobian_apply. */
 pfm_status pfm_jacobian_transpose_apply(pfm_handle* h, const void* v_dev, void* y_dev,
                                         pfm_precision prec);
 
@@ -256,11 +278,15 @@ pfm_status pfm_jacobian_transpose_apply(pfm_handle* h, const void* v_dev, void* 
  * arithmetic (pairs of FP32 numbers, about 48 significant bits) from the FP32
  * Hessian store and its FP32 rounding remainder. This is the outer operator
  * of the mixed-precision FGMRES, whose Krylov directions are FP32 V-cycle
- * outputs. Needs pfm_linearize(PFM_F32). */
+ * outputs (Eq. linAlgEq). Errors: PFM_ERR_INVALID_ARG (NULL vectors),
+ * PFM_ERR_STATE (no tangent from pfm_linearize(PFM_F32)), PFM_ERR_CUDA. */
 pfm_status pfm_jacobian_apply_mixed(pfm_handle* h, const float* v_dev, double* y_dev);
 
-/* pfm_jacobian_apply with HOST arrays: copies v in, applies, copies y out
- * (synchronises). Uses library-owned device buffers. */
+/* pfm_jacobian_apply with HOST arrays v_host, y_host (float or double
+ * [9][n_nodes] by prec; pinned memory lets the copies overlap): v travels to
+ * the device in z-slabs while earlier slabs are applied, y returns plane by
+ * plane (synchronises). Uses library-owned device buffers. Errors: as
+ * pfm_jacobian_apply, PFM_ERR_OOM. */
 pfm_status pfm_jacobian_apply_host(pfm_handle* h, const void* v_host, void* y_host,
                                    pfm_precision prec);
 
@@ -270,7 +296,9 @@ pfm_status pfm_jacobian_apply_host(pfm_handle* h, const void* v_host, void* y_ho
  * nu_post smoothing steps. r_dev, z_dev: device [9][n_nodes] in the precision
  * prec (the precision of the preconditioner built by pfm_linearize). Uses
  * opts->nu_pre, nu_post, smoother, cheb_lo, cheb_hi, omega (NULL = defaults
- * 4, 4, Chebyshev, 0.05, 1.1). */
+ * 4, 4, Chebyshev, 0.05, 1.1). Errors: PFM_ERR_INVALID_ARG (NULL vectors),
+ * PFM_ERR_STATE (no tangent, or prec differs from the preconditioner's),
+ * PFM_ERR_CUDA. */
 pfm_status pfm_vcycle(pfm_handle* h, const void* r_dev, void* z_dev, pfm_precision prec,
                       const pfm_solve_opts* opts);
 
@@ -286,7 +314,10 @@ pfm_status pfm_fgmres_solve(pfm_handle* h, const pfm_solve_opts* opts, const dou
  * J dU = -R solved by pfm_fgmres_solve, until ||R|| <= newton_rtol ||R_0|| or
  * max_newton corrections. U_inout_dev (device double [9][n_nodes]) is the
  * initial iterate on entry and the result on exit; the handle's U_n stays.
- * Synchronises; report (nullable) gets iteration counts, norms and times. */
+ * Synchronises; report (nullable) gets iteration counts, norms and times.
+ * Errors: PFM_ERR_INVALID_ARG (NULL options or state vector), PFM_ERR_STATE
+ * (no state), PFM_ERR_NOT_CONVERGED, PFM_ERR_NONFINITE, PFM_ERR_BREAKDOWN
+ * (U_inout holds the last iterate), PFM_ERR_OOM, PFM_ERR_CUDA. */
 pfm_status pfm_newton_solve(pfm_handle* h, const pfm_solve_opts* opts, double* U_inout_dev,
                             pfm_solve_report* report);
 
@@ -312,13 +343,17 @@ pfm_status pfm_param_grad(pfm_handle* h, const double* w_dev, double* dPi_dtheta
  * energy density W (device double [n]), its gradient (device double
  * [n][15], z = (F row-major, eta_1..6)) and the packed upper triangle of its
  * Hessian (device double [n][120], row-major over r <= c; NULL to skip).
- * Uses the parameters of h and synchronises. */
+ * The density is the local part of Eq. PenPot (elastic energy with the
+ * Hencky strain of Sec. 2.4, chemical, obstacle, dissipation and penalty
+ * terms). Uses the parameters of h and synchronises. Errors:
+ * PFM_ERR_INVALID_ARG (NULL inputs, n < 0), PFM_ERR_CUDA. */
 pfm_status pfm_qp_eval(pfm_handle* h, int64_t n, const double* F_dev, const double* eta_dev,
                        const double* eta_n_dev, double* W_dev, double* grad_dev, double* hess_dev);
 
 /* Copy the stored FP64 Gauss-point Hessians of elements [e0, e0+count) of
  * the finest level to hess_host (host double [count][8][120], Gauss point
- * q = q0 + 2 q1 + 4 q2). Synchronises. */
+ * q = q0 + 2 q1 + 4 q2). Synchronises. Errors: PFM_ERR_INVALID_ARG (range
+ * outside the grid, NULL output), PFM_ERR_STATE (no tangent), PFM_ERR_CUDA. */
 pfm_status pfm_get_hessians(pfm_handle* h, int64_t e0, int64_t count, double* hess_host);
 
 /* Device timing of the hot phases with CUDA events recorded on the handle's
@@ -338,22 +373,22 @@ typedef enum {
   PFM_PROF_COUNT = 6
 } pfm_prof_id;
 
+/* Errors: PFM_ERR_INVALID_ARG (NULL handle). */
 pfm_status pfm_profile_enable(pfm_handle* h, int enable);
 
 /* Number of timed launches of phase id and their summed device time (ms)
- * since profiling was enabled. Synchronises the stream. */
+ * since profiling was enabled. Synchronises the stream. Errors:
+ * PFM_ERR_INVALID_ARG (NULL handle or outputs, id out of range). */
 pfm_status pfm_profile_get(pfm_handle* h, int id, int64_t* launches, double* total_ms);
 
 /* Kernel launches issued by the library in this process so far (all handles). */
 int64_t pfm_launch_count(void);
 
 /* A batch of independent problems of possibly different grid sizes, each a
- * handle with its own Dirichlet data and state, solved together: every
- * problem gets its own CUDA stream, the Newton and FGMRES iterations of all
- * problems advance in lockstep (one synchronisation per iteration for the
- * whole batch), and each problem's V-cycle is replayed from a CUDA graph
- * captured once per linearisation. The handles must outlive the batch and
- * must not be used by other calls while pfm_batch_newton_solve runs.
+ * handle with its own Dirichlet data and state, solved together by
+ * pfm_batch_newton_solve (batched engine or lockstep driver, below). The
+ * handles must outlive the batch and must not be used by other calls while
+ * pfm_batch_newton_solve runs.
  * Errors: PFM_ERR_INVALID_ARG (null handle, count < 1), PFM_ERR_CUDA. */
 typedef struct pfm_batch pfm_batch;
 pfm_status pfm_batch_create(pfm_handle* const* handles, int count, pfm_batch** out);
@@ -368,12 +403,17 @@ const char* pfm_batch_last_error(const pfm_batch* b);
  * continue. Returns the first failing status, PFM_OK if every problem
  * converged. Synchronises.
  * With the mixed-precision options (precond PFM_F32, Chebyshev smoother,
- * V-cycle, double-float outer operator) the batched engine runs: every phase
+ * V-cycle, double-float outer operator) and no contact or binary16
+ * preconditioner store on any problem, the batched engine runs: every phase
  * (linearisation of all levels, eigenvalue estimates, coarse inverses,
  * V-cycle steps, FGMRES vector work) is one launch over all problems, and each
  * FGMRES iteration of the batch is one replayed CUDA graph. Other options, or
- * mode 1 of pfm_batch_set_mode, advance the problems in lockstep with
- * per-problem launches. Both give the same iterates up to rounding. */
+ * mode 1 of pfm_batch_set_mode, advance the problems in lockstep: every
+ * problem on its own CUDA stream with per-problem launches, one
+ * synchronisation per iteration for the whole batch, each problem's V-cycle
+ * replayed from a CUDA graph captured once per linearisation. Both give the
+ * same iterates up to rounding. Errors: as pfm_newton_solve, for the first
+ * failing problem; PFM_ERR_INVALID_ARG (NULL batch, options or vectors). */
 pfm_status pfm_batch_newton_solve(pfm_batch* b, const pfm_solve_opts* opts, double* const* U_inout,
                                   pfm_solve_report* reports);
 
@@ -387,7 +427,8 @@ pfm_status pfm_batch_set_mode(pfm_batch* b, int mode);
  * that owns all device memory through its own allocator, code that must not
  * pay allocation latency or fragment a memory pool mid time step, or a device
  * that is already full. (The paper has no counterpart: this is an interface
- * choice of this library.) Computes what pfm_residual computes for the state
+ * choice of this library.) Computes what pfm_residual computes (Sec. 3.4,
+ * Eq. FinalRes) for the state
  * U_dev / Un_dev (device double [9][n_nodes]) with Dirichlet mask mask_dev
  * (device uint8 [9][n_nodes]) on the grid of *mesh (n_levels ignored) with
  * *params: R_dev (device double [9][n_nodes], zero at Dirichlet DOFs) and,

@@ -155,8 +155,8 @@ pfm_status pfm_set_outer_operator(pfm_handle* h, int double_float);
 pfm_status pfm_set_stream(pfm_handle* h, void* stream);
 
 /* Replace the material parameters of Sec. 2 (same mesh). Invalidates the
- * tangent. Errors: PFM_ERR_INVALID_ARG (NULL pointers, an unknown Hencky
- * mode). */
+ * tangent. Errors: PFM_ERR_INVALID_ARG (NULL pointers, tau <= 0, an unknown
+ * Hencky mode). */
 pfm_status pfm_set_params(pfm_handle* h, const pfm_params* params);
 
 /* Dirichlet data (Sec. 5.1 boundary conditions): mask_dev (device, uint8
@@ -296,7 +296,8 @@ pfm_status pfm_jacobian_apply_host(pfm_handle* h, const void* v_host, void* y_ho
  * nu_post smoothing steps. r_dev, z_dev: device [9][n_nodes] in the precision
  * prec (the precision of the preconditioner built by pfm_linearize). Uses
  * opts->nu_pre, nu_post, smoother, cheb_lo, cheb_hi, omega (NULL = defaults
- * 4, 4, Chebyshev, 0.05, 1.1). Errors: PFM_ERR_INVALID_ARG (NULL vectors),
+ * 4, 4, Chebyshev, 0.05, 1.1). Errors: PFM_ERR_INVALID_ARG (NULL vectors,
+ * nu_pre < 1, nu_post < 0, an unknown smoother, 0 < cheb_lo < cheb_hi violated),
  * PFM_ERR_STATE (no tangent, or prec differs from the preconditioner's),
  * PFM_ERR_CUDA. */
 pfm_status pfm_vcycle(pfm_handle* h, const void* r_dev, void* z_dev, pfm_precision prec,

@@ -201,6 +201,26 @@ class OracleJvp:
         self.fe.jvp(self.disc, self.st, self.v, self.d)
 
 
+def oracle_residual_sample(n_full: int, edge: int, seconds: float):
+    """Time the CPU oracle's residual (energy gradient by second-order jets,
+    Sec. 3.4, Eq. FinalRes) on one core on the same sample. Returns (GDOF/s,
+    seconds per residual)."""
+    from oracle import fe, qp
+
+    st, sample_dofs = oracle_sample_state(n_full, edge)
+    disc = fe.Discretisation(st.mesh)
+    mat = qp.material_from(st.material, st.tau)
+    fe.residual(disc, st, mat)  # warm
+    t0, n = time.perf_counter(), 0
+    while True:
+        fe.residual(disc, st, mat)
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    per = (time.perf_counter() - t0) / n
+    return sample_dofs / per / 1e9, per
+
+
 def oracle_jvp_sample(n_full: int, edge: int, seconds: float, steps: int | None = None):
     """Time the CPU oracle's tangent application on one core on an edge^3
     block of elements of the benchmark state. Returns (GDOF/s, sample
@@ -739,7 +759,9 @@ def gpu_arm(args, rank, world, dist):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         c1, desc1, _ = oracle_jvp_sample(args.n, args.sample, seconds=5.0)
-        single = {"value": c1, "cores": 1, "sample": desc1}
+        r1, rper = oracle_residual_sample(args.n, args.sample, seconds=3.0)
+        single = {"value": c1, "cores": 1, "sample": desc1,
+                  "residual": {"value": r1, "unit": UNIT, "ms": rper * 1e3}}
         try:
             cv, desc, cores = oracle_jvp_all_cores(args.n, args.sample, seconds=10.0)
             cpu = {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,

@@ -20,6 +20,11 @@ def test_single_core_sample():
     assert "3^3-element block" in desc and "576 DOFs" in desc
 
 
+def test_residual_sample():
+    value, per = bench.oracle_residual_sample(8, 3, 0.1)
+    assert value > 0.0 and per > 0.0
+
+
 def test_all_cores_sample():
     value, desc, procs = bench.oracle_jvp_all_cores(8, 3, 1.0)
     assert procs == len(os.sched_getaffinity(0))

@@ -1025,10 +1025,13 @@ pfm_status pfm_set_preconditioner_store(pfm_handle* h, int half) {
   if (half != 0 && half != 1) return h->fail(PFM_ERR_INVALID_ARG, "expected 0 or 1");
   h->pre_h16 = half != 0;
   h->linearized = false;
-  for (auto& lv : h->L) lv.h16_scale = 0.f;
-  if (h->vgraph) {
+  if (h->vgraph) {  // may hold launches that read the copies
     cudaGraphExecDestroy(h->vgraph);
     h->vgraph = nullptr;
+  }
+  for (auto& lv : h->L) {
+    lv.h16_scale = 0.f;
+    if (!h->pre_h16) dfree(lv.H16);  // cudaFree waits for work still reading it
   }
   return PFM_OK;
 }

@@ -75,3 +75,18 @@ def test_oversized_coarse_level_is_rejected(binding, st):
     with pytest.raises(binding.PfmError) as e:
         binding.Problem(16, 16, 16, 64.0, 64.0, 64.0, abi.params_from_material(st.material, st.tau), n_levels=1)
     assert e.value.status == INVALID_ARG
+
+
+@pytest.mark.parametrize("dims, lengths, n_levels, tau", [
+    ((0, 4, 4), (8.0, 8.0, 8.0), 0, 0.1),   # empty grid
+    ((4, 4, 0), (8.0, 8.0, 8.0), 0, 0.1),
+    ((4, 4, 4), (8.0, 0.0, 8.0), 0, 0.1),   # degenerate box
+    ((4, 4, 4), (8.0, 8.0, 8.0), -1, 0.1),  # negative level count
+    ((4, 4, 4), (8.0, 8.0, 8.0), 0, 0.0),   # no time increment
+])
+def test_empty_and_degenerate_problems_are_rejected(binding, st, dims, lengths, n_levels, tau):
+    params = abi.params_from_material(st.material, tau if tau > 0 else 0.1)
+    params.tau = tau
+    with pytest.raises(binding.PfmError) as e:
+        binding.Problem(*dims, *lengths, params, n_levels=n_levels)
+    assert e.value.status == INVALID_ARG

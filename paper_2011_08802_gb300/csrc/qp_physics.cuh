@@ -281,29 +281,13 @@ PFM_HD void jacobi_eig3(T a[3][3], T lam[3], T Q[3][3]) {
         a[p][q] = a[q][p] = T(0);
         continue;
       }
-      // rotation angle phi with tan(2 phi) = 2 a_pq / (a_qq - a_pp) zeroes
-      // a_pq; t = tan(phi), c = cos(phi), s = sin(phi), tau = tan(phi / 2)
-      const T dqp = a[q][q] - a[p][p];
-      T t, c, s, tau;
-      if (fabs(apq) < T(1e-3) * fabs(dqp)) {
-        // small angle (every rotation after a lower-precision seed): with
-        // r = a_pq / (a_qq - a_pp), t = r - r^3 + 2 r^5 - ..., c = 1 - t^2/2 +
-        // 3 t^4/8 - ..., tau = t/2 - t^3/8 + t^5/16 - ...; for |r| < 1e-3 the
-        // dropped terms are below 1e-17 relative
-        const T r = apq / dqp, r2 = r * r;
-        t = r * (T(1) - r2 * (T(1) - T(2) * r2));
-        const T t2 = t * t;
-        c = T(1) - t2 * (T(0.5) - T(0.375) * t2);
-        s = t * c;
-        tau = t * (T(0.5) - t2 * (T(0.125) - T(0.0625) * t2));
-      } else {
-        const T theta = dqp / (T(2) * apq);
-        t = T(1) / (fabs(theta) + sqrt(theta * theta + T(1)));
-        if (theta < T(0)) t = -t;
-        c = T(1) / sqrt(t * t + T(1));
-        s = t * c;
-        tau = s / (T(1) + c);
-      }
+      // rotation angle phi with cot(2 phi) = theta zeroes a_pq; t = tan(phi)
+      T theta = (a[q][q] - a[p][p]) / (T(2) * apq);
+      T t = T(1) / (fabs(theta) + sqrt(theta * theta + T(1)));
+      if (theta < T(0)) t = -t;
+      T c = T(1) / sqrt(t * t + T(1));
+      T s = t * c;
+      T tau = s / (T(1) + c);
       a[p][p] -= t * apq;
       a[q][q] += t * apq;
       a[p][q] = a[q][p] = T(0);

@@ -1,4 +1,5 @@
-// Device-side building blocks of the multigrid kernels, shared by the
+// Building blocks of the multigrid kernels (the transfers also compile for
+// the host, where a test checks them against the oracle), shared by the
 // single-problem kernels (mg_kernels.cu) and the batched kernels (batch.cu):
 // integer-exact 1-D interpolation between structured grids on the same box,
 // state injection, prolongation and restriction at one node, the Chebyshev
@@ -22,7 +23,7 @@ struct Interp1 {
   double t;  // weight of i0+1
 };
 
-__device__ __forceinline__ Interp1 interp1(int i, int nf, int nc) {
+__host__ __device__ __forceinline__ Interp1 interp1(int i, int nf, int nc) {
   // coarse coordinate of fine node i: i*nc/nf
   long long num = (long long)i * nc;
   int I0 = int(num / nf);
@@ -34,7 +35,7 @@ __device__ __forceinline__ Interp1 interp1(int i, int nf, int nc) {
 // Value of the nodal field X (grid nx,ny,nz; field stride n) at the point with
 // per-axis element index i0 and local coordinate t (trilinear).
 template <typename T>
-__device__ __forceinline__ double trilinear(const T* X, int nx, int ny, const int i0[3], const double t[3]) {
+__host__ __device__ __forceinline__ double trilinear(const T* X, int nx, int ny, const int i0[3], const double t[3]) {
   double s = 0.0;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -48,7 +49,7 @@ __device__ __forceinline__ double trilinear(const T* X, int nx, int ny, const in
 }
 
 // Coarse node idx: the fine Q1 field evaluated at its position, all fields.
-__device__ __forceinline__ void inject_node(const Grid& f, const Grid& c, const double* __restrict__ Uf,
+__host__ __device__ __forceinline__ void inject_node(const Grid& f, const Grid& c, const double* __restrict__ Uf,
                                             double* __restrict__ Uc, int64_t idx) {
   const int64_t nnc = c.nn();
   const int64_t nnf = f.nn();
@@ -69,7 +70,7 @@ __device__ __forceinline__ void inject_node(const Grid& f, const Grid& c, const 
 
 // Fine node idx: xf += P xc at its free DOFs.
 template <typename T>
-__device__ __forceinline__ void prolong_node(const Grid& f, const Grid& c, const T* __restrict__ xc,
+__host__ __device__ __forceinline__ void prolong_node(const Grid& f, const Grid& c, const T* __restrict__ xc,
                                              const dmask_t* __restrict__ mf, T* __restrict__ xf, int64_t idx) {
   const int64_t nnf = f.nn();
   const int64_t nnc = c.nn();
@@ -90,7 +91,7 @@ __device__ __forceinline__ void prolong_node(const Grid& f, const Grid& c, const
 // node I collects fine nodes i with |i*nc - I*nf| < nf, weight
 // 1 - |i*nc - I*nf|/nf (per axis).
 template <typename T>
-__device__ __forceinline__ void restrict_node(const Grid& f, const Grid& c, const T* __restrict__ rf,
+__host__ __device__ __forceinline__ void restrict_node(const Grid& f, const Grid& c, const T* __restrict__ rf,
                                               const dmask_t* __restrict__ mc, T* __restrict__ rc, int64_t idx) {
   const int64_t nnf = f.nn();
   const int64_t nnc = c.nn();

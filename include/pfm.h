@@ -427,14 +427,13 @@ pfm_status pfm_batch_set_mode(pfm_batch* b, int mode);
  * memory, for callers that cannot call cudaMalloc: code inside a framework
  * that owns all device memory through its own allocator, code that must not
  * pay allocation latency or fragment a memory pool mid time step, or a device
- * that is already full. (The paper has no counterpart: this is an interface
- * choice of this library.) Computes what pfm_residual computes (Sec. 3.4,
- * Eq. FinalRes) for the state
- * U_dev / Un_dev (device double [9][n_nodes]) with Dirichlet mask mask_dev
- * (device uint8 [9][n_nodes]) on the grid of *mesh (n_levels ignored) with
- * *params: R_dev (device double [9][n_nodes], zero at Dirichlet DOFs) and,
- * if energy_host != NULL, the potential. Enqueued on stream (a cudaStream_t
- * as void*, NULL = default stream); synchronises that stream.
+ * that is already full. The paper has no counterpart: this is an interface
+ * choice of this library. It computes what pfm_residual computes, for the
+ * state U_dev / Un_dev (device double [9][n_nodes]) with Dirichlet mask
+ * mask_dev (device uint8 [9][n_nodes]) on the grid of *mesh (n_levels
+ * ignored) with *params: R_dev (device double [9][n_nodes], zero at Dirichlet
+ * DOFs) and, if energy_host != NULL, the potential. Enqueued on stream (a
+ * cudaStream_t as void*, NULL = default stream); synchronises that stream.
  * Working memory: one file-scope device array, sized for at most 4,194,304
  * nodes (about 8 MB), which every GPU that loads the library keeps until the
  * process exits; larger grids are rejected with PFM_ERR_INVALID_ARG. The first
@@ -443,13 +442,16 @@ pfm_status pfm_batch_set_mode(pfm_batch* b, int mode);
  * calls share the one array, so calls that overlap on the GPU (different
  * streams or host threads) race and must be serialised by the caller.
  * Errors: PFM_ERR_INVALID_ARG (null pointer, bad sizes, too many nodes, a
- * prescribed order-parameter DOF), PFM_ERR_CUDA; the message is returned by
- * pfm_noalloc_last_error(). */
+ * prescribed order-parameter DOF), PFM_ERR_CUDA. On any error the contents of
+ * R_dev are undefined (the prescribed order-parameter check completes after
+ * R_dev has been written). The message is returned by
+ * pfm_noalloc_last_error() on the same host thread. */
 pfm_status pfm_residual_noalloc(const pfm_mesh_desc* mesh, const pfm_params* params,
                                 const uint8_t* mask_dev, const double* U_dev, const double* Un_dev,
                                 double* R_dev, double* energy_host, void* stream);
 
-/* Message of the last pfm_residual_noalloc error ("" if none). */
+/* Message of the last pfm_residual_noalloc error of the calling host thread
+ * ("" if none). */
 const char* pfm_noalloc_last_error(void);
 
 #ifdef __cplusplus

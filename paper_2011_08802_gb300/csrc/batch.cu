@@ -1361,11 +1361,15 @@ pfm_status eng_fgmres(pfm_batch* b, BatchEngine* E) {
     E->itg_launches.resize(E->m, 0);
   }
   // each problem runs at most max_lin_it iterations and starts a cycle at most
-  // once per iteration, so a correct run makes at most 2 max_lin_it + 1 passes
+  // once per iteration, so a correct run makes at most 2 max_lin_it + 1 passes;
+  // the loop stops after 2 (max_lin_it + m) + 8 passes (a margin over that
+  // count) and reports the solver loop's non-termination as not converged
   const int64_t pass_cap = 2 * (int64_t(E->max_lin_it) + E->m) + 8;
   int64_t passes = 0;
   while (E->hflags[0] > 0 || E->hflags[1] > 0) {
-    if (++passes > pass_cap) return b->fail(PFM_ERR_CUDA, "batched FGMRES did not end within its iteration cap");
+    if (++passes > pass_cap)
+      return b->fail(PFM_ERR_NOT_CONVERGED, "batched FGMRES did not end within its pass cap of " +
+                                                std::to_string(pass_cap) + " graph launches");
     if (E->hflags[0] == 0) {  // every running cycle has ended: restart the ones that need it
       eng_cycle_start(E, false);
       BCK(cudaGetLastError());

@@ -86,21 +86,12 @@ __global__ void __launch_bounds__(128) k_linearize(Grid g, DevParams P, const do
 }
 
 // ---- BEGIN tangent application kernel
-// Asynchronous bulk prefetch of a contiguous global range into L2 (the
-// bulk-copy engine; no registers or shared memory involved). Address 16-byte
-// aligned, size a multiple of 16 bytes.
-__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 // y += J v over the elements (y initialised by k_japply_init). Persistent
-// warps walk the element blocks (4 elements each) with a grid stride; before
-// working on a block, lane 0 prefetches the block this warp takes PF strides
-// later, so every warp keeps its next 15 KB (FP32) of Hessians in flight.
+// warps walk the element blocks (4 elements each) with a grid stride.
 #ifndef PFM_JAPPLY_MINB
 #define PFM_JAPPLY_MINB 2
 #endif
-template <typename T, int PF>
+template <typename T>
 __global__ void __launch_bounds__(256, PFM_JAPPLY_MINB) k_japply(Grid g, JParams<T> jp, const T* __restrict__ H,
                                                 const dmask_t* __restrict__ mask,
                                                 const T* __restrict__ v, T* __restrict__ y) {
@@ -108,14 +99,7 @@ __global__ void __launch_bounds__(256, PFM_JAPPLY_MINB) k_japply(Grid g, JParams
   const int64_t wg = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   const int lane = int(threadIdx.x & 31);
-  constexpr unsigned BLK_BYTES = unsigned(HBLK * sizeof(T));
-  if (lane == 0)
-    for (int d = 0; d < PF; ++d)
-      if (wg + d * nw < nblk) prefetch_l2(H + (wg + d * nw) * HBLK, BLK_BYTES);
-  for (int64_t blk = wg; blk < nblk; blk += nw) {
-    if (lane == 0 && blk + PF * nw < nblk) prefetch_l2(H + (blk + PF * nw) * HBLK, BLK_BYTES);
-    japply_block<T>(g, jp, H, mask, v, y, blk, lane);
-  }
+  for (int64_t blk = wg; blk < nblk; blk += nw) japply_block<T>(g, jp, H, mask, v, y, blk, lane);
 }
 
 // ---- END tangent application kernel
@@ -126,7 +110,6 @@ __global__ void __launch_bounds__(256, PFM_JAPPLY_MINB) k_japply(Grid g, JParams
 #ifndef PFM_JAPPLY_H16_MINB
 #define PFM_JAPPLY_H16_MINB PFM_JAPPLY_MINB
 #endif
-template <int PF>
 __global__ void __launch_bounds__(256, PFM_JAPPLY_H16_MINB) k_japply_h16(Grid g, JParams<float> jp, float wh,
                                                     const __half* __restrict__ H,
                                                     const dmask_t* __restrict__ mask,
@@ -135,14 +118,7 @@ __global__ void __launch_bounds__(256, PFM_JAPPLY_H16_MINB) k_japply_h16(Grid g,
   const int64_t wg = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   const int lane = int(threadIdx.x & 31);
-  constexpr unsigned BLK_BYTES = unsigned(HBLK * sizeof(__half));
-  if (lane == 0)
-    for (int d = 0; d < PF; ++d)
-      if (wg + d * nw < nblk) prefetch_l2(H + (wg + d * nw) * HBLK, BLK_BYTES);
-  for (int64_t blk = wg; blk < nblk; blk += nw) {
-    if (lane == 0 && blk + PF * nw < nblk) prefetch_l2(H + (blk + PF * nw) * HBLK, BLK_BYTES);
-    japply_block_h16(g, jp, wh, H, mask, v, y, blk, lane);
-  }
+  for (int64_t blk = wg; blk < nblk; blk += nw) japply_block_h16(g, jp, wh, H, mask, v, y, blk, lane);
 }
 
 // y += J v with v in FP32 (exact input), the tangent as Hhi + Hlo (two FP32
@@ -341,12 +317,6 @@ __global__ void k_identity_rows(int64_t nn, const dmask_t* __restrict__ mask, co
   }
 }
 
-// element blocks a warp prefetches ahead of the one it works on
-#ifndef PFM_JAPPLY_PF
-#define PFM_JAPPLY_PF 0
-#endif
-constexpr int JAPPLY_PF = PFM_JAPPLY_PF;
-
 }  // namespace
 
 void launch_residual(const Grid& g, const DevParams& P, const double* U, const double* Un,
@@ -451,17 +421,17 @@ int sm_count() {
 template <typename T>
 void japply_elem(const Grid& g, const JParams<T>& jp, float, const T* H, const dmask_t* mask, const T* v, T* y,
                  unsigned blocks, int threads, cudaStream_t s) {
-  k_japply<T, JAPPLY_PF><<<blocks, threads, 0, s>>>(g, jp, H, mask, v, y);
+  k_japply<T><<<blocks, threads, 0, s>>>(g, jp, H, mask, v, y);
 }
 inline void japply_elem(const Grid& g, const JParams<float>& jp, float wh, const __half* H, const dmask_t* mask,
                         const float* v, float* y, unsigned blocks, int threads, cudaStream_t s) {
-  k_japply_h16<JAPPLY_PF><<<blocks, threads, 0, s>>>(g, jp, wh, H, mask, v, y);
+  k_japply_h16<<<blocks, threads, 0, s>>>(g, jp, wh, H, mask, v, y);
 }
 template <typename T>
 const void* japply_elem_fn(const T*) {
-  return reinterpret_cast<const void*>(k_japply<T, JAPPLY_PF>);
+  return reinterpret_cast<const void*>(k_japply<T>);
 }
-inline const void* japply_elem_fn(const __half*) { return reinterpret_cast<const void*>(k_japply_h16<JAPPLY_PF>); }
+inline const void* japply_elem_fn(const __half*) { return reinterpret_cast<const void*>(k_japply_h16); }
 
 template <typename T, typename S = T>
 void japply_launch_shape(const Grid& g, const JParams<T>& jp, float wh, const S* H, const dmask_t* mask, const T* v,

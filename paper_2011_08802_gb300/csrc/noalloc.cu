@@ -33,7 +33,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 constexpr int MAX_DEVICES = 64;
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_dev[MAX_DEVICES] = {nullptr};
-std::string g_noalloc_error;
+// one message per host thread, so that two threads that fail at once do not
+// write the same string
+thread_local std::string g_noalloc_error;
 
 // Device address of the scratch array on the current device. The name of a
 // __device__ variable in host code is only a host-side stand-in, so the

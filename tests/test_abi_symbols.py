@@ -47,3 +47,30 @@ def test_version_string(lib):
     f = lib.pfm_version
     f.restype = ctypes.c_char_p
     assert f().decode().startswith("pfm")
+
+
+def _body(src, signature):
+    """Text of the function whose definition starts with ``signature`` (brace matched)."""
+    i = src.index(signature)
+    j = src.index("{", i)
+    depth = 0
+    for k in range(j, len(src)):
+        depth += {"{": 1, "}": -1}.get(src[k], 0)
+        if depth == 0:
+            return src[j:k + 1]
+    raise AssertionError(f"unbalanced braces after {signature}")
+
+
+def test_noalloc_path_names_no_allocator():
+    """pfm_residual_noalloc and the two launchers it calls make no device
+    allocation: no call of cudaMalloc* (or cudaFree*) anywhere in its file or in
+    those launchers' bodies."""
+    csrc = os.path.join(ROOT, "paper_2011_08802_gb300", "csrc")
+    call = re.compile(r"\b(cudaMalloc\w*|cudaFree\w*|cuMemAlloc\w*)\s*\(")
+    code = lambda t: re.sub(r"//[^\n]*", "", re.sub(r"/\*.*?\*/", "", t, flags=re.S))
+    noalloc = code(open(os.path.join(csrc, "noalloc.cu")).read())
+    assert not call.search(noalloc)
+    fe = code(open(os.path.join(csrc, "fe_kernels.cu")).read())
+    kr = code(open(os.path.join(csrc, "krylov_kernels.cu")).read())
+    assert not call.search(_body(fe, "void launch_residual("))
+    assert not call.search(_body(kr, "void launch_build_mask("))

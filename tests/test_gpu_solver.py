@@ -98,9 +98,13 @@ def test_newton_step_matches_oracle(binding, smooth8):
 
 
 def test_newton_converges_quadratically(binding):
-    """Newton's method (Eq. linAlgEq) on the first indentation load step:
-    the residual falls by 1e-9 within five corrections, with a quadratic
-    contraction once in the basin (inexact 1e-10 linear solves)."""
+    """Newton's method (Eq. linAlgEq) on the first indentation load step.
+    With linear solves to a relative residual eta = 1e-10 (inexact Newton),
+    the relative residuals rho_k = ||R_k|| / ||R_0|| obey
+    rho_{k+1} <= eta rho_k + C rho_k^2: quadratic once in the basin, until
+    the eta rho_k and FP64 rounding floors. Asserted: 1e-9 within five
+    corrections, and every step taken from 1e-7 < rho_k <= 1e-2 lands at or
+    below 10 rho_k^2 (plus a 1e-12 floor), with at least one such step."""
     st = inputs.config_indentation(8, seed=5, step=1)
     P = binding.problem_from_state(st)
     U = torch.from_numpy(st.U.copy()).cuda()
@@ -109,10 +113,13 @@ def test_newton_converges_quadratically(binding):
         rep = P.newton_solve(U, abi.default_opts(abi.PFM_F32, max_newton=1, lin_rtol=1e-10, max_lin_it=600))
         norms.append(rep.res0)
     norms.append(rep.res_final)
-    assert norms[-1] < 1e-9 * norms[0], norms
-    # once in the basin, one correction squares the relative error
-    ratios = [norms[k + 1] / norms[k] for k in range(1, 4)]
-    assert min(ratios) < 1e-5, norms
+    rho = [x / norms[0] for x in norms]
+    print("relative Newton residuals:", " ".join(f"{r:.3e}" for r in rho))
+    assert rho[-1] < 1e-9, rho
+    basin = [k for k in range(1, len(rho) - 1) if 1e-7 < rho[k] <= 1e-2]
+    assert basin, rho
+    for k in basin:
+        assert rho[k + 1] <= 10.0 * rho[k] ** 2 + 1e-12, (k, rho)
 
 
 @pytest.mark.parametrize("prec", [abi.PFM_F32, abi.PFM_F64])

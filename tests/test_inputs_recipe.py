@@ -1,6 +1,6 @@
 """The seeded input recipes both paths read (no GPU): the indentation state
-(readings r10, r11: bottom clamped, spherical-cap u_z on the top face, one-
-signed eta noise in the admissible simplex), the parity-test states, the batch
+(bottom clamped, spherical-cap u_z on the top face, one-signed eta noise in
+the admissible simplex of Sec. 2.3), the parity-test states, the batch
 sizes and the direction vectors. The cap is checked against its closed form:
 with R = (a^2 + d^2) / (2 d) the prescribed u_z is -d at the centre and 0 on
 the rim r = a."""
@@ -22,7 +22,7 @@ def test_indentation_state(n, step):
     m = st.mesh
     x, y, z = _grid(m)
     eta = st.U[3:9]
-    assert eta.min() >= 0.0 and eta.max() < 1e-3                 # one-signed noise (reading r11)
+    assert eta.min() >= 0.0 and eta.max() < 1e-3                 # one-signed noise
     assert (1.0 - eta.sum(axis=0)).min() > 0.99                    # eta_0 >= 0: inside the simplex
     np.testing.assert_array_equal(st.Un[3:9], eta)                 # eta_n = eta
     assert not st.Un[0:3].any()

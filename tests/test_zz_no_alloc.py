@@ -66,3 +66,24 @@ def test_noalloc_rejects_grids_beyond_its_scratch(binding):
         binding.residual_noalloc(mesh, params, dummy.to(torch.uint8), dummy, dummy, dummy)
     assert exc.value.status == 1
     assert "at most" in str(exc.value)
+
+
+def test_noalloc_second_call_allocates_no_device_memory(binding):
+    """The defining property: after one warm call (which looks up the scratch
+    array's address and loads the kernels), a further call leaves the device's
+    free memory and torch's allocator exactly as they were."""
+    st = inputs.config_random(6, 5, 4, seed=73, eta_lo=-0.02, eta_hi=0.3, Lx=12.0, Ly=10.0, Lz=8.0)
+    params = abi.params_from_material(st.material, st.tau)
+    mask = torch.from_numpy(st.mask).cuda()
+    U = torch.from_numpy(st.U).cuda()
+    Un = torch.from_numpy(st.Un).cuda()
+    R = torch.empty_like(U)
+    binding.residual_noalloc(st.mesh, params, mask, U, Un, R)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    binding.residual_noalloc(st.mesh, params, mask, U, Un, R)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0

@@ -15,10 +15,13 @@ from .binding import Problem
 
 
 def load_ramp(P: Problem, state: inputs.State, upto: int, n_steps: int = 10, depth_frac: float = 0.02,
-              radius_frac: float = 0.3, opts: abi.SolveOpts | None = None, U: torch.Tensor | None = None):
+              radius_frac: float = 0.3, opts: abi.SolveOpts | None = None, U: torch.Tensor | None = None,
+              on_step=None, check: bool = True):
     """Run load steps 1..upto of a ramp of n_steps to the final cap depth
     depth_frac * L, starting from ``state`` (U and U_n on the host).
-    Returns (U on the device after the last step, list of solve reports)."""
+    ``on_step(k, mask, values, Un, U, report)``, if given, sees every step's
+    Dirichlet data, previous state and result (device tensors). Returns (U on
+    the device after the last step, list of solve reports)."""
     opts = opts or abi.default_opts(abi.PFM_F32, max_newton=12, newton_rtol=1e-8, lin_rtol=1e-8,
                                     max_lin_it=400)
     U = torch.from_numpy(state.U).cuda() if U is None else U
@@ -28,8 +31,10 @@ def load_ramp(P: Problem, state: inputs.State, upto: int, n_steps: int = 10, dep
         mask, values = inputs.indentation_dirichlet(state.mesh, k, n_steps, depth_frac, radius_frac)
         P.set_dirichlet(torch.from_numpy(mask).cuda(), torch.from_numpy(values).cuda())
         P.set_state(U, Un)
-        rep = P.newton_solve(U, opts)
+        rep = P.newton_solve(U, opts, check=check)
         reports.append(rep)
+        if on_step is not None:
+            on_step(k, mask, values, Un, U, rep)
         Un = U.clone()
         P.set_state(U, Un)
     return U, reports

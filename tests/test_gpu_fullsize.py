@@ -2,13 +2,15 @@
 (19,320,201 DOFs, 6 levels) in the launch configuration bench.py times,
 checked on sampled outputs the oracle computes one by one: each sampled node
 needs only its (at most eight) adjacent elements, each sampled element only
-its own Gauss points."""
+its own Gauss points. The Newton correction is also checked by the oracle's
+rows of K x + R over the whole cap footprint of the top element layer."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
 from oracle import fe, qp  # noqa: E402
+from oracle_pool import OraclePool  # noqa: E402
 from paper_2011_08802_gb300 import abi, inputs  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -119,10 +121,28 @@ def test_tangent_rows_fp64_and_fp32(big):
         assert np.all(np.abs(y32[:, n] - yo32)[free] <= 2e-5 * (yabs[free] + 1e-300))
 
 
+def _top_layer_box(st, x, i0, i1):
+    """The top element layer restricted to elements i, j in [i0, i1) as a
+    state of its own (node planes nz-1 and nz), with x restricted alike."""
+    m = st.mesh
+    ii, jj, kk = np.meshgrid(np.arange(i0, i1 + 1), np.arange(i0, i1 + 1), np.arange(m.nz - 1, m.nz + 1),
+                             indexing="ij")
+    nodes = (ii + (m.nx + 1) * (jj + (m.ny + 1) * kk)).transpose(2, 1, 0).reshape(-1)
+    hx, hy, hz = m.h
+    e = i1 - i0
+    sub = inputs.Mesh(e, e, 1, e * hx, e * hy, hz)
+    box = inputs.State(sub, st.U[:, nodes].copy(), st.Un[:, nodes].copy(), st.mask[:, nodes].copy(), st.tau,
+                       st.material)
+    return box, x[:, nodes].copy()
+
+
 def test_newton_correction_rows(big):
     """The mixed-precision Newton correction of the benchmark: global true
     residual (FP64 operator) below 1e-8, and the oracle's residual rows
-    K x + R at the sampled nodes below 1e-8 ||R||."""
+    K x + R below 1e-8 ||R|| at the sampled nodes and at every top-face node
+    over the cap footprint (the cap of radius 0.3 L = 38.4 elements: a box of
+    80 x 80 top-layer elements around it, rows of its 79 x 79 inner top-face
+    nodes, whose adjacent elements all lie in the box)."""
     st, P, mat = big["st"], big["P"], big["mat"]
     P.set_state(torch.from_numpy(st.U).cuda(), torch.from_numpy(st.Un).cuda())
     R = P.residual()
@@ -137,3 +157,12 @@ def test_newton_correction_rows(big):
         d = fe.qp_derivatives(disc, st, mat, order=2)
         row = fe.jvp(disc, st, xh, d)[:, n] + fe.residual(disc, st, mat, d)[:, n]
         assert np.abs(row).max() <= 1e-8 * Rn
+    i0, i1 = N // 2 - 40, N // 2 + 40
+    box, xb = _top_layer_box(st, xh, i0, i1)
+    e = i1 - i0
+    inner = [a + (e + 1) * (b + (e + 1) * 1) for b in range(1, e) for a in range(1, e)]
+    with OraclePool() as pool:
+        rows = pool.rows_Kx_plus_R(box, xb, np.arange(box.mesh.n_elems), inner)
+    worst = float(np.abs(rows).max()) / Rn
+    print(f"cap footprint: {len(inner)} top-face nodes, max |K x + R| / ||R|| = {worst:.3e}")
+    assert worst <= 1e-8

@@ -100,6 +100,14 @@ typedef struct {
   double cheb_lo, cheb_hi;  /* Chebyshev interval as fractions of lambda_max (0.05, 1.1) */
   int cycle_gamma;       /* coarse corrections per level: 1 = V-cycle, 2 = W-cycle (<= 0 read as 1) */
   double nu_growth;      /* smoothing steps on level l: round(nu * nu_growth^l) (<= 0 read as 1) */
+  int deterministic;     /* 1: run the solve as pfm_set_deterministic(h, 1) does (bitwise
+                            reproducible results); 0: the handle's setting */
+  int refine;            /* mixed precision (precond PFM_F32) only: 0 = FGMRES whose every
+                            iteration applies the FP64-class outer operator; 1 = iterative
+                            refinement: inner FGMRES solves with the FP32 operator and the FP32
+                            V-cycle, each to inner_rtol, and after each an FP64-class residual
+                            b - J x (Sec. 3.4 tolerance lin_rtol on that true residual) */
+  double inner_rtol;     /* refine = 1: relative tolerance of each inner solve (e.g. 1e-4) */
 } pfm_solve_opts;
 
 typedef struct {
@@ -108,7 +116,9 @@ typedef struct {
   int lin_its_last;      /* FGMRES iterations of the last correction */
   double res0;           /* ||R(U_0)||_2 */
   double res_final;      /* ||R(U)||_2 after the last correction */
-  double lin_res_final;  /* relative FGMRES residual estimate of the last solve */
+  double lin_res_final;  /* relative residual of the last linear solve: the FGMRES estimate, or
+                            with refine = 1 the FP64-class true residual */
+  int lin_outer_last;    /* refine = 1: refinement steps of the last linear solve (else 0) */
   double ms_residual, ms_linearize, ms_solve, ms_total; /* wall times (ms) */
   pfm_status status;
 } pfm_solve_report;
@@ -148,6 +158,20 @@ pfm_status pfm_set_power_iterations(pfm_handle* h, int iterations);
  * FP32 pipes; 12.8 ms at 128^3 on GB300), 0 = the FP64 kernel of
  * pfm_jacobian_apply (22 ms). Errors: PFM_ERR_INVALID_ARG (other values). */
 pfm_status pfm_set_outer_operator(pfm_handle* h, int double_float);
+
+/* Atomic-free, bitwise reproducible element kernels: with deterministic = 1
+ * the residual, every tangent application (FP32, FP64, binary16 and the
+ * double-float outer operator) and the dense coarse-operator assembly add
+ * their element contributions without atomics (each element writes its
+ * per-node contributions to a handle-owned scratch, then every node sums its
+ * at most 8 contributions in a fixed order; the coarse assembly runs eight
+ * element colours one after another), so that repeated calls on the same
+ * data give bitwise equal results (Sec. 3.4, the tangent of Eq. linAlgEq).
+ * Costs about one extra write and read of 9 values per element node.
+ * Penalty contact (pfm_set_contact) is not covered: calls that would apply
+ * its terms in deterministic mode return PFM_ERR_INVALID_ARG.
+ * Errors: PFM_ERR_INVALID_ARG (NULL handle, other values). */
+pfm_status pfm_set_deterministic(pfm_handle* h, int deterministic);
 
 /* Set the CUDA stream (a cudaStream_t passed as void*, owned by the caller and
  * alive while the handle uses it) for all later calls. Errors:

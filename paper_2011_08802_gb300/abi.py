@@ -50,20 +50,22 @@ class SolveOpts(C.Structure):
                 ("nu_pre", C.c_int), ("nu_post", C.c_int),
                 ("newton_rtol", C.c_double), ("lin_rtol", C.c_double), ("omega", C.c_double),
                 ("precond", C.c_int), ("smoother", C.c_int), ("cheb_lo", C.c_double),
-                ("cheb_hi", C.c_double), ("cycle_gamma", C.c_int), ("nu_growth", C.c_double)]
+                ("cheb_hi", C.c_double), ("cycle_gamma", C.c_int), ("nu_growth", C.c_double),
+                ("deterministic", C.c_int), ("refine", C.c_int), ("inner_rtol", C.c_double)]
 
 
 class SolveReport(C.Structure):
     _fields_ = [("newton_its", C.c_int), ("lin_its_total", C.c_int), ("lin_its_last", C.c_int),
                 ("res0", C.c_double), ("res_final", C.c_double), ("lin_res_final", C.c_double),
-                ("ms_residual", C.c_double), ("ms_linearize", C.c_double),
+                ("lin_outer_last", C.c_int), ("ms_residual", C.c_double), ("ms_linearize", C.c_double),
                 ("ms_solve", C.c_double), ("ms_total", C.c_double), ("status", C.c_int)]
 
 
 def default_opts(precond: int = PFM_F32, **kw) -> SolveOpts:
     o = SolveOpts(max_newton=1, restart=30, max_lin_it=300, nu_pre=2, nu_post=8,
                   newton_rtol=1e-8, lin_rtol=1e-8, omega=0.7, precond=precond,
-                  smoother=0, cheb_lo=0.05, cheb_hi=1.1, cycle_gamma=1, nu_growth=1.25)
+                  smoother=0, cheb_lo=0.05, cheb_hi=1.1, cycle_gamma=1, nu_growth=1.25,
+                  deterministic=0, refine=0, inner_rtol=1e-4)
     for k, v in kw.items():
         setattr(o, k, v)
     return o
@@ -192,6 +194,7 @@ def lib():
         "pfm_get_level": (i32, [H, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(dp)]),
         "pfm_set_power_iterations": (i32, [H, i32]),
         "pfm_set_outer_operator": (i32, [H, i32]),
+        "pfm_set_deterministic": (i32, [H, i32]),
         "pfm_set_params": (i32, [H, C.POINTER(Params)]),
         "pfm_set_dirichlet": (i32, [H, vp, vp]),
         "pfm_set_state": (i32, [H, vp, vp]),
@@ -237,7 +240,7 @@ def exported_symbols():
     """Names of the entry points declared in include/pfm.h."""
     return [
         "pfm_version", "pfm_create", "pfm_destroy", "pfm_last_error", "pfm_get_sizes",
-        "pfm_set_stream", "pfm_get_level", "pfm_set_power_iterations", "pfm_set_outer_operator", "pfm_set_params", "pfm_set_dirichlet", "pfm_set_state", "pfm_get_state",
+        "pfm_set_stream", "pfm_get_level", "pfm_set_power_iterations", "pfm_set_outer_operator", "pfm_set_deterministic", "pfm_set_params", "pfm_set_dirichlet", "pfm_set_state", "pfm_get_state",
         "pfm_residual", "pfm_diagnostics", "pfm_set_contact", "pfm_contact_load", "pfm_set_linearize_arithmetic", "pfm_set_preconditioner_store", "pfm_linearize", "pfm_jacobian_apply", "pfm_jacobian_transpose_apply",
         "pfm_jacobian_apply_host", "pfm_jacobian_apply_mixed", "pfm_vcycle", "pfm_fgmres_solve", "pfm_newton_solve",
         "pfm_qp_eval", "pfm_get_hessians", "pfm_profile_enable", "pfm_profile_get",

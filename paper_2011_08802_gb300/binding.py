@@ -99,6 +99,10 @@ class Problem:
     def set_outer_operator(self, double_float: bool):
         self._check(self._lib.pfm_set_outer_operator(self.h, int(double_float)))
 
+    def set_deterministic(self, on: bool):
+        """``pfm_set_deterministic``: atomic-free, bitwise reproducible element kernels."""
+        self._check(self._lib.pfm_set_deterministic(self.h, int(on)))
+
     def set_power_iterations(self, its: int):
         self._check(self._lib.pfm_set_power_iterations(self.h, its))
 

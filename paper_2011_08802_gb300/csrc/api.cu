@@ -59,6 +59,24 @@ void prof_collect(pfm_handle* h) {
   }
 }
 
+pfm_status bd_scratch(pfm_handle* h, size_t bytes);
+
+// Deterministic mode: make sure the scratch of the atomic-free element kernels
+// exists (9 * 32 + 1 doubles per element block of the finest level, enough for
+// every level and output type); contact terms are not covered.
+pfm_status det_ready(pfm_handle* h) {
+  if (!h->det) return PFM_OK;
+  if (h->contact_on)
+    return h->fail(PFM_ERR_INVALID_ARG, "deterministic mode does not cover penalty contact");
+  return bd_scratch(h, size_t(NF * 32 + 1) * size_t(h->L[0].nblk) * sizeof(double));
+}
+
+// Scratch of the atomic-free element kernels (after det_ready), or null.
+template <typename T>
+T* det_W(pfm_handle* h) {
+  return h->det ? static_cast<T*>(h->bd_scratch) : nullptr;
+}
+
 // Tangent application inside the preconditioner on level l: from the level's
 // store, or from its binary16 copy when that is enabled and current (FP32);
 // timed on the finest level unless `timed` is false.
@@ -69,13 +87,13 @@ void precond_apply(pfm_handle* h, size_t l, const T* x, T* y, bool timed = true)
   if constexpr (sizeof(T) == 4) {
     if (lv.H16 && lv.h16_scale > 0.f) {
       ProfScope ps(h, PFM_PROF_JAPPLY_F16, on);
-      launch_japply_h16(lv.g, h->dp, lv.H16, 1.f / lv.h16_scale, lv.mask, x, y, h->stream);
+      launch_japply_h16(lv.g, h->dp, lv.H16, 1.f / lv.h16_scale, lv.mask, x, y, h->stream, det_W<float>(h));
       if (h->contact_on) launch_contact_apply<T, T, T>(lv.g, LvVec<T>::Kc(lv), lv.mask, x, y, h->stream);
       return;
     }
   }
   ProfScope ps(h, sizeof(T) == 4 ? PFM_PROF_JAPPLY_F32 : PFM_PROF_JAPPLY_F64, on);
-  launch_japply<T>(lv.g, h->dp, LvVec<T>::H(lv), lv.mask, x, y, h->stream);
+  launch_japply<T>(lv.g, h->dp, LvVec<T>::H(lv), lv.mask, x, y, h->stream, det_W<T>(h));
   if (h->contact_on) launch_contact_apply<T, T, T>(lv.g, LvVec<T>::Kc(lv), lv.mask, x, y, h->stream);
 }
 
@@ -243,6 +261,7 @@ pfm_status estimate_lambda(pfm_handle* h, size_t l) {
 // z = M r with r, z in the preconditioner's precision (device arrays of the finest level).
 template <typename T>
 pfm_status apply_vcycle(pfm_handle* h, const T* r, T* z, const SmoothCfg& c) {
+  TRY(det_ready(h));
   TRY(ensure_level_vectors<T>(h));
   Level& f = h->L[0];
   CK(cudaMemcpyAsync(LvVec<T>::b(f), r, sizeof(T) * ndof(f), cudaMemcpyDeviceToDevice, h->stream));
@@ -261,11 +280,12 @@ pfm_status check_ready(pfm_handle* h, bool need_lin) {
 pfm_status residual_impl(pfm_handle* h, double* R, double* energy_host) {
   Level& f = h->L[0];
   cudaStream_t s = h->stream;
-  CK(cudaMemsetAsync(R, 0, sizeof(double) * ndof(f), s));
+  TRY(det_ready(h));
+  if (!h->det) CK(cudaMemsetAsync(R, 0, sizeof(double) * ndof(f), s));  // the atomic form adds into R
   CK(cudaMemsetAsync(h->energy_dev, 0, sizeof(double), s));
   {
     ProfScope ps(h, PFM_PROF_RESIDUAL);
-    launch_residual(f.g, h->dp, f.U, f.Un, f.mask, R, h->energy_dev, s);
+    launch_residual(f.g, h->dp, f.U, f.Un, f.mask, R, h->energy_dev, s, det_W<double>(h));
     if (h->contact_on) launch_contact_residual(f.g, h->contact, f.U, f.mask, R, h->energy_dev, nullptr, s);
   }
   CKL();
@@ -306,6 +326,7 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
     cudaGraphExecDestroy(h->vgraph);
     h->vgraph = nullptr;
   }
+  TRY(det_ready(h));
   const size_t nl = h->L.size();
   for (size_t l = 1; l < nl; ++l) {
     launch_inject_state(h->L[l - 1].g, h->L[l].g, h->L[l - 1].U, h->L[l].U, s);
@@ -370,7 +391,7 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
     }
   }
   Level& c = h->L[nl - 1];
-  launch_coarse_assemble<double>(c.g, h->dp, c.H64, c.mask, h->Kaug, 2 * h->nc_dofs, s);
+  launch_coarse_assemble<double>(c.g, h->dp, c.H64, c.mask, h->Kaug, 2 * h->nc_dofs, s, h->det);
   if (h->contact_on) launch_contact_coarse(c.g, c.Kc64, c.mask, h->Kaug, 2 * h->nc_dofs, s);
   dense_gauss_jordan_inverse(h->Kaug, h->nc_dofs, h->Kinv, h->gj_keys, h->gj_used, h->gj_piv, h->flag_dev, s);
   CKL();
@@ -389,6 +410,7 @@ pfm_status japply_impl(pfm_handle* h, const T* v, T* y) {
   const T* H = LvVec<T>::H(f);
   if (!H || (sizeof(T) == 4 && h->lin_prec != PFM_F32))
     return h->fail(PFM_ERR_STATE, "no tangent in the requested precision (linearize with PFM_F32 for FP32)");
+  TRY(det_ready(h));
   precond_apply<T>(h, 0, v, y);
   CKL();
   return PFM_OK;
@@ -411,6 +433,10 @@ struct Fgm {
   double beta0 = 0.0, beta = 0.0, tol = 0.0, relres = 1.0;
   int total = 0, j = 0;
   bool done = false, converged = false;
+  // inner solve of iterative refinement: FP32 operator, one cycle, stop at
+  // max(inner_rtol ||b||, tol_floor)
+  bool inner = false;
+  double tol_floor = 0.0;
   pfm_status status = PFM_OK;
   std::vector<double> Hh, cs, sn, g;
 };
@@ -460,6 +486,7 @@ pfm_status fgm_begin_enqueue(pfm_handle* h, Fgm& F, const pfm_solve_opts& o, con
     return h->fail(PFM_ERR_STATE, "FP32 preconditioner requested but the tangent was built for FP64");
   if (F.mixed && h->outer_df && (!h->L[0].H32 || !h->L[0].H32lo))
     return h->fail(PFM_ERR_STATE, "the double-float outer operator has no FP32 Hessian pair");
+  TRY(det_ready(h));
   TRY(fgm_alloc(h, F));
   F.Hh.assign(size_t(F.m + 1) * F.m, 0.0);
   F.cs.assign(F.m, 0.0);
@@ -500,7 +527,7 @@ pfm_status fgm_begin_finish(pfm_handle* h, Fgm& F) {
     F.relres = 0.0;
     return PFM_OK;
   }
-  F.tol = F.o.lin_rtol * F.beta0;
+  F.tol = F.inner ? std::max(F.o.inner_rtol * F.beta0, F.tol_floor) : F.o.lin_rtol * F.beta0;
   F.beta = F.beta0;
   return fgm_start_cycle(h, F);
 }
@@ -527,10 +554,18 @@ pfm_status fgm_enqueue(pfm_handle* h, Fgm& F) {
     }
     CK(cudaMemcpyAsync(zj, fl.x32, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
     // w = J z_j with the FP64-accurate operator: either the FP64 kernel or,
-    // since z_j is exactly FP32, the double-float kernel on the FP32 pipes
-    if (h->outer_df) {
+    // since z_j is exactly FP32, the double-float kernel on the FP32 pipes;
+    // inside iterative refinement the FP32 operator of the FP32 store
+    if (F.inner) {
+      {
+        ProfScope ps(h, PFM_PROF_JAPPLY_F32);
+        launch_japply<float>(fl.g, h->dp, fl.H32, fl.mask, zj, fl.y32, s, det_W<float>(h));
+        if (h->contact_on) launch_contact_apply<float, float, float>(fl.g, fl.Kc32, fl.mask, zj, fl.y32, s);
+      }
+      launch_cast_f2d(n, fl.y32, h->wv, s);
+    } else if (h->outer_df) {
       ProfScope ps(h, PFM_PROF_JAPPLY_F64);
-      launch_japply_df(fl.g, h->dp, fl.H32, fl.H32lo, fl.mask, zj, h->wv, s);
+      launch_japply_df(fl.g, h->dp, fl.H32, fl.H32lo, fl.mask, zj, h->wv, s, det_W<double>(h));
       if (h->contact_on) launch_contact_apply<double, float, double>(fl.g, fl.Kc64, fl.mask, zj, h->wv, s);
     } else {
       launch_cast_f2d(n, zj, h->zd, s);
@@ -635,6 +670,10 @@ pfm_status fgm_finish(pfm_handle* h, Fgm& F) {
     F.done = F.converged = true;
     return PFM_OK;
   }
+  if (F.inner) {  // one cycle: the refinement step computes the true residual
+    F.done = true;
+    return PFM_OK;
+  }
   // restart from the true residual r = b - J x
   TRY(japply_impl<double>(h, F.x, h->wv));
   launch_sub<double>(n, F.b, h->wv, h->rv, s);
@@ -669,6 +708,116 @@ pfm_status fgmres_impl(pfm_handle* h, const pfm_solve_opts& o, const double* b, 
   return st;
 }
 
+// y = J x for an FP64 x with FP64-class accuracy: x = x_hi + x_lo (two FP32
+// vectors), J x_hi by the double-float operator and J x_lo (2^-24 smaller) by
+// the FP32 operator, r = b - J x_hi - J x_lo; or with the FP64 kernel when
+// the outer operator is FP64.
+pfm_status true_residual(pfm_handle* h, const double* b, const double* x, double* r) {
+  Level& fl = h->L[0];
+  cudaStream_t s = h->stream;
+  const int64_t n = ndof(fl);
+  if (!h->outer_df) {
+    TRY(japply_impl<double>(h, x, h->wv));
+    launch_sub<double>(n, b, h->wv, r, s);
+    CKL();
+    return PFM_OK;
+  }
+  float* xhi = fl.x32;
+  float* xlo = fl.r32;
+  launch_split_f64(n, x, xhi, xlo, s);
+  {
+    ProfScope ps(h, PFM_PROF_JAPPLY_F64);
+    launch_japply_df(fl.g, h->dp, fl.H32, fl.H32lo, fl.mask, xhi, h->wv, s, det_W<double>(h));
+    if (h->contact_on) launch_contact_apply<double, float, double>(fl.g, fl.Kc64, fl.mask, xhi, h->wv, s);
+  }
+  launch_japply<float>(fl.g, h->dp, fl.H32, fl.mask, xlo, fl.y32, s, det_W<float>(h));
+  if (h->contact_on) launch_contact_apply<float, float, float>(fl.g, fl.Kc32, fl.mask, xlo, fl.y32, s);
+  launch_sub2(n, b, h->wv, fl.y32, r, s);
+  CKL();
+  return PFM_OK;
+}
+
+// Mixed-precision iterative refinement (GMRES-IR of Carson and Higham, 2018)
+// for J x = b, x0 = 0: each step solves J d = r approximately with one cycle
+// of FGMRES(m) whose operator is the FP32 tangent (and whose preconditioner is
+// the FP32 V-cycle), to max(inner_rtol ||r||, 0.3 lin_rtol ||b||), then
+// x += d and r = b - J x with the FP64-class operator, until ||r|| <=
+// lin_rtol ||b|| (the true residual, Sec. 3.4) or max_lin_it inner iterations.
+pfm_status refine_impl(pfm_handle* h, const pfm_solve_opts& o, const double* b, double* x, int* its_out,
+                       double* relres_out, int* outer_out) {
+  Level& fl = h->L[0];
+  cudaStream_t s = h->stream;
+  const int64_t n = ndof(fl);
+  if (h->lin_prec != PFM_F32 || !fl.H32 || (h->outer_df && !fl.H32lo))
+    return h->fail(PFM_ERR_STATE, "iterative refinement needs a tangent built with pfm_linearize(PFM_F32)");
+  TRY(det_ready(h));
+  TRY(ensure_level_vectors<float>(h));
+  TRY(dalloc(h, &h->ir_r, n));
+  TRY(dalloc(h, &h->ir_d, n));
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  double beta0 = 0.0;
+  TRY(norm2(h, b, n, &beta0));
+  int total = 0, outer = 0;
+  double rel = 1.0;
+  pfm_status st = PFM_OK;
+  if (!std::isfinite(beta0)) {
+    st = h->fail(PFM_ERR_NONFINITE, "non-finite right-hand side");
+  } else if (beta0 == 0.0) {
+    rel = 0.0;
+  } else {
+    const double tol = o.lin_rtol * beta0;
+    const double* r = b;  // r_0 = b - J 0
+    for (;;) {
+      Fgm F;
+      pfm_solve_opts oi = o;
+      oi.max_lin_it = o.max_lin_it - total;
+      TRY(fgm_begin_enqueue(h, F, oi, r, h->ir_d));
+      F.inner = true;
+      F.tol_floor = 0.3 * tol;
+      CK(cudaStreamSynchronize(s));
+      st = fgm_begin_finish(h, F);
+      while (st == PFM_OK && !F.done) {
+        st = fgm_enqueue(h, F);
+        if (st != PFM_OK) break;
+        CK(cudaStreamSynchronize(s));
+        st = fgm_finish(h, F);
+      }
+      total += F.total;
+      ++outer;
+      if (st != PFM_OK) break;
+      launch_axpy(n, 1.0, h->ir_d, x, s);
+      CKL();
+      TRY(true_residual(h, b, x, h->ir_r));
+      r = h->ir_r;
+      double rn = 0.0;
+      TRY(norm2(h, r, n, &rn));
+      rel = rn / beta0;
+      if (!std::isfinite(rn)) {
+        st = h->fail(PFM_ERR_NONFINITE, "non-finite residual in iterative refinement");
+        break;
+      }
+      if (rn <= tol) break;
+      if (total >= o.max_lin_it) {
+        st = h->fail(PFM_ERR_NOT_CONVERGED,
+                     "iterative refinement reached max_lin_it at relative residual " + std::to_string(rel));
+        break;
+      }
+    }
+  }
+  if (its_out) *its_out = total;
+  if (relres_out) *relres_out = rel;
+  if (outer_out) *outer_out = outer;
+  return st;
+}
+
+// Linear solve of the Newton step with the options' method.
+pfm_status linear_solve(pfm_handle* h, const pfm_solve_opts& o, const double* b, double* x, int* its_out,
+                        double* relres_out, int* outer_out) {
+  if (o.refine && o.precond == PFM_F32) return refine_impl(h, o, b, x, its_out, relres_out, outer_out);
+  if (outer_out) *outer_out = 0;
+  return fgmres_impl(h, o, b, x, its_out, relres_out);
+}
+
 // Capture the V-cycle on the handle's stream into a CUDA graph (once per
 // linearisation and smoother configuration) so that a batch replays it with
 // one launch per problem and iteration.
@@ -678,7 +827,7 @@ pfm_status capture_vcycle(pfm_handle* h, const SmoothCfg& sc) {
   if (h->vgraph && h->vgraph_prec == key_prec && h->vgraph_cfg.nu_pre == sc.nu_pre &&
       h->vgraph_cfg.nu_post == sc.nu_post && h->vgraph_cfg.type == sc.type && h->vgraph_cfg.omega == sc.omega &&
       h->vgraph_cfg.lo == sc.lo && h->vgraph_cfg.hi == sc.hi && h->vgraph_cfg.gamma == sc.gamma &&
-      h->vgraph_cfg.growth == sc.growth)
+      h->vgraph_cfg.growth == sc.growth && h->vgraph_cfg.det == h->det)
     return PFM_OK;
   if (h->vgraph) {
     cudaGraphExecDestroy(h->vgraph);
@@ -703,15 +852,33 @@ pfm_status capture_vcycle(pfm_handle* h, const SmoothCfg& sc) {
     return h->fail(PFM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   }
   h->vgraph_prec = key_prec;
-  h->vgraph_cfg = {sc.nu_pre, sc.nu_post, sc.type, sc.omega, sc.lo, sc.hi, sc.gamma, sc.growth};
+  h->vgraph_cfg = {sc.nu_pre, sc.nu_post, sc.type, sc.omega, sc.lo, sc.hi, sc.gamma, sc.growth, h->det};
   return PFM_OK;
 }
+
+// opts.deterministic switches the handle's deterministic mode on for one solve
+// (a Newton solve linearises inside it, so its coarse operator is assembled
+// in the reproducible form too).
+struct DetScope {
+  pfm_handle* h;
+  bool saved;
+  DetScope(pfm_handle* h_, const pfm_solve_opts& o) : h(h_), saved(h_->det) {
+    if (o.deterministic) h->det = true;
+  }
+  ~DetScope() {
+    if (h) h->det = saved;
+  }
+  DetScope(const DetScope&) = delete;
+  DetScope& operator=(const DetScope&) = delete;
+  DetScope(DetScope&& o) noexcept : h(o.h), saved(o.saved) { o.h = nullptr; }
+};
 
 bool opts_valid(const pfm_solve_opts& o) {
   return o.restart >= 1 && o.restart <= MAX_RESTART && o.max_lin_it >= 1 && o.nu_pre >= 1 &&
          o.nu_post >= 0 && o.max_newton >= 1 && o.lin_rtol > 0 && o.omega > 0 &&
          (o.precond == PFM_F32 || o.precond == PFM_F64) && (o.smoother == 0 || o.smoother == 1) &&
-         o.cheb_lo > 0 && o.cheb_hi > o.cheb_lo;
+         o.cheb_lo > 0 && o.cheb_hi > o.cheb_lo && (o.deterministic == 0 || o.deterministic == 1) &&
+         (o.refine == 0 || (o.refine == 1 && o.inner_rtol > 0 && o.inner_rtol < 1));
 }
 
 }  // namespace
@@ -885,7 +1052,7 @@ void pfm_destroy(pfm_handle* h) {
     dfree(lv.r32); dfree(lv.d32); dfree(lv.r64); dfree(lv.d64); dfree(lv.Kc64); dfree(lv.Kc32);
   }
   dfree(h->dirval); dfree(h->energy_dev); dfree(h->flag_dev); dfree(h->diag_part); dfree(h->load_dev); dfree(h->R); dfree(h->dU); dfree(h->wv);
-  dfree(h->rv); dfree(h->zd); dfree(h->partial); dfree(h->hdev); dfree(h->V); dfree(h->Kaug); dfree(h->Kinv);
+  dfree(h->rv); dfree(h->zd); dfree(h->ir_r); dfree(h->ir_d); dfree(h->partial); dfree(h->hdev); dfree(h->V); dfree(h->Kaug); dfree(h->Kinv);
   dfree(h->gj_keys); dfree(h->gj_used); dfree(h->gj_piv); dfree(h->amax_dev);
   if (h->Z) cudaFree(h->Z);
   if (h->vgraph) cudaGraphExecDestroy(h->vgraph);
@@ -928,6 +1095,14 @@ pfm_status pfm_get_level(const pfm_handle* h, int level, int* nx, int* ny, int* 
 pfm_status pfm_set_outer_operator(pfm_handle* h, int double_float) {
   if (!h) return PFM_ERR_INVALID_ARG;
   h->outer_df = double_float != 0;
+  return PFM_OK;
+}
+
+pfm_status pfm_set_deterministic(pfm_handle* h, int deterministic) {
+  if (!h) return PFM_ERR_INVALID_ARG;
+  if (deterministic != 0 && deterministic != 1) return h->fail(PFM_ERR_INVALID_ARG, "expected 0 or 1");
+  h->det = deterministic != 0;
+  h->linearized = false;  // the coarse operator is assembled in the chosen form
   return PFM_OK;
 }
 
@@ -1107,9 +1282,10 @@ pfm_status pfm_jacobian_apply_mixed(pfm_handle* h, const float* v_dev, double* y
   Level& f = h->L[0];
   if (h->lin_prec != PFM_F32 || !f.H32 || !f.H32lo)
     return h->fail(PFM_ERR_STATE, "the mixed product needs a tangent built with pfm_linearize(PFM_F32)");
+  TRY(det_ready(h));
   {
     ProfScope ps(h, PFM_PROF_JAPPLY_F64);
-    launch_japply_df(f.g, h->dp, f.H32, f.H32lo, f.mask, v_dev, y_dev, h->stream);
+    launch_japply_df(f.g, h->dp, f.H32, f.H32lo, f.mask, v_dev, y_dev, h->stream, det_W<double>(h));
     if (h->contact_on)
       launch_contact_apply<double, float, double>(f.g, f.Kc64, f.mask, static_cast<const float*>(v_dev),
                                                   static_cast<double*>(y_dev), h->stream);
@@ -1130,7 +1306,7 @@ pfm_status pfm_jacobian_apply_host(pfm_handle* h, const void* v_host, void* y_ho
     h->stage_in = a;
     h->stage_out = b;
   }
-  if (!h->contact_on && (prec == PFM_F32 || prec == PFM_F64)) {
+  if (!h->contact_on && !h->det && (prec == PFM_F32 || prec == PFM_F64)) {
     if (prec == PFM_F32) return japply_host_pipelined<float>(h, v_host, y_host);
     return japply_host_pipelined<double>(h, v_host, y_host);
   }
@@ -1159,8 +1335,11 @@ pfm_status pfm_fgmres_solve(pfm_handle* h, const pfm_solve_opts* opts, const dou
   int its = 0;
   double rel = 0.0;
   double t0 = now_ms();
-  pfm_status st = fgmres_impl(h, *opts, b_dev, x_dev, &its, &rel);
+  DetScope ds(h, *opts);
+  int outer = 0;
+  pfm_status st = linear_solve(h, *opts, b_dev, x_dev, &its, &rel, &outer);
   if (report) {
+    report->lin_outer_last = outer;
     report->lin_its_last = its;
     report->lin_its_total = its;
     report->lin_res_final = rel;
@@ -1179,6 +1358,7 @@ pfm_status pfm_newton_solve(pfm_handle* h, const pfm_solve_opts* opts, double* U
   const int64_t n = ndof(f);
   pfm_solve_report rep{};
   const double t_start = now_ms();
+  DetScope ds(h, *opts);
   CK(cudaMemcpyAsync(f.U, U_inout_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   if (h->have_dirval) launch_mask_values(f.nn, f.mask, h->dirval, f.U, s);
   h->linearized = false;
@@ -1201,7 +1381,9 @@ pfm_status pfm_newton_solve(pfm_handle* h, const pfm_solve_opts* opts, double* U
     int its = 0;
     double rel = 0.0;
     launch_axpy(n, -2.0, h->R, h->R, s);
-    st = fgmres_impl(h, *opts, h->R, h->dU, &its, &rel);
+    int outer = 0;
+    st = linear_solve(h, *opts, h->R, h->dU, &its, &rel, &outer);
+    rep.lin_outer_last = outer;
     rep.ms_solve += now_ms() - t0;
     rep.lin_its_total += its;
     rep.lin_its_last = its;
@@ -1277,7 +1459,8 @@ pfm_status pfm_param_grad(pfm_handle* h, const double* w_dev, double* dPi, doubl
     if (dR_dev) Rk = dR_dev + int64_t(k) * n;
     CK(cudaMemsetAsync(Rk, 0, sizeof(double) * n, s));
     CK(cudaMemsetAsync(h->energy_dev, 0, sizeof(double), s));
-    launch_residual(f.g, dq, f.U, f.Un, f.mask, Rk, h->energy_dev, s);
+    TRY(det_ready(h));
+    launch_residual(f.g, dq, f.U, f.Un, f.mask, Rk, h->energy_dev, s, det_W<double>(h));
     CKL();
     double e = 0.0;
     CK(cudaMemcpyAsync(&e, h->energy_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1433,6 +1616,8 @@ pfm_status pfm_batch_newton_solve(pfm_batch* b, const pfm_solve_opts* opts, doub
   }
   if (b->mode == 0 && batch_engine_supports(*opts, b)) return batch_engine_newton(b, *opts, U_inout, reports);
   std::vector<cudaStream_t> saved(N);
+  std::vector<DetScope> dets;
+  dets.reserve(N);
   for (int p = 0; p < N; ++p) {
     pfm_handle* h = b->hs[p];
     if (!h->have_state) return b->fail(PFM_ERR_STATE, "problem " + std::to_string(p) + " has no U_n");
@@ -1440,6 +1625,7 @@ pfm_status pfm_batch_newton_solve(pfm_batch* b, const pfm_solve_opts* opts, doub
     saved[p] = h->stream;
     h->stream = b->streams[p];
     h->use_graphs = true;
+    dets.emplace_back(h, *opts);
   }
   std::vector<pfm_solve_report> rep(N);
   std::vector<double> res(N, 0.0);

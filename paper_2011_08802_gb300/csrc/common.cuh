@@ -50,23 +50,28 @@ namespace pfm {
 void count_launches(int n);
 
 // element kernels (fe_kernels.cu)
+// The element kernels below take an optional scratch W: null = element
+// contributions added with atomics (rounding order varies between runs);
+// non-null = the atomic-free two-pass form (per-(element, node) contributions
+// in W, summed per node in a fixed order; bitwise reproducible). W holds
+// 9 * 32 * nblk entries of the output type (+ nblk for the residual's energy).
 void launch_residual(const Grid& g, const DevParams& P, const double* U, const double* Un,
-                     const dmask_t* mask, double* R, double* energy, cudaStream_t s);
+                     const dmask_t* mask, double* R, double* energy, cudaStream_t s, double* W = nullptr);
 // arithmetic of the point physics in the linearisation
 enum { LIN_F64 = 0, LIN_F32 = 1, LIN_DF = 2 };
 void launch_linearize(const Grid& g, const DevParams& P, const double* U, const double* Un,
                       double* H64, float* H32, float* H32lo, int arith, cudaStream_t s);
 void launch_japply_df(const Grid& g, const DevParams& P, const float* Hhi, const float* Hlo, const dmask_t* mask,
-                      const float* v, double* y, cudaStream_t s);
+                      const float* v, double* y, cudaStream_t s, double* W = nullptr);
 template <typename T>
 void launch_japply(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, const T* v,
-                   T* y, cudaStream_t s);
+                   T* y, cudaStream_t s, T* W = nullptr);
 // y = J v from a binary16 copy of the FP32 store holding s H (FP32 arithmetic;
 // inv_scale = 1/s), and the conversion that makes that copy: returns s, a
 // power of two putting max |H| in [2^14, 2^15), or 0 on failure (scratch: one
 // device word).
 void launch_japply_h16(const Grid& g, const DevParams& P, const __half* H, float inv_scale, const dmask_t* mask,
-                       const float* v, float* y, cudaStream_t s);
+                       const float* v, float* y, cudaStream_t s, float* W = nullptr);
 float launch_store_to_half(const Grid& g, const float* H32, __half* H16, unsigned* scratch, cudaStream_t s);
 // element blocks [b0, b1) only, on at most `blocks` CTAs (slab pipeline)
 template <typename T>
@@ -98,9 +103,10 @@ template <typename T>
 void launch_smooth(int64_t nn, const T* D, const T* b, const T* y, T omega, T* x, cudaStream_t s);
 template <typename T>
 void launch_sub(int64_t n, const T* b, const T* y, T* r, cudaStream_t s);
+// det: eight element colours one after another, no atomics (bitwise reproducible)
 template <typename T>
 void launch_coarse_assemble(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask,
-                            double* K, int ld, cudaStream_t s);
+                            double* K, int ld, cudaStream_t s, bool det = false);
 template <typename T>
 void launch_cheb_first(int64_t nn, const T* D, const T* src, T c, bool copy_r, bool zero_x, T* r, T* d, T* x,
                        cudaStream_t s);
@@ -142,6 +148,9 @@ template <typename T>
 void launch_fill(int64_t n, T val, T* x, cudaStream_t s);
 void launch_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t s);
 void launch_cast_f2d(int64_t n, const float* a, double* b, cudaStream_t s);
+// x = hi + lo as two FP32 vectors; r = b - a - c
+void launch_split_f64(int64_t n, const double* x, float* hi, float* lo, cudaStream_t s);
+void launch_sub2(int64_t n, const double* b, const double* a, const float* c, double* r, cudaStream_t s);
 void launch_mdot(int64_t n, int k, const double* V, int64_t ldv, const double* w, double* partial,
                  double* out, cudaStream_t s);
 template <typename T>

@@ -323,15 +323,31 @@ inline JParams<T> make_jparams(const Grid& g, const DevParams& P) {
   return jp;
 }
 
+// Nodal result r of this lane (element e = 4 blk + lane/8, local node
+// lane%8) for DOF row idx = f nn + node: added to y with an atomic (DET
+// false), or (DET true, atomic-free) stored to the per-(element, node)
+// scratch W[f ws + 32 blk + lane], 0 where the row is skipped; a node pass
+// then sums each node's contributions in a fixed order.
+template <bool DET, typename TY, typename TW, typename TR>
+__device__ __forceinline__ void scatter_row(TY* __restrict__ y, TW* __restrict__ W, int64_t ws, int f, int64_t blk,
+                                            int lane, int64_t idx, TR r, bool on) {
+  if constexpr (DET) {
+    W[f * ws + blk * 32 + lane] = on ? TW(r) : TW(0);
+  } else {
+    if (on) atomicAdd(&y[idx], TY(r));
+  }
+}
+
 // ---- BEGIN tangent application kernel
 // y += J v on the 4 elements of block blk (this warp; lane = 0..31): gather v
 // at the element nodes (Dirichlet DOFs read as 0), dz = (grad du, d eta_hat)
 // at the Gauss points, sigma = H dz from the packed symmetric store, plus the
 // constant gradient-energy term, scattered back with atomics.
-template <typename T>
+template <typename T, bool DET = false>
 __device__ __forceinline__ void japply_block(const Grid& g, const JParams<T>& jp, const T* __restrict__ H,
                                              const dmask_t* __restrict__ mask, const T* __restrict__ v,
-                                             T* __restrict__ y, int64_t blk, int lane) {
+                                             T* __restrict__ y, int64_t blk, int lane, T* __restrict__ W = nullptr,
+                                             int64_t ws = 0) {
   constexpr int V = 16 / sizeof(T);
   using VT = typename Vec16<T>::type;
   const int l8 = lane & 7;
@@ -375,7 +391,7 @@ __device__ __forceinline__ void japply_block(const Grid& g, const JParams<T>& jp
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     T r = q1_scatter_grad(w * sg[3 * i], w * sg[3 * i + 1], w * sg[3 * i + 2], l8, jp.ihx, jp.ihy, jp.ihz);
-    if (valid && !((dm >> i) & 1)) atomicAdd(&y[i * nn + node], r);
+    scatter_row<DET>(y, W, ws, i, blk, lane, i * nn + node, r, valid && !((dm >> i) & 1));
   }
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
@@ -388,7 +404,7 @@ __device__ __forceinline__ void japply_block(const Grid& g, const JParams<T>& jp
       gf[d] = w * s;
     }
     T r = q1_scatter(w * sg[9 + k], gf[0], gf[1], gf[2], l8, jp.ihx, jp.ihy, jp.ihz);
-    if (valid && !((dm >> (3 + k)) & 1)) atomicAdd(&y[(3 + k) * nn + node], r);
+    scatter_row<DET>(y, W, ws, 3 + k, blk, lane, (3 + k) * nn + node, r, valid && !((dm >> (3 + k)) & 1));
   }
 }
 // ---- END tangent application kernel
@@ -397,10 +413,11 @@ __device__ __forceinline__ void japply_block(const Grid& g, const JParams<T>& jp
 // s H (FP32 arithmetic): the same gather, contraction and scatter as
 // japply_block, with the Hessian part weighted by wh = w / s. The FP32 and
 // FP64 applications keep their own body above.
+template <bool DET = false>
 __device__ __forceinline__ void japply_block_h16(const Grid& g, const JParams<float>& jp, float wh,
                                                  const __half* __restrict__ H, const dmask_t* __restrict__ mask,
                                                  const float* __restrict__ v, float* __restrict__ y, int64_t blk,
-                                                 int lane) {
+                                                 int lane, float* __restrict__ W = nullptr, int64_t ws = 0) {
   constexpr int V = 8;
   const int l8 = lane & 7;
   const int64_t nn = g.nn();
@@ -441,7 +458,7 @@ __device__ __forceinline__ void japply_block_h16(const Grid& g, const JParams<fl
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     float r = q1_scatter_grad(wh * sg[3 * i], wh * sg[3 * i + 1], wh * sg[3 * i + 2], l8, jp.ihx, jp.ihy, jp.ihz);
-    if (valid && !((dm >> i) & 1)) atomicAdd(&y[i * nn + node], r);
+    scatter_row<DET>(y, W, ws, i, blk, lane, i * nn + node, r, valid && !((dm >> i) & 1));
   }
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
@@ -454,7 +471,7 @@ __device__ __forceinline__ void japply_block_h16(const Grid& g, const JParams<fl
       gf[d] = w * s;
     }
     float r = q1_scatter(wh * sg[9 + k], gf[0], gf[1], gf[2], l8, jp.ihx, jp.ihy, jp.ihz);
-    if (valid && !((dm >> (3 + k)) & 1)) atomicAdd(&y[(3 + k) * nn + node], r);
+    scatter_row<DET>(y, W, ws, 3 + k, blk, lane, (3 + k) * nn + node, r, valid && !((dm >> (3 + k)) & 1));
   }
 }
 
@@ -578,10 +595,11 @@ __device__ __forceinline__ dfl cacc_value(const cacc& a) { return df_two_sum(a.s
 // y += J v on element block blk in double-float arithmetic: v in FP32
 // (exact input), the tangent as Hhi + Hlo (two FP32 stores of the FP64
 // Hessians), element contributions added to the FP64 output y.
+template <bool DET = false>
 __device__ __forceinline__ void japply_df_block(const Grid& g, const DfConst& k, const float* __restrict__ Hhi,
                                                 const float* __restrict__ Hlo, const dmask_t* __restrict__ mask,
                                                 const float* __restrict__ v, double* __restrict__ y, int64_t blk,
-                                                int lane) {
+                                                int lane, double* __restrict__ W = nullptr, int64_t ws = 0) {
   const int l8 = lane & 7;
   const int64_t nn = g.nn();
   const int64_t e = blk * 4 + (lane >> 3);
@@ -626,7 +644,7 @@ __device__ __forceinline__ void japply_df_block(const Grid& g, const DfConst& k,
   for (int i = 0; i < 3; ++i) {
     dfl r = q1_scatter_df(dfl{0.f, 0.f}, df_mul(k.w, sg[3 * i]), df_mul(k.w, sg[3 * i + 1]),
                           df_mul(k.w, sg[3 * i + 2]), false, l8, k);
-    if (valid && !((dm >> i) & 1)) atomicAdd(&y[i * nn + node], double(r.hi) + double(r.lo));
+    scatter_row<DET>(y, W, ws, i, blk, lane, i * nn + node, double(r.hi) + double(r.lo), valid && !((dm >> i) & 1));
   }
 #pragma unroll
   for (int kk = 0; kk < 6; ++kk) {
@@ -639,7 +657,51 @@ __device__ __forceinline__ void japply_df_block(const Grid& g, const DfConst& k,
       gf[d] = df_mul(k.w, cacc_value(s));
     }
     dfl r = q1_scatter_df(df_mul(k.w, sg[9 + kk]), gf[0], gf[1], gf[2], true, l8, k);
-    if (valid && !((dm >> (3 + kk)) & 1)) atomicAdd(&y[(3 + kk) * nn + node], double(r.hi) + double(r.lo));
+    scatter_row<DET>(y, W, ws, 3 + kk, blk, lane, (3 + kk) * nn + node, double(r.hi) + double(r.lo),
+                     valid && !((dm >> (3 + kk)) & 1));
+  }
+}
+
+// Node pass of the atomic-free scatter: node n of grid g sums, for every
+// field f, the contributions W[f ws + 32 (e/4) + 8 (e%4) + a] of its (up to 8)
+// adjacent elements e (local node a) in a fixed order (z, then y, then x),
+// and writes y[f nn + n]; a Dirichlet row gets v[f nn + n] (identity row of
+// the tangent) or 0 when v is null (residual).
+template <typename TW, typename TV, typename TY>
+__device__ __forceinline__ void node_gather(const Grid& g, const TW* __restrict__ W, int64_t ws,
+                                            const dmask_t* __restrict__ mask, const TV* __restrict__ v,
+                                            TY* __restrict__ y, int64_t n) {
+  const int64_t nn = g.nn();
+  const int i = int(n % (g.nx + 1));
+  const int j = int((n / (g.nx + 1)) % (g.ny + 1));
+  const int k = int(n / (int64_t(g.nx + 1) * (g.ny + 1)));
+  int64_t col[8];
+  int cnt = 0;
+  for (int dk = 0; dk < 2; ++dk) {
+    const int ek = k - 1 + dk;
+    if (ek < 0 || ek >= g.nz) continue;
+    for (int dj = 0; dj < 2; ++dj) {
+      const int ej = j - 1 + dj;
+      if (ej < 0 || ej >= g.ny) continue;
+      for (int di = 0; di < 2; ++di) {
+        const int ei = i - 1 + di;
+        if (ei < 0 || ei >= g.nx) continue;
+        const int64_t e = ei + int64_t(g.nx) * (ej + int64_t(g.ny) * ek);
+        const int a = (1 - di) + 2 * (1 - dj) + 4 * (1 - dk);
+        col[cnt++] = (e >> 2) * 32 + (e & 3) * 8 + a;
+      }
+    }
+  }
+  const dmask_t dm = mask[n];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    if ((dm >> f) & 1) {
+      y[f * nn + n] = v ? TY(v[f * nn + n]) : TY(0);
+      continue;
+    }
+    TW s = TW(0);
+    for (int c = 0; c < cnt; ++c) s += W[f * ws + col[c]];
+    y[f * nn + n] = TY(s);
   }
 }
 

@@ -24,13 +24,20 @@ namespace pfm {
 namespace {
 
 // ---------------------------------------------------------------------------
+// Residual (and energy) of the elements; DET: atomic-free, the nodal results
+// go to the scratch W (node_gather adds them up) and each warp's energy to
+// W[9 ws + blk] (summed in a fixed order by k_sum_fixed).
+template <bool DET>
 __global__ void __launch_bounds__(128) k_residual(Grid g, DevParams P, const double* __restrict__ U,
                                                   const double* __restrict__ Un,
                                                   const dmask_t* __restrict__ mask,
-                                                  double* __restrict__ R, double* energy) {
+                                                  double* __restrict__ R, double* energy, double* __restrict__ W,
+                                                  int64_t ws) {
   const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t e = tid >> 3;
   const int l8 = int(tid & 7);
+  const int64_t blk = tid >> 5;
+  const int lane = int(tid & 31);
   const bool valid = e < g.ne();
   const int64_t nn = g.nn();
   const int64_t node = valid ? elem_node(g, e, l8) : 0;
@@ -39,8 +46,8 @@ __global__ void __launch_bounds__(128) k_residual(Grid g, DevParams P, const dou
   gather_state<double>(U, nn, node, valid, l8, ihx, ihy, ihz, F, eh, ge);
 #pragma unroll
   for (int k = 0; k < 6; ++k) ehn[k] = q1_value(valid ? Un[(3 + k) * nn + node] : 0.0);
-  double W, gr[NZ];
-  qp_local<double, false>(P, F, eh, ehn, &W, gr, nullptr);
+  double Wd, gr[NZ];
+  qp_local<double, false>(P, F, eh, ehn, &Wd, gr, nullptr);
   double gf[18];
   double Wg = 0.0;
 #pragma unroll
@@ -58,18 +65,47 @@ __global__ void __launch_bounds__(128) k_residual(Grid g, DevParams P, const dou
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     double r = q1_scatter_grad(w * gr[3 * i], w * gr[3 * i + 1], w * gr[3 * i + 2], l8, ihx, ihy, ihz);
-    if (valid && !((dm >> i) & 1)) atomicAdd(&R[i * nn + node], r);
+    scatter_row<DET>(R, W, ws, i, blk, lane, i * nn + node, r, valid && !((dm >> i) & 1));
   }
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     double r = q1_scatter(w * gr[9 + k], w * gf[3 * k], w * gf[3 * k + 1], w * gf[3 * k + 2], l8, ihx,
                           ihy, ihz);
-    if (valid && !((dm >> (3 + k)) & 1)) atomicAdd(&R[(3 + k) * nn + node], r);
+    scatter_row<DET>(R, W, ws, 3 + k, blk, lane, (3 + k) * nn + node, r, valid && !((dm >> (3 + k)) & 1));
   }
   if (energy) {
-    double en = warp_sum(valid ? w * (W + Wg) : 0.0);
-    if ((threadIdx.x & 31) == 0) atomicAdd(energy, en);
+    double en = warp_sum(valid ? w * (Wd + Wg) : 0.0);
+    if constexpr (DET) {
+      if (lane == 0) W[NF * ws + blk] = en;
+    } else {
+      if (lane == 0) atomicAdd(energy, en);
+    }
   }
+}
+
+// Node pass of the atomic-free scatter (node_gather) over all nodes.
+template <typename TW, typename TV, typename TY>
+__global__ void __launch_bounds__(128) k_node_gather(Grid g, const TW* __restrict__ W, int64_t ws,
+                                                     const dmask_t* __restrict__ mask, const TV* __restrict__ v,
+                                                     TY* __restrict__ y) {
+  const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (n >= g.nn()) return;
+  node_gather<TW, TV, TY>(g, W, ws, mask, v, y, n);
+}
+
+// *out += sum of x[0..n) in a fixed order: one CTA of 1024 threads, thread t
+// sums x[t], x[t + 1024], ... in order, then a fixed shared-memory tree.
+__global__ void __launch_bounds__(1024) k_sum_fixed(int64_t n, const double* __restrict__ x, double* out) {
+  __shared__ double part[1024];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += 1024) s += x[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 512; h > 0; h >>= 1) {
+    if (int(threadIdx.x) < h) part[threadIdx.x] += part[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out += part[0];
 }
 
 // Gauss-point Hessians of one level, computed in TC (FP64 for the finest and
@@ -91,15 +127,16 @@ __global__ void __launch_bounds__(128) k_linearize(Grid g, DevParams P, const do
 #ifndef PFM_JAPPLY_MINB
 #define PFM_JAPPLY_MINB 2
 #endif
-template <typename T>
+template <typename T, bool DET>
 __global__ void __launch_bounds__(256, PFM_JAPPLY_MINB) k_japply(Grid g, JParams<T> jp, const T* __restrict__ H,
                                                 const dmask_t* __restrict__ mask,
-                                                const T* __restrict__ v, T* __restrict__ y) {
+                                                const T* __restrict__ v, T* __restrict__ y, T* __restrict__ W,
+                                                int64_t ws) {
   const int64_t nblk = g.nblk();
   const int64_t wg = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   const int lane = int(threadIdx.x & 31);
-  for (int64_t blk = wg; blk < nblk; blk += nw) japply_block<T>(g, jp, H, mask, v, y, blk, lane);
+  for (int64_t blk = wg; blk < nblk; blk += nw) japply_block<T, DET>(g, jp, H, mask, v, y, blk, lane, W, ws);
 }
 
 // ---- END tangent application kernel
@@ -110,15 +147,17 @@ __global__ void __launch_bounds__(256, PFM_JAPPLY_MINB) k_japply(Grid g, JParams
 #ifndef PFM_JAPPLY_H16_MINB
 #define PFM_JAPPLY_H16_MINB PFM_JAPPLY_MINB
 #endif
+template <bool DET>
 __global__ void __launch_bounds__(256, PFM_JAPPLY_H16_MINB) k_japply_h16(Grid g, JParams<float> jp, float wh,
                                                     const __half* __restrict__ H,
                                                     const dmask_t* __restrict__ mask,
-                                                    const float* __restrict__ v, float* __restrict__ y) {
+                                                    const float* __restrict__ v, float* __restrict__ y,
+                                                    float* __restrict__ W, int64_t ws) {
   const int64_t nblk = g.nblk();
   const int64_t wg = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   const int lane = int(threadIdx.x & 31);
-  for (int64_t blk = wg; blk < nblk; blk += nw) japply_block_h16(g, jp, wh, H, mask, v, y, blk, lane);
+  for (int64_t blk = wg; blk < nblk; blk += nw) japply_block_h16<DET>(g, jp, wh, H, mask, v, y, blk, lane, W, ws);
 }
 
 // y += J v with v in FP32 (exact input), the tangent as Hhi + Hlo (two FP32
@@ -128,15 +167,17 @@ __global__ void __launch_bounds__(256, PFM_JAPPLY_H16_MINB) k_japply_h16(Grid g,
 #ifndef PFM_DF_MINB
 #define PFM_DF_MINB 8
 #endif
+template <bool DET>
 __global__ void __launch_bounds__(256, PFM_DF_MINB) k_japply_df(Grid g, DfConst k, const float* __restrict__ Hhi,
                                                      const float* __restrict__ Hlo,
                                                      const dmask_t* __restrict__ mask,
-                                                     const float* __restrict__ v, double* __restrict__ y) {
+                                                     const float* __restrict__ v, double* __restrict__ y,
+                                                     double* __restrict__ W, int64_t ws) {
   const int64_t nblk = g.nblk();
   const int64_t wg = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   const int lane = int(threadIdx.x & 31);
-  for (int64_t blk = wg; blk < nblk; blk += nw) japply_df_block(g, k, Hhi, Hlo, mask, v, y, blk, lane);
+  for (int64_t blk = wg; blk < nblk; blk += nw) japply_df_block<DET>(g, k, Hhi, Hlo, mask, v, y, blk, lane, W, ws);
 }
 
 // y = v at Dirichlet DOFs, 0 elsewhere (FP32 input, FP64 output).
@@ -320,10 +361,21 @@ __global__ void k_identity_rows(int64_t nn, const dmask_t* __restrict__ mask, co
 }  // namespace
 
 void launch_residual(const Grid& g, const DevParams& P, const double* U, const double* Un,
-                     const dmask_t* mask, double* R, double* energy, cudaStream_t s) {
+                     const dmask_t* mask, double* R, double* energy, cudaStream_t s, double* W) {
   const int64_t threads = g.nblk() * 32;
-  k_residual<<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, mask, R, energy);
-  count_launches(1);
+  if (!W) {
+    k_residual<false><<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, mask, R, energy, nullptr, 0);
+    count_launches(1);
+    return;
+  }
+  const int64_t ws = g.nblk() * 32;
+  k_residual<true><<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, mask, R, energy, W, ws);
+  k_node_gather<double, double, double><<<grid_for(g.nn(), 128), 128, 0, s>>>(g, W, ws, mask, nullptr, R);
+  count_launches(2);
+  if (energy) {
+    k_sum_fixed<<<1, 1024, 0, s>>>(g.nblk(), W + NF * ws, energy);
+    count_launches(1);
+  }
 }
 
 void launch_linearize(const Grid& g, const DevParams& P, const double* U, const double* Un,
@@ -420,30 +472,45 @@ int sm_count() {
 // of the Hessian part, used by the scaled binary16 store only)
 template <typename T>
 void japply_elem(const Grid& g, const JParams<T>& jp, float, const T* H, const dmask_t* mask, const T* v, T* y,
-                 unsigned blocks, int threads, cudaStream_t s) {
-  k_japply<T><<<blocks, threads, 0, s>>>(g, jp, H, mask, v, y);
+                 T* W, unsigned blocks, int threads, cudaStream_t s) {
+  if (W)
+    k_japply<T, true><<<blocks, threads, 0, s>>>(g, jp, H, mask, v, y, W, g.nblk() * 32);
+  else
+    k_japply<T, false><<<blocks, threads, 0, s>>>(g, jp, H, mask, v, y, nullptr, 0);
 }
 inline void japply_elem(const Grid& g, const JParams<float>& jp, float wh, const __half* H, const dmask_t* mask,
-                        const float* v, float* y, unsigned blocks, int threads, cudaStream_t s) {
-  k_japply_h16<<<blocks, threads, 0, s>>>(g, jp, wh, H, mask, v, y);
+                        const float* v, float* y, float* W, unsigned blocks, int threads, cudaStream_t s) {
+  if (W)
+    k_japply_h16<true><<<blocks, threads, 0, s>>>(g, jp, wh, H, mask, v, y, W, g.nblk() * 32);
+  else
+    k_japply_h16<false><<<blocks, threads, 0, s>>>(g, jp, wh, H, mask, v, y, nullptr, 0);
 }
 template <typename T>
 const void* japply_elem_fn(const T*) {
-  return reinterpret_cast<const void*>(k_japply<T>);
+  return reinterpret_cast<const void*>(k_japply<T, false>);
 }
-inline const void* japply_elem_fn(const __half*) { return reinterpret_cast<const void*>(k_japply_h16); }
+inline const void* japply_elem_fn(const __half*) { return reinterpret_cast<const void*>(k_japply_h16<false>); }
 
+// One tangent application with launch shape js; with a scratch W (9 * 32 *
+// nblk entries) atomic-free: element pass into W, then the node pass writes
+// every entry of y (no initialisation needed).
 template <typename T, typename S = T>
 void japply_launch_shape(const Grid& g, const JParams<T>& jp, float wh, const S* H, const dmask_t* mask, const T* v,
-                         T* y, const JShape& js, cudaStream_t s) {
+                         T* y, const JShape& js, cudaStream_t s, T* W = nullptr) {
   const int64_t nn = g.nn();
-  k_japply_init<T><<<grid_for(NF * nn, 256) < 4096 ? grid_for(NF * nn, 256) : 4096, 256, 0, s>>>(nn, mask, v, y);
-  count_launches(1);
+  if (!W) {
+    k_japply_init<T><<<grid_for(NF * nn, 256) < 4096 ? grid_for(NF * nn, 256) : 4096, 256, 0, s>>>(nn, mask, v, y);
+    count_launches(1);
+  }
   const int64_t need = (g.nblk() * 32 + js.threads - 1) / js.threads;
   const int64_t full = int64_t(sm_count()) * js.per_sm;
   const unsigned blocks = unsigned(need < full ? need : full);
-  japply_elem(g, jp, wh, H, mask, v, y, blocks, js.threads, s);
+  japply_elem(g, jp, wh, H, mask, v, y, W, blocks, js.threads, s);
   count_launches(1);
+  if (W) {
+    k_node_gather<T, T, T><<<grid_for(nn, 128), 128, 0, s>>>(g, W, g.nblk() * 32, mask, v, y);
+    count_launches(1);
+  }
 }
 
 template <typename T, typename S = T>
@@ -492,18 +559,18 @@ JShape japply_tune(const Grid& g, const JParams<T>& jp, float wh, const S* H, co
 
 template <typename T>
 void launch_japply(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, const T* v,
-                   T* y, cudaStream_t s) {
+                   T* y, cudaStream_t s, T* W) {
   const JParams<T> jp = make_jparams<T>(g, P);
   const JShape js = japply_tune<T>(g, jp, 0.f, H, mask, v, y, s);
-  japply_launch_shape<T>(g, jp, 0.f, H, mask, v, y, js, s);
+  japply_launch_shape<T>(g, jp, 0.f, H, mask, v, y, js, s, W);
 }
 
 void launch_japply_h16(const Grid& g, const DevParams& P, const __half* H, float inv_scale, const dmask_t* mask,
-                      const float* v, float* y, cudaStream_t s) {
+                      const float* v, float* y, cudaStream_t s, float* W) {
   const JParams<float> jp = make_jparams<float>(g, P);
   const float wh = jp.w * inv_scale;
   const JShape js = japply_tune<float, __half>(g, jp, wh, H, mask, v, y, s);
-  japply_launch_shape<float, __half>(g, jp, wh, H, mask, v, y, js, s);
+  japply_launch_shape<float, __half>(g, jp, wh, H, mask, v, y, js, s, W);
 }
 
 float launch_store_to_half(const Grid& g, const float* H32, __half* H16, unsigned* scratch, cudaStream_t s) {
@@ -529,19 +596,29 @@ float launch_store_to_half(const Grid& g, const float* H32, __half* H16, unsigne
 }
 
 void launch_japply_df(const Grid& g, const DevParams& P, const float* Hhi, const float* Hlo, const dmask_t* mask,
-                      const float* v, double* y, cudaStream_t s) {
+                      const float* v, double* y, cudaStream_t s, double* W) {
   const DfConst k = make_dfconst(g, P);
   const int64_t nn = g.nn();
-  k_japply_init_df<<<grid_for(NF * nn, 256) < 4096 ? grid_for(NF * nn, 256) : 4096, 256, 0, s>>>(nn, mask, v, y);
-  count_launches(1);
+  if (!W) {
+    k_japply_init_df<<<grid_for(NF * nn, 256) < 4096 ? grid_for(NF * nn, 256) : 4096, 256, 0, s>>>(nn, mask, v, y);
+    count_launches(1);
+  }
   static int per_sm = 0;
   if (per_sm == 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_japply_df, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_japply_df<false>, 256, 0);
     if (per_sm < 1) per_sm = 1;
   }
   const int64_t need = (g.nblk() * 32 + 255) / 256;
   const int64_t full = int64_t(sm_count()) * per_sm;
-  k_japply_df<<<unsigned(need < full ? need : full), 256, 0, s>>>(g, k, Hhi, Hlo, mask, v, y);
+  const unsigned blocks = unsigned(need < full ? need : full);
+  if (W) {
+    const int64_t ws = g.nblk() * 32;
+    k_japply_df<true><<<blocks, 256, 0, s>>>(g, k, Hhi, Hlo, mask, v, y, W, ws);
+    k_node_gather<double, float, double><<<grid_for(nn, 128), 128, 0, s>>>(g, W, ws, mask, v, y);
+    count_launches(2);
+    return;
+  }
+  k_japply_df<false><<<blocks, 256, 0, s>>>(g, k, Hhi, Hlo, mask, v, y, nullptr, 0);
   count_launches(1);
 }
 
@@ -611,9 +688,9 @@ template void launch_identity_rows<double>(int64_t, const dmask_t*, const double
                                            cudaStream_t);
 
 template void launch_japply<float>(const Grid&, const DevParams&, const float*, const dmask_t*,
-                                   const float*, float*, cudaStream_t);
+                                   const float*, float*, cudaStream_t, float*);
 template void launch_japply<double>(const Grid&, const DevParams&, const double*, const dmask_t*,
-                                     const double*, double*, cudaStream_t);
+                                     const double*, double*, cudaStream_t, double*);
 template void launch_blockdiag<float>(const Grid&, const DevParams&, const float*, const dmask_t*, float*,
                                       float*, cudaStream_t);
 template void launch_blockdiag<double>(const Grid&, const DevParams&, const double*, const dmask_t*, double*,

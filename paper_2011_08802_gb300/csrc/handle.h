@@ -89,6 +89,8 @@ struct pfm_handle {
   double* wv = nullptr;
   double* rv = nullptr;
   double* zd = nullptr;
+  double* ir_r = nullptr;  // iterative refinement: outer residual and inner correction
+  double* ir_d = nullptr;
   double* partial = nullptr;
   double* hdev = nullptr;
   // Krylov basis
@@ -117,6 +119,7 @@ struct pfm_handle {
   bool outer_df = true;  // outer operator of the mixed solve in double-float arithmetic
   bool lin_df = false;   // FP64-class linearisation in double-float instead of FP64 arithmetic
   bool pre_h16 = false;  // FP32 preconditioner reads binary16 Hessian copies
+  bool det = false;      // atomic-free element kernels (pfm_set_deterministic or opts.deterministic)
   unsigned* amax_dev = nullptr;  // one word for the store's max |entry|
   // pinned host slots for Hessenberg columns and scalars
   double* hpin = nullptr;
@@ -124,7 +127,7 @@ struct pfm_handle {
   bool use_graphs = false;
   cudaGraphExec_t vgraph = nullptr;
   int vgraph_prec = -1;
-  struct { int nu_pre, nu_post, type; double omega, lo, hi; int gamma; double growth; } vgraph_cfg{};
+  struct { int nu_pre, nu_post, type; double omega, lo, hi; int gamma; double growth; bool det; } vgraph_cfg{};
   // device timing of hot phases (pairs of events per timed launch)
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[PFM_PROF_COUNT];

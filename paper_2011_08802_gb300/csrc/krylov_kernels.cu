@@ -34,6 +34,24 @@ __global__ void k_cast_f2d(int64_t n, const float* __restrict__ a, double* __res
     b[i] = double(a[i]);
 }
 
+// x = hi + lo with hi = x rounded to FP32 and lo = the remainder rounded to
+// FP32 (x - hi is exact in FP64; |x - hi - lo| <= 2^-48 |x| roughly).
+__global__ void k_split_f64(int64_t n, const double* __restrict__ x, float* __restrict__ hi, float* __restrict__ lo) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double v = x[i];
+    const float h = float(v);
+    hi[i] = h;
+    lo[i] = float(v - double(h));
+  }
+}
+
+// r = b - a - c (FP64 b, a; FP32 c).
+__global__ void k_sub2(int64_t n, const double* __restrict__ b, const double* __restrict__ a,
+                       const float* __restrict__ c, double* __restrict__ r) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    r[i] = (b[i] - a[i]) - double(c[i]);
+}
+
 // partial[blk*kstride + j0 + j] = sum over this block's slice of V_j . w,
 // j = 0..cnt-1 (cnt <= MDOT_CHUNK).
 __global__ void __launch_bounds__(RED_THREADS) k_mdot_partial(int64_t n, int j0, int cnt,
@@ -172,6 +190,16 @@ void launch_cast_d2f(int64_t n, const double* a, float* b, cudaStream_t s) {
   k_cast_d2f<<<grid_for(n, 256), 256, 0, s>>>(n, a, b);
   count_launches(1);
 }
+void launch_split_f64(int64_t n, const double* x, float* hi, float* lo, cudaStream_t s) {
+  k_split_f64<<<grid_for(n, 256), 256, 0, s>>>(n, x, hi, lo);
+  count_launches(1);
+}
+
+void launch_sub2(int64_t n, const double* b, const double* a, const float* c, double* r, cudaStream_t s) {
+  k_sub2<<<grid_for(n, 256), 256, 0, s>>>(n, b, a, c, r);
+  count_launches(1);
+}
+
 void launch_cast_f2d(int64_t n, const float* a, double* b, cudaStream_t s) {
   k_cast_f2d<<<grid_for(n, 256), 256, 0, s>>>(n, a, b);
   count_launches(1);

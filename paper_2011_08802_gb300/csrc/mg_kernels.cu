@@ -88,13 +88,20 @@ __global__ void k_sub(int64_t n, const T* __restrict__ b, const T* __restrict__ 
 
 // Dense coarse operator K (row-major, leading dimension ld) from the stored
 // point Hessians: thread (element, local row l = f*8 + a) adds row l of the
-// element matrix sum_q w (Bz^T H_q Bz + Bg^T G Bg).
+// element matrix sum_q w (Bz^T H_q Bz + Bg^T G Bg). color < 0: every element,
+// added with atomics; color = 0..7: only the elements with
+// (ei & 1) + 2 (ej & 1) + 4 (ek & 1) == color, which share no node, added
+// without atomics (eight launches in colour order give a fixed summation order).
 template <typename T>
 __global__ void k_coarse_assemble(Grid g, DevParams P, const T* __restrict__ H, double* __restrict__ K,
-                                  int ld) {
+                                  int ld, int color) {
   const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t e = tid / 72;
   if (e >= g.ne()) return;
+  if (color >= 0) {
+    const int64_t ei = e % g.nx, ej = (e / g.nx) % g.ny, ek = e / (int64_t(g.nx) * g.ny);
+    if (int((ei & 1) + 2 * (ej & 1) + 4 * (ek & 1)) != color) return;
+  }
   const int l = int(tid % 72);
   const int fl = l / 8, al = l % 8;
   const int64_t nn = g.nn();
@@ -144,7 +151,10 @@ __global__ void k_coarse_assemble(Grid g, DevParams P, const T* __restrict__ H, 
         s += (dNl[0] * dNm[0] + dNl[1] * dNm[1] + dNl[2] * dNm[2]) * P.G[fl - 3][fm - 3];
     }
     const int64_t col = fm * nn + node_of(am);
-    atomicAdd(&K[row * ld + col], w * s);
+    if (color >= 0)
+      K[row * ld + col] += w * s;
+    else
+      atomicAdd(&K[row * ld + col], w * s);
   }
 }
 
@@ -300,11 +310,13 @@ void launch_sub(int64_t n, const T* b, const T* y, T* r, cudaStream_t s) {
 
 template <typename T>
 void launch_coarse_assemble(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask,
-                            double* K, int ld, cudaStream_t s) {
+                            double* K, int ld, cudaStream_t s, bool det) {
   const int n = int(NF * g.nn());
   cudaMemsetAsync(K, 0, sizeof(double) * size_t(n) * ld, s);
-  k_coarse_assemble<T><<<grid_for(g.ne() * 72, 128), 128, 0, s>>>(g, P, H, K, ld);
-  count_launches(1);
+  for (int c = det ? 0 : -1; c < (det ? 8 : 0); ++c) {
+    k_coarse_assemble<T><<<grid_for(g.ne() * 72, 128), 128, 0, s>>>(g, P, H, K, ld, c);
+    count_launches(1);
+  }
   k_coarse_bc<<<grid_for(int64_t(n) * n, 256), 256, 0, s>>>(n, g.nn(), mask, K, ld);
   count_launches(1);
 }
@@ -342,7 +354,7 @@ void launch_coarse_solve(int n, const double* Ainv, const T* b, T* x, cudaStream
   template void launch_smooth<T>(int64_t, const T*, const T*, const T*, T, T*, cudaStream_t);     \
   template void launch_sub<T>(int64_t, const T*, const T*, T*, cudaStream_t);                     \
   template void launch_coarse_assemble<T>(const Grid&, const DevParams&, const T*, const dmask_t*, \
-                                          double*, int, cudaStream_t);                          \
+                                          double*, int, cudaStream_t, bool);                    \
   template void launch_coarse_solve<T>(int, const double*, const T*, T*, cudaStream_t);         \
   template void launch_cheb_first<T>(int64_t, const T*, const T*, T, bool, bool, T*, T*, T*,       \
                                      cudaStream_t);                                             \

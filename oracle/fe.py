@@ -63,24 +63,26 @@ def connectivity(mesh) -> np.ndarray:
     return conn
 
 
-def element_dofs(mesh, conn) -> np.ndarray:
+def element_dofs(mesh, conn, n_fields: int = N_FIELDS) -> np.ndarray:
     """Global DOF of local DOF f*8 + a of each element: f*n_nodes + conn[e,a]."""
     nv = mesh.n_nodes
-    return np.concatenate([f * nv + conn for f in range(N_FIELDS)], axis=1)
+    return np.concatenate([f * nv + conn for f in range(n_fields)], axis=1)
 
 
-def z_maps(N, dN):
-    """Per Gauss point, the linear maps from the 72 element DOFs (local DOF
-    f*8 + a) to the local seeds z = (F_iJ row-major, eta_hat_k) (Bz, 15x72)
-    and to grad eta_hat (Bg, 18x72, row 3k + d)."""
-    Bz = np.zeros((8, 15, 72))
-    Bg = np.zeros((8, 18, 72))
+def z_maps(N, dN, n_var: int = 6):
+    """Per Gauss point, the linear maps from the 8 (3 + n_var) element DOFs
+    (local DOF f*8 + a) to the local seeds z = (F_iJ row-major, eta_hat_k)
+    (Bz, (9 + n_var) rows; 15 x 72 for six variants) and to grad eta_hat
+    (Bg, 3 n_var rows, row 3k + d)."""
+    nd = 8 * (3 + n_var)
+    Bz = np.zeros((8, 9 + n_var, nd))
+    Bg = np.zeros((8, 3 * n_var, nd))
     for q in range(8):
         for a in range(8):
             for i in range(3):
                 for J in range(3):
                     Bz[q, 3 * i + J, i * 8 + a] = dN[q, a, J]
-            for k in range(6):
+            for k in range(n_var):
                 Bz[q, 9 + k, (3 + k) * 8 + a] = N[q, a]
                 for d in range(3):
                     Bg[q, 3 * k + d, (3 + k) * 8 + a] = dN[q, a, d]
@@ -89,24 +91,27 @@ def z_maps(N, dN):
 
 class Discretisation:
     """Mesh-level data of the oracle: connectivity, element DOF map, Gauss
-    point maps. ``elements`` restricts the element loop to a subset."""
+    point maps. ``elements`` restricts the element loop to a subset;
+    ``n_var`` is the number of variants (3 + n_var fields per node)."""
 
-    def __init__(self, mesh, elements=None):
+    def __init__(self, mesh, elements=None, n_var: int = 6):
         self.mesh = mesh
+        self.n_var = n_var
+        self.n_fields = 3 + n_var
         self.conn = connectivity(mesh)
-        self.edofs = element_dofs(mesh, self.conn)
+        self.edofs = element_dofs(mesh, self.conn, self.n_fields)
         self.N, self.dN, self.w = reference_element(mesh.h)
-        self.Bz, self.Bg = z_maps(self.N, self.dN)
+        self.Bz, self.Bg = z_maps(self.N, self.dN, n_var)
         self.elements = np.arange(mesh.n_elems) if elements is None else np.asarray(elements)
 
     def qp_fields(self, U):
-        """F (E,8,3,3), eta_hat (E,8,6) and grad eta_hat (E,8,6,3) at every
-        Gauss point of the selected elements, from nodal U (9, n_nodes)."""
-        ue = U.reshape(-1)[self.edofs[self.elements]]          # (E, 72)
-        z = np.einsum("qzl,el->eqz", self.Bz, ue)              # (E, 8, 15)
-        gz = np.einsum("qzl,el->eqz", self.Bg, ue)             # (E, 8, 18)
+        """F (E,8,3,3), eta_hat (E,8,N) and grad eta_hat (E,8,N,3) at every
+        Gauss point of the selected elements, from nodal U (3 + N, n_nodes)."""
+        ue = U.reshape(-1)[self.edofs[self.elements]]          # (E, 8 (3 + N))
+        z = np.einsum("qzl,el->eqz", self.Bz, ue)              # (E, 8, 9 + N)
+        gz = np.einsum("qzl,el->eqz", self.Bg, ue)             # (E, 8, 3 N)
         F = z[..., :9].reshape(-1, 8, 3, 3) + np.eye(3)
-        return F, z[..., 9:], gz.reshape(-1, 8, 6, 3)
+        return F, z[..., 9:], gz.reshape(-1, 8, self.n_var, 3)
 
 
 def _flatq(x):
@@ -123,23 +128,24 @@ def energy(disc, state, mat) -> float:
 
 
 def qp_derivatives(disc, state, mat, order=2):
-    """Per Gauss point of the selected elements: gradient (E,8,15) and
-    Hessian (E,8,15,15) of W_loc in (F, eta_hat), gradient (E,8,18) and
-    Hessian (18,18) of W_grad in grad eta_hat."""
+    """Per Gauss point of the selected elements: gradient (E,8,9+N) and
+    Hessian (E,8,9+N,9+N) of W_loc in (F, eta_hat), gradient (E,8,3N) and
+    Hessian (3N,3N) of W_grad in grad eta_hat (N = 6: 15 and 18)."""
     F, eh, geh = disc.qp_fields(state.U)
     _, ehn, _ = disc.qp_fields(state.Un)
     E = F.shape[0]
     W = qp.local_energy(_flatq(F), _flatq(eh), _flatq(ehn), mat, order=order)
     Wg = qp.gradient_energy(_flatq(geh), mat, order=order)
-    out = dict(g=W.g.reshape(E, 8, 15), gg=Wg.g.reshape(E, 8, 18))
+    nz = 9 + disc.n_var
+    out = dict(g=W.g.reshape(E, 8, nz), gg=Wg.g.reshape(E, 8, 3 * disc.n_var))
     if order >= 2:
-        out["H"] = W.H.reshape(E, 8, 15, 15)
+        out["H"] = W.H.reshape(E, 8, nz, nz)
         out["HG"] = Wg.H[0]
     return out
 
 
 def residual(disc, state, mat, d=None) -> np.ndarray:
-    """R = dPi/dU as (9, n_nodes), zero at Dirichlet DOFs. The selected
+    """R = dPi/dU as (3 + N, n_nodes), zero at Dirichlet DOFs. The selected
     elements' contributions only (all elements by default)."""
     if d is None:
         d = qp_derivatives(disc, state, mat, order=1)
@@ -152,7 +158,8 @@ def residual(disc, state, mat, d=None) -> np.ndarray:
 
 
 def element_matrices(disc, d) -> np.ndarray:
-    """K_e = sum_q w (Bz_q^T H_q Bz_q + Bg_q^T HG Bg_q), shape (E, 72, 72)."""
+    """K_e = sum_q w (Bz_q^T H_q Bz_q + Bg_q^T HG Bg_q), shape (E, 8 nf, 8 nf)
+    with nf = 3 + N fields (72 x 72 for six variants)."""
     K = np.einsum("qzl,eqzy,qym->elm", disc.Bz, d["H"], disc.Bz, optimize=True)
     K += np.einsum("qzl,zy,qym->lm", disc.Bg, d["HG"], disc.Bg, optimize=True)[None]
     return disc.w * K
@@ -165,8 +172,9 @@ def tangent(disc, state, mat, d=None) -> sp.csr_matrix:
         d = qp_derivatives(disc, state, mat, order=2)
     Ke = element_matrices(disc, d)
     ed = disc.edofs[disc.elements]
-    rows = np.repeat(ed, 72, axis=1).ravel()
-    cols = np.tile(ed, (1, 72)).ravel()
+    nd = ed.shape[1]
+    rows = np.repeat(ed, nd, axis=1).ravel()
+    cols = np.tile(ed, (1, nd)).ravel()
     n = state.U.size
     K = sp.coo_matrix((Ke.ravel(), (rows, cols)), shape=(n, n)).tocsr()
     D = state.mask.reshape(-1).astype(bool)

@@ -41,19 +41,27 @@ N_PHASES = 7          # austenite + 6 martensite variants (Sec. 5.1)
 N_LOCAL = 15          # seeds: F (9, row-major F_iJ) then eta_1..eta_6
 N_GRAD = 18           # seeds: d eta_k / d X_d at index 3*k + d
 LOG_QUAD_POINTS = 24  # Gauss-Legendre points of the log integral
+# The model is written for any number N of variants (Sec. 2.1: phases
+# 0..N); N is read from the material (U has N + 1 entries), the constants
+# above are those of the N = 6 CuAlNi data of Sec. 5.1.
 
 
 @dataclass
 class Material:
-    U: np.ndarray        # (7,3,3) transformation stretches, U[0] = I
-    Lt: np.ndarray       # (7,3,3,3,3) stiffness tensors L_i
-    F0: np.ndarray       # (7,) chemical energies
-    m: np.ndarray        # (7,) mobilities
-    gamma: np.ndarray    # (7,7) interface energies (symmetric)
-    ell: np.ndarray      # (7,7) interface thickness parameters (symmetric)
+    U: np.ndarray        # (N+1,3,3) transformation stretches, U[0] = I
+    Lt: np.ndarray       # (N+1,3,3,3,3) stiffness tensors L_i
+    F0: np.ndarray       # (N+1,) chemical energies
+    m: np.ndarray        # (N+1,) mobilities
+    gamma: np.ndarray    # (N+1,N+1) interface energies (symmetric)
+    ell: np.ndarray      # (N+1,N+1) interface thickness parameters (symmetric)
     eps_eta: float
     tau: float
     hencky: str = "log"  # "log" (exact 1/2 log C) or "pade11" / "pade22" / "pade33" (Sec. 2.4)
+
+    @property
+    def n_var(self) -> int:
+        """Number N of martensite variants (phases 1..N)."""
+        return self.U.shape[0] - 1
 
     def obstacle(self) -> np.ndarray:
         """Coefficients 4 gamma_ij / (pi ell_ij) of Eq. IntEnergy."""
@@ -160,6 +168,24 @@ def material_from(constants: dict, tau: float, C=None, gamma_scale: float = 1.0,
     return Material(U, Lt, F0, m, gamma_scale * g, ell, constants["eps_eta"], tau, hencky)
 
 
+def material_variants(constants: dict, U: np.ndarray, tau: float, hencky: str = "log") -> Material:
+    """Material with the transformation stretches U (N+1,3,3), U[0] = I, of
+    any number N of variants and the remaining constants of Sec. 5.1: one
+    cubic stiffness (C11, C12, C44) for every phase, the martensite chemical
+    energy, mobility and interface data for each variant, the austenite ones
+    for phase 0."""
+    U = np.asarray(U, dtype=np.float64)
+    n_phases = U.shape[0]
+    Lt = np.stack([cubic_stiffness(constants["C11"], constants["C12"], constants["C44"])] * n_phases)
+    F0 = np.array([constants["F0_austenite"]] + [constants["F0_martensite"]] * (n_phases - 1))
+    m = np.full(n_phases, constants["mobility"])
+    g = np.full((n_phases, n_phases), constants["gamma_mm"])
+    g[0, :] = g[:, 0] = constants["gamma_am"]
+    np.fill_diagonal(g, 0.0)
+    ell = np.full((n_phases, n_phases), constants["ell"])
+    return Material(U, Lt, F0, m, g, ell, constants["eps_eta"], tau, hencky)
+
+
 # ---------------------------------------------------------------------------
 
 def _gauss_legendre_01(n: int):
@@ -208,12 +234,12 @@ def hencky_strain(C: Jet, mode: str = "log") -> Jet:
     return matmul(num, inv3(den)) * scale
 
 
-def order_parameters(eta_hat: Jet) -> list:
-    """eta_0 = 1 - sum eta_hat (Sec. 3.1) followed by eta_1..eta_6."""
+def order_parameters(eta_hat: Jet, n_var: int = 6) -> list:
+    """eta_0 = 1 - sum eta_hat (Sec. 3.1) followed by eta_1..eta_N."""
     s = eta_hat[0]
-    for k in range(1, 6):
+    for k in range(1, n_var):
         s = s + eta_hat[k]
-    return [1.0 - s] + [eta_hat[k] for k in range(6)]
+    return [1.0 - s] + [eta_hat[k] for k in range(n_var)]
 
 
 def _contract(Lt: np.ndarray, h: Jet) -> Jet:
@@ -252,23 +278,26 @@ def _neg_part_sq(x: Jet) -> Jet:
 def local_energy(F: np.ndarray, eta_hat: np.ndarray, eta_hat_n: np.ndarray, mat: Material,
                  order: int = 2, parts: bool = False):
     """Local energy density W(F, eta_hat) at B points (everything but the
-    gradient part of the interface energy), as a jet in the 15 seeds
-    (F_iJ row-major, eta_1..eta_6).
+    gradient part of the interface energy), as a jet in the 9 + N seeds
+    (F_iJ row-major, eta_1..eta_N; 15 for the N = 6 data of Sec. 5.1).
 
-    F: (B,3,3); eta_hat, eta_hat_n: (B,6). Returns the scalar jet W, or with
+    F: (B,3,3); eta_hat, eta_hat_n: (B,N). Returns the scalar jet W, or with
     ``parts`` a dict of the separate terms.
     """
     B = F.shape[0]
-    z = Jet.variables(np.concatenate([F.reshape(B, 9), eta_hat], axis=1), N_LOCAL, 0, order)
-    Fj = Jet(z.v[:, :9].reshape(B, 3, 3), z.g[:, :9].reshape(B, 3, 3, N_LOCAL),
-             None if z.H is None else z.H[:, :9].reshape(B, 3, 3, N_LOCAL, N_LOCAL))
-    eh = z[slice(9, 15)]
-    eta = order_parameters(eh)
-    eta_n = [1.0 - eta_hat_n.sum(axis=1)] + [eta_hat_n[:, k] for k in range(6)]
+    nv = mat.n_var
+    n_phases = nv + 1
+    n_local = 9 + nv
+    z = Jet.variables(np.concatenate([F.reshape(B, 9), eta_hat], axis=1), n_local, 0, order)
+    Fj = Jet(z.v[:, :9].reshape(B, 3, 3), z.g[:, :9].reshape(B, 3, 3, n_local),
+             None if z.H is None else z.H[:, :9].reshape(B, 3, 3, n_local, n_local))
+    eh = z[slice(9, n_local)]
+    eta = order_parameters(eh, nv)
+    eta_n = [1.0 - eta_hat_n.sum(axis=1)] + [eta_hat_n[:, k] for k in range(nv)]
 
     # transformation stretch and elastic kinematics (Sec. 2.1, Eq. elasticEn)
     Ft = None
-    for i in range(N_PHASES):
+    for i in range(n_phases):
         Ui = np.broadcast_to(mat.U[i], (B, 3, 3))
         t = _scalar_times_matrix(eta[i], Ui)
         Ft = t if Ft is None else Ft + t
@@ -276,28 +305,28 @@ def local_energy(F: np.ndarray, eta_hat: np.ndarray, eta_hat_n: np.ndarray, mat:
     Ce = matmul(transpose(Fe), Fe)
     He = hencky_strain(Ce, mat.hencky)
     LH = None
-    for i in range(N_PHASES):
+    for i in range(n_phases):
         t = _scalar_jet_times_matrix_jet(eta[i], _contract(mat.Lt[i], He))
         LH = t if LH is None else LH + t
     W_el = det3(Ft) * _ddot(He, LH) * 0.5
 
     W_chem = None
-    for i in range(N_PHASES):
+    for i in range(n_phases):
         t = eta[i] * mat.F0[i]
         W_chem = t if W_chem is None else W_chem + t
     c = mat.obstacle()
     W_obst = None
-    for i in range(N_PHASES):
-        for j in range(i + 1, N_PHASES):
+    for i in range(n_phases):
+        for j in range(i + 1, n_phases):
             t = eta[i] * eta[j] * c[i, j]
             W_obst = t if W_obst is None else W_obst + t
     W_diss = None
-    for i in range(N_PHASES):
+    for i in range(n_phases):
         d = (eta[i] - eta_n[i]) * (1.0 / mat.tau)
         t = d * d * (mat.tau / (2.0 * mat.m[i]))
         W_diss = t if W_diss is None else W_diss + t
     W_pen = None
-    for i in range(N_PHASES):
+    for i in range(n_phases):
         t = _neg_part_sq(eta[i]) * (0.5 * mat.eps_eta)
         W_pen = t if W_pen is None else W_pen + t
 
@@ -329,21 +358,22 @@ def _scalar_jet_times_matrix_jet(s: Jet, M: Jet) -> Jet:
 def gradient_energy(grad_eta_hat: np.ndarray, mat: Material, order: int = 2) -> Jet:
     """Gradient part of Eq. IntEnergy, -sum_{i<j} 4 gamma_ij ell_ij/pi
     grad eta_i . grad eta_j with grad eta_0 = -sum_k grad eta_k, as a jet in
-    the 18 seeds d eta_k / d X_d (index 3k + d). grad_eta_hat: (B,6,3)."""
+    the 3N seeds d eta_k / d X_d (index 3k + d). grad_eta_hat: (B,N,3)."""
     B = grad_eta_hat.shape[0]
-    z = Jet.variables(grad_eta_hat.reshape(B, 18), N_GRAD, 0, order)
-    g = [[z[3 * k + d] for d in range(3)] for k in range(6)]
+    nv = mat.n_var
+    z = Jet.variables(grad_eta_hat.reshape(B, 3 * nv), 3 * nv, 0, order)
+    g = [[z[3 * k + d] for d in range(3)] for k in range(nv)]
     g0 = [None] * 3
     for d in range(3):
         s = g[0][d]
-        for k in range(1, 6):
+        for k in range(1, nv):
             s = s + g[k][d]
         g0[d] = -s
     grads = [g0] + g
     c = mat.obstacle()
     acc = None
-    for i in range(N_PHASES):
-        for j in range(i + 1, N_PHASES):
+    for i in range(nv + 1):
+        for j in range(i + 1, nv + 1):
             dot = grads[i][0] * grads[j][0] + grads[i][1] * grads[j][1] + grads[i][2] * grads[j][2]
             t = dot * (-c[i, j] * mat.ell[i, j] ** 2)
             acc = t if acc is None else acc + t

@@ -102,12 +102,19 @@ typedef struct {
   double nu_growth;      /* smoothing steps on level l: round(nu * nu_growth^l) (<= 0 read as 1) */
   int deterministic;     /* 1: run the solve as pfm_set_deterministic(h, 1) does (bitwise
                             reproducible results); 0: the handle's setting */
-  int refine;            /* mixed precision (precond PFM_F32) only: 0 = FGMRES whose every
-                            iteration applies the FP64-class outer operator; 1 = iterative
-                            refinement: inner FGMRES solves with the FP32 operator and the FP32
-                            V-cycle, each to inner_rtol, and after each an FP64-class residual
-                            b - J x (Sec. 3.4 tolerance lin_rtol on that true residual) */
-  double inner_rtol;     /* refine = 1: relative tolerance of each inner solve (e.g. 1e-4) */
+  int krylov;            /* mixed precision (precond PFM_F32) only, how FGMRES applies J:
+                            0 = the FP64-class outer operator in every iteration;
+                            1 = relaxed products: the FP64-class operator while the residual
+                                estimate is above switch_rtol ||b||, the FP32 operator after it
+                                (an inexact Krylov method whose late products may be less
+                                accurate), then the FP64-class true residual b - J x decides,
+                                and a restart from it follows if lin_rtol is not met;
+                            2 = iterative refinement: inner FGMRES cycles with the FP32
+                                operator, each to switch_rtol times its right-hand side, each
+                                followed by the FP64-class true residual.
+                            Modes 1 and 2 stop on the true residual (Sec. 3.4, lin_rtol). */
+  double switch_rtol;    /* krylov = 1: relative residual estimate below which products are
+                            FP32 (e.g. 1e-3); krylov = 2: inner relative tolerance (e.g. 1e-4) */
 } pfm_solve_opts;
 
 typedef struct {
@@ -117,8 +124,9 @@ typedef struct {
   double res0;           /* ||R(U_0)||_2 */
   double res_final;      /* ||R(U)||_2 after the last correction */
   double lin_res_final;  /* relative residual of the last linear solve: the FGMRES estimate, or
-                            with refine = 1 the FP64-class true residual */
-  int lin_outer_last;    /* refine = 1: refinement steps of the last linear solve (else 0) */
+                            with krylov = 1 or 2 the FP64-class true residual */
+  int lin_outer_last;    /* krylov = 1: FGMRES cycles (restarts + 1), krylov = 2: refinement
+                            steps, of the last linear solve (0 with krylov = 0) */
   double ms_residual, ms_linearize, ms_solve, ms_total; /* wall times (ms) */
   pfm_status status;
 } pfm_solve_report;
@@ -167,7 +175,10 @@ pfm_status pfm_set_outer_operator(pfm_handle* h, int double_float);
  * at most 8 contributions in a fixed order; the coarse assembly runs eight
  * element colours one after another), so that repeated calls on the same
  * data give bitwise equal results (Sec. 3.4, the tangent of Eq. linAlgEq).
- * Costs about one extra write and read of 9 values per element node.
+ * Costs about one extra write and read of 9 values per element node. The
+ * setting takes effect at once for residuals and applications; the coarse
+ * operator keeps the form it was assembled in at the last pfm_linearize
+ * (a Newton solve linearises, so its coarse operator follows the setting).
  * Penalty contact (pfm_set_contact) is not covered: calls that would apply
  * its terms in deterministic mode return PFM_ERR_INVALID_ARG.
  * Errors: PFM_ERR_INVALID_ARG (NULL handle, other values). */

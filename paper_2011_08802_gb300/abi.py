@@ -51,7 +51,7 @@ class SolveOpts(C.Structure):
                 ("newton_rtol", C.c_double), ("lin_rtol", C.c_double), ("omega", C.c_double),
                 ("precond", C.c_int), ("smoother", C.c_int), ("cheb_lo", C.c_double),
                 ("cheb_hi", C.c_double), ("cycle_gamma", C.c_int), ("nu_growth", C.c_double),
-                ("deterministic", C.c_int), ("refine", C.c_int), ("inner_rtol", C.c_double)]
+                ("deterministic", C.c_int), ("krylov", C.c_int), ("switch_rtol", C.c_double)]
 
 
 class SolveReport(C.Structure):
@@ -65,7 +65,7 @@ def default_opts(precond: int = PFM_F32, **kw) -> SolveOpts:
     o = SolveOpts(max_newton=1, restart=30, max_lin_it=300, nu_pre=2, nu_post=8,
                   newton_rtol=1e-8, lin_rtol=1e-8, omega=0.7, precond=precond,
                   smoother=0, cheb_lo=0.05, cheb_hi=1.1, cycle_gamma=1, nu_growth=1.25,
-                  deterministic=0, refine=0, inner_rtol=1e-4)
+                  deterministic=0, krylov=0, switch_rtol=1e-3)
     for k, v in kw.items():
         setattr(o, k, v)
     return o

@@ -433,10 +433,15 @@ struct Fgm {
   double beta0 = 0.0, beta = 0.0, tol = 0.0, relres = 1.0;
   int total = 0, j = 0;
   bool done = false, converged = false;
-  // inner solve of iterative refinement: FP32 operator, one cycle, stop at
-  // max(inner_rtol ||b||, tol_floor)
+  // inner solve of iterative refinement (krylov 2): FP32 operator, one cycle,
+  // stop at max(switch_rtol ||b||, tol_floor)
   bool inner = false;
   double tol_floor = 0.0;
+  // relaxed products (krylov 1): FP32 products once the residual estimate
+  // resest is at most switch_abs; the true residual decides convergence
+  bool relax = false;
+  double switch_abs = 0.0, resest = 0.0;
+  int cycles = 0;
   pfm_status status = PFM_OK;
   std::vector<double> Hh, cs, sn, g;
 };
@@ -481,6 +486,7 @@ pfm_status fgm_begin_enqueue(pfm_handle* h, Fgm& F, const pfm_solve_opts& o, con
   F.x = x;
   F.m = o.restart;
   F.mixed = (o.precond == PFM_F32);
+  F.relax = F.mixed && o.krylov == 1;
   F.sc = smooth_cfg(&o);
   if (F.mixed && h->lin_prec != PFM_F32)
     return h->fail(PFM_ERR_STATE, "FP32 preconditioner requested but the tangent was built for FP64");
@@ -512,6 +518,8 @@ pfm_status fgm_start_cycle(pfm_handle* h, Fgm& F) {
   std::fill(F.g.begin(), F.g.end(), 0.0);
   F.g[0] = F.beta;
   F.j = 0;
+  F.resest = F.beta;
+  ++F.cycles;
   return PFM_OK;
 }
 
@@ -527,13 +535,15 @@ pfm_status fgm_begin_finish(pfm_handle* h, Fgm& F) {
     F.relres = 0.0;
     return PFM_OK;
   }
-  F.tol = F.inner ? std::max(F.o.inner_rtol * F.beta0, F.tol_floor) : F.o.lin_rtol * F.beta0;
+  F.tol = F.inner ? std::max(F.o.switch_rtol * F.beta0, F.tol_floor) : F.o.lin_rtol * F.beta0;
+  F.switch_abs = F.o.switch_rtol * F.beta0;
   F.beta = F.beta0;
   return fgm_start_cycle(h, F);
 }
 
 template <typename T>
 pfm_status capture_vcycle(pfm_handle* h, const SmoothCfg& sc);
+pfm_status true_residual(pfm_handle* h, const double* b, const double* x, double* r);
 
 // z_j = M v_j, w = J z_j, two Gram-Schmidt passes and ||w||^2, with the
 // Hessenberg column copied to the pinned host slots (no synchronisation).
@@ -555,8 +565,9 @@ pfm_status fgm_enqueue(pfm_handle* h, Fgm& F) {
     CK(cudaMemcpyAsync(zj, fl.x32, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
     // w = J z_j with the FP64-accurate operator: either the FP64 kernel or,
     // since z_j is exactly FP32, the double-float kernel on the FP32 pipes;
-    // inside iterative refinement the FP32 operator of the FP32 store
-    if (F.inner) {
+    // inside iterative refinement, and for the relaxed products once the
+    // residual estimate is small, the FP32 operator of the FP32 store
+    if (F.inner || (F.relax && F.resest <= F.switch_abs)) {
       {
         ProfScope ps(h, PFM_PROF_JAPPLY_F32);
         launch_japply<float>(fl.g, h->dp, fl.H32, fl.mask, zj, fl.y32, s, det_W<float>(h));
@@ -653,6 +664,7 @@ pfm_status fgm_finish(pfm_handle* h, Fgm& F) {
   F.g[j + 1] = -F.sn[j] * F.g[j];
   F.g[j] = F.cs[j] * F.g[j];
   F.relres = std::fabs(F.g[j + 1]) / F.beta0;
+  F.resest = std::fabs(F.g[j + 1]);
   const bool conv = std::fabs(F.g[j + 1]) <= F.tol;
   const bool happy = hnorm <= 1e-300;
   if (!conv && !happy && j + 1 < m && F.total < F.o.max_lin_it) {
@@ -666,7 +678,7 @@ pfm_status fgm_finish(pfm_handle* h, Fgm& F) {
     return PFM_OK;
   }
   TRY(fgm_update(h, F, j + 1));
-  if (conv) {
+  if (conv && !F.relax) {
     F.done = F.converged = true;
     return PFM_OK;
   }
@@ -674,9 +686,14 @@ pfm_status fgm_finish(pfm_handle* h, Fgm& F) {
     F.done = true;
     return PFM_OK;
   }
-  // restart from the true residual r = b - J x
-  TRY(japply_impl<double>(h, F.x, h->wv));
-  launch_sub<double>(n, F.b, h->wv, h->rv, s);
+  // restart from the true residual r = b - J x; with relaxed products this
+  // residual also decides convergence (the estimate followed inexact products)
+  if (F.relax) {
+    TRY(true_residual(h, F.b, F.x, h->rv));
+  } else {
+    TRY(japply_impl<double>(h, F.x, h->wv));
+    launch_sub<double>(n, F.b, h->wv, h->rv, s);
+  }
   TRY(norm2(h, h->rv, n, &F.beta));
   F.relres = F.beta / F.beta0;
   if (F.beta <= F.tol) {
@@ -692,7 +709,7 @@ pfm_status fgm_finish(pfm_handle* h, Fgm& F) {
 }
 
 pfm_status fgmres_impl(pfm_handle* h, const pfm_solve_opts& o, const double* b, double* x, int* its_out,
-                       double* relres_out) {
+                       double* relres_out, int* cycles_out = nullptr) {
   Fgm F;
   TRY(fgm_begin_enqueue(h, F, o, b, x));
   CK(cudaStreamSynchronize(h->stream));
@@ -705,6 +722,7 @@ pfm_status fgmres_impl(pfm_handle* h, const pfm_solve_opts& o, const double* b, 
   }
   if (its_out) *its_out = F.total;
   if (relres_out) *relres_out = F.relres;
+  if (cycles_out) *cycles_out = F.relax ? F.cycles : 0;
   return st;
 }
 
@@ -740,7 +758,7 @@ pfm_status true_residual(pfm_handle* h, const double* b, const double* x, double
 // Mixed-precision iterative refinement (GMRES-IR of Carson and Higham, 2018)
 // for J x = b, x0 = 0: each step solves J d = r approximately with one cycle
 // of FGMRES(m) whose operator is the FP32 tangent (and whose preconditioner is
-// the FP32 V-cycle), to max(inner_rtol ||r||, 0.3 lin_rtol ||b||), then
+// the FP32 V-cycle), to max(switch_rtol ||r||, 0.3 lin_rtol ||b||), then
 // x += d and r = b - J x with the FP64-class operator, until ||r|| <=
 // lin_rtol ||b|| (the true residual, Sec. 3.4) or max_lin_it inner iterations.
 pfm_status refine_impl(pfm_handle* h, const pfm_solve_opts& o, const double* b, double* x, int* its_out,
@@ -813,9 +831,8 @@ pfm_status refine_impl(pfm_handle* h, const pfm_solve_opts& o, const double* b, 
 // Linear solve of the Newton step with the options' method.
 pfm_status linear_solve(pfm_handle* h, const pfm_solve_opts& o, const double* b, double* x, int* its_out,
                         double* relres_out, int* outer_out) {
-  if (o.refine && o.precond == PFM_F32) return refine_impl(h, o, b, x, its_out, relres_out, outer_out);
-  if (outer_out) *outer_out = 0;
-  return fgmres_impl(h, o, b, x, its_out, relres_out);
+  if (o.krylov == 2 && o.precond == PFM_F32) return refine_impl(h, o, b, x, its_out, relres_out, outer_out);
+  return fgmres_impl(h, o, b, x, its_out, relres_out, outer_out);
 }
 
 // Capture the V-cycle on the handle's stream into a CUDA graph (once per
@@ -878,7 +895,7 @@ bool opts_valid(const pfm_solve_opts& o) {
          o.nu_post >= 0 && o.max_newton >= 1 && o.lin_rtol > 0 && o.omega > 0 &&
          (o.precond == PFM_F32 || o.precond == PFM_F64) && (o.smoother == 0 || o.smoother == 1) &&
          o.cheb_lo > 0 && o.cheb_hi > o.cheb_lo && (o.deterministic == 0 || o.deterministic == 1) &&
-         (o.refine == 0 || (o.refine == 1 && o.inner_rtol > 0 && o.inner_rtol < 1));
+         (o.krylov == 0 || ((o.krylov == 1 || o.krylov == 2) && o.switch_rtol > 0 && o.switch_rtol < 1));
 }
 
 }  // namespace
@@ -1102,7 +1119,6 @@ pfm_status pfm_set_deterministic(pfm_handle* h, int deterministic) {
   if (!h) return PFM_ERR_INVALID_ARG;
   if (deterministic != 0 && deterministic != 1) return h->fail(PFM_ERR_INVALID_ARG, "expected 0 or 1");
   h->det = deterministic != 0;
-  h->linearized = false;  // the coarse operator is assembled in the chosen form
   return PFM_OK;
 }
 
@@ -1609,6 +1625,7 @@ pfm_status pfm_batch_newton_solve(pfm_batch* b, const pfm_solve_opts* opts, doub
                                   pfm_solve_report* reports) {
   if (!b) return PFM_ERR_INVALID_ARG;
   if (!opts || !U_inout || !opts_valid(*opts)) return b->fail(PFM_ERR_INVALID_ARG, "bad options or state arrays");
+  if (opts->krylov == 2) return b->fail(PFM_ERR_INVALID_ARG, "batches run krylov modes 0 and 1");
   const int N = int(b->hs.size());
   for (int p = 0; p < N; ++p) {
     if (!b->hs[p]->have_state) return b->fail(PFM_ERR_STATE, "problem " + std::to_string(p) + " has no U_n");

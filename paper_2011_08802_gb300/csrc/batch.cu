@@ -1434,7 +1434,8 @@ bool engine_matches(const BatchEngine* E, const pfm_solve_opts& o) {
 }  // namespace
 
 bool batch_engine_supports(const pfm_solve_opts& o, const pfm_batch* b) {
-  if (o.precond != PFM_F32 || o.smoother != 0 || (o.cycle_gamma > 1) || o.restart > BMAXM || o.deterministic)
+  if (o.precond != PFM_F32 || o.smoother != 0 || (o.cycle_gamma > 1) || o.restart > BMAXM || o.deterministic ||
+      o.krylov != 0)
     return false;
   for (const pfm_handle* h : b->hs)
     if (!h->outer_df || h->contact_on || h->pre_h16 || h->det) return false;

@@ -11,6 +11,16 @@
  * geometric-multigrid V-cycle with point-block (9x9) Jacobi smoothing,
  * re-discretised coarse operators and a dense direct coarse solve (Sec. 3.4).
  *
+ * Number of variants. The model has phases 0..N (austenite and N martensite
+ * variants, Sec. 2.1); N = PFM_NV is fixed when the library is compiled:
+ * libpfm.so has N = 6 (the CuAlNi data of Sec. 5.1), libpfm_nv12.so N = 12
+ * (a NiTi-type set with 15 unknowns per node, the footnote of Sec. 5.4).
+ * A C caller compiles against this header with the same PFM_NV (default 6)
+ * and can check the library's value with pfm_variants(). Below, "[9]" and
+ * the figures 7 (phases), 15 (point unknowns) and 120 (Hessian entries) are
+ * those of N = 6; in general they are 3 + N, N + 1, 9 + N and
+ * (9 + N)(10 + N)/2.
+ *
  * Conventions shared by every entry point:
  *  - Units: GPa, nm, s.
  *  - Nodal vectors are field-major "[9][n_nodes]" arrays: fields 0..2 are the
@@ -36,6 +46,10 @@
 
 #include <stddef.h>
 #include <stdint.h>
+
+#ifndef PFM_NV
+#define PFM_NV 6 /* martensite variants N of the library this header describes */
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -67,15 +81,17 @@ typedef struct {
 } pfm_mesh_desc;
 
 /* Material and time-step data of the model (Sec. 2, Sec. 5.1).
- * Phase 0 is austenite, phases 1..6 the martensite variants. */
+ * Phase 0 is austenite, phases 1..N the martensite variants (N = PFM_NV). */
 typedef struct {
-  double Ut[7][9];       /* transformation stretch U_i^t, row-major; Ut[0] = I (Eq. LinMix) */
-  double Lvoigt[7][36];  /* stiffness L_i, 6x6 row-major Voigt matrix acting on the strain
-                            vector (e11,e22,e33,2e23,2e13,2e12) (Eq. elasticEn) */
-  double F0[7];          /* chemical energy F_i^0 (Sec. 2.2) */
-  double mobility[7];    /* m_i (Eq. RateDiss) */
-  double gamma[7][7];    /* interface energy gamma_ij, symmetric, diagonal ignored (Eq. IntEnergy) */
-  double ell[7][7];      /* interface thickness parameter ell_ij, symmetric (Eq. IntEnergy) */
+  double Ut[PFM_NV + 1][9];      /* transformation stretch U_i^t, row-major; Ut[0] = I (Eq. LinMix) */
+  double Lvoigt[PFM_NV + 1][36]; /* stiffness L_i, 6x6 row-major Voigt matrix acting on the strain
+                                    vector (e11,e22,e33,2e23,2e13,2e12) (Eq. elasticEn) */
+  double F0[PFM_NV + 1];         /* chemical energy F_i^0 (Sec. 2.2) */
+  double mobility[PFM_NV + 1];   /* m_i (Eq. RateDiss) */
+  double gamma[PFM_NV + 1][PFM_NV + 1]; /* interface energy gamma_ij, symmetric, diagonal ignored
+                                           (Eq. IntEnergy) */
+  double ell[PFM_NV + 1][PFM_NV + 1];   /* interface thickness parameter ell_ij, symmetric
+                                           (Eq. IntEnergy) */
   double eps_eta;        /* penalty eps_eta (Eq. PenPot) */
   double tau;            /* time increment tau (Sec. 2.3) */
   double gamma_scale;    /* multiplier of every gamma_ij (1 for the paper's data) */
@@ -133,6 +149,10 @@ typedef struct {
 
 /* Version string of the library. */
 const char* pfm_version(void);
+
+/* Number N of martensite variants the library was compiled for (PFM_NV):
+ * nodal vectors have 3 + N fields and pfm_params has N + 1 phases. */
+int pfm_variants(void);
 
 /* Create a problem on a structured grid with the given parameters and build
  * the multigrid level hierarchy (Sec. 3.4: uniform refinement hierarchy).

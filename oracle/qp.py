@@ -154,7 +154,15 @@ def material_from(constants: dict, tau: float, C=None, gamma_scale: float = 1.0,
                   hencky: str = "log") -> Material:
     """Material of Sec. 5.1 from raw constants. ``C`` optionally overrides
     (C11, C12, C44); ``gamma_scale`` multiplies every interface energy;
-    ``hencky`` selects the Hencky strain (exact or a Pade approximant)."""
+    ``hencky`` selects the Hencky strain (exact or a Pade approximant). When
+    the constants carry the stretches themselves (key "U", N + 1 matrices with
+    U[0] = I) any number N of variants is built (``material_variants``)."""
+    if "U" in constants:
+        mat = material_variants(constants, constants["U"], tau, hencky)
+        if C is not None:
+            mat.Lt[:] = cubic_stiffness(*C)
+        mat.gamma = gamma_scale * mat.gamma
+        return mat
     U = variant_stretches(constants["stretch_alpha"], constants["stretch_beta"],
                           constants["stretch_gamma"])
     C11, C12, C44 = C if C is not None else (constants["C11"], constants["C12"], constants["C44"])

@@ -33,12 +33,26 @@ class MeshDesc(C.Structure):
                 ("n_levels", C.c_int)]
 
 
-class Params(C.Structure):
-    _fields_ = [("Ut", (C.c_double * 9) * 7), ("Lvoigt", (C.c_double * 36) * 7),
-                ("F0", C.c_double * 7), ("mobility", C.c_double * 7),
-                ("gamma", (C.c_double * 7) * 7), ("ell", (C.c_double * 7) * 7),
-                ("eps_eta", C.c_double), ("tau", C.c_double), ("gamma_scale", C.c_double),
-                ("hencky", C.c_int)]
+def _params_class(n_var: int):
+    """ctypes layout of pfm_params for a library built with N = n_var variants
+    (N + 1 phases)."""
+    P = n_var + 1
+
+    class _Params(C.Structure):
+        _fields_ = [("Ut", (C.c_double * 9) * P), ("Lvoigt", (C.c_double * 36) * P),
+                    ("F0", C.c_double * P), ("mobility", C.c_double * P),
+                    ("gamma", (C.c_double * P) * P), ("ell", (C.c_double * P) * P),
+                    ("eps_eta", C.c_double), ("tau", C.c_double), ("gamma_scale", C.c_double),
+                    ("hencky", C.c_int)]
+        N_VAR = n_var
+
+    _Params.__name__ = _Params.__qualname__ = "Params" if n_var == 6 else f"Params{n_var}"
+    return _Params
+
+
+#: pfm_params of libpfm.so (N = 6) and of libpfm_nv12.so (N = 12)
+Params = _params_class(6)
+PARAMS = {6: Params, 12: _params_class(12)}
 
 
 # Hencky strain modes of pfm_params.hencky (Sec. 2.4)
@@ -74,34 +88,40 @@ def default_opts(precond: int = PFM_F32, **kw) -> SolveOpts:
 def params_from_material(constants: dict, tau: float, C_override=None,
                          gamma_scale: float = 1.0, hencky: str = "log") -> Params:
     """Fill the parameter block from the raw constants of Sec. 5.1: variant
-    stretches U_1..U_6 from (alpha, beta, gamma), the cubic Voigt stiffness
+    stretches U_1..U_6 from (alpha, beta, gamma), or all N + 1 stretches when
+    the constants carry them (key "U"; the block then has N + 1 phases for the
+    library built with N variants), the cubic Voigt stiffness
     from (C11, C12, C44) for every phase, gamma_0i = gamma_am,
     gamma_ij = gamma_mm, one ell, F_0 = F_a, F_i = F_m, one mobility;
     ``hencky`` names the Hencky strain ("log" or a Pade mode, Sec. 2.4)."""
-    al, be, ga = constants["stretch_alpha"], constants["stretch_beta"], constants["stretch_gamma"]
-    p, q = 0.5 * (al + ga), 0.5 * (al - ga)
-    U = [np.eye(3)]
-    for s in (1.0, -1.0):
-        U.append(np.array([[p, 0, s * q], [0, be, 0], [s * q, 0, p]]))
-    for s in (1.0, -1.0):
-        U.append(np.array([[p, s * q, 0], [s * q, p, 0], [0, 0, be]]))
-    for s in (1.0, -1.0):
-        U.append(np.array([[be, 0, 0], [0, p, s * q], [0, s * q, p]]))
+    if "U" in constants:  # the stretches themselves (any number N of variants)
+        U = [np.asarray(x, dtype=np.float64) for x in constants["U"]]
+    else:
+        al, be, ga = constants["stretch_alpha"], constants["stretch_beta"], constants["stretch_gamma"]
+        p, q = 0.5 * (al + ga), 0.5 * (al - ga)
+        U = [np.eye(3)]
+        for s in (1.0, -1.0):
+            U.append(np.array([[p, 0, s * q], [0, be, 0], [s * q, 0, p]]))
+        for s in (1.0, -1.0):
+            U.append(np.array([[p, s * q, 0], [s * q, p, 0], [0, 0, be]]))
+        for s in (1.0, -1.0):
+            U.append(np.array([[be, 0, 0], [0, p, s * q], [0, s * q, p]]))
+    n_ph = len(U)
     C11, C12, C44 = C_override if C_override is not None else (
         constants["C11"], constants["C12"], constants["C44"])
     Lv = np.zeros((6, 6))
     Lv[:3, :3] = C12
     np.fill_diagonal(Lv[:3, :3], C11)
     Lv[3, 3] = Lv[4, 4] = Lv[5, 5] = C44
-    P = Params()
-    for i in range(7):
+    P = PARAMS[n_ph - 1]()
+    for i in range(n_ph):
         for k in range(9):
             P.Ut[i][k] = U[i].reshape(9)[k]
         for k in range(36):
             P.Lvoigt[i][k] = Lv.reshape(36)[k]
         P.F0[i] = constants["F0_austenite"] if i == 0 else constants["F0_martensite"]
         P.mobility[i] = constants["mobility"]
-        for j in range(7):
+        for j in range(n_ph):
             g = 0.0 if i == j else (constants["gamma_am"] if (i == 0 or j == 0) else constants["gamma_mm"])
             P.gamma[i][j] = g
             P.ell[i][j] = constants["ell"]
@@ -169,23 +189,33 @@ def params_anisotropic(constants: dict, table: dict, tau: float, orientation=Non
     return P
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    """The loaded CUDA library (raises if it has not been built)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    if not os.path.exists(LIB_PATH):
+def lib_path(n_var: int = 6) -> str:
+    """Path of the library built for n_var variants."""
+    return LIB_PATH if n_var == 6 else os.path.join(LIB_DIR, f"nv{n_var}", f"libpfm_nv{n_var}.so")
+
+
+def lib(n_var: int = 6):
+    """The loaded CUDA library for n_var variants (6: libpfm.so, 12:
+    libpfm_nv12.so); raises if it has not been built."""
+    if n_var in _libs:
+        return _libs[n_var]
+    if n_var not in PARAMS:
+        raise ValueError(f"no library for {n_var} variants (built: {sorted(PARAMS)})")
+    path = lib_path(n_var)
+    if not os.path.exists(path):
         raise RuntimeError(
-            f"CUDA library {LIB_PATH} not built: run "
+            f"CUDA library {path} not built: run "
             "`python -c 'import __graft_entry__ as g; g.build()'` first")
-    L = C.CDLL(LIB_PATH)
+    L = C.CDLL(path)
+    Params = PARAMS[n_var]
     vp, i64, i32, dp = C.c_void_p, C.c_int64, C.c_int, C.c_double
     H = C.c_void_p
     sig = {
         "pfm_version": (C.c_char_p, []),
+        "pfm_variants": (C.c_int, []),
         "pfm_create": (i32, [C.POINTER(MeshDesc), C.POINTER(Params), C.POINTER(H)]),
         "pfm_destroy": (None, [H]),
         "pfm_last_error": (C.c_char_p, [H]),
@@ -232,14 +262,21 @@ def lib():
         f = getattr(L, name)
         f.restype = res
         f.argtypes = args
-    _lib = L
+    if L.pfm_variants() != n_var:
+        raise RuntimeError(f"{path} was built for {L.pfm_variants()} variants, not {n_var}")
+    _libs[n_var] = L
     return L
+
+
+def n_var_of(params) -> int:
+    """Number of variants of a parameter block (its library)."""
+    return type(params).N_VAR
 
 
 def exported_symbols():
     """Names of the entry points declared in include/pfm.h."""
     return [
-        "pfm_version", "pfm_create", "pfm_destroy", "pfm_last_error", "pfm_get_sizes",
+        "pfm_version", "pfm_variants", "pfm_create", "pfm_destroy", "pfm_last_error", "pfm_get_sizes",
         "pfm_set_stream", "pfm_get_level", "pfm_set_power_iterations", "pfm_set_outer_operator", "pfm_set_deterministic", "pfm_set_params", "pfm_set_dirichlet", "pfm_set_state", "pfm_get_state",
         "pfm_residual", "pfm_diagnostics", "pfm_set_contact", "pfm_contact_load", "pfm_set_linearize_arithmetic", "pfm_set_preconditioner_store", "pfm_linearize", "pfm_jacobian_apply", "pfm_jacobian_transpose_apply",
         "pfm_jacobian_apply_host", "pfm_jacobian_apply_mixed", "pfm_vcycle", "pfm_fgmres_solve", "pfm_newton_solve",

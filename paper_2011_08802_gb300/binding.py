@@ -44,11 +44,13 @@ def _prec(dtype) -> int:
 
 
 class Problem:
-    """One problem handle (``pfm_create``) on the current CUDA device."""
+    """One problem handle (``pfm_create``) on the current CUDA device, in the
+    library built for the parameter block's number of variants (6 or 12)."""
 
     def __init__(self, nx: int, ny: int, nz: int, Lx: float, Ly: float, Lz: float,
-                 params: abi.Params, n_levels: int = 0, stream=None):
-        L = abi.lib()
+                 params, n_levels: int = 0, stream=None):
+        self.n_var = abi.n_var_of(params)
+        L = abi.lib(self.n_var)
         self._lib = L
         desc = abi.MeshDesc(nx, ny, nz, Lx, Ly, Lz, n_levels)
         h = C.c_void_p()
@@ -60,7 +62,9 @@ class Problem:
         nn, ne, nl = C.c_int64(), C.c_int64(), C.c_int()
         self._check(L.pfm_get_sizes(h, C.byref(nn), C.byref(ne), C.byref(nl)))
         self.n_nodes, self.n_elems, self.n_levels = nn.value, ne.value, nl.value
-        self.shape = (9, self.n_nodes)
+        self.shape = (3 + self.n_var, self.n_nodes)
+        self.n_local = 9 + self.n_var                         # unknowns at a Gauss point
+        self.n_hess = self.n_local * (self.n_local + 1) // 2  # packed Hessian entries
         self.set_stream(stream if stream is not None else torch.cuda.current_stream())
 
     # -- helpers ---------------------------------------------------------
@@ -221,8 +225,8 @@ class Problem:
     def qp_eval(self, F: torch.Tensor, eta: torch.Tensor, eta_n: torch.Tensor, hessian: bool = True):
         n = F.shape[0]
         W = torch.empty(n, dtype=torch.float64, device="cuda")
-        g = torch.empty(n, 15, dtype=torch.float64, device="cuda")
-        H = torch.empty(n, 120, dtype=torch.float64, device="cuda") if hessian else None
+        g = torch.empty(n, self.n_local, dtype=torch.float64, device="cuda")
+        H = torch.empty(n, self.n_hess, dtype=torch.float64, device="cuda") if hessian else None
         self._check(self._lib.pfm_qp_eval(self.h, n, _ptr(F), _ptr(eta), _ptr(eta_n), _ptr(W), _ptr(g), _ptr(H)))
         return W, g, H
 
@@ -243,7 +247,7 @@ class Problem:
         return n.value, ms.value
 
     def get_hessians(self, e0: int, count: int) -> np.ndarray:
-        out = np.empty((count, 8, 120))
+        out = np.empty((count, 8, self.n_hess))
         self._check(self._lib.pfm_get_hessians(self.h, e0, count, _ptr(out)))
         return out
 
@@ -252,9 +256,9 @@ class Batch:
     """``pfm_batch_create`` over existing problems (which must outlive it)."""
 
     def __init__(self, problems):
-        L = abi.lib()
-        self._lib = L
         self.problems = list(problems)
+        L = abi.lib(self.problems[0].n_var if self.problems else 6)
+        self._lib = L
         arr = (C.c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
         b = C.c_void_p()
         st = L.pfm_batch_create(arr, len(self.problems), C.byref(b))
@@ -293,7 +297,7 @@ def residual_noalloc(mesh, params: abi.Params, mask: torch.Tensor, U: torch.Tens
     """``pfm_residual_noalloc``: residual and potential without a handle and
     without device allocation by the library (R is allocated here by torch
     only when the caller passes none). Returns (R, energy)."""
-    L = abi.lib()
+    L = abi.lib(abi.n_var_of(params))
     R = torch.empty_like(U) if R is None else R
     desc = abi.MeshDesc(mesh.nx, mesh.ny, mesh.nz, mesh.Lx, mesh.Ly, mesh.Lz, 0)
     e = C.c_double()
@@ -321,7 +325,7 @@ def levels_to(n: int, coarsest: int = 4) -> int:
     return levels
 
 
-def problem_from_state(state, n_levels: int = 0, params: abi.Params | None = None) -> Problem:
+def problem_from_state(state, n_levels: int = 0, params=None) -> Problem:
     """Create a handle for an ``inputs.State`` and load its mask and state."""
     m = state.mesh
     if params is None:

@@ -1,6 +1,7 @@
-"""Build of libpfm.so: every CUDA translation unit compiled for sm_103a in
-parallel with nvcc, then linked into a shared library in-tree
-(``paper_2011_08802_gb300/_lib/libpfm.so``)."""
+"""Build of libpfm.so (N = 6 variants) and libpfm_nv12.so (N = 12): every CUDA
+translation unit compiled for sm_103a in parallel with nvcc, once per variant
+count, then linked into shared libraries in-tree
+(``paper_2011_08802_gb300/_lib/libpfm.so``, ``_lib/nv12/libpfm_nv12.so``)."""
 from __future__ import annotations
 
 import os
@@ -23,34 +24,53 @@ def nvcc() -> str:
     return "nvcc"
 
 
+# Libraries built by default: the variant count N of the model is a
+# compile-time constant (PFM_NV); N = 6 is the CuAlNi data of Sec. 5.1 and
+# N = 12 a NiTi-type variant set (15 unknowns per node).
+VARIANTS = {6: ("libpfm.so", ""), 12: ("libpfm_nv12.so", "nv12")}
+
+
+def lib_path(n_var: int = 6) -> str:
+    name, sub = VARIANTS[n_var]
+    return os.path.join(OUT, sub, name)
+
+
 def build(verbose: bool = False, ptxas_info: bool = False, out_dir: str | None = None,
-          defines: tuple = ()) -> str:
-    """Compile and link; ``out_dir``/``defines`` build a variant elsewhere
-    (e.g. a launch-configuration sweep) without touching the in-tree library."""
-    out = out_dir or OUT
-    os.makedirs(out, exist_ok=True)
-    objs, procs = [], []
-    for src in SOURCES:
-        obj = os.path.join(out, src.replace(".cu", ".o"))
-        cmd = [nvcc(), *ARCH, *FLAGS, *[f"-D{d}" for d in defines], "-c", os.path.join(CSRC, src), "-o", obj]
-        if ptxas_info:
-            cmd.insert(1, "-Xptxas=-v")
-        objs.append(obj)
-        procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+          defines: tuple = (), n_vars: tuple = (6, 12)) -> str:
+    """Compile and link one library per variant count in ``n_vars`` (all
+    translation units of all of them compiled in parallel); ``out_dir`` and
+    ``defines`` build a variant elsewhere (e.g. a launch-configuration sweep)
+    without touching the in-tree libraries. Returns the N = 6 library path
+    (or the first one built)."""
+    jobs = []
+    for nv in n_vars:
+        name, sub = VARIANTS[nv]
+        out = os.path.join(out_dir or OUT, sub)
+        os.makedirs(out, exist_ok=True)
+        objs = []
+        for src in SOURCES:
+            obj = os.path.join(out, src.replace(".cu", ".o"))
+            cmd = [nvcc(), *ARCH, *FLAGS, f"-DPFM_NV={nv}", *[f"-D{d}" for d in defines], "-c",
+                   os.path.join(CSRC, src), "-o", obj]
+            if ptxas_info:
+                cmd.insert(1, "-Xptxas=-v")
+            objs.append((src, obj, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        jobs.append((os.path.join(out, name), objs))
     failed = []
-    for src, p in procs:
-        log, _ = p.communicate()
-        if verbose or p.returncode != 0 or ptxas_info:
-            sys.stdout.write(log.decode(errors="replace"))
-        if p.returncode != 0:
-            failed.append(src)
+    for _, objs in jobs:
+        for src, _, p in objs:
+            log, _ = p.communicate()
+            if verbose or p.returncode != 0 or ptxas_info:
+                sys.stdout.write(log.decode(errors="replace"))
+            if p.returncode != 0:
+                failed.append(src)
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
-    lib = os.path.join(out, "libpfm.so")
-    tmp = lib + ".tmp"
-    subprocess.check_call([nvcc(), *ARCH, "-shared", *objs, "-o", tmp, "-lcudart"])
-    os.replace(tmp, lib)
-    return lib
+    for lib, objs in jobs:
+        tmp = lib + ".tmp"
+        subprocess.check_call([nvcc(), *ARCH, "-shared", *[o for _, o, _ in objs], "-o", tmp, "-lcudart"])
+        os.replace(tmp, lib)
+    return jobs[0][0]
 
 
 if __name__ == "__main__":

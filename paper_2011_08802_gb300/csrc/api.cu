@@ -371,8 +371,8 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
     CKL();
     if (coarsest) continue;
     if (prec == PFM_F32) {
-      TRY(dalloc(h, &lv.D32, size_t(81) * lv.nn));
-      TRY(bd_scratch(h, size_t(45) * 32 * lv.nblk * sizeof(float)));
+      TRY(dalloc(h, &lv.D32, size_t(NF2) * lv.nn));
+      TRY(bd_scratch(h, size_t(NBD) * 32 * lv.nblk * sizeof(float)));
       launch_blockdiag<float>(lv.g, h->dp, lv.H32, lv.mask, lv.D32, static_cast<float*>(h->bd_scratch), s);
       if (h->contact_on) launch_contact_blockdiag<float>(lv.g, lv.Kc32, lv.D32, s);
       launch_block_invert<float>(lv.nn, lv.mask, lv.D32, h->flag_dev, s);
@@ -380,8 +380,8 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
       TRY(ensure_level_vectors<float>(h));
       TRY(estimate_lambda<float>(h, l));
     } else {
-      TRY(dalloc(h, &lv.D64, size_t(81) * lv.nn));
-      TRY(bd_scratch(h, size_t(45) * 32 * lv.nblk * sizeof(double)));
+      TRY(dalloc(h, &lv.D64, size_t(NF2) * lv.nn));
+      TRY(bd_scratch(h, size_t(NBD) * 32 * lv.nblk * sizeof(double)));
       launch_blockdiag<double>(lv.g, h->dp, lv.H64, lv.mask, lv.D64, static_cast<double*>(h->bd_scratch), s);
       if (h->contact_on) launch_contact_blockdiag<double>(lv.g, lv.Kc64, lv.D64, s);
       launch_block_invert<double>(lv.nn, lv.mask, lv.D64, h->flag_dev, s);
@@ -980,7 +980,9 @@ pfm_status japply_host_pipelined(pfm_handle* h, const void* v_host, void* y_host
 
 extern "C" {
 
-const char* pfm_version(void) { return "pfm 0.1 (sm_103a)"; }
+const char* pfm_version(void) { return "pfm 0.2 (sm_103a)"; }
+
+int pfm_variants(void) { return NV; }
 
 pfm_status pfm_create(const pfm_mesh_desc* mesh, const pfm_params* params, pfm_handle** out) {
   if (!mesh || !params || !out) {

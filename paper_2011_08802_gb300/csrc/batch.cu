@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(128) k_b_linearize(const BLin* __restrict__ S,
 __global__ void k_b_zero_D(const BBd* __restrict__ S, Gate on) {
   const BBd& L = S[blockIdx.y];
   if (!on(L.problem)) return;
-  const int64_t n = 81 * L.g.nn();
+  const int64_t n = NF2 * L.g.nn();
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     L.D[i] = 0.f;
 }
@@ -350,7 +350,7 @@ __global__ void k_b_dinv(const BLev* __restrict__ S, Gate on) {
     for (int f = 0; f < NF; ++f) {
       float s = 0.f;
 #pragma unroll
-      for (int c = 0; c < NF; ++c) s += L.D[(f * 9 + c) * nn + node] * yv[c];
+      for (int c = 0; c < NF; ++c) s += L.D[(f * NF + c) * nn + node] * yv[c];
       r[f * nn + node] = s;
     }
   }
@@ -909,7 +909,7 @@ pfm_status engine_buffers(pfm_handle* h, int m) {
     if (fine || coarsest) TRY(dalloc(h, &lv.H64, hsz));
     if (fine || !coarsest) TRY(dalloc(h, &lv.H32, hsz));
     if (fine) TRY(dalloc(h, &lv.H32lo, hsz));
-    if (!coarsest) TRY(dalloc(h, &lv.D32, size_t(81) * lv.nn));
+    if (!coarsest) TRY(dalloc(h, &lv.D32, size_t(NF2) * lv.nn));
     TRY(dalloc(h, &lv.x32, ndof(lv)));
     TRY(dalloc(h, &lv.b32, ndof(lv)));
     TRY(dalloc(h, &lv.y32, ndof(lv)));
@@ -1195,7 +1195,7 @@ pfm_status eng_linearize(pfm_batch* b, BatchEngine* E, int power_its) {
   }
   const int nA = int(E->A.size());
   if (nA > 0) {
-    k_b_zero_D<<<grid2(81 * E->maxnnBd, nA), BT, 0, s>>>(E->dBd, g);
+    k_b_zero_D<<<grid2(NF2 * E->maxnnBd, nA), BT, 0, s>>>(E->dBd, g);
     k_b_blockdiag<<<gdiv(E->neBd * 8, 128), 128, 0, s>>>(E->dBd, nA, E->neBd, g);
     k_b_block_invert<<<grid2(E->maxnnBd, nA), BT, 0, s>>>(E->dBd, E->singular, g);
     count_launches(3);

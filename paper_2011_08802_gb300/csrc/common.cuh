@@ -10,7 +10,10 @@
 
 namespace pfm {
 
-constexpr int NF = 9;  // unknowns per node: u (3) + eta_hat (6)
+constexpr int NF = 3 + NV;          // unknowns per node: u (3) + eta_hat (N): 9 for N = 6
+constexpr int NBD = NF * (NF + 1) / 2;  // packed upper triangle of a nodal NF x NF block (45)
+constexpr int NF2 = NF * NF;            // entries of a nodal block (81)
+constexpr int NED = 8 * NF;             // unknowns of one element (72)
 
 // Gauss points of the 2-point rule mapped to [0,1]: (1 -+ 1/sqrt(3)) / 2.
 constexpr double GA = 0.21132486540518711775;
@@ -28,18 +31,22 @@ struct Grid {
 };
 
 // Gauss-point Hessian store: element blocks of 4, lane = 8*(e%4) + q, and per
-// lane the 120 packed entries in 16-byte vectors of V = 16/sizeof(S) entries:
-// offset ((blk*(120/V) + entry/V)*32 + lane)*V + entry%V. One warp therefore
+// lane the NH packed entries (120 for N = 6), padded with zeros to NHP, in
+// 16-byte vectors of V = 16/sizeof(S) entries:
+// offset ((blk*(NHP/V) + entry/V)*32 + lane)*V + entry%V. One warp therefore
 // reads 512 contiguous bytes per vector load.
 template <typename S>
 __host__ __device__ inline int64_t hstore_offset(int64_t blk, int entry, int lane) {
   constexpr int V = 16 / sizeof(S);
-  return ((blk * (NH / V) + entry / V) * 32 + lane) * V + entry % V;
+  return ((blk * (NHP / V) + entry / V) * 32 + lane) * V + entry % V;
 }
-constexpr int64_t HBLK = int64_t(NH) * 32;  // entries per element block
+constexpr int64_t HBLK = int64_t(NHP) * 32;  // entries per element block
 
 // Per-node Dirichlet bit mask (bit f set = DOF f prescribed).
 using dmask_t = uint16_t;
+static_assert(NF <= 16, "one 16-bit Dirichlet mask per node");
+constexpr dmask_t MASK_ALL = dmask_t((1u << NF) - 1u);  // every field
+constexpr dmask_t MASK_ETA = dmask_t(MASK_ALL & ~7u);    // the order-parameter fields
 
 }  // namespace pfm
 
@@ -82,7 +89,7 @@ void launch_identity_rows(int64_t nn, const dmask_t* mask, const T* v, T* y, int
 int japply_range_blocks();  // persistent grid of k_japply_range
 template <typename T>
 void launch_blockdiag(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, T* D, T* W,
-                      cudaStream_t s);  // W: scratch of 45 * 32 * nblk entries
+                      cudaStream_t s);  // W: scratch of NBD * 32 * nblk entries
 template <typename T>
 void launch_block_invert(int64_t nn, const dmask_t* mask, T* D, int* singular, cudaStream_t s);
 void launch_qp_eval(const DevParams& P, int64_t n, const double* F, const double* eta,

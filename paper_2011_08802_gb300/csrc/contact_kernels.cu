@@ -175,7 +175,7 @@ __global__ void k_contact_blockdiag(Grid g, const T* __restrict__ K, T* __restri
 #pragma unroll
       for (int cc = 0; cc < 3; ++cc) {
         const T val = Kq[sv[r][cc]];
-        if (val != T(0)) atomicAdd(&D[(r * 9 + cc) * nn + s.node[a]], T(w * s.N[a] * s.N[a]) * val);
+        if (val != T(0)) atomicAdd(&D[(r * NF + cc) * nn + s.node[a]], T(w * s.N[a] * s.N[a]) * val);
       }
 }
 

@@ -1,11 +1,11 @@
 // Microstructure diagnostics of Sec. 5.3 on the nodal state: the violation
-// index I_v = sum_{i=0}^{6} |<eta_i>_-| of the constraints eta_i >= 0, the
-// diffuseness index I_d = 1 - sum_{i=0}^{6} eta_i^4 and the composite
+// index I_v = sum_{i=0}^{N} |<eta_i>_-| of the constraints eta_i >= 0, the
+// diffuseness index I_d = 1 - sum_{i=0}^{N} eta_i^4 and the composite
 // parameter eta* = eta_3 - eta_1, with eta_0 = 1 - sum_k eta_k (Sec. 3.1);
 // and, per horizontal plane z = k h_z, the mean and the maximum of I_v and of
 // I_d over its nodes (the paper plots both against z).
 //
-// HBM-bound: 6 FP64 loads per node (48 B) plus the optional per-node outputs.
+// HBM-bound: N FP64 loads per node (48 B for N = 6) plus the optional per-node outputs.
 // Grid (chunks, planes): a block reduces one contiguous chunk of one plane in
 // a fixed order (strided per thread, then a fixed shuffle tree), and a second
 // kernel sums the chunks of each plane in order, so results are bitwise
@@ -23,7 +23,7 @@ __device__ inline void diag_node(const double* __restrict__ U, int64_t nn, int64
   double eta[NPH];
   double s = 0.0;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < NV; ++k) {
     eta[k + 1] = U[int64_t(3 + k) * nn + n];
     s += eta[k + 1];
   }

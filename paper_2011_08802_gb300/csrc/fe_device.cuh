@@ -91,8 +91,9 @@ __host__ __device__ constexpr int packed_row(int idx) {
   while (r + 1 < NZ && idx >= packed_row_start(r + 1)) ++r;
   return r;
 }
-static_assert(packed_row(0) == 0 && packed_row(14) == 0 && packed_row(15) == 1 && packed_row(20) == 1 &&
-                  packed_row(119) == 14 && packed_row(117) == 13 && packed_row(116) == 12,
+static_assert(packed_row(0) == 0 && packed_row(NZ - 1) == 0 && packed_row(NZ) == 1 &&
+                  packed_row(2 * NZ - 2) == 1 && packed_row(NH - 1) == NZ - 1 && packed_row(NH - 2) == NZ - 2 &&
+                  packed_row(NH - 3) == NZ - 2 && packed_row(NH - 4) == NZ - 3,
               "packed index decode");
 
 __device__ __forceinline__ int64_t elem_node(const Grid& g, int64_t e, int a) {
@@ -107,7 +108,7 @@ __device__ __forceinline__ int64_t elem_node(const Grid& g, int64_t e, int a) {
 template <typename T, typename Src>
 __device__ __forceinline__ void gather_state(const Src* __restrict__ U, int64_t nn, int64_t node,
                                              bool valid, int l8, T ihx, T ihy, T ihz, T F[9],
-                                             T eh[6], T ge[18]) {
+                                             T eh[NV], T ge[3 * NV]) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     T v = valid ? T(U[i * nn + node]) : T(0);
@@ -121,7 +122,7 @@ __device__ __forceinline__ void gather_state(const Src* __restrict__ U, int64_t 
   F[4] += T(1);
   F[8] += T(1);
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < NV; ++k) {
     T v = valid ? T(U[(3 + k) * nn + node]) : T(0);
     q1_gather(v, l8, ihx, ihy, ihz, eh[k], ge[3 * k], ge[3 * k + 1], ge[3 * k + 2]);
   }
@@ -160,7 +161,7 @@ template <> struct Vec16<__half> {
 
 template <typename T>
 struct JParams {
-  T G[6][6];
+  T G[NV][NV];
   T w, ihx, ihy, ihz;
 };
 
@@ -179,27 +180,27 @@ __device__ __forceinline__ void linearize_lane(const Grid& g, const DevParams& P
   const int64_t nn = g.nn();
   const int64_t node = valid ? elem_node(g, e, l8) : 0;
   const TC ihx = TC(1.0 / g.hx), ihy = TC(1.0 / g.hy), ihz = TC(1.0 / g.hz);
-  TC F[9], eh[6], ge[18], ehn[6];
+  TC F[9], eh[NV], ge[3 * NV], ehn[NV];
   gather_state<TC>(U, nn, node, valid, l8, ihx, ihy, ihz, F, eh, ge);
 #pragma unroll
-  for (int k = 0; k < 6; ++k) ehn[k] = q1_value(valid ? TC(Un[(3 + k) * nn + node]) : TC(0));
+  for (int k = 0; k < NV; ++k) ehn[k] = q1_value(valid ? TC(Un[(3 + k) * nn + node]) : TC(0));
   TC W, gr[NZ], Hp[NH];
   qp_local<TC, true>(P, F, eh, ehn, &W, gr, Hp);
-  for (int j = 0; j < NH; ++j) {
-    const double h = valid ? double(Hp[j]) : 0.0;
+  for (int j = 0; j < NHP; ++j) {  // padding entries NH..NHP-1 are stored as zeros
+    const double h = (valid && j < NH) ? double(Hp[j < NH ? j : 0]) : 0.0;
     if (H64) H64[hstore_offset<double>(blk, j, lane)] = h;
     if (H32) H32[hstore_offset<float>(blk, j, lane)] = float(h);
     if (H32lo) H32lo[hstore_offset<float>(blk, j, lane)] = float(h - double(float(h)));
   }
 }
 
-// Nodal 9x9 diagonal blocks. For local node a of the element whose Gauss-point
-// Hessians sit in store block blk at lanes lane0..lane0+7, add to Db (upper
-// triangle, row-major, 45 entries) the sum over the 8 points of
-// w B_a(q)^T H_q B_a(q) plus the gradient-energy block.
+// Nodal NF x NF diagonal blocks (9 x 9 for N = 6). For local node a of the
+// element whose Gauss-point Hessians sit in store block blk at lanes
+// lane0..lane0+7, add to Db (upper triangle, row-major, NBD entries) the sum
+// over the 8 points of w B_a(q)^T H_q B_a(q) plus the gradient-energy block.
 template <typename T>
 __device__ __forceinline__ void blockdiag_accumulate(const JParams<T>& jp, const T* __restrict__ H, int64_t blk,
-                                                     int lane0, int a, T Db[45]) {
+                                                     int lane0, int a, T Db[NBD]) {
   constexpr int V = 16 / sizeof(T);
   using VT = typename Vec16<T>::type;
   const T ih[3] = {jp.ihx, jp.ihy, jp.ihz};
@@ -214,16 +215,16 @@ __device__ __forceinline__ void blockdiag_accumulate(const JParams<T>& jp, const
     const T N = phi[0] * phi[1] * phi[2];
     const T dN[3] = {dphi[0] * phi[1] * phi[2], phi[0] * dphi[1] * phi[2], phi[0] * phi[1] * dphi[2]};
     // column map: DOF u_i -> z rows 3i+J (coef dN_J); eta_k -> z row 9+k (coef N)
-    T Hq[NH];
-    const VT* Hv = reinterpret_cast<const VT*>(H) + blk * (NH / V) * 32 + lane0 + q;
+    T Hq[NHP];
+    const VT* Hv = reinterpret_cast<const VT*>(H) + blk * (NHP / V) * 32 + lane0 + q;
 #pragma unroll
-    for (int jj = 0; jj < NH / V; ++jj) Vec16<T>::unpack(Hv[jj * 32], Hq + jj * V);
+    for (int jj = 0; jj < NHP / V; ++jj) Vec16<T>::unpack(Hv[jj * 32], Hq + jj * V);
     const T g2 = dN[0] * dN[0] + dN[1] * dN[1] + dN[2] * dN[2];
     int idx = 0;
 #pragma unroll
-    for (int r = 0; r < 9; ++r)
+    for (int r = 0; r < NF; ++r)
 #pragma unroll
-      for (int c = r; c < 9; ++c) {
+      for (int c = r; c < NF; ++c) {
         T s = T(0);
         if (r < 3 && c < 3) {
 #pragma unroll
@@ -245,68 +246,68 @@ __device__ __forceinline__ void blockdiag_accumulate(const JParams<T>& jp, const
 }
 
 // (element e, local node a): its element's contribution added to the node's
-// block D[(r*9+c)*nn + node] with atomics (batched engine).
+// block D[(r*NF+c)*nn + node] with atomics (batched engine).
 template <typename T>
 __device__ __forceinline__ void blockdiag_elem_node(const Grid& g, const JParams<T>& jp, const T* __restrict__ H,
                                                     T* __restrict__ D, int64_t e, int a) {
   const int64_t nn = g.nn();
   const int64_t node = elem_node(g, e, a);
-  T Db[45];
+  T Db[NBD];
 #pragma unroll
-  for (int i = 0; i < 45; ++i) Db[i] = T(0);
+  for (int i = 0; i < NBD; ++i) Db[i] = T(0);
   blockdiag_accumulate<T>(jp, H, e >> 2, int(e & 3) * 8, a, Db);
   int idx = 0;
-  for (int r = 0; r < 9; ++r)
-    for (int c = r; c < 9; ++c) {
-      atomicAdd(&D[(r * 9 + c) * nn + node], Db[idx]);
-      if (c != r) atomicAdd(&D[(c * 9 + r) * nn + node], Db[idx]);
+  for (int r = 0; r < NF; ++r)
+    for (int c = r; c < NF; ++c) {
+      atomicAdd(&D[(r * NF + c) * nn + node], Db[idx]);
+      if (c != r) atomicAdd(&D[(c * NF + r) * nn + node], Db[idx]);
       ++idx;
     }
 }
 
-// In-place inverse of one node's 9x9 block (Dirichlet rows/columns replaced
+// In-place inverse of one node's NF x NF block (Dirichlet rows/columns replaced
 // by identity first) by Gauss-Jordan elimination with partial pivoting; a
 // singular block sets *singular and is replaced by the identity.
 template <typename T>
 __device__ __forceinline__ void block_invert_node(int64_t nn, const dmask_t* __restrict__ mask, T* __restrict__ D,
                                                   int* singular, int64_t node) {
   const dmask_t dm = mask[node];
-  T a[9][9], x[9][9];
-  for (int r = 0; r < 9; ++r)
-    for (int c = 0; c < 9; ++c) {
-      T v = D[(r * 9 + c) * nn + node];
+  T a[NF][NF], x[NF][NF];
+  for (int r = 0; r < NF; ++r)
+    for (int c = 0; c < NF; ++c) {
+      T v = D[(r * NF + c) * nn + node];
       if (((dm >> r) & 1) || ((dm >> c) & 1)) v = (r == c) ? T(1) : T(0);
       a[r][c] = v;
       x[r][c] = (r == c) ? T(1) : T(0);
     }
   bool bad = false;
-  for (int k = 0; k < 9; ++k) {
+  for (int k = 0; k < NF; ++k) {
     int p = k;
     T best = fabs(a[k][k]);
-    for (int r = k + 1; r < 9; ++r)
+    for (int r = k + 1; r < NF; ++r)
       if (fabs(a[r][k]) > best) { best = fabs(a[r][k]); p = r; }
     if (!(best > T(0))) { bad = true; break; }
     if (p != k)
-      for (int c = 0; c < 9; ++c) {
+      for (int c = 0; c < NF; ++c) {
         T t = a[k][c]; a[k][c] = a[p][c]; a[p][c] = t;
         t = x[k][c]; x[k][c] = x[p][c]; x[p][c] = t;
       }
     const T ip = T(1) / a[k][k];
-    for (int c = 0; c < 9; ++c) { a[k][c] *= ip; x[k][c] *= ip; }
-    for (int r = 0; r < 9; ++r) {
+    for (int c = 0; c < NF; ++c) { a[k][c] *= ip; x[k][c] *= ip; }
+    for (int r = 0; r < NF; ++r) {
       if (r == k) continue;
       const T f = a[r][k];
       if (f == T(0)) continue;
-      for (int c = 0; c < 9; ++c) { a[r][c] -= f * a[k][c]; x[r][c] -= f * x[k][c]; }
+      for (int c = 0; c < NF; ++c) { a[r][c] -= f * a[k][c]; x[r][c] -= f * x[k][c]; }
     }
   }
   if (bad) {
     atomicExch(singular, 1);
-    for (int r = 0; r < 9; ++r)
-      for (int c = 0; c < 9; ++c) x[r][c] = (r == c) ? T(1) : T(0);
+    for (int r = 0; r < NF; ++r)
+      for (int c = 0; c < NF; ++c) x[r][c] = (r == c) ? T(1) : T(0);
   }
-  for (int r = 0; r < 9; ++r)
-    for (int c = 0; c < 9; ++c) D[(r * 9 + c) * nn + node] = x[r][c];
+  for (int r = 0; r < NF; ++r)
+    for (int c = 0; c < NF; ++c) D[(r * NF + c) * nn + node] = x[r][c];
 }
 
 // Element constants of a level: gradient-energy matrix, quadrature weight and
@@ -314,8 +315,8 @@ __device__ __forceinline__ void block_invert_node(int64_t nn, const dmask_t* __r
 template <typename T>
 inline JParams<T> make_jparams(const Grid& g, const DevParams& P) {
   JParams<T> jp;
-  for (int k = 0; k < 6; ++k)
-    for (int l = 0; l < 6; ++l) jp.G[k][l] = T(P.G[k][l]);
+  for (int k = 0; k < NV; ++k)
+    for (int l = 0; l < NV; ++l) jp.G[k][l] = T(P.G[k][l]);
   jp.w = T(g.w());
   jp.ihx = T(1.0 / g.hx);
   jp.ihy = T(1.0 / g.hy);
@@ -355,8 +356,8 @@ __device__ __forceinline__ void japply_block(const Grid& g, const JParams<T>& jp
   const int64_t e = blk * 4 + (lane >> 3);
   const bool valid = e < g.ne();
   const int64_t node = valid ? elem_node(g, e, l8) : 0;
-  const dmask_t dm = valid ? mask[node] : dmask_t(0x1ff);
-  T dz[NZ], ge[18];
+  const dmask_t dm = valid ? mask[node] : MASK_ALL;
+  T dz[NZ], ge[3 * NV];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     T x = ((dm >> i) & 1) ? T(0) : v[i * nn + node];
@@ -364,7 +365,7 @@ __device__ __forceinline__ void japply_block(const Grid& g, const JParams<T>& jp
     q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, val, dz[3 * i], dz[3 * i + 1], dz[3 * i + 2]);
   }
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < NV; ++k) {
     T x = ((dm >> (3 + k)) & 1) ? T(0) : v[(3 + k) * nn + node];
     q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, dz[9 + k], ge[3 * k], ge[3 * k + 1], ge[3 * k + 2]);
   }
@@ -372,14 +373,15 @@ __device__ __forceinline__ void japply_block(const Grid& g, const JParams<T>& jp
   T sg[NZ];
 #pragma unroll
   for (int r = 0; r < NZ; ++r) sg[r] = T(0);
-  const VT* Hv = reinterpret_cast<const VT*>(H) + blk * (NH / V) * 32 + lane;
+  const VT* Hv = reinterpret_cast<const VT*>(H) + blk * (NHP / V) * 32 + lane;
 #pragma unroll
-  for (int j = 0; j < NH / V; ++j) {
+  for (int j = 0; j < NHP / V; ++j) {
     T hv[V];
     Vec16<T>::unpack(__ldcs(Hv + j * 32), hv);
 #pragma unroll
     for (int t = 0; t < V; ++t) {
       const int idx = j * V + t;
+      if (idx >= NH) continue;  // zero padding of the store
       // (r, c) of packed index idx (constant-folded after unrolling)
       const int r = packed_row(idx);
       const int c = r + (idx - packed_row_start(r));
@@ -394,13 +396,13 @@ __device__ __forceinline__ void japply_block(const Grid& g, const JParams<T>& jp
     scatter_row<DET>(y, W, ws, i, blk, lane, i * nn + node, r, valid && !((dm >> i) & 1));
   }
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < NV; ++k) {
     T gf[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       T s = T(0);
 #pragma unroll
-      for (int l = 0; l < 6; ++l) s += jp.G[k][l] * ge[3 * l + d];
+      for (int l = 0; l < NV; ++l) s += jp.G[k][l] * ge[3 * l + d];
       gf[d] = w * s;
     }
     T r = q1_scatter(w * sg[9 + k], gf[0], gf[1], gf[2], l8, jp.ihx, jp.ihy, jp.ihz);
@@ -424,8 +426,8 @@ __device__ __forceinline__ void japply_block_h16(const Grid& g, const JParams<fl
   const int64_t e = blk * 4 + (lane >> 3);
   const bool valid = e < g.ne();
   const int64_t node = valid ? elem_node(g, e, l8) : 0;
-  const dmask_t dm = valid ? mask[node] : dmask_t(0x1ff);
-  float dz[NZ], ge[18];
+  const dmask_t dm = valid ? mask[node] : MASK_ALL;
+  float dz[NZ], ge[3 * NV];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     float x = ((dm >> i) & 1) ? 0.f : v[i * nn + node];
@@ -433,21 +435,22 @@ __device__ __forceinline__ void japply_block_h16(const Grid& g, const JParams<fl
     q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, val, dz[3 * i], dz[3 * i + 1], dz[3 * i + 2]);
   }
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < NV; ++k) {
     float x = ((dm >> (3 + k)) & 1) ? 0.f : v[(3 + k) * nn + node];
     q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, dz[9 + k], ge[3 * k], ge[3 * k + 1], ge[3 * k + 2]);
   }
   float sg[NZ];
 #pragma unroll
   for (int r = 0; r < NZ; ++r) sg[r] = 0.f;
-  const uint4* Hv = reinterpret_cast<const uint4*>(H) + blk * (NH / V) * 32 + lane;
+  const uint4* Hv = reinterpret_cast<const uint4*>(H) + blk * (NHP / V) * 32 + lane;
 #pragma unroll
-  for (int j = 0; j < NH / V; ++j) {
+  for (int j = 0; j < NHP / V; ++j) {
     float hv[V];
     Vec16<__half>::unpack(__ldcs(Hv + j * 32), hv);
 #pragma unroll
     for (int t = 0; t < V; ++t) {
       const int idx = j * V + t;
+      if (idx >= NH) continue;  // zero padding of the store
       const int r = packed_row(idx);
       const int c = r + (idx - packed_row_start(r));
       sg[r] += hv[t] * dz[c];
@@ -461,13 +464,13 @@ __device__ __forceinline__ void japply_block_h16(const Grid& g, const JParams<fl
     scatter_row<DET>(y, W, ws, i, blk, lane, i * nn + node, r, valid && !((dm >> i) & 1));
   }
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < NV; ++k) {
     float gf[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       float s = 0.f;
 #pragma unroll
-      for (int l = 0; l < 6; ++l) s += jp.G[k][l] * ge[3 * l + d];
+      for (int l = 0; l < NV; ++l) s += jp.G[k][l] * ge[3 * l + d];
       gf[d] = w * s;
     }
     float r = q1_scatter(wh * sg[9 + k], gf[0], gf[1], gf[2], l8, jp.ihx, jp.ihy, jp.ihz);
@@ -514,7 +517,7 @@ __device__ __forceinline__ dfl df_shx(dfl v, int m) { return {shx(v.hi, m), shx(
 
 struct DfConst {
   dfl ga, gb, ihx, ihy, ihz, w;
-  dfl G[6][6];
+  dfl G[NV][NV];
 };
 inline dfl df_host(double x) {
   const float hi = float(x);
@@ -564,8 +567,8 @@ inline DfConst make_dfconst(const Grid& g, const DevParams& P) {
   k.ihy = df_host(1.0 / g.hy);
   k.ihz = df_host(1.0 / g.hz);
   k.w = df_host(g.w());
-  for (int a = 0; a < 6; ++a)
-    for (int b = 0; b < 6; ++b) k.G[a][b] = df_host(P.G[a][b]);
+  for (int a = 0; a < NV; ++a)
+    for (int b = 0; b < NV; ++b) k.G[a][b] = df_host(P.G[a][b]);
   return k;
 }
 
@@ -605,8 +608,8 @@ __device__ __forceinline__ void japply_df_block(const Grid& g, const DfConst& k,
   const int64_t e = blk * 4 + (lane >> 3);
   const bool valid = e < g.ne();
   const int64_t node = valid ? elem_node(g, e, l8) : 0;
-  const dmask_t dm = valid ? mask[node] : dmask_t(0x1ff);
-  dfl dz[NZ], ge[18];
+  const dmask_t dm = valid ? mask[node] : MASK_ALL;
+  dfl dz[NZ], ge[3 * NV];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const float x = ((dm >> i) & 1) ? 0.f : v[i * nn + node];
@@ -614,23 +617,24 @@ __device__ __forceinline__ void japply_df_block(const Grid& g, const DfConst& k,
     q1_gather_df(dfl{x, 0.f}, l8, k, val, dz[3 * i], dz[3 * i + 1], dz[3 * i + 2]);
   }
 #pragma unroll
-  for (int kk = 0; kk < 6; ++kk) {
+  for (int kk = 0; kk < NV; ++kk) {
     const float x = ((dm >> (3 + kk)) & 1) ? 0.f : v[(3 + kk) * nn + node];
     q1_gather_df(dfl{x, 0.f}, l8, k, dz[9 + kk], ge[3 * kk], ge[3 * kk + 1], ge[3 * kk + 2]);
   }
   cacc acc[NZ];
 #pragma unroll
   for (int r = 0; r < NZ; ++r) acc[r] = cacc{0.f, 0.f};
-  const float4* Hh = reinterpret_cast<const float4*>(Hhi) + blk * (NH / 4) * 32 + lane;
-  const float4* Hl = reinterpret_cast<const float4*>(Hlo) + blk * (NH / 4) * 32 + lane;
+  const float4* Hh = reinterpret_cast<const float4*>(Hhi) + blk * (NHP / 4) * 32 + lane;
+  const float4* Hl = reinterpret_cast<const float4*>(Hlo) + blk * (NHP / 4) * 32 + lane;
 #pragma unroll 2
-  for (int j = 0; j < NH / 4; ++j) {
+  for (int j = 0; j < NHP / 4; ++j) {
     float hh[4], hl[4];
     Vec16<float>::unpack(__ldcs(Hh + j * 32), hh);
     Vec16<float>::unpack(__ldcs(Hl + j * 32), hl);
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const int idx = j * 4 + t;
+      if (idx >= NH) continue;  // zero padding of the store
       const int r = packed_row(idx);
       const int c = r + (idx - packed_row_start(r));
       cacc_add(acc[r], hh[t], hl[t], dz[c]);
@@ -647,13 +651,13 @@ __device__ __forceinline__ void japply_df_block(const Grid& g, const DfConst& k,
     scatter_row<DET>(y, W, ws, i, blk, lane, i * nn + node, double(r.hi) + double(r.lo), valid && !((dm >> i) & 1));
   }
 #pragma unroll
-  for (int kk = 0; kk < 6; ++kk) {
+  for (int kk = 0; kk < NV; ++kk) {
     dfl gf[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       cacc s = cacc{0.f, 0.f};
 #pragma unroll
-      for (int l = 0; l < 6; ++l) cacc_add(s, k.G[kk][l].hi, k.G[kk][l].lo, ge[3 * l + d]);
+      for (int l = 0; l < NV; ++l) cacc_add(s, k.G[kk][l].hi, k.G[kk][l].lo, ge[3 * l + d]);
       gf[d] = df_mul(k.w, cacc_value(s));
     }
     dfl r = q1_scatter_df(df_mul(k.w, sg[9 + kk]), gf[0], gf[1], gf[2], true, l8, k);

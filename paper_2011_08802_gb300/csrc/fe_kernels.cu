@@ -42,21 +42,21 @@ __global__ void __launch_bounds__(128) k_residual(Grid g, DevParams P, const dou
   const int64_t nn = g.nn();
   const int64_t node = valid ? elem_node(g, e, l8) : 0;
   const double ihx = 1.0 / g.hx, ihy = 1.0 / g.hy, ihz = 1.0 / g.hz;
-  double F[9], eh[6], ge[18], ehn[6];
+  double F[9], eh[NV], ge[3 * NV], ehn[NV];
   gather_state<double>(U, nn, node, valid, l8, ihx, ihy, ihz, F, eh, ge);
 #pragma unroll
-  for (int k = 0; k < 6; ++k) ehn[k] = q1_value(valid ? Un[(3 + k) * nn + node] : 0.0);
+  for (int k = 0; k < NV; ++k) ehn[k] = q1_value(valid ? Un[(3 + k) * nn + node] : 0.0);
   double Wd, gr[NZ];
   qp_local<double, false>(P, F, eh, ehn, &Wd, gr, nullptr);
-  double gf[18];
+  double gf[3 * NV];
   double Wg = 0.0;
 #pragma unroll
-  for (int k = 0; k < 6; ++k)
+  for (int k = 0; k < NV; ++k)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       double s = 0.0;
 #pragma unroll
-      for (int l = 0; l < 6; ++l) s += P.G[k][l] * ge[3 * l + d];
+      for (int l = 0; l < NV; ++l) s += P.G[k][l] * ge[3 * l + d];
       gf[3 * k + d] = s;
       Wg += 0.5 * ge[3 * k + d] * s;
     }
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(128) k_residual(Grid g, DevParams P, const dou
     scatter_row<DET>(R, W, ws, i, blk, lane, i * nn + node, r, valid && !((dm >> i) & 1));
   }
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < NV; ++k) {
     double r = q1_scatter(w * gr[9 + k], w * gf[3 * k], w * gf[3 * k + 1], w * gf[3 * k + 2], l8, ihx,
                           ihy, ihz);
     scatter_row<DET>(R, W, ws, 3 + k, blk, lane, (3 + k) * nn + node, r, valid && !((dm >> (3 + k)) & 1));
@@ -237,14 +237,14 @@ __global__ void __launch_bounds__(128) k_blockdiag_elem(Grid g, JParams<T> jp, c
   const VT* src = reinterpret_cast<const VT*>(H) + blk * (HBLK / V);
   for (int i = lane; i < int(HBLK / V); i += 32) S[i] = src[i];
   __syncwarp();
-  T Db[45];
+  T Db[NBD];
 #pragma unroll
-  for (int t = 0; t < 45; ++t) Db[t] = T(0);
+  for (int t = 0; t < NBD; ++t) Db[t] = T(0);
   const int64_t e = blk * 4 + (lane >> 3);
   if (e < g.ne()) blockdiag_accumulate<T>(jp, reinterpret_cast<const T*>(S), 0, (lane >> 3) * 8, lane & 7, Db);
   const int64_t stride = g.nblk() * 32;
 #pragma unroll
-  for (int t = 0; t < 45; ++t) W[t * stride + blk * 32 + lane] = Db[t];
+  for (int t = 0; t < NBD; ++t) W[t * stride + blk * 32 + lane] = Db[t];
 }
 
 // Pass 2: node n sums the contributions of its (up to 8) adjacent elements in
@@ -258,9 +258,9 @@ __global__ void __launch_bounds__(128) k_blockdiag_node(Grid g, const T* __restr
   const int j = int((n / (g.nx + 1)) % (g.ny + 1));
   const int k = int(n / (int64_t(g.nx + 1) * (g.ny + 1)));
   const int64_t stride = g.nblk() * 32;
-  T Db[45];
+  T Db[NBD];
 #pragma unroll
-  for (int t = 0; t < 45; ++t) Db[t] = T(0);
+  for (int t = 0; t < NBD; ++t) Db[t] = T(0);
   for (int dk = 0; dk < 2; ++dk) {
     const int ek = k - 1 + dk;
     if (ek < 0 || ek >= g.nz) continue;
@@ -274,17 +274,17 @@ __global__ void __launch_bounds__(128) k_blockdiag_node(Grid g, const T* __restr
         const int a = (1 - di) + 2 * (1 - dj) + 4 * (1 - dk);
         const int64_t col = (e >> 2) * 32 + (e & 3) * 8 + a;
 #pragma unroll
-        for (int t = 0; t < 45; ++t) Db[t] += W[t * stride + col];
+        for (int t = 0; t < NBD; ++t) Db[t] += W[t * stride + col];
       }
     }
   }
   int idx = 0;
 #pragma unroll
-  for (int r = 0; r < 9; ++r)
+  for (int r = 0; r < NF; ++r)
 #pragma unroll
-    for (int c = r; c < 9; ++c) {
-      D[(r * 9 + c) * nn + n] = Db[idx];
-      if (c != r) D[(c * 9 + r) * nn + n] = Db[idx];
+    for (int c = r; c < NF; ++c) {
+      D[(r * NF + c) * nn + n] = Db[idx];
+      if (c != r) D[(c * NF + r) * nn + n] = Db[idx];
       ++idx;
     }
 }
@@ -303,9 +303,9 @@ __global__ void k_qp_eval(DevParams P, int64_t n, const double* __restrict__ F,
                           double* __restrict__ W, double* __restrict__ grad, double* __restrict__ hess) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double Fl[9], e[6], en[6], w, g[NZ], h[NH];
+  double Fl[9], e[NV], en[NV], w, g[NZ], h[NH];
   for (int k = 0; k < 9; ++k) Fl[k] = F[i * 9 + k];
-  for (int k = 0; k < 6; ++k) { e[k] = eta[i * 6 + k]; en[k] = eta_n[i * 6 + k]; }
+  for (int k = 0; k < NV; ++k) { e[k] = eta[i * NV + k]; en[k] = eta_n[i * NV + k]; }
   qp_local<double, true>(P, Fl, e, en, &w, g, h);
   if (W) W[i] = w;
   if (grad)
@@ -330,11 +330,12 @@ __global__ void k_absmax(int64_t n, const float* __restrict__ H, unsigned* __res
 // of the same lane.
 __global__ void k_store_to_half(int64_t nvec, const float4* __restrict__ H32, float s, uint4* __restrict__ H16) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nvec; i += int64_t(gridDim.x) * blockDim.x) {
-    // output vector i = (blk*15 + j)*32 + lane holds entries 8j..8j+7; the
-    // FP32 store has them in vectors (blk*30 + 2j)*32 + lane and (.. + 1)*32 + lane
+    // output vector i = (blk*(NHP/8) + j)*32 + lane holds entries 8j..8j+7;
+    // the FP32 store has them in vectors (blk*(NHP/4) + 2j)*32 + lane and
+    // (.. + 1)*32 + lane
     const int64_t lane = i & 31, bj = i >> 5;
-    const int64_t blk = bj / (NH / 8), j = bj % (NH / 8);
-    const int64_t src = (blk * (NH / 4) + 2 * j) * 32 + lane;
+    const int64_t blk = bj / (NHP / 8), j = bj % (NHP / 8);
+    const int64_t src = (blk * (NHP / 4) + 2 * j) * 32 + lane;
     const float4 a = H32[src], b = H32[src + 32];
     uint4 o;
     __half2* h = reinterpret_cast<__half2*>(&o);

@@ -167,7 +167,7 @@ __global__ void k_build_mask(int64_t nn, const uint8_t* __restrict__ m8, dmask_t
     dmask_t m = 0;
     for (int f = 0; f < NF; ++f)
       if (m8[f * nn + node]) m |= dmask_t(1u << f);
-    if (m & 0x1f8) atomicExch(bad, 1);  // order parameters cannot be prescribed
+    if (m & MASK_ETA) atomicExch(bad, 1);  // order parameters cannot be prescribed
     mask[node] = m;
   }
 }

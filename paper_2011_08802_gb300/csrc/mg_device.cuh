@@ -146,7 +146,7 @@ __device__ __forceinline__ void cheb_first_node(int64_t nn, const T* __restrict_
   for (int f = 0; f < NF; ++f) {
     T s = T(0);
 #pragma unroll
-    for (int cc = 0; cc < NF; ++cc) s += D[(f * 9 + cc) * nn + node] * rv[cc];
+    for (int cc = 0; cc < NF; ++cc) s += D[(f * NF + cc) * nn + node] * rv[cc];
     const T dv = c * s;
     d[f * nn + node] = dv;
     x[f * nn + node] = zero_x ? dv : x[f * nn + node] + dv;
@@ -168,7 +168,7 @@ __device__ __forceinline__ void cheb_step_node(int64_t nn, const T* __restrict__
   for (int f = 0; f < NF; ++f) {
     T s = T(0);
 #pragma unroll
-    for (int cc = 0; cc < NF; ++cc) s += D[(f * 9 + cc) * nn + node] * rv[cc];
+    for (int cc = 0; cc < NF; ++cc) s += D[(f * NF + cc) * nn + node] * rv[cc];
     const T dv = a * d[f * nn + node] + c * s;
     d[f * nn + node] = dv;
     x[f * nn + node] += dv;

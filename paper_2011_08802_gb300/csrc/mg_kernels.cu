@@ -74,7 +74,7 @@ __global__ void k_smooth(int64_t nn, const T* __restrict__ D, const T* __restric
     for (int f = 0; f < NF; ++f) {
       T s = T(0);
 #pragma unroll
-      for (int c = 0; c < NF; ++c) s += D[(f * 9 + c) * nn + node] * r[c];
+      for (int c = 0; c < NF; ++c) s += D[(f * NF + c) * nn + node] * r[c];
       x[f * nn + node] += omega * s;
     }
   }
@@ -96,13 +96,13 @@ template <typename T>
 __global__ void k_coarse_assemble(Grid g, DevParams P, const T* __restrict__ H, double* __restrict__ K,
                                   int ld, int color) {
   const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t e = tid / 72;
+  const int64_t e = tid / NED;
   if (e >= g.ne()) return;
   if (color >= 0) {
     const int64_t ei = e % g.nx, ej = (e / g.nx) % g.ny, ek = e / (int64_t(g.nx) * g.ny);
     if (int((ei & 1) + 2 * (ej & 1) + 4 * (ek & 1)) != color) return;
   }
-  const int l = int(tid % 72);
+  const int l = int(tid % NED);
   const int fl = l / 8, al = l % 8;
   const int64_t nn = g.nn();
   const double ih[3] = {1.0 / g.hx, 1.0 / g.hy, 1.0 / g.hz};
@@ -126,7 +126,7 @@ __global__ void k_coarse_assemble(Grid g, DevParams P, const T* __restrict__ H, 
   const int64_t row = fl * nn + node_of(al);
   const int64_t blk = e >> 2;
   const int lane0 = int(e & 3) * 8;
-  for (int m = 0; m < 72; ++m) {
+  for (int m = 0; m < NED; ++m) {
     const int fm = m / 8, am = m % 8;
     double s = 0.0;
     for (int q = 0; q < 8; ++q) {
@@ -314,7 +314,7 @@ void launch_coarse_assemble(const Grid& g, const DevParams& P, const T* H, const
   const int n = int(NF * g.nn());
   cudaMemsetAsync(K, 0, sizeof(double) * size_t(n) * ld, s);
   for (int c = det ? 0 : -1; c < (det ? 8 : 0); ++c) {
-    k_coarse_assemble<T><<<grid_for(g.ne() * 72, 128), 128, 0, s>>>(g, P, H, K, ld, c);
+    k_coarse_assemble<T><<<grid_for(g.ne() * NED, 128), 128, 0, s>>>(g, P, H, K, ld, c);
     count_launches(1);
   }
   k_coarse_bc<<<grid_for(int64_t(n) * n, 256), 256, 0, s>>>(n, g.nn(), mask, K, ld);

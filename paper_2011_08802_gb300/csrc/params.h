@@ -38,8 +38,8 @@ inline void make_dev_params(const pfm_params& in, DevParams& out) {
         Ahat[i][j] = -c * in.ell[i][j] * in.ell[i][j];
       }
     }
-  for (int k = 0; k < 6; ++k)
-    for (int l = 0; l < 6; ++l)
+  for (int k = 0; k < NV; ++k)
+    for (int l = 0; l < NV; ++l)
       out.G[k][l] = Ahat[k + 1][l + 1] - Ahat[0][l + 1] - Ahat[k + 1][0] + Ahat[0][0];
   out.eps_eta = in.eps_eta;
   // Hencky mode: m-point Gauss-Legendre nodes s_k and weights w_k on [0, 1]

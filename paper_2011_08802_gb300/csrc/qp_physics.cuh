@@ -121,9 +121,20 @@ __device__ __forceinline__ df64 shx(df64 v, int m) {
 }
 #endif
 
-constexpr int NPH = 7;    // phases: austenite + 6 variants (Sec. 5.1)
-constexpr int NZ = 15;    // local unknowns at a point: F (9) + eta_hat (6)
-constexpr int NH = 120;   // packed upper triangle of the 15x15 Hessian
+// Number of martensite variants N, fixed at compile time: 6 for the CuAlNi
+// data of Sec. 5.1 (the default build), 12 for a NiTi-type monoclinic set
+// (15 unknowns per node, the footnote of Sec. 5.4); the library is built once
+// per value (libpfm.so, libpfm_nv12.so).
+#ifndef PFM_NV
+#define PFM_NV 6
+#endif
+constexpr int NV = PFM_NV;
+constexpr int NPH = NV + 1;           // phases: austenite + N variants
+constexpr int NZ = 9 + NV;            // local unknowns at a point: F (9) + eta_hat (N)
+constexpr int NH = NZ * (NZ + 1) / 2; // packed upper triangle of the NZ x NZ Hessian (120 for N = 6)
+// entries stored per Gauss point: NH rounded up to a multiple of 8, so that
+// 16-byte vectors of binary16, FP32 or FP64 entries tile it (120 and 232)
+constexpr int NHP = (NH + 7) / 8 * 8;
 
 // Physical parameters, passed by value to kernels (constant bank).
 struct DevParams {
@@ -132,7 +143,7 @@ struct DevParams {
   double F0[NPH];           // chemical energies F_i^0
   double inv_mtau[NPH];     // 1 / (m_i tau)
   double cobst[NPH][NPH];   // 4 gamma_ij / (pi ell_ij), zero diagonal
-  double G[6][6];           // gradient-energy matrix in eta_hat (per direction)
+  double G[NV][NV];         // gradient-energy matrix in eta_hat (per direction)
   double eps_eta;           // penalty parameter
   int same_L;               // 1 when every phase has the same stiffness (then L(eta) = L sum eta)
   int hencky;               // 0: exact log; m = 1, 2, 3: Pade (m,m) (Gauss-Legendre form below)
@@ -436,13 +447,13 @@ PFM_HD T dd2_log_f1(T x, T y, T z, T fxy, T fyz, T fxz) {
 // Fin: F row-major; eh, ehn: eta_1..eta_6 at t_{n+1} and t_n.
 // Outputs: *W, g[15] = dW/dz, Hp[120] = packed d^2W/dz^2 (if Hp != nullptr).
 template <typename T, bool WANT_HESS>
-PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], const T ehn[6], T* W,
+PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[NV], const T ehn[NV], T* W,
                      T g[NZ], T* Hp) {
   T eta[NPH], etan[NPH];
   {
     T s = 0, sn = 0;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) { eta[k + 1] = eh[k]; etan[k + 1] = ehn[k]; s += eh[k]; sn += ehn[k]; }
+    for (int k = 0; k < NV; ++k) { eta[k + 1] = eh[k]; etan[k + 1] = ehn[k]; s += eh[k]; sn += ehn[k]; }
     eta[0] = T(1) - s;
     etan[0] = T(1) - sn;
   }
@@ -588,9 +599,9 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
   // With eta_0 = 1 - sum eta_hat (Sec. 3.1) the elastic energy depends on
   // eta_hat_k through U(eta) = sum eta_i U_i and L(eta) = sum eta_i L_i, i.e.
   // along dU_k = U_k - U_0 and dL_k = L_k - L_0.
-  T dU[6][3][3], AdU[6][3][3], trAdU[6];  // tr(A dU_k) = (d J_t / d eta_hat_k) / J_t
+  T dU[NV][3][3], AdU[NV][3][3], trAdU[NV];  // tr(A dU_k) = (d J_t / d eta_hat_k) / J_t
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < NV; ++k) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -598,12 +609,12 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
     mm3(A, dU[k], AdU[k]);
     trAdU[k] = AdU[k][0][0] + AdU[k][1][1] + AdU[k][2][2];
   }
-  T gel[6];  // dW_el / d eta_hat_k
+  T gel[NV];  // dW_el / d eta_hat_k
   {
     T ES[3][3];  // E S
     mm3(E, S, ES);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < NV; ++k) {
       // S : dE/d eta_hat_k = -2 tr(S A dU_k E) = -2 tr(E S A dU_k)
       T via_E = T(-2) * tr_ab(ES, AdU[k]);
       gel[k] = T(0.5) * Jt * trAdU[k] * hT + T(0.5) * Jt * (hLh[k + 1] - hLh[0]) + via_E;
@@ -636,12 +647,12 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
 #pragma unroll
       for (int j = 0; j < 3; ++j) g[3 * i + j] = T(2) * Pm[i][j];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) g[9 + k] = gel[k] + (geta[k + 1] - geta[0]);
+    for (int k = 0; k < NV; ++k) g[9 + k] = gel[k] + (geta[k + 1] - geta[0]);
   }
   if (!WANT_HESS) return;
 
   // ---------------------------------------------------------------------
-  // Hessian in the 15 unknowns z = (F_pQ: 0..8, eta_hat_1..6: 9..14), packed
+  // Hessian in the 9 + N unknowns z = (F_pQ: 0..8, eta_hat_1..N: 9..8+N), packed
   // into Hp[hidx(r, c)], r <= c. With eta_0 = 1 - sum eta_hat (Sec. 3.1) every
   // eta-dependence enters through U(eta) = sum eta_i U_i and L(eta) =
   // sum eta_i L_i, so the direction eta_hat_k carries dU_k = U_k - U_0 and
@@ -667,7 +678,7 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
         }
       }
   }
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < NV; ++k) {
     T B[3][3];
     rot_in(Q, AdU[k], B);  // B = Q^T A dU_k Q ; dE~ = -(B Lambda + Lambda B^T)
     for (int v = 0; v < 6; ++v) {
@@ -748,9 +759,9 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
     for (int J = 0; J < 6; ++J) Mb[I][J] *= Jt;
   // (dL_k h) rotated and scaled by c, so that (dL_k h)~ : d~_l = LhT[k] . X~_l;
   // zero when every phase has the same stiffness
-  T LhT[6][6];
+  T LhT[NV][6];
   if (!P.same_L) {
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < NV; ++k) {
       T lv[6], lm[3][3], lr[3][3];
       for (int I = 0; I < 6; ++I) {
         T s = 0;
@@ -780,7 +791,7 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
     // S~ : X~_k (tensor double contraction of symmetric matrices)
     T SX = 0;
     for (int v = 0; v < 6; ++v) SX += (v < 3 ? T(1) : T(2)) * St[sym_i(v)][sym_j(v)] * Xs[k][v];
-    for (int p = 0; p < 6; ++p) {
+    for (int p = 0; p < NV; ++p) {
       T ge = trAdU[p] * SX;
       if (!P.same_L) {
         T d = 0;
@@ -810,8 +821,8 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
   T C[3][3], SE[3][3];
   mtm3(F, F, C);
   mm3(S, E, SE);
-  T Yk[6][3][3], SY[6][3][3], CY[6][3][3], SEU[6][3][3];
-  for (int k = 0; k < 6; ++k) {
+  T Yk[NV][3][3], SY[NV][3][3], CY[NV][3][3], SEU[NV][3][3];
+  for (int k = 0; k < NV; ++k) {
     mm3(AdU[k], A, Yk[k]);
     mm3(S, Yk[k], SY[k]);
     mm3(C, Yk[k], CY[k]);
@@ -819,7 +830,7 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
   }
   // F-eta block: -2 (F N_k)_rQ with N_k = ASA dU_k A + A dU_k ASA, where
   // F ASA dU_k A = M (S Y_k) and F A dU_k ASA = (M dU_k) ASA
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < NV; ++k) {
     T MdU[3][3], t1[3][3], t2[3][3];
     mm3(M, SY[k], t1);
     mm3(M, dU[k], MdU);
@@ -830,9 +841,9 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[6], cons
   // (obstacle, dissipation, penalty), the last written in eta_hat:
   // c_kl - c_k0 - c_0l + c_00 + d_0 + delta_kl d_k, d_i = 1/(m_i tau) + eps [eta_i < 0]
   const T d0 = T(P.inv_mtau[0]) + (eta[0] < T(0) ? T(P.eps_eta) : T(0));
-  for (int p = 0; p < 6; ++p) {
+  for (int p = 0; p < NV; ++p) {
     const T hLp = hLh[p + 1] - hLh[0];
-    for (int q = p; q < 6; ++q) {
+    for (int q = p; q < NV; ++q) {
       const T hLq = hLh[q + 1] - hLh[0];
       T sd2E = T(2) * (tr_ab(SEU[p], Yk[q]) + tr_ab(SEU[q], Yk[p]) + tr_ab(SY[p], CY[q]));
       T Jpq = Jt * (trAdU[p] * trAdU[q] - tr_ab(AdU[p], AdU[q]));

@@ -69,6 +69,52 @@ ORIENTATION_011 = [[1.0, 0.0, 0.0],
 #: Edge of the synthetic cube (nm).
 CUBE_EDGE = 64.0
 
+#: Twelve-variant set (N = 12, 15 unknowns per node; the paper names NiTi as
+#: such a case in the footnote of Sec. 5.4 but gives no data for it). Reading:
+#: a monoclinic stretch of the NiTi B19' type,
+#: U_1 = [[gamma, eps, eps], [eps, alpha, delta], [eps, delta, alpha]], with the
+#: parameter values below, and variants 2..12 its distinct images R U_1 R^T
+#: under the 24 rotations of the cubic group (the stabiliser of U_1 has order
+#: 2: the identity and the half turn about [0 1 -1]). All other constants are
+#: those of Sec. 5.1 above, one per phase.
+MONOCLINIC = dict(alpha=1.0243, gamma=0.9563, delta=0.0580, eps=-0.0427)
+
+
+def cubic_rotations() -> list:
+    """The 24 proper rotations of the cube as signed permutation matrices
+    (determinant +1), in a fixed order: permutations in lexicographic order,
+    then sign patterns in binary order."""
+    import itertools
+    out = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1.0, -1.0), repeat=3):
+            R = np.zeros((3, 3))
+            for i in range(3):
+                R[i, perm[i]] = signs[i]
+            if np.linalg.det(R) > 0:
+                out.append(R)
+    return out
+
+
+def monoclinic_stretches(c: dict = MONOCLINIC) -> np.ndarray:
+    """U_0 = I and the 12 monoclinic variant stretches (13, 3, 3): U_1 from
+    ``c`` and the distinct R U_1 R^T over ``cubic_rotations()`` in order of
+    first appearance."""
+    a, g, d, e = c["alpha"], c["gamma"], c["delta"], c["eps"]
+    U1 = np.array([[g, e, e], [e, a, d], [e, d, a]])
+    U = [np.eye(3)]
+    for R in cubic_rotations():
+        V = R @ U1 @ R.T
+        if not any(np.array_equal(V, W) for W in U[1:]):
+            U.append(V)
+    return np.stack(U)
+
+
+def material_nv12() -> dict:
+    """Material constants of the twelve-variant workload: Sec. 5.1's, with
+    the stretches of ``monoclinic_stretches()`` under the key "U"."""
+    return dict(MATERIAL, U=monoclinic_stretches())
+
 
 @dataclasses.dataclass(frozen=True)
 class Mesh:
@@ -112,9 +158,9 @@ class State:
     Dirichlet mask (1 = prescribed DOF) and the time increment tau."""
 
     mesh: Mesh
-    U: np.ndarray      # (9, n_nodes) float64
-    Un: np.ndarray     # (9, n_nodes) float64
-    mask: np.ndarray   # (9, n_nodes) uint8
+    U: np.ndarray      # (3 + N, n_nodes) float64 (N = 6 variants: 9 fields)
+    Un: np.ndarray     # (3 + N, n_nodes) float64
+    mask: np.ndarray   # (3 + N, n_nodes) uint8
     tau: float
     material: dict
 
@@ -160,11 +206,11 @@ def smooth_displacement(mesh: Mesh, rng: np.random.Generator, max_grad: float,
     return np.stack([_flat(u[c]) for c in range(3)])
 
 
-def face_mask(mesh: Mesh, bottom: bool = True, top: bool = False) -> np.ndarray:
+def face_mask(mesh: Mesh, bottom: bool = True, top: bool = False, n_var: int = N_VARIANTS) -> np.ndarray:
     """Dirichlet mask with all three displacement components prescribed on the
-    bottom (z = 0) and optionally the top (z = Lz) face."""
+    bottom (z = 0) and optionally the top (z = Lz) face (3 + n_var fields)."""
     X, Y, Z = mesh.node_grid()
-    m = np.zeros((N_FIELDS, mesh.n_nodes), dtype=np.uint8)
+    m = np.zeros((3 + n_var, mesh.n_nodes), dtype=np.uint8)
     sel = np.zeros(X.shape, dtype=bool)
     if bottom:
         sel[0] = True
@@ -204,60 +250,64 @@ def cap_displacement(mesh: Mesh, depth: float, radius: float) -> tuple[np.ndarra
 
 
 def indentation_dirichlet(mesh: Mesh, step: int, n_steps: int = 10, depth_frac: float = 0.02,
-                          radius_frac: float = 0.3):
+                          radius_frac: float = 0.3, n_var: int = N_VARIANTS):
     """Mask and values of the indentation load at load step ``step``: bottom
     clamped, u_z prescribed under the cap of depth depth_frac*L*step/n_steps."""
-    return indentation_dirichlet_depth(mesh, depth_frac * mesh.Lz * step / n_steps, radius_frac)
+    return indentation_dirichlet_depth(mesh, depth_frac * mesh.Lz * step / n_steps, radius_frac, n_var)
 
 
-def indentation_dirichlet_depth(mesh: Mesh, depth: float, radius_frac: float = 0.3):
+def indentation_dirichlet_depth(mesh: Mesh, depth: float, radius_frac: float = 0.3, n_var: int = N_VARIANTS):
     """Mask and values of the indentation load at cap depth ``depth``: bottom
     clamped, u_z prescribed under the cap of base radius radius_frac*L (the
     cap nodes stay prescribed at depth 0, with u_z = 0)."""
-    mask = face_mask(mesh, bottom=True, top=False)
+    mask = face_mask(mesh, bottom=True, top=False, n_var=n_var)
     idx, uz = cap_displacement(mesh, depth, radius_frac * mesh.Lx)
     mask[2, idx] = 1
-    values = np.zeros((N_FIELDS, mesh.n_nodes))
+    values = np.zeros((3 + n_var, mesh.n_nodes))
     values[2, idx] = uz
     return mask, values
 
 
 def config_indentation(n: int, seed: int, step: int = 1, n_steps: int = 10,
                        depth_frac: float = 0.02, radius_frac: float = 0.3,
-                       noise: float = 1e-3, tau: float = 0.128) -> State:
+                       noise: float = 1e-3, tau: float = 0.128, n_var: int = N_VARIANTS) -> State:
     """Nano-indentation-like load on an n^3 cube: eta_hat = noise * U[0,1) per
     node and variant (seeded; one-signed so the initial state lies in the
     admissible simplex eta_i >= 0, sum eta_i = 1), u = 0 except the prescribed
-    cap values of load step ``step``, eta_n = eta, bottom clamped."""
+    cap values of load step ``step``, eta_n = eta, bottom clamped. ``n_var``
+    = 12 gives the twelve-variant workload (3 + 12 fields, ``material_nv12``)."""
     mesh = Mesh(n, n, n)
     rng = np.random.default_rng(seed)
-    mask, values = indentation_dirichlet(mesh, step, n_steps, depth_frac, radius_frac)
-    U = np.zeros((N_FIELDS, mesh.n_nodes))
-    U[3:9] = noise * rng.random((6, mesh.n_nodes))
+    mask, values = indentation_dirichlet(mesh, step, n_steps, depth_frac, radius_frac, n_var)
+    U = np.zeros((3 + n_var, mesh.n_nodes))
+    U[3:] = noise * rng.random((n_var, mesh.n_nodes))
     U[mask.astype(bool)] = values[mask.astype(bool)]
     Un = U.copy()
     Un[0:3] = 0.0
-    return State(mesh, U, Un, mask, tau, dict(MATERIAL))
+    material = dict(MATERIAL) if n_var == N_VARIANTS else material_nv12()
+    return State(mesh, U, Un, mask, tau, material)
 
 
 def config_random(nx: int, ny: int, nz: int, seed: int, max_grad: float = 0.04,
                   eta_lo: float = 0.0, eta_hi: float = 0.35, tau: float = 0.1,
                   Lx: float = CUBE_EDGE, Ly: float = CUBE_EDGE, Lz: float = CUBE_EDGE,
-                  un_shift: float = 0.02, top: bool = True) -> State:
+                  un_shift: float = 0.02, top: bool = True, n_var: int = N_VARIANTS) -> State:
     """Parity-test state on a box of nx*ny*nz hexes: smooth u, smooth eta_hat
     mapped to [eta_lo, eta_hi] (negative eta_lo exercises the penalty branch),
-    eta_n = eta minus a smooth seeded shift of size un_shift."""
+    eta_n = eta minus a smooth seeded shift of size un_shift; ``n_var`` = 12
+    for the twelve-variant material."""
     mesh = Mesh(nx, ny, nz, Lx, Ly, Lz)
     rng = np.random.default_rng(seed)
     shape = (nz + 1, ny + 1, nx + 1)
-    U = np.zeros((N_FIELDS, mesh.n_nodes))
+    U = np.zeros((3 + n_var, mesh.n_nodes))
     U[0:3] = smooth_displacement(mesh, rng, max_grad, sigma=1.0)
-    for k in range(6):
+    for k in range(n_var):
         U[3 + k] = _flat(eta_lo + (eta_hi - eta_lo) * _to_unit_interval(smooth_noise(shape, 1.0, rng)))
     Un = U.copy()
-    for k in range(6):
+    for k in range(n_var):
         Un[3 + k] -= un_shift * _flat(smooth_noise(shape, 1.0, rng))
-    return State(mesh, U, Un, face_mask(mesh, True, top), tau, dict(MATERIAL))
+    material = dict(MATERIAL) if n_var == N_VARIANTS else material_nv12()
+    return State(mesh, U, Un, face_mask(mesh, True, top, n_var), tau, material)
 
 
 def direction_vectors(state: State, count: int, seed: int) -> np.ndarray:

@@ -63,6 +63,7 @@ def parse_args():
     p.add_argument("--no-hencky", action="store_true", help="skip the Hencky-mode cost comparison")
     p.add_argument("--no-f16-store", action="store_true",
                    help="skip the Newton step with the binary16 preconditioner store")
+    p.add_argument("--no-nv12", action="store_true", help="skip the twelve-variant measurement")
     p.add_argument("--no-relaxed", action="store_true",
                    help="skip the mixed step with relaxed (late FP32) FGMRES products")
     p.add_argument("--switch-rtol", type=float, default=1e-3,
@@ -584,6 +585,67 @@ def indentation32_measure(dev):
     return out
 
 
+def nv12_measure(dev, n: int):
+    """Twelve variants (libpfm_nv12.so, 15 unknowns per node) on the n^3
+    indentation state, first load step: linearisation of every level, the
+    FP32 tangent application (mean of 20, with its HBM roofline: 8 x 232 x 4 B
+    of Hessians per element, 231 entries padded to 232), the FP64 and
+    double-float applications, and one mixed-precision Newton step (relaxed
+    products, 1e-8)."""
+    import numpy as np
+    import torch
+
+    from paper_2011_08802_gb300 import abi, binding, inputs
+
+    st = inputs.config_indentation(n, seed=5, step=1, n_var=12)
+    P = binding.problem_from_state(st)
+    ndofs = 15 * P.n_nodes
+    out = {"workload": f"{n}^3 Q1 hexes, 12 variants, {ndofs} DOFs, indentation load step 1/10"}
+    P.residual()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    P.linearize(abi.PFM_F32)
+    e1.record()
+    torch.cuda.synchronize()
+    out["linearize_all_levels_ms"] = e0.elapsed_time(e1)
+    for key, dt, fn, reps in (("f32", np.float32, P.jacobian_apply, 20), ("f64", np.float64, P.jacobian_apply, 3),
+                              ("df", np.float32, P.jacobian_apply_mixed, 5)):
+        v = torch.from_numpy(np.random.default_rng(1).standard_normal(P.shape).astype(dt)).to(dev)
+        y = torch.empty(P.shape, dtype=torch.float32 if key == "f32" else torch.float64, device=dev)
+        for _ in range(3):
+            fn(v, y)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn(v, y)
+        b.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / reps
+        out[f"japply_{key}"] = {"ms": t, "gdofs": ndofs / (t * 1e-3) / 1e9}
+    alg = ((P.n_elems + 3) // 4) * 4 * 8 * 232 * 4 + 2 * 4 * ndofs + 2 * P.n_nodes
+    peak, kind = measured_hbm()
+    t = out["japply_f32"]["ms"]
+    out["japply_f32"].update({"bytes_per_launch": alg, "gbs": alg / (t * 1e-3) / 1e9,
+                              "hbm_frac": alg / (t * 1e-3) / 1e9 / peak, "peak_kind": kind})
+    U0 = torch.from_numpy(st.U).to(dev)
+    o = abi.default_opts(abi.PFM_F32, max_newton=1, restart=30, max_lin_it=400, lin_rtol=1e-8, krylov=1,
+                         switch_rtol=1e-4)
+    U = U0.clone()
+    P.newton_solve(U, o)
+    U = U0.clone()
+    torch.cuda.synchronize()
+    e0.record()
+    rep = P.newton_solve(U, o)
+    e1.record()
+    torch.cuda.synchronize()
+    out["newton_step"] = {"s": e0.elapsed_time(e1) / 1e3, "fgmres_its": rep.lin_its_last,
+                          "lin_rel_residual": rep.lin_res_final}
+    P.close()
+    return out
+
+
 def diff_measure(dev):
     """Differentiation workload: the 32^3 indentation state after five load
     steps; 16 seeded directions; device time (CUDA events) of 16 forward
@@ -860,6 +922,10 @@ def gpu_arm(args, rank, world, dist):
     if not args.no_indentation32 and rank == 0:
         ind32 = indentation32_measure(dev)
 
+    nv12 = None
+    if not args.no_nv12 and rank == 0:
+        nv12 = nv12_measure(dev, args.n)
+
     batch = None
     if not args.no_batch:
         P.close()
@@ -910,6 +976,7 @@ def gpu_arm(args, rank, world, dist):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "bytes_per_launch": alg_bytes},
+            "twelve_variants": nv12,
             "indentation32": ind32,
             "relaxed": relaxed,
             "newton_step_s": {"fp32_mg": ms_step / 1e3, "fp64": fp64["s"] if fp64 else None,

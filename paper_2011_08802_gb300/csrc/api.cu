@@ -242,14 +242,16 @@ pfm_status estimate_lambda(pfm_handle* h, size_t l) {
   launch_power_init<T>(lv.nn, lv.mask, x, s);
   launch_dot<T>(n, x, x, h->partial, h->hdev, s);
   launch_scale_inv_sqrt<T>(n, x, h->hdev, x, s);
+  CKL_AT("power iteration start");
   for (int it = 0; it < h->power_its; ++it) {
     precond_apply<T>(h, l, x, y, false);
+    CKL_AT("power iteration: tangent application");
     CK(cudaMemsetAsync(z, 0, sizeof(T) * n, s));
     launch_smooth<T>(lv.nn, D, y, nullptr, T(1), z, s);
     launch_dot<T>(n, z, z, h->partial, h->hdev, s);
     launch_scale_inv_sqrt<T>(n, z, h->hdev, x, s);
+    CKL_AT("power iteration");
   }
-  CKL();
   double dot = 0.0;
   CK(cudaMemcpyAsync(&dot, h->hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -332,7 +334,7 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
     launch_inject_state(h->L[l - 1].g, h->L[l].g, h->L[l - 1].U, h->L[l].U, s);
     launch_inject_state(h->L[l - 1].g, h->L[l].g, h->L[l - 1].Un, h->L[l].Un, s);
   }
-  CKL();
+  CKL_AT("state injection");
   CK(cudaMemsetAsync(h->flag_dev, 0, sizeof(int), s));
   for (size_t l = 0; l < nl; ++l) {
     Level& lv = h->L[l];
@@ -356,6 +358,7 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
       launch_linearize(lv.g, h->dp, lv.U, lv.Un, need64 ? lv.H64 : nullptr, need32 ? lv.H32 : nullptr,
                        needlo ? lv.H32lo : nullptr, arith, s);
     }
+    CKL_AT("Gauss-point Hessians");
     lv.h16_scale = 0.f;
     if (need32 && h->pre_h16) {
       TRY(dalloc(h, &lv.H16, hsz));
@@ -375,8 +378,9 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
       TRY(bd_scratch(h, size_t(NBD) * 32 * lv.nblk * sizeof(float)));
       launch_blockdiag<float>(lv.g, h->dp, lv.H32, lv.mask, lv.D32, static_cast<float*>(h->bd_scratch), s);
       if (h->contact_on) launch_contact_blockdiag<float>(lv.g, lv.Kc32, lv.D32, s);
+      CKL_AT("diagonal blocks");
       launch_block_invert<float>(lv.nn, lv.mask, lv.D32, h->flag_dev, s);
-      CKL();
+      CKL_AT("block inverses");
       TRY(ensure_level_vectors<float>(h));
       TRY(estimate_lambda<float>(h, l));
     } else {
@@ -384,8 +388,9 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
       TRY(bd_scratch(h, size_t(NBD) * 32 * lv.nblk * sizeof(double)));
       launch_blockdiag<double>(lv.g, h->dp, lv.H64, lv.mask, lv.D64, static_cast<double*>(h->bd_scratch), s);
       if (h->contact_on) launch_contact_blockdiag<double>(lv.g, lv.Kc64, lv.D64, s);
+      CKL_AT("diagonal blocks");
       launch_block_invert<double>(lv.nn, lv.mask, lv.D64, h->flag_dev, s);
-      CKL();
+      CKL_AT("block inverses");
       TRY(ensure_level_vectors<double>(h));
       TRY(estimate_lambda<double>(h, l));
     }
@@ -393,8 +398,9 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
   Level& c = h->L[nl - 1];
   launch_coarse_assemble<double>(c.g, h->dp, c.H64, c.mask, h->Kaug, 2 * h->nc_dofs, s, h->det);
   if (h->contact_on) launch_contact_coarse(c.g, c.Kc64, c.mask, h->Kaug, 2 * h->nc_dofs, s);
+  CKL_AT("coarse operator");
   dense_gauss_jordan_inverse(h->Kaug, h->nc_dofs, h->Kinv, h->gj_keys, h->gj_used, h->gj_piv, h->flag_dev, s);
-  CKL();
+  CKL_AT("coarse inverse");
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));

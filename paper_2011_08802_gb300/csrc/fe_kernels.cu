@@ -647,10 +647,11 @@ void launch_blockdiag(const Grid& g, const DevParams& P, const T* H, const dmask
   // 4 element blocks per CTA in FP32 (60 KB of staged Hessians), 2 in FP64
   const int warps = sizeof(T) == 4 ? 4 : 2;
   const int smem = int(warps * HBLK * sizeof(T));
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[sizeof(T) == 8]) {
-    cudaFuncSetAttribute(k_blockdiag_elem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr_set[sizeof(T) == 8] = true;
+  static bool attr_set = false;  // one flag per instantiation (element type)
+  if (!attr_set) {
+    // a failure stays in cudaGetLastError and is reported by the caller's launch check
+    if (cudaFuncSetAttribute(k_blockdiag_elem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess)
+      attr_set = true;
   }
   k_blockdiag_elem<T><<<grid_for(g.nblk() * 32, 32 * warps), 32 * warps, smem, s>>>(g, make_jparams<T>(g, P), H, W);
   k_blockdiag_node<T><<<grid_for(g.nn(), 128), 128, 0, s>>>(g, W, D);

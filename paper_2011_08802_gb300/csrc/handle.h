@@ -177,6 +177,14 @@ struct pfm_batch {
       return h->fail(PFM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_));  \
   } while (0)
 
+// CKL with the name of the step that launched the kernels in the message
+#define CKL_AT(what)                                                                                   \
+  do {                                                                                                 \
+    cudaError_t e_ = cudaGetLastError();                                                               \
+    if (e_ != cudaSuccess)                                                                             \
+      return h->fail(PFM_ERR_CUDA, std::string("kernel launch (") + (what) + "): " + cudaGetErrorString(e_)); \
+  } while (0)
+
 #define TRY(expr)                     \
   do {                                \
     pfm_status s_ = (expr);           \

@@ -6,15 +6,20 @@ Workload (one step): one Newton iteration of the nano-indentation problem on
 a 128^3 trilinear-hexahedron cube (19,320,201 DOFs, 6 multigrid levels, load
 step 1 of 10): residual -> linearisation on every level -> FGMRES(30) with an
 FP32 geometric-multigrid V-cycle inside FP64 FGMRES to a relative residual of
-1e-8 -> update -> new residual. Inputs are seeded and synthetic and resident
-in HBM when the timed region starts; every step restarts from the same state.
+1e-8 -> update -> new residual. FGMRES applies the FP64-class (double-float)
+tangent while its residual estimate is above 1e-4 and the FP32 tangent after
+it (relaxed products); the FP64-class true residual b - J x decides
+convergence. Inputs are seeded and synthetic and resident in HBM when the
+timed region starts; every step restarts from the same state.
 
 Headline value: Jacobian-apply throughput in GDOF/s, i.e. DOFs of the finest
 level per FP32 tangent application, divided by the mean device time of those
 applications inside the timed Newton steps (CUDA events recorded by the
 library on its stream). Also reported: seconds per Newton step for the mixed
-FP32-MG and the all-FP64 solve, the same mixed step with the preconditioner
-reading binary16 copies of its Hessians (FP32 arithmetic, half the bytes),
+FP32-MG and the all-FP64 solve, the mixed step with the FP64-class operator
+in every FGMRES iteration, the mixed step with the preconditioner reading
+binary16 copies of its Hessians (FP32 arithmetic, half the bytes), the 32^3
+ten-load-step configuration, twelve variants,
 the roofline of the tangent application,
 an end-to-end figure through the host-buffer entry point, and the CPU oracle
 timed on a bounded sample, on one core and on every host core at once (one
@@ -64,10 +69,10 @@ def parse_args():
     p.add_argument("--no-f16-store", action="store_true",
                    help="skip the Newton step with the binary16 preconditioner store")
     p.add_argument("--no-nv12", action="store_true", help="skip the twelve-variant measurement")
-    p.add_argument("--no-relaxed", action="store_true",
-                   help="skip the mixed step with relaxed (late FP32) FGMRES products")
-    p.add_argument("--switch-rtol", type=float, default=1e-3,
-                   help="relative residual estimate below which relaxed FGMRES uses FP32 products")
+    p.add_argument("--no-plain", action="store_true",
+                   help="skip the mixed step with the FP64-class operator in every FGMRES iteration")
+    p.add_argument("--switch-rtol", type=float, default=1e-4,
+                   help="relative residual estimate below which FGMRES uses FP32 products (krylov = 1)")
     p.add_argument("--mode", default="newton", choices=["newton", "japply"],
                    help="japply: only K FP32 tangent applications (for profiler captures)")
     return p.parse_args()
@@ -775,7 +780,11 @@ def gpu_arm(args, rank, world, dist):
     ndofs = 9 * P.n_nodes
     U0 = torch.from_numpy(st.U).to(dev)
     Uw = torch.empty_like(U0)
-    opts = abi.default_opts(abi.PFM_F32, max_newton=1, restart=30, max_lin_it=400, lin_rtol=1e-8)
+    # the mixed-precision step: FP32 multigrid inside FP64 FGMRES whose late
+    # products are FP32 once the residual estimate is below switch_rtol
+    # (krylov = 1); the FP64-class true residual decides convergence
+    opts = abi.default_opts(abi.PFM_F32, max_newton=1, restart=30, max_lin_it=400, lin_rtol=1e-8, krylov=1,
+                            switch_rtol=args.switch_rtol)
 
     def step(o):
         Uw.copy_(U0)
@@ -831,7 +840,7 @@ def gpu_arm(args, rank, world, dist):
         true_res = float(torch.linalg.norm(y + R) / torch.linalg.norm(R))
         return true_res, rep.lin_its_last
 
-    res32, its32 = solve_check(abi.PFM_F32)
+    res32, its32 = solve_check(abi.PFM_F32, krylov=1, switch_rtol=args.switch_rtol)
     fp64 = None
     if not args.no_fp64_step:
         o64 = abi.default_opts(abi.PFM_F64, max_newton=1, restart=30, max_lin_it=400, lin_rtol=1e-8)
@@ -868,27 +877,24 @@ def gpu_arm(args, rank, world, dist):
                "japply_gbs": alg16 / (a16 * 1e-3) / 1e9, "japply_hbm_frac": alg16 / (a16 * 1e-3) / 1e9 / peak,
                "bytes_per_launch": alg16}
 
-    # ---- the mixed step with relaxed products (FP32 products once the ------
-    # ---- residual estimate is small, FP64-class true residual decides) -----
-    relaxed = None
-    if not args.no_relaxed:
-        orel = abi.default_opts(abi.PFM_F32, max_newton=1, restart=30, max_lin_it=400, lin_rtol=1e-8,
-                                krylov=1, switch_rtol=args.switch_rtol)
-        step(orel)
+    # ---- the same mixed step with the FP64-class operator in every --------
+    # ---- FGMRES iteration (krylov = 0) --------------------------------------
+    plain = None
+    if not args.no_plain:
+        opl = abi.default_opts(abi.PFM_F32, max_newton=1, restart=30, max_lin_it=400, lin_rtol=1e-8)
+        step(opl)
         torch.cuda.synchronize()
         P.profile_enable(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        rr = [step(orel) for _ in range(3)]
+        rr = [step(opl) for _ in range(3)]
         e1.record()
         torch.cuda.synchronize()
-        nr64, msr64 = P.profile_get(abi.PROF_JAPPLY_F64)
+        np64, msp64 = P.profile_get(abi.PROF_JAPPLY_F64)
         P.profile_enable(False)
-        resr, _ = solve_check(abi.PFM_F32, krylov=1, switch_rtol=args.switch_rtol)
-        relaxed = {"s": e0.elapsed_time(e1) / 3e3, "fgmres_its": rr[-1].lin_its_last,
-                   "cycles": rr[-1].lin_outer_last, "true_rel_residual": resr,
-                   "switch_rtol": args.switch_rtol, "fp64_class_applications_per_step": nr64 / 3,
-                   "fp64_class_ms_per_step": msr64 / 3}
+        resp, _ = solve_check(abi.PFM_F32)
+        plain = {"s": e0.elapsed_time(e1) / 3e3, "fgmres_its": rr[-1].lin_its_last, "true_rel_residual": resp,
+                 "fp64_class_applications_per_step": np64 / 3, "fp64_class_ms_per_step": msp64 / 3}
 
     hencky = None
     aniso = None
@@ -978,16 +984,17 @@ def gpu_arm(args, rank, world, dist):
                          "bytes_per_launch": alg_bytes},
             "twelve_variants": nv12,
             "indentation32": ind32,
-            "relaxed": relaxed,
+            "fp64_class_every_iteration": plain,
             "newton_step_s": {"fp32_mg": ms_step / 1e3, "fp64": fp64["s"] if fp64 else None,
                               "fp32_mg_f16_store": f16["s"] if f16 else None,
-                              "fp32_mg_relaxed": relaxed["s"] if relaxed else None},
+                              "fp32_mg_fp64_class_every_iteration": plain["s"] if plain else None},
             "fgmres_its": {"fp32_mg": rep.lin_its_last, "fp64": fp64["fgmres_its"] if fp64 else None,
                            "fp32_mg_f16_store": f16["fgmres_its"] if f16 else None,
-                           "fp32_mg_relaxed": relaxed["fgmres_its"] if relaxed else None},
+                           "fp32_mg_fp64_class_every_iteration": plain["fgmres_its"] if plain else None},
             "true_rel_residual": {"fp32_mg": res32, "fp64": fp64["true_rel_residual"] if fp64 else None,
                                   "fp32_mg_f16_store": f16["true_rel_residual"] if f16 else None,
-                                  "fp32_mg_relaxed": relaxed["true_rel_residual"] if relaxed else None},
+                                  "fp32_mg_fp64_class_every_iteration":
+                                      plain["true_rel_residual"] if plain else None},
         }
         print(json.dumps(line), flush=True)
     if P is not None:

@@ -129,6 +129,78 @@ __host__ __device__ __forceinline__ void restrict_node(const Grid& f, const Grid
   for (int fld = 0; fld < NF; ++fld) rc[fld * nnc + idx] = ((dm >> fld) & 1) ? T(0) : T(acc[fld]);
 }
 
+// Nested grids (nf = 2 nc on every axis), the case of every level of a
+// power-of-two hierarchy: fine node i of an axis coincides with coarse node
+// i/2 (even i, weight 1) or lies midway between coarse nodes (i-1)/2 and
+// (i+1)/2 (odd i, weights 1/2). These are the weights of the general
+// transfers above on such grids; being powers of two they are exact in
+// binary arithmetic, so the node bodies below form their sums in T (FP32 in
+// the FP32 preconditioner) and take the node from its (i, j, k) position.
+
+// Fine node (i, j, k): xf += P xc at its free DOFs.
+template <typename T>
+__host__ __device__ __forceinline__ void prolong_node_nested(const Grid& f, const Grid& c, const T* __restrict__ xc,
+                                                    const dmask_t* __restrict__ mf, T* __restrict__ xf, int i,
+                                                    int j, int k) {
+  const int64_t nnf = f.nn(), nnc = c.nn();
+  const int64_t idx = i + int64_t(f.nx + 1) * (j + int64_t(f.ny + 1) * k);
+  const dmask_t dm = mf[idx];
+  if (dm == MASK_ALL) return;
+  const int ni = (i & 1) + 1, nj = (j & 1) + 1, nk = (k & 1) + 1;
+  const T w = ((i & 1) ? T(0.5) : T(1)) * ((j & 1) ? T(0.5) : T(1)) * ((k & 1) ? T(0.5) : T(1));
+  const int64_t c0 = (i >> 1) + int64_t(c.nx + 1) * ((j >> 1) + int64_t(c.ny + 1) * (k >> 1));
+  const int64_t sy = c.nx + 1, sz = int64_t(c.nx + 1) * (c.ny + 1);
+  for (int fld = 0; fld < NF; ++fld) {
+    if ((dm >> fld) & 1) continue;
+    const T* X = xc + fld * nnc + c0;
+    T s = T(0);
+    for (int a2 = 0; a2 < nk; ++a2)
+      for (int a1 = 0; a1 < nj; ++a1)
+        for (int a0 = 0; a0 < ni; ++a0) s += X[a0 + a1 * sy + a2 * sz];
+    xf[fld * nnf + idx] += w * s;
+  }
+}
+
+// Coarse node (I, J, K): rc = (P^T rf) there, zero at its Dirichlet DOFs;
+// it collects fine nodes 2I-1, 2I, 2I+1 per axis with weights 1/2, 1, 1/2.
+template <typename T>
+__host__ __device__ __forceinline__ void restrict_node_nested(const Grid& f, const Grid& c, const T* __restrict__ rf,
+                                                     const dmask_t* __restrict__ mc, T* __restrict__ rc, int I,
+                                                     int J, int K) {
+  const int64_t nnf = f.nn(), nnc = c.nn();
+  const int64_t idx = I + int64_t(c.nx + 1) * (J + int64_t(c.ny + 1) * K);
+  const dmask_t dm = mc[idx];
+  const int64_t sy = f.nx + 1, sz = int64_t(f.nx + 1) * (f.ny + 1);
+  for (int fld = 0; fld < NF; ++fld) {
+    if ((dm >> fld) & 1) {
+      rc[fld * nnc + idx] = T(0);
+      continue;
+    }
+    const T* X = rf + fld * nnf;
+    T acc = T(0);
+    for (int dk = -1; dk <= 1; ++dk) {
+      const int k = 2 * K + dk;
+      if (k < 0 || k > f.nz) continue;
+      T sj = T(0);
+      for (int dj = -1; dj <= 1; ++dj) {
+        const int j = 2 * J + dj;
+        if (j < 0 || j > f.ny) continue;
+        const T* row = X + j * sy + k * sz;
+        T si = row[2 * I];
+        if (I > 0) si += T(0.5) * row[2 * I - 1];
+        if (2 * I + 1 <= f.nx) si += T(0.5) * row[2 * I + 1];
+        sj += (dj ? T(0.5) : T(1)) * si;
+      }
+      acc += (dk ? T(0.5) : T(1)) * sj;
+    }
+    rc[fld * nnc + idx] = acc;
+  }
+}
+
+inline __host__ __device__ bool nested(const Grid& f, const Grid& c) {
+  return f.nx == 2 * c.nx && f.ny == 2 * c.ny && f.nz == 2 * c.nz;
+}
+
 // Chebyshev-accelerated point-block Jacobi at one node (Saad, Iterative
 // Methods, Alg. 12.1 applied to D^-1 J). First step: d = c D^-1 r0 with
 // r0 = src (also stored in r when copy_r), x = d (zero_x) or x += d.

@@ -51,6 +51,25 @@ __global__ void k_prolong_add(Grid f, Grid c, const T* __restrict__ xc, const dm
     prolong_node<T>(f, c, xc, mf, xf, idx);
 }
 
+// Nested grids: one thread per fine node (i over x-blocks and threads, j and
+// k over the grid's y and z dimensions, so no index division).
+template <typename T>
+__global__ void __launch_bounds__(128) k_prolong_add_nested(Grid f, Grid c, const T* __restrict__ xc,
+                                                            const dmask_t* __restrict__ mf, T* __restrict__ xf) {
+  const int i = int(blockIdx.x * blockDim.x + threadIdx.x);
+  if (i > f.nx) return;
+  prolong_node_nested<T>(f, c, xc, mf, xf, i, int(blockIdx.y), int(blockIdx.z));
+}
+
+// Nested grids: one thread per coarse node.
+template <typename T>
+__global__ void __launch_bounds__(128) k_restrict_nested(Grid f, Grid c, const T* __restrict__ rf,
+                                                         const dmask_t* __restrict__ mc, T* __restrict__ rc) {
+  const int I = int(blockIdx.x * blockDim.x + threadIdx.x);
+  if (I > c.nx) return;
+  restrict_node_nested<T>(f, c, rf, mc, rc, I, int(blockIdx.y), int(blockIdx.z));
+}
+
 // rc = P^T rf, zero at coarse Dirichlet DOFs.
 template <typename T>
 __global__ void k_restrict(Grid f, Grid c, const T* __restrict__ rf, const dmask_t* __restrict__ mc,
@@ -282,17 +301,30 @@ void launch_coarse_mask(const Grid& fine, const Grid& coarse, const dmask_t* mf,
   count_launches(1);
 }
 
+// y and z node counts within the grid-dimension limit of a 3-D launch
+inline bool grid3_ok(const Grid& g) { return g.ny + 1 <= 65535 && g.nz + 1 <= 65535; }
+
 template <typename T>
 void launch_prolong_add(const Grid& fine, const Grid& coarse, const T* xc, const dmask_t* mf, T* xf,
                         cudaStream_t s) {
-  k_prolong_add<T><<<grid_for(fine.nn(), 256), 256, 0, s>>>(fine, coarse, xc, mf, xf);
+  if (nested(fine, coarse) && grid3_ok(fine)) {
+    const dim3 grid(unsigned((fine.nx + 1 + 127) / 128), unsigned(fine.ny + 1), unsigned(fine.nz + 1));
+    k_prolong_add_nested<T><<<grid, 128, 0, s>>>(fine, coarse, xc, mf, xf);
+  } else {
+    k_prolong_add<T><<<grid_for(fine.nn(), 256), 256, 0, s>>>(fine, coarse, xc, mf, xf);
+  }
   count_launches(1);
 }
 
 template <typename T>
 void launch_restrict(const Grid& fine, const Grid& coarse, const T* rf, const dmask_t* mc, T* rc,
                      cudaStream_t s) {
-  k_restrict<T><<<grid_for(coarse.nn(), 128), 128, 0, s>>>(fine, coarse, rf, mc, rc);
+  if (nested(fine, coarse) && grid3_ok(coarse)) {
+    const dim3 grid(unsigned((coarse.nx + 1 + 127) / 128), unsigned(coarse.ny + 1), unsigned(coarse.nz + 1));
+    k_restrict_nested<T><<<grid, 128, 0, s>>>(fine, coarse, rf, mc, rc);
+  } else {
+    k_restrict<T><<<grid_for(coarse.nn(), 128), 128, 0, s>>>(fine, coarse, rf, mc, rc);
+  }
   count_launches(1);
 }
 

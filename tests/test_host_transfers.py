@@ -33,6 +33,28 @@ extern "C" void host_restrict(const int* fn, const int* cn, const double* rf, co
   const Grid f = grid(fn), c = grid(cn);
   for (int64_t i = 0; i < c.nn(); ++i) restrict_node<double>(f, c, rf, mc, rc, i);
 }
+extern "C" void host_prolong_nested(const int* fn, const int* cn, const double* xc, const unsigned short* mf,
+                                    double* xf) {
+  const Grid f = grid(fn), c = grid(cn);
+  for (int k = 0; k <= f.nz; ++k)
+    for (int j = 0; j <= f.ny; ++j)
+      for (int i = 0; i <= f.nx; ++i) prolong_node_nested<double>(f, c, xc, mf, xf, i, j, k);
+}
+extern "C" void host_restrict_nested(const int* fn, const int* cn, const double* rf, const unsigned short* mc,
+                                     double* rc) {
+  const Grid f = grid(fn), c = grid(cn);
+  for (int k = 0; k <= c.nz; ++k)
+    for (int j = 0; j <= c.ny; ++j)
+      for (int i = 0; i <= c.nx; ++i) restrict_node_nested<double>(f, c, rf, mc, rc, i, j, k);
+}
+extern "C" void host_restrict_nested_f32(const int* fn, const int* cn, const float* rf, const unsigned short* mc,
+                                         float* rc) {
+  const Grid f = grid(fn), c = grid(cn);
+  for (int k = 0; k <= c.nz; ++k)
+    for (int j = 0; j <= c.ny; ++j)
+      for (int i = 0; i <= c.nx; ++i) restrict_node_nested<float>(f, c, rf, mc, rc, i, j, k);
+}
+extern "C" int host_nested(const int* fn, const int* cn) { return nested(grid(fn), grid(cn)) ? 1 : 0; }
 extern "C" void host_inject(const int* fn, const int* cn, const double* Uf, double* Uc) {
   const Grid f = grid(fn), c = grid(cn);
   for (int64_t i = 0; i < c.nn(); ++i) inject_node(f, c, Uf, Uc, i);
@@ -95,3 +117,40 @@ def test_transfers_match_oracle(lib, fine, coarse):
     Uc = np.zeros((9, nc))
     lib.host_inject(_p(fn, C.c_int), _p(cn, C.c_int), _p(Uf, d), _p(Uc, d))
     np.testing.assert_allclose(Uc, T.inject(fine, coarse, Uf), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("fine, coarse", [((8, 8, 8), (4, 4, 4)), ((24, 18, 10), (12, 9, 5)), ((2, 2, 2), (1, 1, 1)),
+                                          ((2, 2, 300), (1, 1, 150))])
+def test_nested_transfers_match_oracle(lib, fine, coarse):
+    """The nested-grid node bodies (weights 1, 1/2 per axis) against the
+    oracle's P and R = P^T, in FP64 and, for the restriction, in FP32."""
+    rng = np.random.default_rng(3 * sum(fine) + sum(coarse))
+    nf, nc = _n(fine), _n(coarse)
+    fn, cn = np.array(fine, dtype=np.int32), np.array(coarse, dtype=np.int32)
+    assert lib.host_nested(_p(fn, C.c_int), _p(cn, C.c_int)) == 1
+    mf = (rng.random((9, nf)) < 0.15).astype(np.uint8)
+    mf[:, 0] = 1  # one node with every field prescribed
+    mc = (rng.random((9, nc)) < 0.15).astype(np.uint8)
+    d = C.c_double
+    xc = rng.standard_normal((9, nc))
+    xf0 = rng.standard_normal((9, nf))
+    xf = xf0.copy()
+    lib.host_prolong_nested(_p(fn, C.c_int), _p(cn, C.c_int), _p(xc, d), _p(_bits(mf), C.c_ushort), _p(xf, d))
+    np.testing.assert_allclose(xf, T.prolong_add(fine, coarse, xc, xf0, mf), rtol=0, atol=1e-13)
+    rf = rng.standard_normal((9, nf))
+    rc = np.zeros((9, nc))
+    lib.host_restrict_nested(_p(fn, C.c_int), _p(cn, C.c_int), _p(rf, d), _p(_bits(mc), C.c_ushort), _p(rc, d))
+    ref = T.restrict(fine, coarse, rf, mc)
+    np.testing.assert_allclose(rc, ref, rtol=0, atol=1e-12)
+    rf32 = rf.astype(np.float32)
+    rc32 = np.zeros((9, nc), dtype=np.float32)
+    lib.host_restrict_nested_f32(_p(fn, C.c_int), _p(cn, C.c_int), _p(rf32, C.c_float),
+                                 _p(_bits(mc), C.c_ushort), _p(rc32, C.c_float))
+    ref32 = T.restrict(fine, coarse, rf32.astype(np.float64), mc)
+    np.testing.assert_allclose(rc32, ref32, rtol=0, atol=2e-6 * np.abs(ref32).max())
+
+
+def test_non_nested_pairs_are_not_nested(lib):
+    for fine, coarse in PAIRS[1:3]:
+        fn, cn = np.array(fine, dtype=np.int32), np.array(coarse, dtype=np.int32)
+        assert lib.host_nested(_p(fn, C.c_int), _p(cn, C.c_int)) == 0

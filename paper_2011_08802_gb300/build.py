@@ -14,7 +14,12 @@ OUT = os.path.join(HERE, "_lib")
 SOURCES = ["fe_kernels.cu", "mg_kernels.cu", "krylov_kernels.cu", "diag_kernels.cu", "contact_kernels.cu",
            "batch.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+# -fno-gnu-unique: function-local statics of templates and inline functions
+# become ordinary weak symbols instead of process-wide unique ones, and the
+# version script (csrc/exports.map) keeps everything but the C ABI local, so
+# libpfm.so and libpfm_nv12.so share no state when one process loads both
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler", "-fno-gnu-unique"]
+EXPORTS = os.path.join(CSRC, "exports.map")
 
 
 def nvcc() -> str:
@@ -68,7 +73,8 @@ def build(verbose: bool = False, ptxas_info: bool = False, out_dir: str | None =
         raise RuntimeError(f"nvcc failed for {failed}")
     for lib, objs in jobs:
         tmp = lib + ".tmp"
-        subprocess.check_call([nvcc(), *ARCH, "-shared", *[o for _, o, _ in objs], "-o", tmp, "-lcudart"])
+        subprocess.check_call([nvcc(), *ARCH, "-shared", *[o for _, o, _ in objs], "-o", tmp, "-lcudart",
+                               "-Xlinker", f"--version-script={EXPORTS}"])
         os.replace(tmp, lib)
     return jobs[0][0]
 

@@ -110,16 +110,26 @@ __global__ void __launch_bounds__(1024) k_sum_fixed(int64_t n, const double* __r
 
 // Gauss-point Hessians of one level, computed in TC (FP64 for the finest and
 // the coarsest level, FP32 for the intermediate levels of an FP32
-// preconditioner) and stored in the requested precisions.
+// preconditioner) and stored in the requested precisions. Warps walk the
+// element blocks with a grid stride, so the launch can bound the number of
+// resident threads (and with it the footprint of the per-thread stack of the
+// point physics, which then stays in L2).
 template <typename TC>
 __global__ void __launch_bounds__(128) k_linearize(Grid g, DevParams P, const double* __restrict__ U,
                                                    const double* __restrict__ Un,
                                                    double* __restrict__ H64, float* __restrict__ H32,
                                                    float* __restrict__ H32lo) {
-  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if ((tid >> 5) >= g.nblk()) return;  // whole warps only (padding lanes stay)
-  linearize_lane<TC>(g, P, U, Un, H64, H32, H32lo, tid >> 5, int(tid & 31));
+  const int64_t w0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t blk = w0; blk < g.nblk(); blk += nw)  // whole warps only (padding lanes stay)
+    linearize_lane<TC>(g, P, U, Un, H64, H32, H32lo, blk, int(threadIdx.x & 31));
 }
+
+// Resident CTAs per SM of the FP64-class linearisation (0: one warp per
+// element block, as many CTAs as that takes).
+#ifndef PFM_LIN_CTAS_PER_SM
+#define PFM_LIN_CTAS_PER_SM 0
+#endif
 
 // ---- BEGIN tangent application kernel
 // Bulk prefetch of a contiguous global range into L2 by the bulk-copy engine
@@ -164,6 +174,11 @@ __global__ void __launch_bounds__(256, PFM_JAPPLY_MINB) k_japply(Grid g, JParams
 #ifndef PFM_JAPPLY_H16_MINB
 #define PFM_JAPPLY_H16_MINB PFM_JAPPLY_MINB
 #endif
+// bulk L2 prefetch of each element block's binary16 Hessians (off: measured
+// slower for this kernel, which is limited by its per-element work)
+#ifndef PFM_H16_PREFETCH
+#define PFM_H16_PREFETCH 0
+#endif
 template <bool DET>
 __global__ void __launch_bounds__(256, PFM_JAPPLY_H16_MINB) k_japply_h16(Grid g, JParams<float> jp, float wh,
                                                     const __half* __restrict__ H,
@@ -174,7 +189,15 @@ __global__ void __launch_bounds__(256, PFM_JAPPLY_H16_MINB) k_japply_h16(Grid g,
   const int64_t wg = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   const int lane = int(threadIdx.x & 31);
+#if PFM_H16_PREFETCH
+  constexpr unsigned BLK_BYTES = unsigned(HBLK * sizeof(__half));
+  for (int64_t blk = wg; blk < nblk; blk += nw) {
+    if (lane == 0) prefetch_l2(H + blk * HBLK, BLK_BYTES);
+    japply_block_h16<DET>(g, jp, wh, H, mask, v, y, blk, lane, W, ws);
+  }
+#else
   for (int64_t blk = wg; blk < nblk; blk += nw) japply_block_h16<DET>(g, jp, wh, H, mask, v, y, blk, lane, W, ws);
+#endif
 }
 
 // y += J v with v in FP32 (exact input), the tangent as Hhi + Hlo (two FP32
@@ -378,6 +401,8 @@ __global__ void k_identity_rows(int64_t nn, const dmask_t* __restrict__ mask, co
 
 }  // namespace
 
+int sm_count();
+
 void launch_residual(const Grid& g, const DevParams& P, const double* U, const double* Un,
                      const dmask_t* mask, double* R, double* energy, cudaStream_t s, double* W) {
   const int64_t threads = g.nblk() * 32;
@@ -399,12 +424,17 @@ void launch_residual(const Grid& g, const DevParams& P, const double* U, const d
 void launch_linearize(const Grid& g, const DevParams& P, const double* U, const double* Un,
                       double* H64, float* H32, float* H32lo, int arith, cudaStream_t s) {
   const int64_t threads = g.nblk() * 32;
+  unsigned blocks = grid_for(threads, 128);
+  if (arith != LIN_F32 && PFM_LIN_CTAS_PER_SM > 0) {
+    const int64_t cap = int64_t(sm_count()) * PFM_LIN_CTAS_PER_SM;
+    if (int64_t(blocks) > cap) blocks = unsigned(cap);
+  }
   if (arith == LIN_F32)
-    k_linearize<float><<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo);
+    k_linearize<float><<<blocks, 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo);
   else if (arith == LIN_DF)
-    k_linearize<df64><<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo);
+    k_linearize<df64><<<blocks, 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo);
   else
-    k_linearize<double><<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo);
+    k_linearize<double><<<blocks, 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo);
   count_launches(1);
 }
 

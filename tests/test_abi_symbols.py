@@ -74,3 +74,23 @@ def test_noalloc_path_names_no_allocator():
     kr = code(open(os.path.join(csrc, "krylov_kernels.cu")).read())
     assert not call.search(_body(fe, "void launch_residual("))
     assert not call.search(_body(kr, "void launch_build_mask("))
+
+
+@pytest.mark.parametrize("n_var", [6, 12])
+def test_libraries_export_only_the_c_abi(lib, n_var):
+    """Both libraries (6 and 12 variants, built from the same sources) export
+    the pfm_* entry points and nothing else, and define no process-wide unique
+    symbols, so one process can load both without their internal state (e.g.
+    function-local statics of templates) being merged."""
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("no nm")
+    path = abi.lib_path(n_var)
+    if not os.path.exists(path):
+        pytest.skip("library not built")
+    import subprocess
+    out = subprocess.check_output([nm, "-D", "--defined-only", path], text=True).split("\n")
+    names = [ln.split()[-1] for ln in out if ln.strip()]
+    assert names and all(n.startswith("pfm_") for n in names), [n for n in names if not n.startswith("pfm_")][:5]
+    kinds = [ln.split()[1] for ln in subprocess.check_output([nm, path], text=True).split("\n") if len(ln.split()) == 3]
+    assert "u" not in kinds

@@ -129,3 +129,30 @@ def test_engine_newton_converges_and_reuses_graphs(binding):
     for a, c in zip(*results):
         assert np.linalg.norm(a - c) <= 1e-7 * np.linalg.norm(a)
     B.close()
+
+
+def test_batch_member_at_the_top_of_the_size_range(binding):
+    """The n = 24 member of the 64-problem benchmark batch (its seed, depth
+    and 2-element coarsest level), solved by the batched engine beside a
+    small problem: the oracle's K x + R over every element and node (chunked
+    over the host cores) is below 1e-8 ||R||."""
+    from oracle_pool import OraclePool
+    ns, depths = inputs.batch_sizes(count=64, seed=4)
+    k = ns.index(24)
+    st = inputs.config_indentation(24, seed=1000 + k, step=1, n_steps=10, depth_frac=depths[k])
+    other = inputs.config_indentation(9, seed=1001, step=1, n_steps=10, depth_frac=0.01)
+    with OraclePool() as pool:
+        probs = [binding.problem_from_state(s, n_levels=binding.levels_to(s.mesh.nx, 2)) for s in (st, other)]
+        B = binding.Batch(probs)
+        Us = [torch.from_numpy(s.U.copy()).cuda() for s in (st, other)]
+        reps = B.newton_solve(Us, abi.default_opts(abi.PFM_F32, max_newton=1, lin_rtol=1e-9, max_lin_it=400))
+        assert all(r.newton_its == 1 for r in reps)
+        x = Us[0].cpu().numpy() - st.U
+        R = pool.residuals([st])[0]
+        rows = pool.rows_Kx_plus_R(st, x, np.arange(st.mesh.n_elems), np.arange(st.mesh.n_nodes))
+        B.close()
+        for P in probs:
+            P.close()
+    rel = np.linalg.norm(rows) / np.linalg.norm(R)
+    print(f"n = 24 batch member: ||K x + R|| / ||R|| = {rel:.3e}")
+    assert rel <= 1e-8

@@ -35,6 +35,23 @@ def ragged():
     return dict(st=st, mat=mat, disc=disc, d=d, K=fe.tangent(disc, st, mat, d), R=fe.residual(disc, st, mat, d))
 
 
+def test_both_libraries_in_one_process(binding, ragged):
+    """A six-variant problem linearised first, then a twelve-variant one on two
+    levels: each library keeps its own launch settings (the diagonal-block
+    kernel's shared-memory size differs between them)."""
+    st6 = inputs.config_random(6, 5, 4, seed=123, eta_lo=0.0, eta_hi=0.3, Lx=12.0, Ly=10.0, Lz=8.0)
+    P6 = binding.problem_from_state(st6)
+    P6.linearize(abi.PFM_F32)
+    P6.linearize(abi.PFM_F64)
+    P12 = binding.problem_from_state(ragged["st"])
+    assert P12.n_levels == 2
+    P12.linearize(abi.PFM_F32)
+    P12.linearize(abi.PFM_F64)
+    P6.linearize(abi.PFM_F32)
+    P6.close()
+    P12.close()
+
+
 def test_library_has_twelve_variants(binding, ragged):
     P = binding.problem_from_state(ragged["st"])
     assert P.n_var == NV and P.shape == (15, ragged["st"].mesh.n_nodes)

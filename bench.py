@@ -634,19 +634,26 @@ def nv12_measure(dev, n: int):
     t = out["japply_f32"]["ms"]
     out["japply_f32"].update({"bytes_per_launch": alg, "gbs": alg / (t * 1e-3) / 1e9,
                               "hbm_frac": alg / (t * 1e-3) / 1e9 / peak, "peak_kind": kind})
+    P.close()
+    # Newton step at the first step of an 80-step ramp (cap depth 0.016 nm):
+    # the 10-step increment compresses the top element layer at 128^3 by
+    # ~25 % and FGMRES does not converge there with twelve variants
+    st = inputs.config_indentation(n, seed=5, step=1, n_steps=80, n_var=12)
+    P = binding.problem_from_state(st)
     U0 = torch.from_numpy(st.U).to(dev)
-    o = abi.default_opts(abi.PFM_F32, max_newton=1, restart=30, max_lin_it=400, lin_rtol=1e-8, krylov=1,
+    o = abi.default_opts(abi.PFM_F32, max_newton=1, restart=30, max_lin_it=200, lin_rtol=1e-8, krylov=1,
                          switch_rtol=1e-4)
     U = U0.clone()
-    P.newton_solve(U, o)
+    P.newton_solve(U, o, check=False)
     U = U0.clone()
     torch.cuda.synchronize()
     e0.record()
-    rep = P.newton_solve(U, o)
+    rep = P.newton_solve(U, o, check=False)
     e1.record()
     torch.cuda.synchronize()
     out["newton_step"] = {"s": e0.elapsed_time(e1) / 1e3, "fgmres_its": rep.lin_its_last,
-                          "lin_rel_residual": rep.lin_res_final}
+                          "lin_rel_residual": rep.lin_res_final, "converged": rep.status == 0,
+                          "load_increment": "step 1 of 80 (cap depth 0.016 nm)"}
     P.close()
     return out
 

@@ -412,6 +412,16 @@ pfm_status pfm_qp_eval(pfm_handle* h, int64_t n, const double* F_dev, const doub
  * outside the grid, NULL output), PFM_ERR_STATE (no tangent), PFM_ERR_CUDA. */
 pfm_status pfm_get_hessians(pfm_handle* h, int64_t e0, int64_t count, double* hess_host);
 
+/* Point-block Jacobi inverses of multigrid level l (0 = finest; not the
+ * coarsest, which is solved directly) after pfm_linearize, for testing: the
+ * inverse of each node's 9x9 diagonal block of the level's tangent (Dirichlet
+ * rows and columns replaced by identity; Sec. 3.4), nodes [n0, n0 + count),
+ * written to inv_host (host double [count][9][9], row-major; stored in the
+ * preconditioner's precision). Synchronises. Errors: PFM_ERR_INVALID_ARG
+ * (level or range out of bounds, NULL output), PFM_ERR_STATE (no tangent),
+ * PFM_ERR_CUDA. */
+pfm_status pfm_get_block_inverses(pfm_handle* h, int level, int64_t n0, int64_t count, double* inv_host);
+
 /* Device timing of the hot phases with CUDA events recorded on the handle's
  * stream around each launch (off by default; enabling clears the counters).
  * Timed phases: PFM_PROF_JAPPLY_F32 / _F64 = one tangent application on the

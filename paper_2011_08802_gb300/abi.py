@@ -245,6 +245,7 @@ def lib(n_var: int = 6):
         "pfm_newton_solve": (i32, [H, C.POINTER(SolveOpts), vp, C.POINTER(SolveReport)]),
         "pfm_qp_eval": (i32, [H, i64, vp, vp, vp, vp, vp, vp]),
         "pfm_get_hessians": (i32, [H, i64, i64, vp]),
+        "pfm_get_block_inverses": (i32, [H, i32, i64, i64, vp]),
         "pfm_profile_enable": (i32, [H, i32]),
         "pfm_profile_get": (i32, [H, i32, C.POINTER(i64), C.POINTER(dp)]),
         "pfm_launch_count": (i64, []),
@@ -280,7 +281,7 @@ def exported_symbols():
         "pfm_set_stream", "pfm_get_level", "pfm_set_power_iterations", "pfm_set_outer_operator", "pfm_set_deterministic", "pfm_set_params", "pfm_set_dirichlet", "pfm_set_state", "pfm_get_state",
         "pfm_residual", "pfm_diagnostics", "pfm_set_contact", "pfm_contact_load", "pfm_set_linearize_arithmetic", "pfm_set_preconditioner_store", "pfm_linearize", "pfm_jacobian_apply", "pfm_jacobian_transpose_apply",
         "pfm_jacobian_apply_host", "pfm_jacobian_apply_mixed", "pfm_vcycle", "pfm_fgmres_solve", "pfm_newton_solve",
-        "pfm_qp_eval", "pfm_get_hessians", "pfm_profile_enable", "pfm_profile_get",
+        "pfm_qp_eval", "pfm_get_hessians", "pfm_get_block_inverses", "pfm_profile_enable", "pfm_profile_get",
         "pfm_launch_count", "pfm_param_grad", "pfm_batch_create", "pfm_batch_destroy",
         "pfm_batch_last_error", "pfm_batch_newton_solve", "pfm_batch_set_mode", "pfm_residual_noalloc", "pfm_noalloc_last_error",
     ]

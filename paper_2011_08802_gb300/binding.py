@@ -246,6 +246,13 @@ class Problem:
         self._check(self._lib.pfm_profile_get(self.h, phase, C.byref(n), C.byref(ms)))
         return n.value, ms.value
 
+    def get_block_inverses(self, level: int, n0: int, count: int) -> np.ndarray:
+        """``pfm_get_block_inverses``: (count, nf, nf) inverted nodal diagonal blocks."""
+        nf = self.shape[0]
+        out = np.empty((count, nf, nf))
+        self._check(self._lib.pfm_get_block_inverses(self.h, level, n0, count, _ptr(out)))
+        return out
+
     def get_hessians(self, e0: int, count: int) -> np.ndarray:
         out = np.empty((count, 8, self.n_hess))
         self._check(self._lib.pfm_get_hessians(self.h, e0, count, _ptr(out)))

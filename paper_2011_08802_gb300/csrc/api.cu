@@ -1532,6 +1532,35 @@ pfm_status pfm_get_hessians(pfm_handle* h, int64_t e0, int64_t count, double* he
   return PFM_OK;
 }
 
+pfm_status pfm_get_block_inverses(pfm_handle* h, int level, int64_t n0, int64_t count, double* inv_host) {
+  TRY(check_ready(h, true));
+  if (level < 0 || level + 1 >= int(h->L.size()))
+    return h->fail(PFM_ERR_INVALID_ARG, "level out of range (the coarsest level has no block inverses)");
+  Level& lv = h->L[level];
+  if (n0 < 0 || count < 0 || n0 + count > lv.nn || (!inv_host && count > 0))
+    return h->fail(PFM_ERR_INVALID_ARG, "node range out of bounds");
+  if (count == 0) return PFM_OK;
+  const bool f32 = h->lin_prec == PFM_F32;
+  if ((f32 && !lv.D32) || (!f32 && !lv.D64)) return h->fail(PFM_ERR_STATE, "no block inverses on this level");
+  std::vector<double> buf(size_t(NF2) * count);
+  std::vector<float> b32(f32 ? size_t(count) : 0);
+  for (int e = 0; e < NF2; ++e) {
+    if (f32) {
+      CK(cudaMemcpyAsync(b32.data(), lv.D32 + int64_t(e) * lv.nn + n0, sizeof(float) * count,
+                         cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      for (int64_t i = 0; i < count; ++i) buf[size_t(e) * count + i] = b32[i];
+    } else {
+      CK(cudaMemcpyAsync(buf.data() + size_t(e) * count, lv.D64 + int64_t(e) * lv.nn + n0, sizeof(double) * count,
+                         cudaMemcpyDeviceToHost, h->stream));
+    }
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  for (int64_t i = 0; i < count; ++i)
+    for (int e = 0; e < NF2; ++e) inv_host[i * NF2 + e] = buf[size_t(e) * count + i];
+  return PFM_OK;
+}
+
 pfm_status pfm_profile_enable(pfm_handle* h, int enable) {
   if (!h) return PFM_ERR_INVALID_ARG;
   prof_collect(h);

@@ -36,17 +36,25 @@ def _oracle_block_inverses(st, n_var):
 
 
 @pytest.mark.parametrize("n_var", [6, 12])
-@pytest.mark.parametrize("prec, tol", [(abi.PFM_F64, 1e-10), (abi.PFM_F32, 1e-4)])
-def test_block_inverses_match_oracle(binding, n_var, prec, tol):
+@pytest.mark.parametrize("prec, unit", [(abi.PFM_F64, 2.0 ** -53), (abi.PFM_F32, 2.0 ** -24)])
+def test_block_inverses_match_oracle(binding, n_var, prec, unit):
+    """Per block, the relative error of the inverse is bounded by a modest
+    multiple of the unit roundoff of the preconditioner's precision times the
+    block's condition number (entries rounded to that precision, summed over
+    the element contributions, then Gauss-Jordan with partial pivoting)."""
     st = inputs.config_random(7, 5, 4, seed=131, eta_lo=-0.02, eta_hi=0.3 if n_var == 6 else 0.07, Lx=14.0,
                               Ly=10.0, Lz=8.0, n_var=n_var)
     inv_o = _oracle_block_inverses(st, n_var)
+    kappa = np.linalg.cond(np.linalg.inv(inv_o))
     P = binding.problem_from_state(st)
     assert P.n_levels >= 2
     P.linearize(prec)
     inv_g = P.get_block_inverses(0, 0, st.mesh.n_nodes)
     err = np.abs(inv_g - inv_o).reshape(len(inv_o), -1).max(1) / np.abs(inv_o).reshape(len(inv_o), -1).max(1)
-    assert err.max() <= tol, (err.max(), int(err.argmax()))
+    bound = 200.0 * unit * kappa
+    print(f"N = {n_var}, prec {prec}: worst error / bound {np.max(err / bound):.3f}, "
+          f"kappa {kappa.min():.1f}..{kappa.max():.1f}")
+    assert np.all(err <= bound), (err.max(), int(np.argmax(err / bound)))
     # a node range in the middle
     n0 = st.mesh.n_nodes // 3
     np.testing.assert_array_equal(P.get_block_inverses(0, n0, 5), inv_g[n0:n0 + 5])

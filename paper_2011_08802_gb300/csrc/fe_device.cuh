@@ -344,11 +344,10 @@ __device__ __forceinline__ void scatter_row(TY* __restrict__ y, TW* __restrict__
 // at the element nodes (Dirichlet DOFs read as 0), dz = (grad du, d eta_hat)
 // at the Gauss points, sigma = H dz from the packed symmetric store, plus the
 // constant gradient-energy term, scattered back with atomics.
-template <typename T, bool DET = false>
+template <typename T>
 __device__ __forceinline__ void japply_block(const Grid& g, const JParams<T>& jp, const T* __restrict__ H,
                                              const dmask_t* __restrict__ mask, const T* __restrict__ v,
-                                             T* __restrict__ y, int64_t blk, int lane, T* __restrict__ W = nullptr,
-                                             int64_t ws = 0) {
+                                             T* __restrict__ y, int64_t blk, int lane) {
   constexpr int V = 16 / sizeof(T);
   using VT = typename Vec16<T>::type;
   const int l8 = lane & 7;
@@ -393,7 +392,7 @@ __device__ __forceinline__ void japply_block(const Grid& g, const JParams<T>& jp
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     T r = q1_scatter_grad(w * sg[3 * i], w * sg[3 * i + 1], w * sg[3 * i + 2], l8, jp.ihx, jp.ihy, jp.ihz);
-    scatter_row<DET>(y, W, ws, i, blk, lane, i * nn + node, r, valid && !((dm >> i) & 1));
+    if (valid && !((dm >> i) & 1)) atomicAdd(&y[i * nn + node], r);
   }
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
@@ -406,10 +405,82 @@ __device__ __forceinline__ void japply_block(const Grid& g, const JParams<T>& jp
       gf[d] = w * s;
     }
     T r = q1_scatter(w * sg[9 + k], gf[0], gf[1], gf[2], l8, jp.ihx, jp.ihy, jp.ihz);
-    scatter_row<DET>(y, W, ws, 3 + k, blk, lane, (3 + k) * nn + node, r, valid && !((dm >> (3 + k)) & 1));
+    if (valid && !((dm >> (3 + k)) & 1)) atomicAdd(&y[(3 + k) * nn + node], r);
   }
 }
 // ---- END tangent application kernel
+
+// The same body in the atomic-free form (deterministic mode): the lane's
+// nodal results go to the scratch W for the node pass (scatter_row).
+// y += J v on the 4 elements of block blk (this warp; lane = 0..31): gather v
+// at the element nodes (Dirichlet DOFs read as 0), dz = (grad du, d eta_hat)
+// at the Gauss points, sigma = H dz from the packed symmetric store, plus the
+// constant gradient-energy term, scattered back with atomics.
+template <typename T>
+__device__ __forceinline__ void japply_block_det(const Grid& g, const JParams<T>& jp, const T* __restrict__ H,
+                                                 const dmask_t* __restrict__ mask, const T* __restrict__ v,
+                                                 T* __restrict__ W, int64_t ws, int64_t blk, int lane) {
+  constexpr int V = 16 / sizeof(T);
+  using VT = typename Vec16<T>::type;
+  const int l8 = lane & 7;
+  const int64_t nn = g.nn();
+  const int64_t e = blk * 4 + (lane >> 3);
+  const bool valid = e < g.ne();
+  const int64_t node = valid ? elem_node(g, e, l8) : 0;
+  const dmask_t dm = valid ? mask[node] : MASK_ALL;
+  T dz[NZ], ge[3 * NV];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T x = ((dm >> i) & 1) ? T(0) : v[i * nn + node];
+    T val;
+    q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, val, dz[3 * i], dz[3 * i + 1], dz[3 * i + 2]);
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    T x = ((dm >> (3 + k)) & 1) ? T(0) : v[(3 + k) * nn + node];
+    q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, dz[9 + k], ge[3 * k], ge[3 * k + 1], ge[3 * k + 2]);
+  }
+  // sigma = H dz from the packed symmetric store
+  T sg[NZ];
+#pragma unroll
+  for (int r = 0; r < NZ; ++r) sg[r] = T(0);
+  const VT* Hv = reinterpret_cast<const VT*>(H) + blk * (NHP / V) * 32 + lane;
+#pragma unroll
+  for (int j = 0; j < NHP / V; ++j) {
+    T hv[V];
+    Vec16<T>::unpack(__ldcs(Hv + j * 32), hv);
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      const int idx = j * V + t;
+      if (idx >= NH) continue;  // zero padding of the store
+      // (r, c) of packed index idx (constant-folded after unrolling)
+      const int r = packed_row(idx);
+      const int c = r + (idx - packed_row_start(r));
+      sg[r] += hv[t] * dz[c];
+      if (c != r) sg[c] += hv[t] * dz[r];
+    }
+  }
+  const T w = jp.w;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T r = q1_scatter_grad(w * sg[3 * i], w * sg[3 * i + 1], w * sg[3 * i + 2], l8, jp.ihx, jp.ihy, jp.ihz);
+    scatter_row<true>(static_cast<T*>(nullptr), W, ws, i, blk, lane, i * nn + node, r, valid && !((dm >> i) & 1));
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    T gf[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      T s = T(0);
+#pragma unroll
+      for (int l = 0; l < NV; ++l) s += jp.G[k][l] * ge[3 * l + d];
+      gf[d] = w * s;
+    }
+    T r = q1_scatter(w * sg[9 + k], gf[0], gf[1], gf[2], l8, jp.ihx, jp.ihy, jp.ihz);
+    scatter_row<true>(static_cast<T*>(nullptr), W, ws, 3 + k, blk, lane, (3 + k) * nn + node, r, valid && !((dm >> (3 + k)) & 1));
+  }
+}
+
 
 // y += J v on element block blk from a binary16 copy of the store holding
 // s H (FP32 arithmetic): the same gather, contraction and scatter as

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(256, PFM_JAPPLY_MINB) k_japply_det(Grid g, JPa
   constexpr unsigned BLK_BYTES = unsigned(HBLK * sizeof(T));
   for (int64_t blk = wg; blk < nblk; blk += nw) {
     if (lane == 0) prefetch_l2(H + blk * HBLK, BLK_BYTES);
-    japply_block<T, true>(g, jp, H, mask, v, nullptr, blk, lane, W, ws);
+    japply_block_det<T>(g, jp, H, mask, v, W, ws, blk, lane);
   }
 }
 

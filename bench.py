@@ -73,8 +73,9 @@ def parse_args():
                    help="skip the mixed step with the FP64-class operator in every FGMRES iteration")
     p.add_argument("--switch-rtol", type=float, default=1e-4,
                    help="relative residual estimate below which FGMRES uses FP32 products (krylov = 1)")
-    p.add_argument("--mode", default="newton", choices=["newton", "japply"],
-                   help="japply: only K FP32 tangent applications (for profiler captures)")
+    p.add_argument("--mode", default="newton", choices=["newton", "japply", "peaks"],
+                   help="japply: only K FP32 tangent applications (for profiler captures); "
+                        "peaks: the FP32 and FP64 FMA throughput of the device (pfm_arith_peak)")
     return p.parse_args()
 
 
@@ -945,6 +946,8 @@ def gpu_arm(args, rank, world, dist):
         P = None
         batch = batch_measure(args, dev)
 
+    peaks = {"fp32_tflops": binding.arith_peak(abi.PFM_F32), "fp64_tflops": binding.arith_peak(abi.PFM_F64)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         c1, desc1, _ = oracle_jvp_sample(args.n, args.sample, seconds=5.0)
@@ -976,6 +979,7 @@ def gpu_arm(args, rank, world, dist):
             "anisotropic_011": aniso,
             "cpu_baseline": cpu,
             "f16_store": f16,
+            "arith_peaks_measured": peaks,
             "phase_ms_per_step": {
                 "japply_f32": ms32 / args.steps, "japply_f64": ms64 / args.steps,
                 "linearize_fine": mslin / args.steps, "residual": msres / args.steps,
@@ -1023,6 +1027,10 @@ def main():
         dist = tdist
     if args.impl == "reference":
         reference_arm(args, rank)
+    elif args.mode == "peaks":
+        from paper_2011_08802_gb300 import abi, binding
+        print(json.dumps({"mode": "peaks", "fp32_tflops": binding.arith_peak(abi.PFM_F32),
+                          "fp64_tflops": binding.arith_peak(abi.PFM_F64)}), flush=True)
     elif args.mode == "japply":
         japply_only(args)
     else:

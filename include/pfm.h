@@ -450,6 +450,16 @@ pfm_status pfm_profile_get(pfm_handle* h, int id, int64_t* launches, double* tot
 /* Kernel launches issued by the library in this process so far (all handles). */
 int64_t pfm_launch_count(void);
 
+/* Measurement aid (the paper has no counterpart): the fused multiply-add
+ * throughput of the current device in TFLOP/s (2 flops per FMA) for
+ * precision PFM_F32 or PFM_F64, from a kernel of 8 independent FMA chains per
+ * thread on 8 x 256 threads per SM (best of three timed runs after one
+ * warm-up). The rooflines of the FP32- and FP64-bound kernels are stated
+ * against these figures. Allocates and frees a small device buffer;
+ * synchronises the device. Errors: PFM_ERR_INVALID_ARG (NULL output or other
+ * precision), PFM_ERR_OOM, PFM_ERR_CUDA. */
+pfm_status pfm_arith_peak(int precision, double* tflops);
+
 /* A batch of independent problems of possibly different grid sizes, each a
  * handle with its own Dirichlet data and state, solved together by
  * pfm_batch_newton_solve (batched engine or lockstep driver, below). The

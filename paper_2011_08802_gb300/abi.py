@@ -249,6 +249,7 @@ def lib(n_var: int = 6):
         "pfm_profile_enable": (i32, [H, i32]),
         "pfm_profile_get": (i32, [H, i32, C.POINTER(i64), C.POINTER(dp)]),
         "pfm_launch_count": (i64, []),
+        "pfm_arith_peak": (i32, [i32, C.POINTER(dp)]),
         "pfm_param_grad": (i32, [H, vp, C.POINTER(dp), C.POINTER(dp), vp]),
         "pfm_batch_create": (i32, [C.POINTER(H), i32, C.POINTER(H)]),
         "pfm_batch_destroy": (None, [H]),
@@ -282,7 +283,7 @@ def exported_symbols():
         "pfm_residual", "pfm_diagnostics", "pfm_set_contact", "pfm_contact_load", "pfm_set_linearize_arithmetic", "pfm_set_preconditioner_store", "pfm_linearize", "pfm_jacobian_apply", "pfm_jacobian_transpose_apply",
         "pfm_jacobian_apply_host", "pfm_jacobian_apply_mixed", "pfm_vcycle", "pfm_fgmres_solve", "pfm_newton_solve",
         "pfm_qp_eval", "pfm_get_hessians", "pfm_get_block_inverses", "pfm_profile_enable", "pfm_profile_get",
-        "pfm_launch_count", "pfm_param_grad", "pfm_batch_create", "pfm_batch_destroy",
+        "pfm_launch_count", "pfm_arith_peak", "pfm_param_grad", "pfm_batch_create", "pfm_batch_destroy",
         "pfm_batch_last_error", "pfm_batch_newton_solve", "pfm_batch_set_mode", "pfm_residual_noalloc", "pfm_noalloc_last_error",
     ]
 

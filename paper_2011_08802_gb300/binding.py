@@ -316,6 +316,15 @@ def residual_noalloc(mesh, params: abi.Params, mask: torch.Tensor, U: torch.Tens
     return R, e.value
 
 
+def arith_peak(precision: int) -> float:
+    """``pfm_arith_peak``: measured FMA throughput (TFLOP/s) of the current device."""
+    t = C.c_double()
+    st = abi.lib().pfm_arith_peak(precision, C.byref(t))
+    if st != 0:
+        raise PfmError(st, "arithmetic peak probe failed")
+    return t.value
+
+
 def launch_count() -> int:
     """Kernel launches issued by the library in this process (``pfm_launch_count``)."""
     return int(abi.lib().pfm_launch_count())

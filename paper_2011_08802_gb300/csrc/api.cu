@@ -18,6 +18,24 @@ using namespace pfm;
 
 namespace {
 std::atomic<int64_t> g_launches{0};
+
+// Arithmetic peak probe: every thread runs 8 independent chains of fused
+// multiply-adds (x = x * a + b) for `iters` steps and stores their sum, so
+// the compiler keeps every operation.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_peak(int iters, T a, T b, T* __restrict__ out) {
+  T x[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) x[c] = T(threadIdx.x + c);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = fma(x[c], a, b);
+  }
+  T s = T(0);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += x[c];
+  out[int64_t(blockIdx.x) * blockDim.x + threadIdx.x] = s;
+}
 }  // namespace
 
 void pfm::count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -1578,6 +1596,42 @@ pfm_status pfm_profile_get(pfm_handle* h, int id, int64_t* launches, double* tot
 }
 
 int64_t pfm_launch_count(void) { return g_launches.load(); }
+
+pfm_status pfm_arith_peak(int precision, double* tflops) {
+  if (!tflops || (precision != PFM_F32 && precision != PFM_F64)) return PFM_ERR_INVALID_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return PFM_ERR_CUDA;
+  const int blocks = sms * 8, threads = 256;
+  const int iters = precision == PFM_F32 ? 1 << 16 : 1 << 11;
+  const size_t bytes = size_t(blocks) * threads * 8;
+  void* out = nullptr;
+  if (cudaMalloc(&out, bytes) != cudaSuccess) return PFM_ERR_OOM;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {  // the first run is a warm-up
+    cudaEventRecord(e0);
+    if (precision == PFM_F32)
+      k_fma_peak<float><<<blocks, threads>>>(iters, 0.999f, 1e-3f, static_cast<float*>(out));
+    else
+      k_fma_peak<double><<<blocks, threads>>>(iters, 0.999, 1e-3, static_cast<double*>(out));
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  pfm::count_launches(4);
+  const cudaError_t e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (e != cudaSuccess) return PFM_ERR_CUDA;
+  *tflops = 2.0 * 8.0 * double(iters) * double(blocks) * threads / (double(best) * 1e-3) / 1e12;
+  return PFM_OK;
+}
 
 }  // extern "C"
 

@@ -241,6 +241,13 @@ pfm_status pfm_get_state(pfm_handle* h, double* U_dev);
  * way. Errors: PFM_ERR_INVALID_ARG (other values). */
 pfm_status pfm_set_linearize_arithmetic(pfm_handle* h, int double_float);
 
+/* Arithmetic of the residual's point physics (pfm_residual and the residuals
+ * of pfm_newton_solve; Sec. 3.4, Eq. FinalRes): 0 = FP64 (default), 1 =
+ * double-float (pairs of FP32 numbers, about 48 significant bits, on the FP32
+ * pipes; divisions, square roots and logarithms in FP64). Element sums and
+ * the output stay FP64. Errors: PFM_ERR_INVALID_ARG (other values). */
+pfm_status pfm_set_residual_arithmetic(pfm_handle* h, int double_float);
+
 /* Storage of the Gauss-point Hessians that the FP32 preconditioner's tangent
  * applications read (smoothing, residuals and eigenvalue estimates of every
  * level but the coarsest; Sec. 3.4): 0 = FP32 (default), 1 = binary16 copies

@@ -139,6 +139,10 @@ class Problem:
         point physics in the FP64-class linearisation."""
         self._check(self._lib.pfm_set_linearize_arithmetic(self.h, int(bool(double_float))))
 
+    def set_residual_arithmetic(self, double_float: bool):
+        """``pfm_set_residual_arithmetic``: residual point physics in FP64 (False) or double-float (True)."""
+        self._check(self._lib.pfm_set_residual_arithmetic(self.h, int(bool(double_float))))
+
     def set_preconditioner_store(self, half: bool):
         """``pfm_set_preconditioner_store``: the FP32 preconditioner reads its
         Gauss-point Hessians from the FP32 store (False) or from per-level

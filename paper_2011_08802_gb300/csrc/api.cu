@@ -305,7 +305,7 @@ pfm_status residual_impl(pfm_handle* h, double* R, double* energy_host) {
   CK(cudaMemsetAsync(h->energy_dev, 0, sizeof(double), s));
   {
     ProfScope ps(h, PFM_PROF_RESIDUAL);
-    launch_residual(f.g, h->dp, f.U, f.Un, f.mask, R, h->energy_dev, s, det_W<double>(h));
+    launch_residual(f.g, h->dp, f.U, f.Un, f.mask, R, h->energy_dev, s, det_W<double>(h), h->res_df);
     if (h->contact_on) launch_contact_residual(f.g, h->contact, f.U, f.mask, R, h->energy_dev, nullptr, s);
   }
   CKL();
@@ -1234,6 +1234,13 @@ pfm_status pfm_set_linearize_arithmetic(pfm_handle* h, int double_float) {
   if (double_float != 0 && double_float != 1) return h->fail(PFM_ERR_INVALID_ARG, "expected 0 or 1");
   h->lin_df = double_float != 0;
   h->linearized = false;
+  return PFM_OK;
+}
+
+pfm_status pfm_set_residual_arithmetic(pfm_handle* h, int double_float) {
+  if (!h) return PFM_ERR_INVALID_ARG;
+  if (double_float != 0 && double_float != 1) return h->fail(PFM_ERR_INVALID_ARG, "expected 0 or 1");
+  h->res_df = double_float != 0;
   return PFM_OK;
 }
 

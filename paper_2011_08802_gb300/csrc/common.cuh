@@ -62,8 +62,10 @@ void count_launches(int n);
 // non-null = the atomic-free two-pass form (per-(element, node) contributions
 // in W, summed per node in a fixed order; bitwise reproducible). W holds
 // 9 * 32 * nblk entries of the output type (+ nblk for the residual's energy).
+// df: the point physics in double-float arithmetic (FP32 pipes) instead of FP64
 void launch_residual(const Grid& g, const DevParams& P, const double* U, const double* Un,
-                     const dmask_t* mask, double* R, double* energy, cudaStream_t s, double* W = nullptr);
+                     const dmask_t* mask, double* R, double* energy, cudaStream_t s, double* W = nullptr,
+                     bool df = false);
 // arithmetic of the point physics in the linearisation
 enum { LIN_F64 = 0, LIN_F32 = 1, LIN_DF = 2 };
 void launch_linearize(const Grid& g, const DevParams& P, const double* U, const double* Un,

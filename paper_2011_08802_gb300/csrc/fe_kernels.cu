@@ -24,10 +24,12 @@ namespace pfm {
 namespace {
 
 // ---------------------------------------------------------------------------
-// Residual (and energy) of the elements; DET: atomic-free, the nodal results
-// go to the scratch W (node_gather adds them up) and each warp's energy to
-// W[9 ws + blk] (summed in a fixed order by k_sum_fixed).
-template <bool DET>
+// Residual (and energy) of the elements, the point physics in TC (FP64, or
+// double-float: pairs of FP32 numbers on the FP32 pipes, about 48 bits);
+// DET: atomic-free, the nodal results go to the scratch W (node_gather adds
+// them up) and each warp's energy to W[9 ws + blk] (summed in a fixed order
+// by k_sum_fixed).
+template <typename TC, bool DET>
 __global__ void __launch_bounds__(128) k_residual(Grid g, DevParams P, const double* __restrict__ U,
                                                   const double* __restrict__ Un,
                                                   const dmask_t* __restrict__ mask,
@@ -41,40 +43,41 @@ __global__ void __launch_bounds__(128) k_residual(Grid g, DevParams P, const dou
   const bool valid = e < g.ne();
   const int64_t nn = g.nn();
   const int64_t node = valid ? elem_node(g, e, l8) : 0;
-  const double ihx = 1.0 / g.hx, ihy = 1.0 / g.hy, ihz = 1.0 / g.hz;
-  double F[9], eh[NV], ge[3 * NV], ehn[NV];
-  gather_state<double>(U, nn, node, valid, l8, ihx, ihy, ihz, F, eh, ge);
+  const TC ihx = TC(1.0 / g.hx), ihy = TC(1.0 / g.hy), ihz = TC(1.0 / g.hz);
+  TC F[9], eh[NV], ge[3 * NV], ehn[NV];
+  gather_state<TC>(U, nn, node, valid, l8, ihx, ihy, ihz, F, eh, ge);
 #pragma unroll
-  for (int k = 0; k < NV; ++k) ehn[k] = q1_value(valid ? Un[(3 + k) * nn + node] : 0.0);
-  double Wd, gr[NZ];
-  qp_local<double, false>(P, F, eh, ehn, &Wd, gr, nullptr);
-  double gf[3 * NV];
-  double Wg = 0.0;
+  for (int k = 0; k < NV; ++k) ehn[k] = q1_value(valid ? TC(Un[(3 + k) * nn + node]) : TC(0.0));
+  TC Wd, gr[NZ];
+  qp_local<TC, false>(P, F, eh, ehn, &Wd, gr, nullptr);
+  TC gf[3 * NV];
+  TC Wg = TC(0.0);
 #pragma unroll
   for (int k = 0; k < NV; ++k)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      double s = 0.0;
+      TC s = TC(0.0);
 #pragma unroll
-      for (int l = 0; l < NV; ++l) s += P.G[k][l] * ge[3 * l + d];
+      for (int l = 0; l < NV; ++l) s += TC(P.G[k][l]) * ge[3 * l + d];
       gf[3 * k + d] = s;
-      Wg += 0.5 * ge[3 * k + d] * s;
+      Wg += TC(0.5) * ge[3 * k + d] * s;
     }
-  const double w = g.w();
+  const TC w = TC(g.w());
   const dmask_t dm = valid ? mask[node] : dmask_t(0);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    double r = q1_scatter_grad(w * gr[3 * i], w * gr[3 * i + 1], w * gr[3 * i + 2], l8, ihx, ihy, ihz);
-    scatter_row<DET>(R, W, ws, i, blk, lane, i * nn + node, r, valid && !((dm >> i) & 1));
+    TC r = q1_scatter_grad(w * gr[3 * i], w * gr[3 * i + 1], w * gr[3 * i + 2], l8, ihx, ihy, ihz);
+    scatter_row<DET>(R, W, ws, i, blk, lane, i * nn + node, double(r), valid && !((dm >> i) & 1));
   }
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    double r = q1_scatter(w * gr[9 + k], w * gf[3 * k], w * gf[3 * k + 1], w * gf[3 * k + 2], l8, ihx,
-                          ihy, ihz);
-    scatter_row<DET>(R, W, ws, 3 + k, blk, lane, (3 + k) * nn + node, r, valid && !((dm >> (3 + k)) & 1));
+    TC r = q1_scatter(w * gr[9 + k], w * gf[3 * k], w * gf[3 * k + 1], w * gf[3 * k + 2], l8, ihx,
+                      ihy, ihz);
+    scatter_row<DET>(R, W, ws, 3 + k, blk, lane, (3 + k) * nn + node, double(r),
+                     valid && !((dm >> (3 + k)) & 1));
   }
   if (energy) {
-    double en = warp_sum(valid ? w * (Wd + Wg) : 0.0);
+    double en = warp_sum(valid ? double(w * (Wd + Wg)) : 0.0);
     if constexpr (DET) {
       if (lane == 0) W[NF * ws + blk] = en;
     } else {
@@ -421,15 +424,21 @@ __global__ void k_identity_rows(int64_t nn, const dmask_t* __restrict__ mask, co
 int sm_count();
 
 void launch_residual(const Grid& g, const DevParams& P, const double* U, const double* Un,
-                     const dmask_t* mask, double* R, double* energy, cudaStream_t s, double* W) {
+                     const dmask_t* mask, double* R, double* energy, cudaStream_t s, double* W, bool df) {
   const int64_t threads = g.nblk() * 32;
   if (!W) {
-    k_residual<false><<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, mask, R, energy, nullptr, 0);
+    if (df)
+      k_residual<df64, false><<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, mask, R, energy, nullptr, 0);
+    else
+      k_residual<double, false><<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, mask, R, energy, nullptr, 0);
     count_launches(1);
     return;
   }
   const int64_t ws = g.nblk() * 32;
-  k_residual<true><<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, mask, R, energy, W, ws);
+  if (df)
+    k_residual<df64, true><<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, mask, R, energy, W, ws);
+  else
+    k_residual<double, true><<<grid_for(threads, 128), 128, 0, s>>>(g, P, U, Un, mask, R, energy, W, ws);
   k_node_gather<double, double, double><<<grid_for(g.nn(), 128), 128, 0, s>>>(g, W, ws, mask, nullptr, R);
   count_launches(2);
   if (energy) {

@@ -118,6 +118,7 @@ struct pfm_handle {
   int power_its = 30;
   bool outer_df = true;  // outer operator of the mixed solve in double-float arithmetic
   bool lin_df = false;   // FP64-class linearisation in double-float instead of FP64 arithmetic
+  bool res_df = false;   // residual point physics in double-float instead of FP64 arithmetic
   bool pre_h16 = false;  // FP32 preconditioner reads binary16 Hessian copies
   bool det = false;      // atomic-free element kernels (pfm_set_deterministic or opts.deterministic)
   unsigned* amax_dev = nullptr;  // one word for the store's max |entry|

@@ -42,6 +42,31 @@ __host__ __device__ inline int64_t hstore_offset(int64_t blk, int entry, int lan
 }
 constexpr int64_t HBLK = int64_t(NHP) * 32;  // entries per element block
 
+// Unsigned 32-bit division by a divisor fixed at launch, as a multiply-high
+// and a shift (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, the round-up variant): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(n, m) + n) >> l for every
+// n < 2^31 (the sum stays below 2^32).
+struct FastDiv {
+  uint32_t d = 1, m = 1, l = 0;
+  static FastDiv make(uint32_t d) {
+    FastDiv f;
+    f.d = d;
+    f.l = 0;
+    while ((uint64_t(1) << f.l) < d) ++f.l;
+    f.m = uint32_t(((uint64_t(1) << 32) * ((uint64_t(1) << f.l) - d)) / d + 1);
+    return f;
+  }
+  __host__ __device__ uint32_t div(uint32_t n) const {
+#ifdef __CUDA_ARCH__
+    const uint32_t t = __umulhi(n, m);
+#else
+    const uint32_t t = uint32_t((uint64_t(n) * m) >> 32);
+#endif
+    return (t + n) >> l;
+  }
+};
+
 // Per-node Dirichlet bit mask (bit f set = DOF f prescribed).
 using dmask_t = uint16_t;
 static_assert(NF <= 16, "one 16-bit Dirichlet mask per node");
@@ -82,6 +107,9 @@ void launch_japply(const Grid& g, const DevParams& P, const T* H, const dmask_t*
 void launch_japply_h16(const Grid& g, const DevParams& P, const __half* H, float inv_scale, const dmask_t* mask,
                        const float* v, float* y, cudaStream_t s, float* W = nullptr);
 float launch_store_to_half(const Grid& g, const float* H32, __half* H16, unsigned* scratch, cudaStream_t s);
+// Number of staged tangent applications whose bounded wait gave up since the
+// last call (they write NaN into y[0]); resets the count.
+int take_wait_timeouts();
 // element blocks [b0, b1) only, on at most `blocks` CTAs (slab pipeline)
 template <typename T>
 void launch_japply_range(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, const T* v, T* y,

@@ -551,6 +551,179 @@ __device__ __forceinline__ void japply_block_h16(const Grid& g, const JParams<fl
 
 
 // ---------------------------------------------------------------------------
+// Bulk copies from global to shared memory by the tensor memory accelerator
+// (cp.async.bulk, completion counted in bytes on an mbarrier), and bounded
+// waits on those barriers.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make barrier initialisations visible to the asynchronous (TMA) proxy
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// order this CTA's generic-proxy accesses of shared memory before later
+// asynchronous-proxy writes into it
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// L2 policy for data read once (the Hessian store): evicted first, so the
+// nodal vectors that every element reads stay resident
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// bytes (a multiple of 16) from global src to shared dst (both 16-byte
+// aligned); completion adds to the barrier's transaction count
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Warp-uniform bounded wait for the completion of the barrier phase with the
+// given parity: true once every lane has seen it, false after about
+// limit_ns nanoseconds (the decision is lane 0's clock, broadcast).
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, unsigned parity, uint64_t limit_ns) {
+  if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+  const uint64_t t0 = global_ns();
+  for (unsigned it = 1;; ++it) {
+    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+    if ((it & 63u) == 0u) {
+      const uint64_t dt = __shfl_sync(0xffffffffu, global_ns() - t0, 0);
+      if (dt > limit_ns) return false;
+    }
+  }
+}
+
+// Element constants of the staged tangent application. The Hessian part is
+// weighted through the input: the gathered vector is x' = wh x (wh = w for an
+// FP32 store, w / s for a binary16 copy holding s H), so sigma = H dz' is
+// already weighted, and the gradient-energy matrix carries w / wh.
+struct JStaged {
+  float Gs[NV][NV];  // (w / wh) G
+  float wh, ihx, ihy, ihz;
+  FastDiv dx, dy;    // element index -> (i, j, k): e = i + nx (j + ny k)
+};
+
+// First half of the staged body, in two steps so that a warp can issue the
+// loads of its next element block before the arithmetic of the current one:
+// staged_load finds this lane's element node and loads its Dirichlet mask
+// and the NF input values (no load depends on another); staged_shuffle then
+// forms dz' = wh (grad du, d eta_hat) and the gradients ge' of the
+// order-parameter increments at this lane's Gauss point.
+struct StagedLane {
+  int64_t node;
+  dmask_t dm;
+  bool valid;
+  float x[NF];
+};
+__device__ __forceinline__ void staged_load(const Grid& g, const JStaged& jp, const dmask_t* __restrict__ mask,
+                                            const float* __restrict__ v, int64_t blk, int lane, StagedLane& s) {
+  const int l8 = lane & 7;
+  const uint32_t e = uint32_t(blk) * 4u + uint32_t(lane >> 3);  // ne < 2^31 (checked by the launcher)
+  s.valid = e < uint32_t(g.ne());
+  s.node = 0;  // padding lanes read node 0 (in bounds) and use none of it
+  if (s.valid) {
+    const uint32_t r = jp.dx.div(e);
+    const uint32_t ei = e - r * uint32_t(g.nx);
+    const uint32_t ek = jp.dy.div(r);
+    const uint32_t ej = r - ek * uint32_t(g.ny);
+    s.node = int64_t(ei + (l8 & 1)) +
+             int64_t(g.nx + 1) * (int64_t(ej + ((l8 >> 1) & 1)) + int64_t(g.ny + 1) * int64_t(ek + (l8 >> 2)));
+  }
+  s.dm = mask[s.node];
+  const int64_t nn = g.nn();
+  const float* vp = v + s.node;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) s.x[f] = vp[f * nn];
+}
+__device__ __forceinline__ void staged_shuffle(const JStaged& jp, StagedLane& s, int lane, float dz[NZ],
+                                               float ge[3 * NV]) {
+  const int l8 = lane & 7;
+  if (!s.valid) s.dm = MASK_ALL;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float x = ((s.dm >> i) & 1) ? 0.f : jp.wh * s.x[i];
+    float val;
+    q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, val, dz[3 * i], dz[3 * i + 1], dz[3 * i + 2]);
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const float x = ((s.dm >> (3 + k)) & 1) ? 0.f : jp.wh * s.x[3 + k];
+    q1_gather(x, l8, jp.ihx, jp.ihy, jp.ihz, dz[9 + k], ge[3 * k], ge[3 * k + 1], ge[3 * k + 2]);
+  }
+}
+
+// Second half: sigma = H dz' from the element block's Hessians staged in
+// shared memory (lane-interleaved 16-byte vectors, the layout of the global
+// store), the gradient-energy term, and the scatter with atomics.
+template <typename S>
+__device__ __forceinline__ void staged_contract_scatter(const Grid& g, const JStaged& jp, const unsigned char* Hs,
+                                                        const StagedLane& s, float* __restrict__ y, int lane,
+                                                        const float dz[NZ],
+                                                        const float ge[3 * NV]) {
+  constexpr int V = 16 / sizeof(S);
+  using VT = typename Vec16<S>::type;
+  const int l8 = lane & 7;
+  const int64_t nn = g.nn();
+  float sg[NZ];
+#pragma unroll
+  for (int r = 0; r < NZ; ++r) sg[r] = 0.f;
+  const VT* Hv = reinterpret_cast<const VT*>(Hs) + lane;
+#pragma unroll
+  for (int j = 0; j < NHP / V; ++j) {
+    float hv[V];
+    Vec16<S>::unpack(Hv[j * 32], hv);
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      const int idx = j * V + t;
+      if (idx >= NH) continue;  // zero padding of the store
+      const int r = packed_row(idx);
+      const int c = r + (idx - packed_row_start(r));
+      sg[r] += hv[t] * dz[c];
+      if (c != r) sg[c] += hv[t] * dz[r];
+    }
+  }
+  float* yp = y + s.node;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float r = q1_scatter_grad(sg[3 * i], sg[3 * i + 1], sg[3 * i + 2], l8, jp.ihx, jp.ihy, jp.ihz);
+    if (s.valid && !((s.dm >> i) & 1)) atomicAdd(yp + i * nn, r);
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    float gf[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float a = 0.f;
+#pragma unroll
+      for (int l = 0; l < NV; ++l) a += jp.Gs[k][l] * ge[3 * l + d];
+      gf[d] = a;
+    }
+    const float r = q1_scatter(sg[9 + k], gf[0], gf[1], gf[2], l8, jp.ihx, jp.ihy, jp.ihz);
+    if (s.valid && !((s.dm >> (3 + k)) & 1)) atomicAdd(yp + (3 + k) * nn, r);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Double-float ("df") arithmetic: a value is an unevaluated sum hi + lo of two
 // FP32 numbers (Dekker 1971, "A floating-point technique for extending the
 // available precision"; Knuth's TwoSum). Only round-to-nearest FP32 adds,

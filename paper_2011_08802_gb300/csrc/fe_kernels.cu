@@ -16,6 +16,8 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <type_traits>
+#include <vector>
 
 #include "common.cuh"
 #include "fe_device.cuh"
@@ -219,6 +221,100 @@ __global__ void __launch_bounds__(256, PFM_JAPPLY_H16_MINB) k_japply_h16(Grid g,
   for (int64_t blk = wg; blk < nblk; blk += nw) japply_block_h16<DET>(g, jp, wh, H, mask, v, y, blk, lane, W, ws);
 #endif
 }
+
+// ---- BEGIN staged tangent application kernel
+// y += J v (FP32 arithmetic) with the Hessian store S (FP32, or the binary16
+// copy s H) staged in shared memory by bulk copies. Warp w of the grid takes
+// element blocks w, w + nw, w + 2 nw, ...; its lane 0 keeps D blocks in
+// flight, each a bulk copy of HBLK entries into one of the warp's D stages
+// with completion counted on that stage's mbarrier, and re-arms a stage as
+// soon as the warp has consumed it. The reads of the store are thus D - 1 to
+// D blocks ahead of the arithmetic whatever the warp's registers, and the
+// Dirichlet masks and input values of the next block are loaded while the
+// current one computes. A wait longer than
+// WAIT_LIMIT_NS gives up: the warp waits (with the same bound) for its other
+// copies, counts the event in g_wait_timeouts and writes NaN into y[0],
+// which the solver's finiteness checks report.
+__device__ int g_wait_timeouts = 0;
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
+
+// resident CTAs per SM that the shared memory of one shape allows, at most 16
+// warps per SM (the body needs about 128 registers): the register bound of
+// the launch
+template <typename S, int D, int WPC>
+constexpr int staged_minb() {
+  constexpr int per = WPC * D * int(HBLK * sizeof(S)) + 1024;
+  constexpr int n = (227 * 1024) / per;
+  constexpr int cap = 16 / WPC;
+  return n < 1 ? 1 : (n > cap ? cap : n);
+}
+
+template <typename S, int D, int WPC>
+__global__ void __launch_bounds__(32 * WPC, (staged_minb<S, D, WPC>())) k_japply_tma(
+    Grid g, JStaged jp, const S* __restrict__ H, const dmask_t* __restrict__ mask, const float* __restrict__ v,
+    float* __restrict__ y) {
+  constexpr unsigned STAGE = unsigned(HBLK * sizeof(S));
+  static_assert(STAGE % 16 == 0, "bulk copy size");
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bars[WPC * D];
+  const int lane = int(threadIdx.x & 31);
+  const int wid = int(threadIdx.x >> 5);
+  unsigned char* st = smem + size_t(wid) * D * STAGE;
+  uint64_t* fb = bars + wid * D;
+  const int64_t nblk = g.nblk();
+  const int64_t w0 = int64_t(blockIdx.x) * WPC + wid;
+  const int64_t nw = int64_t(gridDim.x) * WPC;
+  if (w0 >= nblk) return;  // the whole warp, before any barrier is in use
+  uint64_t pol = 0;
+  if (lane == 0) {
+#pragma unroll
+    for (int s = 0; s < D; ++s) mbar_init(fb + s, 1);
+    fence_mbar_init();
+    pol = l2_evict_first_policy();
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+      const int64_t b = w0 + s * nw;
+      if (b < nblk) {
+        mbar_arrive_expect_tx(fb + s, STAGE);
+        bulk_g2s(st + s * STAGE, H + b * HBLK, STAGE, fb + s, pol);
+      }
+    }
+  }
+  __syncwarp();
+  StagedLane nxt;
+  staged_load(g, jp, mask, v, w0, lane, nxt);
+  unsigned i = 0;
+  for (int64_t blk = w0; blk < nblk; blk += nw, ++i) {
+    const int s = int(i % D);
+    const unsigned par = (i / D) & 1u;
+    StagedLane sl = nxt;
+    // the next block's mask and input values load while this block computes
+    if (blk + nw < nblk) staged_load(g, jp, mask, v, blk + nw, lane, nxt);
+    float dz[NZ], ge[3 * NV];
+    staged_shuffle(jp, sl, lane, dz, ge);
+    if (!mbar_wait_warp(fb + s, par, WAIT_LIMIT_NS)) {
+      // outstanding copies: those of blocks i .. i + D - 1 of this warp
+      for (int t = 0; t < D; ++t)
+        if (blk + t * nw < nblk) mbar_wait_warp(fb + (i + t) % D, ((i + t) / D) & 1u, WAIT_LIMIT_NS);
+      if (lane == 0) {
+        atomicAdd(&g_wait_timeouts, 1);
+        y[0] = __int_as_float(0x7fc00000);
+      }
+      return;
+    }
+    staged_contract_scatter<S>(g, jp, st + s * STAGE, sl, y, lane, dz, ge);
+    __syncwarp();
+    if (lane == 0) {
+      const int64_t nb = blk + D * nw;
+      if (nb < nblk) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(fb + s, STAGE);
+        bulk_g2s(st + s * STAGE, H + nb * HBLK, STAGE, fb + s, pol);
+      }
+    }
+  }
+}
+// ---- END staged tangent application kernel
 
 // y += J v with v in FP32 (exact input), the tangent as Hhi + Hlo (two FP32
 // stores of the FP64 Hessians) and double-float arithmetic throughout; the
@@ -477,7 +573,16 @@ struct JShape {
   int threads = 256;
   int per_sm = 2;
   double ms = 0.0;  // timed milliseconds per application (0 = not timed)
+  int stages = 0;   // > 0: the staged kernel k_japply_tma with this many stages per warp
 };
+
+// Shapes of the staged kernel (stages per warp D, threads = 32 x warps per CTA).
+constexpr int STAGED_SHAPES[][2] = {{2, 128}, {3, 128}, {2, 64}, {2, 32}, {1, 128}};
+bool staged_shape_known(int stages, int threads) {
+  for (const auto& sh : STAGED_SHAPES)
+    if (sh[0] == stages && sh[1] == threads) return true;
+  return false;
+}
 
 std::mutex g_tune_mutex;
 std::map<std::pair<int, int>, JShape> g_tuned;
@@ -485,7 +590,9 @@ bool g_tune_file_read = false;
 
 // The cache file (PFM_AUTOTUNE_FILE) is a JSON array with one object per line:
 //   {"kernel": "k_japply", "precision": "f32", "size_class": 17, "threads": 256,
-//    "ctas_per_sm": 2, "ms_per_application": 1.2713}
+//    "ctas_per_sm": 2, "stages": 0, "ms_per_application": 1.2713}
+// (stages 0: the register-fed kernel; 2 or 3: the staged kernel with that
+// many shared-memory stages per warp)
 void tune_file_read() {
   if (g_tune_file_read) return;
   g_tune_file_read = true;
@@ -496,17 +603,19 @@ void tune_file_read() {
   char line[512];
   while (std::fgets(line, sizeof(line), f)) {
     char prec[8] = {0};
-    int cl, th, ps;
+    int cl, th, ps, stg;
     double ms = 0.0;
     if (std::sscanf(line,
                     " {\"kernel\": \"k_japply\", \"precision\": \"%3[f0-9]\", \"size_class\": %d, \"threads\": %d, "
-                    "\"ctas_per_sm\": %d, \"ms_per_application\": %lf",
-                    prec, &cl, &th, &ps, &ms) == 5) {
+                    "\"ctas_per_sm\": %d, \"stages\": %d, \"ms_per_application\": %lf",
+                    prec, &cl, &th, &ps, &stg, &ms) == 6) {
       const int pr = std::strcmp(prec, "f32") == 0   ? 0
                      : std::strcmp(prec, "f64") == 0 ? 1
                      : std::strcmp(prec, "f16") == 0 ? 2
                                                      : -1;
-      if (pr >= 0 && (th == 128 || th == 256) && ps >= 1 && ps <= 16) g_tuned[{pr, cl}] = JShape{th, ps, ms};
+      const bool classic = stg == 0 && (th == 128 || th == 256);
+      const bool staged = pr != 1 && staged_shape_known(stg, th);
+      if (pr >= 0 && (classic || staged) && ps >= 1 && ps <= 16) g_tuned[{pr, cl}] = JShape{th, ps, ms, stg};
     }
   }
   std::fclose(f);
@@ -523,9 +632,9 @@ void tune_file_write() {
   for (const auto& kv : g_tuned) {
     std::fprintf(f,
                  " {\"kernel\": \"k_japply\", \"precision\": \"%s\", \"size_class\": %d, \"threads\": %d, "
-                 "\"ctas_per_sm\": %d, \"ms_per_application\": %.6f}%s\n",
+                 "\"ctas_per_sm\": %d, \"stages\": %d, \"ms_per_application\": %.6f}%s\n",
                  kv.first.first == 0 ? "f32" : (kv.first.first == 1 ? "f64" : "f16"), kv.first.second,
-                 kv.second.threads, kv.second.per_sm,
+                 kv.second.threads, kv.second.per_sm, kv.second.stages,
                  kv.second.ms, ++i < g_tuned.size() ? "," : "");
   }
   std::fprintf(f, "]\n");
@@ -540,6 +649,68 @@ int sm_count() {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
   return sms;
+}
+
+// ---- staged tangent application (k_japply_tma) ----
+JStaged make_jstaged(const Grid& g, const DevParams& P, double wh) {
+  JStaged j;
+  const double w = g.w();
+  for (int k = 0; k < NV; ++k)
+    for (int l = 0; l < NV; ++l) j.Gs[k][l] = float(w / wh * P.G[k][l]);
+  j.wh = float(wh);
+  j.ihx = float(1.0 / g.hx);
+  j.ihy = float(1.0 / g.hy);
+  j.ihz = float(1.0 / g.hz);
+  j.dx = FastDiv::make(uint32_t(g.nx));
+  j.dy = FastDiv::make(uint32_t(g.ny));
+  return j;
+}
+
+// the staged kernel indexes elements in 32 bits
+bool staged_fits(const Grid& g) { return g.ne() < (int64_t(1) << 31) - 4; }
+
+template <typename S, int D, int WPC>
+int staged_prepare() {  // dynamic shared memory attribute; resident CTAs per SM
+  constexpr int smem = WPC * D * int(HBLK * sizeof(S));
+  static int occ = -1;
+  if (occ < 0) {
+    occ = 0;
+    if (cudaFuncSetAttribute(k_japply_tma<S, D, WPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+        cudaSuccess)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_japply_tma<S, D, WPC>, 32 * WPC, smem);
+    cudaGetLastError();  // a refused shape is simply not offered
+  }
+  return occ;
+}
+
+template <typename S, int D, int WPC>
+void staged_launch_t(const Grid& g, const JStaged& jp, const S* H, const dmask_t* mask, const float* v, float* y,
+                     int per_sm, cudaStream_t s) {
+  constexpr int smem = WPC * D * int(HBLK * sizeof(S));
+  const int64_t need = (g.nblk() + WPC - 1) / WPC;
+  const int64_t full = int64_t(sm_count()) * per_sm;
+  k_japply_tma<S, D, WPC><<<unsigned(need < full ? need : full), 32 * WPC, smem, s>>>(g, jp, H, mask, v, y);
+}
+
+template <typename S>
+int staged_occupancy(int stages, int threads) {
+  if (stages == 2 && threads == 128) return staged_prepare<S, 2, 4>();
+  if (stages == 3 && threads == 128) return staged_prepare<S, 3, 4>();
+  if (stages == 2 && threads == 64) return staged_prepare<S, 2, 2>();
+  if (stages == 2 && threads == 32) return staged_prepare<S, 2, 1>();
+  if (stages == 1 && threads == 128) return staged_prepare<S, 1, 4>();
+  return 0;
+}
+
+template <typename S>
+void staged_launch(const Grid& g, const JStaged& jp, const S* H, const dmask_t* mask, const float* v, float* y,
+                   const JShape& js, cudaStream_t s) {
+  staged_occupancy<S>(js.stages, js.threads);
+  if (js.stages == 2 && js.threads == 128) staged_launch_t<S, 2, 4>(g, jp, H, mask, v, y, js.per_sm, s);
+  else if (js.stages == 3 && js.threads == 128) staged_launch_t<S, 3, 4>(g, jp, H, mask, v, y, js.per_sm, s);
+  else if (js.stages == 2 && js.threads == 64) staged_launch_t<S, 2, 2>(g, jp, H, mask, v, y, js.per_sm, s);
+  else if (js.stages == 2 && js.threads == 32) staged_launch_t<S, 2, 1>(g, jp, H, mask, v, y, js.per_sm, s);
+  else staged_launch_t<S, 1, 4>(g, jp, H, mask, v, y, js.per_sm, s);
 }
 
 // element kernel of the tangent application for a store of type S (wh: weight
@@ -568,18 +739,29 @@ inline const void* japply_elem_fn(const __half*) { return reinterpret_cast<const
 // One tangent application with launch shape js; with a scratch W (9 * 32 *
 // nblk entries) atomic-free: element pass into W, then the node pass writes
 // every entry of y (no initialisation needed).
+// The staged kernel (js.stages > 0) serves the atomic form of FP32 arithmetic
+// only; the atomic-free form and FP64 use the register-fed kernel (with the
+// default shape when the tuned one is staged).
 template <typename T, typename S = T>
 void japply_launch_shape(const Grid& g, const JParams<T>& jp, float wh, const S* H, const dmask_t* mask, const T* v,
-                         T* y, const JShape& js, cudaStream_t s, T* W = nullptr) {
+                         T* y, const JShape& js, cudaStream_t s, T* W = nullptr, const JStaged* jst = nullptr) {
   const int64_t nn = g.nn();
   if (!W) {
     k_japply_init<T><<<grid_for(NF * nn, 256) < 4096 ? grid_for(NF * nn, 256) : 4096, 256, 0, s>>>(nn, mask, v, y);
     count_launches(1);
   }
-  const int64_t need = (g.nblk() * 32 + js.threads - 1) / js.threads;
-  const int64_t full = int64_t(sm_count()) * js.per_sm;
+  if constexpr (std::is_same<T, float>::value) {
+    if (js.stages > 0 && !W && jst) {
+      staged_launch<S>(g, *jst, H, mask, v, y, js, s);
+      count_launches(1);
+      return;
+    }
+  }
+  const JShape cs = js.stages > 0 ? JShape{} : js;
+  const int64_t need = (g.nblk() * 32 + cs.threads - 1) / cs.threads;
+  const int64_t full = int64_t(sm_count()) * cs.per_sm;
   const unsigned blocks = unsigned(need < full ? need : full);
-  japply_elem(g, jp, wh, H, mask, v, y, W, blocks, js.threads, s);
+  japply_elem(g, jp, wh, H, mask, v, y, W, blocks, cs.threads, s);
   count_launches(1);
   if (W) {
     k_node_gather<T, T, T><<<grid_for(nn, 128), 128, 0, s>>>(g, W, g.nblk() * 32, mask, v, y);
@@ -589,7 +771,7 @@ void japply_launch_shape(const Grid& g, const JParams<T>& jp, float wh, const S*
 
 template <typename T, typename S = T>
 JShape japply_tune(const Grid& g, const JParams<T>& jp, float wh, const S* H, const dmask_t* mask, const T* v, T* y,
-                   cudaStream_t s) {
+                   cudaStream_t s, const JStaged* jst = nullptr) {
   const int pr = sizeof(S) == 2 ? 2 : (sizeof(T) == 4 ? 0 : 1);
   int cl = 0;
   for (int64_t b = g.nblk(); b > 1; b >>= 1) ++cl;
@@ -605,29 +787,37 @@ JShape japply_tune(const Grid& g, const JParams<T>& jp, float wh, const S* H, co
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   float best_ms = 1e30f;
+  std::vector<JShape> cand;
   for (int threads : {256, 128}) {
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, japply_elem_fn(H), threads, 0);
-    for (int ps = 1; ps <= occ; ++ps) {
-      JShape js{threads, ps};
-      japply_launch_shape<T, S>(g, jp, wh, H, mask, v, y, js, s);  // warm
-      // best of three timings of three applications each (the shapes differ
-      // by a few per cent, about the run-to-run spread of one timing)
-      float ms = 1e30f;
-      for (int t = 0; t < 3; ++t) {
-        cudaEventRecord(a, s);
-        for (int r = 0; r < 3; ++r) japply_launch_shape<T, S>(g, jp, wh, H, mask, v, y, js, s);
-        cudaEventRecord(b, s);
-        cudaEventSynchronize(b);
-        float m = 0.f;
-        cudaEventElapsedTime(&m, a, b);
-        if (m < ms) ms = m;
+    for (int ps = 1; ps <= occ; ++ps) cand.push_back(JShape{threads, ps, 0.0, 0});
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    if (jst && staged_fits(g))
+      for (const auto& sh : STAGED_SHAPES) {
+        const int occ = staged_occupancy<S>(sh[0], sh[1]);
+        for (int ps = 1; ps <= occ; ++ps) cand.push_back(JShape{sh[1], ps, 0.0, sh[0]});
       }
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = js;
-        best.ms = ms / 3.0;
-      }
+  }
+  for (const JShape& js : cand) {
+    japply_launch_shape<T, S>(g, jp, wh, H, mask, v, y, js, s, nullptr, jst);  // warm
+    // best of three timings of three applications each (the shapes differ
+    // by a few per cent, about the run-to-run spread of one timing)
+    float ms = 1e30f;
+    for (int t = 0; t < 3; ++t) {
+      cudaEventRecord(a, s);
+      for (int r = 0; r < 3; ++r) japply_launch_shape<T, S>(g, jp, wh, H, mask, v, y, js, s, nullptr, jst);
+      cudaEventRecord(b, s);
+      cudaEventSynchronize(b);
+      float m = 0.f;
+      cudaEventElapsedTime(&m, a, b);
+      if (m < ms) ms = m;
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = js;
+      best.ms = ms / 3.0;
     }
   }
   cudaEventDestroy(a);
@@ -641,16 +831,33 @@ template <typename T>
 void launch_japply(const Grid& g, const DevParams& P, const T* H, const dmask_t* mask, const T* v,
                    T* y, cudaStream_t s, T* W) {
   const JParams<T> jp = make_jparams<T>(g, P);
-  const JShape js = japply_tune<T>(g, jp, 0.f, H, mask, v, y, s);
-  japply_launch_shape<T>(g, jp, 0.f, H, mask, v, y, js, s, W);
+  if constexpr (std::is_same<T, float>::value) {
+    const JStaged jst = make_jstaged(g, P, g.w());
+    const JShape js = japply_tune<T>(g, jp, 0.f, H, mask, v, y, s, &jst);
+    japply_launch_shape<T>(g, jp, 0.f, H, mask, v, y, js, s, W, &jst);
+  } else {
+    const JShape js = japply_tune<T>(g, jp, 0.f, H, mask, v, y, s);
+    japply_launch_shape<T>(g, jp, 0.f, H, mask, v, y, js, s, W);
+  }
 }
 
 void launch_japply_h16(const Grid& g, const DevParams& P, const __half* H, float inv_scale, const dmask_t* mask,
                       const float* v, float* y, cudaStream_t s, float* W) {
   const JParams<float> jp = make_jparams<float>(g, P);
   const float wh = jp.w * inv_scale;
-  const JShape js = japply_tune<float, __half>(g, jp, wh, H, mask, v, y, s);
-  japply_launch_shape<float, __half>(g, jp, wh, H, mask, v, y, js, s, W);
+  const JStaged jst = make_jstaged(g, P, g.w() * double(inv_scale));
+  const JShape js = japply_tune<float, __half>(g, jp, wh, H, mask, v, y, s, &jst);
+  japply_launch_shape<float, __half>(g, jp, wh, H, mask, v, y, js, s, W, &jst);
+}
+
+int take_wait_timeouts() {
+  int n = 0;
+  if (cudaMemcpyFromSymbol(&n, g_wait_timeouts, sizeof(int)) != cudaSuccess) return 0;
+  if (n != 0) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof(int));
+  }
+  return n;
 }
 
 float launch_store_to_half(const Grid& g, const float* H32, __half* H16, unsigned* scratch, cudaStream_t s) {

@@ -135,7 +135,17 @@ struct pfm_handle {
   int64_t prof_n[PFM_PROF_COUNT] = {0};
   double prof_ms[PFM_PROF_COUNT] = {0};
 
+  // A non-finite result may come from a staged tangent application whose
+  // bounded wait for its copies gave up (it writes NaN into its output); such
+  // events are reported as PFM_ERR_TIMEOUT.
   pfm_status fail(pfm_status s, const std::string& m) {
+    if (s == PFM_ERR_NONFINITE) {
+      const int n = pfm::take_wait_timeouts();
+      if (n > 0) {
+        err = m + " (" + std::to_string(n) + " bounded waits of the staged tangent application gave up)";
+        return PFM_ERR_TIMEOUT;
+      }
+    }
     err = m;
     return s;
   }

@@ -397,8 +397,10 @@ def reduce_over_ranks(ms_step, ms32, n32, ndofs, dist, device):
 
 
 def japply_only(args):
-    """K FP32 tangent applications on the benchmark state (profiler driver);
-    prints the mean device time per application (CUDA events)."""
+    """K tangent applications on the benchmark state (profiler driver): FP32,
+    FP64, the double-float outer operator and FP32 arithmetic from the
+    binary16 store; prints the mean device time per application (CUDA
+    events)."""
     import numpy as np
     import torch
 
@@ -440,6 +442,23 @@ def japply_only(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     out["df"] = {"ms": ms, "GDOF/s": 9 * P.n_nodes / ms / 1e6}
+    # FP32 arithmetic from the binary16 copies of the preconditioner's store
+    P.set_preconditioner_store(True)
+    P.linearize(abi.PFM_F32)
+    v = torch.from_numpy(np.random.default_rng(1).standard_normal(P.shape).astype(np.float32)).cuda()
+    y = torch.empty_like(v)
+    for _ in range(args.warmup):
+        P.jacobian_apply(v, y)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        P.jacobian_apply(v, y)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    nblk = (P.n_elems + 3) // 4
+    gb = (nblk * 4 * 8 * 120 * 2 + 2 * 9 * P.n_nodes * 4 + 2 * P.n_nodes) / 1e9
+    out["f16"] = {"ms": ms, "GDOF/s": 9 * P.n_nodes / ms / 1e6, "GB/s": gb / ms * 1e3}
     print(json.dumps(out), flush=True)
     P.close()
 
@@ -451,7 +470,7 @@ def batch_measure(args, dev):
     pfm_batch_newton_solve with the batched engine (one launch per phase over
     all problems, graph-replayed FGMRES iterations) and with the per-problem
     lockstep driver, against the same problems solved one after another with
-    pfm_newton_solve."""
+    pfm_newton_solve; and the engine with the binary16 preconditioner store."""
     import torch
 
     from paper_2011_08802_gb300 import abi, binding, inputs
@@ -512,11 +531,22 @@ def batch_measure(args, dev):
         P.linearize(abi.PFM_F32)
         y = P.jacobian_apply(u1 - u0)
         true_res.append(float(torch.linalg.norm(y + R) / torch.linalg.norm(R)))
+    # the engine with every preconditioner level reading binary16 copies
+    for P in probs:
+        P.set_preconditioner_store(True)
+    batched(0)
+    t0 = time.perf_counter()
+    reps16 = batched(0)
+    t_b16 = time.perf_counter() - t0
+    for P in probs:
+        P.set_preconditioner_store(False)
     B.close()
     for P in probs:
         P.close()
     r0 = reps[0]
     return {"problems": len(probs), "n_range": [min(ns), max(ns)], "total_dofs": dofs,
+            "batch_f16_store_s": t_b16, "batch_f16_store_fgmres_its_max": max(r.lin_its_last for r in reps16),
+            "batch_f16_store_ok": all(r.status == 0 for r in reps16),
             "batch_s": t_bat, "sequential_s": t_seq, "speedup": t_seq / t_bat,
             "lockstep_s": t_ls, "engine_launches": l_bat, "lockstep_launches": l_ls,
             "engine_phase_ms": {"residual": r0.ms_residual, "linearize": r0.ms_linearize, "solve": r0.ms_solve},

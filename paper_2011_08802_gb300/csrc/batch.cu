@@ -11,8 +11,10 @@
 // a CUDA graph and replayed; the host reads one flag word per iteration.
 //
 // Supported: the mixed-precision solve (FP32 V-cycle with Chebyshev
-// smoothing inside FP64 FGMRES, double-float outer operator). Other options
-// use the per-problem lockstep driver of api.cu.
+// smoothing inside FP64 FGMRES, double-float outer operator), with the FP32
+// stores or, when every problem has the binary16 option on, their binary16
+// copies in the V-cycle. Other options use the per-problem lockstep driver
+// of api.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -40,7 +42,10 @@ struct BLev {
   int64_t blk0;    // first element block of this level in the set's numbering
   float inv_theta, inv_delta;  // Chebyshev coefficients 1/theta, 1/delta
   int problem;     // index of the problem in the batch (gate lookup)
-  int pad;
+  int level;       // level of the problem
+  __half* H16;     // binary16 copy s H of the store (engines with the binary16 option)
+  float h16s;      // its power-of-two scale s
+  float wh;        // weight w / s of its Hessian part
 };
 
 // Per-problem on/off gate of a launch: on[problem * stride] != 0. The V-cycle
@@ -170,8 +175,10 @@ __device__ __forceinline__ int find_entry(const S* __restrict__ set, int ns, int
 // ---------------------------------------------------------------------------
 // FP32 V-cycle kernels
 
-// y += J v over all element blocks of the set; v = vec[vsel], y = vec[ysel].
+// y += J v over all element blocks of the set; v = vec[vsel], y = vec[ysel],
+// from the FP32 stores or (H16) from their binary16 copies.
 // Each warp caches the descriptor of its current problem in shared memory.
+template <bool H16>
 __global__ void __launch_bounds__(256) k_b_japply(const BLev* __restrict__ S, int ns, int64_t nblk, int vsel,
                                                   int ysel, Gate on) {
   __shared__ BLev cache[8];
@@ -190,9 +197,38 @@ __global__ void __launch_bounds__(256) k_b_japply(const BLev* __restrict__ S, in
       cur = p;
     }
     const BLev& L = cache[wid];
-    if (on(L.problem) && blk - L.blk0 < L.g.nblk())
-      japply_block<float>(L.g, L.jp, L.H, L.mask, L.vec[vsel], L.vec[ysel], blk - L.blk0, lane);
+    if (on(L.problem) && blk - L.blk0 < L.g.nblk()) {
+      if constexpr (H16)
+        japply_block_h16<false>(L.g, L.jp, L.wh, L.H16, L.mask, L.vec[vsel], L.vec[ysel], blk - L.blk0, lane);
+      else
+        japply_block<float>(L.g, L.jp, L.H, L.mask, L.vec[vsel], L.vec[ysel], blk - L.blk0, lane);
+    }
   }
+}
+
+// max |H| of every level's FP32 store, as float bits in amax[entry]
+// (non-negative floats order as their bit patterns; NaN counts as +infinity)
+__global__ void k_b_absmax(const BLev* __restrict__ S, unsigned* __restrict__ amax, Gate on) {
+  const BLev& L = S[blockIdx.y];
+  if (!on(L.problem)) return;
+  const int64_t n = L.g.nblk() * HBLK;
+  float m = 0.f;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    m = absmax_step(m, L.H[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(amax + blockIdx.y, __float_as_uint(m));
+}
+
+// binary16 copy h16s H of every level's FP32 store
+__global__ void k_b_to_half(const BLev* __restrict__ S, Gate on) {
+  const BLev& L = S[blockIdx.y];
+  if (!on(L.problem)) return;
+  const int64_t nvec = L.g.nblk() * HBLK / 8;
+  uint4* out = reinterpret_cast<uint4*>(L.H16);
+  const float4* in = reinterpret_cast<const float4*>(L.H);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nvec; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = half_vector(in, L.h16s, i);
 }
 
 // y = v at Dirichlet DOFs, 0 elsewhere (identity rows of J).
@@ -830,6 +866,9 @@ struct BatchEngine {
   double* hres = nullptr;  // pinned: per-problem norms / lambda estimates
   int* hact = nullptr;     // pinned: Newton activity
   int grid_japply = 0, grid_df = 0, grid_j64 = 0;
+  bool h16 = false;             // the V-cycle applies the binary16 copies of the stores
+  unsigned* amax = nullptr;     // per A-set level: max |H| bits
+  unsigned* hamax = nullptr;    // pinned copy
   cudaGraphExec_t vgraph = nullptr;
   std::vector<cudaGraphExec_t> itg;
   std::vector<int64_t> itg_launches;  // kernels in each iteration graph
@@ -861,6 +900,7 @@ struct BatchEngine {
     if (hflags) cudaFreeHost(hflags);
     if (hres) cudaFreeHost(hres);
     if (hact) cudaFreeHost(hact);
+    if (hamax) cudaFreeHost(hamax);
   }
   Gate gate_fgm() const { return Gate{&dF[0].active, int(sizeof(BFgm) / sizeof(int))}; }
   Gate gate_act() const { return Gate{dact, 1}; }
@@ -909,6 +949,7 @@ pfm_status engine_buffers(pfm_handle* h, int m) {
     if (fine || coarsest) TRY(dalloc(h, &lv.H64, hsz));
     if (fine || !coarsest) TRY(dalloc(h, &lv.H32, hsz));
     if (fine) TRY(dalloc(h, &lv.H32lo, hsz));
+    if (h->pre_h16 && !coarsest) TRY(dalloc(h, &lv.H16, hsz));
     if (!coarsest) TRY(dalloc(h, &lv.D32, size_t(NF2) * lv.nn));
     TRY(dalloc(h, &lv.x32, ndof(lv)));
     TRY(dalloc(h, &lv.b32, ndof(lv)));
@@ -1015,6 +1056,8 @@ pfm_status engine_build(pfm_batch* b, const pfm_solve_opts& o, BatchEngine** out
       L.vec[VR] = lv.r32;
       L.vec[VD] = lv.d32;
       L.problem = p;
+      L.level = l;
+      L.H16 = h->pre_h16 ? lv.H16 : nullptr;
       auto& Ds = E->D[l];
       L.blk0 = Ds.nblk;
       Ds.nblk += lv.nblk;
@@ -1102,13 +1145,18 @@ pfm_status engine_build(pfm_batch* b, const pfm_solve_opts& o, BatchEngine** out
   up(E->alloc(&E->flags, 2));
   up(E->alloc(&E->dact, np));
   up(E->alloc(&E->singular, 1));
+  up(E->alloc(&E->amax, std::max<size_t>(E->A.size(), 1)));
   if (e == cudaSuccess) e = cudaMemset(E->dF, 0, sizeof(BFgm) * np);
+  if (e == cudaSuccess)
+    e = cudaMallocHost(reinterpret_cast<void**>(&E->hamax), sizeof(unsigned) * std::max<size_t>(E->A.size(), 1));
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&E->hflags), sizeof(int) * 2);
   if (e == cudaSuccess)
     e = cudaMallocHost(reinterpret_cast<void**>(&E->hres), sizeof(double) * std::max<size_t>(np, E->A.size()));
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&E->hact), sizeof(int) * np);
   if (e != cudaSuccess) return fail(b->fail(PFM_ERR_OOM, std::string("engine tables: ") + cudaGetErrorString(e)));
-  E->grid_japply = persistent_blocks(k_b_japply, 256, std::max<int64_t>(E->nblkA, 1) * 32);
+  E->h16 = b->hs[0]->pre_h16;  // the same for every problem (batch_engine_supports)
+  E->grid_japply = E->h16 ? persistent_blocks(k_b_japply<true>, 256, std::max<int64_t>(E->nblkA, 1) * 32)
+                          : persistent_blocks(k_b_japply<false>, 256, std::max<int64_t>(E->nblkA, 1) * 32);
   E->grid_df = persistent_blocks(k_b_japply_df, 256, E->nblkO * 32);
   E->grid_j64 = persistent_blocks(k_b_japply64, 256, E->nblkO * 32);
   *out = E;
@@ -1119,7 +1167,10 @@ pfm_status engine_build(pfm_batch* b, const pfm_solve_opts& o, BatchEngine** out
 void eng_japply(BatchEngine* E, const BLev* dS, int ns, int64_t nblk, int64_t maxnn, int v, int y, Gate g) {
   k_b_init<<<grid2(NF * maxnn, ns), BT, 0, E->s>>>(dS, v, y, g);
   const int blocks = std::max(1, std::min<int>(E->grid_japply, int(gdiv(nblk * 32, 256))));
-  k_b_japply<<<blocks, 256, 0, E->s>>>(dS, ns, nblk, v, y, g);
+  if (E->h16)
+    k_b_japply<true><<<blocks, 256, 0, E->s>>>(dS, ns, nblk, v, y, g);
+  else
+    k_b_japply<false><<<blocks, 256, 0, E->s>>>(dS, ns, nblk, v, y, g);
   count_launches(2);
 }
 
@@ -1194,6 +1245,40 @@ pfm_status eng_linearize(pfm_batch* b, BatchEngine* E, int power_its) {
     count_launches(1);
   }
   const int nA = int(E->A.size());
+  if (E->h16 && nA > 0) {
+    // binary16 copies of every preconditioner level's store: max |H| of all
+    // levels in one launch, the power-of-two scales on the host (as for a
+    // single problem), the copies in one launch
+    BCK(cudaMemsetAsync(E->amax, 0, sizeof(unsigned) * nA, s));
+    const dim3 ga(unsigned(sm_count_b()) * 2, unsigned(nA));
+    k_b_absmax<<<ga, BT, 0, s>>>(E->dA, E->amax, g);
+    count_launches(1);
+    BCK(cudaMemcpyAsync(E->hamax, E->amax, sizeof(unsigned) * nA, cudaMemcpyDeviceToHost, s));
+    BCK(cudaStreamSynchronize(s));
+    for (int i = 0; i < nA; ++i) {
+      BLev& L = E->A[i];
+      if (!E->hact[L.problem]) continue;
+      float amax = 0.f;
+      std::memcpy(&amax, &E->hamax[i], sizeof(float));
+      if (!std::isfinite(amax))
+        return b->fail(PFM_ERR_NONFINITE, "binary16 store: non-finite Hessian entries in problem " +
+                                              std::to_string(L.problem));
+      L.h16s = half_store_scale(amax);
+      L.wh = float(L.g.w() / double(L.h16s));
+      b->hs[L.problem]->L[L.level].h16_scale = L.h16s;
+      for (auto& Ls : E->D[L.level].S)
+        if (Ls.problem == L.problem) {
+          Ls.h16s = L.h16s;
+          Ls.wh = L.wh;
+        }
+    }
+    BCK(cudaMemcpyAsync(E->dA, E->A.data(), sizeof(BLev) * nA, cudaMemcpyHostToDevice, s));
+    for (auto& Ds : E->D)
+      if (!Ds.S.empty())
+        BCK(cudaMemcpyAsync(Ds.dS, Ds.S.data(), sizeof(BLev) * Ds.S.size(), cudaMemcpyHostToDevice, s));
+    k_b_to_half<<<ga, BT, 0, s>>>(E->dA, g);
+    count_launches(1);
+  }
   if (nA > 0) {
     k_b_zero_D<<<grid2(NF2 * E->maxnnBd, nA), BT, 0, s>>>(E->dBd, g);
     k_b_blockdiag<<<gdiv(E->neBd * 8, 128), 128, 0, s>>>(E->dBd, nA, E->neBd, g);
@@ -1413,6 +1498,7 @@ std::vector<uint64_t> engine_signature(const pfm_batch* b) {
   for (const pfm_handle* h : b->hs) {
     for (const Level& lv : h->L) {
       add(lv.U); add(lv.Un); add(lv.mask); add(lv.H64); add(lv.H32); add(lv.H32lo); add(lv.D32);
+      add(h->pre_h16 ? lv.H16 : nullptr);
       add(lv.x32); add(lv.b32); add(lv.y32); add(lv.r32); add(lv.d32);
     }
     add(h->V); add(h->Z); add(h->wv); add(h->dU); add(h->R); add(h->rv); add(h->Kaug); add(h->Kinv);
@@ -1438,7 +1524,7 @@ bool batch_engine_supports(const pfm_solve_opts& o, const pfm_batch* b) {
       o.krylov != 0)
     return false;
   for (const pfm_handle* h : b->hs)
-    if (!h->outer_df || h->contact_on || h->pre_h16 || h->det) return false;
+    if (!h->outer_df || h->contact_on || h->det || h->pre_h16 != b->hs[0]->pre_h16) return false;
   return true;
 }
 

@@ -107,6 +107,9 @@ void launch_japply(const Grid& g, const DevParams& P, const T* H, const dmask_t*
 void launch_japply_h16(const Grid& g, const DevParams& P, const __half* H, float inv_scale, const dmask_t* mask,
                        const float* v, float* y, cudaStream_t s, float* W = nullptr);
 float launch_store_to_half(const Grid& g, const float* H32, __half* H16, unsigned* scratch, cudaStream_t s);
+// power-of-two scale s of the binary16 copy for a store whose largest entry
+// has magnitude amax (finite)
+float half_store_scale(float amax);
 // Number of staged tangent applications whose bounded wait gave up since the
 // last call (they write NaN into y[0]); resets the count.
 int take_wait_timeouts();

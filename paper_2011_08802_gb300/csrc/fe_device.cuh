@@ -550,6 +550,31 @@ __device__ __forceinline__ void japply_block_h16(const Grid& g, const JParams<fl
 }
 
 
+// Output vector i of the binary16 copy s H of an FP32 store: vector i =
+// (blk*(NHP/8) + j)*32 + lane holds entries 8j..8j+7 of that lane, which the
+// FP32 store keeps in its vectors (blk*(NHP/4) + 2j)*32 + lane and the one 32
+// vectors later.
+__device__ __forceinline__ uint4 half_vector(const float4* __restrict__ H32, float s, int64_t i) {
+  const int64_t lane = i & 31, bj = i >> 5;
+  const int64_t blk = bj / (NHP / 8), j = bj % (NHP / 8);
+  const int64_t src = (blk * (NHP / 4) + 2 * j) * 32 + lane;
+  const float4 a = H32[src], b = H32[src + 32];
+  uint4 o;
+  __half2* h = reinterpret_cast<__half2*>(&o);
+  h[0] = __floats2half2_rn(a.x * s, a.y * s);
+  h[1] = __floats2half2_rn(a.z * s, a.w * s);
+  h[2] = __floats2half2_rn(b.x * s, b.y * s);
+  h[3] = __floats2half2_rn(b.z * s, b.w * s);
+  return o;
+}
+
+// running max of |x| in which a NaN counts as +infinity (so that a
+// non-finite store is always detected)
+__device__ __forceinline__ float absmax_step(float m, float x) {
+  const float a = fabsf(x);
+  return a == a ? fmaxf(m, a) : __int_as_float(0x7f800000);
+}
+
 // ---------------------------------------------------------------------------
 // Bulk copies from global to shared memory by the tensor memory accelerator
 // (cp.async.bulk, completion counted in bytes on an mbarrier), and bounded

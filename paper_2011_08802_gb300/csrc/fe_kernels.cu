@@ -238,14 +238,15 @@ __global__ void __launch_bounds__(256, PFM_JAPPLY_H16_MINB) k_japply_h16(Grid g,
 __device__ int g_wait_timeouts = 0;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 
-// resident CTAs per SM that the shared memory of one shape allows, at most 16
-// warps per SM (the body needs about 128 registers): the register bound of
-// the launch
+// resident CTAs per SM that the shared memory of one shape allows, at most 20
+// warps per SM (the binary16 body fits in 96 registers without spills, the
+// FP32 body needs about 125 and is limited by shared memory first): the
+// register bound of the launch
 template <typename S, int D, int WPC>
 constexpr int staged_minb() {
   constexpr int per = WPC * D * int(HBLK * sizeof(S)) + 1024;
   constexpr int n = (227 * 1024) / per;
-  constexpr int cap = 16 / WPC;
+  constexpr int cap = 20 / WPC;
   return n < 1 ? 1 : (n > cap ? cap : n);
 }
 
@@ -454,11 +455,12 @@ __global__ void k_qp_eval(DevParams P, int64_t n, const double* __restrict__ F,
 }
 
 // max |H| over an FP32 store (non-negative floats order as their bit
-// patterns, so an integer atomicMax on the bits is a float max).
+// patterns, so an integer atomicMax on the bits is a float max; a NaN entry
+// gives +infinity).
 __global__ void k_absmax(int64_t n, const float* __restrict__ H, unsigned* __restrict__ out) {
   float m = 0.f;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    m = fmaxf(m, fabsf(H[i]));
+    m = absmax_step(m, H[i]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
@@ -468,22 +470,8 @@ __global__ void k_absmax(int64_t n, const float* __restrict__ H, unsigned* __res
 // per 16-byte output vector (8 entries of one lane), read as two FP32 vectors
 // of the same lane.
 __global__ void k_store_to_half(int64_t nvec, const float4* __restrict__ H32, float s, uint4* __restrict__ H16) {
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nvec; i += int64_t(gridDim.x) * blockDim.x) {
-    // output vector i = (blk*(NHP/8) + j)*32 + lane holds entries 8j..8j+7;
-    // the FP32 store has them in vectors (blk*(NHP/4) + 2j)*32 + lane and
-    // (.. + 1)*32 + lane
-    const int64_t lane = i & 31, bj = i >> 5;
-    const int64_t blk = bj / (NHP / 8), j = bj % (NHP / 8);
-    const int64_t src = (blk * (NHP / 4) + 2 * j) * 32 + lane;
-    const float4 a = H32[src], b = H32[src + 32];
-    uint4 o;
-    __half2* h = reinterpret_cast<__half2*>(&o);
-    h[0] = __floats2half2_rn(a.x * s, a.y * s);
-    h[1] = __floats2half2_rn(a.z * s, a.w * s);
-    h[2] = __floats2half2_rn(b.x * s, b.y * s);
-    h[3] = __floats2half2_rn(b.z * s, b.w * s);
-    H16[i] = o;
-  }
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nvec; i += int64_t(gridDim.x) * blockDim.x)
+    H16[i] = half_vector(H32, s, i);
 }
 
 inline unsigned grid_for(int64_t threads, int block) {
@@ -860,6 +848,14 @@ int take_wait_timeouts() {
   return n;
 }
 
+float half_store_scale(float amax) {
+  // the largest entry lands in [2^14, 2^15): far from the binary16 maximum
+  // (65504) and with 2^-24 / 2^15 ~ 2^-39 of the largest entry still resolved
+  int e = 0;
+  std::frexp(amax > 0.f ? amax : 1.f, &e);  // amax = m 2^e, m in [0.5, 1)
+  return std::ldexp(1.f, 15 - e);
+}
+
 float launch_store_to_half(const Grid& g, const float* H32, __half* H16, unsigned* scratch, cudaStream_t s) {
   const int64_t n = g.nblk() * HBLK;
   cudaMemsetAsync(scratch, 0, sizeof(unsigned), s);
@@ -871,11 +867,7 @@ float launch_store_to_half(const Grid& g, const float* H32, __half* H16, unsigne
   float amax = 0.f;
   std::memcpy(&amax, &bits, sizeof(float));
   if (!std::isfinite(amax)) return 0.f;
-  // the largest entry lands in [2^14, 2^15): far from the binary16 maximum
-  // (65504) and with 2^-24 / 2^15 ~ 2^-39 of the largest entry still resolved
-  int e = 0;
-  std::frexp(amax > 0.f ? amax : 1.f, &e);  // amax = m 2^e, m in [0.5, 1)
-  const float scale = std::ldexp(1.f, 15 - e);
+  const float scale = half_store_scale(amax);
   k_store_to_half<<<unsigned(sm_count()) * 8, 256, 0, s>>>(n / 8, reinterpret_cast<const float4*>(H32), scale,
                                                             reinterpret_cast<uint4*>(H16));
   count_launches(1);

@@ -156,3 +156,35 @@ def test_batch_member_at_the_top_of_the_size_range(binding):
     rel = np.linalg.norm(rows) / np.linalg.norm(R)
     print(f"n = 24 batch member: ||K x + R|| / ||R|| = {rel:.3e}")
     assert rel <= 1e-8
+
+
+def test_engine_with_binary16_store(binding):
+    """Every problem with the binary16 preconditioner store: the batched
+    engine (binary16 copies made for all levels of all problems at once, the
+    V-cycle applying them) gives the lockstep driver's Newton iterates to the
+    solve tolerance, with the same FGMRES iteration counts up to one, and it
+    really runs as the engine (a small fraction of the lockstep launches)."""
+    sts = _uneven()
+    opts = abi.default_opts(abi.PFM_F32, max_newton=2, lin_rtol=1e-10, max_lin_it=600)
+    out = []
+    for mode in (0, 1):
+        probs = [binding.problem_from_state(st) for st in sts]
+        for P in probs:
+            P.set_preconditioner_store(True)
+        B = binding.Batch(probs)
+        B.set_mode(mode)
+        Us = [torch.from_numpy(st.U.copy()).cuda() for st in sts]
+        l0 = binding.launch_count()
+        reps = B.newton_solve(Us, opts, check=False)
+        launches = binding.launch_count() - l0
+        assert all(r.newton_its == 2 and r.lin_res_final <= 1e-10 for r in reps), \
+            [(r.newton_its, r.lin_res_final) for r in reps]
+        out.append(([u.cpu().numpy() for u in Us], [r.lin_its_total for r in reps], launches))
+        B.close()
+        for P in probs:
+            P.close()
+    for k, st in enumerate(sts):
+        d0, d1 = out[0][0][k] - st.U, out[1][0][k] - st.U
+        assert np.linalg.norm(d0 - d1) <= 1e-6 * np.linalg.norm(d1), k
+        assert abs(out[0][1][k] - out[1][1][k]) <= 1, (out[0][1][k], out[1][1][k])
+    assert out[0][2] * 3 < out[1][2], (out[0][2], out[1][2])

@@ -112,7 +112,7 @@ typedef struct {
                             PFM_F64: every step in FP64 */
   int smoother;          /* 0: Chebyshev-accelerated point-block Jacobi on the interval
                             [cheb_lo, cheb_hi] * lambda_max(D^-1 J) (lambda_max estimated by
-                            power iteration at pfm_linearize); 1: damped point-block Jacobi */
+                            Lanczos steps at pfm_linearize); 1: damped point-block Jacobi */
   double cheb_lo, cheb_hi;  /* Chebyshev interval as fractions of lambda_max (0.05, 1.1) */
   int cycle_gamma;       /* coarse corrections per level: 1 = V-cycle, 2 = W-cycle (<= 0 read as 1) */
   double nu_growth;      /* smoothing steps on level l: round(nu * nu_growth^l) (<= 0 read as 1) */
@@ -171,13 +171,16 @@ const char* pfm_last_error(const pfm_handle* h);
 pfm_status pfm_get_sizes(const pfm_handle* h, int64_t* n_nodes, int64_t* n_elems, int* n_levels);
 
 /* Multigrid level l (0 = finest): element counts and, after pfm_linearize,
- * the power-iteration estimate of lambda_max(D^-1 J) used by the Chebyshev
- * smoother (0 on the coarsest level, which is solved directly).
+ * the Lanczos estimate of lambda_max(D^-1 J) used by the Chebyshev smoother
+ * (0 on the coarsest level, which is solved directly).
  * Errors: PFM_ERR_INVALID_ARG (NULL handle, level out of range). */
 pfm_status pfm_get_level(const pfm_handle* h, int level, int* nx, int* ny, int* nz, double* lambda_max);
 
-/* Power-iteration steps of the smoother's eigenvalue estimate (default 30,
- * 1..1000); takes effect at the next pfm_linearize.
+/* Steps of the smoother's eigenvalue estimate (default 10, 1..1000): the
+ * Lanczos process for J D^-1 in the D^-1 inner product on every smoothed
+ * level, whose largest Ritz value is the lambda_max of the Chebyshev
+ * interval (the name is kept from an earlier power-iteration estimate).
+ * Takes effect at the next pfm_linearize.
  * Errors: PFM_ERR_INVALID_ARG (out of range). */
 pfm_status pfm_set_power_iterations(pfm_handle* h, int iterations);
 

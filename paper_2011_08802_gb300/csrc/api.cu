@@ -246,35 +246,69 @@ pfm_status ensure_level_vectors(pfm_handle* h) {
   return PFM_OK;
 }
 
-// lambda_max(D^-1 J) on level l by power_its steps of the power iteration from a
-// fixed pseudo-random start (normalised on the device; one read at the end).
+// lambda_max(D^-1 J) on level l by power_its steps of the Lanczos process
+// (Saad, Numerical Methods for Large Eigenvalue Problems, Alg. 6.5) for
+// A = J D^-1, which is self-adjoint in the inner product <u, v> = u^T D^-1 v
+// and has the eigenvalues of D^-1 J: from a fixed pseudo-random q_0 with
+// z_0 = D^-1 q_0 (both scaled to <q_0, q_0> = 1), step j forms u = J z_j,
+// alpha_j = z_j^T u, u -= alpha_j q_j + beta_{j-1} q_{j-1}, w = D^-1 u,
+// beta_j^2 = u^T w, q_{j+1} = u / beta_j, z_{j+1} = w / beta_j; the scalars stay
+// on the device (FP64 dots) and are read once at the end, and the largest
+// eigenvalue of the tridiagonal (alpha, beta) is the estimate. Its Ritz
+// value approaches lambda_max from below much faster than a power iteration
+// (the spectrum of D^-1 J is dense near its top).
 template <typename T>
 pfm_status estimate_lambda(pfm_handle* h, size_t l) {
   Level& lv = h->L[l];
   cudaStream_t s = h->stream;
   const int64_t n = ndof(lv);
-  T* x = LvVec<T>::x(lv);
-  T* y = LvVec<T>::y(lv);
-  T* z = LvVec<T>::r(lv);
-  const T* D = LvVec<T>::D(lv);
-  launch_power_init<T>(lv.nn, lv.mask, x, s);
-  launch_dot<T>(n, x, x, h->partial, h->hdev, s);
-  launch_scale_inv_sqrt<T>(n, x, h->hdev, x, s);
-  CKL_AT("power iteration start");
-  for (int it = 0; it < h->power_its; ++it) {
-    precond_apply<T>(h, l, x, y, false);
-    CKL_AT("power iteration: tangent application");
-    CK(cudaMemsetAsync(z, 0, sizeof(T) * n, s));
-    launch_smooth<T>(lv.nn, D, y, nullptr, T(1), z, s);
-    launch_dot<T>(n, z, z, h->partial, h->hdev, s);
-    launch_scale_inv_sqrt<T>(n, z, h->hdev, x, s);
-    CKL_AT("power iteration");
+  const int K = h->power_its;
+  if (h->lz_cap < 2 * K + 1) {
+    dfree(h->lz);
+    TRY(dalloc(h, &h->lz, size_t(2 * K + 1)));
+    h->lz_cap = 2 * K + 1;
   }
-  double dot = 0.0;
-  CK(cudaMemcpyAsync(&dot, h->hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  double* al = h->lz;
+  double* be = h->lz + K;
+  double* nrm = h->lz + 2 * K;
+  T* q = LvVec<T>::x(lv);
+  T* qp = LvVec<T>::b(lv);
+  T* z = LvVec<T>::d(lv);
+  T* u = LvVec<T>::y(lv);
+  T* w = LvVec<T>::r(lv);
+  const T* D = LvVec<T>::D(lv);
+  auto dinv = [&](const T* src, T* dst) {  // dst = D^-1 src
+    CK(cudaMemsetAsync(dst, 0, sizeof(T) * n, s));
+    launch_smooth<T>(lv.nn, D, src, nullptr, T(1), dst, s);
+    return PFM_OK;
+  };
+  launch_power_init<T>(lv.nn, lv.mask, q, s);
+  TRY(dinv(q, z));
+  launch_dot<T>(n, q, z, h->partial, nrm, s);
+  launch_scale_inv_sqrt<T>(n, q, nrm, q, s);
+  launch_scale_inv_sqrt<T>(n, z, nrm, z, s);
+  CK(cudaMemsetAsync(qp, 0, sizeof(T) * n, s));
+  CKL_AT("eigenvalue estimate start");
+  for (int j = 0; j < K; ++j) {
+    precond_apply<T>(h, l, z, u, false);
+    CKL_AT("eigenvalue estimate: tangent application");
+    launch_dot<T>(n, z, u, h->partial, al + j, s);
+    launch_lanczos_orth<T>(n, u, q, qp, al + j, j > 0 ? be + j - 1 : nullptr, s);
+    TRY(dinv(u, w));
+    launch_dot<T>(n, u, w, h->partial, be + j, s);
+    if (j + 1 < K) {
+      std::swap(q, qp);
+      launch_scale_inv_sqrt<T>(n, u, be + j, q, s);
+      launch_scale_inv_sqrt<T>(n, w, be + j, z, s);
+    }
+    CKL_AT("eigenvalue estimate");
+  }
+  std::vector<double> hab(size_t(2 * K));
+  CK(cudaMemcpyAsync(hab.data(), h->lz, sizeof(double) * 2 * K, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  if (!(dot > 0.0) || !std::isfinite(dot)) return h->fail(PFM_ERR_BREAKDOWN, "smoother eigenvalue estimate failed");
-  lv.lam = std::sqrt(dot);
+  const double lam = tridiag_max_eig(hab.data(), hab.data() + K, K);
+  if (!(lam > 0.0) || !std::isfinite(lam)) return h->fail(PFM_ERR_BREAKDOWN, "smoother eigenvalue estimate failed");
+  lv.lam = lam;
   return PFM_OK;
 }
 
@@ -1094,6 +1128,7 @@ void pfm_destroy(pfm_handle* h) {
     dfree(lv.x32); dfree(lv.b32); dfree(lv.y32); dfree(lv.x64); dfree(lv.b64); dfree(lv.y64);
     dfree(lv.r32); dfree(lv.d32); dfree(lv.r64); dfree(lv.d64); dfree(lv.Kc64); dfree(lv.Kc32);
   }
+  dfree(h->lz);
   dfree(h->dirval); dfree(h->energy_dev); dfree(h->flag_dev); dfree(h->diag_part); dfree(h->load_dev); dfree(h->R); dfree(h->dU); dfree(h->wv);
   dfree(h->rv); dfree(h->zd); dfree(h->ir_r); dfree(h->ir_d); dfree(h->partial); dfree(h->hdev); dfree(h->V); dfree(h->Kaug); dfree(h->Kinv);
   dfree(h->gj_keys); dfree(h->gj_used); dfree(h->gj_piv); dfree(h->amax_dev);
@@ -1150,7 +1185,7 @@ pfm_status pfm_set_deterministic(pfm_handle* h, int deterministic) {
 
 pfm_status pfm_set_power_iterations(pfm_handle* h, int iterations) {
   if (!h) return PFM_ERR_INVALID_ARG;
-  if (iterations < 1 || iterations > 1000) return h->fail(PFM_ERR_INVALID_ARG, "power iterations must be in 1..1000");
+  if (iterations < 1 || iterations > 1000) return h->fail(PFM_ERR_INVALID_ARG, "Lanczos steps must be in 1..1000");
   h->power_its = iterations;
   h->linearized = false;
   return PFM_OK;

@@ -371,13 +371,13 @@ __global__ void k_b_power_init(const BLev* __restrict__ S, Gate on) {
     x[i] = float(power_init_value(i, nn, L.mask));
 }
 
-// r = D^-1 y (one point-block Jacobi step from zero)
-__global__ void k_b_dinv(const BLev* __restrict__ S, Gate on) {
+// vec[dst] = D^-1 vec[src] (one point-block Jacobi step from zero)
+__global__ void k_b_dinv(const BLev* __restrict__ S, int src, int dst, Gate on) {
   const BLev& L = S[blockIdx.y];
   if (!on(L.problem)) return;
   const int64_t nn = L.g.nn();
-  const float* y = L.vec[VY];
-  float* r = L.vec[VR];
+  const float* y = L.vec[src];
+  float* r = L.vec[dst];
   for (int64_t node = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; node < nn; node += int64_t(gridDim.x) * blockDim.x) {
     float yv[NF];
 #pragma unroll
@@ -392,15 +392,16 @@ __global__ void k_b_dinv(const BLev* __restrict__ S, Gate on) {
   }
 }
 
-// partial[(entry * BCH + chunk)] = sum over the chunk of vec[sel]^2 (FP64 accumulation)
-__global__ void __launch_bounds__(BT) k_b_norm2_32(const BLev* __restrict__ S, int sel, double* __restrict__ partial,
-                                                   Gate on) {
+// partial[(entry * BCH + chunk)] = sum over the chunk of vec[sa] . vec[sb] (FP64 accumulation)
+__global__ void __launch_bounds__(BT) k_b_dot_32(const BLev* __restrict__ S, int sa, int sb,
+                                                 double* __restrict__ partial, Gate on) {
   const BLev& L = S[blockIdx.y];
   const int64_t n = on(L.problem) ? NF * L.g.nn() : 0;
-  const float* a = L.vec[sel];
+  const float* a = L.vec[sa];
+  const float* c = L.vec[sb];
   double acc = 0.0;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    acc += double(a[i]) * double(a[i]);
+    acc += double(a[i]) * double(c[i]);
   __shared__ double red[BT / 32];
   for (int m = 16; m > 0; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -421,17 +422,42 @@ __global__ void k_b_reduce_chunks(int ns, int chunks, const double* __restrict__
   out[e] = s;
 }
 
-// x = r / sqrt(dot[entry])  (power iteration normalisation)
-__global__ void k_b_normalise(const BLev* __restrict__ S, int src, const double* __restrict__ dot, Gate on) {
+// vec[dst] = vec[src] / sqrt(dot[entry]) (0 for a non-positive dot)
+__global__ void k_b_scale(const BLev* __restrict__ S, int src, int dst, const double* __restrict__ dot, Gate on) {
   const BLev& L = S[blockIdx.y];
   if (!on(L.problem)) return;
   const int64_t n = NF * L.g.nn();
   const double d = dot[blockIdx.y];
-  const float s = d > 0.0 ? float(1.0 / sqrt(d)) : 0.f;
+  const float sc = d > 0.0 ? float(1.0 / sqrt(d)) : 0.f;
   const float* a = L.vec[src];
-  float* x = L.vec[VX];
+  float* x = L.vec[dst];
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    x[i] = a[i] * s;
+    x[i] = a[i] * sc;
+}
+
+// vec[sel] = 0
+__global__ void k_b_zero(const BLev* __restrict__ S, int sel, Gate on) {
+  const BLev& L = S[blockIdx.y];
+  if (!on(L.problem)) return;
+  const int64_t n = NF * L.g.nn();
+  float* x = L.vec[sel];
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    x[i] = 0.f;
+}
+
+// Lanczos step of every entry: vec[u] -= alpha[e] vec[q] + sqrt(beta2prev[e]) vec[qp]
+__global__ void k_b_lanczos_orth(const BLev* __restrict__ S, int usel, int qsel, int qpsel,
+                                 const double* __restrict__ alpha, const double* __restrict__ beta2prev, Gate on) {
+  const BLev& L = S[blockIdx.y];
+  if (!on(L.problem)) return;
+  const int64_t n = NF * L.g.nn();
+  const float a = float(alpha[blockIdx.y]);
+  const float bq = beta2prev ? float(sqrt(beta2prev[blockIdx.y])) : 0.f;
+  float* u = L.vec[usel];
+  const float* q = L.vec[qsel];
+  const float* qp = L.vec[qpsel];
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    u[i] -= a * q[i] + (beta2prev ? bq * qp[i] : 0.f);
 }
 
 // Gauss-Jordan over the batch: blockIdx.y = problem
@@ -868,6 +894,9 @@ struct BatchEngine {
   int grid_japply = 0, grid_df = 0, grid_j64 = 0;
   bool h16 = false;             // the V-cycle applies the binary16 copies of the stores
   unsigned* amax = nullptr;     // per A-set level: max |H| bits
+  double* lz = nullptr;         // Lanczos alpha, beta^2 and start norms of the A-set levels
+  double* hlz = nullptr;        // pinned copy of alpha and beta^2
+  size_t lz_cap = 0;
   unsigned* hamax = nullptr;    // pinned copy
   cudaGraphExec_t vgraph = nullptr;
   std::vector<cudaGraphExec_t> itg;
@@ -901,6 +930,7 @@ struct BatchEngine {
     if (hres) cudaFreeHost(hres);
     if (hact) cudaFreeHost(hact);
     if (hamax) cudaFreeHost(hamax);
+    if (hlz) cudaFreeHost(hlz);
   }
   Gate gate_fgm() const { return Gate{&dF[0].active, int(sizeof(BFgm) / sizeof(int))}; }
   Gate gate_act() const { return Gate{dact, 1}; }
@@ -1284,22 +1314,51 @@ pfm_status eng_linearize(pfm_batch* b, BatchEngine* E, int power_its) {
     k_b_blockdiag<<<gdiv(E->neBd * 8, 128), 128, 0, s>>>(E->dBd, nA, E->neBd, g);
     k_b_block_invert<<<grid2(E->maxnnBd, nA), BT, 0, s>>>(E->dBd, E->singular, g);
     count_launches(3);
-    // power iteration for lambda_max(D^-1 J) on every non-coarsest level at once
-    const dim3 gv(BCH, unsigned(nA));
-    k_b_power_init<<<grid2(NF * E->maxnnA, nA), BT, 0, s>>>(E->dA, g);
-    k_b_norm2_32<<<gv, BT, 0, s>>>(E->dA, VX, E->partial, g);
-    k_b_reduce_chunks<<<gdiv(nA, 128), 128, 0, s>>>(nA, BCH, E->partial, E->dots);
-    k_b_normalise<<<grid2(NF * E->maxnnA, nA), BT, 0, s>>>(E->dA, VX, E->dots, g);
-    count_launches(4);
-    for (int it = 0; it < power_its; ++it) {
-      eng_japply(E, E->dA, nA, E->nblkA, E->maxnnA, VX, VY, g);
-      k_b_dinv<<<grid2(E->maxnnA, nA), BT, 0, s>>>(E->dA, g);
-      k_b_norm2_32<<<gv, BT, 0, s>>>(E->dA, VR, E->partial, g);
-      k_b_reduce_chunks<<<gdiv(nA, 128), 128, 0, s>>>(nA, BCH, E->partial, E->dots);
-      k_b_normalise<<<grid2(NF * E->maxnnA, nA), BT, 0, s>>>(E->dA, VR, E->dots, g);
-      count_launches(4);
+    // Lanczos estimate of lambda_max(D^-1 J) on every non-coarsest level at
+    // once (the single-problem estimate_lambda, entry by entry): q = VX / VB
+    // alternating with q_prev, z = VD, u = VY, w = VR
+    const int K = power_its;
+    const size_t nlz = size_t(2 * K + 1) * nA;
+    if (E->lz_cap < nlz) {
+      BCK(E->alloc(&E->lz, nlz));
+      if (E->hlz) cudaFreeHost(E->hlz);
+      E->hlz = nullptr;
+      BCK(cudaMallocHost(reinterpret_cast<void**>(&E->hlz), sizeof(double) * nlz));
+      E->lz_cap = nlz;
     }
-    BCK(cudaMemcpyAsync(E->hres, E->dots, sizeof(double) * nA, cudaMemcpyDeviceToHost, s));
+    double* al = E->lz;                     // [K][nA]
+    double* be = E->lz + size_t(K) * nA;    // [K][nA]
+    double* nrm = E->lz + size_t(2 * K) * nA;
+    const dim3 gv(BCH, unsigned(nA));
+    const dim3 gn = grid2(E->maxnnA, nA), gf = grid2(NF * E->maxnnA, nA);
+    auto dot = [&](int a, int c, double* out) {
+      k_b_dot_32<<<gv, BT, 0, s>>>(E->dA, a, c, E->partial, g);
+      k_b_reduce_chunks<<<gdiv(nA, 128), 128, 0, s>>>(nA, BCH, E->partial, out);
+    };
+    int qs = VX, qps = VB;
+    k_b_power_init<<<gf, BT, 0, s>>>(E->dA, g);
+    k_b_dinv<<<gn, BT, 0, s>>>(E->dA, VX, VD, g);
+    dot(VX, VD, nrm);
+    k_b_scale<<<gf, BT, 0, s>>>(E->dA, VX, VX, nrm, g);
+    k_b_scale<<<gf, BT, 0, s>>>(E->dA, VD, VD, nrm, g);
+    k_b_zero<<<gf, BT, 0, s>>>(E->dA, VB, g);
+    count_launches(7);
+    for (int j = 0; j < K; ++j) {
+      eng_japply(E, E->dA, nA, E->nblkA, E->maxnnA, VD, VY, g);
+      dot(VD, VY, al + size_t(j) * nA);
+      k_b_lanczos_orth<<<gf, BT, 0, s>>>(E->dA, VY, qs, qps, al + size_t(j) * nA,
+                                         j > 0 ? be + size_t(j - 1) * nA : nullptr, g);
+      k_b_dinv<<<gn, BT, 0, s>>>(E->dA, VY, VR, g);
+      dot(VY, VR, be + size_t(j) * nA);
+      count_launches(6);
+      if (j + 1 < K) {
+        std::swap(qs, qps);
+        k_b_scale<<<gf, BT, 0, s>>>(E->dA, VY, qs, be + size_t(j) * nA, g);
+        k_b_scale<<<gf, BT, 0, s>>>(E->dA, VR, VD, be + size_t(j) * nA, g);
+        count_launches(2);
+      }
+    }
+    BCK(cudaMemcpyAsync(E->hlz, E->lz, sizeof(double) * size_t(2 * K) * nA, cudaMemcpyDeviceToHost, s));
   }
   // dense coarse operators (one assembly per problem) and their inverses (one launch per step for all)
   for (int p = 0; p < E->np; ++p) {
@@ -1326,15 +1385,14 @@ pfm_status eng_linearize(pfm_batch* b, BatchEngine* E, int power_its) {
   if (sing) return b->fail(PFM_ERR_BREAKDOWN, "singular diagonal block or coarse operator in the batch");
   // Chebyshev coefficients from the eigenvalue estimates
   bool changed = false;
+  std::vector<double> ab(size_t(2 * power_its));
   for (int i = 0; i < nA; ++i) {
-    const double dot = E->hres[i];
-    if (!(dot > 0.0) || !std::isfinite(dot)) {
-      if (!E->hact[E->Aidx[i].first]) continue;
+    if (!E->hact[E->Aidx[i].first]) continue;
+    for (int j = 0; j < 2 * power_its; ++j) ab[j] = E->hlz[size_t(j) * nA + i];
+    const double lam = tridiag_max_eig(ab.data(), ab.data() + power_its, power_its);
+    if (!(lam > 0.0) || !std::isfinite(lam))
       return b->fail(PFM_ERR_BREAKDOWN, "smoother eigenvalue estimate failed for problem " +
                                             std::to_string(E->Aidx[i].first));
-    }
-    if (!E->hact[E->Aidx[i].first]) continue;
-    const double lam = std::sqrt(dot);
     const int p = E->Aidx[i].first, l = E->Aidx[i].second;
     b->hs[p]->L[l].lam = lam;
     const float it = float(2.0 / ((E->hi + E->lo) * lam)), id = float(2.0 / ((E->hi - E->lo) * lam));

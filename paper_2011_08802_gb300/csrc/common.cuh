@@ -4,7 +4,9 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
+#include <limits>
 
 #include "qp_physics.cuh"
 
@@ -66,6 +68,47 @@ struct FastDiv {
     return (t + n) >> l;
   }
 };
+
+// Largest eigenvalue of the symmetric tridiagonal matrix T of a Lanczos run
+// (host code): diagonal alpha[0..m), squared off-diagonal beta2[0..m-1).
+// The run is cut at the first alpha that is not finite, or the first beta2
+// that is not positive and finite (an invariant subspace was reached; T is
+// then exact). Bisection on the Sturm count of T - x I (the number of negative
+// pivots of its LDL^T factorisation equals the number of eigenvalues below x;
+// Wilkinson, The Algebraic Eigenvalue Problem, 1965, Ch. 5) inside the
+// Gershgorin interval. Returns NaN if no step is usable.
+inline double tridiag_max_eig(const double* alpha, const double* beta2, int m) {
+  int k = 0;
+  while (k < m && alpha[k] == alpha[k] && alpha[k] - alpha[k] == 0.0) {
+    ++k;
+    if (k < m && !(beta2[k - 1] > 0.0 && beta2[k - 1] - beta2[k - 1] == 0.0)) break;
+  }
+  m = k;
+  if (m == 0) return std::numeric_limits<double>::quiet_NaN();
+  auto offd = [&](int i) { return (i >= 0 && i < m - 1) ? std::sqrt(beta2[i]) : 0.0; };
+  double lo = alpha[0], hi = alpha[0];
+  for (int i = 0; i < m; ++i) {
+    const double r = offd(i - 1) + offd(i);
+    lo = alpha[i] - r < lo ? alpha[i] - r : lo;
+    hi = alpha[i] + r > hi ? alpha[i] + r : hi;
+  }
+  auto below = [&](double x) {  // eigenvalues of T below x
+    int c = 0;
+    double d = 1.0;
+    for (int i = 0; i < m; ++i) {
+      d = alpha[i] - x - (i > 0 ? beta2[i - 1] / d : 0.0);
+      if (d == 0.0) d = -1e-300;  // x at an eigenvalue of a leading block: count it below
+      c += d < 0.0;
+    }
+    return c;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * (hi > -lo ? hi : -lo); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (below(mid) == m) hi = mid;
+    else lo = mid;
+  }
+  return hi;
+}
 
 // Per-node Dirichlet bit mask (bit f set = DOF f prescribed).
 using dmask_t = uint16_t;
@@ -156,6 +199,11 @@ template <typename T>
 void launch_power_init(int64_t nn, const dmask_t* mask, T* x, cudaStream_t s);
 template <typename T>
 void launch_scale_inv_sqrt(int64_t n, const T* y, const double* dot, T* x, cudaStream_t s);
+// Lanczos step: u -= alpha q + sqrt(beta2prev) qp (alpha, beta2prev: device
+// scalars; beta2prev null for the first step)
+template <typename T>
+void launch_lanczos_orth(int64_t n, T* u, const T* q, const T* qp, const double* alpha, const double* beta2prev,
+                         cudaStream_t s);
 int dense_gauss_jordan_inverse(double* Maug, int n, double* Ainv, unsigned long long* keys, int* used, int* piv,
                                int* singular, cudaStream_t s);
 template <typename T>

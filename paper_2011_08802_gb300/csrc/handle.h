@@ -115,7 +115,9 @@ struct pfm_handle {
   cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
   cudaEvent_t pipe_ev_in[PIPE_SLABS] = {}, pipe_ev_done[PIPE_SLABS] = {};
   cudaEvent_t pipe_ev_start = nullptr;
-  int power_its = 30;
+  int power_its = 10;     // Lanczos steps of the smoother's eigenvalue estimate
+  double* lz = nullptr;   // their alpha and beta^2 (device), and one norm
+  int lz_cap = 0;
   bool outer_df = true;  // outer operator of the mixed solve in double-float arithmetic
   bool lin_df = false;   // FP64-class linearisation in double-float instead of FP64 arithmetic
   bool res_df = false;   // residual point physics in double-float instead of FP64 arithmetic

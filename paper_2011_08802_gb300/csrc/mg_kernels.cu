@@ -262,7 +262,24 @@ __global__ void k_scale_inv_sqrt(int64_t n, const T* __restrict__ y, const doubl
     x[i] = y[i] * s;
 }
 
+// u -= alpha q + sqrt(beta2prev) qp (one Lanczos three-term step)
+template <typename T>
+__global__ void k_lanczos_orth(int64_t n, T* __restrict__ u, const T* __restrict__ q, const T* __restrict__ qp,
+                               const double* __restrict__ alpha, const double* __restrict__ beta2prev) {
+  const T a = T(*alpha);
+  const T b = beta2prev ? T(sqrt(*beta2prev)) : T(0);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    u[i] -= a * q[i] + (beta2prev ? b * qp[i] : T(0));
+}
+
 }  // namespace
+
+template <typename T>
+void launch_lanczos_orth(int64_t n, T* u, const T* q, const T* qp, const double* alpha, const double* beta2prev,
+                         cudaStream_t s) {
+  k_lanczos_orth<T><<<grid_for(n, 256), 256, 0, s>>>(n, u, q, qp, alpha, beta2prev);
+  count_launches(1);
+}
 
 template <typename T>
 void launch_cheb_first(int64_t nn, const T* D, const T* src, T c, bool copy_r, bool zero_x, T* r, T* d, T* x,
@@ -392,7 +409,9 @@ void launch_coarse_solve(int n, const double* Ainv, const T* b, T* x, cudaStream
                                      cudaStream_t);                                             \
   template void launch_cheb_step<T>(int64_t, const T*, const T*, T, T, T*, T*, T*, cudaStream_t); \
   template void launch_power_init<T>(int64_t, const dmask_t*, T*, cudaStream_t);                  \
-  template void launch_scale_inv_sqrt<T>(int64_t, const T*, const double*, T*, cudaStream_t);
+  template void launch_scale_inv_sqrt<T>(int64_t, const T*, const double*, T*, cudaStream_t);     \
+  template void launch_lanczos_orth<T>(int64_t, T*, const T*, const T*, const double*, const double*, \
+                                       cudaStream_t);
 PFM_INST(float)
 PFM_INST(double)
 #undef PFM_INST

@@ -100,6 +100,18 @@ typedef struct {
                             pade22, pade33); other values are rejected (PFM_ERR_INVALID_ARG) */
 } pfm_params;
 
+/* Scalar material data of the CuAlNi example of Sec. 5.1, from which
+ * pfm_params_from_cubic builds a parameter block (units GPa, nm, s). */
+typedef struct {
+  double stretch_alpha, stretch_beta, stretch_gamma; /* alpha, beta, gamma of the variant stretches */
+  double C11, C12, C44;           /* one cubic stiffness for every phase (Voigt, crystal axes) */
+  double F0_austenite, F0_martensite; /* chemical energies F_0 and F_i, i >= 1 */
+  double mobility;                /* m_i, every phase */
+  double gamma_am, gamma_mm;      /* interface energies gamma_0i and gamma_ij, i, j >= 1 */
+  double ell;                     /* interface thickness parameter, every pair */
+  double eps_eta;                 /* penalty eps_eta */
+} pfm_cubic_material;
+
 typedef struct {
   int max_newton;        /* Newton iteration cap (>= 1) */
   int restart;           /* FGMRES restart length m (1..64) */
@@ -153,6 +165,40 @@ const char* pfm_version(void);
 /* Number N of martensite variants the library was compiled for (PFM_NV):
  * nodal vectors have 3 + N fields and pfm_params has N + 1 phases. */
 int pfm_variants(void);
+
+/* Parameter blocks without writing them by hand (host functions, no GPU
+ * needed, no allocation). */
+
+/* *out = the model data of Sec. 5.1 from the scalars in *m: phase 0 the
+ * austenite with U_0 = I, phases 1..6 the orthorhombic variants with
+ * U_1 = [[p, 0, q], [0, beta, 0], [q, 0, p]], p = (alpha + gamma)/2,
+ * q = (alpha - gamma)/2, U_2 the same with -q, U_3, U_4 the pattern with the
+ * shear in the (1,2) plane and beta on axis 3, U_5, U_6 with beta on axis 1
+ * and the shear in the (2,3) plane (the matrices printed in Sec. 5.1); the
+ * cubic Voigt stiffness (C11, C12, C44) for every phase (Eq. elasticEn);
+ * gamma_0i = gamma_am, gamma_ij = gamma_mm (i, j >= 1), one ell (Eq.
+ * IntEnergy); F_0, F_i, one mobility, eps_eta, tau; gamma_scale = 1; hencky
+ * as in pfm_params. Errors: PFM_ERR_INVALID_ARG (null pointer, hencky outside
+ * 0..3, a library built for N != 6 variants). */
+pfm_status pfm_params_from_cubic(const pfm_cubic_material* m, double tau, int hencky, pfm_params* out);
+
+/* Anisotropic stiffness of Table 1 in the crystal frame of *p: the
+ * austenite gets the cubic matrix (cubic[0..2] = c11, c12, c44), every
+ * variant i >= 1 the orthorhombic matrix ortho[0..8] = (c11, c22, c33, c44,
+ * c55, c66, c12, c13, c23) in its own axes 1, 2, 3, which are the
+ * eigenvectors of its stretch U_i (in p->Ut) with the eigenvalues closest to
+ * axis_stretch[0..2] (alpha, beta, gamma for CuAlNi), turned into the crystal
+ * frame with the Bond matrix of those axes (engineering shear strains).
+ * Errors: PFM_ERR_INVALID_ARG (null pointer, a stretch that is not
+ * symmetric positive definite). */
+pfm_status pfm_params_orthorhombic_stiffness(pfm_params* p, const double cubic[3], const double ortho[9],
+                                             const double axis_stretch[3]);
+
+/* Turn every stretch and stiffness of *p from the crystal frame into the lab
+ * frame: U -> R U R^T and L -> M L M^T with M the Bond matrix of R (row i of R
+ * = lab axis i in crystal coordinates; R orthogonal, row-major). Errors:
+ * PFM_ERR_INVALID_ARG (null pointer, R not orthogonal to 1e-12). */
+pfm_status pfm_params_rotate(pfm_params* p, const double R[9]);
 
 /* Create a problem on a structured grid with the given parameters and build
  * the multigrid level hierarchy (Sec. 3.4: uniform refinement hierarchy).

@@ -59,6 +59,13 @@ PARAMS = {6: Params, 12: _params_class(12)}
 HENCKY = {"log": 0, "pade11": 1, "pade22": 2, "pade33": 3}
 
 
+class CubicMaterial(C.Structure):
+    """pfm_cubic_material: the scalar model data of Sec. 5.1."""
+    _fields_ = [(n, C.c_double) for n in (
+        "stretch_alpha", "stretch_beta", "stretch_gamma", "C11", "C12", "C44", "F0_austenite",
+        "F0_martensite", "mobility", "gamma_am", "gamma_mm", "ell", "eps_eta")]
+
+
 class SolveOpts(C.Structure):
     _fields_ = [("max_newton", C.c_int), ("restart", C.c_int), ("max_lin_it", C.c_int),
                 ("nu_pre", C.c_int), ("nu_post", C.c_int),
@@ -260,6 +267,10 @@ def lib(n_var: int = 6):
         "pfm_residual_noalloc": (i32, [C.POINTER(MeshDesc), C.POINTER(Params), vp, vp, vp, vp,
                                        C.POINTER(dp), vp]),
         "pfm_noalloc_last_error": (C.c_char_p, []),
+        "pfm_params_from_cubic": (i32, [C.POINTER(CubicMaterial), dp, i32, C.POINTER(Params)]),
+        "pfm_params_orthorhombic_stiffness": (i32, [C.POINTER(Params), C.POINTER(dp), C.POINTER(dp),
+                                                    C.POINTER(dp)]),
+        "pfm_params_rotate": (i32, [C.POINTER(Params), C.POINTER(dp)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -286,6 +297,7 @@ def exported_symbols():
         "pfm_qp_eval", "pfm_get_hessians", "pfm_get_block_inverses", "pfm_profile_enable", "pfm_profile_get",
         "pfm_launch_count", "pfm_arith_peak", "pfm_param_grad", "pfm_batch_create", "pfm_batch_destroy",
         "pfm_batch_last_error", "pfm_batch_newton_solve", "pfm_batch_set_mode", "pfm_residual_noalloc", "pfm_noalloc_last_error",
+        "pfm_params_from_cubic", "pfm_params_orthorhombic_stiffness", "pfm_params_rotate",
     ]
 
 

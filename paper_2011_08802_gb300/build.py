@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 SOURCES = ["fe_kernels.cu", "mg_kernels.cu", "krylov_kernels.cu", "diag_kernels.cu", "contact_kernels.cu",
-           "batch.cu", "api.cu", "noalloc.cu"]
+           "batch.cu", "api.cu", "noalloc.cu", "params_build.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fno-gnu-unique: function-local statics of templates and inline functions
 # become ordinary weak symbols instead of process-wide unique ones, and the

@@ -65,6 +65,21 @@ inline void make_dev_params(const pfm_params& in, DevParams& out) {
   for (int p = 1; p < NPH; ++p)
     for (int k = 0; k < 36; ++k)
       if (in.Lvoigt[p][k] != in.Lvoigt[0][k]) out.same_L = 0;
+  // one stiffness with cubic symmetry in the frame of the parameter block:
+  // c11 on the normal diagonal, c12 off it, c44 on the shear diagonal, zero
+  // elsewhere; then L = c12 I x I + c44 (2 I_sym) + (c11 - c12 - 2 c44) sum_n e_n^4
+  const double* L0 = in.Lvoigt[0];
+  const double c11 = L0[0], c12 = L0[1], c44 = L0[21];
+  bool cubic = out.same_L == 1;
+  for (int I = 0; I < 6 && cubic; ++I)
+    for (int J = 0; J < 6; ++J) {
+      const double want = (I < 3 && J < 3) ? (I == J ? c11 : c12) : (I == J ? c44 : 0.0);
+      if (L0[6 * I + J] != want) cubic = false;
+    }
+  out.cubic = cubic ? 1 : 0;
+  out.cub_lambda = c12;
+  out.cub_mu = c44;
+  out.cub_delta = c11 - c12 - 2.0 * c44;
 }
 
 }  // namespace pfm

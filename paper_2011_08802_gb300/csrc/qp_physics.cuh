@@ -146,6 +146,8 @@ struct DevParams {
   double G[NV][NV];         // gradient-energy matrix in eta_hat (per direction)
   double eps_eta;           // penalty parameter
   int same_L;               // 1 when every phase has the same stiffness (then L(eta) = L sum eta)
+  int cubic;                // 1 when that stiffness is cubic in the frame of the data:
+  double cub_lambda, cub_mu, cub_delta;  // L = lambda I x I + 2 mu I_sym + delta sum_n e_n^4
   int hencky;               // 0: exact log; m = 1, 2, 3: Pade (m,m) (Gauss-Legendre form below)
   double pade_s[3], pade_w[3];  // m-point Gauss-Legendre nodes and weights on [0, 1]
 };
@@ -692,7 +694,27 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[NV], con
   for (int v = 0; v < 6; ++v) cv[v] = T(0.5) * f1[sym_i(v)][sym_j(v)] * (v < 3 ? T(1) : T(2));
   // L~ = Nv^T L(eta) Nv with v(Q d~ Q^T) = Nv v(d~)
   T Lt[6][6];
-  {
+  if (P.cubic) {
+    // cubic stiffness: the isotropic part lambda I x I + 2 mu I_sym is the
+    // same in every basis, and the cubic part delta sum_n e_n^4 turns into
+    // delta sum_n w_n w_n^T with w_n[A] = r_a r_b for the slot A = (a, b) and
+    // r = row n of Q (e_n in the eigenbasis); all scaled by sum eta
+    const T lam_c = T(P.cub_lambda) * esum, mu_c = T(P.cub_mu) * esum, del_c = T(P.cub_delta) * esum;
+    T w[3][6];
+#pragma unroll
+    for (int n = 0; n < 3; ++n)
+#pragma unroll
+      for (int A_ = 0; A_ < 6; ++A_) w[n][A_] = Q[n][sym_i(A_)] * Q[n][sym_j(A_)];
+#pragma unroll
+    for (int A_ = 0; A_ < 6; ++A_)
+#pragma unroll
+      for (int B = A_; B < 6; ++B) {
+        T v = del_c * (w[0][A_] * w[0][B] + w[1][A_] * w[1][B] + w[2][A_] * w[2][B]);
+        if (A_ < 3 && B < 3) v += lam_c;
+        if (A_ == B) v += A_ < 3 ? T(2) * mu_c : mu_c;
+        Lt[A_][B] = Lt[B][A_] = v;
+      }
+  } else {
     T Nv[6][6];
     for (int I = 0; I < 6; ++I) {
       const int i = sym_i(I), j = sym_j(I);

@@ -149,3 +149,37 @@ def test_indentation_newton_at_16_cubed(binding):
     assert np.linalg.norm(R1) <= 1e-7 * np.linalg.norm(R0)
     assert abs(rep.res0 - np.linalg.norm(R0)) <= 1e-10 * np.linalg.norm(R0)
     P.close()
+
+
+def test_batched_engine_with_twelve_variants(binding):
+    """Three twelve-variant indentation problems of uneven size (a non-nested
+    hierarchy among them) in one batch: the batched engine (one launch per
+    phase over all problems) and the per-problem lockstep driver give the same
+    Newton corrections to the solve tolerance, and each meets it against the
+    FP64 operator of its own problem."""
+    sts = [inputs.config_indentation(n, seed=300 + n, step=1, n_var=NV) for n in (5, 8, 9)]
+    opts = abi.default_opts(abi.PFM_F32, max_newton=1, lin_rtol=1e-10, max_lin_it=600)
+    out = []
+    for mode in (0, 1):
+        probs = [binding.problem_from_state(st) for st in sts]
+        B = binding.Batch(probs)
+        B.set_mode(mode)
+        Us = [torch.from_numpy(st.U.copy()).cuda() for st in sts]
+        reps = B.newton_solve(Us, opts, check=False)
+        assert all(r.newton_its == 1 and r.lin_res_final <= 1e-10 for r in reps), \
+            [(r.newton_its, r.lin_res_final) for r in reps]
+        out.append([u.cpu().numpy() for u in Us])
+        if mode == 0:
+            for P, st, U1 in zip(probs, sts, Us):
+                U0 = torch.from_numpy(st.U).cuda()
+                P.set_state(U0, torch.from_numpy(st.Un).cuda())
+                R = P.residual()
+                P.linearize(abi.PFM_F64)
+                y = P.jacobian_apply(U1 - U0)
+                assert float(torch.linalg.norm(y + R) / torch.linalg.norm(R)) <= 1e-9
+        B.close()
+        for P in probs:
+            P.close()
+    for k, st in enumerate(sts):
+        d0, d1 = out[0][k] - st.U, out[1][k] - st.U
+        assert np.linalg.norm(d0 - d1) <= 1e-6 * np.linalg.norm(d1), k

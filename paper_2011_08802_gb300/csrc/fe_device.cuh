@@ -646,6 +646,15 @@ struct JStaged {
   float Gs[NV][NV];  // (w / wh) G
   float wh, ihx, ihy, ihz;
   FastDiv dx, dy;    // element index -> (i, j, k): e = i + nx (j + ny k)
+#if PFM_NV == 6
+  // G = g_alpha I + g_beta 1 1^T (both times w / wh) when g_diag_plus_ones:
+  // the form G takes when every austenite-variant pair shares one interface
+  // energy and every variant-variant pair another (Sec. 5.1 data); the
+  // twelve-variant build keeps the general product only (with both forms its
+  // fully unrolled body takes nvcc more than 60 GB and 15 minutes)
+  int g_diag_plus_ones;
+  float g_alpha, g_beta;
+#endif
 };
 
 // First half of the staged body, in two steps so that a warp can issue the
@@ -733,11 +742,29 @@ __device__ __forceinline__ void staged_contract_scatter(const Grid& g, const JSt
     const float r = q1_scatter_grad(sg[3 * i], sg[3 * i + 1], sg[3 * i + 2], l8, jp.ihx, jp.ihy, jp.ihz);
     if (s.valid && !((s.dm >> i) & 1)) atomicAdd(yp + i * nn, r);
   }
+#if PFM_NV == 6
+  // gradient-energy term G ge per direction: with G = alpha I + beta 1 1^T
+  // it is alpha ge_k + beta sum_l ge_l (12 operations instead of 36)
+  float bsum[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    float t = 0.f;
+#pragma unroll
+    for (int l = 0; l < NV; ++l) t += ge[3 * l + d];
+    bsum[d] = jp.g_beta * t;
+  }
+#endif
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
     float gf[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
+#if PFM_NV == 6
+      if (jp.g_diag_plus_ones) {
+        gf[d] = fmaf(jp.g_alpha, ge[3 * k + d], bsum[d]);
+        continue;
+      }
+#endif
       float a = 0.f;
 #pragma unroll
       for (int l = 0; l < NV; ++l) a += jp.Gs[k][l] * ge[3 * l + d];

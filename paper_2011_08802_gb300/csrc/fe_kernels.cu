@@ -651,6 +651,17 @@ JStaged make_jstaged(const Grid& g, const DevParams& P, double wh) {
   j.ihz = float(1.0 / g.hz);
   j.dx = FastDiv::make(uint32_t(g.nx));
   j.dy = FastDiv::make(uint32_t(g.ny));
+#if PFM_NV == 6
+  // G = alpha I + beta 1 1^T exactly (equal off-diagonal and equal diagonal entries)?
+  const double beta = P.G[0][1], diag = P.G[0][0];
+  bool ones = true;
+  for (int k = 0; k < NV; ++k)
+    for (int l = 0; l < NV; ++l)
+      if (P.G[k][l] != (k == l ? diag : beta)) ones = false;
+  j.g_diag_plus_ones = ones ? 1 : 0;
+  j.g_alpha = float(w / wh * (diag - beta));
+  j.g_beta = float(w / wh * beta);
+#endif
   return j;
 }
 

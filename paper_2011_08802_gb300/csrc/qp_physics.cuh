@@ -601,25 +601,27 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[NV], con
   // With eta_0 = 1 - sum eta_hat (Sec. 3.1) the elastic energy depends on
   // eta_hat_k through U(eta) = sum eta_i U_i and L(eta) = sum eta_i L_i, i.e.
   // along dU_k = U_k - U_0 and dL_k = L_k - L_0.
-  T dU[NV][3][3], AdU[NV][3][3], trAdU[NV];  // tr(A dU_k) = (d J_t / d eta_hat_k) / J_t
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) dU[k][i][j] = T(P.U[k + 1][i][j]) - T(P.U[0][i][j]);
-    mm3(A, dU[k], AdU[k]);
-    trAdU[k] = AdU[k][0][0] + AdU[k][1][1] + AdU[k][2][2];
-  }
-  T gel[NV];  // dW_el / d eta_hat_k
+  // dU_k is symmetric (a difference of stretches), so tr(X dU_k) = <X^T, dU_k>.
+  T trAdU[NV];  // tr(A dU_k) = (d J_t / d eta_hat_k) / J_t
+  T gel[NV];    // dW_el / d eta_hat_k
   {
-    T ES[3][3];  // E S
+    T ES[3][3], ESA[3][3];  // E S, E S A
     mm3(E, S, ES);
+    mm3(ES, A, ESA);
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
+      T ta = 0, te = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const T d = T(P.U[k + 1][i][j]) - T(P.U[0][i][j]);
+          ta += A[i][j] * d;
+          te += ESA[j][i] * d;
+        }
+      trAdU[k] = ta;
       // S : dE/d eta_hat_k = -2 tr(S A dU_k E) = -2 tr(E S A dU_k)
-      T via_E = T(-2) * tr_ab(ES, AdU[k]);
-      gel[k] = T(0.5) * Jt * trAdU[k] * hT + T(0.5) * Jt * (hLh[k + 1] - hLh[0]) + via_E;
+      gel[k] = T(0.5) * Jt * trAdU[k] * hT + T(0.5) * Jt * (hLh[k + 1] - hLh[0]) + T(-2) * te;
     }
   }
   // chemical, obstacle, dissipation, penalty: dW/d eta_i per phase
@@ -652,6 +654,16 @@ PFM_HD_BIG void qp_local(const DevParams& P, const T Fin[9], const T eh[NV], con
     for (int k = 0; k < NV; ++k) g[9 + k] = gel[k] + (geta[k + 1] - geta[0]);
   }
   if (!WANT_HESS) return;
+  // the direction eta_hat_k carries dU_k = U_k - U_0; A dU_k enters below
+  T dU[NV][3][3], AdU[NV][3][3];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) dU[k][i][j] = T(P.U[k + 1][i][j]) - T(P.U[0][i][j]);
+    mm3(A, dU[k], AdU[k]);
+  }
 
   // ---------------------------------------------------------------------
   // Hessian in the 9 + N unknowns z = (F_pQ: 0..8, eta_hat_1..N: 9..8+N), packed

@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(32 * WPC, (staged_minb<S, D, WPC>())) k_japply
 // element contributions are added to the FP64 output y (initialised by
 // k_japply_init_df). Same persistent warp mapping as k_japply.
 #ifndef PFM_DF_MINB
-#define PFM_DF_MINB 8
+#define PFM_DF_MINB (PFM_NV == 6 ? 2 : 8)
 #endif
 template <bool DET>
 __global__ void __launch_bounds__(256, PFM_DF_MINB) k_japply_df(Grid g, DfConst k, const float* __restrict__ Hhi,

@@ -509,8 +509,9 @@ __global__ void k_b_store_z(const BOut* __restrict__ O, const BFgm* __restrict__
   }
 }
 
-// w += J Z_j in double-float arithmetic over all element blocks
-__global__ void __launch_bounds__(256) k_b_japply_df(const BOut* __restrict__ O, const BFgm* __restrict__ F, int np,
+// w += J Z_j in double-float arithmetic over all element blocks (2 CTAs per
+// SM at 128 registers, as the single-problem kernel)
+__global__ void __launch_bounds__(256, (PFM_NV == 6 ? 2 : 1)) k_b_japply_df(const BOut* __restrict__ O, const BFgm* __restrict__ F, int np,
                                                      int64_t nblk, int j) {
   const int lane = threadIdx.x & 31;
   const int64_t wg = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;

@@ -31,8 +31,11 @@ namespace {
 // DET: atomic-free, the nodal results go to the scratch W (node_gather adds
 // them up) and each warp's energy to W[9 ws + blk] (summed in a fixed order
 // by k_sum_fixed).
+#ifndef PFM_RES_MINB
+#define PFM_RES_MINB 2
+#endif
 template <typename TC, bool DET>
-__global__ void __launch_bounds__(128) k_residual(Grid g, DevParams P, const double* __restrict__ U,
+__global__ void __launch_bounds__(128, PFM_RES_MINB) k_residual(Grid g, DevParams P, const double* __restrict__ U,
                                                   const double* __restrict__ Un,
                                                   const dmask_t* __restrict__ mask,
                                                   double* __restrict__ R, double* energy, double* __restrict__ W,

@@ -1001,10 +1001,9 @@ pfm_status japply_host_pipelined(pfm_handle* h, const void* v_host, void* y_host
   for (int s = 0; s < S; ++s) {
     const int64_t k0 = int64_t(g.nz) * s / S, k1 = int64_t(g.nz) * (s + 1) / S;  // element layers [k0, k1)
     const int64_t need = k1 + 1;                                                   // node planes [0, k1]
-    if (need > in_done) {
-      for (int fld = 0; fld < NF; ++fld)
-        CK(cudaMemcpyAsync(vd + fld * nn + in_done * plane, vh + fld * nn + in_done * plane,
-                           sizeof(T) * (need - in_done) * plane, cudaMemcpyHostToDevice, h->pipe_in));
+    if (need > in_done) {  // node planes [in_done, need) of every field: one 2-D copy
+      CK(cudaMemcpy2DAsync(vd + in_done * plane, sizeof(T) * nn, vh + in_done * plane, sizeof(T) * nn,
+                           sizeof(T) * (need - in_done) * plane, NF, cudaMemcpyHostToDevice, h->pipe_in));
       in_done = need;
     }
     CK(cudaEventRecord(h->pipe_ev_in[s], h->pipe_in));
@@ -1023,9 +1022,8 @@ pfm_status japply_host_pipelined(pfm_handle* h, const void* v_host, void* y_host
     CK(cudaEventRecord(h->pipe_ev_done[s], sc));
     CK(cudaStreamWaitEvent(h->pipe_out, h->pipe_ev_done[s], 0));
     if (ready > out_done) {
-      for (int fld = 0; fld < NF; ++fld)
-        CK(cudaMemcpyAsync(yh + fld * nn + out_done * plane, yd + fld * nn + out_done * plane,
-                           sizeof(T) * (ready - out_done) * plane, cudaMemcpyDeviceToHost, h->pipe_out));
+      CK(cudaMemcpy2DAsync(yh + out_done * plane, sizeof(T) * nn, yd + out_done * plane, sizeof(T) * nn,
+                           sizeof(T) * (ready - out_done) * plane, NF, cudaMemcpyDeviceToHost, h->pipe_out));
       out_done = ready;
     }
   }

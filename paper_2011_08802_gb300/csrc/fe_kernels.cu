@@ -490,7 +490,11 @@ __global__ void __launch_bounds__(256, PFM_JAPPLY_MINB) k_japply_range(Grid g, J
   const int64_t wg = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   const int lane = int(threadIdx.x & 31);
-  for (int64_t blk = b0 + wg; blk < b1; blk += nw) japply_block<T>(g, jp, H, mask, v, y, blk, lane);
+  constexpr unsigned BLK_BYTES = unsigned(HBLK * sizeof(T));
+  for (int64_t blk = b0 + wg; blk < b1; blk += nw) {
+    if (lane == 0) prefetch_l2(H + blk * HBLK, BLK_BYTES);
+    japply_block<T>(g, jp, H, mask, v, y, blk, lane);
+  }
 }
 
 // y = v at the Dirichlet DOFs of nodes [n0, n1) (their rows are identity;

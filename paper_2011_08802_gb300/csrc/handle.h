@@ -111,7 +111,10 @@ struct pfm_handle {
   // staging for the host-buffer entry point, and its slab pipeline
   void* stage_in = nullptr;
   void* stage_out = nullptr;
-  static constexpr int PIPE_SLABS = 8;
+#ifndef PFM_PIPE_SLABS
+#define PFM_PIPE_SLABS 8
+#endif
+  static constexpr int PIPE_SLABS = PFM_PIPE_SLABS;
   cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
   cudaEvent_t pipe_ev_in[PIPE_SLABS] = {}, pipe_ev_done[PIPE_SLABS] = {};
   cudaEvent_t pipe_ev_start = nullptr;

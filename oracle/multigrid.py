@@ -97,3 +97,24 @@ def nested_coarse_mask(fine_dims, fine_mask: np.ndarray) -> np.ndarray:
     nf = fine_mask.shape[0]
     m = fine_mask.reshape(nf, nz + 1, ny + 1, nx + 1)
     return np.ascontiguousarray(m[:, ::2, ::2, ::2].reshape(nf, -1))
+
+
+def nearest_fine_index(I: int, n_coarse: int, n_fine: int) -> int:
+    """Index of the fine node nearest to coarse node I along one axis of the
+    same box (coarse node at I / n_coarse, fine nodes at i / n_fine): the
+    nearest integer to I n_fine / n_coarse, a coarse node exactly midway
+    between two fine nodes taking the one of larger index."""
+    return (2 * I * n_fine + n_coarse) // (2 * n_coarse)
+
+
+def coarse_mask(fine_dims, coarse_dims, fine_mask: np.ndarray) -> np.ndarray:
+    """Dirichlet mask of the next level (reading r16): a coarse DOF is
+    prescribed when the DOF of the nearest fine node is."""
+    nf = fine_mask.shape[0]
+    fx, fy, fz = fine_dims
+    cx, cy, cz = coarse_dims
+    m = fine_mask.reshape(nf, fz + 1, fy + 1, fx + 1)
+    ii = [nearest_fine_index(I, cx, fx) for I in range(cx + 1)]
+    jj = [nearest_fine_index(J, cy, fy) for J in range(cy + 1)]
+    kk = [nearest_fine_index(K, cz, fz) for K in range(cz + 1)]
+    return np.ascontiguousarray(m[:, kk][:, :, jj][:, :, :, ii].reshape(nf, -1))

@@ -2,8 +2,9 @@
 Jacobi smoothing, restriction, prolongation, the dense coarse inverse, on
 re-discretised levels) against the oracle's V-cycle (oracle/multigrid.py) on
 the same state, right-hand side and smoother eigenvalue estimates (GPU
-tests): nested two- and three-level hierarchies with the penalty branch
-active. The smoother's lambda_max is an input of the method, read from the
+tests): nested two- and three-level hierarchies and non-nested ones (odd
+grid dimensions: coarse states by Q1 interpolation, coarse Dirichlet DOFs by
+the nearest fine node), with the penalty branch active. The smoother's lambda_max is an input of the method, read from the
 library (pfm_get_level) and handed to the oracle."""
 import numpy as np
 import pytest
@@ -36,7 +37,7 @@ def _oracle_levels(st, n_levels, lams):
         if l > 0:
             U = transfer.inject(dims[l - 1], d, U)
             Un = transfer.inject(dims[l - 1], d, Un)
-            mask = mg.nested_coarse_mask(dims[l - 1], mask)
+            mask = mg.coarse_mask(dims[l - 1], d, mask)
         mesh = inputs.Mesh(d[0], d[1], d[2], m.Lx, m.Ly, m.Lz)
         s = inputs.State(mesh, U, Un, mask, st.tau, st.material)
         K = fe.tangent(fe.Discretisation(mesh), s, mat)
@@ -48,7 +49,7 @@ def _oracle_levels(st, n_levels, lams):
     return levels
 
 
-@pytest.mark.parametrize("dims, n_levels", [((6, 4, 4), 2), ((8, 4, 4), 3)])
+@pytest.mark.parametrize("dims, n_levels", [((6, 4, 4), 2), ((8, 4, 4), 3), ((9, 7, 6), 2), ((10, 6, 5), 3)])
 def test_vcycle_matches_oracle(binding, dims, n_levels):
     nx, ny, nz = dims
     st = inputs.config_random(nx, ny, nz, seed=40 + nx, eta_lo=-0.02, eta_hi=0.3,

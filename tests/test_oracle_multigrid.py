@@ -91,3 +91,23 @@ def test_one_level_is_the_exact_solve_and_block_inverses():
     f = np.arange(2 * 27).reshape(2, 27).astype(np.uint8) % 2
     np.testing.assert_array_equal(mg.nested_coarse_mask((2, 2, 2), f), f[:, [0, 2, 6, 8, 18, 20, 24, 26]])
     np.testing.assert_allclose(transfer.prolongation((2, 2, 2), (1, 1, 1))[[0, 2, 6, 8, 18, 20, 24, 26]], np.eye(8))
+
+
+def test_coarse_mask_nearest_fine_node():
+    # one axis: 9 -> 5 elements puts coarse nodes at 0, 1.8, 3.6, 5.4, 7.2, 9 fine spacings
+    assert [mg.nearest_fine_index(I, 5, 9) for I in range(6)] == [0, 2, 4, 5, 7, 9]
+    # 3 -> 2: the middle coarse node lies midway between fine nodes 1 and 2
+    assert [mg.nearest_fine_index(I, 2, 3) for I in range(3)] == [0, 2, 3]
+    # nested grids: the coincident node
+    rng = np.random.default_rng(1)
+    f = (rng.random((3, 5 * 3 * 7)) < 0.4).astype(np.uint8)  # fine grid (4, 2, 6)
+    np.testing.assert_array_equal(mg.coarse_mask((4, 2, 6), (2, 1, 3), f), mg.nested_coarse_mask((4, 2, 6), f))
+    # a non-nested 3-D case checked node by node against the coordinates
+    f = (rng.random((2, 10 * 8 * 7)) < 0.3).astype(np.uint8)  # fine grid (9, 7, 6)
+    c = mg.coarse_mask((9, 7, 6), (5, 4, 3), f)
+    for K in range(4):
+        for J in range(5):
+            for I in range(6):
+                x, y, z = I * 9 / 5, J * 7 / 4, K * 6 / 3
+                i, j, k = (int(np.floor(t + 0.5)) for t in (x, y, z))
+                np.testing.assert_array_equal(c[:, I + 6 * (J + 5 * K)], f[:, i + 10 * (j + 8 * k)])

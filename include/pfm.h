@@ -366,6 +366,20 @@ pfm_status pfm_residual(pfm_handle* h, double* R_dev, double* energy_host);
  * entries met by the binary16 copy), PFM_ERR_CUDA. */
 pfm_status pfm_linearize(pfm_handle* h, pfm_precision precond);
 
+/* pfm_linearize and pfm_residual of the same state in one pass over the
+ * elements (Sec. 3.4: the Newton iteration needs both at its starting state,
+ * and both evaluate the same point physics): R_dev (device double
+ * [9][n_nodes], zero at Dirichlet DOFs) and, if energy_host != NULL, the
+ * potential (synchronises), as pfm_residual returns them, and the tangent as
+ * pfm_linearize leaves it. Formed in one pass when the residual and the
+ * finest-level linearisation use the same arithmetic (both FP64, the
+ * default, or both double-float: pfm_set_residual_arithmetic,
+ * pfm_set_linearize_arithmetic), else by the two calls in turn.
+ * pfm_newton_solve takes its first residual this way.
+ * Errors: as pfm_linearize and pfm_residual (PFM_ERR_INVALID_ARG for a NULL
+ * R_dev or an unknown precision). */
+pfm_status pfm_linearize_residual(pfm_handle* h, pfm_precision precond, double* R_dev, double* energy_host);
+
 /* y = J v with J = dR/dU at the last linearisation (Eq. linAlgEq), matrix
  * free from the stored Gauss-point Hessians; v_dev, y_dev are device arrays
  * [9][n_nodes] of float (PFM_F32) or double (PFM_F64). FP32 needs an FP32

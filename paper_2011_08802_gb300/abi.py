@@ -244,6 +244,7 @@ def lib(n_var: int = 6):
         "pfm_set_preconditioner_store": (i32, [H, i32]),
         "pfm_contact_load": (i32, [H, C.POINTER(dp), C.POINTER(dp)]),
         "pfm_linearize": (i32, [H, i32]),
+        "pfm_linearize_residual": (i32, [H, i32, vp, C.POINTER(dp)]),
         "pfm_jacobian_apply": (i32, [H, vp, vp, i32]),
         "pfm_jacobian_transpose_apply": (i32, [H, vp, vp, i32]),
         "pfm_jacobian_apply_host": (i32, [H, vp, vp, i32]),
@@ -292,7 +293,7 @@ def exported_symbols():
     return [
         "pfm_version", "pfm_variants", "pfm_create", "pfm_destroy", "pfm_last_error", "pfm_get_sizes",
         "pfm_set_stream", "pfm_get_level", "pfm_set_power_iterations", "pfm_set_outer_operator", "pfm_set_deterministic", "pfm_set_params", "pfm_set_dirichlet", "pfm_set_state", "pfm_get_state",
-        "pfm_residual", "pfm_diagnostics", "pfm_set_contact", "pfm_contact_load", "pfm_set_linearize_arithmetic", "pfm_set_residual_arithmetic", "pfm_set_preconditioner_store", "pfm_linearize", "pfm_jacobian_apply", "pfm_jacobian_transpose_apply",
+        "pfm_residual", "pfm_diagnostics", "pfm_set_contact", "pfm_contact_load", "pfm_set_linearize_arithmetic", "pfm_set_residual_arithmetic", "pfm_set_preconditioner_store", "pfm_linearize", "pfm_linearize_residual", "pfm_jacobian_apply", "pfm_jacobian_transpose_apply",
         "pfm_jacobian_apply_host", "pfm_jacobian_apply_mixed", "pfm_vcycle", "pfm_fgmres_solve", "pfm_newton_solve",
         "pfm_qp_eval", "pfm_get_hessians", "pfm_get_block_inverses", "pfm_profile_enable", "pfm_profile_get",
         "pfm_launch_count", "pfm_arith_peak", "pfm_param_grad", "pfm_batch_create", "pfm_batch_destroy",

@@ -181,6 +181,13 @@ class Problem:
     def linearize(self, precond: int = PFM_F32):
         self._check(self._lib.pfm_linearize(self.h, precond))
 
+    def linearize_residual(self, precond: int = PFM_F32, R: torch.Tensor | None = None, energy: bool = False):
+        """linearize and residual of the same state in one pass."""
+        R = torch.empty(self.shape, dtype=torch.float64, device="cuda") if R is None else R
+        e = C.c_double()
+        self._check(self._lib.pfm_linearize_residual(self.h, precond, _ptr(R), C.byref(e) if energy else None))
+        return (R, e.value) if energy else R
+
     def jacobian_apply(self, v: torch.Tensor, y: torch.Tensor | None = None) -> torch.Tensor:
         y = torch.empty_like(v) if y is None else y
         self._check(self._lib.pfm_jacobian_apply(self.h, _ptr(v), _ptr(y), _prec(v.dtype)))

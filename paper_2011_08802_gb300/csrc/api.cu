@@ -374,7 +374,14 @@ pfm_status bd_scratch(pfm_handle* h, size_t bytes) {
   return PFM_OK;
 }
 
-pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
+// Residual of the finest level formed by its linearisation pass (both in the
+// same FP64-class arithmetic): the two share the point physics of the state.
+bool residual_fusable(const pfm_handle* h) { return h->res_df == h->lin_df; }
+
+// R_fused: when set (residual_fusable), the finest level's linearisation also
+// writes the residual of the state into R_fused (and the energy into
+// energy_dev), as residual_impl would.
+pfm_status linearize_impl(pfm_handle* h, pfm_precision prec, double* R_fused = nullptr) {
   cudaStream_t s = h->stream;
   if (h->vgraph) {  // smoother coefficients change with the eigenvalue estimates
     cudaGraphExecDestroy(h->vgraph);
@@ -407,8 +414,17 @@ pfm_status linearize_impl(pfm_handle* h, pfm_precision prec) {
       // the others FP64-class ones (FP64 or double-float arithmetic)
       const bool fp32_compute = !fine && !coarsest && prec == PFM_F32;
       const int arith = fp32_compute ? LIN_F32 : (h->lin_df ? LIN_DF : LIN_F64);
-      launch_linearize(lv.g, h->dp, lv.U, lv.Un, need64 ? lv.H64 : nullptr, need32 ? lv.H32 : nullptr,
-                       needlo ? lv.H32lo : nullptr, arith, s);
+      if (fine && R_fused) {
+        if (!h->det) CK(cudaMemsetAsync(R_fused, 0, sizeof(double) * ndof(lv), s));
+        CK(cudaMemsetAsync(h->energy_dev, 0, sizeof(double), s));
+        const LinResidual res{lv.mask, R_fused, h->energy_dev, det_W<double>(h)};
+        launch_linearize(lv.g, h->dp, lv.U, lv.Un, need64 ? lv.H64 : nullptr, need32 ? lv.H32 : nullptr,
+                         needlo ? lv.H32lo : nullptr, arith, s, &res);
+        if (h->contact_on) launch_contact_residual(lv.g, h->contact, lv.U, lv.mask, R_fused, h->energy_dev, nullptr, s);
+      } else {
+        launch_linearize(lv.g, h->dp, lv.U, lv.Un, need64 ? lv.H64 : nullptr, need32 ? lv.H32 : nullptr,
+                         needlo ? lv.H32lo : nullptr, arith, s);
+      }
     }
     CKL_AT("Gauss-point Hessians");
     lv.h16_scale = 0.f;
@@ -1342,6 +1358,22 @@ pfm_status pfm_linearize(pfm_handle* h, pfm_precision precond) {
   return linearize_impl(h, precond);
 }
 
+pfm_status pfm_linearize_residual(pfm_handle* h, pfm_precision precond, double* R_dev, double* energy_host) {
+  TRY(check_ready(h, false));
+  if (precond != PFM_F32 && precond != PFM_F64) return h->fail(PFM_ERR_INVALID_ARG, "bad precision");
+  if (!R_dev) return h->fail(PFM_ERR_INVALID_ARG, "null output");
+  if (!residual_fusable(h)) {
+    TRY(residual_impl(h, R_dev, energy_host));
+    return linearize_impl(h, precond);
+  }
+  TRY(linearize_impl(h, precond, R_dev));
+  if (energy_host) {
+    CK(cudaMemcpyAsync(energy_host, h->energy_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return PFM_OK;
+}
+
 pfm_status pfm_jacobian_apply(pfm_handle* h, const void* v_dev, void* y_dev, pfm_precision prec) {
   TRY(check_ready(h, true));
   if (!v_dev || !y_dev || v_dev == y_dev) return h->fail(PFM_ERR_INVALID_ARG, "null or aliased vectors");
@@ -1445,18 +1477,37 @@ pfm_status pfm_newton_solve(pfm_handle* h, const pfm_solve_opts* opts, double* U
   if (h->have_dirval) launch_mask_values(f.nn, f.mask, h->dirval, f.U, s);
   h->linearized = false;
   double t0 = now_ms();
-  TRY(residual_impl(h, h->R, nullptr));
+  // The first iteration linearises at the starting state whatever its
+  // residual (only a zero residual ends the solve before it), so that
+  // residual comes out of the linearisation pass (Sec. 3.4: both evaluate the
+  // point physics of the same state).
+  const bool fused = opts->max_newton > 0 && residual_fusable(h);
   double res = 0.0;
-  TRY(norm2(h, h->R, n, &res));
-  rep.ms_residual += now_ms() - t0;
-  rep.res0 = res;
   pfm_status st = PFM_OK;
-  if (!std::isfinite(res)) st = h->fail(PFM_ERR_NONFINITE, "non-finite residual");
+  if (fused) {
+    st = linearize_impl(h, opts->precond, h->R);
+    rep.ms_linearize += now_ms() - t0;
+    TRY(norm2(h, h->R, n, &res));
+    if (st != PFM_OK && (res == 0.0 || !std::isfinite(res))) {
+      // a failed linearisation of a state with a zero or non-finite residual
+      // reports what the residual says
+      h->linearized = false;
+      st = PFM_OK;
+    }
+  } else {
+    TRY(residual_impl(h, h->R, nullptr));
+    TRY(norm2(h, h->R, n, &res));
+    rep.ms_residual += now_ms() - t0;
+  }
+  rep.res0 = res;
+  if (st == PFM_OK && !std::isfinite(res)) st = h->fail(PFM_ERR_NONFINITE, "non-finite residual");
   for (int it = 0; st == PFM_OK && it < opts->max_newton; ++it) {
     if (res == 0.0 || (it > 0 && res <= opts->newton_rtol * rep.res0)) break;
-    t0 = now_ms();
-    st = linearize_impl(h, opts->precond);
-    rep.ms_linearize += now_ms() - t0;
+    if (!(fused && it == 0)) {
+      t0 = now_ms();
+      st = linearize_impl(h, opts->precond);
+      rep.ms_linearize += now_ms() - t0;
+    }
     if (st != PFM_OK) break;
     // J dU = b with b = -R (R negated in place; the solver uses wv/rv/zd as work)
     t0 = now_ms();

@@ -136,8 +136,18 @@ void launch_residual(const Grid& g, const DevParams& P, const double* U, const d
                      bool df = false);
 // arithmetic of the point physics in the linearisation
 enum { LIN_F64 = 0, LIN_F32 = 1, LIN_DF = 2 };
+// optional residual of the same state formed in the linearisation pass (FP64
+// and double-float arithmetic): R (zeroed by the caller unless W is set),
+// energy (optional), W the atomic-free scratch as for launch_residual
+struct LinResidual {
+  const dmask_t* mask;
+  double* R;
+  double* energy;
+  double* W;
+};
 void launch_linearize(const Grid& g, const DevParams& P, const double* U, const double* Un,
-                      double* H64, float* H32, float* H32lo, int arith, cudaStream_t s);
+                      double* H64, float* H32, float* H32lo, int arith, cudaStream_t s,
+                      const LinResidual* res = nullptr);
 void launch_japply_df(const Grid& g, const DevParams& P, const float* Hhi, const float* Hlo, const dmask_t* mask,
                       const float* v, double* y, cudaStream_t s, double* W = nullptr);
 template <typename T>

@@ -165,15 +165,23 @@ struct JParams {
   T w, ihx, ihy, ihz;
 };
 
+struct NoLinTail {
+  template <typename TC>
+  __device__ void operator()(const TC*, const TC*, TC, int64_t, bool, int) const {}
+};
+
 // Gauss-point Hessians of element block blk (this warp; lane = 8 e + q),
 // computed in TC (FP64 for the finest and the coarsest level, FP32 for the
 // intermediate levels of an FP32 preconditioner) and stored in the requested
-// precisions (null stores are skipped).
-template <typename TC>
+// precisions (null stores are skipped). tail(ge, gr, W, node, valid, l8)
+// sees the point's eta gradients, energy gradient and energy density (the
+// residual of the same state can be formed from them without a second
+// evaluation of the point physics).
+template <typename TC, typename Tail = NoLinTail>
 __device__ __forceinline__ void linearize_lane(const Grid& g, const DevParams& P, const double* __restrict__ U,
                                                const double* __restrict__ Un, double* __restrict__ H64,
                                                float* __restrict__ H32, float* __restrict__ H32lo, int64_t blk,
-                                               int lane) {
+                                               int lane, const Tail& tail = Tail{}) {
   const int64_t e = blk * 4 + (lane >> 3);
   const int l8 = lane & 7;
   const bool valid = e < g.ne();
@@ -186,6 +194,7 @@ __device__ __forceinline__ void linearize_lane(const Grid& g, const DevParams& P
   for (int k = 0; k < NV; ++k) ehn[k] = q1_value(valid ? TC(Un[(3 + k) * nn + node]) : TC(0));
   TC W, gr[NZ], Hp[NH];
   qp_local<TC, true>(P, F, eh, ehn, &W, gr, Hp);
+  tail(ge, gr, W, node, valid, l8);
   for (int j = 0; j < NHP; ++j) {  // padding entries NH..NHP-1 are stored as zeros
     const double h = (valid && j < NH) ? double(Hp[j < NH ? j : 0]) : 0.0;
     if (H64) H64[hstore_offset<double>(blk, j, lane)] = h;

@@ -34,27 +34,17 @@ namespace {
 #ifndef PFM_RES_MINB
 #define PFM_RES_MINB 2
 #endif
+// Residual rows and energy of one Gauss point (lane = 8 e + q of block blk)
+// from its eta gradients ge, energy gradient gr and energy density Wd: the
+// gradient-energy flux G grad eta, the nodal rows scattered (DET: to the
+// scratch W) with Dirichlet rows left out, the energy summed per warp.
 template <typename TC, bool DET>
-__global__ void __launch_bounds__(128, PFM_RES_MINB) k_residual(Grid g, DevParams P, const double* __restrict__ U,
-                                                  const double* __restrict__ Un,
-                                                  const dmask_t* __restrict__ mask,
-                                                  double* __restrict__ R, double* energy, double* __restrict__ W,
-                                                  int64_t ws) {
-  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t e = tid >> 3;
-  const int l8 = int(tid & 7);
-  const int64_t blk = tid >> 5;
-  const int lane = int(tid & 31);
-  const bool valid = e < g.ne();
+__device__ __forceinline__ void residual_tail(const Grid& g, const DevParams& P, const TC* ge, const TC* gr, TC Wd,
+                                              int64_t node, bool valid, int l8, int64_t blk, int lane,
+                                              const dmask_t* __restrict__ mask, double* __restrict__ R,
+                                              double* energy, double* __restrict__ W, int64_t ws) {
   const int64_t nn = g.nn();
-  const int64_t node = valid ? elem_node(g, e, l8) : 0;
   const TC ihx = TC(1.0 / g.hx), ihy = TC(1.0 / g.hy), ihz = TC(1.0 / g.hz);
-  TC F[9], eh[NV], ge[3 * NV], ehn[NV];
-  gather_state<TC>(U, nn, node, valid, l8, ihx, ihy, ihz, F, eh, ge);
-#pragma unroll
-  for (int k = 0; k < NV; ++k) ehn[k] = q1_value(valid ? TC(Un[(3 + k) * nn + node]) : TC(0.0));
-  TC Wd, gr[NZ];
-  qp_local<TC, false>(P, F, eh, ehn, &Wd, gr, nullptr);
   TC gf[3 * NV];
   TC Wg = TC(0.0);
 #pragma unroll
@@ -91,6 +81,30 @@ __global__ void __launch_bounds__(128, PFM_RES_MINB) k_residual(Grid g, DevParam
   }
 }
 
+template <typename TC, bool DET>
+__global__ void __launch_bounds__(128, PFM_RES_MINB) k_residual(Grid g, DevParams P, const double* __restrict__ U,
+                                                  const double* __restrict__ Un,
+                                                  const dmask_t* __restrict__ mask,
+                                                  double* __restrict__ R, double* energy, double* __restrict__ W,
+                                                  int64_t ws) {
+  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t e = tid >> 3;
+  const int l8 = int(tid & 7);
+  const int64_t blk = tid >> 5;
+  const int lane = int(tid & 31);
+  const bool valid = e < g.ne();
+  const int64_t nn = g.nn();
+  const int64_t node = valid ? elem_node(g, e, l8) : 0;
+  const TC ihx = TC(1.0 / g.hx), ihy = TC(1.0 / g.hy), ihz = TC(1.0 / g.hz);
+  TC F[9], eh[NV], ge[3 * NV], ehn[NV];
+  gather_state<TC>(U, nn, node, valid, l8, ihx, ihy, ihz, F, eh, ge);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) ehn[k] = q1_value(valid ? TC(Un[(3 + k) * nn + node]) : TC(0.0));
+  TC Wd, gr[NZ];
+  qp_local<TC, false>(P, F, eh, ehn, &Wd, gr, nullptr);
+  residual_tail<TC, DET>(g, P, ge, gr, Wd, node, valid, l8, blk, lane, mask, R, energy, W, ws);
+}
+
 // Node pass of the atomic-free scatter (node_gather) over all nodes.
 template <typename TW, typename TV, typename TY>
 __global__ void __launch_bounds__(128) k_node_gather(Grid g, const TW* __restrict__ W, int64_t ws,
@@ -122,15 +136,33 @@ __global__ void __launch_bounds__(1024) k_sum_fixed(int64_t n, const double* __r
 // element blocks with a grid stride, so the launch can bound the number of
 // resident threads (and with it the footprint of the per-thread stack of the
 // point physics, which then stays in L2).
+// With R set (FP64-class TC only), the same pass also forms the residual
+// and energy of the state (as k_residual: atomics into R and *energy, or with
+// RW set the atomic-free scratch for the node pass).
 template <typename TC>
 __global__ void __launch_bounds__(128) k_linearize(Grid g, DevParams P, const double* __restrict__ U,
                                                    const double* __restrict__ Un,
                                                    double* __restrict__ H64, float* __restrict__ H32,
-                                                   float* __restrict__ H32lo) {
+                                                   float* __restrict__ H32lo, const dmask_t* __restrict__ mask,
+                                                   double* __restrict__ R, double* energy,
+                                                   double* __restrict__ RW) {
   const int64_t w0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int lane = int(threadIdx.x & 31);
+  const int64_t ws = g.nblk() * 32;
   for (int64_t blk = w0; blk < g.nblk(); blk += nw)  // whole warps only (padding lanes stay)
-    linearize_lane<TC>(g, P, U, Un, H64, H32, H32lo, blk, int(threadIdx.x & 31));
+    linearize_lane<TC>(g, P, U, Un, H64, H32, H32lo, blk, lane,
+                       [&](const TC* ge, const TC* gr, TC Wd, int64_t node, bool valid, int l8) {
+                         if constexpr (!std::is_same<TC, float>::value) {
+                           if (R == nullptr) return;  // warp-uniform
+                           if (RW)
+                             residual_tail<TC, true>(g, P, ge, gr, Wd, node, valid, l8, blk, lane, mask, R,
+                                                     energy, RW, ws);
+                           else
+                             residual_tail<TC, false>(g, P, ge, gr, Wd, node, valid, l8, blk, lane, mask, R,
+                                                      energy, nullptr, 0);
+                         }
+                       });
 }
 
 // Resident CTAs per SM of the FP64-class linearisation (0: one warp per
@@ -539,20 +571,35 @@ void launch_residual(const Grid& g, const DevParams& P, const double* U, const d
 }
 
 void launch_linearize(const Grid& g, const DevParams& P, const double* U, const double* Un,
-                      double* H64, float* H32, float* H32lo, int arith, cudaStream_t s) {
+                      double* H64, float* H32, float* H32lo, int arith, cudaStream_t s, const LinResidual* res) {
   const int64_t threads = g.nblk() * 32;
   unsigned blocks = grid_for(threads, 128);
   if (arith != LIN_F32 && PFM_LIN_CTAS_PER_SM > 0) {
     const int64_t cap = int64_t(sm_count()) * PFM_LIN_CTAS_PER_SM;
     if (int64_t(blocks) > cap) blocks = unsigned(cap);
   }
+  // the residual is formed in FP64-class arithmetic only
+  const bool with_res = res && res->R && arith != LIN_F32;
+  const dmask_t* mask = with_res ? res->mask : nullptr;
+  double* R = with_res ? res->R : nullptr;
+  double* energy = with_res ? res->energy : nullptr;
+  double* RW = with_res ? res->W : nullptr;
   if (arith == LIN_F32)
-    k_linearize<float><<<blocks, 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo);
+    k_linearize<float><<<blocks, 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo, nullptr, nullptr, nullptr, nullptr);
   else if (arith == LIN_DF)
-    k_linearize<df64><<<blocks, 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo);
+    k_linearize<df64><<<blocks, 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo, mask, R, energy, RW);
   else
-    k_linearize<double><<<blocks, 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo);
+    k_linearize<double><<<blocks, 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo, mask, R, energy, RW);
   count_launches(1);
+  if (RW) {  // node pass of the atomic-free form, as in launch_residual
+    const int64_t ws = g.nblk() * 32;
+    k_node_gather<double, double, double><<<grid_for(g.nn(), 128), 128, 0, s>>>(g, RW, ws, mask, nullptr, R);
+    count_launches(1);
+    if (energy) {
+      k_sum_fixed<<<1, 1024, 0, s>>>(g.nblk(), RW + NF * ws, energy);
+      count_launches(1);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

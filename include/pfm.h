@@ -372,9 +372,9 @@ pfm_status pfm_linearize(pfm_handle* h, pfm_precision precond);
  * [9][n_nodes], zero at Dirichlet DOFs) and, if energy_host != NULL, the
  * potential (synchronises), as pfm_residual returns them, and the tangent as
  * pfm_linearize leaves it. Formed in one pass when the residual and the
- * finest-level linearisation use the same arithmetic (both FP64, the
- * default, or both double-float: pfm_set_residual_arithmetic,
- * pfm_set_linearize_arithmetic), else by the two calls in turn.
+ * finest-level linearisation both use FP64 arithmetic (the default; see
+ * pfm_set_residual_arithmetic, pfm_set_linearize_arithmetic), else by the two
+ * calls in turn.
  * pfm_newton_solve takes its first residual this way.
  * Errors: as pfm_linearize and pfm_residual (PFM_ERR_INVALID_ARG for a NULL
  * R_dev or an unknown precision). */

@@ -374,9 +374,9 @@ pfm_status bd_scratch(pfm_handle* h, size_t bytes) {
   return PFM_OK;
 }
 
-// Residual of the finest level formed by its linearisation pass (both in the
-// same FP64-class arithmetic): the two share the point physics of the state.
-bool residual_fusable(const pfm_handle* h) { return h->res_df == h->lin_df; }
+// Residual of the finest level formed by its linearisation pass (both in FP64
+// arithmetic): the two share the point physics of the state.
+bool residual_fusable(const pfm_handle* h) { return !h->res_df && !h->lin_df; }
 
 // R_fused: when set (residual_fusable), the finest level's linearisation also
 // writes the residual of the state into R_fused (and the energy into

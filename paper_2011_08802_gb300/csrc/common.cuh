@@ -136,9 +136,9 @@ void launch_residual(const Grid& g, const DevParams& P, const double* U, const d
                      bool df = false);
 // arithmetic of the point physics in the linearisation
 enum { LIN_F64 = 0, LIN_F32 = 1, LIN_DF = 2 };
-// optional residual of the same state formed in the linearisation pass (FP64
-// and double-float arithmetic): R (zeroed by the caller unless W is set),
-// energy (optional), W the atomic-free scratch as for launch_residual
+// optional residual of the same state formed in the linearisation pass
+// (arith == LIN_F64 only; ignored otherwise): R (zeroed by the caller unless W
+// is set), energy (optional), W the atomic-free scratch as for launch_residual
 struct LinResidual {
   const dmask_t* mask;
   double* R;

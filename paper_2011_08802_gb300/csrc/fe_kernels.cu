@@ -81,6 +81,16 @@ __device__ __forceinline__ void residual_tail(const Grid& g, const DevParams& P,
   }
 }
 
+// Out-of-line copy for the linearisation pass, so that the register
+// allocation of its point physics does not see the residual's scatter.
+template <typename TC, bool DET>
+__device__ __noinline__ void residual_tail_call(const Grid& g, const DevParams& P, const TC* ge, const TC* gr, TC Wd,
+                                                int64_t node, bool valid, int l8, int64_t blk, int lane,
+                                                const dmask_t* __restrict__ mask, double* __restrict__ R,
+                                                double* energy, double* __restrict__ W, int64_t ws) {
+  residual_tail<TC, DET>(g, P, ge, gr, Wd, node, valid, l8, blk, lane, mask, R, energy, W, ws);
+}
+
 template <typename TC, bool DET>
 __global__ void __launch_bounds__(128, PFM_RES_MINB) k_residual(Grid g, DevParams P, const double* __restrict__ U,
                                                   const double* __restrict__ Un,
@@ -136,10 +146,11 @@ __global__ void __launch_bounds__(1024) k_sum_fixed(int64_t n, const double* __r
 // element blocks with a grid stride, so the launch can bound the number of
 // resident threads (and with it the footprint of the per-thread stack of the
 // point physics, which then stays in L2).
-// With R set (FP64-class TC only), the same pass also forms the residual
-// and energy of the state (as k_residual: atomics into R and *energy, or with
-// RW set the atomic-free scratch for the node pass).
-template <typename TC>
+// RES (FP64 only): the same pass also forms the residual and energy of the
+// state (as k_residual: atomics into R and *energy, or with RW set the
+// atomic-free scratch for the node pass); a separate instance, so that the
+// plain linearisation keeps its own register allocation.
+template <typename TC, bool RES = false>
 __global__ void __launch_bounds__(128) k_linearize(Grid g, DevParams P, const double* __restrict__ U,
                                                    const double* __restrict__ Un,
                                                    double* __restrict__ H64, float* __restrict__ H32,
@@ -149,20 +160,23 @@ __global__ void __launch_bounds__(128) k_linearize(Grid g, DevParams P, const do
   const int64_t w0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   const int lane = int(threadIdx.x & 31);
-  const int64_t ws = g.nblk() * 32;
-  for (int64_t blk = w0; blk < g.nblk(); blk += nw)  // whole warps only (padding lanes stay)
-    linearize_lane<TC>(g, P, U, Un, H64, H32, H32lo, blk, lane,
-                       [&](const TC* ge, const TC* gr, TC Wd, int64_t node, bool valid, int l8) {
-                         if constexpr (!std::is_same<TC, float>::value) {
-                           if (R == nullptr) return;  // warp-uniform
+  for (int64_t blk = w0; blk < g.nblk(); blk += nw) {  // whole warps only (padding lanes stay)
+    if constexpr (RES) {
+      static_assert(std::is_same<TC, double>::value, "residual pass in FP64 only");
+      const int64_t ws = g.nblk() * 32;
+      linearize_lane<TC>(g, P, U, Un, H64, H32, H32lo, blk, lane,
+                         [&](const TC* ge, const TC* gr, TC Wd, int64_t node, bool valid, int l8) {
                            if (RW)
-                             residual_tail<TC, true>(g, P, ge, gr, Wd, node, valid, l8, blk, lane, mask, R,
-                                                     energy, RW, ws);
+                             residual_tail_call<TC, true>(g, P, ge, gr, Wd, node, valid, l8, blk, lane, mask, R,
+                                                          energy, RW, ws);
                            else
-                             residual_tail<TC, false>(g, P, ge, gr, Wd, node, valid, l8, blk, lane, mask, R,
-                                                      energy, nullptr, 0);
-                         }
-                       });
+                             residual_tail_call<TC, false>(g, P, ge, gr, Wd, node, valid, l8, blk, lane, mask,
+                                                           R, energy, nullptr, 0);
+                         });
+    } else {
+      linearize_lane<TC>(g, P, U, Un, H64, H32, H32lo, blk, lane);
+    }
+  }
 }
 
 // Resident CTAs per SM of the FP64-class linearisation (0: one warp per
@@ -578,8 +592,8 @@ void launch_linearize(const Grid& g, const DevParams& P, const double* U, const 
     const int64_t cap = int64_t(sm_count()) * PFM_LIN_CTAS_PER_SM;
     if (int64_t(blocks) > cap) blocks = unsigned(cap);
   }
-  // the residual is formed in FP64-class arithmetic only
-  const bool with_res = res && res->R && arith != LIN_F32;
+  // the residual is formed in the FP64 pass only
+  const bool with_res = res && res->R && arith == LIN_F64;
   const dmask_t* mask = with_res ? res->mask : nullptr;
   double* R = with_res ? res->R : nullptr;
   double* energy = with_res ? res->energy : nullptr;
@@ -587,9 +601,11 @@ void launch_linearize(const Grid& g, const DevParams& P, const double* U, const 
   if (arith == LIN_F32)
     k_linearize<float><<<blocks, 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo, nullptr, nullptr, nullptr, nullptr);
   else if (arith == LIN_DF)
-    k_linearize<df64><<<blocks, 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo, mask, R, energy, RW);
+    k_linearize<df64><<<blocks, 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo, nullptr, nullptr, nullptr, nullptr);
+  else if (with_res)
+    k_linearize<double, true><<<blocks, 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo, mask, R, energy, RW);
   else
-    k_linearize<double><<<blocks, 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo, mask, R, energy, RW);
+    k_linearize<double><<<blocks, 128, 0, s>>>(g, P, U, Un, H64, H32, H32lo, nullptr, nullptr, nullptr, nullptr);
   count_launches(1);
   if (RW) {  // node pass of the atomic-free form, as in launch_residual
     const int64_t ws = g.nblk() * 32;

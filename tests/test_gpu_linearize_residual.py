@@ -1,11 +1,11 @@
 """Residual formed by the linearisation pass (GPU tests): pfm_linearize_residual
 (and the first residual of pfm_newton_solve) returns the residual and energy
 of Sec. 3.4, Eq. FinalRes, from the same pass over the elements that computes
-the Gauss-point Hessians. Checked against the oracle and the separate
-residual kernel in FP64 and double-float arithmetic, atomic and atomic-free;
-the tangent it leaves is the one pfm_linearize leaves (bitwise in the
-atomic-free form); with the residual and the linearisation in different
-arithmetic the call falls back to the two passes."""
+the Gauss-point Hessians (FP64 arithmetic; with double-float arithmetic in
+either the call falls back to the two passes). Checked against the oracle
+and the separate residual kernel, atomic and atomic-free, in both forms; the
+tangent it leaves is the one pfm_linearize leaves (bitwise in the atomic-free
+form)."""
 import numpy as np
 import pytest
 

@@ -155,7 +155,9 @@ typedef struct {
                             with krylov = 1 or 2 the FP64-class true residual */
   int lin_outer_last;    /* krylov = 1: FGMRES cycles (restarts + 1), krylov = 2: refinement
                             steps, of the last linear solve (0 with krylov = 0) */
-  double ms_residual, ms_linearize, ms_solve, ms_total; /* wall times (ms) */
+  double ms_residual, ms_linearize, ms_solve, ms_total; /* wall times (ms); the starting residual,
+                            when formed by the linearisation pass (pfm_linearize_residual), counts
+                            in ms_linearize */
   pfm_status status;
 } pfm_solve_report;
 
@@ -440,6 +442,8 @@ pfm_status pfm_fgmres_solve(pfm_handle* h, const pfm_solve_opts* opts, const dou
  * J dU = -R solved by pfm_fgmres_solve, until ||R|| <= newton_rtol ||R_0|| or
  * max_newton corrections. U_inout_dev (device double [9][n_nodes]) is the
  * initial iterate on entry and the result on exit; the handle's U_n stays.
+ * The first correction always linearises at U_0 (unless R(U_0) = 0), so R(U_0)
+ * comes from that linearisation pass (pfm_linearize_residual).
  * Synchronises; report (nullable) gets iteration counts, norms and times.
  * Errors: PFM_ERR_INVALID_ARG (NULL options or state vector), PFM_ERR_STATE
  * (no state), PFM_ERR_NOT_CONVERGED, PFM_ERR_NONFINITE, PFM_ERR_BREAKDOWN
